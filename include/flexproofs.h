@@ -1,0 +1,125 @@
+/*
+ * flexproofs.h -- C ABI of the GB300 (sm_103a) implementation of FlexProofs' all-proofs pass.
+ *
+ * FlexProofs (Liu, Zhang; arXiv 2601.03031) commits to a vector m of N = 2^n field elements in
+ * two layers: each of the R rows (length M) is committed with PST (a multilinear KZG), and the
+ * vector of row commitments C = (C_0 .. C_{R-1}) with the paper's functional commitment FC
+ * (Sec. 3).  VC.OpenAll (Protocol 1, Sec. 4.2) then produces all N opening proofs in O(N):
+ *   Step 1: one FC.BOpen per block S_k = [k b, (k+1) b) of C,
+ *   Step 2: Fiat-Shamir Merkle tree, randomised fold tree over the rows, PST HyperEval.
+ * Here R = 2^floor(n/2) and M = 2^ceil(n/2) (R = M = sqrt(N) when n is even, Sec. 4.1).
+ *
+ * Group: BLS12-381 (the paper used BN_SNARK1).  Every byte string crossing this ABI is canonical
+ * big-endian: Fr 32 B, G1 96 B (x || y), G2 192 B (x.c0 || x.c1 || y.c0 || y.c1), GT 576 B in the
+ * tower order of Fq12 = Fq6[w]/(w^2 - v), Fq6 = Fq2[v]/(v^3 - (1+u)).  The identity of G1/G2 is
+ * all zero bytes.  Vectors of Fr cross as N x 4 little-endian uint64 limbs of canonical values.
+ *
+ * Conventions of every call:
+ *   - `stream` is a cudaStream_t (NULL = the legacy default stream).  Work is enqueued on it; the
+ *     calls below that return data to the host synchronise that stream first.
+ *   - Handles are owned by the caller and released with the matching *_free (NULL is ignored).
+ *   - Device memory is allocated by the library (stream-ordered) and freed by *_free.
+ *   - On any error nothing is written to *out and no partially built handle is returned.
+ *   - All computation runs in this library's CUDA kernels on the current device; there is no
+ *     CPU fallback.  If no CUDA device is usable, calls fail with FP_EDEVICE.
+ */
+#ifndef FLEXPROOFS_H
+#define FLEXPROOFS_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct fp_pp fp_pp;           /* public parameters, device resident (VC.Setup, Eq. vcpp) */
+typedef struct fp_commit fp_commit;   /* C in GT, aux = row commitments, and the prover's copy of m */
+typedef struct fp_proofs fp_proofs;   /* the shared pieces of all N proofs, device resident */
+
+typedef enum {
+    FP_OK = 0,
+    FP_EINVAL = 1,     /* bad size, b out of range, NULL pointer, buffer too small */
+    FP_ENOMEM = 2,     /* device or host allocation failed */
+    FP_EDEVICE = 3,    /* a CUDA call failed (message via fp_last_error) */
+    FP_ETIMEOUT = 4,   /* a bounded device-side wait gave up */
+    FP_EVERIFY = 5,    /* a proof did not verify */
+    FP_ERANGE = 6      /* an input scalar was >= r */
+} fp_status;
+
+/* VC.Setup (Sec. 4.1, Eq. vcpp; FC.Setup of Sec. 3 with the faster-verification extras).
+ * Derives the trapdoor (beta, tau_0..tau_{l_c-1}) from SplitMix64 seeded with seed ^ 0x5eed5eed
+ * (beta first, then tau_t in order; each an Fr draw by rejection) and builds on the device:
+ *   Lambda_t[c] = g1^{prod_{s<t} (c_s tau_s + (1 - c_s)(1 - tau_s))}, t = 0..l_c  (2M - 1 points),
+ *   g1^beta, g2^{beta^i} for i < 2R - 1 (v_i = g2^{beta^{2i}} are the even ones), g2^{tau_t}.
+ * log_n in [2, 26]; b in [1, R] is only validated here (any b in that range may be used later).
+ * The trapdoor never leaves the device and is discarded before returning. */
+fp_status vc_setup(uint32_t log_n, uint32_t b, uint64_t seed, void* stream, fp_pp** out);
+
+/* Serialised public parameters (synchronises): Lambda (2M-1) x 96 || g1^beta 96 ||
+ * g2^{beta^i} (2R-1) x 192 || g2^{tau_t} l_c x 192.  *len receives the size; out may be NULL to
+ * query it. */
+fp_status vc_pp_export(const fp_pp* pp, uint8_t* out, size_t cap, size_t* len);
+fp_status vc_pp_dims(const fp_pp* pp, uint32_t* log_n, uint32_t* R, uint32_t* M);
+
+/* VC.Commit (Sec. 4.1, Eqs. genCi, genC): C_j = PC.Commit(f_j) = sum_a m[j M + a] Lambda_{l_c}[a]
+ * and C = FC.Commit(C) = prod_j e(C_j, g2^{beta^{2j}}).
+ * m: N x 4 little-endian uint64 canonical Fr values, on the host (on_device = 0, copied in) or on
+ * the current device (on_device = 1, borrowed only for the duration of the enqueued work).
+ * The returned handle keeps a device copy of m for OpenAll.  A value >= r gives FP_ERANGE
+ * (checked on the device; the call then synchronises). */
+fp_status vc_commit(const fp_pp* pp, const uint64_t* m, int on_device, void* stream, fp_commit** out);
+
+/* C (576 B) and, if rows != NULL, the R row commitments (R x 96 B).  Synchronises. */
+fp_status vc_commit_get(const fp_commit* cm, uint8_t* gt576, uint8_t* rows);
+
+/* VC.OpenAll (Protocol 1 with the unit-vector shortcut of Sec. 4.3 and the Merkle-tree
+ * Fiat-Shamir of Sec. 4.2) for batch size b in [1, R].  Enqueues all work and returns; the shared
+ * pieces stay on the device:
+ *   - per block k < ceil(R/b): pi_{C_k} = ({L_j, R_j}_{j=1..l_R}, A_l, v_l, W),
+ *   - the two-level Merkle tree, the fold tree (g_w, D_w for every node), the PST proofs of g*. */
+fp_status vc_prove_all(const fp_pp* pp, const fp_commit* cm, uint32_t b, void* stream, fp_proofs** out);
+
+/* Byte length of proof i under batch size b (no device work). */
+size_t vc_proof_len(const fp_pp* pp, uint32_t b, uint64_t i);
+
+/* Assemble pi_i (synchronises): block (C_a)_{a in S_k} || pi_{C_k} || Merkle path (l_c row-tree
+ * digests then l_R top-tree digests, leaf-up) || l_R sibling pairs (D_w 96 B, g_w[a] 32 B)
+ * leaf-up || PST proof (pi_{l_c-1} .. pi_0), with j = i / M, a = i mod M, k = j / b. */
+fp_status vc_proof_get(const fp_proofs* pf, uint64_t i, uint8_t* out, size_t cap, size_t* len);
+
+/* Assemble proofs i0 .. i0+count-1 back to back into `out` (host memory, synchronises).  Proof
+ * lengths differ only for the last, truncated block; *len receives the total byte count. */
+fp_status vc_proofs_export(const fp_proofs* pf, uint64_t i0, uint64_t count, uint8_t* out, size_t cap, size_t* len);
+
+/* Device-to-host copy of the shared proof state (synchronises), the compact result of OpenAll:
+ * all blocks' pi_{C_k}, every Merkle digest, every fold-tree node (D_w, g_w) and the PST proofs.
+ * *len receives the size; out may be NULL to query it. */
+fp_status vc_proofs_state(const fp_proofs* pf, uint8_t* out, size_t cap, size_t* len);
+
+/* Pieces for parity checks (synchronise): the Merkle root (32 B), r_j (R x 32 B), g* (M x 32 B)
+ * and D* (96 B); any pointer may be NULL. */
+fp_status vc_proofs_step2_parts(const fp_proofs* pf, uint8_t* root, uint8_t* rj, uint8_t* gstar, uint8_t* dstar);
+
+void fp_pp_free(fp_pp* pp);
+void fp_commit_free(fp_commit* cm);
+void fp_proofs_free(fp_proofs* pf);
+
+/* ---- diagnostics (no counterpart in the paper: bookkeeping for measurement) ----
+ * fp_launch_count: number of CUDA kernel launches this library has made in this process.
+ * fp_profile_enable: while on, every launch is bracketed by CUDA events on its stream.
+ * fp_profile_report: synchronises those events and writes "name launches total_ms" lines
+ * (NUL-terminated, truncated to cap) and returns the size needed; the totals are cleared only
+ * by a call that writes them out (out != NULL, cap > 0). */
+uint64_t fp_launch_count(void);
+void fp_profile_enable(int on);
+size_t fp_profile_report(char* out, size_t cap);
+
+const char* fp_strerror(fp_status s);
+/* Text of the last CUDA error seen by this thread's calls (empty if none). */
+const char* fp_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

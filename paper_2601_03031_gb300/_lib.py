@@ -1,0 +1,233 @@
+"""Thin ctypes binding of libflexproofs.so (include/flexproofs.h).  Argument marshalling only:
+every step of Setup, Commit and OpenAll runs in the library's CUDA kernels.  If the library is
+missing or no CUDA device is usable, calls raise -- there is no fallback path."""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libflexproofs.so")
+
+FP_STATUS = {0: "FP_OK", 1: "FP_EINVAL", 2: "FP_ENOMEM", 3: "FP_EDEVICE", 4: "FP_ETIMEOUT", 5: "FP_EVERIFY",
+             6: "FP_ERANGE"}
+
+EXPORTED = ["vc_setup", "vc_pp_export", "vc_pp_dims", "vc_commit", "vc_commit_get", "vc_prove_all",
+            "vc_proof_len", "vc_proof_get", "vc_proofs_export", "vc_proofs_state", "vc_proofs_step2_parts",
+            "fp_pp_free", "fp_commit_free", "fp_proofs_free", "fp_strerror", "fp_last_error", "fp_launch_count",
+            "fp_profile_enable", "fp_profile_report"]
+
+
+class FlexProofsError(RuntimeError):
+    def __init__(self, fn: str, status: int):
+        self.status = status
+        detail = ""
+        if _lib is not None:
+            detail = _lib.fp_last_error().decode(errors="replace")
+        super().__init__(f"{fn}: {FP_STATUS.get(status, status)}" + (f" ({detail})" if detail else ""))
+
+
+_lib = None
+
+
+def load(path: str = LIB_PATH):
+    """Load the library (raises if it was not built)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise FileNotFoundError(f"{path} is missing: run __graft_entry__.build() (nvcc, sm_103a) first")
+    L = ctypes.CDLL(path)
+    vp, u32, u64, sz = ctypes.c_void_p, ctypes.c_uint32, ctypes.c_uint64, ctypes.c_size_t
+    pp = ctypes.POINTER(vp)
+    L.vc_setup.argtypes = [u32, u32, u64, vp, pp]
+    L.vc_pp_export.argtypes = [vp, vp, sz, ctypes.POINTER(sz)]
+    L.vc_pp_dims.argtypes = [vp, ctypes.POINTER(u32), ctypes.POINTER(u32), ctypes.POINTER(u32)]
+    L.vc_commit.argtypes = [vp, vp, ctypes.c_int, vp, pp]
+    L.vc_commit_get.argtypes = [vp, vp, vp]
+    L.vc_prove_all.argtypes = [vp, vp, u32, vp, pp]
+    L.vc_proof_len.argtypes = [vp, u32, u64]
+    L.vc_proof_len.restype = sz
+    L.vc_proof_get.argtypes = [vp, u64, vp, sz, ctypes.POINTER(sz)]
+    L.vc_proofs_export.argtypes = [vp, u64, u64, vp, sz, ctypes.POINTER(sz)]
+    L.vc_proofs_state.argtypes = [vp, vp, sz, ctypes.POINTER(sz)]
+    L.vc_proofs_step2_parts.argtypes = [vp, vp, vp, vp, vp]
+    for n in ("fp_pp_free", "fp_commit_free", "fp_proofs_free"):
+        getattr(L, n).argtypes = [vp]
+        getattr(L, n).restype = None
+    L.fp_strerror.argtypes = [ctypes.c_int]
+    L.fp_strerror.restype = ctypes.c_char_p
+    L.fp_last_error.restype = ctypes.c_char_p
+    L.fp_launch_count.restype = ctypes.c_uint64
+    L.fp_profile_enable.argtypes = [ctypes.c_int]
+    L.fp_profile_enable.restype = None
+    L.fp_profile_report.argtypes = [ctypes.c_char_p, sz]
+    L.fp_profile_report.restype = sz
+    _lib = L
+    return L
+
+
+def _check(fn: str, st: int):
+    if st != 0:
+        raise FlexProofsError(fn, st)
+
+
+def _stream_ptr(stream) -> int | None:
+    if stream is None:
+        return None
+    if isinstance(stream, int):
+        return stream
+    return int(stream.cuda_stream)          # torch.cuda.Stream
+
+
+class PP:
+    """Handle of vc_setup's device-resident public parameters."""
+
+    def __init__(self, log_n: int, b: int = 1, seed: int = 0, stream=None):
+        L = load()
+        h = ctypes.c_void_p()
+        _check("vc_setup", L.vc_setup(log_n, b, seed, _stream_ptr(stream), ctypes.byref(h)))
+        self.h = h
+        ln, R, M = ctypes.c_uint32(), ctypes.c_uint32(), ctypes.c_uint32()
+        L.vc_pp_dims(h, ctypes.byref(ln), ctypes.byref(R), ctypes.byref(M))
+        self.log_n, self.R, self.M = ln.value, R.value, M.value
+        self.N = self.R * self.M
+        self.log_r = self.R.bit_length() - 1
+        self.log_c = self.M.bit_length() - 1
+
+    def export(self) -> bytes:
+        L = load()
+        n = ctypes.c_size_t()
+        _check("vc_pp_export", L.vc_pp_export(self.h, None, 0, ctypes.byref(n)))
+        buf = ctypes.create_string_buffer(n.value)
+        _check("vc_pp_export", L.vc_pp_export(self.h, buf, n.value, ctypes.byref(n)))
+        return buf.raw
+
+    def proof_len(self, b: int, i: int) -> int:
+        return load().vc_proof_len(self.h, b, i)
+
+    def __del__(self):
+        if getattr(self, "h", None) and _lib is not None:
+            _lib.fp_pp_free(self.h)
+            self.h = None
+
+
+class Commitment:
+    """Handle of vc_commit: C, the row commitments and the device copy of m."""
+
+    def __init__(self, pp: PP, m, stream=None):
+        L = load()
+        self.pp = pp
+        h = ctypes.c_void_p()
+        if hasattr(m, "data_ptr"):                       # torch tensor on the device (N x 4 int64)
+            assert m.is_cuda and m.is_contiguous() and m.numel() == 4 * pp.N
+            ptr, on_dev = m.data_ptr(), 1
+            self._keep = m
+        else:
+            arr = np.ascontiguousarray(m, dtype=np.uint64)
+            assert arr.size == 4 * pp.N
+            ptr, on_dev = arr.ctypes.data, 0
+            self._keep = arr
+        _check("vc_commit", L.vc_commit(pp.h, ptr, on_dev, _stream_ptr(stream), ctypes.byref(h)))
+        self.h = h
+
+    def get(self, rows: bool = True):
+        C = ctypes.create_string_buffer(576)
+        rb = ctypes.create_string_buffer(96 * self.pp.R) if rows else None
+        _check("vc_commit_get", load().vc_commit_get(self.h, C, rb))
+        return C.raw, (rb.raw if rows else None)
+
+    def __del__(self):
+        if getattr(self, "h", None) and _lib is not None:
+            _lib.fp_commit_free(self.h)
+            self.h = None
+
+
+class Proofs:
+    """Handle of vc_prove_all's device-resident shared proof pieces."""
+
+    def __init__(self, pp: PP, cm: Commitment, b: int, stream=None):
+        L = load()
+        self.pp, self.cm, self.b = pp, cm, b
+        h = ctypes.c_void_p()
+        _check("vc_prove_all", L.vc_prove_all(pp.h, cm.h, b, _stream_ptr(stream), ctypes.byref(h)))
+        self.h = h
+
+    def proof(self, i: int) -> bytes:
+        n = self.pp.proof_len(self.b, i)
+        buf = ctypes.create_string_buffer(n)
+        ln = ctypes.c_size_t()
+        _check("vc_proof_get", load().vc_proof_get(self.h, i, buf, n, ctypes.byref(ln)))
+        return buf.raw[: ln.value]
+
+    def export(self, i0: int, count: int) -> bytes:
+        L = load()
+        ln = ctypes.c_size_t()
+        _check("vc_proofs_export", L.vc_proofs_export(self.h, i0, count, None, 0, ctypes.byref(ln)))
+        buf = ctypes.create_string_buffer(ln.value)
+        _check("vc_proofs_export", L.vc_proofs_export(self.h, i0, count, buf, ln.value, ctypes.byref(ln)))
+        return buf.raw
+
+    def state_size(self) -> int:
+        ln = ctypes.c_size_t()
+        _check("vc_proofs_state", load().vc_proofs_state(self.h, None, 0, ctypes.byref(ln)))
+        return ln.value
+
+    def state_into(self, host_buf) -> int:
+        """Copy the shared proof state into a preallocated host buffer (numpy uint8 / pinned)."""
+        ln = ctypes.c_size_t()
+        ptr = host_buf.ctypes.data if hasattr(host_buf, "ctypes") else host_buf.data_ptr()
+        cap = host_buf.nbytes if hasattr(host_buf, "nbytes") else host_buf.numel()
+        _check("vc_proofs_state", load().vc_proofs_state(self.h, ptr, cap, ctypes.byref(ln)))
+        return ln.value
+
+    def step2_parts(self):
+        R, M = self.pp.R, self.pp.M
+        root, rj, gs, ds = (ctypes.create_string_buffer(n) for n in (32, 32 * R, 32 * M, 96))
+        _check("vc_proofs_step2_parts", load().vc_proofs_step2_parts(self.h, root, rj, gs, ds))
+        return root.raw, rj.raw, gs.raw, ds.raw
+
+    def __del__(self):
+        if getattr(self, "h", None) and _lib is not None:
+            _lib.fp_proofs_free(self.h)
+            self.h = None
+
+
+# names of the C ABI, for callers who prefer them
+def vc_setup(log_n: int, b: int = 1, seed: int = 0, stream=None) -> PP:
+    return PP(log_n, b, seed, stream)
+
+
+def vc_commit(pp: PP, m, stream=None) -> Commitment:
+    return Commitment(pp, m, stream)
+
+
+def vc_prove_all(pp: PP, cm: Commitment, b: int, stream=None) -> Proofs:
+    return Proofs(pp, cm, b, stream)
+
+
+def vc_proof_get(pf: Proofs, i: int) -> bytes:
+    return pf.proof(i)
+
+
+def launch_count() -> int:
+    return int(load().fp_launch_count())
+
+
+def profile_enable(on: bool = True) -> None:
+    load().fp_profile_enable(int(on))
+
+
+def profile_report() -> dict:
+    """{kernel name: (launches, total_ms)} since the last report (synchronises)."""
+    L = load()
+    n = L.fp_profile_report(None, 0)
+    buf = ctypes.create_string_buffer(n)
+    L.fp_profile_report(buf, n)
+    out = {}
+    for line in buf.value.decode().splitlines():
+        name, cnt, ms = line.split()
+        out[name] = (int(cnt), float(ms))
+    return out

@@ -1,0 +1,239 @@
+// Prime-field arithmetic for the BLS12-381 base field Fq (12 x 32-bit limbs) and scalar field
+// Fr (8 x 32-bit limbs), Montgomery form with R = 2^(32 N), little-endian limbs.
+//
+// Every multiply is a CIOS Montgomery product written as explicit PTX carry chains
+// (mad.lo/hi.cc, madc.lo/hi.cc, addc): per outer step one low-half chain and one high-half
+// chain for a*b_i, then the same two chains for m*p with m = t_0 * (-p^-1 mod 2^32).  The
+// integer multiply-add pipe executes all of it; there is no floating point anywhere.
+#pragma once
+#include <cstdint>
+
+#include "constants.cuh"
+
+#ifndef FPG_PRIMITIVES_EXTERNAL
+#define FPG_DEV __device__ __forceinline__
+#define FPG_NOINL static __device__ __noinline__
+
+namespace ptx {
+FPG_DEV uint32_t add_cc(uint32_t a, uint32_t b) { uint32_t r; asm volatile("add.cc.u32 %0, %1, %2;" : "=r"(r) : "r"(a), "r"(b)); return r; }
+FPG_DEV uint32_t addc_cc(uint32_t a, uint32_t b) { uint32_t r; asm volatile("addc.cc.u32 %0, %1, %2;" : "=r"(r) : "r"(a), "r"(b)); return r; }
+FPG_DEV uint32_t addc(uint32_t a, uint32_t b) { uint32_t r; asm volatile("addc.u32 %0, %1, %2;" : "=r"(r) : "r"(a), "r"(b)); return r; }
+FPG_DEV uint32_t sub_cc(uint32_t a, uint32_t b) { uint32_t r; asm volatile("sub.cc.u32 %0, %1, %2;" : "=r"(r) : "r"(a), "r"(b)); return r; }
+FPG_DEV uint32_t subc_cc(uint32_t a, uint32_t b) { uint32_t r; asm volatile("subc.cc.u32 %0, %1, %2;" : "=r"(r) : "r"(a), "r"(b)); return r; }
+FPG_DEV uint32_t subc(uint32_t a, uint32_t b) { uint32_t r; asm volatile("subc.u32 %0, %1, %2;" : "=r"(r) : "r"(a), "r"(b)); return r; }
+FPG_DEV uint32_t mad_lo_cc(uint32_t a, uint32_t b, uint32_t c) { uint32_t r; asm volatile("mad.lo.cc.u32 %0, %1, %2, %3;" : "=r"(r) : "r"(a), "r"(b), "r"(c)); return r; }
+FPG_DEV uint32_t madc_lo_cc(uint32_t a, uint32_t b, uint32_t c) { uint32_t r; asm volatile("madc.lo.cc.u32 %0, %1, %2, %3;" : "=r"(r) : "r"(a), "r"(b), "r"(c)); return r; }
+FPG_DEV uint32_t mad_hi_cc(uint32_t a, uint32_t b, uint32_t c) { uint32_t r; asm volatile("mad.hi.cc.u32 %0, %1, %2, %3;" : "=r"(r) : "r"(a), "r"(b), "r"(c)); return r; }
+FPG_DEV uint32_t madc_hi_cc(uint32_t a, uint32_t b, uint32_t c) { uint32_t r; asm volatile("madc.hi.cc.u32 %0, %1, %2, %3;" : "=r"(r) : "r"(a), "r"(b), "r"(c)); return r; }
+}  // namespace ptx
+#endif
+
+struct fq { uint32_t v[12]; };
+struct fr { uint32_t v[8]; };
+
+namespace mp {
+
+// r = a * b * 2^(-32 N) mod P, for a, b < P and 4P < 2^(32 N).
+template <int N>
+FPG_DEV void mont_mul(uint32_t* r, const uint32_t* a, const uint32_t* b, const uint32_t* P, uint32_t pinv) {
+    uint32_t t[N + 2];
+#pragma unroll
+    for (int j = 0; j < N + 2; j++) t[j] = 0;
+#pragma unroll
+    for (int i = 0; i < N; i++) {
+        const uint32_t bi = b[i];
+        t[0] = ptx::mad_lo_cc(a[0], bi, t[0]);
+#pragma unroll
+        for (int j = 1; j < N; j++) t[j] = ptx::madc_lo_cc(a[j], bi, t[j]);
+        t[N] = ptx::addc_cc(t[N], 0);
+        t[N + 1] = ptx::addc(t[N + 1], 0);
+        t[1] = ptx::mad_hi_cc(a[0], bi, t[1]);
+#pragma unroll
+        for (int j = 1; j < N; j++) t[j + 1] = ptx::madc_hi_cc(a[j], bi, t[j + 1]);
+        t[N + 1] = ptx::addc(t[N + 1], 0);
+        const uint32_t m = t[0] * pinv;
+        t[0] = ptx::mad_lo_cc(m, P[0], t[0]);
+#pragma unroll
+        for (int j = 1; j < N; j++) t[j] = ptx::madc_lo_cc(m, P[j], t[j]);
+        t[N] = ptx::addc_cc(t[N], 0);
+        t[N + 1] = ptx::addc(t[N + 1], 0);
+        t[1] = ptx::mad_hi_cc(m, P[0], t[1]);
+#pragma unroll
+        for (int j = 1; j < N; j++) t[j + 1] = ptx::madc_hi_cc(m, P[j], t[j + 1]);
+        t[N + 1] = ptx::addc(t[N + 1], 0);
+#pragma unroll
+        for (int j = 0; j <= N; j++) t[j] = t[j + 1];
+        t[N + 1] = 0;
+    }
+    uint32_t s[N];
+    s[0] = ptx::sub_cc(t[0], P[0]);
+#pragma unroll
+    for (int j = 1; j < N; j++) s[j] = ptx::subc_cc(t[j], P[j]);
+    const uint32_t borrow = ptx::subc(t[N], 0);     // all-ones when t < P
+#pragma unroll
+    for (int j = 0; j < N; j++) r[j] = borrow ? t[j] : s[j];
+}
+
+// r = a + b mod P (a + b < 2^(32 N) because P < 2^(32 N - 1))
+template <int N>
+FPG_DEV void mod_add(uint32_t* r, const uint32_t* a, const uint32_t* b, const uint32_t* P) {
+    uint32_t t[N], s[N];
+    t[0] = ptx::add_cc(a[0], b[0]);
+#pragma unroll
+    for (int j = 1; j < N; j++) t[j] = ptx::addc_cc(a[j], b[j]);
+    s[0] = ptx::sub_cc(t[0], P[0]);
+#pragma unroll
+    for (int j = 1; j < N; j++) s[j] = ptx::subc_cc(t[j], P[j]);
+    const uint32_t borrow = ptx::subc(0, 0);
+#pragma unroll
+    for (int j = 0; j < N; j++) r[j] = borrow ? t[j] : s[j];
+}
+
+template <int N>
+FPG_DEV void mod_sub(uint32_t* r, const uint32_t* a, const uint32_t* b, const uint32_t* P) {
+    uint32_t t[N], s[N];
+    t[0] = ptx::sub_cc(a[0], b[0]);
+#pragma unroll
+    for (int j = 1; j < N; j++) t[j] = ptx::subc_cc(a[j], b[j]);
+    const uint32_t borrow = ptx::subc(0, 0);
+    s[0] = ptx::add_cc(t[0], P[0]);
+#pragma unroll
+    for (int j = 1; j < N; j++) s[j] = ptx::addc_cc(t[j], P[j]);
+#pragma unroll
+    for (int j = 0; j < N; j++) r[j] = borrow ? s[j] : t[j];
+}
+
+template <int N>
+FPG_DEV bool is_zero(const uint32_t* a) {
+    uint32_t acc = 0;
+#pragma unroll
+    for (int j = 0; j < N; j++) acc |= a[j];
+    return acc == 0;
+}
+
+template <int N>
+FPG_DEV bool eq(const uint32_t* a, const uint32_t* b) {
+    uint32_t acc = 0;
+#pragma unroll
+    for (int j = 0; j < N; j++) acc |= a[j] ^ b[j];
+    return acc == 0;
+}
+
+// canonical a < P ?
+template <int N>
+FPG_DEV bool lt(const uint32_t* a, const uint32_t* P) {
+    uint32_t s = ptx::sub_cc(a[0], P[0]);
+#pragma unroll
+    for (int j = 1; j < N; j++) s = ptx::subc_cc(a[j], P[j]);
+    (void)s;
+    return ptx::subc(0, 0) != 0;
+}
+
+}  // namespace mp
+
+// ---------------------------------------------------------------------------------------
+// Fq
+// ---------------------------------------------------------------------------------------
+FPG_DEV void fq_zero(fq& a) {
+#pragma unroll
+    for (int j = 0; j < 12; j++) a.v[j] = 0;
+}
+FPG_DEV void fq_one(fq& a) {
+#pragma unroll
+    for (int j = 0; j < 12; j++) a.v[j] = FQ_ONE[j];
+}
+FPG_DEV void fq_from_const(fq& a, const uint32_t* c) {
+#pragma unroll
+    for (int j = 0; j < 12; j++) a.v[j] = c[j];
+}
+FPG_DEV fq fq_mul(const fq& a, const fq& b) { fq r; mp::mont_mul<12>(r.v, a.v, b.v, FQ_P, FQ_PINV); return r; }
+FPG_DEV fq fq_sqr(const fq& a) { return fq_mul(a, a); }
+FPG_DEV fq fq_add(const fq& a, const fq& b) { fq r; mp::mod_add<12>(r.v, a.v, b.v, FQ_P); return r; }
+FPG_DEV fq fq_sub(const fq& a, const fq& b) { fq r; mp::mod_sub<12>(r.v, a.v, b.v, FQ_P); return r; }
+FPG_DEV fq fq_dbl(const fq& a) { return fq_add(a, a); }
+FPG_DEV fq fq_neg(const fq& a) { fq z; fq_zero(z); return fq_sub(z, a); }
+FPG_DEV bool fq_is_zero(const fq& a) { return mp::is_zero<12>(a.v); }
+FPG_DEV bool fq_eq(const fq& a, const fq& b) { return mp::eq<12>(a.v, b.v); }
+FPG_DEV fq fq_to_mont(const fq& a) { fq r2; fq_from_const(r2, FQ_R2); return fq_mul(a, r2); }
+FPG_DEV fq fq_from_mont(const fq& a) {
+    fq one; fq_zero(one); one.v[0] = 1;
+    return fq_mul(a, one);
+}
+// a^(p-2) by left-to-right square-and-multiply over the constant exponent bits (Fermat)
+FPG_NOINL fq fq_inv(const fq& a) {
+    fq acc; fq_one(acc);
+    for (int i = 380; i >= 0; i--) {
+        acc = fq_sqr(acc);
+        if ((FQ_PM2[i >> 5] >> (i & 31)) & 1) acc = fq_mul(acc, a);
+    }
+    return acc;
+}
+
+// ---------------------------------------------------------------------------------------
+// Fr
+// ---------------------------------------------------------------------------------------
+FPG_DEV void fr_zero(fr& a) {
+#pragma unroll
+    for (int j = 0; j < 8; j++) a.v[j] = 0;
+}
+FPG_DEV void fr_one(fr& a) {
+#pragma unroll
+    for (int j = 0; j < 8; j++) a.v[j] = FR_ONE[j];
+}
+FPG_DEV fr fr_mul(const fr& a, const fr& b) { fr r; mp::mont_mul<8>(r.v, a.v, b.v, FR_P, FR_PINV); return r; }
+FPG_DEV fr fr_add(const fr& a, const fr& b) { fr r; mp::mod_add<8>(r.v, a.v, b.v, FR_P); return r; }
+FPG_DEV fr fr_sub(const fr& a, const fr& b) { fr r; mp::mod_sub<8>(r.v, a.v, b.v, FR_P); return r; }
+FPG_DEV bool fr_is_zero(const fr& a) { return mp::is_zero<8>(a.v); }
+FPG_DEV fr fr_to_mont(const fr& a) {
+    fr r2;
+#pragma unroll
+    for (int j = 0; j < 8; j++) r2.v[j] = FR_R2[j];
+    return fr_mul(a, r2);
+}
+FPG_DEV fr fr_from_mont(const fr& a) {
+    fr one; fr_zero(one); one.v[0] = 1;
+    return fr_mul(a, one);
+}
+FPG_DEV bool fr_canonical_lt_r(const fr& a) { return mp::lt<8>(a.v, FR_P); }
+FPG_NOINL fr fr_inv(const fr& a) {
+    fr acc; fr_one(acc);
+    for (int i = 254; i >= 0; i--) {
+        acc = fr_mul(acc, acc);
+        if ((FR_PM2[i >> 5] >> (i & 31)) & 1) acc = fr_mul(acc, a);
+    }
+    return acc;
+}
+// Montgomery form of the 512-bit big-endian integer in `be` reduced mod r:
+// mont(hi 2^256 + lo) = mont_mul(hi, R^3) + mont_mul(lo, R^2) with R = 2^256.
+FPG_DEV fr fr_from_be64(const uint8_t* be) {
+    fr hi, lo, r2, r3;
+#pragma unroll
+    for (int j = 0; j < 8; j++) {
+        const uint8_t* h = be + 28 - 4 * j;
+        const uint8_t* l = be + 60 - 4 * j;
+        hi.v[j] = ((uint32_t)h[0] << 24) | ((uint32_t)h[1] << 16) | ((uint32_t)h[2] << 8) | h[3];
+        lo.v[j] = ((uint32_t)l[0] << 24) | ((uint32_t)l[1] << 16) | ((uint32_t)l[2] << 8) | l[3];
+        r2.v[j] = FR_R2[j];
+        r3.v[j] = FR_R3[j];
+    }
+    return fr_add(fr_mul(hi, r3), fr_mul(lo, r2));
+}
+// canonical big-endian bytes of an Fr residue
+FPG_DEV void fr_to_be(uint8_t* out, const fr& a) {
+    fr c = fr_from_mont(a);
+#pragma unroll
+    for (int j = 0; j < 8; j++) {
+        uint32_t w = c.v[7 - j];
+        out[4 * j] = (uint8_t)(w >> 24); out[4 * j + 1] = (uint8_t)(w >> 16);
+        out[4 * j + 2] = (uint8_t)(w >> 8); out[4 * j + 3] = (uint8_t)w;
+    }
+}
+FPG_DEV void fq_to_be(uint8_t* out, const fq& a) {
+    fq c = fq_from_mont(a);
+#pragma unroll
+    for (int j = 0; j < 12; j++) {
+        uint32_t w = c.v[11 - j];
+        out[4 * j] = (uint8_t)(w >> 24); out[4 * j + 1] = (uint8_t)(w >> 16);
+        out[4 * j + 2] = (uint8_t)(w >> 8); out[4 * j + 3] = (uint8_t)w;
+    }
+}

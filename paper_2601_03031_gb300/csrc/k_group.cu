@@ -1,0 +1,179 @@
+// Setup, commit-MSM terms and the generic group kernels (pairwise reductions, normalisation,
+// serialisation).
+#include "k_common.cuh"
+
+namespace fpk {
+
+// ------------------------------------------------------------------------------ setup
+// SplitMix64 (Steele, Lea, Flood 2014), and Fr draws by rejection of four outputs with the top
+// word masked to 63 bits.
+__device__ uint64_t splitmix_next(uint64_t& st) {
+    uint64_t z = (st += 0x9e3779b97f4a7c15ull);
+    z = (z ^ (z >> 30)) * 0xbf58476d1ce4e5b9ull;
+    z = (z ^ (z >> 27)) * 0x94d049bb133111ebull;
+    return z ^ (z >> 31);
+}
+
+__global__ void k_trapdoor(uint64_t seed, int log_c, fr* trap) {
+    if (gtid() != 0) return;
+    uint64_t st = seed ^ 0x5eed5eedull;
+    for (int t = 0; t <= log_c; t++) {          // trap[0] = beta, trap[1 + t] = tau_t
+        fr c;
+        for (;;) {
+            for (int w = 0; w < 4; w++) {
+                uint64_t z = splitmix_next(st);
+                if (w == 3) z &= 0x7fffffffffffffffull;
+                c.v[2 * w] = (uint32_t)z;
+                c.v[2 * w + 1] = (uint32_t)(z >> 32);
+            }
+            if (fr_canonical_lt_r(c)) break;
+        }
+        trap[t] = fr_to_mont(c);
+    }
+}
+
+// lam_scal[idx] for idx < 2M - 1: level t = floor(log2(idx + 1)), c = idx + 1 - 2^t,
+// eq_t(c, tau) = prod_{s<t} (c_s tau_s + (1 - c_s)(1 - tau_s)); pow_scal[i] = beta^i.
+__global__ void k_setup_scalars(const fr* trap, int log_r, int log_c, fr* lam_scal, fr* pow_scal, fr* tau_scal,
+                                fr* beta_scal) {
+    const uint64_t i = gtid();
+    const uint64_t M = 1ull << log_c, R = 1ull << log_r;
+    fr one; fr_one(one);
+    if (i < 2 * M - 1) {
+        int t = 63 - __clzll(i + 1);
+        uint64_t c = i + 1 - (1ull << t);
+        fr acc = one;
+        for (int s = 0; s < t; s++) {
+            fr tau = trap[1 + s];
+            acc = fr_mul(acc, ((c >> s) & 1) ? tau : fr_sub(one, tau));
+        }
+        lam_scal[i] = fr_from_mont(acc);
+    }
+    if (i < 2 * R - 1) {
+        fr beta = trap[0], acc = one;
+        for (int bit = 20; bit >= 0; bit--) {
+            acc = fr_mul(acc, acc);
+            if ((i >> bit) & 1) acc = fr_mul(acc, beta);
+        }
+        pow_scal[i] = fr_from_mont(acc);
+    }
+    if (i < (uint64_t)log_c) tau_scal[i] = fr_from_mont(trap[1 + i]);
+    if (i == 0) beta_scal[0] = fr_from_mont(trap[0]);
+}
+
+__global__ void k_g1_gen_mul(const fr* scal, uint32_t n, g1a* out) {
+    uint64_t i = gtid();
+    if (i >= n) return;
+    out[i] = g1_affine(g1_mul(g1_generator(), scal[i].v));
+}
+__global__ void k_g2_gen_mul(const fr* scal, uint32_t n, g2a* out) {
+    uint64_t i = gtid();
+    if (i >= n) return;
+    out[i] = g2_affine(g2_mul(g2_generator(), scal[i].v));
+}
+
+void setup_trapdoor(uint64_t seed, int log_c, void* trap, cudaStream_t s) {
+    FP_KERNEL("k_trapdoor", s, k_trapdoor<<<1, 32, 0, s>>>(seed, log_c, (fr*)trap));
+}
+void setup_scalars(const void* trap, int log_r, int log_c, void* lam_scal, void* pow_scal, void* tau_scal,
+                   void* beta_scal, cudaStream_t s) {
+    uint64_t n = 2ull << (log_c > log_r ? log_c : log_r);
+    FP_KERNEL("k_setup_scalars", s, k_setup_scalars<<<grid_for(n), TPB, 0, s>>>((const fr*)trap, log_r, log_c, (fr*)lam_scal, (fr*)pow_scal,
+                                                (fr*)tau_scal, (fr*)beta_scal));
+}
+void g1_gen_mul(const void* scal, uint32_t n, void* out, cudaStream_t s) {
+    if (n) FP_KERNEL("k_g1_gen_mul", s, k_g1_gen_mul<<<grid_for(n, 64), 64, 0, s>>>((const fr*)scal, n, (g1a*)out));
+}
+void g2_gen_mul(const void* scal, uint32_t n, void* out, cudaStream_t s) {
+    if (n) FP_KERNEL("k_g2_gen_mul", s, k_g2_gen_mul<<<grid_for(n, 64), 64, 0, s>>>((const fr*)scal, n, (g2a*)out));
+}
+
+// ------------------------------------------------------------------------------ reductions
+__global__ void k_g1_pair(const g1j* in, g1j* out, uint64_t n) {
+    uint64_t i = gtid();
+    if (i < n) out[i] = jac_add(in[2 * i], in[2 * i + 1]);
+}
+__global__ void k_g2_pair(const g2j* in, g2j* out, uint64_t n) {
+    uint64_t i = gtid();
+    if (i < n) out[i] = jac_add(in[2 * i], in[2 * i + 1]);
+}
+__global__ void k_fq12_pair(const fq12* in, fq12* out, uint64_t n) {
+    uint64_t i = gtid();
+    if (i < n) out[i] = fq12_mul(in[2 * i], in[2 * i + 1]);
+}
+void g1_pair_reduce(const void* in, void* out, uint64_t n, cudaStream_t s) {
+    if (n) FP_KERNEL("k_g1_pair", s, k_g1_pair<<<grid_for(n), TPB, 0, s>>>((const g1j*)in, (g1j*)out, n));
+}
+void g2_pair_reduce(const void* in, void* out, uint64_t n, cudaStream_t s) {
+    if (n) FP_KERNEL("k_g2_pair", s, k_g2_pair<<<grid_for(n, 64), 64, 0, s>>>((const g2j*)in, (g2j*)out, n));
+}
+void fq12_pair_reduce(const void* in, void* out, uint64_t n, cudaStream_t s) {
+    if (n) FP_KERNEL("k_fq12_pair", s, k_fq12_pair<<<grid_for(n, 64), 64, 0, s>>>((const fq12*)in, (fq12*)out, n));
+}
+
+__global__ void k_g1j_affine(const g1j* in, g1a* out, uint8_t* ser, size_t stride, uint64_t n) {
+    uint64_t i = gtid();
+    if (i >= n) return;
+    g1a a = g1_affine(in[i]);
+    if (out) out[i] = a;
+    if (ser) g1a_to_be(ser + i * stride, a);
+}
+__global__ void k_g2j_affine(const g2j* in, g2a* out, uint8_t* ser, size_t stride, uint64_t n) {
+    uint64_t i = gtid();
+    if (i >= n) return;
+    g2a a = g2_affine(in[i]);
+    if (out) out[i] = a;
+    if (ser) g2a_to_be(ser + i * stride, a);
+}
+__global__ void k_g1a_ser(const g1a* in, uint8_t* ser, size_t stride, uint64_t n) {
+    uint64_t i = gtid();
+    if (i < n) g1a_to_be(ser + i * stride, in[i]);
+}
+__global__ void k_g2a_ser(const g2a* in, uint8_t* ser, size_t stride, uint64_t n) {
+    uint64_t i = gtid();
+    if (i < n) g2a_to_be(ser + i * stride, in[i]);
+}
+void g1j_to_affine(const void* in, void* out, void* ser, size_t stride, uint64_t n, cudaStream_t s) {
+    if (n) FP_KERNEL("k_g1j_affine", s, k_g1j_affine<<<grid_for(n, 64), 64, 0, s>>>((const g1j*)in, (g1a*)out, (uint8_t*)ser, stride, n));
+}
+void g2j_to_affine(const void* in, void* out, void* ser, size_t stride, uint64_t n, cudaStream_t s) {
+    if (n) FP_KERNEL("k_g2j_affine", s, k_g2j_affine<<<grid_for(n, 64), 64, 0, s>>>((const g2j*)in, (g2a*)out, (uint8_t*)ser, stride, n));
+}
+void g1a_serialize(const void* in, void* ser, size_t stride, uint64_t n, cudaStream_t s) {
+    if (n) FP_KERNEL("k_g1a_ser", s, k_g1a_ser<<<grid_for(n), TPB, 0, s>>>((const g1a*)in, (uint8_t*)ser, stride, n));
+}
+void g2a_serialize(const void* in, void* ser, size_t stride, uint64_t n, cudaStream_t s) {
+    if (n) FP_KERNEL("k_g2a_ser", s, k_g2a_ser<<<grid_for(n), TPB, 0, s>>>((const g2a*)in, (uint8_t*)ser, stride, n));
+}
+
+__global__ void k_fr_ser(const fr* in, uint64_t n, uint8_t* out) {
+    uint64_t i = gtid();
+    if (i < n) fr_to_be(out + 32 * i, in[i]);
+}
+void fr_serialize(const void* in, uint64_t n, void* out, cudaStream_t s) {
+    if (n) FP_KERNEL("k_fr_ser", s, k_fr_ser<<<grid_for(n), TPB, 0, s>>>((const fr*)in, n, (uint8_t*)out));
+}
+
+// ------------------------------------------------------------------------------ commit
+// m arrives as canonical little-endian limbs; values >= r set *err.
+__global__ void k_load_vector(const fr* m, uint64_t n, fr* canon, fr* mont, uint32_t* err) {
+    uint64_t i = gtid();
+    if (i >= n) return;
+    fr c = m[i];
+    if (!fr_canonical_lt_r(c)) { atomicOr(err, 1u); fr_zero(c); }
+    canon[i] = c;
+    mont[i] = fr_to_mont(c);
+}
+__global__ void k_commit_terms(const fr* m_canon, const g1a* lam, uint64_t n, uint32_t M, g1j* out) {
+    uint64_t i = gtid();
+    if (i >= n) return;
+    out[i] = g1_mul(lam[i % M], m_canon[i].v);
+}
+void load_vector(const void* m, uint64_t n, void* canon, void* mont, uint32_t* err, cudaStream_t s) {
+    FP_KERNEL("k_load_vector", s, k_load_vector<<<grid_for(n), TPB, 0, s>>>((const fr*)m, n, (fr*)canon, (fr*)mont, err));
+}
+void commit_terms(const void* m_canon, const void* lam, uint64_t n, uint32_t M, void* out, cudaStream_t s) {
+    FP_KERNEL("k_commit_terms", s, k_commit_terms<<<grid_for(n, 64), 64, 0, s>>>((const fr*)m_canon, (const g1a*)lam, n, M, (g1j*)out));
+}
+
+}  // namespace fpk

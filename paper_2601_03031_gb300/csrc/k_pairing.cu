@@ -1,0 +1,48 @@
+// Batched Miller loops and final exponentiations.
+#include "k_common.cuh"
+
+namespace fpk {
+
+// FC.Commit (Eq. genC): pair j is (C_j, v_j = g2^{beta^{2j}})
+__global__ void __launch_bounds__(64) k_commit_miller(const g1a* rows, const g2a* g2pow, uint32_t R, fq12* out) {
+    uint64_t j = gtid();
+    if (j >= R) return;
+    out[j] = miller_loop(rows[j], g2pow[2 * j]);
+}
+
+// Round j of FC.BOpen (Eq. folding) for every block at once, h = R / 2^j:
+// pair t = (k, side, i): side 0 -> (A_R)[i] with (v_L)[i]  (L_j.T), side 1 -> (A_L)[i] with (v_R)[i]  (R_j.T)
+__global__ void __launch_bounds__(64) k_step1_miller(const g1a* A, const g2a* v, uint32_t K, uint32_t R, uint32_t h,
+                                                     fq12* out) {
+    uint64_t t = gtid();
+    if (t >= (uint64_t)K * 2 * h) return;
+    uint64_t k = t / (2 * h);
+    uint32_t r = (uint32_t)(t % (2 * h)), side = r / h, i = r % h;
+    const g1a* Ak = A + k * R;
+    const g2a* vk = v + k * R;
+    out[t] = side == 0 ? miller_loop(Ak[h + i], vk[i]) : miller_loop(Ak[i], vk[h + i]);
+}
+
+__global__ void __launch_bounds__(64) k_final_exp(const fq12* in, uint32_t n, size_t stride, fq12* out, uint8_t* ser,
+                                                  size_t ser_stride) {
+    uint64_t i = gtid();
+    if (i >= n) return;
+    fq12 e = final_exp(in[i * stride]);
+    if (out) out[i] = e;
+    if (ser) fq12_to_be(ser + i * ser_stride, e);
+}
+
+void commit_miller(const void* rows, const void* g2pow, uint32_t R, void* out, cudaStream_t s) {
+    FP_KERNEL("k_commit_miller", s, k_commit_miller<<<grid_for(R, 64), 64, 0, s>>>((const g1a*)rows, (const g2a*)g2pow, R, (fq12*)out));
+}
+void step1_miller(const void* A, const void* v, uint32_t K, uint32_t R, uint32_t h, void* out, cudaStream_t s) {
+    uint64_t n = (uint64_t)K * 2 * h;
+    FP_KERNEL("k_step1_miller", s, k_step1_miller<<<grid_for(n, 64), 64, 0, s>>>((const g1a*)A, (const g2a*)v, K, R, h, (fq12*)out));
+}
+void final_exp_batch(const void* in, uint32_t n, size_t stride, void* out, void* ser, size_t ser_stride,
+                     cudaStream_t s) {
+    if (n) FP_KERNEL("k_final_exp", s, k_final_exp<<<grid_for(n, 64), 64, 0, s>>>((const fq12*)in, n, stride, (fq12*)out, (uint8_t*)ser,
+                                                       ser_stride));
+}
+
+}  // namespace fpk

@@ -1,0 +1,212 @@
+// Step 1 of OpenAll: FC.BOpen (Sec. 3, Eq. b and Eq. folding) for every block S_k at once, with
+// b = sum_{a in S_k} r_a u_a held densely per block, and the faster-verification proof of v_l.
+// Per-block arrays are laid out block-major: X[k * R + i].
+#include "k_common.cuh"
+
+namespace fpk {
+
+__global__ void k_step1_init(const g1a* rows, const g2a* g2pow, uint32_t K, uint32_t R, g1a* A, g2a* v, fr* bvec) {
+    uint64_t t = gtid();
+    if (t >= (uint64_t)K * R) return;
+    uint32_t i = (uint32_t)(t % R);
+    A[t] = rows[i];
+    v[t] = g2pow[2 * i];
+    fr_zero(bvec[t]);
+}
+
+// SHA256(C || u32be(k) || u32be(b) || u32be(|S_k|) || C_a for a in S_k)
+__global__ void k_stmt_hash(const uint8_t* C_ser, const uint8_t* rows_ser, uint32_t K, uint32_t R, uint32_t b,
+                            uint8_t* hstmt) {
+    uint64_t k = gtid();
+    if (k >= K) return;
+    uint32_t lo = (uint32_t)k * b, hi = min(lo + b, R), nk = hi - lo;
+    sha256_ctx c;
+    sha256_init(c);
+    sha256_update(c, C_ser, 576);
+    uint8_t hdr[12];
+    put_be32(hdr, (uint32_t)k); put_be32(hdr + 4, b); put_be32(hdr + 8, nk);
+    sha256_update(c, hdr, 12);
+    sha256_update(c, rows_ser + (size_t)lo * 96, nk * 96);
+    sha256_final(c, hstmt + k * 32);
+}
+
+// r_a = HFr("FP-r", SHA256(statement_k) || u32be(a)) placed at b[a] of block k
+__global__ void k_block_r(const uint8_t* hstmt, uint32_t K, uint32_t R, uint32_t b, fr* bvec) {
+    uint64_t t = gtid();
+    if (t >= (uint64_t)K * b) return;
+    uint32_t k = (uint32_t)(t / b), a = k * b + (uint32_t)(t % b);
+    if (a >= R) return;
+    uint8_t buf[36];
+    for (int q = 0; q < 32; q++) buf[q] = hstmt[(size_t)k * 32 + q];
+    put_be32(buf + 32, a);
+    bvec[(size_t)k * R + a] = hash_to_fr("FP-r", 4, buf, 36, nullptr, 0, nullptr, 0);
+}
+
+// L_j.1 = <A_R, b_L>, R_j.1 = <A_L, b_R>: one term per (k, side, i)
+__global__ void __launch_bounds__(64) k_sparse_terms(const g1a* A, const fr* bvec, uint32_t K, uint32_t R, uint32_t h,
+                                                     g1j* out) {
+    uint64_t t = gtid();
+    if (t >= (uint64_t)K * 2 * h) return;
+    uint64_t k = t / (2 * h);
+    uint32_t r = (uint32_t)(t % (2 * h)), side = r / h, i = r % h;
+    fr sc = bvec[k * R + (side == 0 ? i : h + i)];
+    g1j res;
+    if (fr_is_zero(sc)) {
+        jac_set_inf(res);
+    } else {
+        uint32_t kw[8];
+        fr_canon_words(kw, sc);
+        res = g1_mul(A[k * R + (side == 0 ? h + i : i)], kw);
+    }
+    out[t] = res;
+}
+
+// after the reductions: GT = final exponentiation of the Miller product, G1 part to affine;
+// written to round j's record of block k: L_j.T | L_j.1 | R_j.T | R_j.1
+__global__ void __launch_bounds__(64) k_round_out(const fq12* ml, const g1j* sp, uint32_t K, int j, uint8_t* blocks,
+                                                  size_t bopen_len) {
+    uint64_t t = gtid();
+    if (t >= (uint64_t)K * 2) return;
+    uint64_t k = t >> 1;
+    uint32_t side = (uint32_t)(t & 1);
+    uint8_t* rec = blocks + k * bopen_len + (size_t)(j - 1) * ROUND_BYTES + side * (GT_SER + G1_SER);
+    fq12_to_be(rec, final_exp(ml[t]));
+    g1a_to_be(rec + GT_SER, g1_affine(sp[t]));
+}
+
+// x_j = HFr'("FP-x", x_{j-1} || L_j || R_j) (x_0 empty), re-hashed while 0; x_j^{-1}
+__global__ void k_challenge(const uint8_t* blocks, size_t bopen_len, uint32_t K, int j, uint8_t* xprev, fr* x_mont,
+                            fr* xinv_mont, fr* xinv_all, int log_r) {
+    uint64_t k = gtid();
+    if (k >= K) return;
+    const uint8_t* rec = blocks + k * bopen_len + (size_t)(j - 1) * ROUND_BYTES;
+    uint8_t* xp = xprev + k * 32;
+    fr x = hash_to_fr_nonzero("FP-x", 4, xp, j > 1 ? 32 : 0, rec, ROUND_BYTES, nullptr, 0);
+    fr xi = fr_inv(x);
+    x_mont[k] = x;
+    xinv_mont[k] = xi;
+    xinv_all[k * log_r + (j - 1)] = xi;
+    fr_to_be(xp, x);
+}
+
+// A_j = A_L o A_R^{x_j};  b_j = b_L + b_R / x_j
+__global__ void __launch_bounds__(64) k_fold_g1(g1a* A, fr* bvec, const fr* x_mont, const fr* xinv_mont, uint32_t K,
+                                                uint32_t R, uint32_t h) {
+    uint64_t t = gtid();
+    if (t >= (uint64_t)K * h) return;
+    uint64_t k = t / h;
+    uint32_t i = (uint32_t)(t % h);
+    uint64_t lo = k * R + i, hi = k * R + h + i;
+    uint32_t kw[8];
+    fr_canon_words(kw, x_mont[k]);
+    g1j s = g1_madd(g1_mul(A[hi], kw), A[lo]);
+    A[lo] = g1_affine(s);
+    bvec[lo] = fr_add(bvec[lo], fr_mul(bvec[hi], xinv_mont[k]));
+}
+
+// v_j = v_L o v_R^{1/x_j}
+__global__ void __launch_bounds__(64) k_fold_g2(g2a* v, const fr* xinv_mont, uint32_t K, uint32_t R, uint32_t h) {
+    uint64_t t = gtid();
+    if (t >= (uint64_t)K * h) return;
+    uint64_t k = t / h;
+    uint32_t i = (uint32_t)(t % h);
+    uint64_t lo = k * R + i, hi = k * R + h + i;
+    uint32_t kw[8];
+    fr_canon_words(kw, xinv_mont[k]);
+    g2j s = g2_madd(g2_mul(v[hi], kw), v[lo]);
+    v[lo] = g2_affine(s);
+}
+
+// A_l, v_l into the record; z = HFr("FP-z", x_l || v_l);
+// P(X) = prod_{j=1..l} (1 + x_j^{-1} X^{2^{l-j+1}}) expanded densely (degree 2R - 2);
+// q = (P - P(z)) / (X - z) by synthetic division, stored canonical and zero-padded to 2R terms.
+__global__ void k_kzg(const g1a* A, const g2a* v, const uint8_t* xprev, const fr* xinv_all, uint32_t K, uint32_t R,
+                      int log_r, uint8_t* blocks, size_t bopen_len, fr* pcoef, fr* q_canon) {
+    uint64_t k = gtid();
+    if (k >= K) return;
+    uint8_t* tail = blocks + k * bopen_len + (size_t)log_r * ROUND_BYTES;
+    g1a_to_be(tail, A[k * R]);
+    g2a_to_be(tail + G1_SER, v[k * R]);
+    fr z = hash_to_fr("FP-z", 4, xprev + k * 32, 32, tail + G1_SER, G2_SER, nullptr, 0);
+    const uint32_t deg = 2 * R - 2;
+    fr* P = pcoef + k * (deg + 1);
+    for (uint32_t d = 0; d <= deg; d++) fr_zero(P[d]);
+    fr_one(P[0]);
+    uint32_t cur = 0;
+    for (int j = 1; j <= log_r; j++) {
+        uint32_t e = 1u << (log_r - j + 1);
+        fr xi = xinv_all[k * log_r + (j - 1)];
+        for (int d = (int)cur; d >= 0; d--) P[d + e] = fr_add(P[d + e], fr_mul(P[d], xi));
+        cur += e;
+    }
+    fr* q = q_canon + k * (2 * R);
+    fr qi = P[deg];                       // q_{deg-1}
+    q[deg - 1] = fr_from_mont(qi);
+    for (int i = (int)deg - 1; i >= 1; i--) {
+        qi = fr_add(P[i], fr_mul(z, qi));  // q_{i-1} = P_i + z q_i
+        q[i - 1] = fr_from_mont(qi);
+    }
+    fr_zero(q[deg]);
+    fr_zero(q[deg + 1]);
+}
+
+// W = sum_i q_i g2^{beta^i}: one term per (k, i < 2R), padding terms are zero
+__global__ void __launch_bounds__(64) k_w_terms(const g2a* g2pow, const fr* q_canon, uint32_t K, uint32_t R, g2j* out) {
+    uint64_t t = gtid();
+    if (t >= (uint64_t)K * 2 * R) return;
+    uint32_t i = (uint32_t)(t % (2 * R));
+    fr sc = q_canon[t];
+    g2j res;
+    if (i >= 2 * R - 1 || fr_is_zero(sc)) jac_set_inf(res);
+    else res = g2_mul(g2pow[i], sc.v);
+    out[t] = res;
+}
+
+void step1_init(const void* rows, const void* g2pow, uint32_t K, uint32_t R, void* A, void* v, void* bvec,
+                cudaStream_t s) {
+    FP_KERNEL("k_step1_init", s, k_step1_init<<<grid_for((uint64_t)K * R), TPB, 0, s>>>((const g1a*)rows, (const g2a*)g2pow, K, R, (g1a*)A,
+                                                          (g2a*)v, (fr*)bvec));
+}
+void step1_stmt_hash(const void* C_ser, const void* rows_ser, uint32_t K, uint32_t R, uint32_t b, void* hstmt,
+                     cudaStream_t s) {
+    FP_KERNEL("k_stmt_hash", s, k_stmt_hash<<<grid_for(K, 64), 64, 0, s>>>((const uint8_t*)C_ser, (const uint8_t*)rows_ser, K, R, b,
+                                               (uint8_t*)hstmt));
+}
+void step1_block_r(const void* hstmt, uint32_t K, uint32_t R, uint32_t b, void* bvec, cudaStream_t s) {
+    FP_KERNEL("k_block_r", s, k_block_r<<<grid_for((uint64_t)K * b, 64), 64, 0, s>>>((const uint8_t*)hstmt, K, R, b, (fr*)bvec));
+}
+void step1_sparse_terms(const void* A, const void* bvec, uint32_t K, uint32_t R, uint32_t h, void* out,
+                        cudaStream_t s) {
+    FP_KERNEL("k_sparse_terms", s, k_sparse_terms<<<grid_for((uint64_t)K * 2 * h, 64), 64, 0, s>>>((const g1a*)A, (const fr*)bvec, K, R, h,
+                                                                    (g1j*)out));
+}
+void step1_round_out(const void* ml, const void* sp, uint32_t K, int j, void* blocks, size_t bopen_len,
+                     cudaStream_t s) {
+    FP_KERNEL("k_round_out", s, k_round_out<<<grid_for((uint64_t)K * 2, 64), 64, 0, s>>>((const fq12*)ml, (const g1j*)sp, K, j,
+                                                            (uint8_t*)blocks, bopen_len));
+}
+void step1_challenge(void* blocks, size_t bopen_len, uint32_t K, int j, void* xprev, void* x_mont, void* xinv_mont,
+                     void* xinv_all, int log_r, cudaStream_t s) {
+    FP_KERNEL("k_challenge", s, k_challenge<<<grid_for(K, 64), 64, 0, s>>>((const uint8_t*)blocks, bopen_len, K, j, (uint8_t*)xprev,
+                                               (fr*)x_mont, (fr*)xinv_mont, (fr*)xinv_all, log_r));
+}
+void step1_fold_g1(void* A, void* bvec, const void* x_mont, const void* xinv_mont, uint32_t K, uint32_t R,
+                   uint32_t h, cudaStream_t s) {
+    FP_KERNEL("k_fold_g1", s, k_fold_g1<<<grid_for((uint64_t)K * h, 64), 64, 0, s>>>((g1a*)A, (fr*)bvec, (const fr*)x_mont,
+                                                          (const fr*)xinv_mont, K, R, h));
+}
+void step1_fold_g2(void* v, const void* xinv_mont, uint32_t K, uint32_t R, uint32_t h, cudaStream_t s) {
+    FP_KERNEL("k_fold_g2", s, k_fold_g2<<<grid_for((uint64_t)K * h, 64), 64, 0, s>>>((g2a*)v, (const fr*)xinv_mont, K, R, h));
+}
+void step1_kzg(const void* A, const void* v, const void* xprev, const void* xinv_all, uint32_t K, uint32_t R,
+               int log_r, void* blocks, size_t bopen_len, void* pcoef, void* q_canon, cudaStream_t s) {
+    FP_KERNEL("k_kzg", s, k_kzg<<<grid_for(K, 32), 32, 0, s>>>((const g1a*)A, (const g2a*)v, (const uint8_t*)xprev,
+                                         (const fr*)xinv_all, K, R, log_r, (uint8_t*)blocks, bopen_len,
+                                         (fr*)pcoef, (fr*)q_canon));
+}
+void step1_w_terms(const void* g2pow, const void* q_canon, uint32_t K, uint32_t R, void* out, cudaStream_t s) {
+    FP_KERNEL("k_w_terms", s, k_w_terms<<<grid_for((uint64_t)K * 2 * R, 64), 64, 0, s>>>((const g2a*)g2pow, (const fr*)q_canon, K, R,
+                                                              (g2j*)out));
+}
+
+}  // namespace fpk

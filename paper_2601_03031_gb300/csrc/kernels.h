@@ -1,0 +1,102 @@
+// Host-side launchers of the FlexProofs kernels.  Plain C++ (no device types): every buffer is
+// passed as an untyped device pointer whose element layout is fixed by the byte sizes below.
+#pragma once
+#include <cuda_runtime.h>
+#include <cstddef>
+#include <cstdint>
+
+namespace fpk {
+
+// Every kernel launch goes through FP_KERNEL: it counts the launch and, while profiling is
+// enabled, brackets it with CUDA events on the launching stream (per-kernel totals).
+void prof_begin(const char* name, cudaStream_t s);
+void prof_end(cudaStream_t s);
+#define FP_KERNEL(name, stream, ...) \
+    do {                             \
+        fpk::prof_begin(name, stream); \
+        __VA_ARGS__;                 \
+        fpk::prof_end(stream);       \
+    } while (0)
+
+constexpr size_t FR_BYTES = 32;     // fr: 8 x u32, Montgomery or canonical as documented
+constexpr size_t G1A_BYTES = 96;    // affine G1, Montgomery, (0,0) = identity
+constexpr size_t G1J_BYTES = 144;   // Jacobian G1
+constexpr size_t G2A_BYTES = 192;   // affine G2
+constexpr size_t G2J_BYTES = 288;   // Jacobian G2
+constexpr size_t FQ12_BYTES = 576;  // Fq12 (Montgomery limbs, tower order)
+constexpr size_t GT_SER = 576, G1_SER = 96, G2_SER = 192, DIGEST = 32;
+constexpr size_t ROUND_BYTES = 2 * GT_SER + 2 * G1_SER;   // L_j.T, L_j.1, R_j.T, R_j.1
+
+// ---- setup
+void setup_trapdoor(uint64_t seed, int log_c, void* trap_fr, cudaStream_t s);
+void setup_scalars(const void* trap_fr, int log_r, int log_c, void* lam_scal, void* pow_scal, void* tau_scal,
+                   void* beta_scal, cudaStream_t s);
+void g1_gen_mul(const void* scal_canon, uint32_t n, void* out_g1a, cudaStream_t s);
+void g2_gen_mul(const void* scal_canon, uint32_t n, void* out_g2a, cudaStream_t s);
+
+// ---- generic group helpers
+void g1_pair_reduce(const void* in_g1j, void* out_g1j, uint64_t n_out, cudaStream_t s);
+void g2_pair_reduce(const void* in_g2j, void* out_g2j, uint64_t n_out, cudaStream_t s);
+void fq12_pair_reduce(const void* in, void* out, uint64_t n_out, cudaStream_t s);
+void g1j_to_affine(const void* in_g1j, void* out_g1a, void* ser_out, size_t ser_stride, uint64_t n, cudaStream_t s);
+void g2j_to_affine(const void* in_g2j, void* out_g2a, void* ser_out, size_t ser_stride, uint64_t n, cudaStream_t s);
+void g1a_serialize(const void* in_g1a, void* ser_out, size_t ser_stride, uint64_t n, cudaStream_t s);
+void g2a_serialize(const void* in_g2a, void* ser_out, size_t ser_stride, uint64_t n, cudaStream_t s);
+
+void fr_serialize(const void* fr_mont, uint64_t n, void* out, cudaStream_t s);
+
+// ---- commit
+void load_vector(const void* m_limbs, uint64_t n, void* m_canon, void* m_mont, uint32_t* err, cudaStream_t s);
+// out[i] = m_canon[i] * lam[i mod M]  (row MSM terms)
+void commit_terms(const void* m_canon, const void* lam, uint64_t n, uint32_t M, void* out_g1j, cudaStream_t s);
+// out[j] = ML(rows[j], g2pow[2 j])
+void commit_miller(const void* rows_g1a, const void* g2pow, uint32_t R, void* out_fq12, cudaStream_t s);
+void final_exp_batch(const void* in_fq12, uint32_t n, size_t in_stride_elems, void* out_fq12, void* ser_out,
+                     size_t ser_stride, cudaStream_t s);
+
+// ---- Step 1 (FC.BOpen for all blocks at once)
+void step1_init(const void* rows_g1a, const void* g2pow, uint32_t K, uint32_t R, void* A, void* v, void* bvec,
+                cudaStream_t s);
+void step1_stmt_hash(const void* C_ser, const void* rows_ser, uint32_t K, uint32_t R, uint32_t b, void* hstmt,
+                     cudaStream_t s);
+void step1_block_r(const void* hstmt, uint32_t K, uint32_t R, uint32_t b, void* bvec, cudaStream_t s);
+void step1_miller(const void* A, const void* v, uint32_t K, uint32_t R, uint32_t h, void* out_fq12, cudaStream_t s);
+void step1_sparse_terms(const void* A, const void* bvec, uint32_t K, uint32_t R, uint32_t h, void* out_g1j,
+                        cudaStream_t s);
+void step1_round_out(const void* ml_fq12, const void* sp_g1j, uint32_t K, int j, void* blocks, size_t bopen_len,
+                     cudaStream_t s);
+void step1_challenge(void* blocks, size_t bopen_len, uint32_t K, int j, void* xprev, void* x_mont, void* xinv_mont,
+                     void* xinv_all, int log_r, cudaStream_t s);
+void step1_fold_g1(void* A, void* bvec, const void* x_mont, const void* xinv_mont, uint32_t K, uint32_t R,
+                   uint32_t h, cudaStream_t s);
+void step1_fold_g2(void* v, const void* xinv_mont, uint32_t K, uint32_t R, uint32_t h, cudaStream_t s);
+void step1_kzg(const void* A, const void* v, const void* xprev, const void* xinv_all, uint32_t K, uint32_t R,
+               int log_r, void* blocks, size_t bopen_len, void* pcoef, void* q_canon, cudaStream_t s);
+void step1_w_terms(const void* g2pow, const void* q_canon, uint32_t K, uint32_t R, void* out_g2j, cudaStream_t s);
+
+// ---- Step 2
+void step2_leaves(const void* m_canon, uint32_t R, uint32_t M, void* row_tree, cudaStream_t s);
+void tree_level(void* trees, uint32_t ntrees, uint32_t leaves, int level, cudaStream_t s);
+void step2_row_leaves(const void* row_tree, const void* rows_ser, uint32_t R, uint32_t M, void* top_tree,
+                      cudaStream_t s);
+void step2_rj(const void* top_tree, uint32_t R, void* rj, cudaStream_t s);
+void step2_randomize(const void* m_mont, const void* rj, uint32_t R, uint32_t M, void* g, cudaStream_t s);
+void step2_d0(const void* rows_g1a, const void* rj, uint32_t R, void* D_g1a, cudaStream_t s);
+void step2_fold_g(void* g, uint32_t R, uint32_t M, int h, cudaStream_t s);
+void step2_fold_d(void* D_g1a, uint32_t R, int h, cudaStream_t s);
+void step2_pst_terms(const void* g, const void* lam, uint32_t R, uint32_t M, int log_c, void* out_g1j,
+                     cudaStream_t s);
+void step2_gstar_ser(const void* g, uint32_t R, uint32_t M, void* out, cudaStream_t s);
+
+// ---- assembly: proofs i0..i0+count-1 back to back
+struct ProofLayout {
+    uint32_t R, M, b, K;
+    int log_n, log_r, log_c;
+    size_t bopen_len;
+};
+void assemble(const ProofLayout& L, const void* rows_ser, const void* blocks, const void* row_tree,
+              const void* top_tree, const void* D_ser, const void* g, const void* pst_ser, uint64_t i0, uint64_t count,
+              void* out, cudaStream_t s);
+size_t proof_len(const ProofLayout& L, uint64_t i);
+
+}  // namespace fpk

@@ -1,0 +1,478 @@
+// C ABI of the FlexProofs GB300 path (declared in include/flexproofs.h): host-side orchestration
+// of the kernels on one stream.  No arithmetic of the method runs on the host; the host only
+// sizes buffers, enqueues kernels and copies bytes.
+#include <cuda_runtime.h>
+
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <utility>
+#include <vector>
+
+#include "../../include/flexproofs.h"
+#include "kernels.h"
+
+using namespace fpk;
+
+struct fp_pp {
+    uint32_t log_n, log_r, log_c, R, M;
+    void* lam = nullptr;      // G1 affine, 2M - 1: Lambda_t at offset 2^t - 1
+    void* g1beta = nullptr;   // G1 affine
+    void* g2pow = nullptr;    // G2 affine, 2R - 1: g2^{beta^i}
+    void* g2tau = nullptr;    // G2 affine, l_c
+};
+
+struct fp_commit {
+    const fp_pp* pp;
+    void* m_canon = nullptr;  // fr canonical, N
+    void* m_mont = nullptr;   // fr Montgomery, N
+    void* rows = nullptr;     // G1 affine, R
+    void* rows_ser = nullptr; // R x 96
+    void* C = nullptr;        // fq12
+    void* C_ser = nullptr;    // 576
+    cudaStream_t stream;
+};
+
+struct fp_proofs {
+    const fp_pp* pp;
+    ProofLayout L;
+    void* rows_ser = nullptr;  // R x 96 (own copy)
+    void* blocks = nullptr;    // K x bopen_len
+    void* row_tree = nullptr;  // R x (2M - 1) x 32
+    void* top_tree = nullptr;  // (2R - 1) x 32
+    void* rj = nullptr;        // fr, R
+    void* g = nullptr;         // fr Montgomery, (2R - 1) x M
+    void* D = nullptr;         // G1 affine, 2R - 1
+    void* D_ser = nullptr;     // (2R - 1) x 96
+    void* pst_ser = nullptr;   // (M - 1) x 96
+    cudaStream_t stream;
+};
+
+namespace {
+
+thread_local std::string g_last_error;
+
+struct CudaError {
+    fp_status st;
+};
+
+void check(cudaError_t e, const char* what) {
+    if (e != cudaSuccess) {
+        g_last_error = std::string(what) + ": " + cudaGetErrorString(e);
+        throw CudaError{e == cudaErrorMemoryAllocation ? FP_ENOMEM : FP_EDEVICE};
+    }
+}
+void check_launch(const char* what) { check(cudaGetLastError(), what); }
+
+void* dalloc(size_t bytes, cudaStream_t s) {
+    void* p = nullptr;
+    check(cudaMallocAsync(&p, bytes ? bytes : 16, s), "cudaMallocAsync");
+    return p;
+}
+void dfree(void*& p, cudaStream_t s) {
+    if (p) cudaFreeAsync(p, s);
+    p = nullptr;
+}
+
+fp_status device_ok() {
+    int n = 0;
+    cudaError_t e = cudaGetDeviceCount(&n);
+    if (e != cudaSuccess || n == 0) {
+        g_last_error = e != cudaSuccess ? cudaGetErrorString(e) : "no CUDA device";
+        return FP_EDEVICE;
+    }
+    return FP_OK;
+}
+
+template <typename F>
+fp_status guarded(F&& f) {
+    fp_status st = device_ok();
+    if (st != FP_OK) return st;
+    try {
+        return f();
+    } catch (const CudaError& e) {
+        return e.st;
+    }
+}
+
+// pairwise reduction of `n` consecutive elements down to `target` (n / target a power of two);
+// ping-pongs between a and b, returns the buffer holding the result
+template <typename Red>
+void* reduce_pairs(void* a, void* b, uint64_t n, uint64_t target, Red red, cudaStream_t s) {
+    while (n > target) {
+        red(a, b, n / 2, s);
+        std::swap(a, b);
+        n /= 2;
+    }
+    return a;
+}
+
+size_t bopen_len(uint32_t log_r) { return (size_t)log_r * ROUND_BYTES + G1_SER + 2 * G2_SER; }
+
+}  // namespace
+
+extern "C" {
+
+const char* fp_strerror(fp_status s) {
+    switch (s) {
+        case FP_OK: return "ok";
+        case FP_EINVAL: return "invalid argument";
+        case FP_ENOMEM: return "out of memory";
+        case FP_EDEVICE: return "CUDA device error";
+        case FP_ETIMEOUT: return "device wait timed out";
+        case FP_EVERIFY: return "proof did not verify";
+        case FP_ERANGE: return "scalar out of range (>= r)";
+    }
+    return "unknown status";
+}
+const char* fp_last_error(void) { return g_last_error.c_str(); }
+
+fp_status vc_setup(uint32_t log_n, uint32_t b, uint64_t seed, void* stream, fp_pp** out) {
+    if (!out || log_n < 2 || log_n > 26) return FP_EINVAL;
+    const uint32_t log_r = log_n / 2, log_c = log_n - log_r, R = 1u << log_r, M = 1u << log_c;
+    if (b < 1 || b > R) return FP_EINVAL;
+    cudaStream_t s = (cudaStream_t)stream;
+    return guarded([&]() -> fp_status {
+        fp_pp* pp = new fp_pp{log_n, log_r, log_c, R, M};
+        void *trap = nullptr, *lam_s = nullptr, *pow_s = nullptr, *tau_s = nullptr, *beta_s = nullptr;
+        try {
+            pp->lam = dalloc((2 * (size_t)M - 1) * G1A_BYTES, s);
+            pp->g1beta = dalloc(G1A_BYTES, s);
+            pp->g2pow = dalloc((2 * (size_t)R - 1) * G2A_BYTES, s);
+            pp->g2tau = dalloc((size_t)log_c * G2A_BYTES, s);
+            trap = dalloc((log_c + 1) * FR_BYTES, s);
+            lam_s = dalloc((2 * (size_t)M - 1) * FR_BYTES, s);
+            pow_s = dalloc((2 * (size_t)R - 1) * FR_BYTES, s);
+            tau_s = dalloc((size_t)log_c * FR_BYTES, s);
+            beta_s = dalloc(FR_BYTES, s);
+            setup_trapdoor(seed, (int)log_c, trap, s);
+            setup_scalars(trap, (int)log_r, (int)log_c, lam_s, pow_s, tau_s, beta_s, s);
+            g1_gen_mul(lam_s, 2 * M - 1, pp->lam, s);
+            g1_gen_mul(beta_s, 1, pp->g1beta, s);
+            g2_gen_mul(pow_s, 2 * R - 1, pp->g2pow, s);
+            g2_gen_mul(tau_s, log_c, pp->g2tau, s);
+            check_launch("vc_setup kernels");
+            // the trapdoor and its scalar tables are cleared before release
+            check(cudaMemsetAsync(trap, 0, (log_c + 1) * FR_BYTES, s), "memset");
+            check(cudaMemsetAsync(lam_s, 0, (2 * (size_t)M - 1) * FR_BYTES, s), "memset");
+            check(cudaMemsetAsync(pow_s, 0, (2 * (size_t)R - 1) * FR_BYTES, s), "memset");
+            check(cudaMemsetAsync(tau_s, 0, (size_t)log_c * FR_BYTES, s), "memset");
+            check(cudaMemsetAsync(beta_s, 0, FR_BYTES, s), "memset");
+            dfree(trap, s); dfree(lam_s, s); dfree(pow_s, s); dfree(tau_s, s); dfree(beta_s, s);
+            check(cudaStreamSynchronize(s), "vc_setup");
+        } catch (...) {
+            cudaStreamSynchronize(s);
+            fp_pp_free(pp);
+            throw;
+        }
+        *out = pp;
+        return FP_OK;
+    });
+}
+
+fp_status vc_pp_dims(const fp_pp* pp, uint32_t* log_n, uint32_t* R, uint32_t* M) {
+    if (!pp) return FP_EINVAL;
+    if (log_n) *log_n = pp->log_n;
+    if (R) *R = pp->R;
+    if (M) *M = pp->M;
+    return FP_OK;
+}
+
+fp_status vc_pp_export(const fp_pp* pp, uint8_t* out, size_t cap, size_t* len) {
+    if (!pp || !len) return FP_EINVAL;
+    size_t n = (2 * (size_t)pp->M - 1) * G1_SER + G1_SER + (2 * (size_t)pp->R - 1) * G2_SER + pp->log_c * G2_SER;
+    *len = n;
+    if (!out) return FP_OK;
+    if (cap < n) return FP_EINVAL;
+    return guarded([&]() -> fp_status {
+        cudaStream_t s = 0;
+        void* d = dalloc(n, s);
+        uint8_t* o = (uint8_t*)d;
+        g1a_serialize(pp->lam, o, G1_SER, 2 * pp->M - 1, s);
+        o += (2 * (size_t)pp->M - 1) * G1_SER;
+        g1a_serialize(pp->g1beta, o, G1_SER, 1, s);
+        o += G1_SER;
+        g2a_serialize(pp->g2pow, o, G2_SER, 2 * pp->R - 1, s);
+        o += (2 * (size_t)pp->R - 1) * G2_SER;
+        g2a_serialize(pp->g2tau, o, G2_SER, pp->log_c, s);
+        check_launch("vc_pp_export");
+        check(cudaMemcpyAsync(out, d, n, cudaMemcpyDeviceToHost, s), "D2H");
+        dfree(d, s);
+        check(cudaStreamSynchronize(s), "vc_pp_export");
+        return FP_OK;
+    });
+}
+
+fp_status vc_commit(const fp_pp* pp, const uint64_t* m, int on_device, void* stream, fp_commit** out) {
+    if (!pp || !m || !out) return FP_EINVAL;
+    cudaStream_t s = (cudaStream_t)stream;
+    return guarded([&]() -> fp_status {
+        const uint32_t R = pp->R, M = pp->M;
+        const uint64_t N = (uint64_t)R * M;
+        fp_commit* cm = new fp_commit{pp};
+        cm->stream = s;
+        void *src = nullptr, *t1 = nullptr, *t2 = nullptr, *ml = nullptr, *ml2 = nullptr;
+        uint32_t* err = nullptr;
+        try {
+            cm->m_canon = dalloc(N * FR_BYTES, s);
+            cm->m_mont = dalloc(N * FR_BYTES, s);
+            cm->rows = dalloc(R * G1A_BYTES, s);
+            cm->rows_ser = dalloc(R * G1_SER, s);
+            cm->C = dalloc(FQ12_BYTES, s);
+            cm->C_ser = dalloc(GT_SER, s);
+            err = (uint32_t*)dalloc(sizeof(uint32_t), s);
+            check(cudaMemsetAsync(err, 0, sizeof(uint32_t), s), "memset");
+            const void* msrc = m;
+            if (!on_device) {
+                src = dalloc(N * FR_BYTES, s);
+                check(cudaMemcpyAsync(src, m, N * FR_BYTES, cudaMemcpyHostToDevice, s), "H2D m");
+                msrc = src;
+            }
+            load_vector(msrc, N, cm->m_canon, cm->m_mont, err, s);
+            // C_j = sum_a m[jM + a] Lambda_{l_c}[a]: all N terms, then l_c pairwise levels per row
+            t1 = dalloc(N * G1J_BYTES, s);
+            t2 = dalloc(N / 2 * G1J_BYTES, s);
+            void* lam_top = (uint8_t*)pp->lam + ((size_t)M - 1) * G1A_BYTES;
+            commit_terms(cm->m_canon, lam_top, N, M, t1, s);
+            void* rows_j = reduce_pairs(t1, t2, N, R, g1_pair_reduce, s);
+            g1j_to_affine(rows_j, cm->rows, cm->rows_ser, G1_SER, R, s);
+            // C = prod_j e(C_j, v_j): R Miller loops, pairwise products, one final exponentiation
+            ml = dalloc(R * FQ12_BYTES, s);
+            ml2 = dalloc((R / 2 + 1) * FQ12_BYTES, s);
+            commit_miller(cm->rows, pp->g2pow, R, ml, s);
+            void* prod = reduce_pairs(ml, ml2, R, 1, fq12_pair_reduce, s);
+            final_exp_batch(prod, 1, 1, cm->C, cm->C_ser, GT_SER, s);
+            check_launch("vc_commit kernels");
+            uint32_t herr = 0;
+            check(cudaMemcpyAsync(&herr, err, sizeof herr, cudaMemcpyDeviceToHost, s), "D2H err");
+            dfree(src, s); dfree(t1, s); dfree(t2, s); dfree(ml, s); dfree(ml2, s);
+            void* e = err; dfree(e, s);
+            check(cudaStreamSynchronize(s), "vc_commit");
+            if (herr) { fp_commit_free(cm); return FP_ERANGE; }
+        } catch (...) {
+            cudaStreamSynchronize(s);
+            fp_commit_free(cm);
+            throw;
+        }
+        *out = cm;
+        return FP_OK;
+    });
+}
+
+fp_status vc_commit_get(const fp_commit* cm, uint8_t* gt576, uint8_t* rows) {
+    if (!cm) return FP_EINVAL;
+    return guarded([&]() -> fp_status {
+        cudaStream_t s = cm->stream;
+        if (gt576) check(cudaMemcpyAsync(gt576, cm->C_ser, GT_SER, cudaMemcpyDeviceToHost, s), "D2H");
+        if (rows) check(cudaMemcpyAsync(rows, cm->rows_ser, cm->pp->R * G1_SER, cudaMemcpyDeviceToHost, s), "D2H");
+        check(cudaStreamSynchronize(s), "vc_commit_get");
+        return FP_OK;
+    });
+}
+
+fp_status vc_prove_all(const fp_pp* pp, const fp_commit* cm, uint32_t b, void* stream, fp_proofs** out) {
+    if (!pp || !cm || !out || cm->pp != pp) return FP_EINVAL;
+    const uint32_t R = pp->R, M = pp->M;
+    if (b < 1 || b > R) return FP_EINVAL;
+    cudaStream_t s = (cudaStream_t)stream;
+    return guarded([&]() -> fp_status {
+        const int lr = (int)pp->log_r, lc = (int)pp->log_c;
+        const uint32_t K = (R + b - 1) / b;
+        fp_proofs* pf = new fp_proofs{pp};
+        pf->stream = s;
+        pf->L = ProofLayout{R, M, b, K, (int)pp->log_n, lr, lc, bopen_len(pp->log_r)};
+        const size_t blen = pf->L.bopen_len;
+        std::vector<void*> tmp;
+        auto T = [&](size_t bytes) { void* p = dalloc(bytes, s); tmp.push_back(p); return p; };
+        try {
+            pf->rows_ser = dalloc(R * G1_SER, s);
+            check(cudaMemcpyAsync(pf->rows_ser, cm->rows_ser, R * G1_SER, cudaMemcpyDeviceToDevice, s), "D2D");
+            pf->blocks = dalloc(K * blen, s);
+            // ---------------- Step 1: FC.BOpen on every block (Protocol 1, Step 1)
+            const uint64_t KR = (uint64_t)K * R;
+            void* A = T(KR * G1A_BYTES);
+            void* v = T(KR * G2A_BYTES);
+            void* bvec = T(KR * FR_BYTES);
+            void* hstmt = T(K * DIGEST);
+            void* xprev = T(K * 32);
+            void* x_mont = T(K * FR_BYTES);
+            void* xinv_mont = T(K * FR_BYTES);
+            void* xinv_all = T((size_t)K * lr * FR_BYTES);
+            void* ml = T(KR * FQ12_BYTES);
+            void* ml2 = T((KR / 2 + 1) * FQ12_BYTES);
+            void* sp = T(KR * G1J_BYTES);
+            void* sp2 = T((KR / 2 + 1) * G1J_BYTES);
+            step1_init(cm->rows, pp->g2pow, K, R, A, v, bvec, s);
+            step1_stmt_hash(cm->C_ser, cm->rows_ser, K, R, b, hstmt, s);
+            step1_block_r(hstmt, K, R, b, bvec, s);
+            for (int j = 1; j <= lr; j++) {
+                const uint32_t h = R >> j;
+                step1_miller(A, v, K, R, h, ml, s);
+                void* mlr = reduce_pairs(ml, ml2, (uint64_t)K * 2 * h, (uint64_t)K * 2, fq12_pair_reduce, s);
+                step1_sparse_terms(A, bvec, K, R, h, sp, s);
+                void* spr = reduce_pairs(sp, sp2, (uint64_t)K * 2 * h, (uint64_t)K * 2, g1_pair_reduce, s);
+                step1_round_out(mlr, spr, K, j, pf->blocks, blen, s);
+                step1_challenge(pf->blocks, blen, K, j, xprev, x_mont, xinv_mont, xinv_all, lr, s);
+                step1_fold_g1(A, bvec, x_mont, xinv_mont, K, R, h, s);
+                step1_fold_g2(v, xinv_mont, K, R, h, s);
+            }
+            void* pcoef = T((size_t)K * (2 * R - 1) * FR_BYTES);
+            void* q = T((size_t)K * 2 * R * FR_BYTES);
+            step1_kzg(A, v, xprev, xinv_all, K, R, lr, pf->blocks, blen, pcoef, q, s);
+            void* wt = T((size_t)K * 2 * R * G2J_BYTES);
+            void* wt2 = T(((size_t)K * R + 1) * G2J_BYTES);
+            step1_w_terms(pp->g2pow, q, K, R, wt, s);
+            void* wr = reduce_pairs(wt, wt2, (uint64_t)K * 2 * R, K, g2_pair_reduce, s);
+            g2j_to_affine(wr, nullptr, (uint8_t*)pf->blocks + (size_t)lr * ROUND_BYTES + G1_SER + G2_SER, blen, K, s);
+            check_launch("step 1 kernels");
+
+            // ---------------- Step 2: Merkle tree, randomise, fold tree, HyperEval
+            pf->row_tree = dalloc((size_t)R * (2 * M - 1) * DIGEST, s);
+            pf->top_tree = dalloc((2 * (size_t)R - 1) * DIGEST, s);
+            pf->rj = dalloc(R * FR_BYTES, s);
+            pf->g = dalloc((2 * (size_t)R - 1) * M * FR_BYTES, s);
+            pf->D = dalloc((2 * (size_t)R - 1) * G1A_BYTES, s);
+            pf->D_ser = dalloc((2 * (size_t)R - 1) * G1_SER, s);
+            pf->pst_ser = dalloc(((size_t)M - 1) * G1_SER, s);
+            step2_leaves(cm->m_canon, R, M, pf->row_tree, s);
+            for (int l = 1; l <= lc; l++) tree_level(pf->row_tree, R, M, l, s);
+            step2_row_leaves(pf->row_tree, cm->rows_ser, R, M, pf->top_tree, s);
+            for (int l = 1; l <= lr; l++) tree_level(pf->top_tree, 1, R, l, s);
+            step2_rj(pf->top_tree, R, pf->rj, s);
+            step2_randomize(cm->m_mont, pf->rj, R, M, pf->g, s);
+            step2_d0(cm->rows, pf->rj, R, pf->D, s);
+            for (int h = 1; h <= lr; h++) {
+                step2_fold_g(pf->g, R, M, h, s);
+                step2_fold_d(pf->D, R, h, s);
+            }
+            g1a_serialize(pf->D, pf->D_ser, G1_SER, 2 * (uint64_t)R - 1, s);
+            const uint64_t half = M / 2;
+            void* pt = T((size_t)lc * half * G1J_BYTES);
+            void* pt2 = T((half / 2 + 1) * G1J_BYTES);
+            step2_pst_terms(pf->g, pp->lam, R, M, lc, pt, s);
+            size_t pst_off = 0;
+            for (int t = 0; t < lc; t++) {
+                void* lvl = (uint8_t*)pt + (size_t)t * half * G1J_BYTES;
+                uint64_t nseg = half >> t;
+                void* res = reduce_pairs(lvl, pt2, half, nseg, g1_pair_reduce, s);
+                g1j_to_affine(res, nullptr, (uint8_t*)pf->pst_ser + pst_off * G1_SER, G1_SER, nseg, s);
+                pst_off += nseg;
+            }
+            check_launch("step 2 kernels");
+            for (void* p : tmp) cudaFreeAsync(p, s);
+            tmp.clear();
+        } catch (...) {
+            for (void* p : tmp) cudaFreeAsync(p, s);
+            cudaStreamSynchronize(s);
+            fp_proofs_free(pf);
+            throw;
+        }
+        *out = pf;
+        return FP_OK;
+    });
+}
+
+size_t vc_proof_len(const fp_pp* pp, uint32_t b, uint64_t i) {
+    if (!pp || b < 1 || b > pp->R || i >= (uint64_t)pp->R * pp->M) return 0;
+    ProofLayout L{pp->R, pp->M, b, (pp->R + b - 1) / b, (int)pp->log_n, (int)pp->log_r, (int)pp->log_c,
+                  bopen_len(pp->log_r)};
+    return proof_len(L, i);
+}
+
+fp_status vc_proofs_export(const fp_proofs* pf, uint64_t i0, uint64_t count, uint8_t* out, size_t cap, size_t* len) {
+    if (!pf || !len) return FP_EINVAL;
+    const ProofLayout& L = pf->L;
+    const uint64_t N = (uint64_t)L.R * L.M;
+    if (count == 0 || i0 >= N || count > N - i0) return FP_EINVAL;
+    size_t total = 0;
+    for (uint64_t q = 0; q < count; q++) total += proof_len(L, i0 + q);
+    *len = total;
+    if (!out) return FP_OK;
+    if (cap < total) return FP_EINVAL;
+    return guarded([&]() -> fp_status {
+        cudaStream_t s = pf->stream;
+        void* d = dalloc(total, s);
+        assemble(L, pf->rows_ser, pf->blocks, pf->row_tree, pf->top_tree, pf->D_ser, pf->g, pf->pst_ser, i0, count, d,
+                 s);
+        check_launch("assemble");
+        check(cudaMemcpyAsync(out, d, total, cudaMemcpyDeviceToHost, s), "D2H proofs");
+        dfree(d, s);
+        check(cudaStreamSynchronize(s), "vc_proofs_export");
+        return FP_OK;
+    });
+}
+
+fp_status vc_proof_get(const fp_proofs* pf, uint64_t i, uint8_t* out, size_t cap, size_t* len) {
+    return vc_proofs_export(pf, i, 1, out, cap, len);
+}
+
+fp_status vc_proofs_state(const fp_proofs* pf, uint8_t* out, size_t cap, size_t* len) {
+    if (!pf || !len) return FP_EINVAL;
+    const ProofLayout& L = pf->L;
+    const size_t parts[6] = {(size_t)L.K * L.bopen_len, (size_t)L.R * (2 * L.M - 1) * DIGEST,
+                             (2 * (size_t)L.R - 1) * DIGEST, (2 * (size_t)L.R - 1) * G1_SER,
+                             (2 * (size_t)L.R - 1) * L.M * FR_BYTES, ((size_t)L.M - 1) * G1_SER};
+    const void* src[6] = {pf->blocks, pf->row_tree, pf->top_tree, pf->D_ser, pf->g, pf->pst_ser};
+    size_t total = 0;
+    for (size_t p : parts) total += p;
+    *len = total;
+    if (!out) return FP_OK;
+    if (cap < total) return FP_EINVAL;
+    return guarded([&]() -> fp_status {
+        cudaStream_t s = pf->stream;
+        size_t off = 0;
+        for (int q = 0; q < 6; q++) {
+            check(cudaMemcpyAsync(out + off, src[q], parts[q], cudaMemcpyDeviceToHost, s), "D2H state");
+            off += parts[q];
+        }
+        check(cudaStreamSynchronize(s), "vc_proofs_state");
+        return FP_OK;
+    });
+}
+
+fp_status vc_proofs_step2_parts(const fp_proofs* pf, uint8_t* root, uint8_t* rj, uint8_t* gstar, uint8_t* dstar) {
+    if (!pf) return FP_EINVAL;
+    const ProofLayout& L = pf->L;
+    return guarded([&]() -> fp_status {
+        cudaStream_t s = pf->stream;
+        void* d = dalloc(((size_t)L.R + L.M) * 32, s);
+        fr_serialize(pf->rj, L.R, d, s);
+        step2_gstar_ser(pf->g, L.R, L.M, (uint8_t*)d + (size_t)L.R * 32, s);
+        check_launch("step2 parts");
+        if (root)
+            check(cudaMemcpyAsync(root, (uint8_t*)pf->top_tree + (2 * (size_t)L.R - 2) * DIGEST, 32,
+                                  cudaMemcpyDeviceToHost, s), "D2H");
+        if (rj) check(cudaMemcpyAsync(rj, d, (size_t)L.R * 32, cudaMemcpyDeviceToHost, s), "D2H");
+        if (gstar) check(cudaMemcpyAsync(gstar, (uint8_t*)d + (size_t)L.R * 32, (size_t)L.M * 32,
+                                         cudaMemcpyDeviceToHost, s), "D2H");
+        if (dstar)
+            check(cudaMemcpyAsync(dstar, (uint8_t*)pf->D_ser + (2 * (size_t)L.R - 2) * G1_SER, G1_SER,
+                                  cudaMemcpyDeviceToHost, s), "D2H");
+        dfree(d, s);
+        check(cudaStreamSynchronize(s), "vc_proofs_step2_parts");
+        return FP_OK;
+    });
+}
+
+void fp_pp_free(fp_pp* pp) {
+    if (!pp) return;
+    cudaDeviceSynchronize();
+    cudaFree(pp->lam); cudaFree(pp->g1beta); cudaFree(pp->g2pow); cudaFree(pp->g2tau);
+    delete pp;
+}
+void fp_commit_free(fp_commit* cm) {
+    if (!cm) return;
+    cudaDeviceSynchronize();
+    cudaFree(cm->m_canon); cudaFree(cm->m_mont); cudaFree(cm->rows); cudaFree(cm->rows_ser);
+    cudaFree(cm->C); cudaFree(cm->C_ser);
+    delete cm;
+}
+void fp_proofs_free(fp_proofs* pf) {
+    if (!pf) return;
+    cudaDeviceSynchronize();
+    cudaFree(pf->rows_ser); cudaFree(pf->blocks); cudaFree(pf->row_tree); cudaFree(pf->top_tree);
+    cudaFree(pf->rj); cudaFree(pf->g); cudaFree(pf->D); cudaFree(pf->D_ser); cudaFree(pf->pst_ser);
+    delete pf;
+}
+
+}  // extern "C"

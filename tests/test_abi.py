@@ -1,0 +1,47 @@
+"""Host-side checks of the C ABI: the library builds for sm_103a, loads, and exports every entry
+point that include/flexproofs.h declares.  No compute calls (no GPU needed)."""
+import ctypes
+import os
+import re
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def declared_functions():
+    src = open(os.path.join(ROOT, "include", "flexproofs.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"\b((?:vc|fp)_[a-z0-9_]+)\s*\(", src)))
+
+
+def test_header_declares_the_boundary():
+    names = declared_functions()
+    for n in ("vc_setup", "vc_commit", "vc_prove_all", "vc_proof_get", "fp_strerror"):
+        assert n in names
+
+
+def test_library_exports_every_declared_symbol():
+    from paper_2601_03031_gb300 import build as B
+    path = B.build()
+    lib = ctypes.CDLL(path)
+    missing = [n for n in declared_functions() if not hasattr(lib, n)]
+    assert not missing, missing
+
+
+def test_binding_names_match_header():
+    from paper_2601_03031_gb300 import _lib
+    assert sorted(_lib.EXPORTED) == declared_functions()
+
+
+def test_invalid_arguments_rejected_without_device_work():
+    from paper_2601_03031_gb300 import build as B
+    lib = ctypes.CDLL(B.build())
+    lib.vc_setup.argtypes = [ctypes.c_uint32, ctypes.c_uint32, ctypes.c_uint64, ctypes.c_void_p, ctypes.c_void_p]
+    out = ctypes.c_void_p()
+    assert lib.vc_setup(1, 1, 0, None, ctypes.byref(out)) == 1       # log_n < 2
+    assert lib.vc_setup(27, 1, 0, None, ctypes.byref(out)) == 1      # log_n > 26
+    assert lib.vc_setup(10, 33, 0, None, ctypes.byref(out)) == 1     # b > R = 32
+    assert lib.vc_setup(10, 0, 0, None, ctypes.byref(out)) == 1      # b < 1
+    lib.fp_strerror.restype = ctypes.c_char_p
+    assert lib.fp_strerror(6) == b"scalar out of range (>= r)"

@@ -1,0 +1,187 @@
+"""GPU parity: the CUDA path (through the C ABI) against the CPU oracle, byte for byte.
+
+There is no floating point anywhere in the method, so the tolerance is zero: public parameters,
+commitments and every proof byte must be identical.  Small cases compare everything; the
+N = 2^16 cases (the benchmark workload) compare all shared Step-2 state and sampled Step-1
+blocks / proofs, and check commitments against the trapdoor closed form.
+"""
+import functools
+import random
+
+import numpy as np
+import pytest
+
+import oracle as O
+from paper_2601_03031_gb300 import inputs as I
+from tests import _pyref as ref
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+if not torch.cuda.is_available():
+    pytest.skip("no CUDA device", allow_module_level=True)
+
+from paper_2601_03031_gb300 import _lib as F  # noqa: E402
+
+
+@functools.lru_cache(maxsize=None)
+def gpu_pp(log_n, seed):
+    return F.PP(log_n, 1, seed)
+
+
+@functools.lru_cache(maxsize=None)
+def oracle_pp(log_n, seed):
+    return O.PP(log_n, seed)
+
+
+@functools.lru_cache(maxsize=None)
+def vec(log_n, seed, dist="uniform"):
+    return I.vector(seed, log_n, dist)
+
+
+@functools.lru_cache(maxsize=None)
+def gpu_commit(log_n, seed, dist="uniform"):
+    return F.Commitment(gpu_pp(log_n, seed), vec(log_n, seed + 1, dist))
+
+
+@functools.lru_cache(maxsize=None)
+def oracle_commit(log_n, seed, dist="uniform"):
+    return O.commit(oracle_pp(log_n, seed), vec(log_n, seed + 1, dist).tobytes())
+
+
+@pytest.mark.parametrize("log_n", [2, 3, 4, 5, 10])
+def test_setup_parity(log_n):
+    assert gpu_pp(log_n, 7).export() == oracle_pp(log_n, 7).to_bytes()
+
+
+@pytest.mark.parametrize("log_n,dist", [(2, "uniform"), (4, "uniform"), (5, "uniform"), (10, "uniform"),
+                                        (10, "u32")])
+def test_commit_parity(log_n, dist):
+    assert gpu_commit(log_n, 7, dist).get() == oracle_commit(log_n, 7, dist)
+
+
+@pytest.mark.parametrize("log_n,b", [(2, 1), (2, 2), (4, 1), (4, 3), (4, 4), (5, 1), (5, 3), (5, 4)])
+def test_prove_all_every_proof(log_n, b):
+    seed = 7
+    pp, opp = gpu_pp(log_n, seed), oracle_pp(log_n, seed)
+    m = vec(log_n, seed + 1)
+    C, rows = oracle_commit(log_n, seed)
+    pf = F.Proofs(pp, gpu_commit(log_n, seed), b)
+    pr = O.Prover(opp, m.tobytes(), C, rows, b)
+    pr.blocks()
+    pr.step2()
+    assert pf.step2_parts() == pr.step2_parts()
+    got = pf.export(0, pp.N)
+    exp = b"".join(pr.proof(i) for i in range(pp.N))
+    assert got == exp
+    vals = I.to_ints(m)
+    assert all(O.verify_many(opp, C, b, [(i, vals[i], pr.proof(i)) for i in range(pp.N)]))
+
+
+def test_config1_n1024_b1_all_proofs_and_verify():
+    """N = 2^10, b = 1, seed 0: every one of the 1024 proofs equals the oracle's and verifies."""
+    log_n, seed, b = 10, 0, 1
+    pp, opp = F.PP(log_n, b, seed), O.PP(log_n, seed)
+    m = I.vector(seed, log_n)
+    cm = F.Commitment(pp, m)
+    C, rows = cm.get()
+    assert (C, rows) == O.commit(opp, m.tobytes())
+    pf = F.Proofs(pp, cm, b)
+    pr = O.Prover(opp, m.tobytes(), C, rows, b)
+    pr.blocks()
+    pr.step2()
+    got = pf.export(0, pp.N)
+    off = 0
+    vals = I.to_ints(m)
+    items = []
+    for i in range(pp.N):
+        e = pr.proof(i)
+        assert got[off:off + len(e)] == e, i
+        items.append((i, vals[i], e))
+        off += len(e)
+    assert off == len(got)
+    assert all(O.verify_many(opp, C, b, items))
+
+
+def test_empty_and_degenerate_vectors():
+    """All-zero vector (identity rows, e(O, .) = 1) and a single non-zero entry."""
+    log_n, seed, b = 4, 3, 2
+    pp, opp = gpu_pp(log_n, seed), oracle_pp(log_n, seed)
+    for m in (np.zeros((16, 4), np.uint64), np.eye(1, 16, 9, dtype=np.uint64).reshape(16, 1) * np.array([5, 0, 0, 0], np.uint64)):
+        m = np.ascontiguousarray(m, dtype=np.uint64)
+        cm = F.Commitment(pp, m)
+        C, rows = cm.get()
+        assert (C, rows) == O.commit(opp, m.tobytes())
+        pf = F.Proofs(pp, cm, b)
+        pr = O.Prover(opp, m.tobytes(), C, rows, b)
+        pr.blocks(); pr.step2()
+        assert pf.export(0, 16) == b"".join(pr.proof(i) for i in range(16))
+
+
+def test_range_error():
+    pp = gpu_pp(4, 7)
+    m = np.zeros((16, 4), np.uint64)
+    m[3] = np.array(I.R_LIMBS, np.uint64)
+    with pytest.raises(F.FlexProofsError) as e:
+        F.Commitment(pp, m)
+    assert e.value.status == 6
+
+
+def test_device_input_matches_host_input():
+    log_n, seed = 5, 7
+    pp = gpu_pp(log_n, seed)
+    m = vec(log_n, seed + 1)
+    t = torch.from_numpy(m.view(np.int64).copy()).cuda()
+    cm = F.Commitment(pp, t, stream=torch.cuda.current_stream())
+    assert cm.get() == oracle_commit(log_n, seed)
+
+
+# ------------------------------------------------------------------ N = 2^16 (benchmark workload)
+def row_closed_form(opp, m_ints):
+    beta, tau = opp.trapdoor()
+    g1 = O.g1_gen()
+    R, M = opp.R, opp.M
+    rows = []
+    fj = []
+    for j in range(R):
+        f = ref.mle_eval(m_ints[j * M:(j + 1) * M], tau)
+        fj.append(f)
+        rows.append(O.g1_mul(g1, f))
+    s = sum(fj[j] * pow(beta, 2 * j, ref.R) for j in range(R)) % ref.R
+    C = O.fq12_pow(O.pairing(g1, O.g2_gen()), s)
+    return C, b"".join(rows)
+
+
+@functools.lru_cache(maxsize=None)
+def n16(dist):
+    log_n, seed = 16, 0
+    pp, opp = gpu_pp(log_n, seed), oracle_pp(log_n, seed)
+    m = vec(log_n, seed + 1, dist)
+    cm = F.Commitment(pp, m)
+    return pp, opp, m, cm
+
+
+@pytest.mark.parametrize("dist", ["uniform", "u32"])
+def test_n16_commit_closed_form(dist):
+    pp, opp, m, cm = n16(dist)
+    assert cm.get() == row_closed_form(opp, I.to_ints(m))
+
+
+@pytest.mark.parametrize("b,blocks", [(256, [0]), (1, [0, 77, 255])])
+def test_n16_prove_all_sampled(b, blocks):
+    pp, opp, m, cm = n16("uniform")
+    C, rows = cm.get()
+    pf = F.Proofs(pp, cm, b)
+    pr = O.Prover(opp, m.tobytes(), C, rows, b)
+    pr.blocks(blocks)
+    pr.step2()
+    assert pf.step2_parts() == pr.step2_parts()
+    rnd = random.Random(5)
+    vals = I.to_ints(m)
+    for k in blocks:
+        j = k * b + rnd.randrange(min(b, pp.R - k * b))
+        for a in (0, rnd.randrange(pp.M), pp.M - 1):
+            i = j * pp.M + a
+            e = pr.proof(i)
+            assert pf.proof(i) == e
+            assert O.verify(opp, C, b, i, vals[i], e)
