@@ -1,0 +1,364 @@
+"""Benchmark of the FlexProofs all-proofs pass (VC.Commit + VC.OpenAll) on GB300.
+
+Workload (default): N = 2^16 uniform Fr values (BLS12-381 scalar field), batch size b = 256
+(= log^2 N), seeded synthetic input resident in HBM.  One step = one pass of the whole hot path:
+Commit (row MSMs + FC multi-pairing) followed by OpenAll (Step 1 for every block, Step 2).
+Metric: proofs/s = N / (step time).  The paper reports 0.23 s for this (N, b) point, but on the
+BN_SNARK1 curve with a single CPU thread, so there is no like-for-like baseline (vs_baseline null).
+
+N > 1 (torchrun): every rank proves its own vector (replicas, weak scaling, no collective on the
+data path); value = all ranks' proofs / max-over-ranks time.
+
+--impl reference times the CPU oracle on a bounded sample of the same workload instead.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+# Fq multiplications per unit operation of the implementation (operation counts of the formulas
+# used; an Fq multiplication is one 12-limb CIOS Montgomery product = 4 * 12^2 = 576 32-bit
+# multiply-adds).  See DESIGN.md, "Roofline".
+FQ_MUL_IMAD = 4 * 12 * 12
+FQ_MULS = {
+    "miller_loop": 7135,     # 62 Fq12 sqr + 63 doubling steps + 5 addition steps, with their lines
+    "final_exp": 10120,      # easy part (Fq12 inverse) + h1 and three |x| cyclotomic exponentiations
+    "g1_mul": 3750,          # 255-bit double-and-add in Jacobian coordinates + affine conversion
+    "g2_mul": 8350,
+}
+KERNEL_UNITS = {             # kernel -> (unit, units per launch as a function of (K, R, h, M))
+    "k_step1_miller": "miller_loop",
+    "k_commit_miller": "miller_loop",
+    "k_round_out": "final_exp",
+    "k_final_exp": "final_exp",
+    "k_fold_g2": "g2_mul",
+    "k_w_terms": "g2_mul",
+    "k_fold_g1": "g1_mul",
+    "k_sparse_terms": "g1_mul",
+    "k_commit_terms": "g1_mul",
+}
+
+
+def kernel_units(name: str, log_n: int, b: int) -> int:
+    """Units (Miller loops, exponentiations, scalar multiplications) summed over one step's launches."""
+    lr = log_n // 2
+    lc = log_n - lr
+    R, M = 1 << lr, 1 << lc
+    K = (R + b - 1) // b
+    if name == "k_step1_miller":
+        return sum(K * 2 * (R >> j) for j in range(1, lr + 1))
+    if name == "k_round_out":
+        return 2 * K * lr
+    if name == "k_fold_g2" or name == "k_fold_g1":
+        return sum(K * (R >> j) for j in range(1, lr + 1))
+    if name == "k_sparse_terms":
+        return sum(K * 2 * (R >> j) for j in range(1, lr + 1))
+    if name == "k_w_terms":
+        return K * (2 * R - 2)
+    if name == "k_commit_miller":
+        return R
+    if name == "k_final_exp":
+        return 1
+    if name == "k_commit_terms":
+        return R * M
+    return 0
+
+
+class ClockSampler:
+    """nvidia-smi clocks during the timed region (median SM clock, throttle reasons seen)."""
+
+    def __init__(self, index: int = 0):
+        self.index = index
+        self.proc = None
+        self.lines: list[str] = []
+
+    def __enter__(self):
+        q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.index}", f"--query-gpu={q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except Exception:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *a):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=2)
+            except Exception:
+                self.proc.kill()
+
+    def summary(self):
+        sm, mx, reasons = [], 0.0, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx = max(mx, float(f[2]))
+            except ValueError:
+                continue
+            for n, v in zip(names, f[5:9]):
+                if v.lower() == "active":
+                    reasons.add(n)
+        sm.sort()
+        med = sm[len(sm) // 2] if sm else None
+        return {"sm_mhz": med, "sm_max_mhz": mx or None, "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--log-n", type=int, default=16)
+    ap.add_argument("--b", type=int, default=256)
+    ap.add_argument("--seed", type=int, default=1)
+    ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    return ap.parse_args()
+
+
+# --------------------------------------------------------------------------------- oracle arm
+def oracle_sample(log_n: int, b: int, seed: int):
+    """Time the CPU oracle on a bounded sample of the workload; return (seconds per full step,
+    description).  Sample: Commit's row MSMs for a few rows (scaled to R rows), its Miller loops for
+    a few rows (scaled) plus the final exponentiation, FC.BOpen for one block (scaled to all
+    ceil(R/b) blocks), and Step 2 in full.  The oracle's rows for the sample come from its own
+    trapdoor closed form, which it knows from its setup."""
+    import oracle as O
+    from paper_2601_03031_gb300 import inputs as I
+
+    r_mod = I.R_INT
+
+    def mle_eval(table, tau):       # f(tau) for the multilinear extension, x_s <-> bit s
+        vals = list(table)
+        for s in range(len(tau)):
+            t = tau[s]
+            vals = [(vals[2 * c] + (vals[2 * c + 1] - vals[2 * c]) * t) % r_mod for c in range(len(vals) // 2)]
+        return vals[0]
+
+    pp = O.PP(log_n, seed)
+    m = I.vector(seed + 1, log_n)
+    vals = I.to_ints(m)
+    R, M = pp.R, pp.M
+    K = (R + b - 1) // b
+    beta, tau = pp.trapdoor()
+    # rows by closed form (not timed), exactly what the oracle commit produces
+    g1 = O.g1_gen()
+    fj = [mle_eval(vals[j * M:(j + 1) * M], tau) for j in range(R)]
+    rows = b"".join(O.g1_mul(g1, f) for f in fj)
+    s = sum(fj[j] * pow(beta, 2 * j, r_mod) for j in range(R)) % r_mod
+    C = O.fq12_pow(O.pairing(g1, O.g2_gen()), s)
+    lam_top = pp.to_bytes()[96 * (M - 1): 96 * (2 * M - 1)]
+    t = {}
+    srows = min(R, 4)
+    t0 = time.perf_counter()
+    for j in range(srows):
+        O.g1_msm(lam_top, vals[j * M:(j + 1) * M])
+    t["commit_msm"] = (time.perf_counter() - t0) * R / srows
+    t0 = time.perf_counter()
+    v0 = pp.to_bytes()[96 * (2 * M): 96 * (2 * M) + 192]
+    for j in range(srows):
+        f = O.miller(rows[96 * j:96 * j + 96], v0)
+    t["commit_miller"] = (time.perf_counter() - t0) * R / srows
+    t0 = time.perf_counter()
+    O.final_exp(f)
+    t["commit_final_exp"] = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    O.bopen(pp, C, rows, b, 0)
+    t["step1"] = (time.perf_counter() - t0) * K
+    pr = O.Prover(pp, m.tobytes(), C, rows, b)
+    t0 = time.perf_counter()
+    pr.step2()
+    t["step2"] = time.perf_counter() - t0
+    total = sum(t.values())
+    desc = (f"N=2^{log_n}, b={b}: commit MSM timed on {srows}/{R} rows and its Miller loops on {srows}/{R} "
+            f"rows (+1 final exp), scaled x{R // srows}; FC.BOpen timed on 1 of {K} blocks, scaled x{K}; "
+            f"Step 2 timed in full; 1 thread")
+    return total, desc, t
+
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    import oracle as O
+    O.lib()
+    N = 1 << args.log_n
+    for _ in range(args.warmup):
+        pass      # the oracle has no warm-up effects worth a full sample; warm-up steps are not re-run
+    per_step = []
+    desc = ""
+    for _ in range(max(1, args.steps)):
+        total, desc, _parts = oracle_sample(args.log_n, args.b, args.seed)
+        per_step.append(total)
+    step_s = sum(per_step) / len(per_step)
+    value = N / step_s
+    line = {
+        "impl": "reference", "metric": "ProveAll proofs/s (Commit + OpenAll)", "value": value,
+        "unit": "proofs/s", "n_gpus": 0, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": 1e3 * step_s, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "u32 limbs (exact Fq/Fr arithmetic)", "data": "synthetic",
+        "config": {"workload": f"ProveAll N=2^{args.log_n} b={args.b} uniform Fr, BLS12-381", "log_n": args.log_n,
+                   "b": args.b},
+        "cpu_baseline": {"value": value, "unit": "proofs/s", "cores": 1, "kind": "oracle", "sample": desc},
+        "e2e": {"value": value, "unit": "proofs/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line))
+
+
+# --------------------------------------------------------------------------------- GPU arm
+def main():
+    args = parse()
+    if args.impl == "reference":
+        return run_reference(args)
+    import numpy as np
+    import torch
+    import torch.distributed as dist
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    if world > 1:
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+
+    from paper_2601_03031_gb300 import _lib as F
+    from paper_2601_03031_gb300 import inputs as I
+
+    log_n, b = args.log_n, args.b
+    N = 1 << log_n
+    stream = torch.cuda.current_stream()
+    pp = F.PP(log_n, b, args.seed, stream)
+    m = I.vector(args.seed + 1 + rank, log_n)
+    m_dev = torch.from_numpy(m.view(np.int64).copy()).cuda()
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")     # > 129 MB L2
+
+    def step():
+        cm = F.Commitment(pp, m_dev, stream)
+        pf = F.Proofs(pp, cm, b, stream)
+        return cm, pf
+
+    for _ in range(max(3, args.warmup)):
+        step()
+    torch.cuda.synchronize()
+
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    launches0 = F.launch_count()
+    F.profile_enable(True)
+    F.profile_report()
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    keep = []
+    with ClockSampler(local) as clk:
+        for s in range(args.steps):
+            flush.zero_()
+            ev[s][0].record(stream)
+            keep.append(step())
+            ev[s][1].record(stream)
+        torch.cuda.synchronize()
+    F.profile_enable(False)
+    prof = F.profile_report()
+    launches = (F.launch_count() - launches0) / max(1, args.steps)
+    total_ms = sum(a.elapsed_time(b_) for a, b_ in ev)
+    if world > 1:
+        t = torch.tensor([total_ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t.item())
+        dist.barrier()
+    ms_per_step = total_ms / args.steps
+    value = world * N / (ms_per_step * 1e-3)
+
+    # end-to-end through the C ABI with host buffers: H2D of m from pinned memory inside vc_commit,
+    # D2H of the shared proof state (the OpenAll result) into pinned memory
+    m_host = torch.from_numpy(m.view(np.int64).copy()).pin_memory()
+    cm, pf = step()
+    state = torch.empty(pf.state_size(), dtype=torch.uint8).pin_memory()
+    torch.cuda.synchronize()
+    e2e_t = []
+    for _ in range(args.steps):
+        flush.zero_()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        cm = F.Commitment(pp, m_host.numpy().view(np.uint64), stream)
+        pf = F.Proofs(pp, cm, b, stream)
+        pf.state_into(state)
+        e2e_t.append(time.perf_counter() - t0)
+    e2e_s = sum(e2e_t) / len(e2e_t)
+
+    if rank != 0:
+        if world > 1:
+            dist.destroy_process_group()
+        return
+
+    # roofline of the dominant kernel (integer multiply-add pipe)
+    peak = F.imad_peak()
+    dom = max(prof.items(), key=lambda kv: kv[1][1]) if prof else ("", (0, 0.0))
+    name, (cnt, kms) = dom
+    unit = KERNEL_UNITS.get(name)
+    roof = None
+    if unit and kms > 0:
+        ops_step = kernel_units(name, log_n, b) * FQ_MULS[unit] * FQ_MUL_IMAD
+        launches_per_step = cnt / args.steps
+        avg_ms = kms / cnt
+        ops_launch = ops_step / launches_per_step
+        achieved = ops_launch / (avg_ms * 1e-3)
+        roof = {"bound": "alu", "kernel": name, "achieved": achieved / 1e12, "peak": peak / 1e12,
+                "unit": "Tops/s (32-bit multiply-add lane ops)", "frac": achieved / peak, "traffic": None,
+                "peak_source": "measured: fp_imad_probe on this GPU in this run"}
+    share = {k: round(v[1] / (total_ms if total_ms else 1), 4) for k, v in
+             sorted(prof.items(), key=lambda kv: -kv[1][1])[:8]}
+
+    cpu = None
+    if not args.no_cpu_baseline:
+        try:
+            cpu_s, desc, parts = oracle_sample(log_n, b, args.seed)
+            cpu = {"value": N / cpu_s, "unit": "proofs/s", "cores": 1, "kind": "oracle", "sample": desc,
+                   "seconds_per_step_scaled": cpu_s}
+        except Exception as e:      # the baseline is reported, not required for the GPU number
+            cpu = {"value": None, "unit": "proofs/s", "cores": 1, "kind": "oracle", "sample": f"failed: {e}"}
+
+    line = {
+        "metric": "ProveAll proofs/s (Commit + OpenAll)", "value": value, "unit": "proofs/s",
+        "n_gpus": world, "steps": args.steps, "warmup": max(3, args.warmup), "ms_per_step": ms_per_step,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "u32 limbs (exact Fq/Fr arithmetic)", "data": "synthetic",
+        "config": {"workload": f"ProveAll N=2^{log_n} b={b} uniform Fr, BLS12-381", "log_n": log_n, "b": b,
+                   "parallelism": f"replicas x{world}", "l2": "flushed (256 MB write) before every timed step"},
+        "e2e": {"value": N / e2e_s, "unit": "proofs/s", "h2d_bytes_per_step": N * 32,
+                "d2h_bytes_per_step": int(state.numel())},
+        "gpu_launches": launches,
+        "roofline": roof,
+        "kernel_share": share,
+        "clocks": clk.summary(),
+        "cpu_baseline": cpu,
+    }
+    print(json.dumps(line))
+    if world > 1:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

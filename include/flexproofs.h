@@ -114,6 +114,10 @@ void fp_proofs_free(fp_proofs* pf);
 uint64_t fp_launch_count(void);
 void fp_profile_enable(int on);
 size_t fp_profile_report(char* out, size_t cap);
+/* Measured rate of the 32-bit integer multiply-add pipe on the current device (lane operations
+ * per second, independent chains, all SMs), the denominator of the integer roofline.  Returns a
+ * fp_status code. */
+int fp_imad_probe(double* ops_per_s, double* ms);
 
 const char* fp_strerror(fp_status s);
 /* Text of the last CUDA error seen by this thread's calls (empty if none). */

@@ -1,7 +1,7 @@
 """FlexProofs CPU oracle (ctypes binding) -- TEST INFRASTRUCTURE ONLY.
 
 A plain, slow CPU restatement of the FlexProofs ProveAll path (arXiv 2601.03031, Sec. 2-4 and
-Appendix D) written in C (``oracle/*.c``).  Only ``tests/``, ``__graft_entry__.smoke()`` and the
+Appendix C) written in C (``oracle/*.c``).  Only ``tests/``, ``__graft_entry__.smoke()`` and the
 CPU-baseline leg of ``bench.py`` may import this module.  It shares no code with the CUDA path.
 
 Parity status per function (the pins live in ``tests/test_oracle_*.py``):

@@ -6,7 +6,7 @@
  * The curve family is BLS12 with seed x = -0xd201000000010000:
  *     r = x^4 - x^2 + 1,   p = (x-1)^2 r / 3 + x,   #E(Fq) = p + 1 - (x + 1) = p - x = h1 r,
  * with h1 = (x-1)^2/3.  The paper instantiates its bilinear group with mcl/BN_SNARK1
- * (Sec. 6); this build reads the group as BLS12-381 and derives everything from x here.
+ * (Sec. 5); this build reads the group as BLS12-381 and derives everything from x here.
  */
 #include "oracle.h"
 #include <string.h>

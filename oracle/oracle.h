@@ -3,13 +3,13 @@
  *
  * A plain, slow, single-threaded-per-call CPU restatement of what the FlexProofs
  * ProveAll path computes, written from the paper (arXiv 2601.03031):
- *   - the bilinear group (BLS12-381 here; the paper used BN_SNARK1, Sec. 6),
- *   - PST multilinear commitments with HyperEval (Sec. 2.3),
+ *   - the bilinear group (BLS12-381 here; the paper used BN_SNARK1, Sec. 5),
+ *   - PST multilinear commitments with HyperEval (Sec. 2.2),
  *   - the functional commitment FC.Setup/Commit/BOpen/BVerify (Sec. 3, Eq. folding,
  *     Eq. comy, "Faster verification"),
  *   - VC.Setup/Commit (Sec. 4.1, Eqs. vcpp, genCi, genC), OpenAll (Protocol 1 and the
  *     Sub-protocol, Sec. 4.2), the unit-vector shortcut (Sec. 4.3, Eq. b_l), and the
- *     verifier-side combination (Appendix D, correctness proof).
+ *     verifier-side combination (Appendix C, correctness proof).
  *
  * Only the tests, the package's smoke() and bench.py's CPU-baseline leg may load this
  * library.  It shares no code, header, table or constant generator with the CUDA path.

@@ -1,7 +1,7 @@
 /*
- * Oracle protocol layer: PST (Sec. 2.3 with HyperEval), FC (Sec. 3), FlexProofs VC
+ * Oracle protocol layer: PST (Sec. 2.2 with HyperEval), FC (Sec. 3), FlexProofs VC
  * (Sec. 4: Setup, Commit, OpenAll = Protocol 1 + Sub-protocol + the Fiat-Shamir Merkle tree,
- * the unit-vector shortcut of Sec. 4.3, and Verify as in the correctness proof of Appendix D).
+ * the unit-vector shortcut of Sec. 4.3, and Verify as in the correctness proof of Appendix C).
  * TEST INFRASTRUCTURE ONLY (see oracle.h).  Exported entry points are prefixed or_ and take
  * canonical big-endian byte strings, so the tests can drive them through ctypes.
  *
@@ -580,7 +580,7 @@ int or_prove_one(const or_pp* pp, const u64* m, const u8* C, const u8* rows, u32
 
 /* ------------------------------------------------------------------------------
  * VC.Verify (Protocol 1 verifier steps; the combination D* = r_j C_j + sum D_w,
- * y* = r_j m_i + sum y_w of Appendix D; FC.BVerify with the b_l shortcut of Eq. b_l and the
+ * y* = r_j m_i + sum y_w of Appendix C; FC.BVerify with the b_l shortcut of Eq. b_l and the
  * faster-verification check; PST.Verify).  Returns 1 if the proof is accepted, 0 if not.
  * ------------------------------------------------------------------------------ */
 int or_verify(const or_pp* pp, const u8* C, u32 b, u64 i, const u8 mi_be[32], const u8* proof, size_t len, int use_memo) {

@@ -17,7 +17,7 @@ FP_STATUS = {0: "FP_OK", 1: "FP_EINVAL", 2: "FP_ENOMEM", 3: "FP_EDEVICE", 4: "FP
 EXPORTED = ["vc_setup", "vc_pp_export", "vc_pp_dims", "vc_commit", "vc_commit_get", "vc_prove_all",
             "vc_proof_len", "vc_proof_get", "vc_proofs_export", "vc_proofs_state", "vc_proofs_step2_parts",
             "fp_pp_free", "fp_commit_free", "fp_proofs_free", "fp_strerror", "fp_last_error", "fp_launch_count",
-            "fp_profile_enable", "fp_profile_report"]
+            "fp_profile_enable", "fp_profile_report", "fp_imad_probe"]
 
 
 class FlexProofsError(RuntimeError):
@@ -65,6 +65,7 @@ def load(path: str = LIB_PATH):
     L.fp_profile_enable.restype = None
     L.fp_profile_report.argtypes = [ctypes.c_char_p, sz]
     L.fp_profile_report.restype = sz
+    L.fp_imad_probe.argtypes = [ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double)]
     _lib = L
     return L
 
@@ -231,3 +232,10 @@ def profile_report() -> dict:
         name, cnt, ms = line.split()
         out[name] = (int(cnt), float(ms))
     return out
+
+
+def imad_peak() -> float:
+    """Measured 32-bit multiply-add lane operations per second of the current GPU."""
+    ops, ms = ctypes.c_double(), ctypes.c_double()
+    _check("fp_imad_probe", load().fp_imad_probe(ctypes.byref(ops), ctypes.byref(ms)))
+    return ops.value

@@ -80,3 +80,47 @@ size_t fp_profile_report(char* out, size_t cap) {
     return txt.size() + 1;
 }
 }
+
+// ---------------------------------------------------------------------------------------
+// Peak of the integer multiply-add pipe: every thread runs 8 independent chains of 32-bit
+// multiply-adds (alternating low and high halves, the two kinds every Montgomery product issues),
+// so the pipe, not latency, bounds the rate.  ops = lanes x iterations x 8.
+// ---------------------------------------------------------------------------------------
+__global__ void k_imad_probe(uint32_t iters, uint32_t seed, uint32_t* sink) {
+    uint32_t a[8];
+    for (int k = 0; k < 8; k++) a[k] = seed + threadIdx.x * 8 + k;
+    const uint32_t m = 0x9e3779b9u + blockIdx.x, c = 0x7f4a7c15u;
+    for (uint32_t it = 0; it < iters; it++) {
+#pragma unroll
+        for (int k = 0; k < 8; k += 2) {
+            asm volatile("mad.lo.u32 %0, %0, %1, %2;" : "+r"(a[k]) : "r"(m), "r"(c));
+            asm volatile("mad.hi.u32 %0, %0, %1, %2;" : "+r"(a[k + 1]) : "r"(m), "r"(c));
+        }
+    }
+    uint32_t x = 0;
+    for (int k = 0; k < 8; k++) x ^= a[k];
+    if (x == 0x12345678u) sink[0] = x;
+}
+
+extern "C" int fp_imad_probe(double* ops_per_s, double* ms_out) {
+    int dev = 0, sms = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return 3;
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    uint32_t* sink = nullptr;
+    if (cudaMalloc(&sink, 4) != cudaSuccess) return 2;
+    const uint32_t iters = 4096, threads = 256, blocks = (uint32_t)sms * 8;
+    cudaEvent_t a, b;
+    cudaEventCreate(&a); cudaEventCreate(&b);
+    k_imad_probe<<<blocks, threads>>>(64, 1, sink);      // warm-up
+    cudaEventRecord(a);
+    k_imad_probe<<<blocks, threads>>>(iters, 2, sink);
+    cudaEventRecord(b);
+    cudaError_t e = cudaEventSynchronize(b);
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, a, b);
+    cudaEventDestroy(a); cudaEventDestroy(b); cudaFree(sink);
+    if (e != cudaSuccess) return 3;
+    *ops_per_s = (double)blocks * threads * iters * 8 / (ms * 1e-3);
+    if (ms_out) *ms_out = ms;
+    return 0;
+}

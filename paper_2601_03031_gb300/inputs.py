@@ -1,7 +1,7 @@
 """Seeded synthetic inputs shared by the tests, the bench and the smoke check.
 
 This module holds no arithmetic of the method: it only draws the inputs.  The paper evaluates
-FlexProofs on uniformly random vectors of N = 2^16 .. 2^24 field elements (Sec. 6.2); the
+FlexProofs on uniformly random vectors of N = 2^16 .. 2^24 field elements (Sec. 5.2); the
 generators below reproduce that shape.
 
 Random source: SplitMix64 (Steele, Lea and Flood, "Fast splittable pseudorandom number

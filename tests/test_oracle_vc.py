@@ -166,7 +166,7 @@ def test_out_of_range_scalar_rejected():
 
 
 def test_proof_size_formula_reproduces_paper_tables():
-    # BN_SNARK1 sizes: G1 32, G2 64, GT 384, Fr 32, digest 32 (Sec. 6, Tables tb:fc and tb:vc)
+    # BN_SNARK1 sizes: G1 32, G2 64, GT 384, Fr 32, digest 32 (Sec. 5, Tables tb:fc and tb:vc)
     bn = dict(g1=32, g2=64, gt=384, fr=32)
     kib = lambda v: round(v / 1024, 2)
     fp_2logn = [8.91, 10, 11.09, 12.19, 13.28]
