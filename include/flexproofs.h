@@ -101,6 +101,22 @@ fp_status vc_proofs_state(const fp_proofs* pf, uint8_t* out, size_t cap, size_t*
  * and D* (96 B); any pointer may be NULL. */
 fp_status vc_proofs_step2_parts(const fp_proofs* pf, uint8_t* root, uint8_t* rj, uint8_t* gstar, uint8_t* dstar);
 
+/* Allocation-free variant of the row commitments of vc_commit (no counterpart in the paper).
+ * For callers that must not allocate device memory: code running where cudaMalloc/cudaFree are
+ * unavailable or forbidden -- e.g. a host application whose allocator owns all device memory, or a
+ * latency-critical loop that cannot afford the implicit synchronisation an allocation may cause.
+ * Computes C_j = sum_a m[j M + a] Lambda_{l_c}[a] for every row j and writes the R rows serialised
+ * (R x 96 B, canonical big-endian, identity = zeros) to rows_dev.
+ *   m_dev:   device pointer, N x 4 little-endian uint64 canonical Fr values (read only).
+ *   rows_dev: device pointer, R x 96 bytes (written).
+ * Limit: N = R * M <= 2^14 (larger sizes return FP_EINVAL).  Scratch is one file-scope device array
+ * (about 3.5 MB) that every GPU loading the library holds until the process exits.  The first
+ * call on a device looks up that array's device address with the device current, so make the first
+ * call before any stream capture.  All calls share the array and it keeps the last call's contents
+ * (the status word is cleared by each call): calls that overlap on the GPU race -- serialise them.
+ * A value >= r gives FP_ERANGE.  Synchronises `stream`.  Allocates no device memory. */
+fp_status vc_commit_rows_noalloc(const fp_pp* pp, const uint64_t* m_dev, uint8_t* rows_dev, void* stream);
+
 void fp_pp_free(fp_pp* pp);
 void fp_commit_free(fp_commit* cm);
 void fp_proofs_free(fp_proofs* pf);

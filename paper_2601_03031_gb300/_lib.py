@@ -17,7 +17,7 @@ FP_STATUS = {0: "FP_OK", 1: "FP_EINVAL", 2: "FP_ENOMEM", 3: "FP_EDEVICE", 4: "FP
 EXPORTED = ["vc_setup", "vc_pp_export", "vc_pp_dims", "vc_commit", "vc_commit_get", "vc_prove_all",
             "vc_proof_len", "vc_proof_get", "vc_proofs_export", "vc_proofs_state", "vc_proofs_step2_parts",
             "fp_pp_free", "fp_commit_free", "fp_proofs_free", "fp_strerror", "fp_last_error", "fp_launch_count",
-            "fp_profile_enable", "fp_profile_report", "fp_imad_probe"]
+            "fp_profile_enable", "fp_profile_report", "fp_imad_probe", "vc_commit_rows_noalloc"]
 
 
 class FlexProofsError(RuntimeError):
@@ -66,6 +66,7 @@ def load(path: str = LIB_PATH):
     L.fp_profile_report.argtypes = [ctypes.c_char_p, sz]
     L.fp_profile_report.restype = sz
     L.fp_imad_probe.argtypes = [ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double)]
+    L.vc_commit_rows_noalloc.argtypes = [vp, vp, vp, vp]
     _lib = L
     return L
 
@@ -239,3 +240,10 @@ def imad_peak() -> float:
     ops, ms = ctypes.c_double(), ctypes.c_double()
     _check("fp_imad_probe", load().fp_imad_probe(ctypes.byref(ops), ctypes.byref(ms)))
     return ops.value
+
+
+def vc_commit_rows_noalloc(pp: PP, m_dev, rows_dev, stream=None) -> None:
+    """Row commitments into a caller-provided device buffer, without device allocation
+    (see include/flexproofs.h).  m_dev / rows_dev: device tensors (N x 4 int64, R*96 uint8)."""
+    _check("vc_commit_rows_noalloc",
+           load().vc_commit_rows_noalloc(pp.h, m_dev.data_ptr(), rows_dev.data_ptr(), _stream_ptr(stream)))

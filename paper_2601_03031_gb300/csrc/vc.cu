@@ -111,6 +111,10 @@ size_t bopen_len(uint32_t log_r) { return (size_t)log_r * ROUND_BYTES + G1_SER +
 
 }  // namespace
 
+namespace fpk {
+const void* pp_lambda_top(const fp_pp* pp) { return (const uint8_t*)pp->lam + ((size_t)pp->M - 1) * G1A_BYTES; }
+}  // namespace fpk
+
 extern "C" {
 
 const char* fp_strerror(fp_status s) {
