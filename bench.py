@@ -31,10 +31,12 @@ FQ_MUL_IMAD = 4 * 12 * 12
 FQ_MULS = {
     "miller_loop": 7135,     # 62 Fq12 sqr + 63 doubling steps + 5 addition steps, with their lines
     "final_exp": 10120,      # easy part (Fq12 inverse) + h1 and three |x| cyclotomic exponentiations
-    "g1_mul": 3750,          # 255-bit double-and-add in Jacobian coordinates + affine conversion
-    "g2_mul": 8350,
+    "g1_mul": 2000,          # GLV: ~128 doublings + ~96 mixed additions over 3 affine points
+    "g2_mul": 3300,          # GLS: 64 doublings + ~60 mixed additions over a 15-point affine table
 }
-KERNEL_UNITS = {             # kernel -> (unit, units per launch as a function of (K, R, h, M))
+KERNEL_UNITS = {             # kernel -> unit whose Fq-multiplication count is in FQ_MULS
+    "k_round_terms": ("miller_loop", "g1_mul"),
+    "k_fold": ("g1_mul", "g2_mul"),
     "k_step1_miller": "miller_loop",
     "k_commit_miller": "miller_loop",
     "k_round_out": "final_exp",
@@ -53,14 +55,12 @@ def kernel_units(name: str, log_n: int, b: int) -> int:
     lc = log_n - lr
     R, M = 1 << lr, 1 << lc
     K = (R + b - 1) // b
-    if name == "k_step1_miller":
+    if name in ("k_step1_miller", "k_round_terms", "k_sparse_terms"):
         return sum(K * 2 * (R >> j) for j in range(1, lr + 1))
     if name == "k_round_out":
         return 2 * K * lr
     if name == "k_fold_g2" or name == "k_fold_g1":
         return sum(K * (R >> j) for j in range(1, lr + 1))
-    if name == "k_sparse_terms":
-        return sum(K * 2 * (R >> j) for j in range(1, lr + 1))
     if name == "k_w_terms":
         return K * (2 * R - 2)
     if name == "k_commit_miller":
@@ -320,7 +320,8 @@ def main():
     unit = KERNEL_UNITS.get(name)
     roof = None
     if unit and kms > 0:
-        ops_step = kernel_units(name, log_n, b) * FQ_MULS[unit] * FQ_MUL_IMAD
+        units = unit if isinstance(unit, tuple) else (unit,)
+        ops_step = kernel_units(name, log_n, b) * sum(FQ_MULS[u] for u in units) * FQ_MUL_IMAD
         launches_per_step = cnt / args.steps
         avg_ms = kms / cnt
         ops_launch = ops_step / launches_per_step

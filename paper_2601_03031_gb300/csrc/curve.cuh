@@ -148,8 +148,6 @@ FPG_DEV g2j g2_from_affine(const g2a& a) {
     r.X = a.x; r.Y = a.y; fq2_one(r.Z);
     return r;
 }
-FPG_DEV g1j g1_mul(const g1a& p, const uint32_t* k) { return jac_mul_affine(p.x, p.y, g1a_is_inf(p), k); }
-FPG_DEV g2j g2_mul(const g2a& p, const uint32_t* k) { return jac_mul_affine(p.x, p.y, g2a_is_inf(p), k); }
 FPG_DEV g1j g1_madd(const g1j& p, const g1a& q) { return g1a_is_inf(q) ? p : jac_madd(p, q.x, q.y); }
 FPG_DEV g2j g2_madd(const g2j& p, const g2a& q) { return g2a_is_inf(q) ? p : jac_madd(p, q.x, q.y); }
 FPG_DEV g1a g1a_neg(const g1a& p) { return g1a_is_inf(p) ? p : g1a{p.x, fq_neg(p.y)}; }
@@ -164,6 +162,156 @@ FPG_DEV g2a g2_generator() {
     fq_from_const(g.y.c0, G2_GEN_Y0); fq_from_const(g.y.c1, G2_GEN_Y1);
     return g;
 }
+
+// ---------------------------------------------------------------------------------------
+// Endomorphism-split scalar multiplication.
+//   G1 (GLV): phi(x, y) = (omega x, y) = [-x^2] on G1, so with k = k0 + k1 |x|^2 (k0 < |x|^2),
+//             k P = k0 P + k1 (-phi(P)): 128-bit halves, one joint double-and-add.
+//   G2 (GLS): psi = untwist-Frobenius-twist acts as [x] on G2, so with base-|x| digits
+//             k = d0 + d1 |x| + d2 |x|^2 + d3 |x|^3 (x < 0), k Q = d0 Q - d1 psi Q + d2 psi^2 Q - d3 psi^3 Q:
+//             64-bit digits, a 16-entry table of subset sums (normalised to affine with one
+//             inversion), one joint double-and-add.
+// ---------------------------------------------------------------------------------------
+
+// q = floor(k / D) and rem = k - q D for a 256-bit k and a constant D < 2^(32 ND), using the
+// Barrett constant bar = floor(2^256 / D) (NB limbs) and at most a few correction steps.
+template <int ND, int NB>
+FPG_DEV void div_by_const(uint32_t* q, uint32_t* rem, const uint32_t* k, const uint32_t* D, const uint32_t* bar) {
+    uint32_t prod[8 + NB];
+    for (int i = 0; i < 8 + NB; i++) prod[i] = 0;
+    for (int i = 0; i < 8; i++) {
+        uint64_t carry = 0;
+        for (int j = 0; j < NB; j++) {
+            uint64_t t = (uint64_t)k[i] * bar[j] + prod[i + j] + carry;
+            prod[i + j] = (uint32_t)t;
+            carry = t >> 32;
+        }
+        prod[i + NB] = (uint32_t)carry;
+    }
+    for (int j = 0; j < NB; j++) q[j] = prod[8 + j];          // estimate, at most a few too small
+    uint32_t r[8];
+    {
+        uint32_t qd[8];
+        for (int i = 0; i < 8; i++) qd[i] = 0;
+        for (int i = 0; i < NB; i++) {
+            uint64_t carry = 0;
+            for (int j = 0; j < ND && i + j < 8; j++) {
+                uint64_t t = (uint64_t)q[i] * D[j] + qd[i + j] + carry;
+                qd[i + j] = (uint32_t)t;
+                carry = t >> 32;
+            }
+            if (i + ND < 8) qd[i + ND] = (uint32_t)carry;
+        }
+        int64_t borrow = 0;
+        for (int i = 0; i < 8; i++) {
+            int64_t d = (int64_t)k[i] - qd[i] - borrow;
+            borrow = d < 0;
+            r[i] = (uint32_t)d;
+        }
+    }
+    for (int it = 0; it < 4; it++) {                          // while r >= D: r -= D, q += 1
+        bool ge = true;
+        for (int i = 7; i >= 0; i--) {
+            uint32_t di = i < ND ? D[i] : 0;
+            if (r[i] != di) { ge = r[i] > di; break; }
+        }
+        if (!ge) break;
+        int64_t borrow = 0;
+        for (int i = 0; i < 8; i++) {
+            int64_t d = (int64_t)r[i] - (i < ND ? D[i] : 0) - borrow;
+            borrow = d < 0;
+            r[i] = (uint32_t)d;
+        }
+        for (int i = 0; i < NB; i++) if (++q[i] != 0) break;
+    }
+    for (int i = 0; i < ND; i++) rem[i] = r[i];
+}
+
+FPG_DEV int bit_of(const uint32_t* a, int i) { return (a[i >> 5] >> (i & 31)) & 1; }
+
+// k P for affine P in G1 and a canonical scalar k < r.  The three non-zero digit pairs select one of
+// three affine points (P, -phi(P), P - phi(P)), so every step is one doubling and at most one mixed
+// addition with the same code path in every lane.
+FPG_NOINL g1j g1_mul_glv(const g1a& P, const uint32_t* k) {
+    g1j acc;
+    jac_set_inf(acc);
+    if (g1a_is_inf(P)) return acc;
+    uint32_t k1[5], k0[4];
+    div_by_const<4, 5>(k1, k0, k, GLV_D, GLV_BARRETT);
+    fq om;
+    fq_from_const(om, GLV_OMEGA);
+    g1a T[4];
+    T[1] = P;
+    T[2] = {fq_mul(P.x, om), fq_neg(P.y)};                                     // -phi(P)
+    T[3] = g1_affine(jac_madd(g1_from_affine(P), T[2].x, T[2].y));              // P - phi(P) = [1 + x^2] P
+    int top = 159;
+    while (top >= 0 && !(top < 128 && bit_of(k0, top)) && !bit_of(k1, top)) top--;
+    for (int i = top; i >= 0; i--) {
+        acc = jac_dbl(acc);
+        const int s = (i < 128 ? bit_of(k0, i) : 0) | (bit_of(k1, i) << 1);
+        if (s) acc = jac_madd(acc, T[s].x, T[s].y);
+    }
+    return acc;
+}
+
+FPG_DEV g2a g2_psi(const g2a& p) {
+    fq2 cx, cy;
+    fq_from_const(cx.c0, PSI_CX0); fq_from_const(cx.c1, PSI_CX1);
+    fq_from_const(cy.c0, PSI_CY0); fq_from_const(cy.c1, PSI_CY1);
+    return {fq2_mul(fq2_conj(p.x), cx), fq2_mul(fq2_conj(p.y), cy)};
+}
+
+// k Q for affine Q in G2 and a canonical scalar k < r
+FPG_NOINL g2j g2_mul_gls(const g2a& Q, const uint32_t* k) {
+    g2j acc;
+    jac_set_inf(acc);
+    if (g2a_is_inf(Q)) return acc;
+    uint32_t q1[7], q2[7], q3[7], d[4][2];
+    div_by_const<2, 7>(q1, d[0], k, GLS_D, GLS_BARRETT);
+    uint32_t t8[8];
+    for (int i = 0; i < 8; i++) t8[i] = i < 7 ? q1[i] : 0;
+    div_by_const<2, 7>(q2, d[1], t8, GLS_D, GLS_BARRETT);
+    for (int i = 0; i < 8; i++) t8[i] = i < 7 ? q2[i] : 0;
+    div_by_const<2, 7>(q3, d[2], t8, GLS_D, GLS_BARRETT);
+    d[3][0] = q3[0]; d[3][1] = q3[1];
+    // bases B_i = (-1)^i psi^i(Q)
+    g2a B[4];
+    B[0] = Q;
+    for (int i = 1; i < 4; i++) B[i] = g2_psi(B[i - 1]);
+    B[1].y = fq2_neg(B[1].y);
+    B[3].y = fq2_neg(B[3].y);
+    // subset sums T[s] = sum_{i in s} B_i, then affine with one inversion (Montgomery's trick)
+    g2j T[16];
+    for (int s = 1; s < 16; s++) {
+        int top = 31 - __clz(s);
+        int rest = s & ~(1 << top);
+        T[s] = rest ? jac_madd(T[rest], B[top].x, B[top].y) : g2_from_affine(B[top]);
+    }
+    fq2 pre[16];
+    pre[1] = T[1].Z;
+    for (int s = 2; s < 16; s++) pre[s] = fq2_mul(pre[s - 1], T[s].Z);
+    fq2 inv = fq2_inv(pre[15]);
+    g2a TA[16];
+    for (int s = 15; s >= 1; s--) {
+        fq2 zi = s > 1 ? fq2_mul(inv, pre[s - 1]) : inv;
+        if (s > 1) inv = fq2_mul(inv, T[s].Z);
+        fq2 zi2 = fq2_sqr(zi);
+        TA[s].x = fq2_mul(T[s].X, zi2);
+        TA[s].y = fq2_mul(T[s].Y, fq2_mul(zi2, zi));
+    }
+    int top = 63;
+    while (top >= 0 && !(bit_of(d[0], top) | bit_of(d[1], top) | bit_of(d[2], top) | bit_of(d[3], top))) top--;
+    for (int i = top; i >= 0; i--) {
+        acc = jac_dbl(acc);
+        int s = bit_of(d[0], i) | (bit_of(d[1], i) << 1) | (bit_of(d[2], i) << 2) | (bit_of(d[3], i) << 3);
+        if (s) acc = jac_madd(acc, TA[s].x, TA[s].y);
+    }
+    return acc;
+}
+
+// scalar multiplication by a canonical k < r (GLV on G1, GLS on G2)
+FPG_DEV g1j g1_mul(const g1a& p, const uint32_t* k) { return g1_mul_glv(p, k); }
+FPG_DEV g2j g2_mul(const g2a& p, const uint32_t* k) { return g2_mul_gls(p, k); }
 
 // canonical big-endian serialisation (identity = all zero bytes)
 FPG_DEV void g1a_to_be(uint8_t* out, const g1a& p) { fq_to_be(out, p.x); fq_to_be(out + 48, p.y); }

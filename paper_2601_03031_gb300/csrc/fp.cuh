@@ -129,6 +129,75 @@ FPG_DEV bool lt(const uint32_t* a, const uint32_t* P) {
     return ptx::subc(0, 0) != 0;
 }
 
+// Plain modular inverse of x (0 < x < P, P odd) by the binary extended Euclidean algorithm
+// (Stein's gcd with the Bezout coefficients kept mod P).  Invariants: x1 * x = u, x2 * x = v (mod P).
+// Variable time; the values inverted here are public.  Returns 0 for x = 0.
+template <int N>
+FPG_DEV void binv(uint32_t* r, const uint32_t* x, const uint32_t* P) {
+    uint32_t u[N], v[N], x1[N], x2[N];
+#pragma unroll
+    for (int j = 0; j < N; j++) { u[j] = x[j]; v[j] = P[j]; x1[j] = 0; x2[j] = 0; }
+    x1[0] = 1;
+    if (is_zero<N>(u)) {
+#pragma unroll
+        for (int j = 0; j < N; j++) r[j] = 0;
+        return;
+    }
+    auto is_one = [](const uint32_t* a) {
+        uint32_t acc = a[0] ^ 1u;
+#pragma unroll
+        for (int j = 1; j < N; j++) acc |= a[j];
+        return acc == 0;
+    };
+    // a <- a / 2 mod P for a < P: add P when odd (the sum has N+1 words), then shift right
+    auto halve = [&](uint32_t* a) {
+        uint32_t hi = 0;
+        if (a[0] & 1) {
+            a[0] = ptx::add_cc(a[0], P[0]);
+#pragma unroll
+            for (int j = 1; j < N; j++) a[j] = ptx::addc_cc(a[j], P[j]);
+            hi = ptx::addc(0, 0);
+        }
+#pragma unroll
+        for (int j = 0; j < N - 1; j++) a[j] = __funnelshift_r(a[j], a[j + 1], 1);
+        a[N - 1] = __funnelshift_r(a[N - 1], hi, 1);
+    };
+    auto shr1 = [](uint32_t* a) {
+#pragma unroll
+        for (int j = 0; j < N - 1; j++) a[j] = __funnelshift_r(a[j], a[j + 1], 1);
+        a[N - 1] >>= 1;
+    };
+    // every pass shifts or subtracts; for canonical input < 4 * 32N passes suffice, the bound only
+    // guarantees termination on a non-canonical input (the result is then meaningless)
+    for (int guard = 0; guard < 8 * 32 * N && !is_one(u) && !is_one(v); guard++) {
+        if (!(u[0] & 1)) { shr1(u); halve(x1); continue; }
+        if (!(v[0] & 1)) { shr1(v); halve(x2); continue; }
+        // u >= v ?  t = u - v
+        uint32_t t[N];
+        t[0] = ptx::sub_cc(u[0], v[0]);
+#pragma unroll
+        for (int j = 1; j < N; j++) t[j] = ptx::subc_cc(u[j], v[j]);
+        const uint32_t borrow = ptx::subc(0, 0);
+        if (!borrow) {
+#pragma unroll
+            for (int j = 0; j < N; j++) u[j] = t[j];
+            mod_sub<N>(x1, x1, x2, P);
+        } else {
+            v[0] = ptx::sub_cc(v[0], u[0]);
+#pragma unroll
+            for (int j = 1; j < N; j++) v[j] = ptx::subc_cc(v[j], u[j]);
+            mod_sub<N>(x2, x2, x1, P);
+        }
+    }
+    if (is_one(u)) {
+#pragma unroll
+        for (int j = 0; j < N; j++) r[j] = x1[j];
+    } else {
+#pragma unroll
+        for (int j = 0; j < N; j++) r[j] = x2[j];
+    }
+}
+
 }  // namespace mp
 
 // ---------------------------------------------------------------------------------------
@@ -159,14 +228,13 @@ FPG_DEV fq fq_from_mont(const fq& a) {
     fq one; fq_zero(one); one.v[0] = 1;
     return fq_mul(a, one);
 }
-// a^(p-2) by left-to-right square-and-multiply over the constant exponent bits (Fermat)
+// Inverse of a Montgomery residue aR: the plain inverse (aR)^-1 by binary extended gcd, then one
+// Montgomery product with R^3 gives a^-1 R.  0 maps to 0.
 FPG_NOINL fq fq_inv(const fq& a) {
-    fq acc; fq_one(acc);
-    for (int i = 380; i >= 0; i--) {
-        acc = fq_sqr(acc);
-        if ((FQ_PM2[i >> 5] >> (i & 31)) & 1) acc = fq_mul(acc, a);
-    }
-    return acc;
+    fq t, r3;
+    mp::binv<12>(t.v, a.v, FQ_P);
+    fq_from_const(r3, FQ_R3);
+    return fq_mul(t, r3);
 }
 
 // ---------------------------------------------------------------------------------------
@@ -196,12 +264,11 @@ FPG_DEV fr fr_from_mont(const fr& a) {
 }
 FPG_DEV bool fr_canonical_lt_r(const fr& a) { return mp::lt<8>(a.v, FR_P); }
 FPG_NOINL fr fr_inv(const fr& a) {
-    fr acc; fr_one(acc);
-    for (int i = 254; i >= 0; i--) {
-        acc = fr_mul(acc, acc);
-        if ((FR_PM2[i >> 5] >> (i & 31)) & 1) acc = fr_mul(acc, a);
-    }
-    return acc;
+    fr t, r3;
+    mp::binv<8>(t.v, a.v, FR_P);
+#pragma unroll
+    for (int j = 0; j < 8; j++) r3.v[j] = FR_R3[j];
+    return fr_mul(t, r3);
 }
 // Montgomery form of the 512-bit big-endian integer in `be` reduced mod r:
 // mont(hi 2^256 + lo) = mont_mul(hi, R^3) + mont_mul(lo, R^2) with R = 2^256.

@@ -68,6 +68,63 @@ def g1_mul(k, pt):  # affine double-and-add, only for the order check
 assert g1_mul(R, G1) is None
 
 XI = (1, 1)
+
+
+def f2inv(a):
+    n = pow((a[0] * a[0] + a[1] * a[1]) % P, -1, P)
+    return (a[0] * n % P, (-a[1]) * n % P)
+
+
+# GLV on G1: phi(x, y) = (omega x, y) acts as [lambda] with lambda = -x^2 mod r for the cube root of
+# unity omega picked below; k = k0 + k1 |x|^2 gives k P = k0 P + k1 (-phi(P)).
+_g = 2
+while pow(_g, (P - 1) // 3, P) == 1:
+    _g += 1
+_w = pow(_g, (P - 1) // 3, P)
+OMEGA = None
+for _om in (_w, _w * _w % P):
+    if g1_mul((-X * X) % R, G1) == ((_om * G1[0]) % P, G1[1]):
+        OMEGA = _om
+assert OMEGA is not None
+XABS = -X
+D_GLV = XABS * XABS
+BAR_GLV = (1 << 256) // D_GLV           # Barrett constant for floor(k / |x|^2), k < 2^256
+BAR_X = (1 << 256) // XABS              # Barrett constant for floor(k / |x|)
+# GLS on G2: psi(x, y) = (conj(x) cx, conj(y) cy), cx = xi^-((p-1)/3), cy = xi^-((p-1)/2), acts as [x];
+# with base-|x| digits d_i of k, k Q = d0 Q - d1 psi(Q) + d2 psi^2(Q) - d3 psi^3(Q).
+PSI_CX = f2inv(f2pow(XI, (P - 1) // 3))
+PSI_CY = f2inv(f2pow(XI, (P - 1) // 2))
+
+
+def psi(pt):
+    (x0, x1), (y0, y1) = pt
+    return (f2mul((x0, (-x1) % P), PSI_CX), f2mul((y0, (-y1) % P), PSI_CY))
+
+
+def g2_affine_mul(k, pt):          # affine double-and-add on the twist, only for the check below
+    def add(A, B):
+        if A is None: return B
+        if B is None: return A
+        if A[0] == B[0]:
+            if ((A[1][0] + B[1][0]) % P, (A[1][1] + B[1][1]) % P) == (0, 0): return None
+            num = f2mul((3, 0), f2mul(A[0], A[0]))
+            lam = f2mul(num, f2inv(((2 * A[1][0]) % P, (2 * A[1][1]) % P)))
+        else:
+            lam = f2mul(((B[1][0] - A[1][0]) % P, (B[1][1] - A[1][1]) % P),
+                        f2inv(((B[0][0] - A[0][0]) % P, (B[0][1] - A[0][1]) % P)))
+        l2 = f2mul(lam, lam)
+        x3 = ((l2[0] - A[0][0] - B[0][0]) % P, (l2[1] - A[0][1] - B[0][1]) % P)
+        t = f2mul(lam, ((A[0][0] - x3[0]) % P, (A[0][1] - x3[1]) % P))
+        return (x3, ((t[0] - A[1][0]) % P, (t[1] - A[1][1]) % P))
+    acc = None
+    for bit in bin(k)[2:]:
+        acc = add(acc, acc)
+        if bit == "1":
+            acc = add(acc, pt)
+    return acc
+
+
+assert psi(G2) == g2_affine_mul(X % R, G2)
 FROB1 = [f2pow(XI, k * (P - 1) // 6) for k in range(6)]
 FROB2 = [f2pow(XI, k * (P * P - 1) // 6) for k in range(6)]
 assert all(c[1] == 0 for c in FROB2)
@@ -118,6 +175,7 @@ out.append(f"#define FQ_PINV 0x{(-pow(P, -1, 2**32)) % 2**32:08x}u\n")
 out.append(arr("FQ_ONE", mont(1, 12), 12))
 out.append(arr("FQ_R2", (1 << 768) % P, 12))
 out.append(arr("FQ_PM2", P - 2, 12))
+out.append(arr("FQ_R3", (1 << 1152) % P, 12))
 out.append(arr("FR_P", R, 8))
 out.append(f"#define FR_PINV 0x{(-pow(R, -1, 2**32)) % 2**32:08x}u\n")
 out.append(arr("FR_ONE", mont(1, 8), 8))
@@ -136,6 +194,15 @@ for k in range(6):
     out.append(arr(f"FROB1_{k}_C1", mont(FROB1[k][1], 12), 12))
     out.append(arr(f"FROB2_{k}", mont(FROB2[k][0], 12), 12))
 out.append(f"#define BLS_X_ABS 0x{-X:016x}ull\n")
+out.append(arr("GLV_OMEGA", mont(OMEGA, 12), 12))
+out.append(arr("GLV_D", D_GLV, 4))
+out.append(arr("GLV_BARRETT", BAR_GLV, 5))
+out.append(arr("GLS_D", XABS, 2))
+out.append(arr("GLS_BARRETT", BAR_X, 7))
+out.append(arr("PSI_CX0", mont(PSI_CX[0], 12), 12))
+out.append(arr("PSI_CX1", mont(PSI_CX[1], 12), 12))
+out.append(arr("PSI_CY0", mont(PSI_CY[0], 12), 12))
+out.append(arr("PSI_CY1", mont(PSI_CY[1], 12), 12))
 out.append(arr("BLS_H1", H1, 4))
 out.append("__constant__ uint32_t SHA256_K[64] = {" + ", ".join(f"0x{k:08x}u" for k in SHA_K) + "};\n")
 out.append("__constant__ uint32_t SHA256_H0[8] = {" + ", ".join(f"0x{k:08x}u" for k in SHA_H) + "};\n")

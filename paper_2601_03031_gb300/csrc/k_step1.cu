@@ -61,6 +61,54 @@ __global__ void __launch_bounds__(64) k_sparse_terms(const g1a* A, const fr* bve
     out[t] = res;
 }
 
+// Round j's two independent batches in one launch: blocks [0, nb_ml) run the Miller loops of
+// k_step1_miller's pairs, the remaining blocks the sparse G1 terms of k_sparse_terms.
+__global__ void __launch_bounds__(64) k_round_terms(const g1a* A, const g2a* v, const fr* bvec, uint32_t K,
+                                                    uint32_t R, uint32_t h, uint32_t nb_ml, fq12* ml_out,
+                                                    g1j* sp_out) {
+    const bool ml = blockIdx.x < nb_ml;
+    uint64_t t = (uint64_t)(ml ? blockIdx.x : blockIdx.x - nb_ml) * blockDim.x + threadIdx.x;
+    if (t >= (uint64_t)K * 2 * h) return;
+    uint64_t k = t / (2 * h);
+    uint32_t r = (uint32_t)(t % (2 * h)), side = r / h, i = r % h;
+    const g1a* Ak = A + k * R;
+    if (ml) {
+        const g2a* vk = v + k * R;
+        ml_out[t] = side == 0 ? miller_loop(Ak[h + i], vk[i]) : miller_loop(Ak[i], vk[h + i]);
+        return;
+    }
+    fr sc = bvec[k * R + (side == 0 ? i : h + i)];
+    g1j res;
+    if (fr_is_zero(sc)) {
+        jac_set_inf(res);
+    } else {
+        uint32_t kw[8];
+        fr_canon_words(kw, sc);
+        res = g1_mul(Ak[side == 0 ? h + i : i], kw);
+    }
+    sp_out[t] = res;
+}
+
+// Both folds of round j in one launch: blocks [0, nb_g2) fold v, the remaining blocks fold A and b.
+__global__ void __launch_bounds__(64) k_fold(g1a* A, g2a* v, fr* bvec, const fr* x_mont, const fr* xinv_mont,
+                                             uint32_t K, uint32_t R, uint32_t h, uint32_t nb_g2) {
+    const bool g2 = blockIdx.x < nb_g2;
+    uint64_t t = (uint64_t)(g2 ? blockIdx.x : blockIdx.x - nb_g2) * blockDim.x + threadIdx.x;
+    if (t >= (uint64_t)K * h) return;
+    uint64_t k = t / h;
+    uint32_t i = (uint32_t)(t % h);
+    uint64_t lo = k * R + i, hi = k * R + h + i;
+    uint32_t kw[8];
+    if (g2) {
+        fr_canon_words(kw, xinv_mont[k]);
+        v[lo] = g2_affine(g2_madd(g2_mul(v[hi], kw), v[lo]));
+    } else {
+        fr_canon_words(kw, x_mont[k]);
+        A[lo] = g1_affine(g1_madd(g1_mul(A[hi], kw), A[lo]));
+        bvec[lo] = fr_add(bvec[lo], fr_mul(bvec[hi], xinv_mont[k]));
+    }
+}
+
 // after the reductions: GT = final exponentiation of the Miller product, G1 part to affine;
 // written to round j's record of block k: L_j.T | L_j.1 | R_j.T | R_j.1
 __global__ void __launch_bounds__(64) k_round_out(const fq12* ml, const g1j* sp, uint32_t K, int j, uint8_t* blocks,
@@ -209,4 +257,20 @@ void step1_w_terms(const void* g2pow, const void* q_canon, uint32_t K, uint32_t 
                                                               (g2j*)out));
 }
 
+}  // namespace fpk
+
+namespace fpk {
+void step1_round_terms(const void* A, const void* v, const void* bvec, uint32_t K, uint32_t R, uint32_t h,
+                       void* ml_out, void* sp_out, cudaStream_t s) {
+    uint64_t n = (uint64_t)K * 2 * h;
+    uint32_t nb = grid_for(n, 64);
+    FP_KERNEL("k_round_terms", s, k_round_terms<<<2 * nb, 64, 0, s>>>((const g1a*)A, (const g2a*)v, (const fr*)bvec,
+                                                                      K, R, h, nb, (fq12*)ml_out, (g1j*)sp_out));
+}
+void step1_fold(void* A, void* v, void* bvec, const void* x_mont, const void* xinv_mont, uint32_t K, uint32_t R,
+                uint32_t h, cudaStream_t s) {
+    uint32_t nb = grid_for((uint64_t)K * h, 64);
+    FP_KERNEL("k_fold", s, k_fold<<<2 * nb, 64, 0, s>>>((g1a*)A, (g2a*)v, (fr*)bvec, (const fr*)x_mont,
+                                                        (const fr*)xinv_mont, K, R, h, nb));
+}
 }  // namespace fpk

@@ -5,6 +5,7 @@
 
 #include <cstdio>
 #include <cstring>
+#include <mutex>
 #include <string>
 #include <utility>
 #include <vector>
@@ -108,6 +109,24 @@ void* reduce_pairs(void* a, void* b, uint64_t n, uint64_t target, Red red, cudaS
 }
 
 size_t bopen_len(uint32_t log_r) { return (size_t)log_r * ROUND_BYTES + G1_SER + 2 * G2_SER; }
+
+// One auxiliary non-blocking stream per device, created on first use; Step 2 of OpenAll runs on it
+// concurrently with Step 1, ordered by a fork/join pair of events created per call.
+cudaStream_t g_aux[64];
+std::mutex g_aux_mu;
+cudaStream_t aux_stream() {
+    int dev = 0;
+    check(cudaGetDevice(&dev), "cudaGetDevice");
+    std::lock_guard<std::mutex> lk(g_aux_mu);
+    cudaStream_t& a = g_aux[dev & 63];
+    if (!a) check(cudaStreamCreateWithFlags(&a, cudaStreamNonBlocking), "cudaStreamCreate");
+    return a;
+}
+cudaEvent_t new_event() {
+    cudaEvent_t e = nullptr;
+    check(cudaEventCreateWithFlags(&e, cudaEventDisableTiming), "cudaEventCreate");
+    return e;
+}
 
 }  // namespace
 
@@ -292,7 +311,46 @@ fp_status vc_prove_all(const fp_pp* pp, const fp_commit* cm, uint32_t b, void* s
             pf->rows_ser = dalloc(R * G1_SER, s);
             check(cudaMemcpyAsync(pf->rows_ser, cm->rows_ser, R * G1_SER, cudaMemcpyDeviceToDevice, s), "D2D");
             pf->blocks = dalloc(K * blen, s);
-            // ---------------- Step 1: FC.BOpen on every block (Protocol 1, Step 1)
+            // Step 2 depends only on the commitment: it runs on a second stream, concurrently with Step 1
+            pf->row_tree = dalloc((size_t)R * (2 * M - 1) * DIGEST, s);
+            pf->top_tree = dalloc((2 * (size_t)R - 1) * DIGEST, s);
+            pf->rj = dalloc(R * FR_BYTES, s);
+            pf->g = dalloc((2 * (size_t)R - 1) * M * FR_BYTES, s);
+            pf->D = dalloc((2 * (size_t)R - 1) * G1A_BYTES, s);
+            pf->D_ser = dalloc((2 * (size_t)R - 1) * G1_SER, s);
+            pf->pst_ser = dalloc(((size_t)M - 1) * G1_SER, s);
+            const uint64_t half = M / 2;
+            void* pt = T((size_t)lc * half * G1J_BYTES);
+            void* pt2 = T((half / 2 + 1) * G1J_BYTES);
+            cudaStream_t s2 = aux_stream();
+            cudaEvent_t ev_fork = new_event(), ev_join = new_event();
+            check(cudaEventRecord(ev_fork, s), "event");
+            check(cudaStreamWaitEvent(s2, ev_fork, 0), "wait");
+            // ---------------- Step 2: Merkle tree, randomise, fold tree, HyperEval (stream s2)
+            step2_leaves(cm->m_canon, R, M, pf->row_tree, s2);
+            for (int l = 1; l <= lc; l++) tree_level(pf->row_tree, R, M, l, s2);
+            step2_row_leaves(pf->row_tree, cm->rows_ser, R, M, pf->top_tree, s2);
+            for (int l = 1; l <= lr; l++) tree_level(pf->top_tree, 1, R, l, s2);
+            step2_rj(pf->top_tree, R, pf->rj, s2);
+            step2_randomize(cm->m_mont, pf->rj, R, M, pf->g, s2);
+            step2_d0(cm->rows, pf->rj, R, pf->D, s2);
+            for (int h = 1; h <= lr; h++) {
+                step2_fold_g(pf->g, R, M, h, s2);
+                step2_fold_d(pf->D, R, h, s2);
+            }
+            g1a_serialize(pf->D, pf->D_ser, G1_SER, 2 * (uint64_t)R - 1, s2);
+            step2_pst_terms(pf->g, pp->lam, R, M, lc, pt, s2);
+            size_t pst_off = 0;
+            for (int t = 0; t < lc; t++) {
+                void* lvl = (uint8_t*)pt + (size_t)t * half * G1J_BYTES;
+                uint64_t nseg = half >> t;
+                void* res = reduce_pairs(lvl, pt2, half, nseg, g1_pair_reduce, s2);
+                g1j_to_affine(res, nullptr, (uint8_t*)pf->pst_ser + pst_off * G1_SER, G1_SER, nseg, s2);
+                pst_off += nseg;
+            }
+            check(cudaEventRecord(ev_join, s2), "event");
+
+            // ---------------- Step 1: FC.BOpen on every block (Protocol 1, Step 1), stream s
             const uint64_t KR = (uint64_t)K * R;
             void* A = T(KR * G1A_BYTES);
             void* v = T(KR * G2A_BYTES);
@@ -311,14 +369,12 @@ fp_status vc_prove_all(const fp_pp* pp, const fp_commit* cm, uint32_t b, void* s
             step1_block_r(hstmt, K, R, b, bvec, s);
             for (int j = 1; j <= lr; j++) {
                 const uint32_t h = R >> j;
-                step1_miller(A, v, K, R, h, ml, s);
+                step1_round_terms(A, v, bvec, K, R, h, ml, sp, s);
                 void* mlr = reduce_pairs(ml, ml2, (uint64_t)K * 2 * h, (uint64_t)K * 2, fq12_pair_reduce, s);
-                step1_sparse_terms(A, bvec, K, R, h, sp, s);
                 void* spr = reduce_pairs(sp, sp2, (uint64_t)K * 2 * h, (uint64_t)K * 2, g1_pair_reduce, s);
                 step1_round_out(mlr, spr, K, j, pf->blocks, blen, s);
                 step1_challenge(pf->blocks, blen, K, j, xprev, x_mont, xinv_mont, xinv_all, lr, s);
-                step1_fold_g1(A, bvec, x_mont, xinv_mont, K, R, h, s);
-                step1_fold_g2(v, xinv_mont, K, R, h, s);
+                step1_fold(A, v, bvec, x_mont, xinv_mont, K, R, h, s);
             }
             void* pcoef = T((size_t)K * (2 * R - 1) * FR_BYTES);
             void* q = T((size_t)K * 2 * R * FR_BYTES);
@@ -329,39 +385,9 @@ fp_status vc_prove_all(const fp_pp* pp, const fp_commit* cm, uint32_t b, void* s
             void* wr = reduce_pairs(wt, wt2, (uint64_t)K * 2 * R, K, g2_pair_reduce, s);
             g2j_to_affine(wr, nullptr, (uint8_t*)pf->blocks + (size_t)lr * ROUND_BYTES + G1_SER + G2_SER, blen, K, s);
             check_launch("step 1 kernels");
-
-            // ---------------- Step 2: Merkle tree, randomise, fold tree, HyperEval
-            pf->row_tree = dalloc((size_t)R * (2 * M - 1) * DIGEST, s);
-            pf->top_tree = dalloc((2 * (size_t)R - 1) * DIGEST, s);
-            pf->rj = dalloc(R * FR_BYTES, s);
-            pf->g = dalloc((2 * (size_t)R - 1) * M * FR_BYTES, s);
-            pf->D = dalloc((2 * (size_t)R - 1) * G1A_BYTES, s);
-            pf->D_ser = dalloc((2 * (size_t)R - 1) * G1_SER, s);
-            pf->pst_ser = dalloc(((size_t)M - 1) * G1_SER, s);
-            step2_leaves(cm->m_canon, R, M, pf->row_tree, s);
-            for (int l = 1; l <= lc; l++) tree_level(pf->row_tree, R, M, l, s);
-            step2_row_leaves(pf->row_tree, cm->rows_ser, R, M, pf->top_tree, s);
-            for (int l = 1; l <= lr; l++) tree_level(pf->top_tree, 1, R, l, s);
-            step2_rj(pf->top_tree, R, pf->rj, s);
-            step2_randomize(cm->m_mont, pf->rj, R, M, pf->g, s);
-            step2_d0(cm->rows, pf->rj, R, pf->D, s);
-            for (int h = 1; h <= lr; h++) {
-                step2_fold_g(pf->g, R, M, h, s);
-                step2_fold_d(pf->D, R, h, s);
-            }
-            g1a_serialize(pf->D, pf->D_ser, G1_SER, 2 * (uint64_t)R - 1, s);
-            const uint64_t half = M / 2;
-            void* pt = T((size_t)lc * half * G1J_BYTES);
-            void* pt2 = T((half / 2 + 1) * G1J_BYTES);
-            step2_pst_terms(pf->g, pp->lam, R, M, lc, pt, s);
-            size_t pst_off = 0;
-            for (int t = 0; t < lc; t++) {
-                void* lvl = (uint8_t*)pt + (size_t)t * half * G1J_BYTES;
-                uint64_t nseg = half >> t;
-                void* res = reduce_pairs(lvl, pt2, half, nseg, g1_pair_reduce, s);
-                g1j_to_affine(res, nullptr, (uint8_t*)pf->pst_ser + pst_off * G1_SER, G1_SER, nseg, s);
-                pst_off += nseg;
-            }
+            check(cudaStreamWaitEvent(s, ev_join, 0), "join");
+            cudaEventDestroy(ev_fork);
+            cudaEventDestroy(ev_join);
             check_launch("step 2 kernels");
             for (void* p : tmp) cudaFreeAsync(p, s);
             tmp.clear();
