@@ -59,7 +59,7 @@ def kernel_units(name: str, log_n: int, b: int) -> int:
         return sum(K * 2 * (R >> j) for j in range(1, lr + 1))
     if name == "k_round_out":
         return 2 * K * lr
-    if name == "k_fold_g2" or name == "k_fold_g1":
+    if name in ("k_fold_g2", "k_fold_g1", "k_fold"):
         return sum(K * (R >> j) for j in range(1, lr + 1))
     if name == "k_w_terms":
         return K * (2 * R - 2)

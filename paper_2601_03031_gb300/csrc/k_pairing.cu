@@ -1,4 +1,5 @@
 // Batched Miller loops and final exponentiations.
+#include "group12.cuh"
 #include "k_common.cuh"
 
 namespace fpk {
@@ -32,8 +33,48 @@ __global__ void __launch_bounds__(64) k_final_exp(const fq12* in, uint32_t n, si
     if (ser) fq12_to_be(ser + i * ser_stride, e);
 }
 
+// Final exponentiations with one group of 8 lanes per element (group12.cuh).  Element t is written
+// serialised at ser + (t / per) * stride_a + (t % per) * stride_b (and to out[t] if out != null).
+// Groups past n repeat element 0 without storing, so every lane of a warp runs the same code.
+__global__ void __launch_bounds__(64) k_final_exp_g(const fq12* in, uint32_t n, fq12* out, uint8_t* ser,
+                                                    uint32_t per, size_t stride_a, size_t stride_b) {
+    __shared__ fq2 xb[8][8], yb[8][8];
+    const int grp = threadIdx.x >> 3, lane = threadIdx.x & 7;
+    const uint64_t t = (uint64_t)blockIdx.x * 8 + grp;
+    const bool valid = t < n;
+    const G12 g{lane, xb[grp]};
+    const fq2 e = g_final_exp(g, yb[grp], g_load(in[valid ? t : 0], lane));
+    if (!valid || lane >= 6) return;
+    if (out) g_store(out[t], lane, e);
+    if (ser) {
+        uint8_t* o = ser + (t / per) * stride_a + (t % per) * stride_b + 96 * g_tower_pos(lane);
+        fq_to_be(o, e.c0);
+        fq_to_be(o + 48, e.c1);
+    }
+}
+
+void final_exp_group(const void* in, uint32_t n, void* out, void* ser, uint32_t per, size_t stride_a,
+                     size_t stride_b, cudaStream_t s) {
+    if (n) FP_KERNEL("k_final_exp_g", s, k_final_exp_g<<<(n + 7) / 8, 64, 0, s>>>((const fq12*)in, n, (fq12*)out,
+                                                                                (uint8_t*)ser, per, stride_a,
+                                                                                stride_b));
+}
+
+// FC.Commit's Miller loops on 8-lane groups: pair j = (C_j, v_j)
+__global__ void __launch_bounds__(64) k_commit_miller_g(const g1a* rows, const g2a* g2pow, uint32_t R, fq12* out) {
+    __shared__ GMill sm[8];
+    const int grp = threadIdx.x >> 3, lane = threadIdx.x & 7;
+    const uint64_t j0 = (uint64_t)blockIdx.x * 8 + grp;
+    const bool valid = j0 < R;
+    const uint64_t j = valid ? j0 : 0;
+    const fq2 f = g_miller(sm[grp], lane, rows[j], g2pow[2 * j]);
+    if (valid) g_store(out[j], lane, f);
+}
+
 void commit_miller(const void* rows, const void* g2pow, uint32_t R, void* out, cudaStream_t s) {
-    FP_KERNEL("k_commit_miller", s, k_commit_miller<<<grid_for(R, 64), 64, 0, s>>>((const g1a*)rows, (const g2a*)g2pow, R, (fq12*)out));
+    FP_KERNEL("k_commit_miller_g", s, k_commit_miller_g<<<(R + 7) / 8, 64, 0, s>>>((const g1a*)rows,
+                                                                                  (const g2a*)g2pow, R,
+                                                                                  (fq12*)out));
 }
 void step1_miller(const void* A, const void* v, uint32_t K, uint32_t R, uint32_t h, void* out, cudaStream_t s) {
     uint64_t n = (uint64_t)K * 2 * h;

@@ -1,6 +1,7 @@
 // Step 1 of OpenAll: FC.BOpen (Sec. 3, Eq. b and Eq. folding) for every block S_k at once, with
 // b = sum_{a in S_k} r_a u_a held densely per block, and the faster-verification proof of v_l.
 // Per-block arrays are laid out block-major: X[k * R + i].
+#include "group12.cuh"
 #include "k_common.cuh"
 
 namespace fpk {
@@ -89,6 +90,43 @@ __global__ void __launch_bounds__(64) k_round_terms(const g1a* A, const g2a* v, 
     sp_out[t] = res;
 }
 
+// Round j's two independent batches in one launch, Miller loops on 8-lane groups: blocks
+// [0, nb_ml) hold 8 pairs each (one group per pair, group12.cuh), the remaining blocks the sparse G1
+// terms (one thread each).  Pair t = (k, side, i) as in k_step1_miller.
+__global__ void __launch_bounds__(64) k_round_terms_g(const g1a* A, const g2a* v, const fr* bvec, uint32_t K,
+                                                      uint32_t R, uint32_t h, uint32_t nb_ml, fq12* ml_out,
+                                                      g1j* sp_out) {
+    __shared__ GMill sm[8];
+    const uint64_t n = (uint64_t)K * 2 * h;
+    if (blockIdx.x < nb_ml) {
+        const int grp = threadIdx.x >> 3, lane = threadIdx.x & 7;
+        const uint64_t t0 = (uint64_t)blockIdx.x * 8 + grp;
+        const bool valid = t0 < n;
+        const uint64_t t = valid ? t0 : 0;
+        const uint64_t k = t / (2 * h);
+        const uint32_t r = (uint32_t)(t % (2 * h)), side = r / h, i = r % h;
+        const g1a* Ak = A + k * R;
+        const g2a* vk = v + k * R;
+        const fq2 f = side == 0 ? g_miller(sm[grp], lane, Ak[h + i], vk[i]) : g_miller(sm[grp], lane, Ak[i], vk[h + i]);
+        if (valid) g_store(ml_out[t], lane, f);
+        return;
+    }
+    uint64_t t = (uint64_t)(blockIdx.x - nb_ml) * blockDim.x + threadIdx.x;
+    if (t >= n) return;
+    uint64_t k = t / (2 * h);
+    uint32_t r = (uint32_t)(t % (2 * h)), side = r / h, i = r % h;
+    fr sc = bvec[k * R + (side == 0 ? i : h + i)];
+    g1j res;
+    if (fr_is_zero(sc)) {
+        jac_set_inf(res);
+    } else {
+        uint32_t kw[8];
+        fr_canon_words(kw, sc);
+        res = g1_mul(A[k * R + (side == 0 ? h + i : i)], kw);
+    }
+    sp_out[t] = res;
+}
+
 // Both folds of round j in one launch: blocks [0, nb_g2) fold v, the remaining blocks fold A and b.
 __global__ void __launch_bounds__(64) k_fold(g1a* A, g2a* v, fr* bvec, const fr* x_mont, const fr* xinv_mont,
                                              uint32_t K, uint32_t R, uint32_t h, uint32_t nb_g2) {
@@ -107,6 +145,15 @@ __global__ void __launch_bounds__(64) k_fold(g1a* A, g2a* v, fr* bvec, const fr*
         A[lo] = g1_affine(g1_madd(g1_mul(A[hi], kw), A[lo]));
         bvec[lo] = fr_add(bvec[lo], fr_mul(bvec[hi], xinv_mont[k]));
     }
+}
+
+// the G1 parts of round j's record (the GT parts are written by k_final_exp_g)
+__global__ void __launch_bounds__(64) k_round_g1_out(const g1j* sp, uint32_t K, int j, uint8_t* blocks,
+                                                     size_t bopen_len) {
+    uint64_t t = gtid();
+    if (t >= (uint64_t)K * 2) return;
+    uint8_t* rec = blocks + (t >> 1) * bopen_len + (size_t)(j - 1) * ROUND_BYTES + (t & 1) * (GT_SER + G1_SER);
+    g1a_to_be(rec + GT_SER, g1_affine(sp[t]));
 }
 
 // after the reductions: GT = final exponentiation of the Miller product, G1 part to affine;
@@ -230,6 +277,15 @@ void step1_sparse_terms(const void* A, const void* bvec, uint32_t K, uint32_t R,
 }
 void step1_round_out(const void* ml, const void* sp, uint32_t K, int j, void* blocks, size_t bopen_len,
                      cudaStream_t s) {
+    // GT parts: one 8-lane group per final exponentiation; G1 parts: one thread each
+    final_exp_group(ml, 2 * K, nullptr, (uint8_t*)blocks + (size_t)(j - 1) * ROUND_BYTES, 2, bopen_len,
+                    GT_SER + G1_SER, s);
+    FP_KERNEL("k_round_g1_out", s, k_round_g1_out<<<grid_for((uint64_t)K * 2, 64), 64, 0, s>>>((const g1j*)sp, K, j,
+                                                                                          (uint8_t*)blocks,
+                                                                                          bopen_len));
+}
+void step1_round_out_serial(const void* ml, const void* sp, uint32_t K, int j, void* blocks, size_t bopen_len,
+                            cudaStream_t s) {
     FP_KERNEL("k_round_out", s, k_round_out<<<grid_for((uint64_t)K * 2, 64), 64, 0, s>>>((const fq12*)ml, (const g1j*)sp, K, j,
                                                             (uint8_t*)blocks, bopen_len));
 }
@@ -263,9 +319,10 @@ namespace fpk {
 void step1_round_terms(const void* A, const void* v, const void* bvec, uint32_t K, uint32_t R, uint32_t h,
                        void* ml_out, void* sp_out, cudaStream_t s) {
     uint64_t n = (uint64_t)K * 2 * h;
-    uint32_t nb = grid_for(n, 64);
-    FP_KERNEL("k_round_terms", s, k_round_terms<<<2 * nb, 64, 0, s>>>((const g1a*)A, (const g2a*)v, (const fr*)bvec,
-                                                                      K, R, h, nb, (fq12*)ml_out, (g1j*)sp_out));
+    uint32_t nb_ml = (uint32_t)((n + 7) / 8), nb_sp = grid_for(n, 64);
+    FP_KERNEL("k_round_terms_g", s,
+              k_round_terms_g<<<nb_ml + nb_sp, 64, 0, s>>>((const g1a*)A, (const g2a*)v, (const fr*)bvec, K, R, h,
+                                                           nb_ml, (fq12*)ml_out, (g1j*)sp_out));
 }
 void step1_fold(void* A, void* v, void* bvec, const void* x_mont, const void* xinv_mont, uint32_t K, uint32_t R,
                 uint32_t h, cudaStream_t s) {

@@ -51,6 +51,8 @@ void load_vector(const void* m_limbs, uint64_t n, void* m_canon, void* m_mont, u
 void commit_terms(const void* m_canon, const void* lam, uint64_t n, uint32_t M, void* out_g1j, cudaStream_t s);
 // out[j] = ML(rows[j], g2pow[2 j])
 void commit_miller(const void* rows_g1a, const void* g2pow, uint32_t R, void* out_fq12, cudaStream_t s);
+void final_exp_group(const void* in_fq12, uint32_t n, void* out_fq12, void* ser, uint32_t per, size_t stride_a,
+                     size_t stride_b, cudaStream_t s);
 void final_exp_batch(const void* in_fq12, uint32_t n, size_t in_stride_elems, void* out_fq12, void* ser_out,
                      size_t ser_stride, cudaStream_t s);
 

@@ -264,7 +264,7 @@ fp_status vc_commit(const fp_pp* pp, const uint64_t* m, int on_device, void* str
             ml2 = dalloc((R / 2 + 1) * FQ12_BYTES, s);
             commit_miller(cm->rows, pp->g2pow, R, ml, s);
             void* prod = reduce_pairs(ml, ml2, R, 1, fq12_pair_reduce, s);
-            final_exp_batch(prod, 1, 1, cm->C, cm->C_ser, GT_SER, s);
+            final_exp_group(prod, 1, cm->C, cm->C_ser, 1, GT_SER, 0, s);
             check_launch("vc_commit kernels");
             uint32_t herr = 0;
             check(cudaMemcpyAsync(&herr, err, sizeof herr, cudaMemcpyDeviceToHost, s), "D2H err");
