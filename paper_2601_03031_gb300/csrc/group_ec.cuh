@@ -1,0 +1,211 @@
+// Scalar multiplication on a group of 8 lanes, for the latency-bound folds of Step 1.
+//
+// Points are homogeneous projective (X : Y : Z) with the identity (0 : 1 : 0), and every addition
+// and doubling uses the complete formulas of Renes, Costello and Batina (EUROCRYPT 2016) for a = 0
+// (addition: Algorithm 7, doubling: Algorithm 9, b3 = 3b).  They have no exceptional cases, so the
+// identity, P + P and P + (-P) need no branch, and each formula is two phases of at most six
+// independent field products: lane t (t < 6) computes product t of the phase, the lanes exchange
+// the products through shared memory, and every lane forms the linear combinations itself.
+// The scalar is split by the endomorphisms (GLV on G1, GLS on G2, see curve.cuh) and consumed by a
+// joint double-and-add over a table of subset sums that always adds (the empty subset is the
+// identity), so all groups of a warp run the same instruction stream.
+#pragma once
+#include "group12.cuh"
+
+template <typename F> struct GPt { F X, Y, Z; };
+template <typename F> struct GEc {
+    F sc[8];          // products of the current phase
+    GPt<F> tab[16];   // subset sums of the split bases
+};
+
+FPG_DEV fq f_b3(const fq& a) {            // 3 b = 12 on G1
+    const fq t = fq_add(fq_dbl(a), a);
+    return fq_dbl(fq_dbl(t));
+}
+FPG_DEV fq2 f_b3(const fq2& a) {          // 3 b' = 12 (1 + u) on the twist
+    const fq2 x = fq2_mul_xi(a);
+    const fq2 t = fq2_add(fq2_dbl(x), x);
+    return fq2_dbl(fq2_dbl(t));
+}
+
+template <typename F>
+FPG_DEV void gec_phase(GEc<F>& sm, int lane, const F& a, const F& b) {
+    const F p = f_mul(a, b);
+    gsync();
+    if (lane < 6) sm.sc[lane] = p;
+    gsync();
+}
+
+template <typename F>
+FPG_DEV GPt<F> gec_identity() {
+    GPt<F> r;
+    f_set_zero(r.X); f_set_one(r.Y); f_set_zero(r.Z);
+    return r;
+}
+
+// P + Q, complete (RCB16 Algorithm 7, a = 0)
+template <typename F>
+FPG_NOINL GPt<F> gec_add(GEc<F>& sm, int lane, const GPt<F>& P, const GPt<F>& Q) {
+    F a, b;
+    switch (lane) {
+        case 0: a = P.X; b = Q.X; break;
+        case 1: a = P.Y; b = Q.Y; break;
+        case 2: a = P.Z; b = Q.Z; break;
+        case 3: a = f_add(P.X, P.Y); b = f_add(Q.X, Q.Y); break;
+        case 4: a = f_add(P.Y, P.Z); b = f_add(Q.Y, Q.Z); break;
+        default: a = f_add(P.X, P.Z); b = f_add(Q.X, Q.Z); break;
+    }
+    gec_phase(sm, lane, a, b);
+    const F t0 = sm.sc[0], t1 = sm.sc[1], t2 = sm.sc[2];
+    const F t3 = f_sub(sm.sc[3], f_add(t0, t1));
+    const F t4 = f_sub(sm.sc[4], f_add(t1, t2));
+    const F y3 = f_b3(f_sub(sm.sc[5], f_add(t0, t2)));
+    const F x3 = f_add(f_dbl(t0), t0);
+    const F bt2 = f_b3(t2);
+    const F z3 = f_add(t1, bt2);
+    const F u1 = f_sub(t1, bt2);
+    switch (lane) {
+        case 0: a = t4; b = y3; break;
+        case 1: a = t3; b = u1; break;
+        case 2: a = y3; b = x3; break;
+        case 3: a = u1; b = z3; break;
+        case 4: a = x3; b = t3; break;
+        default: a = z3; b = t4; break;
+    }
+    gec_phase(sm, lane, a, b);
+    GPt<F> r;
+    r.X = f_sub(sm.sc[1], sm.sc[0]);
+    r.Y = f_add(sm.sc[3], sm.sc[2]);
+    r.Z = f_add(sm.sc[5], sm.sc[4]);
+    return r;
+}
+
+// 2P, complete (RCB16 Algorithm 9, a = 0)
+template <typename F>
+FPG_NOINL GPt<F> gec_dbl(GEc<F>& sm, int lane, const GPt<F>& P) {
+    F a, b;
+    switch (lane) {
+        case 0: a = P.Y; b = P.Y; break;
+        case 1: a = P.Y; b = P.Z; break;
+        case 2: a = P.Z; b = P.Z; break;
+        default: a = P.X; b = P.Y; break;
+    }
+    gec_phase(sm, lane, a, b);
+    const F t0 = sm.sc[0], t1 = sm.sc[1], xy = sm.sc[3];
+    const F z8 = f_dbl(f_dbl(f_dbl(t0)));
+    const F bt2 = f_b3(sm.sc[2]);
+    const F y3a = f_add(t0, bt2);
+    const F t0p = f_sub(t0, f_add(f_dbl(bt2), bt2));
+    switch (lane) {
+        case 0: a = bt2; b = z8; break;
+        case 1: a = t1; b = z8; break;
+        case 2: a = t0p; b = y3a; break;
+        default: a = t0p; b = xy; break;
+    }
+    gec_phase(sm, lane, a, b);
+    GPt<F> r;
+    r.X = f_dbl(sm.sc[3]);
+    r.Y = f_add(sm.sc[0], sm.sc[2]);
+    r.Z = sm.sc[1];
+    return r;
+}
+
+// table of subset sums tab[s] = sum_{i in s} B_i for s < 2^nb (tab[0] = identity); every lane holds
+// the same B_i and the same results, lane 0 stores them
+template <typename F>
+FPG_DEV void gec_table(GEc<F>& sm, int lane, const GPt<F>* B, int nb) {
+    gsync();
+    if (lane == 0) {
+        sm.tab[0] = gec_identity<F>();
+        for (int i = 0; i < nb; i++) sm.tab[1 << i] = B[i];
+    }
+    gsync();
+    for (int s = 3; s < (1 << nb); s++) {
+        if (!(s & (s - 1))) continue;                          // single bases are already in place
+        const int top = 31 - __clz(s);
+        const GPt<F> r = gec_add(sm, lane, sm.tab[s & ~(1 << top)], sm.tab[1 << top]);
+        gsync();
+        if (lane == 0) sm.tab[s] = r;
+        gsync();
+    }
+}
+
+template <typename F>
+FPG_DEV GPt<F> gec_from_affine(const F& x, const F& y) {
+    GPt<F> r;
+    r.X = x; r.Y = y; f_set_one(r.Z);
+    return r;
+}
+
+// affine (x, y) = (X/Z, Y/Z); (0, 0) for the identity
+template <typename F>
+FPG_DEV void gec_to_affine(F& x, F& y, const GPt<F>& P) {
+    if (f_is_zero(P.Z)) { f_set_zero(x); f_set_zero(y); return; }
+    const F zi = f_inv(P.Z);
+    x = f_mul(P.X, zi);
+    y = f_mul(P.Y, zi);
+}
+
+// k P on G1 for a canonical k < r (GLV: k = k0 + k1 |x|^2, bases P and -phi(P)), projective
+FPG_NOINL GPt<fq> gec_g1_mul_proj(GEc<fq>& sm, int lane, const g1a& P, const uint32_t* k) {
+    uint32_t k1[5], k0[4];
+    div_by_const<4, 5>(k1, k0, k, GLV_D, GLV_BARRETT);
+    fq om;
+    fq_from_const(om, GLV_OMEGA);
+    const bool inf = g1a_is_inf(P);
+    GPt<fq> B[2];
+    B[0] = inf ? gec_identity<fq>() : gec_from_affine(P.x, P.y);
+    B[1] = inf ? gec_identity<fq>() : gec_from_affine(fq_mul(P.x, om), fq_neg(P.y));
+    gec_table(sm, lane, B, 2);
+    GPt<fq> acc = gec_identity<fq>();
+    for (int i = 127; i >= 0; i--) {
+        acc = gec_dbl(sm, lane, acc);
+        const int s = bit_of(k0, i) | (bit_of(k1, i) << 1);
+        acc = gec_add(sm, lane, acc, sm.tab[s]);
+    }
+    return acc;
+}
+FPG_DEV g1a gec_g1_mul(GEc<fq>& sm, int lane, const g1a& P, const uint32_t* k) {
+    g1a r;
+    gec_to_affine(r.x, r.y, gec_g1_mul_proj(sm, lane, P, k));
+    return r;
+}
+
+// k Q on G2 for a canonical k < r (GLS: base-|x| digits, bases (-1)^i psi^i(Q)), projective
+FPG_NOINL GPt<fq2> gec_g2_mul_proj(GEc<fq2>& sm, int lane, const g2a& Q, const uint32_t* k) {
+    uint32_t q1[7], q2[7], q3[7], d[4][2];
+    div_by_const<2, 7>(q1, d[0], k, GLS_D, GLS_BARRETT);
+    uint32_t t8[8];
+    for (int i = 0; i < 8; i++) t8[i] = i < 7 ? q1[i] : 0;
+    div_by_const<2, 7>(q2, d[1], t8, GLS_D, GLS_BARRETT);
+    for (int i = 0; i < 8; i++) t8[i] = i < 7 ? q2[i] : 0;
+    div_by_const<2, 7>(q3, d[2], t8, GLS_D, GLS_BARRETT);
+    d[3][0] = q3[0];
+    d[3][1] = q3[1];
+    const bool inf = g2a_is_inf(Q);
+    g2a b = Q;
+    GPt<fq2> B[4];
+    for (int i = 0; i < 4; i++) {
+        if (i) b = g2_psi(b);
+        const fq2 y = (i & 1) ? fq2_neg(b.y) : b.y;
+        B[i] = inf ? gec_identity<fq2>() : gec_from_affine(b.x, y);
+    }
+    gec_table(sm, lane, B, 4);
+    GPt<fq2> acc = gec_identity<fq2>();
+    for (int i = 63; i >= 0; i--) {
+        acc = gec_dbl(sm, lane, acc);
+        const int s = bit_of(d[0], i) | (bit_of(d[1], i) << 1) | (bit_of(d[2], i) << 2) | (bit_of(d[3], i) << 3);
+        acc = gec_add(sm, lane, acc, sm.tab[s]);
+    }
+    return acc;
+}
+FPG_DEV g2a gec_g2_mul(GEc<fq2>& sm, int lane, const g2a& Q, const uint32_t* k) {
+    g2a r;
+    gec_to_affine(r.x, r.y, gec_g2_mul_proj(sm, lane, Q, k));
+    return r;
+}
+
+template <typename F>
+FPG_DEV GPt<F> gec_from_affine_or_inf(const F& x, const F& y) {
+    return (f_is_zero(x) && f_is_zero(y)) ? gec_identity<F>() : gec_from_affine(x, y);
+}

@@ -1,7 +1,7 @@
 // Step 1 of OpenAll: FC.BOpen (Sec. 3, Eq. b and Eq. folding) for every block S_k at once, with
 // b = sum_{a in S_k} r_a u_a held densely per block, and the faster-verification proof of v_l.
 // Per-block arrays are laid out block-major: X[k * R + i].
-#include "group12.cuh"
+#include "group_ec.cuh"
 #include "k_common.cuh"
 
 namespace fpk {
@@ -156,6 +156,44 @@ __global__ void __launch_bounds__(64) k_round_g1_out(const g1j* sp, uint32_t K, 
     g1a_to_be(rec + GT_SER, g1_affine(sp[t]));
 }
 
+// Both folds of round j on 8-lane groups (group_ec.cuh): blocks [0, nb2) fold 8 points of v each,
+// the remaining blocks 8 points of A (and the matching entries of b).  Point t = (k, i < h).
+union FoldSmem {
+    GEc<fq2> g2[8];
+    GEc<fq> g1[8];
+};
+__global__ void __launch_bounds__(64) k_fold_grp(g1a* A, g2a* v, fr* bvec, const fr* x_mont, const fr* xinv_mont,
+                                                 uint32_t K, uint32_t R, uint32_t h, uint32_t nb2) {
+    __shared__ FoldSmem sm;
+    const int grp = threadIdx.x >> 3, lane = threadIdx.x & 7;
+    const bool g2 = blockIdx.x < nb2;
+    const uint64_t t0 = (uint64_t)(g2 ? blockIdx.x : blockIdx.x - nb2) * 8 + grp;
+    const bool valid = t0 < (uint64_t)K * h;
+    const uint64_t t = valid ? t0 : 0;
+    const uint64_t k = t / h;
+    const uint32_t i = (uint32_t)(t % h);
+    const uint64_t lo = k * R + i, hi = k * R + h + i;
+    uint32_t kw[8];
+    if (g2) {
+        fr_canon_words(kw, xinv_mont[k]);
+        const GPt<fq2> r = gec_add(sm.g2[grp], lane, gec_g2_mul_proj(sm.g2[grp], lane, v[hi], kw),
+                                   gec_from_affine_or_inf(v[lo].x, v[lo].y));
+        g2a o;
+        gec_to_affine(o.x, o.y, r);
+        if (valid && lane == 0) v[lo] = o;
+    } else {
+        fr_canon_words(kw, x_mont[k]);
+        const GPt<fq> r = gec_add(sm.g1[grp], lane, gec_g1_mul_proj(sm.g1[grp], lane, A[hi], kw),
+                                  gec_from_affine_or_inf(A[lo].x, A[lo].y));
+        g1a o;
+        gec_to_affine(o.x, o.y, r);
+        if (valid && lane == 0) {
+            A[lo] = o;
+            bvec[lo] = fr_add(bvec[lo], fr_mul(bvec[hi], xinv_mont[k]));
+        }
+    }
+}
+
 // after the reductions: GT = final exponentiation of the Miller product, G1 part to affine;
 // written to round j's record of block k: L_j.T | L_j.1 | R_j.T | R_j.1
 __global__ void __launch_bounds__(64) k_round_out(const fq12* ml, const g1j* sp, uint32_t K, int j, uint8_t* blocks,
@@ -284,6 +322,15 @@ void step1_round_out(const void* ml, const void* sp, uint32_t K, int j, void* bl
                                                                                           (uint8_t*)blocks,
                                                                                           bopen_len));
 }
+void step1_gt_out(const void* ml, uint32_t K, int j, void* blocks, size_t bopen_len, cudaStream_t s) {
+    final_exp_group(ml, 2 * K, nullptr, (uint8_t*)blocks + (size_t)(j - 1) * ROUND_BYTES, 2, bopen_len,
+                    GT_SER + G1_SER, s);
+}
+void step1_g1_out(const void* sp, uint32_t K, int j, void* blocks, size_t bopen_len, cudaStream_t s) {
+    FP_KERNEL("k_round_g1_out", s, k_round_g1_out<<<grid_for((uint64_t)K * 2, 64), 64, 0, s>>>((const g1j*)sp, K, j,
+                                                                                          (uint8_t*)blocks,
+                                                                                          bopen_len));
+}
 void step1_round_out_serial(const void* ml, const void* sp, uint32_t K, int j, void* blocks, size_t bopen_len,
                             cudaStream_t s) {
     FP_KERNEL("k_round_out", s, k_round_out<<<grid_for((uint64_t)K * 2, 64), 64, 0, s>>>((const fq12*)ml, (const g1j*)sp, K, j,
@@ -324,8 +371,25 @@ void step1_round_terms(const void* A, const void* v, const void* bvec, uint32_t 
               k_round_terms_g<<<nb_ml + nb_sp, 64, 0, s>>>((const g1a*)A, (const g2a*)v, (const fr*)bvec, K, R, h,
                                                            nb_ml, (fq12*)ml_out, (g1j*)sp_out));
 }
+void step1_miller_g(const void* A, const void* v, uint32_t K, uint32_t R, uint32_t h, void* ml_out, cudaStream_t s) {
+    uint64_t n = (uint64_t)K * 2 * h;
+    if (n >= 16384) {          // enough pairs to fill the GPU one per thread: less work than 8-lane groups
+        step1_miller(A, v, K, R, h, ml_out, s);
+        return;
+    }
+    uint32_t nb_ml = (uint32_t)((n + 7) / 8);
+    FP_KERNEL("k_round_terms_g", s,
+              k_round_terms_g<<<nb_ml, 64, 0, s>>>((const g1a*)A, (const g2a*)v, nullptr, K, R, h, nb_ml,
+                                                   (fq12*)ml_out, nullptr));
+}
 void step1_fold(void* A, void* v, void* bvec, const void* x_mont, const void* xinv_mont, uint32_t K, uint32_t R,
                 uint32_t h, cudaStream_t s) {
+    if ((uint64_t)K * h <= 4096) {      // few points: one 8-lane group per point for latency
+        uint32_t nb = (uint32_t)(((uint64_t)K * h + 7) / 8);
+        FP_KERNEL("k_fold_grp", s, k_fold_grp<<<2 * nb, 64, 0, s>>>((g1a*)A, (g2a*)v, (fr*)bvec, (const fr*)x_mont,
+                                                                    (const fr*)xinv_mont, K, R, h, nb));
+        return;
+    }
     uint32_t nb = grid_for((uint64_t)K * h, 64);
     FP_KERNEL("k_fold", s, k_fold<<<2 * nb, 64, 0, s>>>((g1a*)A, (g2a*)v, (fr*)bvec, (const fr*)x_mont,
                                                         (const fr*)xinv_mont, K, R, h, nb));

@@ -67,6 +67,9 @@ void step1_sparse_terms(const void* A, const void* bvec, uint32_t K, uint32_t R,
                         cudaStream_t s);
 void step1_round_terms(const void* A, const void* v, const void* bvec, uint32_t K, uint32_t R, uint32_t h,
                        void* ml_out_fq12, void* sp_out_g1j, cudaStream_t s);
+void step1_miller_g(const void* A, const void* v, uint32_t K, uint32_t R, uint32_t h, void* ml_out, cudaStream_t s);
+void step1_g1_out(const void* sp_g1j, uint32_t K, int j, void* blocks, size_t bopen_len, cudaStream_t s);
+void step1_gt_out(const void* ml_fq12, uint32_t K, int j, void* blocks, size_t bopen_len, cudaStream_t s);
 void step1_fold(void* A, void* v, void* bvec, const void* x_mont, const void* xinv_mont, uint32_t K, uint32_t R,
                 uint32_t h, cudaStream_t s);
 void step1_round_out(const void* ml_fq12, const void* sp_g1j, uint32_t K, int j, void* blocks, size_t bopen_len,

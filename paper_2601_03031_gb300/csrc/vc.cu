@@ -110,16 +110,25 @@ void* reduce_pairs(void* a, void* b, uint64_t n, uint64_t target, Red red, cudaS
 
 size_t bopen_len(uint32_t log_r) { return (size_t)log_r * ROUND_BYTES + G1_SER + 2 * G2_SER; }
 
-// One auxiliary non-blocking stream per device, created on first use; Step 2 of OpenAll runs on it
-// concurrently with Step 1, ordered by a fork/join pair of events created per call.
-cudaStream_t g_aux[64];
+// Internal non-blocking streams per device, created on first use: OpenAll's latency-bound Step 1
+// runs on two high-priority streams (the round chain, and the sparse G1 terms that overlap it),
+// the throughput-bound Step 2 on a low-priority stream; all are forked from and joined back to the
+// caller's stream with events created per call.
+struct Streams { cudaStream_t hi = nullptr, sp = nullptr, lo = nullptr; };
+Streams g_streams[64];
 std::mutex g_aux_mu;
-cudaStream_t aux_stream() {
+Streams& streams() {
     int dev = 0;
     check(cudaGetDevice(&dev), "cudaGetDevice");
     std::lock_guard<std::mutex> lk(g_aux_mu);
-    cudaStream_t& a = g_aux[dev & 63];
-    if (!a) check(cudaStreamCreateWithFlags(&a, cudaStreamNonBlocking), "cudaStreamCreate");
+    Streams& a = g_streams[dev & 63];
+    if (!a.hi) {
+        int lo = 0, hi = 0;
+        check(cudaDeviceGetStreamPriorityRange(&lo, &hi), "priority range");
+        check(cudaStreamCreateWithPriority(&a.hi, cudaStreamNonBlocking, hi), "cudaStreamCreate");
+        check(cudaStreamCreateWithPriority(&a.sp, cudaStreamNonBlocking, hi), "cudaStreamCreate");
+        check(cudaStreamCreateWithPriority(&a.lo, cudaStreamNonBlocking, lo), "cudaStreamCreate");
+    }
     return a;
 }
 cudaEvent_t new_event() {
@@ -322,10 +331,30 @@ fp_status vc_prove_all(const fp_pp* pp, const fp_commit* cm, uint32_t b, void* s
             const uint64_t half = M / 2;
             void* pt = T((size_t)lc * half * G1J_BYTES);
             void* pt2 = T((half / 2 + 1) * G1J_BYTES);
-            cudaStream_t s2 = aux_stream();
-            cudaEvent_t ev_fork = new_event(), ev_join = new_event();
+            // every buffer is allocated (stream-ordered on s) before the fork to the internal streams
+            const uint64_t KR = (uint64_t)K * R;
+            void* A = T(KR * G1A_BYTES);
+            void* v = T(KR * G2A_BYTES);
+            void* bvec = T(KR * FR_BYTES);
+            void* hstmt = T(K * DIGEST);
+            void* xprev = T(K * 32);
+            void* x_mont = T(K * FR_BYTES);
+            void* xinv_mont = T(K * FR_BYTES);
+            void* xinv_all = T((size_t)K * lr * FR_BYTES);
+            void* ml = T(KR * FQ12_BYTES);
+            void* ml2 = T((KR / 2 + 1) * FQ12_BYTES);
+            void* sp = T(KR * G1J_BYTES);
+            void* sp2 = T((KR / 2 + 1) * G1J_BYTES);
+            void* pcoef = T((size_t)K * (2 * R - 1) * FR_BYTES);
+            void* q = T((size_t)K * 2 * R * FR_BYTES);
+            void* wt = T((size_t)K * 2 * R * G2J_BYTES);
+            void* wt2 = T(((size_t)K * R + 1) * G2J_BYTES);
+            Streams& st = streams();
+            cudaStream_t s2 = st.lo, s1 = st.hi, s3 = st.sp;
+            cudaEvent_t ev_fork = new_event(), ev_join = new_event(), ev_join1 = new_event();
             check(cudaEventRecord(ev_fork, s), "event");
             check(cudaStreamWaitEvent(s2, ev_fork, 0), "wait");
+            check(cudaStreamWaitEvent(s1, ev_fork, 0), "wait");
             // ---------------- Step 2: Merkle tree, randomise, fold tree, HyperEval (stream s2)
             step2_leaves(cm->m_canon, R, M, pf->row_tree, s2);
             for (int l = 1; l <= lc; l++) tree_level(pf->row_tree, R, M, l, s2);
@@ -350,40 +379,37 @@ fp_status vc_prove_all(const fp_pp* pp, const fp_commit* cm, uint32_t b, void* s
             }
             check(cudaEventRecord(ev_join, s2), "event");
 
-            // ---------------- Step 1: FC.BOpen on every block (Protocol 1, Step 1), stream s
-            const uint64_t KR = (uint64_t)K * R;
-            void* A = T(KR * G1A_BYTES);
-            void* v = T(KR * G2A_BYTES);
-            void* bvec = T(KR * FR_BYTES);
-            void* hstmt = T(K * DIGEST);
-            void* xprev = T(K * 32);
-            void* x_mont = T(K * FR_BYTES);
-            void* xinv_mont = T(K * FR_BYTES);
-            void* xinv_all = T((size_t)K * lr * FR_BYTES);
-            void* ml = T(KR * FQ12_BYTES);
-            void* ml2 = T((KR / 2 + 1) * FQ12_BYTES);
-            void* sp = T(KR * G1J_BYTES);
-            void* sp2 = T((KR / 2 + 1) * G1J_BYTES);
-            step1_init(cm->rows, pp->g2pow, K, R, A, v, bvec, s);
-            step1_stmt_hash(cm->C_ser, cm->rows_ser, K, R, b, hstmt, s);
-            step1_block_r(hstmt, K, R, b, bvec, s);
+            // ---------------- Step 1: FC.BOpen on every block (Protocol 1, Step 1)
+            // round chain on s1; each round's sparse G1 terms on s3, overlapping its Miller loops and
+            // final exponentiations, joined before the challenge
+            cudaEvent_t ev_folded = new_event(), ev_sparse = new_event();
+            step1_init(cm->rows, pp->g2pow, K, R, A, v, bvec, s1);
+            step1_stmt_hash(cm->C_ser, cm->rows_ser, K, R, b, hstmt, s1);
+            step1_block_r(hstmt, K, R, b, bvec, s1);
             for (int j = 1; j <= lr; j++) {
                 const uint32_t h = R >> j;
-                step1_round_terms(A, v, bvec, K, R, h, ml, sp, s);
-                void* mlr = reduce_pairs(ml, ml2, (uint64_t)K * 2 * h, (uint64_t)K * 2, fq12_pair_reduce, s);
-                void* spr = reduce_pairs(sp, sp2, (uint64_t)K * 2 * h, (uint64_t)K * 2, g1_pair_reduce, s);
-                step1_round_out(mlr, spr, K, j, pf->blocks, blen, s);
-                step1_challenge(pf->blocks, blen, K, j, xprev, x_mont, xinv_mont, xinv_all, lr, s);
-                step1_fold(A, v, bvec, x_mont, xinv_mont, K, R, h, s);
+                check(cudaEventRecord(ev_folded, s1), "event");
+                check(cudaStreamWaitEvent(s3, ev_folded, 0), "wait");
+                step1_sparse_terms(A, bvec, K, R, h, sp, s3);
+                void* spr = reduce_pairs(sp, sp2, (uint64_t)K * 2 * h, (uint64_t)K * 2, g1_pair_reduce, s3);
+                step1_g1_out(spr, K, j, pf->blocks, blen, s3);
+                check(cudaEventRecord(ev_sparse, s3), "event");
+                step1_miller_g(A, v, K, R, h, ml, s1);
+                void* mlr = reduce_pairs(ml, ml2, (uint64_t)K * 2 * h, (uint64_t)K * 2, fq12_pair_reduce, s1);
+                step1_gt_out(mlr, K, j, pf->blocks, blen, s1);
+                check(cudaStreamWaitEvent(s1, ev_sparse, 0), "wait");
+                step1_challenge(pf->blocks, blen, K, j, xprev, x_mont, xinv_mont, xinv_all, lr, s1);
+                step1_fold(A, v, bvec, x_mont, xinv_mont, K, R, h, s1);
             }
-            void* pcoef = T((size_t)K * (2 * R - 1) * FR_BYTES);
-            void* q = T((size_t)K * 2 * R * FR_BYTES);
-            step1_kzg(A, v, xprev, xinv_all, K, R, lr, pf->blocks, blen, pcoef, q, s);
-            void* wt = T((size_t)K * 2 * R * G2J_BYTES);
-            void* wt2 = T(((size_t)K * R + 1) * G2J_BYTES);
-            step1_w_terms(pp->g2pow, q, K, R, wt, s);
-            void* wr = reduce_pairs(wt, wt2, (uint64_t)K * 2 * R, K, g2_pair_reduce, s);
-            g2j_to_affine(wr, nullptr, (uint8_t*)pf->blocks + (size_t)lr * ROUND_BYTES + G1_SER + G2_SER, blen, K, s);
+            step1_kzg(A, v, xprev, xinv_all, K, R, lr, pf->blocks, blen, pcoef, q, s1);
+            step1_w_terms(pp->g2pow, q, K, R, wt, s1);
+            void* wr = reduce_pairs(wt, wt2, (uint64_t)K * 2 * R, K, g2_pair_reduce, s1);
+            g2j_to_affine(wr, nullptr, (uint8_t*)pf->blocks + (size_t)lr * ROUND_BYTES + G1_SER + G2_SER, blen, K, s1);
+            check(cudaEventRecord(ev_join1, s1), "event");
+            check(cudaStreamWaitEvent(s, ev_join1, 0), "join");
+            cudaEventDestroy(ev_folded);
+            cudaEventDestroy(ev_sparse);
+            cudaEventDestroy(ev_join1);
             check_launch("step 1 kernels");
             check(cudaStreamWaitEvent(s, ev_join, 0), "join");
             cudaEventDestroy(ev_fork);
