@@ -36,6 +36,7 @@ extern "C" {
 typedef struct fp_pp fp_pp;           /* public parameters, device resident (VC.Setup, Eq. vcpp) */
 typedef struct fp_commit fp_commit;   /* C in GT, aux = row commitments, and the prover's copy of m */
 typedef struct fp_proofs fp_proofs;   /* the shared pieces of all N proofs, device resident */
+typedef struct fp_g1_bases fp_g1_bases; /* G1 bases of a multi-scalar multiplication, device resident */
 
 typedef enum {
     FP_OK = 0,
@@ -116,6 +117,46 @@ fp_status vc_proofs_step2_parts(const fp_proofs* pf, uint8_t* root, uint8_t* rj,
  * (the status word is cleared by each call): calls that overlap on the GPU race -- serialise them.
  * A value >= r gives FP_ERANGE.  Synchronises `stream`.  Allocates no device memory. */
 fp_status vc_commit_rows_noalloc(const fp_pp* pp, const uint64_t* m_dev, uint8_t* rows_dev, void* stream);
+
+/* ---- G1 multi-scalar multiplication ----
+ * The operation behind PST.Commit (C_j = sum_a m[j M + a] Lambda[a], Sec. 4.1, Eq. genCi) and the
+ * PST proofs of HyperEval (Sec. 2), exposed on its own: a batched Pippenger MSM (signed-digit
+ * windows over the GLV halves of each scalar, bucket counting sort, bucket accumulation, bucket
+ * and window reduction), exact like everything here.
+ *
+ * fp_g1_bases_from_scalars: bases P_i = s_i g1 for i < n (s: n x 4 little-endian uint64, any
+ *   256-bit values; host or device pointer per on_device).  Synchronises.
+ * fp_g1_bases_load: bases from n serialised affine points (n x 96 B, canonical big-endian, all-zero
+ *   bytes = identity), host or device pointer per on_device.  A coordinate >= p or a point off
+ *   y^2 = x^3 + 4 gives FP_EINVAL (no handle).  Synchronises.
+ * Both limit n < 2^30.  The handle holds 2n affine points (P_i and the GLV partner -phi(P_i)),
+ * 192 B per base. */
+fp_status fp_g1_bases_from_scalars(const uint64_t* s, uint64_t n, int on_device, void* stream, fp_g1_bases** out);
+fp_status fp_g1_bases_load(const uint8_t* pts, uint64_t n, int on_device, void* stream, fp_g1_bases** out);
+uint64_t fp_g1_bases_count(const fp_g1_bases* P);
+void fp_g1_bases_free(fp_g1_bases* P);
+
+/* out[j] = sum_{i<n} k[j n + i] P[(j n + i) mod npts] for j < nbatch, npts = the handle's base count
+ * (so nbatch sums over the same n bases when npts = n, or over consecutive slices).
+ *   k:   n * nbatch scalars, 4 little-endian uint64 each, any 256-bit values (the integer
+ *        combination is computed; for bases in G1 it equals the one with k mod r).
+ *   out: nbatch x 96 B serialised affine points (identity = zeros).
+ *   on_device = 1: k and out are device pointers and the call only enqueues (no synchronisation;
+ *        scratch is allocated and freed stream-ordered on `stream`).  on_device = 0: both are host
+ *        pointers, copied in and out, and the call synchronises.
+ *   window: bits per signed digit in [4, 16], or 0 for the library's choice (fp_msm_window).
+ * n = 0 gives identities.  Sizes whose bucket lists exceed 2^32 entries give FP_EINVAL. */
+fp_status fp_msm_g1(const fp_g1_bases* P, const uint64_t* k, uint64_t n, uint32_t nbatch, int on_device, int window,
+                    void* stream, uint8_t* out);
+/* The window fp_msm_g1 uses for (n, nbatch) when given 0: the last fp_msm_autotune result for
+ * that shape, else a cost model (per-phase throughput and per-thread latency of the field
+ * products). */
+int fp_msm_window(uint64_t n, uint32_t nbatch);
+/* Times fp_msm_g1 on `stream` for windows around the model's choice with the given device
+ * scalars (n * nbatch), keeps the fastest for (n, nbatch), and returns it (and its time in ms if
+ * best_ms != NULL).  Synchronises. */
+fp_status fp_msm_autotune(const fp_g1_bases* P, const uint64_t* k_dev, uint64_t n, uint32_t nbatch, void* stream,
+                          int* window, double* best_ms);
 
 void fp_pp_free(fp_pp* pp);
 void fp_commit_free(fp_commit* cm);

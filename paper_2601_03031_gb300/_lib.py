@@ -17,7 +17,9 @@ FP_STATUS = {0: "FP_OK", 1: "FP_EINVAL", 2: "FP_ENOMEM", 3: "FP_EDEVICE", 4: "FP
 EXPORTED = ["vc_setup", "vc_pp_export", "vc_pp_dims", "vc_commit", "vc_commit_get", "vc_prove_all",
             "vc_proof_len", "vc_proof_get", "vc_proofs_export", "vc_proofs_state", "vc_proofs_step2_parts",
             "fp_pp_free", "fp_commit_free", "fp_proofs_free", "fp_strerror", "fp_last_error", "fp_launch_count",
-            "fp_profile_enable", "fp_profile_report", "fp_imad_probe", "vc_commit_rows_noalloc"]
+            "fp_profile_enable", "fp_profile_report", "fp_imad_probe", "vc_commit_rows_noalloc",
+            "fp_g1_bases_from_scalars", "fp_g1_bases_load", "fp_g1_bases_count", "fp_g1_bases_free", "fp_msm_g1",
+            "fp_msm_window", "fp_msm_autotune"]
 
 
 class FlexProofsError(RuntimeError):
@@ -67,6 +69,16 @@ def load(path: str = LIB_PATH):
     L.fp_profile_report.restype = sz
     L.fp_imad_probe.argtypes = [ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double)]
     L.vc_commit_rows_noalloc.argtypes = [vp, vp, vp, vp]
+    L.fp_g1_bases_from_scalars.argtypes = [vp, u64, ctypes.c_int, vp, pp]
+    L.fp_g1_bases_load.argtypes = [vp, u64, ctypes.c_int, vp, pp]
+    L.fp_g1_bases_count.argtypes = [vp]
+    L.fp_g1_bases_count.restype = u64
+    L.fp_g1_bases_free.argtypes = [vp]
+    L.fp_g1_bases_free.restype = None
+    L.fp_msm_g1.argtypes = [vp, vp, u64, u32, ctypes.c_int, ctypes.c_int, vp, vp]
+    L.fp_msm_window.argtypes = [u64, u32]
+    L.fp_msm_window.restype = ctypes.c_int
+    L.fp_msm_autotune.argtypes = [vp, vp, u64, u32, vp, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_double)]
     _lib = L
     return L
 
@@ -247,3 +259,73 @@ def vc_commit_rows_noalloc(pp: PP, m_dev, rows_dev, stream=None) -> None:
     (see include/flexproofs.h).  m_dev / rows_dev: device tensors (N x 4 int64, R*96 uint8)."""
     _check("vc_commit_rows_noalloc",
            load().vc_commit_rows_noalloc(pp.h, m_dev.data_ptr(), rows_dev.data_ptr(), _stream_ptr(stream)))
+
+
+def _ptr_of(x):
+    """(pointer, on_device, keep-alive) of a torch CUDA tensor, numpy array or bytes."""
+    if hasattr(x, "data_ptr"):
+        assert x.is_cuda and x.is_contiguous()
+        return x.data_ptr(), 1, x
+    if isinstance(x, (bytes, bytearray)):
+        arr = np.frombuffer(bytes(x), dtype=np.uint8)
+        return arr.ctypes.data, 0, arr
+    arr = np.ascontiguousarray(x)
+    return arr.ctypes.data, 0, arr
+
+
+class G1Bases:
+    """Device-resident bases of fp_msm_g1: from scalars (P_i = s_i g1; n x 4 uint64 limbs) or from
+    serialised affine points (n x 96 bytes)."""
+
+    def __init__(self, scalars=None, points=None, stream=None):
+        L = load()
+        h = ctypes.c_void_p()
+        if scalars is not None:
+            ptr, dev, keep = _ptr_of(scalars if hasattr(scalars, "data_ptr") else
+                                     np.ascontiguousarray(scalars, dtype=np.uint64))
+            n = (scalars.numel() if hasattr(scalars, "numel") else keep.size) // 4
+            _check("fp_g1_bases_from_scalars", L.fp_g1_bases_from_scalars(ptr, n, dev, _stream_ptr(stream),
+                                                                          ctypes.byref(h)))
+        else:
+            ptr, dev, keep = _ptr_of(points)
+            n = (points.numel() if hasattr(points, "numel") else keep.size) // 96
+            _check("fp_g1_bases_load", L.fp_g1_bases_load(ptr, n, dev, _stream_ptr(stream), ctypes.byref(h)))
+        self.h = h
+        self.n = int(L.fp_g1_bases_count(h))
+
+    def __del__(self):
+        if getattr(self, "h", None) and _lib is not None:
+            _lib.fp_g1_bases_free(self.h)
+            self.h = None
+
+
+def msm_g1(bases: G1Bases, k, nbatch: int = 1, window: int = 0, stream=None, out=None):
+    """sum_i k[j n + i] P[(j n + i) mod npts] for j < nbatch.  Host input (numpy n*nbatch x 4
+    uint64): returns nbatch x 96 bytes.  Device input (torch int64 tensor): enqueues into the
+    device uint8 tensor `out` (nbatch * 96) and returns it."""
+    L = load()
+    if hasattr(k, "data_ptr"):
+        n = k.numel() // 4 // nbatch
+        assert out is not None and out.is_cuda and out.numel() >= 96 * nbatch
+        _check("fp_msm_g1", L.fp_msm_g1(bases.h, k.data_ptr(), n, nbatch, 1, window, _stream_ptr(stream),
+                                        out.data_ptr()))
+        return out
+    arr = np.ascontiguousarray(k, dtype=np.uint64)
+    n = arr.size // 4 // nbatch
+    buf = ctypes.create_string_buffer(96 * nbatch)
+    _check("fp_msm_g1", L.fp_msm_g1(bases.h, arr.ctypes.data if arr.size else None, n, nbatch, 0, window,
+                                    _stream_ptr(stream), buf))
+    return buf.raw
+
+
+def msm_window(n: int, nbatch: int = 1) -> int:
+    return int(load().fp_msm_window(n, nbatch))
+
+
+def msm_autotune(bases: G1Bases, k_dev, nbatch: int = 1, stream=None):
+    """Measured best window for this shape (kept for later calls with window 0) and its time in ms."""
+    c, ms = ctypes.c_int(), ctypes.c_double()
+    n = k_dev.numel() // 4 // nbatch
+    _check("fp_msm_autotune", load().fp_msm_autotune(bases.h, k_dev.data_ptr(), n, nbatch, _stream_ptr(stream),
+                                                     ctypes.byref(c), ctypes.byref(ms)))
+    return c.value, ms.value

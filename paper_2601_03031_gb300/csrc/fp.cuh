@@ -215,7 +215,16 @@ FPG_DEV void fq_from_const(fq& a, const uint32_t* c) {
 #pragma unroll
     for (int j = 0; j < 12; j++) a.v[j] = c[j];
 }
-FPG_DEV fq fq_mul(const fq& a, const fq& b) { fq r; mp::mont_mul<12>(r.v, a.v, b.v, FQ_P, FQ_PINV); return r; }
+// The Montgomery products are out of line: one copy of the ~700-instruction body per translation
+// unit instead of one per call site.  Inlined, a group operation's dozen products overflow the
+// instruction cache and every product runs about three times slower; the call costs a few moves
+// (arguments and result travel in registers).
+static __device__ __noinline__ fq fq_mul_ool(fq a, fq b) {
+    fq r;
+    mp::mont_mul<12>(r.v, a.v, b.v, FQ_P, FQ_PINV);
+    return r;
+}
+FPG_DEV fq fq_mul(const fq& a, const fq& b) { return fq_mul_ool(a, b); }
 FPG_DEV fq fq_sqr(const fq& a) { return fq_mul(a, a); }
 FPG_DEV fq fq_add(const fq& a, const fq& b) { fq r; mp::mod_add<12>(r.v, a.v, b.v, FQ_P); return r; }
 FPG_DEV fq fq_sub(const fq& a, const fq& b) { fq r; mp::mod_sub<12>(r.v, a.v, b.v, FQ_P); return r; }
@@ -248,7 +257,12 @@ FPG_DEV void fr_one(fr& a) {
 #pragma unroll
     for (int j = 0; j < 8; j++) a.v[j] = FR_ONE[j];
 }
-FPG_DEV fr fr_mul(const fr& a, const fr& b) { fr r; mp::mont_mul<8>(r.v, a.v, b.v, FR_P, FR_PINV); return r; }
+static __device__ __noinline__ fr fr_mul_ool(fr a, fr b) {
+    fr r;
+    mp::mont_mul<8>(r.v, a.v, b.v, FR_P, FR_PINV);
+    return r;
+}
+FPG_DEV fr fr_mul(const fr& a, const fr& b) { return fr_mul_ool(a, b); }
 FPG_DEV fr fr_add(const fr& a, const fr& b) { fr r; mp::mod_add<8>(r.v, a.v, b.v, FR_P); return r; }
 FPG_DEV fr fr_sub(const fr& a, const fr& b) { fr r; mp::mod_sub<8>(r.v, a.v, b.v, FR_P); return r; }
 FPG_DEV bool fr_is_zero(const fr& a) { return mp::is_zero<8>(a.v); }

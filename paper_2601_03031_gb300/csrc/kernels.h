@@ -5,6 +5,8 @@
 #include <cstddef>
 #include <cstdint>
 
+#include "msm.h"
+
 namespace fpk {
 
 // Every kernel launch goes through FP_KERNEL: it counts the launch and, while profiling is
@@ -107,5 +109,17 @@ void assemble(const ProofLayout& L, const void* rows_ser, const void* blocks, co
               const void* top_tree, const void* D_ser, const void* g, const void* pst_ser, uint64_t i0, uint64_t count,
               void* out, cudaStream_t s);
 size_t proof_len(const ProofLayout& L, uint64_t i);
+
+
+// ---- G1 multi-scalar multiplication (batched Pippenger; shape in msm.h)
+MsmShape msm_shape(uint64_t n, uint32_t nbatch, uint64_t npts, int c);
+size_t msm_scratch_bytes(const MsmShape& sh);
+int msm_window_model(uint64_t n, uint32_t nbatch);
+// bases: 2 npts affine G1 [P_i | -phi(P_i)]; k_canon: n nbatch x 8 u32; out_g1a / ser_out optional
+void msm_g1(const void* bases, const void* k_canon, const MsmShape& sh, void* scratch, void* out_g1a, void* ser_out,
+            cudaStream_t s);
+// bases table from n serialised points (err |= 1 on a bad point); or the second half from the first
+void msm_bases_load(const void* be96, uint64_t n, void* tab, uint32_t* err, cudaStream_t s);
+void msm_bases_endo(void* tab, uint64_t n, cudaStream_t s);
 
 }  // namespace fpk

@@ -1,0 +1,419 @@
+// Batched Pippenger multi-scalar multiplication on G1:
+//     out[j] = sum_{i < n} k[j n + i] P[(j n + i) mod npts],   j < nbatch,
+// for affine bases P (Montgomery form) and 256-bit scalars k (any value; the result is the integer
+// combination, which for bases in G1 equals the combination with k mod r).
+//
+//   0. GLV split: k = k0 + k1 |x|^2 with k0 < |x|^2 < 2^128 and k1 < 2^129; since
+//      phi(x, y) = (omega x, y) acts as [-x^2] on G1, k P = k0 P + k1 (-phi(P)).  The bases table
+//      holds P_i and -phi(P_i), so every term becomes two half-length terms.
+//   1. signed c-bit digits of each half, d in (-2^(c-1), 2^(c-1)] with a carry into the next
+//      window; W = ceil(130 / c) windows absorb the last carry.  Key (batch, window, |d| - 1) selects
+//      one of B = 2^(c-1) buckets; a negative digit negates the base.
+//   2. counting sort of the (base, window) entries by key: histogram with atomics, exclusive scan,
+//      scatter of base index | sign bit;
+//   3. one thread per bucket sums its bases with XYZZ mixed additions;
+//   4. bucket reduction sum_b (b + 1) B_b: the B buckets of a window are cut into S segments of L;
+//      a thread per segment forms its running sums plus (start) x (segment sum), and the segment
+//      results are added pairwise;
+//   5. per batch, Horner over the windows (c doublings each) on an 8-lane group with the complete
+//      projective formulas, then one inversion to affine.
+// XYZZ coordinates: x = X / ZZ, y = Y / ZZZ (ZZ^3 = ZZZ^2), identity ZZ = 0; formulas madd-2008-s,
+// add-2008-s and dbl-2008-s-1 of the Explicit-Formulas Database (curve coefficient a = 0).
+#include <algorithm>
+#include <cmath>
+
+#include "group_ec.cuh"
+#include "k_common.cuh"
+
+namespace fpk {
+
+struct xyzz { fq X, Y, ZZ, ZZZ; };
+
+FPG_DEV void xyzz_inf(xyzz& p) { fq_zero(p.X); fq_zero(p.Y); fq_zero(p.ZZ); fq_zero(p.ZZZ); }
+FPG_DEV bool xyzz_is_inf(const xyzz& p) { return fq_is_zero(p.ZZ); }
+
+FPG_NOINL xyzz xyzz_dbl(const xyzz& p) {
+    if (xyzz_is_inf(p)) return p;
+    const fq U = fq_dbl(p.Y), V = fq_sqr(U), W = fq_mul(U, V), S = fq_mul(p.X, V);
+    const fq X2 = fq_sqr(p.X), M = fq_add(fq_dbl(X2), X2);
+    xyzz r;
+    r.X = fq_sub(fq_sqr(M), fq_dbl(S));
+    r.Y = fq_sub(fq_mul(M, fq_sub(S, r.X)), fq_mul(W, p.Y));
+    r.ZZ = fq_mul(V, p.ZZ);
+    r.ZZZ = fq_mul(W, p.ZZZ);
+    return r;
+}
+// 2 (x, y) for an affine point (y != 0 on this curve: no point of order 2)
+FPG_DEV xyzz xyzz_dbl_affine(const fq& x, const fq& y) {
+    const fq U = fq_dbl(y), V = fq_sqr(U), W = fq_mul(U, V), S = fq_mul(x, V);
+    const fq X2 = fq_sqr(x), M = fq_add(fq_dbl(X2), X2);
+    xyzz r;
+    r.X = fq_sub(fq_sqr(M), fq_dbl(S));
+    r.Y = fq_sub(fq_mul(M, fq_sub(S, r.X)), fq_mul(W, y));
+    r.ZZ = V;
+    r.ZZZ = W;
+    return r;
+}
+// p + (x, y), the second point affine and not the identity
+FPG_NOINL xyzz xyzz_madd(const xyzz& p, const fq& x, const fq& y) {
+    xyzz r;
+    if (xyzz_is_inf(p)) { r.X = x; r.Y = y; fq_one(r.ZZ); fq_one(r.ZZZ); return r; }
+    const fq U2 = fq_mul(x, p.ZZ), S2 = fq_mul(y, p.ZZZ);
+    const fq P = fq_sub(U2, p.X), R = fq_sub(S2, p.Y);
+    if (fq_is_zero(P)) {
+        if (fq_is_zero(R)) return xyzz_dbl_affine(x, y);
+        xyzz_inf(r);
+        return r;
+    }
+    const fq PP = fq_sqr(P), PPP = fq_mul(P, PP), Q = fq_mul(p.X, PP);
+    r.X = fq_sub(fq_sub(fq_sqr(R), PPP), fq_dbl(Q));
+    r.Y = fq_sub(fq_mul(R, fq_sub(Q, r.X)), fq_mul(p.Y, PPP));
+    r.ZZ = fq_mul(p.ZZ, PP);
+    r.ZZZ = fq_mul(p.ZZZ, PPP);
+    return r;
+}
+FPG_NOINL xyzz xyzz_add(const xyzz& p, const xyzz& q) {
+    if (xyzz_is_inf(p)) return q;
+    if (xyzz_is_inf(q)) return p;
+    const fq U1 = fq_mul(p.X, q.ZZ), U2 = fq_mul(q.X, p.ZZ);
+    const fq S1 = fq_mul(p.Y, q.ZZZ), S2 = fq_mul(q.Y, p.ZZZ);
+    const fq P = fq_sub(U2, U1), R = fq_sub(S2, S1);
+    xyzz r;
+    if (fq_is_zero(P)) {
+        if (fq_is_zero(R)) return xyzz_dbl(p);
+        xyzz_inf(r);
+        return r;
+    }
+    const fq PP = fq_sqr(P), PPP = fq_mul(P, PP), Q = fq_mul(U1, PP);
+    r.X = fq_sub(fq_sub(fq_sqr(R), PPP), fq_dbl(Q));
+    r.Y = fq_sub(fq_mul(R, fq_sub(Q, r.X)), fq_mul(S1, PPP));
+    r.ZZ = fq_mul(fq_mul(p.ZZ, q.ZZ), PP);
+    r.ZZZ = fq_mul(fq_mul(p.ZZZ, q.ZZZ), PPP);
+    return r;
+}
+// m p for m >= 1 (double-and-add from the top set bit)
+FPG_DEV xyzz xyzz_mul_small(const xyzz& p, uint32_t m) {
+    xyzz acc = p;
+    for (int i = 30 - __clz(m); i >= 0; i--) {
+        acc = xyzz_dbl(acc);
+        if ((m >> i) & 1) acc = xyzz_add(acc, p);
+    }
+    return acc;
+}
+
+// ---------------------------------------------------------------------------- digits
+FPG_DEV uint32_t win_bits(const uint32_t* a, int nw, int lo, int c) {
+    const int word = lo >> 5, bit = lo & 31;
+    const uint64_t two = (uint64_t)(word < nw ? a[word] : 0) | ((uint64_t)(word + 1 < nw ? a[word + 1] : 0) << 32);
+    return (uint32_t)(two >> bit) & ((1u << c) - 1);
+}
+
+// calls emit(half, window, digit) for every non-zero signed digit of the GLV halves of k
+template <typename Emit>
+FPG_DEV void msm_digits(const uint32_t* k, const MsmShape& sh, Emit&& emit) {
+    uint32_t k1[5], k0[4];
+    div_by_const<4, 5>(k1, k0, k, GLV_D, GLV_BARRETT);
+    for (int h = 0; h < 2; h++) {
+        const uint32_t* a = h ? k1 : k0;
+        const int nw = h ? 5 : 4;
+        int32_t carry = 0;
+        for (int w = 0; w < sh.W; w++) {
+            int32_t d = (int32_t)win_bits(a, nw, w * sh.c, sh.c) + carry;
+            carry = d > (int32_t)sh.B;
+            if (carry) d -= 1 << sh.c;
+            if (d) emit(h, w, d);
+        }
+    }
+}
+
+__global__ void k_msm_count(const fr* k, MsmShape sh, uint32_t* counts) {
+    const uint64_t t = gtid();
+    if (t >= sh.n * sh.nbatch) return;
+    const uint64_t base = (t / sh.n) * sh.W;
+    const fr s = k[t];
+    msm_digits(s.v, sh, [&](int, int w, int32_t d) {
+        atomicAdd(&counts[(base + w) * sh.B + (uint32_t)(d < 0 ? -d : d) - 1], 1u);
+    });
+}
+
+__global__ void k_msm_scatter(const fr* k, MsmShape sh, uint32_t* cursor, uint32_t* list) {
+    const uint64_t t = gtid();
+    if (t >= sh.n * sh.nbatch) return;
+    const uint64_t base = (t / sh.n) * sh.W;
+    const uint32_t pidx = (uint32_t)(t % sh.npts);
+    const fr s = k[t];
+    msm_digits(s.v, sh, [&](int h, int w, int32_t d) {
+        const uint32_t pos = atomicAdd(&cursor[(base + w) * sh.B + (uint32_t)(d < 0 ? -d : d) - 1], 1u);
+        list[pos] = (pidx + (h ? (uint32_t)sh.npts : 0u)) | (d < 0 ? 0x80000000u : 0u);
+    });
+}
+
+// ---------------------------------------------------------------------------- scan
+// exclusive scan, one level: each block of 1024 scans its slice and reports its total
+__global__ void __launch_bounds__(1024) k_scan_block(const uint32_t* in, uint32_t* out, uint64_t n, uint32_t* sums) {
+    __shared__ uint32_t s[1024];
+    const uint64_t i = (uint64_t)blockIdx.x * 1024 + threadIdx.x;
+    const uint32_t v = i < n ? in[i] : 0;
+    s[threadIdx.x] = v;
+    __syncthreads();
+    for (int off = 1; off < 1024; off <<= 1) {
+        const uint32_t add = threadIdx.x >= (unsigned)off ? s[threadIdx.x - off] : 0;
+        __syncthreads();
+        s[threadIdx.x] += add;
+        __syncthreads();
+    }
+    if (i < n) out[i] = s[threadIdx.x] - v;
+    if (threadIdx.x == 1023) sums[blockIdx.x] = s[1023];
+}
+__global__ void __launch_bounds__(1024) k_scan_add(uint32_t* out, uint64_t n, const uint32_t* block_prefix) {
+    const uint64_t i = (uint64_t)blockIdx.x * 1024 + threadIdx.x;
+    if (i < n) out[i] += block_prefix[blockIdx.x];
+}
+
+static size_t scan_tmp_words(uint64_t n) {
+    size_t w = 0;
+    while (n > 1) {
+        n = (n + 1023) / 1024;
+        w += 2 * n;
+    }
+    return w + 2;
+}
+// exclusive scan of n values; tmp holds scan_tmp_words(n) words
+static void exclusive_scan(const uint32_t* in, uint32_t* out, uint64_t n, uint32_t* tmp, cudaStream_t s) {
+    const uint64_t nb = (n + 1023) / 1024;
+    FP_KERNEL("k_scan_block", s, k_scan_block<<<(unsigned)nb, 1024, 0, s>>>(in, out, n, tmp));
+    if (nb > 1) {
+        exclusive_scan(tmp, tmp + nb, nb, tmp + 2 * nb, s);
+        FP_KERNEL("k_scan_add", s, k_scan_add<<<(unsigned)nb, 1024, 0, s>>>(out, n, tmp + nb));
+    }
+}
+
+// ---------------------------------------------------------------------------- buckets
+__global__ void __launch_bounds__(128) k_msm_bucket(const g1a* pts, MsmShape sh, const uint32_t* offsets,
+                                                    const uint32_t* counts, const uint32_t* list, xyzz* buckets) {
+    const uint64_t key = gtid();
+    if (key >= sh.nkeys()) return;
+    const uint32_t off = offsets[key], cnt = counts[key];
+    xyzz acc;
+    xyzz_inf(acc);
+    for (uint32_t q = 0; q < cnt; q++) {
+        const uint32_t e = list[off + q];
+        const g1a p = pts[e & 0x7fffffffu];
+        if (g1a_is_inf(p)) continue;
+        acc = xyzz_madd(acc, p.x, (e >> 31) ? fq_neg(p.y) : p.y);
+    }
+    buckets[key] = acc;
+}
+
+// segment s of a window: buckets b in [s L, (s + 1) L) give sum_b (b + 1) B_b
+__global__ void __launch_bounds__(128) k_msm_segment(MsmShape sh, const xyzz* buckets, xyzz* segs) {
+    const uint64_t t = gtid();
+    if (t >= sh.nsegs()) return;
+    const uint64_t win = t / sh.S;
+    const uint32_t s = (uint32_t)(t % sh.S), L = sh.B / sh.S;
+    const xyzz* bk = buckets + win * sh.B + (uint64_t)s * L;
+    xyzz run, acc;
+    xyzz_inf(run);
+    xyzz_inf(acc);
+    for (int b = (int)L - 1; b >= 0; b--) {
+        run = xyzz_add(run, bk[b]);
+        acc = xyzz_add(acc, run);                   // sum_b (b - s L + 1) B_b
+    }
+    if (s && !xyzz_is_inf(run)) acc = xyzz_add(acc, xyzz_mul_small(run, s * L));
+    segs[t] = acc;
+}
+
+__global__ void k_msm_pair(const xyzz* in, xyzz* out, uint64_t n) {
+    const uint64_t i = gtid();
+    if (i < n) out[i] = xyzz_add(in[2 * i], in[2 * i + 1]);
+}
+
+// window sums to homogeneous projective (X ZZZ : Y ZZ : ZZ ZZZ), identity (0 : 1 : 0)
+__global__ void k_msm_to_proj(const xyzz* in, GPt<fq>* out, uint64_t n) {
+    const uint64_t i = gtid();
+    if (i >= n) return;
+    const xyzz p = in[i];
+    GPt<fq> r;
+    if (xyzz_is_inf(p)) {
+        r = gec_identity<fq>();
+    } else {
+        r.X = fq_mul(p.X, p.ZZZ);
+        r.Y = fq_mul(p.Y, p.ZZ);
+        r.Z = fq_mul(p.ZZ, p.ZZZ);
+    }
+    out[i] = r;
+}
+
+// per batch, on 8 lanes: sum_w 2^(c w) S_w by Horner from the top window, then affine
+__global__ void __launch_bounds__(64) k_msm_final(MsmShape sh, const GPt<fq>* win, g1a* out, uint8_t* ser) {
+    __shared__ GEc<fq> sm[8];
+    const int grp = threadIdx.x >> 3, lane = threadIdx.x & 7;
+    const uint64_t j0 = (uint64_t)blockIdx.x * 8 + grp;
+    const bool valid = j0 < sh.nbatch;
+    const uint64_t j = valid ? j0 : 0;                // idle groups repeat batch 0's work
+    GPt<fq> acc = win[j * sh.W + sh.W - 1];
+    for (int w = sh.W - 2; w >= 0; w--) {
+        for (int q = 0; q < sh.c; q++) acc = gec_dbl(sm[grp], lane, acc);
+        acc = gec_add(sm[grp], lane, acc, win[j * sh.W + w]);
+    }
+    g1a a;
+    gec_to_affine(a.x, a.y, acc);
+    if (valid && lane == 0) {
+        if (out) out[j] = a;
+        if (ser) g1a_to_be(ser + j * G1_SER, a);
+    }
+}
+
+// ---------------------------------------------------------------------------- bases
+// first half of the bases table from serialised affine points; err |= 1 for a point that is not
+// canonical or not on y^2 = x^3 + 4 (all-zero bytes = identity)
+__global__ void k_bases_load(const uint8_t* be, uint64_t n, g1a* tab, uint32_t* err) {
+    const uint64_t i = gtid();
+    if (i >= n) return;
+    const uint8_t* p = be + i * G1_SER;
+    fq c[2];
+    bool zero = true;
+    for (int h = 0; h < 2; h++) {
+        for (int w = 0; w < 12; w++) {
+            const uint8_t* q = p + h * 48 + (11 - w) * 4;
+            c[h].v[w] = ((uint32_t)q[0] << 24) | ((uint32_t)q[1] << 16) | ((uint32_t)q[2] << 8) | q[3];
+            zero = zero && c[h].v[w] == 0;
+        }
+    }
+    g1a a;
+    fq_zero(a.x);
+    fq_zero(a.y);
+    if (!zero) {
+        if (!mp::lt<12>(c[0].v, FQ_P) || !mp::lt<12>(c[1].v, FQ_P)) {
+            atomicOr(err, 1u);
+        } else {
+            a.x = fq_to_mont(c[0]);
+            a.y = fq_to_mont(c[1]);
+            fq four;
+            fq_one(four);
+            four = fq_dbl(fq_dbl(four));
+            if (!fq_eq(fq_sqr(a.y), fq_add(fq_mul(fq_sqr(a.x), a.x), four))) atomicOr(err, 1u);
+        }
+    }
+    tab[i] = a;
+}
+
+// second half of the table: -phi(P) = (omega x, -y)
+__global__ void k_bases_endo(g1a* tab, uint64_t n) {
+    const uint64_t i = gtid();
+    if (i >= n) return;
+    fq om;
+    fq_from_const(om, GLV_OMEGA);
+    const g1a p = tab[i];
+    tab[n + i] = g1a_is_inf(p) ? p : g1a{fq_mul(p.x, om), fq_neg(p.y)};
+}
+
+void msm_bases_load(const void* be96, uint64_t n, void* tab, uint32_t* err, cudaStream_t s) {
+    if (!n) return;
+    FP_KERNEL("k_bases_load", s, k_bases_load<<<grid_for(n, 128), 128, 0, s>>>((const uint8_t*)be96, n, (g1a*)tab,
+                                                                              err));
+    FP_KERNEL("k_bases_endo", s, k_bases_endo<<<grid_for(n, 128), 128, 0, s>>>((g1a*)tab, n));
+}
+void msm_bases_endo(void* tab, uint64_t n, cudaStream_t s) {
+    if (n) FP_KERNEL("k_bases_endo", s, k_bases_endo<<<grid_for(n, 128), 128, 0, s>>>((g1a*)tab, n));
+}
+
+// ---------------------------------------------------------------------------- shape and driver
+MsmShape msm_shape(uint64_t n, uint32_t nbatch, uint64_t npts, int c) {
+    MsmShape sh;
+    sh.n = n;
+    sh.nbatch = nbatch;
+    sh.npts = npts;
+    sh.c = c;
+    sh.W = (130 + c - 1) / c;
+    sh.B = 1u << (c - 1);
+    // segments of at least 4 buckets, at most about 2^15 segment threads
+    uint32_t S = sh.B;
+    while (S > 1 && sh.B / S < 4) S >>= 1;
+    while (S > 1 && (uint64_t)nbatch * sh.W * S > (1u << 15)) S >>= 1;
+    sh.S = S;
+    return sh;
+}
+
+size_t msm_scratch_bytes(const MsmShape& sh) {
+    const uint64_t nk = sh.nkeys();
+    auto r = [](size_t b) { return (b + 255) & ~(size_t)255; };
+    size_t b = 3 * r(nk * 4) + r(scan_tmp_words(nk) * 4);
+    b += r(sh.entries_max() * 4);
+    b += r(nk * sizeof(xyzz));
+    b += 2 * r(sh.nsegs() * sizeof(xyzz));
+    b += r((uint64_t)sh.nbatch * sh.W * sizeof(GPt<fq>));
+    return b;
+}
+
+// Window size from a cost model: per phase the larger of the throughput time (about 1.9e10 Fq
+// products/s over the GPU) and the latency of one thread's dependent chain (about 1.3 us per
+// product); mixed addition 10 products, addition 14, group doubling/addition about 2 x 1.5.
+int msm_window_model(uint64_t n, uint32_t nbatch) {
+    const double tp = 1.0 / 1.9e10, lat = 1.3e-6;
+    int best = 8;
+    double bestt = 1e300;
+    for (int c = 4; c <= 16; c++) {
+        const MsmShape sh = msm_shape(n, nbatch, n, c);
+        if (sh.nkeys() > (1ull << 26) || sh.entries_max() > 0xffffffffull) continue;
+        const double entries = 2.0 * (double)n * nbatch * sh.W * (1.0 - 1.0 / (double)(1u << c));
+        const double per_bucket = entries / (double)sh.nkeys();
+        const double t_bucket = std::max(entries * 10 * tp, per_bucket * 10 * lat);
+        const double L = (double)(sh.B / sh.S);
+        const double t_seg = std::max((double)sh.nkeys() * 2 * 14 * tp, (2 * L + 1.5 * (c - 1)) * 14 * lat);
+        const double t_pair = std::log2((double)sh.S) * 14 * lat;
+        const double t_final = (double)sh.W * (sh.c * 2 + 2) * 1.5 * lat;
+        const double t = t_bucket + t_seg + t_pair + t_final;
+        if (t < bestt) {
+            bestt = t;
+            best = c;
+        }
+    }
+    return best;
+}
+
+void msm_g1(const void* bases, const void* k_canon, const MsmShape& sh, void* scratch, void* out_g1a, void* ser_out,
+            cudaStream_t s) {
+    const uint64_t nk = sh.nkeys(), nseg = sh.nsegs(), nwin = (uint64_t)sh.nbatch * sh.W;
+    uint8_t* p = (uint8_t*)scratch;
+    auto take = [&](size_t bytes) {
+        uint8_t* r = p;
+        p += (bytes + 255) & ~(size_t)255;
+        return (void*)r;
+    };
+    uint32_t* counts = (uint32_t*)take(nk * 4);
+    uint32_t* offsets = (uint32_t*)take(nk * 4);
+    uint32_t* cursor = (uint32_t*)take(nk * 4);
+    uint32_t* scan_tmp = (uint32_t*)take(scan_tmp_words(nk) * 4);
+    uint32_t* list = (uint32_t*)take(sh.entries_max() * 4);
+    xyzz* buckets = (xyzz*)take(nk * sizeof(xyzz));
+    xyzz* seg_a = (xyzz*)take(nseg * sizeof(xyzz));
+    xyzz* seg_b = (xyzz*)take(nseg * sizeof(xyzz));
+    GPt<fq>* proj = (GPt<fq>*)take(nwin * sizeof(GPt<fq>));
+    const uint64_t terms = sh.n * sh.nbatch;
+    cudaMemsetAsync(counts, 0, nk * 4, s);
+    if (terms) {
+        FP_KERNEL("k_msm_count", s,
+                  k_msm_count<<<grid_for(terms, 128), 128, 0, s>>>((const fr*)k_canon, sh, counts));
+    }
+    exclusive_scan(counts, offsets, nk, scan_tmp, s);
+    cudaMemcpyAsync(cursor, offsets, nk * 4, cudaMemcpyDeviceToDevice, s);
+    if (terms) {
+        FP_KERNEL("k_msm_scatter", s,
+                  k_msm_scatter<<<grid_for(terms, 128), 128, 0, s>>>((const fr*)k_canon, sh, cursor, list));
+    }
+    FP_KERNEL("k_msm_bucket", s, k_msm_bucket<<<grid_for(nk, 128), 128, 0, s>>>((const g1a*)bases, sh, offsets,
+                                                                               counts, list, buckets));
+    FP_KERNEL("k_msm_segment", s, k_msm_segment<<<grid_for(nseg, 128), 128, 0, s>>>(sh, buckets, seg_a));
+    xyzz* a = seg_a;
+    xyzz* b = seg_b;
+    for (uint64_t m = nseg; m > nwin; m /= 2) {
+        FP_KERNEL("k_msm_pair", s, k_msm_pair<<<grid_for(m / 2, 128), 128, 0, s>>>(a, b, m / 2));
+        std::swap(a, b);
+    }
+    FP_KERNEL("k_msm_to_proj", s, k_msm_to_proj<<<grid_for(nwin, 128), 128, 0, s>>>(a, proj, nwin));
+    FP_KERNEL("k_msm_final", s, k_msm_final<<<grid_for(sh.nbatch, 8), 64, 0, s>>>(sh, proj, (g1a*)out_g1a,
+                                                                                  (uint8_t*)ser_out));
+}
+
+}  // namespace fpk

@@ -3,6 +3,7 @@
 // sizes buffers, enqueues kernels and copies bytes.
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <cstdio>
 #include <cstring>
 #include <mutex>
@@ -18,6 +19,7 @@ using namespace fpk;
 struct fp_pp {
     uint32_t log_n, log_r, log_c, R, M;
     void* lam = nullptr;      // G1 affine, 2M - 1: Lambda_t at offset 2^t - 1
+    void* lam_tab = nullptr;  // G1 affine, 2M: Lambda_{l_c} and its GLV partners (MSM bases)
     void* g1beta = nullptr;   // G1 affine
     void* g2pow = nullptr;    // G2 affine, 2R - 1: g2^{beta^i}
     void* g2tau = nullptr;    // G2 affine, l_c
@@ -32,6 +34,11 @@ struct fp_commit {
     void* C = nullptr;        // fq12
     void* C_ser = nullptr;    // 576
     cudaStream_t stream;
+};
+
+struct fp_g1_bases {
+    uint64_t n;
+    void* tab = nullptr;      // G1 affine, 2n: P_i, then -phi(P_i) (the GLV partner)
 };
 
 struct fp_proofs {
@@ -180,6 +187,10 @@ fp_status vc_setup(uint32_t log_n, uint32_t b, uint64_t seed, void* stream, fp_p
             setup_trapdoor(seed, (int)log_c, trap, s);
             setup_scalars(trap, (int)log_r, (int)log_c, lam_s, pow_s, tau_s, beta_s, s);
             g1_gen_mul(lam_s, 2 * M - 1, pp->lam, s);
+            pp->lam_tab = dalloc(2 * (size_t)M * G1A_BYTES, s);
+            check(cudaMemcpyAsync(pp->lam_tab, (uint8_t*)pp->lam + ((size_t)M - 1) * G1A_BYTES, (size_t)M * G1A_BYTES,
+                                  cudaMemcpyDeviceToDevice, s), "D2D");
+            msm_bases_endo(pp->lam_tab, M, s);
             g1_gen_mul(beta_s, 1, pp->g1beta, s);
             g2_gen_mul(pow_s, 2 * R - 1, pp->g2pow, s);
             g2_gen_mul(tau_s, log_c, pp->g2tau, s);
@@ -261,13 +272,10 @@ fp_status vc_commit(const fp_pp* pp, const uint64_t* m, int on_device, void* str
                 msrc = src;
             }
             load_vector(msrc, N, cm->m_canon, cm->m_mont, err, s);
-            // C_j = sum_a m[jM + a] Lambda_{l_c}[a]: all N terms, then l_c pairwise levels per row
-            t1 = dalloc(N * G1J_BYTES, s);
-            t2 = dalloc(N / 2 * G1J_BYTES, s);
-            void* lam_top = (uint8_t*)pp->lam + ((size_t)M - 1) * G1A_BYTES;
-            commit_terms(cm->m_canon, lam_top, N, M, t1, s);
-            void* rows_j = reduce_pairs(t1, t2, N, R, g1_pair_reduce, s);
-            g1j_to_affine(rows_j, cm->rows, cm->rows_ser, G1_SER, R, s);
+            // C_j = sum_a m[jM + a] Lambda_{l_c}[a]: R MSMs of M terms over the shared bases
+            const MsmShape sh = msm_shape(M, R, M, fp_msm_window(M, R));
+            t1 = dalloc(msm_scratch_bytes(sh), s);
+            msm_g1(pp->lam_tab, cm->m_canon, sh, t1, cm->rows, cm->rows_ser, s);
             // C = prod_j e(C_j, v_j): R Miller loops, pairwise products, one final exponentiation
             ml = dalloc(R * FQ12_BYTES, s);
             ml2 = dalloc((R / 2 + 1) * FQ12_BYTES, s);
@@ -510,10 +518,207 @@ fp_status vc_proofs_step2_parts(const fp_proofs* pf, uint8_t* root, uint8_t* rj,
     });
 }
 
+/* ---------------------------------------------------------------- G1 multi-scalar multiplication */
+
+fp_status fp_g1_bases_from_scalars(const uint64_t* s_limbs, uint64_t n, int on_device, void* stream,
+                                   fp_g1_bases** out) {
+    if (!out || (!s_limbs && n) || n >= (1ull << 30)) return FP_EINVAL;
+    cudaStream_t s = (cudaStream_t)stream;
+    return guarded([&]() -> fp_status {
+        fp_g1_bases* P = new fp_g1_bases{n};
+        void* src = nullptr;
+        try {
+            P->tab = dalloc(2 * n * G1A_BYTES, s);
+            const void* sc = s_limbs;
+            if (!on_device && n) {
+                src = dalloc(n * FR_BYTES, s);
+                check(cudaMemcpyAsync(src, s_limbs, n * FR_BYTES, cudaMemcpyHostToDevice, s), "H2D s");
+                sc = src;
+            }
+            if (n) g1_gen_mul(sc, (uint32_t)n, P->tab, s);
+            msm_bases_endo(P->tab, n, s);
+            check_launch("fp_g1_bases_from_scalars");
+            dfree(src, s);
+            check(cudaStreamSynchronize(s), "fp_g1_bases_from_scalars");
+        } catch (...) {
+            cudaStreamSynchronize(s);
+            fp_g1_bases_free(P);
+            throw;
+        }
+        *out = P;
+        return FP_OK;
+    });
+}
+
+fp_status fp_g1_bases_load(const uint8_t* pts, uint64_t n, int on_device, void* stream, fp_g1_bases** out) {
+    if (!out || (!pts && n) || n >= (1ull << 30)) return FP_EINVAL;
+    cudaStream_t s = (cudaStream_t)stream;
+    return guarded([&]() -> fp_status {
+        fp_g1_bases* P = new fp_g1_bases{n};
+        void* src = nullptr;
+        uint32_t* err = nullptr;
+        uint32_t herr = 0;
+        try {
+            P->tab = dalloc(2 * n * G1A_BYTES, s);
+            err = (uint32_t*)dalloc(sizeof(uint32_t), s);
+            check(cudaMemsetAsync(err, 0, sizeof(uint32_t), s), "memset");
+            const void* be = pts;
+            if (!on_device && n) {
+                src = dalloc(n * G1_SER, s);
+                check(cudaMemcpyAsync(src, pts, n * G1_SER, cudaMemcpyHostToDevice, s), "H2D points");
+                be = src;
+            }
+            msm_bases_load(be, n, P->tab, err, s);
+            check_launch("fp_g1_bases_load");
+            check(cudaMemcpyAsync(&herr, err, sizeof herr, cudaMemcpyDeviceToHost, s), "D2H err");
+            dfree(src, s);
+            void* e = err;
+            dfree(e, s);
+            check(cudaStreamSynchronize(s), "fp_g1_bases_load");
+        } catch (...) {
+            cudaStreamSynchronize(s);
+            fp_g1_bases_free(P);
+            throw;
+        }
+        if (herr) {
+            fp_g1_bases_free(P);
+            return FP_EINVAL;
+        }
+        *out = P;
+        return FP_OK;
+    });
+}
+
+uint64_t fp_g1_bases_count(const fp_g1_bases* P) { return P ? P->n : 0; }
+
+}  // extern "C"
+
+namespace {
+// windows chosen by fp_msm_autotune, per (terms, batches)
+std::mutex g_tune_mu;
+std::vector<std::pair<std::pair<uint64_t, uint32_t>, int>> g_tuned;
+
+int tuned_window(uint64_t n, uint32_t nbatch) {
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    for (auto& e : g_tuned)
+        if (e.first.first == n && e.first.second == nbatch) return e.second;
+    return 0;
+}
+
+bool msm_shape_ok(const MsmShape& sh) {
+    return sh.entries_max() <= 0xffffffffull && sh.nkeys() <= 0xffffffffull;
+}
+
+// enqueue one MSM; the scalars and the serialised output are device pointers
+void msm_enqueue(const fp_g1_bases* P, const void* k_dev, const MsmShape& sh, void* out_ser, cudaStream_t s) {
+    void* scratch = dalloc(msm_scratch_bytes(sh), s);
+    msm_g1(P->tab, k_dev, sh, scratch, nullptr, out_ser, s);
+    check_launch("fp_msm_g1");
+    dfree(scratch, s);
+}
+}  // namespace
+
+extern "C" {
+
+int fp_msm_window(uint64_t n, uint32_t nbatch) {
+    const int t = tuned_window(n, nbatch);
+    return t ? t : msm_window_model(n, nbatch);
+}
+
+fp_status fp_msm_g1(const fp_g1_bases* P, const uint64_t* k, uint64_t n, uint32_t nbatch, int on_device,
+                    int window, void* stream, uint8_t* out) {
+    if (!P || !out || (!k && n && nbatch) || (n && !P->n)) return FP_EINVAL;
+    if (window != 0 && (window < 4 || window > 16)) return FP_EINVAL;
+    if (!nbatch) return FP_OK;
+    const int c = window ? window : fp_msm_window(n, nbatch);
+    const MsmShape sh = msm_shape(n, nbatch, P->n ? P->n : 1, c);
+    if (!msm_shape_ok(sh)) return FP_EINVAL;
+    cudaStream_t s = (cudaStream_t)stream;
+    return guarded([&]() -> fp_status {
+        void *kd = nullptr, *od = nullptr;
+        try {
+            const void* kp = k;
+            void* op = out;
+            if (!on_device) {
+                kd = dalloc(n * nbatch * FR_BYTES, s);
+                if (n) check(cudaMemcpyAsync(kd, k, n * nbatch * FR_BYTES, cudaMemcpyHostToDevice, s), "H2D k");
+                od = dalloc((size_t)nbatch * G1_SER, s);
+                kp = kd;
+                op = od;
+            }
+            msm_enqueue(P, kp, sh, op, s);
+            if (!on_device) {
+                check(cudaMemcpyAsync(out, od, (size_t)nbatch * G1_SER, cudaMemcpyDeviceToHost, s), "D2H msm");
+                dfree(kd, s);
+                dfree(od, s);
+                check(cudaStreamSynchronize(s), "fp_msm_g1");
+            }
+        } catch (...) {
+            cudaStreamSynchronize(s);
+            dfree(kd, s);
+            dfree(od, s);
+            throw;
+        }
+        return FP_OK;
+    });
+}
+
+fp_status fp_msm_autotune(const fp_g1_bases* P, const uint64_t* k_dev, uint64_t n, uint32_t nbatch, void* stream,
+                          int* window, double* best_ms) {
+    if (!P || !window || !k_dev || !n || !nbatch || !P->n) return FP_EINVAL;
+    cudaStream_t s = (cudaStream_t)stream;
+    return guarded([&]() -> fp_status {
+        const int c0 = msm_window_model(n, nbatch);
+        void* od = dalloc((size_t)nbatch * G1_SER, s);
+        cudaEvent_t e0, e1;
+        check(cudaEventCreate(&e0), "cudaEventCreate");
+        check(cudaEventCreate(&e1), "cudaEventCreate");
+        int best = c0;
+        float bt = 1e30f;
+        for (int c = std::max(4, c0 - 3); c <= std::min(16, c0 + 3); c++) {
+            const MsmShape sh = msm_shape(n, nbatch, P->n, c);
+            if (!msm_shape_ok(sh)) continue;
+            msm_enqueue(P, k_dev, sh, od, s);            // warm-up (allocation pool, caches)
+            check(cudaEventRecord(e0, s), "cudaEventRecord");
+            msm_enqueue(P, k_dev, sh, od, s);
+            check(cudaEventRecord(e1, s), "cudaEventRecord");
+            check(cudaEventSynchronize(e1), "cudaEventSynchronize");
+            float ms = 0;
+            check(cudaEventElapsedTime(&ms, e0, e1), "cudaEventElapsedTime");
+            if (ms < bt) {
+                bt = ms;
+                best = c;
+            }
+        }
+        cudaEventDestroy(e0);
+        cudaEventDestroy(e1);
+        dfree(od, s);
+        check(cudaStreamSynchronize(s), "fp_msm_autotune");
+        {
+            std::lock_guard<std::mutex> lk(g_tune_mu);
+            bool found = false;
+            for (auto& e : g_tuned)
+                if (e.first.first == n && e.first.second == nbatch) { e.second = best; found = true; }
+            if (!found) g_tuned.push_back({{n, nbatch}, best});
+        }
+        *window = best;
+        if (best_ms) *best_ms = bt;
+        return FP_OK;
+    });
+}
+
+void fp_g1_bases_free(fp_g1_bases* P) {
+    if (!P) return;
+    cudaDeviceSynchronize();
+    cudaFree(P->tab);
+    delete P;
+}
+
+
 void fp_pp_free(fp_pp* pp) {
     if (!pp) return;
     cudaDeviceSynchronize();
-    cudaFree(pp->lam); cudaFree(pp->g1beta); cudaFree(pp->g2pow); cudaFree(pp->g2tau);
+    cudaFree(pp->lam); cudaFree(pp->lam_tab); cudaFree(pp->g1beta); cudaFree(pp->g2pow); cudaFree(pp->g2tau);
     delete pp;
 }
 void fp_commit_free(fp_commit* cm) {

@@ -45,3 +45,23 @@ def test_invalid_arguments_rejected_without_device_work():
     assert lib.vc_setup(10, 0, 0, None, ctypes.byref(out)) == 1      # b < 1
     lib.fp_strerror.restype = ctypes.c_char_p
     assert lib.fp_strerror(6) == b"scalar out of range (>= r)"
+
+
+def test_msm_window_model_and_argument_checks():
+    """fp_msm_window is host logic (cost model); fp_msm_g1 rejects bad arguments before device work."""
+    from paper_2601_03031_gb300 import build as B
+    lib = ctypes.CDLL(B.build())
+    lib.fp_msm_window.argtypes = [ctypes.c_uint64, ctypes.c_uint32]
+    ws = [lib.fp_msm_window(1 << k, 1) for k in range(8, 25)]
+    assert all(4 <= w <= 16 for w in ws)
+    assert ws == sorted(ws)                           # more terms never pick a smaller window
+    assert lib.fp_msm_window(1024, 1024) <= lib.fp_msm_window(1 << 20, 1)
+    lib.fp_msm_g1.argtypes = [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_uint64, ctypes.c_uint32, ctypes.c_int,
+                              ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p]
+    buf = ctypes.create_string_buffer(96)
+    assert lib.fp_msm_g1(None, None, 0, 1, 0, 0, None, buf) == 1      # no bases
+    lib.fp_g1_bases_from_scalars.argtypes = [ctypes.c_void_p, ctypes.c_uint64, ctypes.c_int, ctypes.c_void_p,
+                                             ctypes.c_void_p]
+    out = ctypes.c_void_p()
+    assert lib.fp_g1_bases_from_scalars(None, 5, 0, None, ctypes.byref(out)) == 1   # NULL scalars, n > 0
+    assert lib.fp_g1_bases_from_scalars(None, 1 << 30, 0, None, ctypes.byref(out)) == 1
