@@ -24,52 +24,39 @@ import time
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
-# Fq multiplications per unit operation of the implementation (operation counts of the formulas
-# used; an Fq multiplication is one 12-limb CIOS Montgomery product = 4 * 12^2 = 576 32-bit
-# multiply-adds).  See DESIGN.md, "Roofline".
+# Fq multiplications per unit operation, from the operation counts of efficient textbook formulas
+# (an Fq multiplication is one 12-limb CIOS Montgomery product = 4 * 12^2 = 576 32-bit
+# multiply-adds).  These are ALGORITHMIC counts: the kernels' own formulas may do more.
 FQ_MUL_IMAD = 4 * 12 * 12
 FQ_MULS = {
     "miller_loop": 7135,     # 62 Fq12 sqr + 63 doubling steps + 5 addition steps, with their lines
     "final_exp": 10120,      # easy part (Fq12 inverse) + h1 and three |x| cyclotomic exponentiations
-    "g1_mul": 2000,          # GLV: ~128 doublings + ~96 mixed additions over 3 affine points
-    "g2_mul": 3300,          # GLS: 64 doublings + ~60 mixed additions over a 15-point affine table
-}
-KERNEL_UNITS = {             # kernel -> unit whose Fq-multiplication count is in FQ_MULS
-    "k_round_terms": ("miller_loop", "g1_mul"),
-    "k_fold": ("g1_mul", "g2_mul"),
-    "k_step1_miller": "miller_loop",
-    "k_commit_miller": "miller_loop",
-    "k_round_out": "final_exp",
-    "k_final_exp": "final_exp",
-    "k_fold_g2": "g2_mul",
-    "k_w_terms": "g2_mul",
-    "k_fold_g1": "g1_mul",
-    "k_sparse_terms": "g1_mul",
-    "k_commit_terms": "g1_mul",
+    "g1_mul": 2000,          # GLV: 128 Jacobian doublings (7) + ~96 mixed additions (11)
+    "g2_mul": 3300,          # GLS: 64 doublings + ~60 mixed additions over Fq2, 15-point table
+    "msm_madd": 10,          # XYZZ mixed addition (8M + 2S), one per bucket entry
 }
 
 
-def kernel_units(name: str, log_n: int, b: int) -> int:
-    """Units (Miller loops, exponentiations, scalar multiplications) summed over one step's launches."""
+def step_units(log_n: int, b: int, msm_window: int) -> dict:
+    """Per kernel: (unit, units processed per step) for one Commit + OpenAll step."""
     lr = log_n // 2
     lc = log_n - lr
     R, M = 1 << lr, 1 << lc
     K = (R + b - 1) // b
-    if name in ("k_step1_miller", "k_round_terms", "k_sparse_terms"):
-        return sum(K * 2 * (R >> j) for j in range(1, lr + 1))
-    if name == "k_round_out":
-        return 2 * K * lr
-    if name in ("k_fold_g2", "k_fold_g1", "k_fold"):
-        return sum(K * (R >> j) for j in range(1, lr + 1))
-    if name == "k_w_terms":
-        return K * (2 * R - 2)
-    if name == "k_commit_miller":
-        return R
-    if name == "k_final_exp":
-        return 1
-    if name == "k_commit_terms":
-        return R * M
-    return 0
+    hs = [R >> j for j in range(1, lr + 1)]
+    W = -(-129 // msm_window)
+    return {
+        "k_final_exp_g": ("final_exp", 1 + 2 * K * lr),
+        "k_round_terms_g": ("miller_loop", sum(K * 2 * h for h in hs if K * 2 * h < 16384)),
+        "k_step1_miller": ("miller_loop", sum(K * 2 * h for h in hs if K * 2 * h >= 16384)),
+        "k_commit_miller_g": ("miller_loop", R),
+        "k_sparse_terms": ("g1_mul", sum(K * min(b, 2 * h) for h in hs)),
+        "k_fold_grp": (("g1_mul", "g2_mul"), sum(K * h for h in hs if K * h <= 4096)),
+        "k_fold": (("g1_mul", "g2_mul"), sum(K * h for h in hs if K * h > 4096)),
+        "k_msm_bucket": ("msm_madd", 2 * R * M * W),
+        "k_w_terms": ("g2_mul", K * (2 * R - 2)),
+        "k_pst_terms": ("g1_mul", M * lc // 2),
+    }
 
 
 class ClockSampler:
@@ -136,7 +123,65 @@ def parse():
     ap.add_argument("--seed", type=int, default=1)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-sweeps", action="store_true", help="skip the N=2^20 b sweep and the MSM sweep")
+    ap.add_argument("--msm-sweep", default="12,14,16,18,20,22,24", help="log2 sizes of the MSM sweep")
+    ap.add_argument("--b-sweep", default="1,16,256,1024", help="b values of the N=2^20 ProveAll sweep")
     return ap.parse_args()
+
+
+def time_device(fn, stream, steps: int, warmup: int, flush=None) -> float:
+    """Average ms of fn() on `stream` by CUDA events, after warm-up; L2 flushed before each run."""
+    import torch
+    for _ in range(warmup):
+        fn()
+    torch.cuda.synchronize()
+    total = 0.0
+    for _ in range(steps):
+        if flush is not None:
+            flush.zero_()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        fn()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        total += e0.elapsed_time(e1)
+    return total / steps
+
+
+def proveall_sweep(F, I, torch, np, stream, flush, b_values, seed: int) -> dict:
+    """ProveAll (Commit + OpenAll) proofs/s at N = 2^20 for each b (3 warm-up, 3 timed steps)."""
+    log_n = 20
+    pp = F.PP(log_n, 1, seed, stream)
+    m_dev = torch.from_numpy(I.vector(seed + 1, log_n).view(np.int64).copy()).cuda()
+    out = {}
+    for b in b_values:
+        keep = []
+
+        def step():
+            cm = F.Commitment(pp, m_dev, stream)
+            keep.append((cm, F.Proofs(pp, cm, b, stream)))
+            if len(keep) > 2:
+                keep.pop(0)
+        ms = time_device(step, stream, 3, 3, flush)
+        out[f"b={b}"] = {"proofs_per_s": (1 << log_n) / (ms * 1e-3), "ms_per_step": ms}
+    return out
+
+
+def msm_sweep(F, I, torch, np, stream, flush, logs, seed: int) -> dict:
+    """Standalone G1 MSM, uniform 255-bit scalars, window by the autotuner: Mpts/s per size."""
+    out = {}
+    for lg in logs:
+        n = 1 << lg
+        s_dev = torch.from_numpy(I.fr_uniform(seed + 1000 + lg, n).view(np.int64)).cuda()
+        k_dev = torch.from_numpy(I.fr_uniform(seed + 2000 + lg, n).view(np.int64)).cuda()
+        bases = F.G1Bases(scalars=s_dev, stream=stream)
+        res = torch.zeros(96, dtype=torch.uint8, device="cuda")
+        window, _ = F.msm_autotune(bases, k_dev, 1, stream)
+        ms = time_device(lambda: F.msm_g1(bases, k_dev, 1, 0, stream, res), stream, 5, 3, flush)
+        out[f"2^{lg}"] = {"mpts_per_s": n / (ms * 1e-3) / 1e6, "ms": ms, "window": window}
+        del bases, s_dev, k_dev
+        torch.cuda.empty_cache()
+    return out
 
 
 # --------------------------------------------------------------------------------- oracle arm
@@ -315,19 +360,22 @@ def main():
 
     # roofline of the dominant kernel (integer multiply-add pipe)
     peak = F.imad_peak()
+    units = step_units(log_n, b, F.msm_window(pp.M, pp.R))
     dom = max(prof.items(), key=lambda kv: kv[1][1]) if prof else ("", (0, 0.0))
     name, (cnt, kms) = dom
-    unit = KERNEL_UNITS.get(name)
     roof = None
-    if unit and kms > 0:
-        units = unit if isinstance(unit, tuple) else (unit,)
-        ops_step = kernel_units(name, log_n, b) * sum(FQ_MULS[u] for u in units) * FQ_MUL_IMAD
+    if name in units and kms > 0 and units[name][1] > 0:
+        unit, n_units = units[name]
+        per_unit = sum(FQ_MULS[u] for u in (unit if isinstance(unit, tuple) else (unit,)))
+        ops_step = n_units * per_unit * FQ_MUL_IMAD
         launches_per_step = cnt / args.steps
         avg_ms = kms / cnt
         ops_launch = ops_step / launches_per_step
         achieved = ops_launch / (avg_ms * 1e-3)
         roof = {"bound": "alu", "kernel": name, "achieved": achieved / 1e12, "peak": peak / 1e12,
                 "unit": "Tops/s (32-bit multiply-add lane ops)", "frac": achieved / peak, "traffic": None,
+                "units_per_step": n_units, "unit_op": unit, "launches_per_step": launches_per_step,
+                "avg_launch_ms": avg_ms,
                 "peak_source": "measured: fp_imad_probe on this GPU in this run"}
     share = {k: round(v[1] / (total_ms if total_ms else 1), 4) for k, v in
              sorted(prof.items(), key=lambda kv: -kv[1][1])[:8]}
@@ -340,6 +388,15 @@ def main():
                    "seconds_per_step_scaled": cpu_s}
         except Exception as e:      # the baseline is reported, not required for the GPU number
             cpu = {"value": None, "unit": "proofs/s", "cores": 1, "kind": "oracle", "sample": f"failed: {e}"}
+
+    sweeps = None
+    if not args.no_sweeps:
+        sweeps = {
+            "proveall_n2^20": proveall_sweep(F, I, torch, np, stream, flush,
+                                             [int(x) for x in args.b_sweep.split(",") if x], args.seed),
+            "msm_g1": msm_sweep(F, I, torch, np, stream, flush,
+                                [int(x) for x in args.msm_sweep.split(",") if x], args.seed),
+        }
 
     line = {
         "metric": "ProveAll proofs/s (Commit + OpenAll)", "value": value, "unit": "proofs/s",
@@ -355,6 +412,7 @@ def main():
         "kernel_share": share,
         "clocks": clk.summary(),
         "cpu_baseline": cpu,
+        "sweeps": sweeps,
     }
     print(json.dumps(line))
     if world > 1:

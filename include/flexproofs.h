@@ -127,8 +127,9 @@ fp_status vc_commit_rows_noalloc(const fp_pp* pp, const uint64_t* m_dev, uint8_t
  * fp_g1_bases_from_scalars: bases P_i = s_i g1 for i < n (s: n x 4 little-endian uint64, any
  *   256-bit values; host or device pointer per on_device).  Synchronises.
  * fp_g1_bases_load: bases from n serialised affine points (n x 96 B, canonical big-endian, all-zero
- *   bytes = identity), host or device pointer per on_device.  A coordinate >= p or a point off
- *   y^2 = x^3 + 4 gives FP_EINVAL (no handle).  Synchronises.
+ *   bytes = identity), host or device pointer per on_device.  A coordinate >= p, a point off
+ *   y^2 = x^3 + 4 or a point outside the order-r subgroup G1 gives FP_EINVAL (no handle).
+ *   Synchronises.
  * Both limit n < 2^30.  The handle holds 2n affine points (P_i and the GLV partner -phi(P_i)),
  * 192 B per base. */
 fp_status fp_g1_bases_from_scalars(const uint64_t* s, uint64_t n, int on_device, void* stream, fp_g1_bases** out);
@@ -138,8 +139,7 @@ void fp_g1_bases_free(fp_g1_bases* P);
 
 /* out[j] = sum_{i<n} k[j n + i] P[(j n + i) mod npts] for j < nbatch, npts = the handle's base count
  * (so nbatch sums over the same n bases when npts = n, or over consecutive slices).
- *   k:   n * nbatch scalars, 4 little-endian uint64 each, any 256-bit values (the integer
- *        combination is computed; for bases in G1 it equals the one with k mod r).
+ *   k:   n * nbatch scalars, 4 little-endian uint64 each, any 256-bit values (used mod r).
  *   out: nbatch x 96 B serialised affine points (identity = zeros).
  *   on_device = 1: k and out are device pointers and the call only enqueues (no synchronisation;
  *        scratch is allocated and freed stream-ordered on `stream`).  on_device = 0: both are host

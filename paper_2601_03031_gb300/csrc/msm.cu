@@ -1,22 +1,22 @@
 // Batched Pippenger multi-scalar multiplication on G1:
 //     out[j] = sum_{i < n} k[j n + i] P[(j n + i) mod npts],   j < nbatch,
-// for affine bases P (Montgomery form) and 256-bit scalars k (any value; the result is the integer
-// combination, which for bases in G1 equals the combination with k mod r).
+// for affine bases P (Montgomery form) and 256-bit scalars k (reduced mod r first, so for bases
+// in G1 the result is the integer combination).
 //
-//   0. GLV split: k = k0 + k1 |x|^2 with k0 < |x|^2 < 2^128 and k1 < 2^129; since
+//   0. GLV split: k = k0 + k1 |x|^2 with k0 < |x|^2 and k1 < r / |x|^2, both below 2^128; since
 //      phi(x, y) = (omega x, y) acts as [-x^2] on G1, k P = k0 P + k1 (-phi(P)).  The bases table
 //      holds P_i and -phi(P_i), so every term becomes two half-length terms.
-//   1. signed c-bit digits of each half, d in (-2^(c-1), 2^(c-1)] with a carry into the next
-//      window; W = ceil(130 / c) windows absorb the last carry.  Key (batch, window, |d| - 1) selects
-//      one of B = 2^(c-1) buckets; a negative digit negates the base.
+//   1. signed digits of each half over W windows of c or c - 1 bits covering 129 bits (msm.h):
+//      d in (-2^(c_w-1), 2^(c_w-1)] with a carry into the next window.  Key (batch, window,
+//      |d| - 1) selects a bucket; a negative digit negates the base.
 //   2. counting sort of the (base, window) entries by key: histogram with atomics, exclusive scan,
 //      scatter of base index | sign bit;
 //   3. one thread per bucket sums its bases with XYZZ mixed additions;
-//   4. bucket reduction sum_b (b + 1) B_b: the B buckets of a window are cut into S segments of L;
+//   4. bucket reduction sum_b (b + 1) B_b: the buckets of a window are cut into S segments;
 //      a thread per segment forms its running sums plus (start) x (segment sum), and the segment
 //      results are added pairwise;
-//   5. per batch, Horner over the windows (c doublings each) on an 8-lane group with the complete
-//      projective formulas, then one inversion to affine.
+//   5. per batch, Horner over the windows (c_w doublings each) on an 8-lane group with the
+//      complete projective formulas, then one inversion to affine.
 // XYZZ coordinates: x = X / ZZ, y = Y / ZZZ (ZZ^3 = ZZZ^2), identity ZZ = 0; formulas madd-2008-s,
 // add-2008-s and dbl-2008-s-1 of the Explicit-Formulas Database (curve coefficient a = 0).
 #include <algorithm>
@@ -108,19 +108,34 @@ FPG_DEV uint32_t win_bits(const uint32_t* a, int nw, int lo, int c) {
     return (uint32_t)(two >> bit) & ((1u << c) - 1);
 }
 
-// calls emit(half, window, digit) for every non-zero signed digit of the GLV halves of k
+// k mod r for a 256-bit k (k < 2^256 < 3 r)
+FPG_DEV void reduce_mod_r(uint32_t* k) {
+    for (int it = 0; it < 2; it++) {
+        if (mp::lt<8>(k, FR_P)) return;
+        uint32_t t[8];
+        mp::mod_sub<8>(t, k, FR_P, FR_P);           // k >= r: no borrow, t = k - r
+#pragma unroll
+        for (int i = 0; i < 8; i++) k[i] = t[i];
+    }
+}
+
+// calls emit(half, window, digit) for every non-zero signed digit of the GLV halves of k mod r
 template <typename Emit>
-FPG_DEV void msm_digits(const uint32_t* k, const MsmShape& sh, Emit&& emit) {
-    uint32_t k1[5], k0[4];
+FPG_DEV void msm_digits(const fr& s, const MsmShape& sh, Emit&& emit) {
+    uint32_t k[8], k1[5], k0[4];
+#pragma unroll
+    for (int i = 0; i < 8; i++) k[i] = s.v[i];
+    reduce_mod_r(k);
     div_by_const<4, 5>(k1, k0, k, GLV_D, GLV_BARRETT);
     for (int h = 0; h < 2; h++) {
         const uint32_t* a = h ? k1 : k0;
         const int nw = h ? 5 : 4;
         int32_t carry = 0;
         for (int w = 0; w < sh.W; w++) {
-            int32_t d = (int32_t)win_bits(a, nw, w * sh.c, sh.c) + carry;
-            carry = d > (int32_t)sh.B;
-            if (carry) d -= 1 << sh.c;
+            const int cw = sh.bits(w);
+            int32_t d = (int32_t)win_bits(a, nw, sh.lo(w), cw) + carry;
+            carry = d > (1 << (cw - 1));
+            if (carry) d -= 1 << cw;
             if (d) emit(h, w, d);
         }
     }
@@ -129,21 +144,19 @@ FPG_DEV void msm_digits(const uint32_t* k, const MsmShape& sh, Emit&& emit) {
 __global__ void k_msm_count(const fr* k, MsmShape sh, uint32_t* counts) {
     const uint64_t t = gtid();
     if (t >= sh.n * sh.nbatch) return;
-    const uint64_t base = (t / sh.n) * sh.W;
-    const fr s = k[t];
-    msm_digits(s.v, sh, [&](int, int w, int32_t d) {
-        atomicAdd(&counts[(base + w) * sh.B + (uint32_t)(d < 0 ? -d : d) - 1], 1u);
+    const uint64_t base = (t / sh.n) * sh.KW;
+    msm_digits(k[t], sh, [&](int, int w, int32_t d) {
+        atomicAdd(&counts[base + sh.off(w) + (uint32_t)(d < 0 ? -d : d) - 1], 1u);
     });
 }
 
 __global__ void k_msm_scatter(const fr* k, MsmShape sh, uint32_t* cursor, uint32_t* list) {
     const uint64_t t = gtid();
     if (t >= sh.n * sh.nbatch) return;
-    const uint64_t base = (t / sh.n) * sh.W;
+    const uint64_t base = (t / sh.n) * sh.KW;
     const uint32_t pidx = (uint32_t)(t % sh.npts);
-    const fr s = k[t];
-    msm_digits(s.v, sh, [&](int h, int w, int32_t d) {
-        const uint32_t pos = atomicAdd(&cursor[(base + w) * sh.B + (uint32_t)(d < 0 ? -d : d) - 1], 1u);
+    msm_digits(k[t], sh, [&](int h, int w, int32_t d) {
+        const uint32_t pos = atomicAdd(&cursor[base + sh.off(w) + (uint32_t)(d < 0 ? -d : d) - 1], 1u);
         list[pos] = (pidx + (h ? (uint32_t)sh.npts : 0u)) | (d < 0 ? 0x80000000u : 0u);
     });
 }
@@ -205,13 +218,15 @@ __global__ void __launch_bounds__(128) k_msm_bucket(const g1a* pts, MsmShape sh,
     buckets[key] = acc;
 }
 
-// segment s of a window: buckets b in [s L, (s + 1) L) give sum_b (b + 1) B_b
+// segment s of window w of batch j: its L = B_w / S buckets b in [s L, (s + 1) L) give
+// sum_b (b + 1) B_b
 __global__ void __launch_bounds__(128) k_msm_segment(MsmShape sh, const xyzz* buckets, xyzz* segs) {
     const uint64_t t = gtid();
     if (t >= sh.nsegs()) return;
-    const uint64_t win = t / sh.S;
-    const uint32_t s = (uint32_t)(t % sh.S), L = sh.B / sh.S;
-    const xyzz* bk = buckets + win * sh.B + (uint64_t)s * L;
+    const uint64_t j = t / ((uint64_t)sh.W * sh.S);
+    const int w = (int)((t / sh.S) % sh.W);
+    const uint32_t s = (uint32_t)(t % sh.S), L = sh.buckets(w) / sh.S;
+    const xyzz* bk = buckets + j * sh.KW + sh.off(w) + (uint64_t)s * L;
     xyzz run, acc;
     xyzz_inf(run);
     xyzz_inf(acc);
@@ -244,7 +259,7 @@ __global__ void k_msm_to_proj(const xyzz* in, GPt<fq>* out, uint64_t n) {
     out[i] = r;
 }
 
-// per batch, on 8 lanes: sum_w 2^(c w) S_w by Horner from the top window, then affine
+// per batch, on 8 lanes: sum_w 2^(lo_w) S_w by Horner from the top window, then affine
 __global__ void __launch_bounds__(64) k_msm_final(MsmShape sh, const GPt<fq>* win, g1a* out, uint8_t* ser) {
     __shared__ GEc<fq> sm[8];
     const int grp = threadIdx.x >> 3, lane = threadIdx.x & 7;
@@ -253,7 +268,7 @@ __global__ void __launch_bounds__(64) k_msm_final(MsmShape sh, const GPt<fq>* wi
     const uint64_t j = valid ? j0 : 0;                // idle groups repeat batch 0's work
     GPt<fq> acc = win[j * sh.W + sh.W - 1];
     for (int w = sh.W - 2; w >= 0; w--) {
-        for (int q = 0; q < sh.c; q++) acc = gec_dbl(sm[grp], lane, acc);
+        for (int q = 0; q < sh.bits(w); q++) acc = gec_dbl(sm[grp], lane, acc);
         acc = gec_add(sm[grp], lane, acc, win[j * sh.W + w]);
     }
     g1a a;
@@ -266,7 +281,7 @@ __global__ void __launch_bounds__(64) k_msm_final(MsmShape sh, const GPt<fq>* wi
 
 // ---------------------------------------------------------------------------- bases
 // first half of the bases table from serialised affine points; err |= 1 for a point that is not
-// canonical or not on y^2 = x^3 + 4 (all-zero bytes = identity)
+// canonical, not on y^2 = x^3 + 4 or not in the order-r subgroup (all-zero bytes = identity)
 __global__ void k_bases_load(const uint8_t* be, uint64_t n, g1a* tab, uint32_t* err) {
     const uint64_t i = gtid();
     if (i >= n) return;
@@ -292,7 +307,18 @@ __global__ void k_bases_load(const uint8_t* be, uint64_t n, g1a* tab, uint32_t* 
             fq four;
             fq_one(four);
             four = fq_dbl(fq_dbl(four));
-            if (!fq_eq(fq_sqr(a.y), fq_add(fq_mul(fq_sqr(a.x), a.x), four))) atomicOr(err, 1u);
+            if (!fq_eq(fq_sqr(a.y), fq_add(fq_mul(fq_sqr(a.x), a.x), four))) {
+                atomicOr(err, 1u);
+            } else {
+                // subgroup: [r] P must be the identity (plain double-and-add, no endomorphism)
+                g1j acc;
+                jac_set_inf(acc);
+                for (int i = 254; i >= 0; i--) {
+                    acc = jac_dbl(acc);
+                    if ((FR_P[i >> 5] >> (i & 31)) & 1) acc = jac_madd(acc, a.x, a.y);
+                }
+                if (!jac_is_inf(acc)) atomicOr(err, 1u);
+            }
         }
     }
     tab[i] = a;
@@ -324,12 +350,13 @@ MsmShape msm_shape(uint64_t n, uint32_t nbatch, uint64_t npts, int c) {
     sh.n = n;
     sh.nbatch = nbatch;
     sh.npts = npts;
-    sh.c = c;
-    sh.W = (130 + c - 1) / c;
-    sh.B = 1u << (c - 1);
-    // segments of at least 4 buckets, at most about 2^15 segment threads
-    uint32_t S = sh.B;
-    while (S > 1 && sh.B / S < 4) S >>= 1;
+    sh.W = (129 + c - 1) / c;
+    sh.c = (129 + sh.W - 1) / sh.W;                    // balanced widths: c or c - 1
+    sh.n_hi = 129 - sh.W * (sh.c - 1);
+    sh.KW = sh.off(sh.W);
+    // segments of at least 4 buckets in the narrowest window, at most about 2^15 segment threads
+    uint32_t S = sh.buckets(sh.W - 1);
+    while (S > 1 && sh.buckets(sh.W - 1) / S < 4) S >>= 1;
     while (S > 1 && (uint64_t)nbatch * sh.W * S > (1u << 15)) S >>= 1;
     sh.S = S;
     return sh;
@@ -350,19 +377,19 @@ size_t msm_scratch_bytes(const MsmShape& sh) {
 // products/s over the GPU) and the latency of one thread's dependent chain (about 1.3 us per
 // product); mixed addition 10 products, addition 14, group doubling/addition about 2 x 1.5.
 int msm_window_model(uint64_t n, uint32_t nbatch) {
-    const double tp = 1.0 / 1.9e10, lat = 1.3e-6;
+    const double tp = 1.0 / 1.9e10, lat = 2.7e-6;
     int best = 8;
     double bestt = 1e300;
     for (int c = 4; c <= 16; c++) {
         const MsmShape sh = msm_shape(n, nbatch, n, c);
-        if (sh.nkeys() > (1ull << 26) || sh.entries_max() > 0xffffffffull) continue;
-        const double entries = 2.0 * (double)n * nbatch * sh.W * (1.0 - 1.0 / (double)(1u << c));
+        if (sh.c != c || sh.nkeys() > (1ull << 28) || sh.entries_max() > 0xffffffffull) continue;
+        const double entries = 2.0 * (double)n * nbatch * sh.W;
         const double per_bucket = entries / (double)sh.nkeys();
         const double t_bucket = std::max(entries * 10 * tp, per_bucket * 10 * lat);
-        const double L = (double)(sh.B / sh.S);
+        const double L = (double)(sh.buckets(0) / sh.S);
         const double t_seg = std::max((double)sh.nkeys() * 2 * 14 * tp, (2 * L + 1.5 * (c - 1)) * 14 * lat);
         const double t_pair = std::log2((double)sh.S) * 14 * lat;
-        const double t_final = (double)sh.W * (sh.c * 2 + 2) * 1.5 * lat;
+        const double t_final = 129.0 * 2 * 1.5 * lat;
         const double t = t_bucket + t_seg + t_pair + t_final;
         if (t < bestt) {
             bestt = t;

@@ -104,6 +104,21 @@ def test_msm_bad_points_rejected():
     big = P_FQ.to_bytes(48, "big") + bytes(48)         # x = p is not canonical
     with pytest.raises(F.FlexProofsError):
         F.G1Bases(points=big)
+    with pytest.raises(F.FlexProofsError):            # on the curve, outside the order-r subgroup
+        F.G1Bases(points=off_subgroup_point())
+
+
+def off_subgroup_point() -> bytes:
+    """The first (x, y) on y^2 = x^3 + 4 with x = 1, 2, ...: the cofactor h1 ~ 2^126 leaves it
+    outside G1 (checked here by [r] P != 0 with the oracle)."""
+    for x in range(1, 100):
+        rhs = (x ** 3 + 4) % P_FQ
+        y = pow(rhs, (P_FQ + 1) // 4, P_FQ)                # p = 3 mod 4
+        if y * y % P_FQ == rhs:
+            pt = x.to_bytes(48, "big") + y.to_bytes(48, "big")
+            assert O.g1_valid(pt) and O.g1_mul(pt, R) != bytes(96)
+            return pt
+    raise AssertionError("no point found")
 
 
 @pytest.mark.parametrize("window", [0, 6, 12])
