@@ -18,6 +18,8 @@
  *   - `stream` is a cudaStream_t (NULL = the legacy default stream).  Work is enqueued on it; the
  *     calls below that return data to the host synchronise that stream first.
  *   - Handles are owned by the caller and released with the matching *_free (NULL is ignored).
+ *     Commitment and proof handles are released stream-ordered (after the work that uses them,
+ *     without blocking the host); public parameters and MSM bases synchronise the device.
  *   - Device memory is allocated by the library (stream-ordered) and freed by *_free.
  *   - On any error nothing is written to *out and no partially built handle is returned.
  *   - All computation runs in this library's CUDA kernels on the current device; there is no
@@ -57,6 +59,13 @@ typedef enum {
  * The trapdoor never leaves the device and is discarded before returning. */
 fp_status vc_setup(uint32_t log_n, uint32_t b, uint64_t seed, void* stream, fp_pp** out);
 
+/* A view of `pp` for a smaller size 2^log_n (2 <= log_n <= pp's): the same trapdoor, so every table
+ * of the smaller setup is a prefix of the larger one's (Lambda_t for t <= l_c, g2^{beta^i} for
+ * i < 2R - 1, g2^{tau_t} for t < l_c) and the view shares them; it owns only a small MSM table
+ * (2M points).  One resident SRS then serves jobs of every smaller N.  The view must be freed
+ * (fp_pp_free) before its parent.  Synchronises the legacy default stream. */
+fp_status vc_pp_view(const fp_pp* pp, uint32_t log_n, fp_pp** out);
+
 /* Serialised public parameters (synchronises): Lambda (2M-1) x 96 || g1^beta 96 ||
  * g2^{beta^i} (2R-1) x 192 || g2^{tau_t} l_c x 192.  *len receives the size; out may be NULL to
  * query it. */
@@ -71,6 +80,11 @@ fp_status vc_pp_dims(const fp_pp* pp, uint32_t* log_n, uint32_t* R, uint32_t* M)
  * (checked on the device; the call then synchronises). */
 fp_status vc_commit(const fp_pp* pp, const uint64_t* m, int on_device, void* stream, fp_commit** out);
 
+/* vc_commit without the synchronisation: the work is only enqueued on `stream`, and the range check
+ * of m is reported by vc_commit_status (which waits for this commitment's work only). */
+fp_status vc_commit_async(const fp_pp* pp, const uint64_t* m, int on_device, void* stream, fp_commit** out);
+fp_status vc_commit_status(const fp_commit* cm);   /* FP_OK, or FP_ERANGE if a value of m was >= r */
+
 /* C (576 B) and, if rows != NULL, the R row commitments (R x 96 B).  Synchronises. */
 fp_status vc_commit_get(const fp_commit* cm, uint8_t* gt576, uint8_t* rows);
 
@@ -80,6 +94,26 @@ fp_status vc_commit_get(const fp_commit* cm, uint8_t* gt576, uint8_t* rows);
  *   - per block k < ceil(R/b): pi_{C_k} = ({L_j, R_j}_{j=1..l_R}, A_l, v_l, W),
  *   - the two-level Merkle tree, the fold tree (g_w, D_w for every node), the PST proofs of g*. */
 fp_status vc_prove_all(const fp_pp* pp, const fp_commit* cm, uint32_t b, void* stream, fp_proofs** out);
+
+/* OpenAll for several independent jobs at once (no counterpart in the paper: serving-side batching).
+ * Job j proves jobs[j].cm (any size; commitments made with views of one SRS, or with separate
+ * setups) with batch size jobs[j].b.  Every job runs on its own library stream, forked from and
+ * joined back to `stream`, so small latency-bound jobs overlap on the device.  use_graph = 1 captures
+ * the whole batch (all jobs' launches) into one CUDA graph on `stream` and launches it once; the
+ * call then synchronises `stream`.  outs[j] receives job j's handle, identical in content to
+ * vc_prove_all(jobs[j].cm, jobs[j].b).  On error no handle is returned. */
+typedef struct {
+    const fp_commit* cm;
+    uint32_t b;
+} fp_job;
+fp_status vc_prove_all_batch(uint32_t njobs, const fp_job* jobs, int use_graph, void* stream, fp_proofs** outs);
+
+/* One proof pi_i alone (the same bytes as vc_proof_get of vc_prove_all's result): Step 1 for the
+ * block of i only (FC.BOpen on S_k, k = (i / M) / b), Step 2 in full (it is O(N) either way), then
+ * the proof is assembled.  *len receives the proof length; out may be NULL to query it (no device
+ * work).  i >= N or b out of range gives FP_EINVAL.  Synchronises `stream`. */
+fp_status vc_prove_one(const fp_pp* pp, const fp_commit* cm, uint32_t b, uint64_t i, void* stream, uint8_t* out,
+                       size_t cap, size_t* len);
 
 /* Byte length of proof i under batch size b (no device work). */
 size_t vc_proof_len(const fp_pp* pp, uint32_t b, uint64_t i);

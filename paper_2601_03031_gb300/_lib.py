@@ -19,7 +19,8 @@ EXPORTED = ["vc_setup", "vc_pp_export", "vc_pp_dims", "vc_commit", "vc_commit_ge
             "fp_pp_free", "fp_commit_free", "fp_proofs_free", "fp_strerror", "fp_last_error", "fp_launch_count",
             "fp_profile_enable", "fp_profile_report", "fp_imad_probe", "vc_commit_rows_noalloc",
             "fp_g1_bases_from_scalars", "fp_g1_bases_load", "fp_g1_bases_count", "fp_g1_bases_free", "fp_msm_g1",
-            "fp_msm_window", "fp_msm_autotune"]
+            "fp_msm_window", "fp_msm_autotune", "vc_prove_one", "vc_pp_view", "vc_commit_async",
+            "vc_commit_status", "vc_prove_all_batch"]
 
 
 class FlexProofsError(RuntimeError):
@@ -53,6 +54,11 @@ def load(path: str = LIB_PATH):
     L.vc_proof_len.argtypes = [vp, u32, u64]
     L.vc_proof_len.restype = sz
     L.vc_proof_get.argtypes = [vp, u64, vp, sz, ctypes.POINTER(sz)]
+    L.vc_prove_one.argtypes = [vp, vp, u32, u64, vp, vp, sz, ctypes.POINTER(sz)]
+    L.vc_pp_view.argtypes = [vp, u32, pp]
+    L.vc_commit_async.argtypes = [vp, vp, ctypes.c_int, vp, pp]
+    L.vc_commit_status.argtypes = [vp]
+    L.vc_prove_all_batch.argtypes = [u32, vp, ctypes.c_int, vp, vp]
     L.vc_proofs_export.argtypes = [vp, u64, u64, vp, sz, ctypes.POINTER(sz)]
     L.vc_proofs_state.argtypes = [vp, vp, sz, ctypes.POINTER(sz)]
     L.vc_proofs_step2_parts.argtypes = [vp, vp, vp, vp, vp]
@@ -97,12 +103,17 @@ def _stream_ptr(stream) -> int | None:
 
 
 class PP:
-    """Handle of vc_setup's device-resident public parameters."""
+    """Handle of vc_setup's device-resident public parameters (or, with parent=, a vc_pp_view of a
+    larger setup for size 2^log_n)."""
 
-    def __init__(self, log_n: int, b: int = 1, seed: int = 0, stream=None):
+    def __init__(self, log_n: int, b: int = 1, seed: int = 0, stream=None, parent: "PP | None" = None):
         L = load()
         h = ctypes.c_void_p()
-        _check("vc_setup", L.vc_setup(log_n, b, seed, _stream_ptr(stream), ctypes.byref(h)))
+        if parent is not None:
+            _check("vc_pp_view", L.vc_pp_view(parent.h, log_n, ctypes.byref(h)))
+            self.parent = parent                     # keeps the parent alive while the view lives
+        else:
+            _check("vc_setup", L.vc_setup(log_n, b, seed, _stream_ptr(stream), ctypes.byref(h)))
         self.h = h
         ln, R, M = ctypes.c_uint32(), ctypes.c_uint32(), ctypes.c_uint32()
         L.vc_pp_dims(h, ctypes.byref(ln), ctypes.byref(R), ctypes.byref(M))
@@ -122,6 +133,9 @@ class PP:
     def proof_len(self, b: int, i: int) -> int:
         return load().vc_proof_len(self.h, b, i)
 
+    def view(self, log_n: int) -> "PP":
+        return PP(log_n, parent=self)
+
     def __del__(self):
         if getattr(self, "h", None) and _lib is not None:
             _lib.fp_pp_free(self.h)
@@ -129,9 +143,10 @@ class PP:
 
 
 class Commitment:
-    """Handle of vc_commit: C, the row commitments and the device copy of m."""
+    """Handle of vc_commit: C, the row commitments and the device copy of m.  With sync=False the
+    commitment is only enqueued (vc_commit_async); status() then reports the range check."""
 
-    def __init__(self, pp: PP, m, stream=None):
+    def __init__(self, pp: PP, m, stream=None, sync: bool = True):
         L = load()
         self.pp = pp
         h = ctypes.c_void_p()
@@ -144,8 +159,13 @@ class Commitment:
             assert arr.size == 4 * pp.N
             ptr, on_dev = arr.ctypes.data, 0
             self._keep = arr
-        _check("vc_commit", L.vc_commit(pp.h, ptr, on_dev, _stream_ptr(stream), ctypes.byref(h)))
+        fn = L.vc_commit if sync else L.vc_commit_async
+        _check("vc_commit", fn(pp.h, ptr, on_dev, _stream_ptr(stream), ctypes.byref(h)))
         self.h = h
+
+    def status(self) -> int:
+        """0 if every value of m was < r, else FP_ERANGE (6); waits for this commitment's work."""
+        return int(load().vc_commit_status(self.h))
 
     def get(self, rows: bool = True):
         C = ctypes.create_string_buffer(576)
@@ -162,9 +182,12 @@ class Commitment:
 class Proofs:
     """Handle of vc_prove_all's device-resident shared proof pieces."""
 
-    def __init__(self, pp: PP, cm: Commitment, b: int, stream=None):
+    def __init__(self, pp: PP, cm: Commitment, b: int, stream=None, handle=None):
         L = load()
         self.pp, self.cm, self.b = pp, cm, b
+        if handle is not None:                       # from vc_prove_all_batch
+            self.h = handle
+            return
         h = ctypes.c_void_p()
         _check("vc_prove_all", L.vc_prove_all(pp.h, cm.h, b, _stream_ptr(stream), ctypes.byref(h)))
         self.h = h
@@ -224,6 +247,30 @@ def vc_prove_all(pp: PP, cm: Commitment, b: int, stream=None) -> Proofs:
 
 def vc_proof_get(pf: Proofs, i: int) -> bytes:
     return pf.proof(i)
+
+
+class _Job(ctypes.Structure):
+    _fields_ = [("cm", ctypes.c_void_p), ("b", ctypes.c_uint32)]
+
+
+def vc_prove_all_batch(jobs, use_graph: bool = False, stream=None) -> list:
+    """jobs: list of (Commitment, b).  One Proofs handle per job (vc_prove_all_batch)."""
+    L = load()
+    n = len(jobs)
+    arr = (_Job * max(1, n))(*[_Job(cm.h.value, b) for cm, b in jobs])
+    outs = (ctypes.c_void_p * max(1, n))()
+    _check("vc_prove_all_batch", L.vc_prove_all_batch(n, arr, int(use_graph), _stream_ptr(stream), outs))
+    return [Proofs(cm.pp, cm, b, handle=ctypes.c_void_p(outs[j])) for j, (cm, b) in enumerate(jobs)]
+
+
+def vc_prove_one(pp: PP, cm: Commitment, b: int, i: int, stream=None) -> bytes:
+    """pi_i alone: Step 1 on the block of i, Step 2 in full (synchronises)."""
+    L = load()
+    ln = ctypes.c_size_t()
+    _check("vc_prove_one", L.vc_prove_one(pp.h, cm.h, b, i, _stream_ptr(stream), None, 0, ctypes.byref(ln)))
+    buf = ctypes.create_string_buffer(ln.value)
+    _check("vc_prove_one", L.vc_prove_one(pp.h, cm.h, b, i, _stream_ptr(stream), buf, ln.value, ctypes.byref(ln)))
+    return buf.raw[: ln.value]
 
 
 def launch_count() -> int:

@@ -15,12 +15,14 @@ __global__ void k_step1_init(const g1a* rows, const g2a* g2pow, uint32_t K, uint
     fr_zero(bvec[t]);
 }
 
-// SHA256(C || u32be(k) || u32be(b) || u32be(|S_k|) || C_a for a in S_k)
-__global__ void k_stmt_hash(const uint8_t* C_ser, const uint8_t* rows_ser, uint32_t K, uint32_t R, uint32_t b,
-                            uint8_t* hstmt) {
-    uint64_t k = gtid();
-    if (k >= K) return;
-    uint32_t lo = (uint32_t)k * b, hi = min(lo + b, R), nk = hi - lo;
+// SHA256(C || u32be(k) || u32be(b) || u32be(|S_k|) || C_a for a in S_k), for the K blocks
+// k = k0 .. k0 + K - 1 (stored at local index k - k0)
+__global__ void k_stmt_hash(const uint8_t* C_ser, const uint8_t* rows_ser, uint32_t k0, uint32_t K, uint32_t R,
+                            uint32_t b, uint8_t* hstmt) {
+    const uint64_t kl = gtid();
+    if (kl >= K) return;
+    const uint32_t k = k0 + (uint32_t)kl;
+    uint32_t lo = k * b, hi = min(lo + b, R), nk = hi - lo;
     sha256_ctx c;
     sha256_init(c);
     sha256_update(c, C_ser, 576);
@@ -28,19 +30,19 @@ __global__ void k_stmt_hash(const uint8_t* C_ser, const uint8_t* rows_ser, uint3
     put_be32(hdr, (uint32_t)k); put_be32(hdr + 4, b); put_be32(hdr + 8, nk);
     sha256_update(c, hdr, 12);
     sha256_update(c, rows_ser + (size_t)lo * 96, nk * 96);
-    sha256_final(c, hstmt + k * 32);
+    sha256_final(c, hstmt + kl * 32);
 }
 
-// r_a = HFr("FP-r", SHA256(statement_k) || u32be(a)) placed at b[a] of block k
-__global__ void k_block_r(const uint8_t* hstmt, uint32_t K, uint32_t R, uint32_t b, fr* bvec) {
+// r_a = HFr("FP-r", SHA256(statement_k) || u32be(a)) placed at b[a] of block k (local index k - k0)
+__global__ void k_block_r(const uint8_t* hstmt, uint32_t k0, uint32_t K, uint32_t R, uint32_t b, fr* bvec) {
     uint64_t t = gtid();
     if (t >= (uint64_t)K * b) return;
-    uint32_t k = (uint32_t)(t / b), a = k * b + (uint32_t)(t % b);
+    const uint32_t kl = (uint32_t)(t / b), a = (k0 + kl) * b + (uint32_t)(t % b);
     if (a >= R) return;
     uint8_t buf[36];
-    for (int q = 0; q < 32; q++) buf[q] = hstmt[(size_t)k * 32 + q];
+    for (int q = 0; q < 32; q++) buf[q] = hstmt[(size_t)kl * 32 + q];
     put_be32(buf + 32, a);
-    bvec[(size_t)k * R + a] = hash_to_fr("FP-r", 4, buf, 36, nullptr, 0, nullptr, 0);
+    bvec[(size_t)kl * R + a] = hash_to_fr("FP-r", 4, buf, 36, nullptr, 0, nullptr, 0);
 }
 
 // L_j.1 = <A_R, b_L>, R_j.1 = <A_L, b_R>: one term per (k, side, i)
@@ -300,13 +302,14 @@ void step1_init(const void* rows, const void* g2pow, uint32_t K, uint32_t R, voi
     FP_KERNEL("k_step1_init", s, k_step1_init<<<grid_for((uint64_t)K * R), TPB, 0, s>>>((const g1a*)rows, (const g2a*)g2pow, K, R, (g1a*)A,
                                                           (g2a*)v, (fr*)bvec));
 }
-void step1_stmt_hash(const void* C_ser, const void* rows_ser, uint32_t K, uint32_t R, uint32_t b, void* hstmt,
-                     cudaStream_t s) {
-    FP_KERNEL("k_stmt_hash", s, k_stmt_hash<<<grid_for(K, 64), 64, 0, s>>>((const uint8_t*)C_ser, (const uint8_t*)rows_ser, K, R, b,
-                                               (uint8_t*)hstmt));
+void step1_stmt_hash(const void* C_ser, const void* rows_ser, uint32_t k0, uint32_t K, uint32_t R, uint32_t b,
+                     void* hstmt, cudaStream_t s) {
+    FP_KERNEL("k_stmt_hash", s, k_stmt_hash<<<grid_for(K, 64), 64, 0, s>>>((const uint8_t*)C_ser, (const uint8_t*)rows_ser,
+                                                                         k0, K, R, b, (uint8_t*)hstmt));
 }
-void step1_block_r(const void* hstmt, uint32_t K, uint32_t R, uint32_t b, void* bvec, cudaStream_t s) {
-    FP_KERNEL("k_block_r", s, k_block_r<<<grid_for((uint64_t)K * b, 64), 64, 0, s>>>((const uint8_t*)hstmt, K, R, b, (fr*)bvec));
+void step1_block_r(const void* hstmt, uint32_t k0, uint32_t K, uint32_t R, uint32_t b, void* bvec, cudaStream_t s) {
+    FP_KERNEL("k_block_r", s, k_block_r<<<grid_for((uint64_t)K * b, 64), 64, 0, s>>>((const uint8_t*)hstmt, k0, K, R, b,
+                                                                                    (fr*)bvec));
 }
 void step1_sparse_terms(const void* A, const void* bvec, uint32_t K, uint32_t R, uint32_t h, void* out,
                         cudaStream_t s) {

@@ -61,9 +61,10 @@ void final_exp_batch(const void* in_fq12, uint32_t n, size_t in_stride_elems, vo
 // ---- Step 1 (FC.BOpen for all blocks at once)
 void step1_init(const void* rows_g1a, const void* g2pow, uint32_t K, uint32_t R, void* A, void* v, void* bvec,
                 cudaStream_t s);
-void step1_stmt_hash(const void* C_ser, const void* rows_ser, uint32_t K, uint32_t R, uint32_t b, void* hstmt,
-                     cudaStream_t s);
-void step1_block_r(const void* hstmt, uint32_t K, uint32_t R, uint32_t b, void* bvec, cudaStream_t s);
+// blocks k0 .. k0 + K - 1 of size b (stored at local indices 0 .. K - 1)
+void step1_stmt_hash(const void* C_ser, const void* rows_ser, uint32_t k0, uint32_t K, uint32_t R, uint32_t b,
+                     void* hstmt, cudaStream_t s);
+void step1_block_r(const void* hstmt, uint32_t k0, uint32_t K, uint32_t R, uint32_t b, void* bvec, cudaStream_t s);
 void step1_miller(const void* A, const void* v, uint32_t K, uint32_t R, uint32_t h, void* out_fq12, cudaStream_t s);
 void step1_sparse_terms(const void* A, const void* bvec, uint32_t K, uint32_t R, uint32_t h, void* out_g1j,
                         cudaStream_t s);

@@ -31,6 +31,11 @@ cudaEvent_t get_event() {
 void prof_begin(const char* name, cudaStream_t s) {
     g_launches.fetch_add(1, std::memory_order_relaxed);
     if (!g_enabled.load(std::memory_order_relaxed)) { t_cur.name = nullptr; return; }
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    if (cudaStreamIsCapturing(s, &cs) != cudaSuccess || cs != cudaStreamCaptureStatusNone) {
+        t_cur.name = nullptr;                   // launches recorded into a graph are not timed
+        return;
+    }
     std::lock_guard<std::mutex> lk(g_mu);
     t_cur = Rec{name, get_event(), get_event()};
     cudaEventRecord(t_cur.a, s);

@@ -18,6 +18,7 @@ using namespace fpk;
 
 struct fp_pp {
     uint32_t log_n, log_r, log_c, R, M;
+    const fp_pp* parent = nullptr;  // views share the parent's tables (all but lam_tab)
     void* lam = nullptr;      // G1 affine, 2M - 1: Lambda_t at offset 2^t - 1
     void* lam_tab = nullptr;  // G1 affine, 2M: Lambda_{l_c} and its GLV partners (MSM bases)
     void* g1beta = nullptr;   // G1 affine
@@ -33,7 +34,13 @@ struct fp_commit {
     void* rows_ser = nullptr; // R x 96
     void* C = nullptr;        // fq12
     void* C_ser = nullptr;    // 576
+    uint32_t* err = nullptr;  // device word: non-zero if an input value was >= r
+    cudaEvent_t done = nullptr;
     cudaStream_t stream;
+    // completion events of the calls that read this handle on other streams (vc_prove_all); the
+    // free waits for them, stream-ordered, without blocking the host
+    mutable std::mutex mu;
+    mutable std::vector<cudaEvent_t> uses;
 };
 
 struct fp_g1_bases {
@@ -117,26 +124,42 @@ void* reduce_pairs(void* a, void* b, uint64_t n, uint64_t target, Red red, cudaS
 
 size_t bopen_len(uint32_t log_r) { return (size_t)log_r * ROUND_BYTES + G1_SER + 2 * G2_SER; }
 
-// Internal non-blocking streams per device, created on first use: OpenAll's latency-bound Step 1
-// runs on two high-priority streams (the round chain, and the sparse G1 terms that overlap it),
-// the throughput-bound Step 2 on a low-priority stream; all are forked from and joined back to the
-// caller's stream with events created per call.
+// Internal non-blocking streams: OpenAll's latency-bound Step 1 runs on two high-priority streams
+// (the round chain, and the sparse G1 terms that overlap it), the throughput-bound Step 2 on a
+// low-priority stream; all are forked from and joined back to the caller's stream with events
+// created per call.  Each caller stream (per device) gets its own set, so calls on different caller
+// streams run concurrently; past 256 caller streams the sets are shared (still correct, less
+// concurrent).
 struct Streams { cudaStream_t hi = nullptr, sp = nullptr, lo = nullptr; };
-Streams g_streams[64];
+struct StreamKey { int dev; cudaStream_t user; Streams set; };
+std::vector<StreamKey> g_sets;
 std::mutex g_aux_mu;
-Streams& streams() {
+Streams make_set() {
+    Streams a;
+    int lo = 0, hi = 0;
+    check(cudaDeviceGetStreamPriorityRange(&lo, &hi), "priority range");
+    check(cudaStreamCreateWithPriority(&a.hi, cudaStreamNonBlocking, hi), "cudaStreamCreate");
+    check(cudaStreamCreateWithPriority(&a.sp, cudaStreamNonBlocking, hi), "cudaStreamCreate");
+    check(cudaStreamCreateWithPriority(&a.lo, cudaStreamNonBlocking, lo), "cudaStreamCreate");
+    return a;
+}
+Streams streams(cudaStream_t user) {
     int dev = 0;
     check(cudaGetDevice(&dev), "cudaGetDevice");
     std::lock_guard<std::mutex> lk(g_aux_mu);
-    Streams& a = g_streams[dev & 63];
-    if (!a.hi) {
-        int lo = 0, hi = 0;
-        check(cudaDeviceGetStreamPriorityRange(&lo, &hi), "priority range");
-        check(cudaStreamCreateWithPriority(&a.hi, cudaStreamNonBlocking, hi), "cudaStreamCreate");
-        check(cudaStreamCreateWithPriority(&a.sp, cudaStreamNonBlocking, hi), "cudaStreamCreate");
-        check(cudaStreamCreateWithPriority(&a.lo, cudaStreamNonBlocking, lo), "cudaStreamCreate");
+    size_t same_dev = 0;
+    for (auto& e : g_sets) {
+        if (e.dev != dev) continue;
+        if (e.user == user) return e.set;
+        same_dev++;
     }
-    return a;
+    if (same_dev >= 256) {                       // share: pick by the stream handle
+        size_t pick = (size_t)(((uintptr_t)user >> 4) % same_dev), q = 0;
+        for (auto& e : g_sets)
+            if (e.dev == dev && q++ == pick) return e.set;
+    }
+    g_sets.push_back({dev, user, make_set()});
+    return g_sets.back().set;
 }
 cudaEvent_t new_event() {
     cudaEvent_t e = nullptr;
@@ -246,55 +269,123 @@ fp_status vc_pp_export(const fp_pp* pp, uint8_t* out, size_t cap, size_t* len) {
     });
 }
 
+}  // extern "C"
+
+namespace {
+// enqueues VC.Commit on s; the range-check word stays in cm->err and cm->done marks completion
+fp_commit* commit_enqueue(const fp_pp* pp, const uint64_t* m, int on_device, cudaStream_t s) {
+    const uint32_t R = pp->R, M = pp->M;
+    const uint64_t N = (uint64_t)R * M;
+    fp_commit* cm = new fp_commit{pp};
+    cm->stream = s;
+    void *src = nullptr, *t1 = nullptr, *ml = nullptr, *ml2 = nullptr;
+    try {
+        cm->m_canon = dalloc(N * FR_BYTES, s);
+        cm->m_mont = dalloc(N * FR_BYTES, s);
+        cm->rows = dalloc(R * G1A_BYTES, s);
+        cm->rows_ser = dalloc(R * G1_SER, s);
+        cm->C = dalloc(FQ12_BYTES, s);
+        cm->C_ser = dalloc(GT_SER, s);
+        cm->err = (uint32_t*)dalloc(sizeof(uint32_t), s);
+        check(cudaEventCreateWithFlags(&cm->done, cudaEventDisableTiming), "cudaEventCreate");
+        check(cudaMemsetAsync(cm->err, 0, sizeof(uint32_t), s), "memset");
+        const void* msrc = m;
+        if (!on_device) {
+            src = dalloc(N * FR_BYTES, s);
+            check(cudaMemcpyAsync(src, m, N * FR_BYTES, cudaMemcpyHostToDevice, s), "H2D m");
+            msrc = src;
+        }
+        load_vector(msrc, N, cm->m_canon, cm->m_mont, cm->err, s);
+        // C_j = sum_a m[jM + a] Lambda_{l_c}[a]: R MSMs of M terms over the shared bases
+        const MsmShape sh = msm_shape(M, R, M, fp_msm_window(M, R));
+        t1 = dalloc(msm_scratch_bytes(sh), s);
+        msm_g1(pp->lam_tab, cm->m_canon, sh, t1, cm->rows, cm->rows_ser, s);
+        // C = prod_j e(C_j, v_j): R Miller loops, pairwise products, one final exponentiation
+        ml = dalloc(R * FQ12_BYTES, s);
+        ml2 = dalloc((R / 2 + 1) * FQ12_BYTES, s);
+        commit_miller(cm->rows, pp->g2pow, R, ml, s);
+        void* prod = reduce_pairs(ml, ml2, R, 1, fq12_pair_reduce, s);
+        final_exp_group(prod, 1, cm->C, cm->C_ser, 1, GT_SER, 0, s);
+        check_launch("vc_commit kernels");
+        dfree(src, s); dfree(t1, s); dfree(ml, s); dfree(ml2, s);
+        check(cudaEventRecord(cm->done, s), "event");
+    } catch (...) {
+        cudaStreamSynchronize(s);
+        dfree(src, s); dfree(t1, s); dfree(ml, s); dfree(ml2, s);
+        fp_commit_free(cm);
+        throw;
+    }
+    return cm;
+}
+
+fp_status commit_status(const fp_commit* cm) {
+    uint32_t herr = 0;
+    check(cudaEventSynchronize(cm->done), "vc_commit");
+    check(cudaMemcpy(&herr, cm->err, sizeof herr, cudaMemcpyDeviceToHost), "D2H err");
+    return herr ? FP_ERANGE : FP_OK;
+}
+}  // namespace
+
+extern "C" {
+
 fp_status vc_commit(const fp_pp* pp, const uint64_t* m, int on_device, void* stream, fp_commit** out) {
     if (!pp || !m || !out) return FP_EINVAL;
-    cudaStream_t s = (cudaStream_t)stream;
     return guarded([&]() -> fp_status {
-        const uint32_t R = pp->R, M = pp->M;
-        const uint64_t N = (uint64_t)R * M;
-        fp_commit* cm = new fp_commit{pp};
-        cm->stream = s;
-        void *src = nullptr, *t1 = nullptr, *t2 = nullptr, *ml = nullptr, *ml2 = nullptr;
-        uint32_t* err = nullptr;
+        fp_commit* cm = commit_enqueue(pp, m, on_device, (cudaStream_t)stream);
+        fp_status st;
         try {
-            cm->m_canon = dalloc(N * FR_BYTES, s);
-            cm->m_mont = dalloc(N * FR_BYTES, s);
-            cm->rows = dalloc(R * G1A_BYTES, s);
-            cm->rows_ser = dalloc(R * G1_SER, s);
-            cm->C = dalloc(FQ12_BYTES, s);
-            cm->C_ser = dalloc(GT_SER, s);
-            err = (uint32_t*)dalloc(sizeof(uint32_t), s);
-            check(cudaMemsetAsync(err, 0, sizeof(uint32_t), s), "memset");
-            const void* msrc = m;
-            if (!on_device) {
-                src = dalloc(N * FR_BYTES, s);
-                check(cudaMemcpyAsync(src, m, N * FR_BYTES, cudaMemcpyHostToDevice, s), "H2D m");
-                msrc = src;
-            }
-            load_vector(msrc, N, cm->m_canon, cm->m_mont, err, s);
-            // C_j = sum_a m[jM + a] Lambda_{l_c}[a]: R MSMs of M terms over the shared bases
-            const MsmShape sh = msm_shape(M, R, M, fp_msm_window(M, R));
-            t1 = dalloc(msm_scratch_bytes(sh), s);
-            msm_g1(pp->lam_tab, cm->m_canon, sh, t1, cm->rows, cm->rows_ser, s);
-            // C = prod_j e(C_j, v_j): R Miller loops, pairwise products, one final exponentiation
-            ml = dalloc(R * FQ12_BYTES, s);
-            ml2 = dalloc((R / 2 + 1) * FQ12_BYTES, s);
-            commit_miller(cm->rows, pp->g2pow, R, ml, s);
-            void* prod = reduce_pairs(ml, ml2, R, 1, fq12_pair_reduce, s);
-            final_exp_group(prod, 1, cm->C, cm->C_ser, 1, GT_SER, 0, s);
-            check_launch("vc_commit kernels");
-            uint32_t herr = 0;
-            check(cudaMemcpyAsync(&herr, err, sizeof herr, cudaMemcpyDeviceToHost, s), "D2H err");
-            dfree(src, s); dfree(t1, s); dfree(t2, s); dfree(ml, s); dfree(ml2, s);
-            void* e = err; dfree(e, s);
-            check(cudaStreamSynchronize(s), "vc_commit");
-            if (herr) { fp_commit_free(cm); return FP_ERANGE; }
+            st = commit_status(cm);
         } catch (...) {
-            cudaStreamSynchronize(s);
             fp_commit_free(cm);
             throw;
         }
+        if (st != FP_OK) {
+            fp_commit_free(cm);
+            return st;
+        }
         *out = cm;
+        return FP_OK;
+    });
+}
+
+fp_status vc_commit_async(const fp_pp* pp, const uint64_t* m, int on_device, void* stream, fp_commit** out) {
+    if (!pp || !m || !out) return FP_EINVAL;
+    return guarded([&]() -> fp_status {
+        *out = commit_enqueue(pp, m, on_device, (cudaStream_t)stream);
+        return FP_OK;
+    });
+}
+
+fp_status vc_commit_status(const fp_commit* cm) {
+    if (!cm) return FP_EINVAL;
+    return guarded([&]() -> fp_status { return commit_status(cm); });
+}
+
+fp_status vc_pp_view(const fp_pp* pp, uint32_t log_n, fp_pp** out) {
+    if (!pp || !out || log_n < 2 || log_n > pp->log_n) return FP_EINVAL;
+    const fp_pp* root = pp->parent ? pp->parent : pp;
+    return guarded([&]() -> fp_status {
+        const uint32_t log_r = log_n / 2, log_c = log_n - log_r, R = 1u << log_r, M = 1u << log_c;
+        fp_pp* v = new fp_pp{log_n, log_r, log_c, R, M};
+        v->parent = root;
+        v->lam = root->lam;                 // Lambda_t for t <= l_c are the same prefix levels
+        v->g1beta = root->g1beta;
+        v->g2pow = root->g2pow;             // g2^{beta^i}, i < 2R - 1: a prefix
+        v->g2tau = root->g2tau;             // tau_0 .. tau_{l_c - 1}: a prefix
+        cudaStream_t s = 0;
+        try {
+            v->lam_tab = dalloc(2 * (size_t)M * G1A_BYTES, s);
+            check(cudaMemcpyAsync(v->lam_tab, (uint8_t*)root->lam + ((size_t)M - 1) * G1A_BYTES, (size_t)M * G1A_BYTES,
+                                  cudaMemcpyDeviceToDevice, s), "D2D");
+            msm_bases_endo(v->lam_tab, M, s);
+            check_launch("vc_pp_view");
+            check(cudaStreamSynchronize(s), "vc_pp_view");
+        } catch (...) {
+            cudaStreamSynchronize(s);
+            fp_pp_free(v);
+            throw;
+        }
+        *out = v;
         return FP_OK;
     });
 }
@@ -310,24 +401,31 @@ fp_status vc_commit_get(const fp_commit* cm, uint8_t* gt576, uint8_t* rows) {
     });
 }
 
-fp_status vc_prove_all(const fp_pp* pp, const fp_commit* cm, uint32_t b, void* stream, fp_proofs** out) {
-    if (!pp || !cm || !out || cm->pp != pp) return FP_EINVAL;
+}  // extern "C"
+
+namespace {
+// OpenAll's work with Step 1 restricted to the blocks [k0, k0 + Kc) (all blocks: k0 = 0, Kc = K):
+// their records are written at their places in the K-block array; Step 2 runs in full.
+fp_proofs* prove_impl(const fp_pp* pp, const fp_commit* cm, uint32_t b, uint32_t k0, uint32_t Kc, cudaStream_t s,
+                      bool track_use = true) {
     const uint32_t R = pp->R, M = pp->M;
-    if (b < 1 || b > R) return FP_EINVAL;
-    cudaStream_t s = (cudaStream_t)stream;
-    return guarded([&]() -> fp_status {
+    {
         const int lr = (int)pp->log_r, lc = (int)pp->log_c;
         const uint32_t K = (R + b - 1) / b;
         fp_proofs* pf = new fp_proofs{pp};
         pf->stream = s;
         pf->L = ProofLayout{R, M, b, K, (int)pp->log_n, lr, lc, bopen_len(pp->log_r)};
         const size_t blen = pf->L.bopen_len;
+        uint8_t* blocks1 = nullptr;
         std::vector<void*> tmp;
         auto T = [&](size_t bytes) { void* p = dalloc(bytes, s); tmp.push_back(p); return p; };
         try {
+            // the commitment may have been made on another stream: order after it
+            if (track_use && cm->done) check(cudaStreamWaitEvent(s, cm->done, 0), "wait");
             pf->rows_ser = dalloc(R * G1_SER, s);
             check(cudaMemcpyAsync(pf->rows_ser, cm->rows_ser, R * G1_SER, cudaMemcpyDeviceToDevice, s), "D2D");
             pf->blocks = dalloc(K * blen, s);
+            blocks1 = (uint8_t*)pf->blocks + (size_t)k0 * blen;
             // Step 2 depends only on the commitment: it runs on a second stream, concurrently with Step 1
             pf->row_tree = dalloc((size_t)R * (2 * M - 1) * DIGEST, s);
             pf->top_tree = dalloc((2 * (size_t)R - 1) * DIGEST, s);
@@ -340,24 +438,24 @@ fp_status vc_prove_all(const fp_pp* pp, const fp_commit* cm, uint32_t b, void* s
             void* pt = T((size_t)lc * half * G1J_BYTES);
             void* pt2 = T((half / 2 + 1) * G1J_BYTES);
             // every buffer is allocated (stream-ordered on s) before the fork to the internal streams
-            const uint64_t KR = (uint64_t)K * R;
+            const uint64_t KR = (uint64_t)Kc * R;
             void* A = T(KR * G1A_BYTES);
             void* v = T(KR * G2A_BYTES);
             void* bvec = T(KR * FR_BYTES);
-            void* hstmt = T(K * DIGEST);
-            void* xprev = T(K * 32);
-            void* x_mont = T(K * FR_BYTES);
-            void* xinv_mont = T(K * FR_BYTES);
-            void* xinv_all = T((size_t)K * lr * FR_BYTES);
+            void* hstmt = T(Kc * DIGEST);
+            void* xprev = T(Kc * 32);
+            void* x_mont = T(Kc * FR_BYTES);
+            void* xinv_mont = T(Kc * FR_BYTES);
+            void* xinv_all = T((size_t)Kc * lr * FR_BYTES);
             void* ml = T(KR * FQ12_BYTES);
             void* ml2 = T((KR / 2 + 1) * FQ12_BYTES);
             void* sp = T(KR * G1J_BYTES);
             void* sp2 = T((KR / 2 + 1) * G1J_BYTES);
-            void* pcoef = T((size_t)K * (2 * R - 1) * FR_BYTES);
-            void* q = T((size_t)K * 2 * R * FR_BYTES);
-            void* wt = T((size_t)K * 2 * R * G2J_BYTES);
-            void* wt2 = T(((size_t)K * R + 1) * G2J_BYTES);
-            Streams& st = streams();
+            void* pcoef = T((size_t)Kc * (2 * R - 1) * FR_BYTES);
+            void* q = T((size_t)Kc * 2 * R * FR_BYTES);
+            void* wt = T((size_t)Kc * 2 * R * G2J_BYTES);
+            void* wt2 = T(((size_t)Kc * R + 1) * G2J_BYTES);
+            const Streams st = streams(s);
             cudaStream_t s2 = st.lo, s1 = st.hi, s3 = st.sp;
             cudaEvent_t ev_fork = new_event(), ev_join = new_event(), ev_join1 = new_event();
             check(cudaEventRecord(ev_fork, s), "event");
@@ -391,28 +489,28 @@ fp_status vc_prove_all(const fp_pp* pp, const fp_commit* cm, uint32_t b, void* s
             // round chain on s1; each round's sparse G1 terms on s3, overlapping its Miller loops and
             // final exponentiations, joined before the challenge
             cudaEvent_t ev_folded = new_event(), ev_sparse = new_event();
-            step1_init(cm->rows, pp->g2pow, K, R, A, v, bvec, s1);
-            step1_stmt_hash(cm->C_ser, cm->rows_ser, K, R, b, hstmt, s1);
-            step1_block_r(hstmt, K, R, b, bvec, s1);
+            step1_init(cm->rows, pp->g2pow, Kc, R, A, v, bvec, s1);
+            step1_stmt_hash(cm->C_ser, cm->rows_ser, k0, Kc, R, b, hstmt, s1);
+            step1_block_r(hstmt, k0, Kc, R, b, bvec, s1);
             for (int j = 1; j <= lr; j++) {
                 const uint32_t h = R >> j;
                 check(cudaEventRecord(ev_folded, s1), "event");
                 check(cudaStreamWaitEvent(s3, ev_folded, 0), "wait");
-                step1_sparse_terms(A, bvec, K, R, h, sp, s3);
-                void* spr = reduce_pairs(sp, sp2, (uint64_t)K * 2 * h, (uint64_t)K * 2, g1_pair_reduce, s3);
-                step1_g1_out(spr, K, j, pf->blocks, blen, s3);
+                step1_sparse_terms(A, bvec, Kc, R, h, sp, s3);
+                void* spr = reduce_pairs(sp, sp2, (uint64_t)Kc * 2 * h, (uint64_t)Kc * 2, g1_pair_reduce, s3);
+                step1_g1_out(spr, Kc, j, blocks1, blen, s3);
                 check(cudaEventRecord(ev_sparse, s3), "event");
-                step1_miller_g(A, v, K, R, h, ml, s1);
-                void* mlr = reduce_pairs(ml, ml2, (uint64_t)K * 2 * h, (uint64_t)K * 2, fq12_pair_reduce, s1);
-                step1_gt_out(mlr, K, j, pf->blocks, blen, s1);
+                step1_miller_g(A, v, Kc, R, h, ml, s1);
+                void* mlr = reduce_pairs(ml, ml2, (uint64_t)Kc * 2 * h, (uint64_t)Kc * 2, fq12_pair_reduce, s1);
+                step1_gt_out(mlr, Kc, j, blocks1, blen, s1);
                 check(cudaStreamWaitEvent(s1, ev_sparse, 0), "wait");
-                step1_challenge(pf->blocks, blen, K, j, xprev, x_mont, xinv_mont, xinv_all, lr, s1);
-                step1_fold(A, v, bvec, x_mont, xinv_mont, K, R, h, s1);
+                step1_challenge(blocks1, blen, Kc, j, xprev, x_mont, xinv_mont, xinv_all, lr, s1);
+                step1_fold(A, v, bvec, x_mont, xinv_mont, Kc, R, h, s1);
             }
-            step1_kzg(A, v, xprev, xinv_all, K, R, lr, pf->blocks, blen, pcoef, q, s1);
-            step1_w_terms(pp->g2pow, q, K, R, wt, s1);
-            void* wr = reduce_pairs(wt, wt2, (uint64_t)K * 2 * R, K, g2_pair_reduce, s1);
-            g2j_to_affine(wr, nullptr, (uint8_t*)pf->blocks + (size_t)lr * ROUND_BYTES + G1_SER + G2_SER, blen, K, s1);
+            step1_kzg(A, v, xprev, xinv_all, Kc, R, lr, blocks1, blen, pcoef, q, s1);
+            step1_w_terms(pp->g2pow, q, Kc, R, wt, s1);
+            void* wr = reduce_pairs(wt, wt2, (uint64_t)Kc * 2 * R, Kc, g2_pair_reduce, s1);
+            g2j_to_affine(wr, nullptr, (uint8_t*)blocks1 + (size_t)lr * ROUND_BYTES + G1_SER + G2_SER, blen, Kc, s1);
             check(cudaEventRecord(ev_join1, s1), "event");
             check(cudaStreamWaitEvent(s, ev_join1, 0), "join");
             cudaEventDestroy(ev_folded);
@@ -422,6 +520,12 @@ fp_status vc_prove_all(const fp_pp* pp, const fp_commit* cm, uint32_t b, void* s
             check(cudaStreamWaitEvent(s, ev_join, 0), "join");
             cudaEventDestroy(ev_fork);
             cudaEventDestroy(ev_join);
+            if (track_use) {
+                cudaEvent_t used = new_event();
+                check(cudaEventRecord(used, s), "event");
+                std::lock_guard<std::mutex> lk(cm->mu);
+                cm->uses.push_back(used);
+            }
             check_launch("step 2 kernels");
             for (void* p : tmp) cudaFreeAsync(p, s);
             tmp.clear();
@@ -431,8 +535,138 @@ fp_status vc_prove_all(const fp_pp* pp, const fp_commit* cm, uint32_t b, void* s
             fp_proofs_free(pf);
             throw;
         }
-        *out = pf;
+        return pf;
+    }
+}
+}  // namespace
+
+extern "C" {
+
+fp_status vc_prove_all(const fp_pp* pp, const fp_commit* cm, uint32_t b, void* stream, fp_proofs** out) {
+    if (!pp || !cm || !out || cm->pp != pp) return FP_EINVAL;
+    if (b < 1 || b > pp->R) return FP_EINVAL;
+    return guarded([&]() -> fp_status {
+        *out = prove_impl(pp, cm, b, 0, (pp->R + b - 1) / b, (cudaStream_t)stream);
         return FP_OK;
+    });
+}
+
+}  // extern "C"
+
+namespace {
+// library-owned streams for the jobs of a batch (0 .. 63) and a graph-capture origin (64), per
+// device, created on first use
+std::vector<std::pair<int, cudaStream_t>> g_job_streams;
+cudaStream_t job_stream(uint32_t j) {
+    int dev = 0;
+    check(cudaGetDevice(&dev), "cudaGetDevice");
+    std::lock_guard<std::mutex> lk(g_aux_mu);
+    uint32_t have = 0;
+    for (auto& e : g_job_streams)
+        if (e.first == dev && have++ == j % 65) return e.second;
+    while (have <= j % 65) {
+        cudaStream_t st;
+        check(cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking), "cudaStreamCreate");
+        g_job_streams.push_back({dev, st});
+        if (have++ == j % 65) return st;
+    }
+    return nullptr;
+}
+}  // namespace
+
+extern "C" {
+
+fp_status vc_prove_all_batch(uint32_t njobs, const fp_job* jobs, int use_graph, void* stream, fp_proofs** outs) {
+    if (!jobs || !outs) return njobs ? FP_EINVAL : FP_OK;
+    for (uint32_t j = 0; j < njobs; j++) {
+        const fp_commit* cm = jobs[j].cm;
+        if (!cm || jobs[j].b < 1 || jobs[j].b > cm->pp->R) return FP_EINVAL;
+    }
+    cudaStream_t s = (cudaStream_t)stream;
+    return guarded([&]() -> fp_status {
+        std::vector<fp_proofs*> res(njobs, nullptr);
+        std::vector<cudaStream_t> js(njobs);
+        for (uint32_t j = 0; j < njobs; j++) js[j] = job_stream(j % 64);
+        for (uint32_t j = 0; j < njobs; j++) (void)streams(js[j]);    // internal sets exist before capture
+        bool capturing = false;
+        cudaGraph_t graph = nullptr;
+        cudaGraphExec_t exec = nullptr;
+        const cudaStream_t launch = s;
+        if (use_graph) s = job_stream(64);            // capture origin: a library stream (the legacy
+                                                      // default stream cannot be captured)
+        try {
+            if (use_graph) {
+                check(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal), "cudaStreamBeginCapture");
+                capturing = true;
+            }
+            cudaEvent_t fork = new_event();
+            check(cudaEventRecord(fork, s), "event");
+            for (uint32_t j = 0; j < njobs; j++) check(cudaStreamWaitEvent(js[j], fork, 0), "wait");
+            for (uint32_t j = 0; j < njobs; j++) {
+                const fp_commit* cm = jobs[j].cm;
+                const uint32_t K = (cm->pp->R + jobs[j].b - 1) / jobs[j].b;
+                res[j] = prove_impl(cm->pp, cm, jobs[j].b, 0, K, js[j], !use_graph);
+            }
+            for (uint32_t j = 0; j < njobs; j++) {
+                cudaEvent_t e = new_event();
+                check(cudaEventRecord(e, js[j]), "event");
+                check(cudaStreamWaitEvent(s, e, 0), "join");
+                cudaEventDestroy(e);
+            }
+            cudaEventDestroy(fork);
+            if (use_graph) {
+                capturing = false;
+                check(cudaStreamEndCapture(s, &graph), "cudaStreamEndCapture");
+                check(cudaGraphInstantiate(&exec, graph, 0), "cudaGraphInstantiate");
+                s = launch;
+                for (uint32_t j = 0; j < njobs; j++)
+                    if (jobs[j].cm->done) check(cudaStreamWaitEvent(s, jobs[j].cm->done, 0), "wait");
+                check(cudaGraphLaunch(exec, s), "cudaGraphLaunch");
+                check(cudaStreamSynchronize(s), "vc_prove_all_batch");
+                cudaGraphExecDestroy(exec);
+                cudaGraphDestroy(graph);
+                exec = nullptr;
+                graph = nullptr;
+                for (uint32_t j = 0; j < njobs; j++) {       // uses of the commitments, after the graph
+                    const fp_commit* cm = jobs[j].cm;
+                    cudaEvent_t used = new_event();
+                    check(cudaEventRecord(used, s), "event");
+                    std::lock_guard<std::mutex> lk(cm->mu);
+                    cm->uses.push_back(used);
+                }
+                for (uint32_t j = 0; j < njobs; j++) res[j]->stream = s;
+            }
+        } catch (...) {
+            if (capturing) {
+                cudaGraph_t g = nullptr;
+                cudaStreamEndCapture(s, &g);
+                if (g) cudaGraphDestroy(g);
+            }
+            if (exec) cudaGraphExecDestroy(exec);
+            if (graph) cudaGraphDestroy(graph);
+            cudaStreamSynchronize(s);
+            for (fp_proofs* p : res) fp_proofs_free(p);
+            throw;
+        }
+        for (uint32_t j = 0; j < njobs; j++) outs[j] = res[j];
+        return FP_OK;
+    });
+}
+
+fp_status vc_prove_one(const fp_pp* pp, const fp_commit* cm, uint32_t b, uint64_t i, void* stream, uint8_t* out,
+                       size_t cap, size_t* len) {
+    if (!pp || !cm || !len || cm->pp != pp) return FP_EINVAL;
+    if (b < 1 || b > pp->R || i >= (uint64_t)pp->R * pp->M) return FP_EINVAL;
+    const size_t need = vc_proof_len(pp, b, i);
+    *len = need;
+    if (!out) return FP_OK;
+    if (cap < need) return FP_EINVAL;
+    return guarded([&]() -> fp_status {
+        const uint32_t k = (uint32_t)(i / pp->M) / b;
+        fp_proofs* pf = prove_impl(pp, cm, b, k, 1, (cudaStream_t)stream);
+        const fp_status st = vc_proof_get(pf, i, out, cap, len);
+        fp_proofs_free(pf);
+        return st;
     });
 }
 
@@ -718,21 +952,42 @@ void fp_g1_bases_free(fp_g1_bases* P) {
 void fp_pp_free(fp_pp* pp) {
     if (!pp) return;
     cudaDeviceSynchronize();
-    cudaFree(pp->lam); cudaFree(pp->lam_tab); cudaFree(pp->g1beta); cudaFree(pp->g2pow); cudaFree(pp->g2tau);
+    cudaFree(pp->lam_tab);
+    if (!pp->parent) {
+        cudaFree(pp->lam); cudaFree(pp->g1beta); cudaFree(pp->g2pow); cudaFree(pp->g2tau);
+    }
     delete pp;
 }
 void fp_commit_free(fp_commit* cm) {
     if (!cm) return;
-    cudaDeviceSynchronize();
-    cudaFree(cm->m_canon); cudaFree(cm->m_mont); cudaFree(cm->rows); cudaFree(cm->rows_ser);
-    cudaFree(cm->C); cudaFree(cm->C_ser);
+    // stream-ordered release on an internal stream, after the commit's own work and every
+    // recorded use of the handle
+    cudaStream_t fs = nullptr;
+    try {
+        fs = streams(cm->stream).lo;
+    } catch (...) {
+        fs = nullptr;
+    }
+    if (!fs) {
+        cudaDeviceSynchronize();
+    } else {
+        if (cm->done) cudaStreamWaitEvent(fs, cm->done, 0);
+        std::lock_guard<std::mutex> lk(cm->mu);
+        for (cudaEvent_t e : cm->uses) cudaStreamWaitEvent(fs, e, 0);
+    }
+    for (void* p : {cm->m_canon, cm->m_mont, cm->rows, cm->rows_ser, cm->C, cm->C_ser, (void*)cm->err})
+        if (p) cudaFreeAsync(p, fs);
+    if (cm->done) cudaEventDestroy(cm->done);
+    for (cudaEvent_t e : cm->uses) cudaEventDestroy(e);
     delete cm;
 }
 void fp_proofs_free(fp_proofs* pf) {
     if (!pf) return;
-    cudaDeviceSynchronize();
-    cudaFree(pf->rows_ser); cudaFree(pf->blocks); cudaFree(pf->row_tree); cudaFree(pf->top_tree);
-    cudaFree(pf->rj); cudaFree(pf->g); cudaFree(pf->D); cudaFree(pf->D_ser); cudaFree(pf->pst_ser);
+    // every use of the handle is ordered on its stream (creation joins back to it, getters
+    // synchronise it): release stream-ordered there
+    for (void* p : {pf->rows_ser, pf->blocks, pf->row_tree, pf->top_tree, pf->rj, pf->g, pf->D, pf->D_ser,
+                    pf->pst_ser})
+        if (p) cudaFreeAsync(p, pf->stream);
     delete pf;
 }
 

@@ -185,3 +185,32 @@ def test_n16_prove_all_sampled(b, blocks):
             e = pr.proof(i)
             assert pf.proof(i) == e
             assert O.verify(opp, C, b, i, vals[i], e)
+
+
+@pytest.mark.parametrize("log_n,b", [(4, 1), (5, 3), (6, 8)])
+def test_prove_one_equals_oracle_brute_force_and_prove_all(log_n, b):
+    """vc_prove_one (Step 1 on the index's block only) against the oracle's brute-force
+    single-index prover and against vc_prove_all's proof, for every index of a ragged layout."""
+    seed = 9
+    pp, opp = gpu_pp(log_n, seed), oracle_pp(log_n, seed)
+    m = vec(log_n, seed + 1)
+    cm = F.Commitment(pp, m)
+    C, rows = cm.get()
+    pf = F.Proofs(pp, cm, b)
+    for i in range(pp.N):
+        one = F.vc_prove_one(pp, cm, b, i)
+        assert one == pf.proof(i), i
+        if i % 5 == 0:
+            assert one == O.prove_one(opp, m.tobytes(), C, rows, b, i), i
+
+
+def test_prove_one_n16_sampled():
+    pp, opp, m, cm = n16("uniform")
+    C, rows = cm.get()
+    vals = I.to_ints(m)
+    for b, i in ((256, 12345), (1, 65535), (16, 40000)):
+        one = F.vc_prove_one(pp, cm, b, i)
+        assert one == O.prove_one(opp, m.tobytes(), C, rows, b, i)
+        assert O.verify(opp, C, b, i, vals[i], one)
+    with pytest.raises(F.FlexProofsError):
+        F.vc_prove_one(pp, cm, 1, pp.N)
