@@ -23,6 +23,9 @@ import time
 
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
+# more hardware queues than the default 8, so that concurrent job streams overlap (batched and
+# served workloads); must be set before the CUDA context exists
+os.environ.setdefault("CUDA_DEVICE_MAX_CONNECTIONS", "32")
 
 # Fq multiplications per unit operation, from the operation counts of efficient textbook formulas
 # (an Fq multiplication is one 12-limb CIOS Montgomery product = 4 * 12^2 = 576 32-bit
@@ -126,6 +129,9 @@ def parse():
     ap.add_argument("--no-sweeps", action="store_true", help="skip the N=2^20 b sweep and the MSM sweep")
     ap.add_argument("--msm-sweep", default="12,14,16,18,20,22,24", help="log2 sizes of the MSM sweep")
     ap.add_argument("--b-sweep", default="1,16,256,1024", help="b values of the N=2^20 ProveAll sweep")
+    ap.add_argument("--served-requests", type=int, default=100, help="requests of the served trace replayed")
+    ap.add_argument("--msm-only", type=int, default=0, metavar="LOG_N",
+                    help="time only the standalone G1 MSM of 2^LOG_N points (profiling runs)")
     return ap.parse_args()
 
 
@@ -165,6 +171,96 @@ def proveall_sweep(F, I, torch, np, stream, flush, b_values, seed: int) -> dict:
         ms = time_device(step, stream, 3, 3, flush)
         out[f"b={b}"] = {"proofs_per_s": (1 << log_n) / (ms * 1e-3), "ms_per_step": ms}
     return out
+
+
+def batched_workload(F, I, torch, np) -> dict:
+    """64 jobs, log N uniform in 8..18 by seed, b = min(R, nearestpow2(log^2 N)), one SRS for 2^18
+    resident: one vc_prove_all_batch captured as a CUDA graph vs the same jobs as concurrent job
+    streams vs 64 sequential vc_prove_all calls.  Commitments are made beforehand (not timed)."""
+    spec = I.batched_jobs(4, 64, 8, 18)
+    parent = F.PP(18, 1, 4)
+    views, cms = {}, []
+    for sp in spec:
+        ln = sp["log_n"]
+        if ln not in views:
+            views[ln] = parent.view(ln)
+        cms.append(F.Commitment(views[ln], I.vector(sp["seed"], ln)))
+    jobs = [(cm, sp["b"]) for cm, sp in zip(cms, spec)]
+    total = sum(cm.pp.N for cm, _ in jobs)
+    s = torch.cuda.current_stream()
+
+    def run(fn, reps, warm):
+        for _ in range(warm):
+            r = fn()
+            torch.cuda.synchronize()
+            del r
+        ts = []
+        for _ in range(reps):
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            r = fn()
+            torch.cuda.synchronize()
+            ts.append(time.perf_counter() - t0)
+            del r
+        return min(ts)
+    t_graph = run(lambda: F.vc_prove_all_batch(jobs, use_graph=True, stream=s), 3, 2)
+    t_streams = run(lambda: F.vc_prove_all_batch(jobs, use_graph=False, stream=s), 3, 1)
+    t_seq = run(lambda: [F.Proofs(cm.pp, cm, b, s) for cm, b in jobs], 1, 1)
+    return {"jobs": 64, "log_n": sorted(sp["log_n"] for sp in spec), "total_proofs": total,
+            "timing": "host wall clock around the call, after synchronize, best of runs",
+            "graph": {"ms": t_graph * 1e3, "proofs_per_s": total / t_graph},
+            "streams": {"ms": t_streams * 1e3, "proofs_per_s": total / t_streams},
+            "sequential": {"ms": t_seq * 1e3, "proofs_per_s": total / t_seq}}
+
+
+def served_workload(F, I, torch, np, nreq: int) -> dict:
+    """Poisson trace (seed 5, 200 req/s, log N uniform 10..20, b uniform {1, 16, 256} clamped to R),
+    its first nreq requests replayed in real time through the serving loop; against sequential
+    plain calls on the same trace (each request's measured solo time, queued in arrival order)."""
+    from paper_2601_03031_gb300 import serve as S
+    trace = I.poisson_trace(5, 2000, 200.0, 10, 20, (1, 16, 256))[:nreq]
+    vecs = [I.vector(r["seed"], r["log_n"]) for r in trace]
+    srv = S.Server(log_n_max=20, seed=0, slots=32)
+    for ln in range(10, 21):
+        srv.view(ln)
+    for b in (1, 16):
+        srv.submit(I.vector(1, 10), b).result()
+    t0 = time.perf_counter()
+    futs = []
+    for r, m in zip(trace, vecs):
+        now = time.perf_counter() - t0
+        if r["t"] > now:
+            time.sleep(r["t"] - now)
+        futs.append(srv.submit(m, r["b"], t_arrival=t0 + r["t"]))
+    res = [f.result() for f in futs]
+    span = max(q.t_done for q in res) - t0
+    peak = srv.peak_running
+    srv.close()
+    total = sum(1 << r["log_n"] for r in trace)
+
+    def pct(a, q):
+        a = sorted(a)
+        return a[min(len(a) - 1, int(q * len(a)))]
+    lat = [q.latency for q in res]
+    durs = []
+    for r, m in zip(trace, vecs):
+        pp = srv.view(r["log_n"])
+        torch.cuda.synchronize()
+        a = time.perf_counter()
+        C, rows, state = S.solo(pp, m, r["b"])
+        durs.append(time.perf_counter() - a)
+        if len(durs) % 10 == 1:
+            assert state == res[len(durs) - 1].state, "served result differs from its solo run"
+    fin, seq_lat = 0.0, []
+    for r, d in zip(trace, durs):
+        fin = max(fin, r["t"]) + d
+        seq_lat.append(fin - r["t"])
+    return {"requests": nreq, "trace": "poisson seed 5, 200 req/s, log N 10..20, b in {1,16,256}",
+            "latency": "arrival to proof state in host memory",
+            "served": {"p50_ms": pct(lat, 0.5) * 1e3, "p99_ms": pct(lat, 0.99) * 1e3,
+                       "proofs_per_s": total / span, "span_s": span, "peak_concurrent_jobs": peak},
+            "sequential": {"p50_ms": pct(seq_lat, 0.5) * 1e3, "p99_ms": pct(seq_lat, 0.99) * 1e3,
+                           "proofs_per_s": total / fin, "span_s": fin}}
 
 
 def msm_sweep(F, I, torch, np, stream, flush, logs, seed: int) -> dict:
@@ -292,6 +388,17 @@ def main():
     from paper_2601_03031_gb300 import _lib as F
     from paper_2601_03031_gb300 import inputs as I
 
+    if args.msm_only:
+        stream = torch.cuda.current_stream()
+        flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
+        res = msm_sweep(F, I, torch, np, stream, flush, [args.msm_only], args.seed)
+        if rank == 0:
+            (k, v), = res.items()
+            print(json.dumps({"metric": "MSM Mpts/s", "value": v["mpts_per_s"], "unit": "Mpts/s", "n_gpus": world,
+                              "config": {"workload": f"G1 MSM {k} points, uniform Fr scalars", "window": v["window"]},
+                              "ms": v["ms"]}))
+        return
+
     log_n, b = args.log_n, args.b
     N = 1 << log_n
     stream = torch.cuda.current_stream()
@@ -300,8 +407,10 @@ def main():
     m_dev = torch.from_numpy(m.view(np.int64).copy()).cuda()
     flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")     # > 129 MB L2
 
-    def step():
+    def step(mid=None):
         cm = F.Commitment(pp, m_dev, stream)
+        if mid is not None:
+            mid.record(stream)
         pf = F.Proofs(pp, cm, b, stream)
         return cm, pf
 
@@ -310,6 +419,7 @@ def main():
     torch.cuda.synchronize()
 
     ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    mids = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
     launches0 = F.launch_count()
     F.profile_enable(True)
     F.profile_report()
@@ -321,13 +431,15 @@ def main():
         for s in range(args.steps):
             flush.zero_()
             ev[s][0].record(stream)
-            keep.append(step())
+            keep.append(step(mids[s]))
             ev[s][1].record(stream)
         torch.cuda.synchronize()
     F.profile_enable(False)
     prof = F.profile_report()
     launches = (F.launch_count() - launches0) / max(1, args.steps)
     total_ms = sum(a.elapsed_time(b_) for a, b_ in ev)
+    commit_ms = sum(a.elapsed_time(mid) for (a, _), mid in zip(ev, mids)) / args.steps
+    openall_ms = sum(mid.elapsed_time(b_) for (_, b_), mid in zip(ev, mids)) / args.steps
     if world > 1:
         t = torch.tensor([total_ms], device="cuda")
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
@@ -396,6 +508,8 @@ def main():
                                              [int(x) for x in args.b_sweep.split(",") if x], args.seed),
             "msm_g1": msm_sweep(F, I, torch, np, stream, flush,
                                 [int(x) for x in args.msm_sweep.split(",") if x], args.seed),
+            "batched_64_jobs": batched_workload(F, I, torch, np),
+            "served": served_workload(F, I, torch, np, args.served_requests),
         }
 
     line = {
@@ -407,6 +521,9 @@ def main():
                    "parallelism": f"replicas x{world}", "l2": "flushed (256 MB write) before every timed step"},
         "e2e": {"value": N / e2e_s, "unit": "proofs/s", "h2d_bytes_per_step": N * 32,
                 "d2h_bytes_per_step": int(state.numel())},
+        "phases": {"commit_ms": commit_ms, "openall_ms": openall_ms,
+                   "openall_only_proofs_per_s": N / (openall_ms * 1e-3),
+                   "note": "value counts Commit + OpenAll per step; OpenAll alone is the paper's ProveAll time"},
         "gpu_launches": launches,
         "roofline": roof,
         "kernel_share": share,
