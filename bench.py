@@ -49,12 +49,12 @@ def step_units(log_n: int, b: int, msm_window: int) -> dict:
     hs = [R >> j for j in range(1, lr + 1)]
     W = -(-129 // msm_window)
     return {
-        "k_final_exp_g": ("final_exp", 1 + 2 * K * lr),
-        "k_round_terms_g": ("miller_loop", sum(K * 2 * h for h in hs if K * 2 * h < 16384)),
+        "k_final_exp_w": ("final_exp", 1 + 2 * K * lr),
+        "k_round_miller_w": ("miller_loop", sum(K * 2 * h for h in hs if K * 2 * h < 16384)),
         "k_step1_miller": ("miller_loop", sum(K * 2 * h for h in hs if K * 2 * h >= 16384)),
-        "k_commit_miller_g": ("miller_loop", R),
-        "k_sparse_terms": ("g1_mul", sum(K * min(b, 2 * h) for h in hs)),
-        "k_fold_grp": (("g1_mul", "g2_mul"), sum(K * h for h in hs if K * h <= 4096)),
+        "k_commit_miller_w": ("miller_loop", R),
+        "k_sparse_g": ("g1_mul", sum(K * min(b, 2 * h) for h in hs)),
+        "k_fold_w": (("g1_mul", "g2_mul"), sum(K * h for h in hs if K * h <= 4096)),
         "k_fold": (("g1_mul", "g2_mul"), sum(K * h for h in hs if K * h > 4096)),
         "k_msm_bucket": ("msm_madd", 2 * R * M * W),
         "k_w_terms": ("g2_mul", K * (2 * R - 2)),

@@ -209,3 +209,152 @@ template <typename F>
 FPG_DEV GPt<F> gec_from_affine_or_inf(const F& x, const F& y) {
     return (f_is_zero(x) && f_is_zero(y)) ? gec_identity<F>() : gec_from_affine(x, y);
 }
+
+// ---------------------------------------------------------------------------------------
+// G2 on one warp: the same complete formulas, but each of a phase's six Fq2 products is split
+// into its three Karatsuba Fq products (m0 = a0 b0, m1 = a1 b1, m2 = (a0 + a1)(b0 + b1)), one per
+// lane 0..17, so a phase costs one Fq product instead of three.  Lanes 0..11 then form the six
+// Fq2 results (re = m0 - m1, im = m2 - m0 - m1) and every lane continues with the same linear
+// combinations.
+// ---------------------------------------------------------------------------------------
+struct GEcW {
+    fq2 sc[8];
+    fq p[18];
+    GPt<fq2> tab[16];
+};
+
+// operands of product q = L / 3 come from sel(q, a, b); lane L computes component L % 3
+template <typename Sel>
+FPG_DEV void gecw_phase(GEcW& sm, int L, Sel&& sel) {
+    if (L < 18) {
+        const int q = L / 3, kind = L - 3 * q;
+        fq2 a, b;
+        sel(q, a, b);
+        fq zero;
+        fq_zero(zero);
+        const fq x = fq_add(kind == 1 ? a.c1 : a.c0, kind == 2 ? a.c1 : zero);
+        const fq y = fq_add(kind == 1 ? b.c1 : b.c0, kind == 2 ? b.c1 : zero);
+        sm.p[L] = fq_mul(x, y);
+    }
+    __syncwarp();
+    fq r;
+    if (L < 12) {
+        const fq* m = &sm.p[3 * (L >> 1)];
+        r = (L & 1) ? fq_sub(m[2], fq_add(m[0], m[1])) : fq_sub(m[0], m[1]);
+    }
+    __syncwarp();
+    if (L < 12) {
+        fq* c = &sm.sc[L >> 1].c0;
+        c[L & 1] = r;
+    }
+    __syncwarp();
+}
+
+// P + Q, complete (RCB16 Algorithm 7, a = 0), on one warp
+FPG_NOINL GPt<fq2> gecw_add(GEcW& sm, int L, const GPt<fq2>& P, const GPt<fq2>& Q) {
+    gecw_phase(sm, L, [&](int q, fq2& a, fq2& b) {
+        switch (q) {
+            case 0: a = P.X; b = Q.X; break;
+            case 1: a = P.Y; b = Q.Y; break;
+            case 2: a = P.Z; b = Q.Z; break;
+            case 3: a = f_add(P.X, P.Y); b = f_add(Q.X, Q.Y); break;
+            case 4: a = f_add(P.Y, P.Z); b = f_add(Q.Y, Q.Z); break;
+            default: a = f_add(P.X, P.Z); b = f_add(Q.X, Q.Z); break;
+        }
+    });
+    const fq2 t0 = sm.sc[0], t1 = sm.sc[1], t2 = sm.sc[2];
+    const fq2 t3 = f_sub(sm.sc[3], f_add(t0, t1));
+    const fq2 t4 = f_sub(sm.sc[4], f_add(t1, t2));
+    const fq2 y3 = f_b3(f_sub(sm.sc[5], f_add(t0, t2)));
+    const fq2 x3 = f_add(f_dbl(t0), t0);
+    const fq2 bt2 = f_b3(t2);
+    const fq2 z3 = f_add(t1, bt2);
+    const fq2 u1 = f_sub(t1, bt2);
+    gecw_phase(sm, L, [&](int q, fq2& a, fq2& b) {
+        switch (q) {
+            case 0: a = t4; b = y3; break;
+            case 1: a = t3; b = u1; break;
+            case 2: a = y3; b = x3; break;
+            case 3: a = u1; b = z3; break;
+            case 4: a = x3; b = t3; break;
+            default: a = z3; b = t4; break;
+        }
+    });
+    GPt<fq2> r;
+    r.X = f_sub(sm.sc[1], sm.sc[0]);
+    r.Y = f_add(sm.sc[3], sm.sc[2]);
+    r.Z = f_add(sm.sc[5], sm.sc[4]);
+    return r;
+}
+
+// 2P, complete (RCB16 Algorithm 9, a = 0), on one warp
+FPG_NOINL GPt<fq2> gecw_dbl(GEcW& sm, int L, const GPt<fq2>& P) {
+    gecw_phase(sm, L, [&](int q, fq2& a, fq2& b) {
+        switch (q) {
+            case 0: a = P.Y; b = P.Y; break;
+            case 1: a = P.Y; b = P.Z; break;
+            case 2: a = P.Z; b = P.Z; break;
+            default: a = P.X; b = P.Y; break;
+        }
+    });
+    const fq2 t0 = sm.sc[0], t1 = sm.sc[1], xy = sm.sc[3];
+    const fq2 z8 = f_dbl(f_dbl(f_dbl(t0)));
+    const fq2 bt2 = f_b3(sm.sc[2]);
+    const fq2 y3a = f_add(t0, bt2);
+    const fq2 t0p = f_sub(t0, f_add(f_dbl(bt2), bt2));
+    gecw_phase(sm, L, [&](int q, fq2& a, fq2& b) {
+        switch (q) {
+            case 0: a = bt2; b = z8; break;
+            case 1: a = t1; b = z8; break;
+            case 2: a = t0p; b = y3a; break;
+            default: a = t0p; b = xy; break;
+        }
+    });
+    GPt<fq2> r;
+    r.X = f_dbl(sm.sc[3]);
+    r.Y = f_add(sm.sc[0], sm.sc[2]);
+    r.Z = sm.sc[1];
+    return r;
+}
+
+// k Q on G2 for a canonical k < r (GLS, as gec_g2_mul_proj), on one warp
+FPG_NOINL GPt<fq2> gecw_g2_mul_proj(GEcW& sm, int L, const g2a& Q, const uint32_t* k) {
+    uint32_t q1[7], q2[7], q3[7], d[4][2];
+    div_by_const<2, 7>(q1, d[0], k, GLS_D, GLS_BARRETT);
+    uint32_t t8[8];
+    for (int i = 0; i < 8; i++) t8[i] = i < 7 ? q1[i] : 0;
+    div_by_const<2, 7>(q2, d[1], t8, GLS_D, GLS_BARRETT);
+    for (int i = 0; i < 8; i++) t8[i] = i < 7 ? q2[i] : 0;
+    div_by_const<2, 7>(q3, d[2], t8, GLS_D, GLS_BARRETT);
+    d[3][0] = q3[0];
+    d[3][1] = q3[1];
+    const bool inf = g2a_is_inf(Q);
+    g2a b = Q;
+    GPt<fq2> B[4];
+    for (int i = 0; i < 4; i++) {
+        if (i) b = g2_psi(b);
+        const fq2 y = (i & 1) ? fq2_neg(b.y) : b.y;
+        B[i] = inf ? gec_identity<fq2>() : gec_from_affine(b.x, y);
+    }
+    __syncwarp();
+    if (L == 0) {
+        sm.tab[0] = gec_identity<fq2>();
+        for (int i = 0; i < 4; i++) sm.tab[1 << i] = B[i];
+    }
+    __syncwarp();
+    for (int s = 3; s < 16; s++) {
+        if (!(s & (s - 1))) continue;
+        const int top = 31 - __clz(s);
+        const GPt<fq2> r = gecw_add(sm, L, sm.tab[s & ~(1 << top)], sm.tab[1 << top]);
+        __syncwarp();
+        if (L == 0) sm.tab[s] = r;
+        __syncwarp();
+    }
+    GPt<fq2> acc = gec_identity<fq2>();
+    for (int i = 63; i >= 0; i--) {
+        acc = gecw_dbl(sm, L, acc);
+        const int s = bit_of(d[0], i) | (bit_of(d[1], i) << 1) | (bit_of(d[2], i) << 2) | (bit_of(d[3], i) << 3);
+        acc = gecw_add(sm, L, acc, sm.tab[s]);
+    }
+    return acc;
+}

@@ -1,6 +1,7 @@
 // Batched Miller loops and final exponentiations.
 #include "group12.cuh"
 #include "k_common.cuh"
+#include "warp12.cuh"
 
 namespace fpk {
 
@@ -53,11 +54,61 @@ __global__ void __launch_bounds__(64) k_final_exp_g(const fq12* in, uint32_t n, 
     }
 }
 
+// one warp per final exponentiation (warp12.cuh): value t's result goes to out[t] and/or its
+// serialisation to ser + (t / per) stride_a + (t % per) stride_b
+__global__ void __launch_bounds__(128) k_final_exp_w(const fq12* in, uint32_t n, fq12* out, uint8_t* ser,
+                                                     uint32_t per, size_t stride_a, size_t stride_b) {
+    __shared__ W12 sm[4];
+    const int w = threadIdx.x >> 5, L = threadIdx.x & 31;
+    const uint64_t t = (uint64_t)blockIdx.x * 4 + w;
+    if (t >= n) return;                                   // warp-uniform
+    W12& W = sm[w];
+    w_from_tower(W.s[0], in[t]);
+    w_final_exp(W);
+    if (L < 12) {
+        const int tp = w_tower_pos(L >> 1), e = L & 1;
+        const fq v = W.s[2][L];
+        if (out) reinterpret_cast<fq*>(&out[t])[2 * tp + e] = v;
+        if (ser) fq_to_be(ser + (t / per) * stride_a + (t % per) * stride_b + 96 * tp + 48 * e, v);
+    }
+}
+
 void final_exp_group(const void* in, uint32_t n, void* out, void* ser, uint32_t per, size_t stride_a,
                      size_t stride_b, cudaStream_t s) {
-    if (n) FP_KERNEL("k_final_exp_g", s, k_final_exp_g<<<(n + 7) / 8, 64, 0, s>>>((const fq12*)in, n, (fq12*)out,
-                                                                                (uint8_t*)ser, per, stride_a,
-                                                                                stride_b));
+    if (n) FP_KERNEL("k_final_exp_w", s, k_final_exp_w<<<(n + 3) / 4, 128, 0, s>>>((const fq12*)in, n, (fq12*)out,
+                                                                                  (uint8_t*)ser, per, stride_a,
+                                                                                  stride_b));
+}
+
+// Miller loops, one warp per pair (warp12.cuh).  Pair t of Step 1 round h: t = (k, side, i) with
+// side 0: (A_k[h + i], v_k[i]) and side 1: (A_k[i], v_k[h + i]); Commit: (C_j, v_j = g2pow[2 j]).
+__global__ void __launch_bounds__(128) k_round_miller_w(const g1a* A, const g2a* v, uint32_t K, uint32_t R,
+                                                        uint32_t h, fq12* out) {
+    __shared__ WMill sm[4];
+    const int w = threadIdx.x >> 5, L = threadIdx.x & 31;
+    const uint64_t t = (uint64_t)blockIdx.x * 4 + w;
+    if (t >= (uint64_t)K * 2 * h) return;                 // warp-uniform
+    const uint64_t k = t / (2 * h);
+    const uint32_t r = (uint32_t)(t % (2 * h)), side = r / h, i = r % h;
+    const g1a* Ak = A + k * R;
+    const g2a* vk = v + k * R;
+    if (side == 0) w_miller(sm[w], Ak[h + i], vk[i]);
+    else w_miller(sm[w], Ak[i], vk[h + i]);
+    if (L < 12) reinterpret_cast<fq*>(&out[t])[2 * w_tower_pos(L >> 1) + (L & 1)] = sm[w].f[L];
+}
+__global__ void __launch_bounds__(128) k_commit_miller_w(const g1a* rows, const g2a* g2pow, uint32_t R, fq12* out) {
+    __shared__ WMill sm[4];
+    const int w = threadIdx.x >> 5, L = threadIdx.x & 31;
+    const uint64_t j = (uint64_t)blockIdx.x * 4 + w;
+    if (j >= R) return;
+    w_miller(sm[w], rows[j], g2pow[2 * j]);
+    if (L < 12) reinterpret_cast<fq*>(&out[j])[2 * w_tower_pos(L >> 1) + (L & 1)] = sm[w].f[L];
+}
+void round_miller_w(const void* A, const void* v, uint32_t K, uint32_t R, uint32_t h, void* out, cudaStream_t s) {
+    const uint64_t n = (uint64_t)K * 2 * h;
+    FP_KERNEL("k_round_miller_w", s, k_round_miller_w<<<(unsigned)((n + 3) / 4), 128, 0, s>>>((const g1a*)A,
+                                                                                             (const g2a*)v, K, R, h,
+                                                                                             (fq12*)out));
 }
 
 // FC.Commit's Miller loops on 8-lane groups: pair j = (C_j, v_j)
@@ -72,9 +123,15 @@ __global__ void __launch_bounds__(64) k_commit_miller_g(const g1a* rows, const g
 }
 
 void commit_miller(const void* rows, const void* g2pow, uint32_t R, void* out, cudaStream_t s) {
-    FP_KERNEL("k_commit_miller_g", s, k_commit_miller_g<<<(R + 7) / 8, 64, 0, s>>>((const g1a*)rows,
-                                                                                  (const g2a*)g2pow, R,
-                                                                                  (fq12*)out));
+    if ((uint64_t)R * 32 > 16384 * 32) {           // many pairs: one thread each does less work in total
+        FP_KERNEL("k_commit_miller", s, k_commit_miller<<<grid_for(R, 64), 64, 0, s>>>((const g1a*)rows,
+                                                                                       (const g2a*)g2pow, R,
+                                                                                       (fq12*)out));
+        return;
+    }
+    FP_KERNEL("k_commit_miller_w", s, k_commit_miller_w<<<(R + 3) / 4, 128, 0, s>>>((const g1a*)rows,
+                                                                                   (const g2a*)g2pow, R,
+                                                                                   (fq12*)out));
 }
 void step1_miller(const void* A, const void* v, uint32_t K, uint32_t R, uint32_t h, void* out, cudaStream_t s) {
     uint64_t n = (uint64_t)K * 2 * h;

@@ -1,6 +1,8 @@
 // Step 1 of OpenAll: FC.BOpen (Sec. 3, Eq. b and Eq. folding) for every block S_k at once, with
 // b = sum_{a in S_k} r_a u_a held densely per block, and the faster-verification proof of v_l.
 // Per-block arrays are laid out block-major: X[k * R + i].
+#include <algorithm>
+
 #include "group_ec.cuh"
 #include "k_common.cuh"
 
@@ -196,6 +198,82 @@ __global__ void __launch_bounds__(64) k_fold_grp(g1a* A, g2a* v, fr* bvec, const
     }
 }
 
+// Both folds of round j for few points: blocks [0, nb2) fold 4 points of v each (one warp per point,
+// group_ec.cuh GEcW), the remaining blocks 16 points of A (8-lane groups) and the entries of b.
+union FoldSmemW {
+    GEcW g2[4];
+    GEc<fq> g1[16];
+};
+__global__ void __launch_bounds__(128) k_fold_w(g1a* A, g2a* v, fr* bvec, const fr* x_mont, const fr* xinv_mont,
+                                                uint32_t K, uint32_t R, uint32_t h, uint32_t nb2) {
+    __shared__ FoldSmemW sm;
+    uint32_t kw[8];
+    if (blockIdx.x < nb2) {
+        const int w = threadIdx.x >> 5, L = threadIdx.x & 31;
+        const uint64_t t = (uint64_t)blockIdx.x * 4 + w;
+        if (t >= (uint64_t)K * h) return;                     // warp-uniform
+        const uint64_t k = t / h;
+        const uint32_t i = (uint32_t)(t % h);
+        const uint64_t lo = k * R + i, hi = k * R + h + i;
+        fr_canon_words(kw, xinv_mont[k]);
+        const GPt<fq2> r = gecw_add(sm.g2[w], L, gecw_g2_mul_proj(sm.g2[w], L, v[hi], kw),
+                                    gec_from_affine_or_inf(v[lo].x, v[lo].y));
+        g2a o;
+        gec_to_affine(o.x, o.y, r);
+        __syncwarp();
+        if (L == 0) v[lo] = o;
+        return;
+    }
+    const int grp = threadIdx.x >> 3, lane = threadIdx.x & 7;
+    const uint64_t t0 = (uint64_t)(blockIdx.x - nb2) * 16 + grp;
+    const bool valid = t0 < (uint64_t)K * h;
+    const uint64_t t = valid ? t0 : 0;
+    const uint64_t k = t / h;
+    const uint32_t i = (uint32_t)(t % h);
+    const uint64_t lo = k * R + i, hi = k * R + h + i;
+    fr_canon_words(kw, x_mont[k]);
+    const GPt<fq> r = gec_add(sm.g1[grp], lane, gec_g1_mul_proj(sm.g1[grp], lane, A[hi], kw),
+                              gec_from_affine_or_inf(A[lo].x, A[lo].y));
+    g1a o;
+    gec_to_affine(o.x, o.y, r);
+    __syncwarp();
+    if (valid && lane == 0) {
+        A[lo] = o;
+        bvec[lo] = fr_add(bvec[lo], fr_mul(bvec[hi], xinv_mont[k]));
+    }
+}
+
+// L_j.1 and R_j.1 terms at the support of b only, one 8-lane group per term, for the blocks
+// k0 .. k0 + K - 1 (local index k - k0).  Block k's vector b is
+// non-zero only at its statement indices S_k = [k b, k b + |S_k|) folded mod the current length 2h:
+// term t < min(|S_k|, 2h) sits at p = (k b + t) mod 2h (all p < 2h when |S_k| > 2h); p < h is an
+// L_j.1 term b[p] A[h + p], p >= h an R_j.1 term b[p] A[p - h].  Results go to the dense per-block
+// layout out[k 2h + p] (Jacobian), whose other entries the caller has zeroed (Z = 0: identity).
+__global__ void __launch_bounds__(128) k_sparse_g(const g1a* A, const fr* bvec, uint32_t k0, uint32_t K, uint32_t R,
+                                                  uint32_t h, uint32_t b, uint32_t cmax, g1j* out) {
+    __shared__ GEc<fq> sm[16];
+    const int grp = threadIdx.x >> 3, lane = threadIdx.x & 7;
+    const uint64_t u0 = (uint64_t)blockIdx.x * 16 + grp;
+    uint64_t k = u0 / cmax;
+    uint32_t t = (uint32_t)(u0 % cmax);
+    bool valid = k < K;
+    uint32_t sk = valid ? min(b, R - (k0 + (uint32_t)k) * b) : 1;
+    valid = valid && t < min(sk, 2 * h);
+    if (!valid) { k = 0; t = 0; sk = min(b, R - k0 * b); }    // dummy work keeps the warp uniform
+    const uint32_t p = sk <= 2 * h ? (uint32_t)(((uint64_t)(k0 + k) * b + t) % (2 * h)) : t;
+    uint32_t kw[8];
+    fr_canon_words(kw, bvec[k * R + p]);
+    const GPt<fq> r = gec_g1_mul_proj(sm[grp], lane, A[k * R + (p < h ? h + p : p - h)], kw);
+    __syncwarp();
+    if (valid && lane == 0) {
+        g1j o;                                                // (X : Y : Z) -> Jacobian (X Z, Y Z^2, Z)
+        o.X = fq_mul(r.X, r.Z);
+        o.Y = fq_mul(r.Y, fq_sqr(r.Z));
+        o.Z = r.Z;
+        out[k * 2 * h + p] = o;
+    }
+}
+
 // after the reductions: GT = final exponentiation of the Miller product, G1 part to affine;
 // written to round j's record of block k: L_j.T | L_j.1 | R_j.T | R_j.1
 __global__ void __launch_bounds__(64) k_round_out(const fq12* ml, const g1j* sp, uint32_t K, int j, uint8_t* blocks,
@@ -311,10 +389,12 @@ void step1_block_r(const void* hstmt, uint32_t k0, uint32_t K, uint32_t R, uint3
     FP_KERNEL("k_block_r", s, k_block_r<<<grid_for((uint64_t)K * b, 64), 64, 0, s>>>((const uint8_t*)hstmt, k0, K, R, b,
                                                                                     (fr*)bvec));
 }
-void step1_sparse_terms(const void* A, const void* bvec, uint32_t K, uint32_t R, uint32_t h, void* out,
-                        cudaStream_t s) {
-    FP_KERNEL("k_sparse_terms", s, k_sparse_terms<<<grid_for((uint64_t)K * 2 * h, 64), 64, 0, s>>>((const g1a*)A, (const fr*)bvec, K, R, h,
-                                                                    (g1j*)out));
+void step1_sparse_terms(const void* A, const void* bvec, uint32_t k0, uint32_t K, uint32_t R, uint32_t h, uint32_t b,
+                        void* out, cudaStream_t s) {
+    const uint32_t cmax = std::min(b, 2 * h);
+    cudaMemsetAsync(out, 0, (size_t)K * 2 * h * G1J_BYTES, s);
+    FP_KERNEL("k_sparse_g", s, k_sparse_g<<<(unsigned)(((uint64_t)K * cmax + 15) / 16), 128, 0, s>>>(
+                                   (const g1a*)A, (const fr*)bvec, k0, K, R, h, b, cmax, (g1j*)out));
 }
 void step1_round_out(const void* ml, const void* sp, uint32_t K, int j, void* blocks, size_t bopen_len,
                      cudaStream_t s) {
@@ -380,17 +460,14 @@ void step1_miller_g(const void* A, const void* v, uint32_t K, uint32_t R, uint32
         step1_miller(A, v, K, R, h, ml_out, s);
         return;
     }
-    uint32_t nb_ml = (uint32_t)((n + 7) / 8);
-    FP_KERNEL("k_round_terms_g", s,
-              k_round_terms_g<<<nb_ml, 64, 0, s>>>((const g1a*)A, (const g2a*)v, nullptr, K, R, h, nb_ml,
-                                                   (fq12*)ml_out, nullptr));
+    round_miller_w(A, v, K, R, h, ml_out, s);      // few pairs: one warp each, for latency
 }
 void step1_fold(void* A, void* v, void* bvec, const void* x_mont, const void* xinv_mont, uint32_t K, uint32_t R,
                 uint32_t h, cudaStream_t s) {
-    if ((uint64_t)K * h <= 4096) {      // few points: one 8-lane group per point for latency
-        uint32_t nb = (uint32_t)(((uint64_t)K * h + 7) / 8);
-        FP_KERNEL("k_fold_grp", s, k_fold_grp<<<2 * nb, 64, 0, s>>>((g1a*)A, (g2a*)v, (fr*)bvec, (const fr*)x_mont,
-                                                                    (const fr*)xinv_mont, K, R, h, nb));
+    if ((uint64_t)K * h <= 4096) {      // few points: a warp per G2 point, an 8-lane group per G1 point
+        const uint32_t nb2 = (uint32_t)(((uint64_t)K * h + 3) / 4), nb1 = (uint32_t)(((uint64_t)K * h + 15) / 16);
+        FP_KERNEL("k_fold_w", s, k_fold_w<<<nb2 + nb1, 128, 0, s>>>((g1a*)A, (g2a*)v, (fr*)bvec, (const fr*)x_mont,
+                                                                  (const fr*)xinv_mont, K, R, h, nb2));
         return;
     }
     uint32_t nb = grid_for((uint64_t)K * h, 64);

@@ -66,8 +66,12 @@ void step1_stmt_hash(const void* C_ser, const void* rows_ser, uint32_t k0, uint3
                      void* hstmt, cudaStream_t s);
 void step1_block_r(const void* hstmt, uint32_t k0, uint32_t K, uint32_t R, uint32_t b, void* bvec, cudaStream_t s);
 void step1_miller(const void* A, const void* v, uint32_t K, uint32_t R, uint32_t h, void* out_fq12, cudaStream_t s);
-void step1_sparse_terms(const void* A, const void* bvec, uint32_t K, uint32_t R, uint32_t h, void* out_g1j,
-                        cudaStream_t s);
+// the same Miller loops with one warp per pair (few pairs: latency)
+void round_miller_w(const void* A, const void* v, uint32_t K, uint32_t R, uint32_t h, void* out_fq12, cudaStream_t s);
+// L_j.1 / R_j.1 terms at the support of the b vectors of blocks k0 .. k0 + K - 1 (blocks of size b),
+// dense per-block layout
+void step1_sparse_terms(const void* A, const void* bvec, uint32_t k0, uint32_t K, uint32_t R, uint32_t h, uint32_t b,
+                        void* out_g1j, cudaStream_t s);
 void step1_round_terms(const void* A, const void* v, const void* bvec, uint32_t K, uint32_t R, uint32_t h,
                        void* ml_out_fq12, void* sp_out_g1j, cudaStream_t s);
 void step1_miller_g(const void* A, const void* v, uint32_t K, uint32_t R, uint32_t h, void* ml_out, cudaStream_t s);

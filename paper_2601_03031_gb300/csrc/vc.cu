@@ -496,7 +496,7 @@ fp_proofs* prove_impl(const fp_pp* pp, const fp_commit* cm, uint32_t b, uint32_t
                 const uint32_t h = R >> j;
                 check(cudaEventRecord(ev_folded, s1), "event");
                 check(cudaStreamWaitEvent(s3, ev_folded, 0), "wait");
-                step1_sparse_terms(A, bvec, Kc, R, h, sp, s3);
+                step1_sparse_terms(A, bvec, k0, Kc, R, h, b, sp, s3);
                 void* spr = reduce_pairs(sp, sp2, (uint64_t)Kc * 2 * h, (uint64_t)Kc * 2, g1_pair_reduce, s3);
                 step1_g1_out(spr, Kc, j, blocks1, blen, s3);
                 check(cudaEventRecord(ev_sparse, s3), "event");

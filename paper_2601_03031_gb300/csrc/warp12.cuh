@@ -1,0 +1,548 @@
+// Fq12 arithmetic on one warp: the Fq products of an operation are spread one per lane and round.
+//
+// A Montgomery product is ~700 multiply-add instructions that one warp issues at the integer
+// pipe's rate whatever their dependency structure, so a single lane cannot make one faster; what
+// shortens a chain of Fq12 operations is doing all of an operation's products at once.  Values
+// live in shared memory, flat as Fq2[w]/(w^6 - xi) (xi = 1 + u): Fq index 2k + e holds component
+// e (0 = real, 1 = u) of the coefficient of w^k, k = 0..5 (w^2 = v, so flat k = 0,2,4 are the tower's
+// c0.c0, c0.c1, c0.c2 and k = 1,3,5 are c1.c0, c1.c1, c1.c2).  Every operation is
+//   1. products: lane L computes products L, L + 32, ... of the operation's list,
+//   2. __syncwarp, then 12 (or 24) lanes form the output Fq components as sums of products,
+//   3. __syncwarp.
+// All 32 lanes run every operation (no lane-dependent synchronisation), so one warp handles one
+// Fq12 value at a time.
+//   product c = a b:        36 Fq2 products a_i b_j, each 3 Fq products (Karatsuba): 108
+//   cyclotomic squaring:    Granger-Scott, 3 Fq4 squarings of 7 Fq products each: 21
+//   Frobenius p / p^2:      20 / 10 Fq products by constants
+#pragma once
+#include "pairing.cuh"
+
+struct W12 {
+    fq p[108];          // products of the current operation
+    fq s[5][12];        // value slots (flat order)
+    fq h[24];           // partial sums
+};
+
+FPG_DEV void wsync() { __syncwarp(); }
+FPG_DEV int w_lane() { return (int)(threadIdx.x & 31); }
+
+// tower position of flat coefficient k (0..5): even k -> c0.c(k/2), odd k -> c1.c(k/2)
+FPG_DEV int w_tower_pos(int k) { return (k & 1) ? 3 + (k >> 1) : (k >> 1); }
+
+FPG_DEV fq fq_select(bool c, const fq& a, const fq& b) {
+    fq r;
+#pragma unroll
+    for (int j = 0; j < 12; j++) r.v[j] = c ? a.v[j] : b.v[j];
+    return r;
+}
+
+// dst (flat) <- f (tower order: six consecutive Fq2, each (c0, c1))
+FPG_DEV void w_from_tower(fq* dst, const fq12& f) {
+    const int L = w_lane();
+    if (L < 12) dst[L] = reinterpret_cast<const fq*>(&f)[2 * w_tower_pos(L >> 1) + (L & 1)];
+    wsync();
+}
+FPG_DEV void w_copy(fq* dst, const fq* src) {
+    const int L = w_lane();
+    wsync();
+    if (L < 12) dst[L] = src[L];
+    wsync();
+}
+
+// out = a b (out may alias a or b)
+FPG_NOINL void w_mul(W12& W, fq* out, const fq* a, const fq* b) {
+    const int L = w_lane();
+    fq zero;
+    fq_zero(zero);
+    for (int t = L; t < 108; t += 32) {
+        const int q = t / 3, kind = t - 3 * q, i = q / 6, j = q - 6 * i;
+        // kind 0: a_i.0 b_j.0, kind 1: a_i.1 b_j.1, kind 2: (a_i.0 + a_i.1)(b_j.0 + b_j.1)
+        const fq x = fq_add(a[2 * i + (kind == 1)], kind == 2 ? a[2 * i + 1] : zero);
+        const fq y = fq_add(b[2 * j + (kind == 1)], kind == 2 ? b[2 * j + 1] : zero);
+        W.p[t] = fq_mul(x, y);
+    }
+    wsync();
+    // lane L < 24: output component o = L % 12 (coefficient k, part e), terms i in [3 hf, 3 hf + 3)
+    if (L < 24) {
+        const int o = L % 12, hf = L / 12, k = o >> 1, e = o & 1;
+        fq acc = zero;
+        for (int i = 3 * hf; i < 3 * hf + 3; i++) {
+            int j = k - i;
+            const bool wrap = j < 0;                 // w^(i + j) with i + j >= 6: times xi
+            if (wrap) j += 6;
+            const fq* m = &W.p[3 * (6 * i + j)];
+            const fq m01 = fq_add(m[0], m[1]);
+            const fq re = fq_sub(m[0], m[1]);
+            const fq im = fq_sub(m[2], m01);
+            // (re + im u)(1 + u) = (re - im) + (re + im) u
+            const fq x = fq_select(wrap, fq_select(e, fq_add(re, im), fq_sub(re, im)), e ? im : re);
+            acc = fq_add(acc, x);
+        }
+        W.h[L] = acc;
+    }
+    wsync();
+    if (L < 12) out[L] = fq_add(W.h[L], W.h[L + 12]);
+    wsync();
+}
+
+// out = a^2 for a in the cyclotomic subgroup (Granger-Scott).  Pairs (z_p, z_{p+3}), p = 0, 1, 2,
+// are Fq4 elements a + b s (s = w^3, s^2 = xi): A_p = a^2 + xi b^2, B_p = 2 a b, and
+//   c0 = 3 A0 - 2 z0, c3 = 3 B0 + 2 z3, c1 = 3 xi B2 + 2 z1, c4 = 3 A2 - 2 z4, c2 = 3 A1 - 2 z2,
+//   c5 = 3 B1 + 2 z5.
+// Products per pair (a = a0 + a1 u, b = b0 + b1 u): s1 = (a0 + a1)(a0 - a1), s2 = a0 a1,
+// t1 = (b0 + b1)(b0 - b1), t2 = b0 b1, k0 = a0 b0, k1 = a1 b1, k2 = (a0 + a1)(b0 + b1); then
+// a^2 = s1 + 2 s2 u, b^2 = t1 + 2 t2 u, a b = (k0 - k1) + (k2 - k0 - k1) u.
+FPG_NOINL void w_cyc_sqr(W12& W, fq* out, const fq* z) {
+    const int L = w_lane();
+    if (L < 21) {
+        const int p = L / 7, r = L - 7 * p;
+        const fq a0 = z[2 * p], a1 = z[2 * p + 1], b0 = z[2 * p + 6], b1 = z[2 * p + 7];
+        const bool ua = r < 2 || r == 4 || r == 5 || r == 6;            // x built from a
+        const fq xs = ua ? a0 : b0, xt = ua ? a1 : b1;
+        // x: r in {0, 2, 6}: xs + xt; r in {1, 3, 4}: xs; r == 5: a1
+        const fq xsum = fq_add(xs, xt);
+        fq x = (r == 0 || r == 2 || r == 6) ? xsum : (r == 5 ? a1 : xs);
+        // y: r == 0: a0 - a1; r == 1: a1; r == 2: b0 - b1; r == 3: b1; r == 4: b0; r == 5: b1;
+        //    r == 6: b0 + b1
+        const fq ys = (r < 2) ? a0 : b0, yt = (r < 2) ? a1 : b1;
+        const fq ydiff = fq_sub(ys, yt), ysum = fq_add(ys, yt);
+        fq y = (r == 0 || r == 2) ? ydiff : (r == 6 ? ysum : (r == 4 ? b0 : (r == 1 ? a1 : b1)));
+        W.p[L] = fq_mul(x, y);
+    }
+    wsync();
+    if (L < 12) {
+        const int k = L >> 1, e = L & 1;
+        // coefficient k -> (pair, kind): kind 0: 3A - 2z, 1: 3B + 2z, 2: 3 xi B + 2z
+        const int pair = (k == 0 || k == 3) ? 0 : (k == 2 || k == 5) ? 1 : 2;
+        const int kind = (k == 0 || k == 2 || k == 4) ? 0 : (k == 1 ? 2 : 1);
+        const fq* m = &W.p[7 * pair];
+        const fq s1 = m[0], s2 = m[1], t1 = m[2], t2 = m[3], k0 = m[4], k1 = m[5], k2 = m[6];
+        const fq t2d = fq_dbl(t2);
+        const fq Are = fq_sub(fq_add(s1, t1), t2d);
+        const fq Aim = fq_add(fq_add(fq_dbl(s2), t1), t2d);
+        const fq Bre = fq_dbl(fq_sub(k0, k1));
+        const fq Bim = fq_dbl(fq_sub(k2, fq_add(k0, k1)));
+        fq V;
+        if (kind == 0) V = e ? Aim : Are;
+        else if (kind == 1) V = e ? Bim : Bre;
+        else V = e ? fq_add(Bre, Bim) : fq_sub(Bre, Bim);
+        const fq V3 = fq_add(fq_dbl(V), V);
+        const fq z2 = fq_dbl(z[L]);
+        W.h[L] = kind == 0 ? fq_sub(V3, z2) : fq_add(V3, z2);
+    }
+    wsync();
+    if (L < 12) out[L] = W.h[L];
+    wsync();
+}
+
+// out = conj(a) = a^(p^6): coefficients of odd k negated
+FPG_DEV void w_conj(fq* out, const fq* a) {
+    const int L = w_lane();
+    wsync();
+    if (L < 12) {
+        const fq v = a[L];
+        out[L] = ((L >> 1) & 1) ? fq_neg(v) : v;
+    }
+    wsync();
+}
+
+// out = a^p: coefficient k -> conj(a_k) gamma1_k (gamma1_0 = 1);
+// (x0 - x1 u)(g0 + g1 u) = (x0 g0 + x1 g1) + (x0 g1 - x1 g0) u
+FPG_NOINL void w_frob(W12& W, fq* out, const fq* a) {
+    const int L = w_lane();
+    if (L < 20) {
+        const int k = 1 + (L >> 2), r = L & 3;
+        const fq2 g = frob1_coef(k);
+        const fq x = (r == 0 || r == 2) ? a[2 * k] : a[2 * k + 1];
+        const fq y = (r == 0 || r == 3) ? g.c0 : g.c1;
+        W.p[L] = fq_mul(x, y);
+    }
+    wsync();
+    if (L < 12) {
+        const int k = L >> 1, e = L & 1;
+        fq v;
+        if (k == 0) v = e ? fq_neg(a[1]) : a[0];
+        else {
+            const fq* m = &W.p[4 * (k - 1)];
+            v = e ? fq_sub(m[2], m[3]) : fq_add(m[0], m[1]);
+        }
+        W.h[L] = v;
+    }
+    wsync();
+    if (L < 12) out[L] = W.h[L];
+    wsync();
+}
+
+// out = a^(p^2): coefficient k times gamma2_k in Fq (gamma2_0 = 1)
+FPG_NOINL void w_frob2(W12& W, fq* out, const fq* a) {
+    const int L = w_lane();
+    if (L < 10) {
+        const int k = 1 + (L >> 1);
+        W.p[L] = fq_mul(a[2 * k + (L & 1)], frob2_coef(k));
+    }
+    wsync();
+    if (L < 12) W.h[L] = L < 2 ? a[L] : W.p[L - 2];
+    wsync();
+    if (L < 12) out[L] = W.h[L];
+    wsync();
+}
+
+// out = a^-1 (one lane, tower arithmetic)
+FPG_NOINL void w_inv(fq* out, const fq* a) {
+    const int L = w_lane();
+    wsync();
+    if (L == 0) {
+        fq12 f;
+        fq* fc = reinterpret_cast<fq*>(&f);
+        for (int o = 0; o < 12; o++) fc[2 * w_tower_pos(o >> 1) + (o & 1)] = a[o];
+        const fq12 fi = fq12_inv(f);
+        const fq* ic = reinterpret_cast<const fq*>(&fi);
+        for (int o = 0; o < 12; o++) out[o] = ic[2 * w_tower_pos(o >> 1) + (o & 1)];
+    }
+    wsync();
+}
+
+// acc = base^e for base in the cyclotomic subgroup (e little-endian words, e > 0); acc != base
+FPG_NOINL void w_cyc_exp(W12& W, fq* acc, const fq* base, const uint32_t* e, int bits) {
+    int i = bits - 1;
+    while (i >= 0 && !((e[i >> 5] >> (i & 31)) & 1)) i--;
+    w_copy(acc, base);
+    for (i = i - 1; i >= 0; i--) {
+        w_cyc_sqr(W, acc, acc);
+        if ((e[i >> 5] >> (i & 31)) & 1) w_mul(W, acc, acc, base);
+    }
+}
+
+// slot 2 <- f^((p^12 - 1)/r) for f in slot 0 (slots 0..4 are used).  Easy part t = conj(f) f^-1,
+// g = t^(p^2) t; hard part g^d with d = h1 (x + p)(x^2 + p^2 - 1) + 1, h1 = (x - 1)^2 / 3, x < 0.
+FPG_NOINL void w_final_exp(W12& W) {
+    fq* s0 = W.s[0];
+    fq* s1 = W.s[1];
+    fq* s2 = W.s[2];
+    fq* s3 = W.s[3];
+    fq* s4 = W.s[4];
+    const uint32_t xabs[2] = {(uint32_t)BLS_X_ABS, (uint32_t)(BLS_X_ABS >> 32)};
+    const uint32_t h1[4] = {BLS_H1[0], BLS_H1[1], BLS_H1[2], BLS_H1[3]};
+    w_inv(s1, s0);                      // f^-1
+    w_conj(s0, s0);                     // conj(f)
+    w_mul(W, s2, s0, s1);               // t
+    w_frob2(W, s3, s2);
+    w_mul(W, s3, s3, s2);               // g = t^(p^2) t
+    w_cyc_exp(W, s4, s3, h1, 126);      // a = g^h1
+    w_cyc_exp(W, s0, s4, xabs, 64);     // a^|x|
+    w_conj(s0, s0);                     // a^x
+    w_frob(W, s1, s4);                  // a^p
+    w_mul(W, s0, s0, s1);               // b = a^(x + p)
+    w_cyc_exp(W, s1, s0, xabs, 64);
+    w_cyc_exp(W, s2, s1, xabs, 64);     // b^(x^2)
+    w_frob2(W, s1, s0);
+    w_mul(W, s2, s2, s1);               // b^(x^2 + p^2)
+    w_conj(s1, s0);
+    w_mul(W, s2, s2, s1);               // c = b^(x^2 + p^2 - 1)
+    w_mul(W, s2, s2, s3);               // c g
+}
+
+// ---------------------------------------------------------------------------------------
+// Miller loop on one warp: same projective formulas as miller_loop in pairing.cuh.
+// Doubling step, T = (X, Y, Z), P with m3x = -3 xP, y2 = 2 yP, b' = 4 xi:
+//   line l0 + l2 w^2 + l3 w^3 = (Y^2 - 3 b' Z^2) + (m3x X^2) w^2 + (y2 Y Z) w^3,
+//   2T = (2 X Y (Y^2 - 9 b' Z^2), (Y^2 + 9 b' Z^2)^2 - 108 (b' Z^2)^2, 8 Y^2 Y Z),
+//   rounds: A = f^2 products (57) + X^2, Y^2, Z^2, YZ, XY (12); B = the line and 2T products
+//   (14); C = f^2 * line (54).
+// Addition step with Q: theta = Y - yQ Z, lambda = X - xQ Z,
+//   line = (theta xQ - lambda yQ) + (-theta xP) w^2 + (lambda yP) w^3,
+//   C = theta^2, D = lambda^2, E = D lambda, F = Z C, G = X D, H = E + F - 2G,
+//   T + Q = (lambda H, theta (G - H) - Y E, Z E),
+//   rounds: A = yQ Z, xQ Z (6); B = line, theta^2, lambda^2 (14); C = f * line (54) + E, F, G
+//   (9); D = lambda H, theta (G - H), Y E, Z E (12).
+// Fq2 products x y by Karatsuba: m0 = x0 y0, m1 = x1 y1, m2 = (x0 + x1)(y0 + y1),
+// re = m0 - m1, im = m2 - m0 - m1; squares x^2: m0 = (x0 + x1)(x0 - x1), m1 = x0 x1, re = m0,
+// im = 2 m1.
+// ---------------------------------------------------------------------------------------
+struct WMill {
+    fq p[72];       // products of a round
+    fq f[12];       // running value (flat)
+    fq g[12];       // f^2
+    fq T[6];        // X, Y, Z
+    fq Q[4];        // xQ, yQ
+    fq v[16];       // round results: T products, line helpers
+    fq l[6];        // line l0, l2, l3
+    fq h[24];
+};
+
+FPG_DEV void kara_ops(fq& x, fq& y, const fq* a, const fq* b, int kind) {
+    fq zero;
+    fq_zero(zero);
+    x = fq_add(a[kind == 1], kind == 2 ? a[1] : zero);
+    y = fq_add(b[kind == 1], kind == 2 ? b[1] : zero);
+}
+FPG_DEV void sq_ops(fq& x, fq& y, const fq* a, int kind) {
+    x = kind ? a[0] : fq_add(a[0], a[1]);
+    y = kind ? a[1] : fq_sub(a[0], a[1]);
+}
+// component e of a Karatsuba product / of a square, from its products m
+FPG_DEV fq kara_part(const fq* m, int e) { return e ? fq_sub(m[2], fq_add(m[0], m[1])) : fq_sub(m[0], m[1]); }
+FPG_DEV fq sq_part(const fq* m, int e) { return e ? fq_dbl(m[1]) : m[0]; }
+// component e of (re + im u) times xi = 1 + u when tw
+FPG_DEV fq twist_part(const fq& re, const fq& im, int e, bool tw) {
+    return tw ? (e ? fq_add(re, im) : fq_sub(re, im)) : (e ? im : re);
+}
+FPG_DEV fq fq_mul_small(const fq& a, unsigned k) {          // k a for a small constant k
+    fq acc;
+    fq_zero(acc);
+    for (int i = 31 - __clz(k); i >= 0; i--) {
+        acc = fq_dbl(acc);
+        if ((k >> i) & 1) acc = fq_add(acc, a);
+    }
+    return acc;
+}
+
+// f (S.f) times the sparse line (S.l) -> products S.p[0..53]; combine writes S.f
+FPG_DEV void wm_line_products(WMill& S, const fq* src, int t) {
+    const int q = t / 3, kind = t - 3 * q, term = q / 6, k = q - 6 * term;
+    const int i = term == 0 ? k : (term == 1 ? (k + 4) % 6 : (k + 3) % 6);
+    fq x, y;
+    kara_ops(x, y, src + 2 * i, S.l + 2 * term, kind);
+    S.p[t] = fq_mul(x, y);
+}
+FPG_DEV fq wm_line_combine(const WMill& S, int o) {
+    const int k = o >> 1, e = o & 1;
+    fq acc = twist_part(kara_part(&S.p[3 * k], 0), kara_part(&S.p[3 * k], 1), e, false);
+    acc = fq_add(acc, twist_part(kara_part(&S.p[3 * (6 + k)], 0), kara_part(&S.p[3 * (6 + k)], 1), e, k < 2));
+    acc = fq_add(acc, twist_part(kara_part(&S.p[3 * (12 + k)], 0), kara_part(&S.p[3 * (12 + k)], 1), e, k < 3));
+    return acc;
+}
+
+FPG_NOINL void wm_dbl(WMill& S, const fq& m3x, const fq& y2) {
+    const int L = w_lane();
+    // round A
+    for (int t = L; t < 69; t += 32) {
+        fq x, y;
+        if (t < 12) {
+            sq_ops(x, y, S.f + 2 * (t >> 1), t & 1);
+        } else if (t < 57) {
+            const int c = (t - 12) / 3, kind = t - 12 - 3 * c;
+            int i = 0, rem = c;
+            while (rem >= 5 - i) { rem -= 5 - i; i++; }
+            kara_ops(x, y, S.f + 2 * i, S.f + 2 * (i + 1 + rem), kind);
+        } else {
+            const int u = t - 57;
+            if (u < 6) sq_ops(x, y, S.T + 2 * (u >> 1), u & 1);                 // X^2, Y^2, Z^2
+            else if (u < 9) kara_ops(x, y, S.T + 2, S.T + 4, u - 6);             // Y Z
+            else kara_ops(x, y, S.T, S.T + 2, u - 9);                            // X Y
+        }
+        S.p[t] = fq_mul(x, y);
+    }
+    wsync();
+    if (L < 12) {                                  // f^2, coefficient k, component e
+        const int k = L >> 1, e = L & 1;
+        fq acc;
+        fq_zero(acc);
+        for (int i = 0; i < 6; i++) {
+            int j = k - i;
+            if (j < 0) j += 6;
+            if (i > j) continue;
+            const bool wrap = i + j >= 6;
+            fq re, im;
+            if (i == j) {
+                re = sq_part(&S.p[2 * i], 0);
+                im = sq_part(&S.p[2 * i], 1);
+            } else {
+                const int c = i * (11 - i) / 2 + (j - i - 1);
+                re = fq_dbl(kara_part(&S.p[12 + 3 * c], 0));
+                im = fq_dbl(kara_part(&S.p[12 + 3 * c], 1));
+            }
+            acc = fq_add(acc, twist_part(re, im, e, wrap));
+        }
+        S.g[L] = acc;
+    } else if (L < 22) {                           // XX, YY, ZZ, YZ, XY (re, im)
+        const int v = L - 12, which = v >> 1, e = v & 1;
+        S.v[v] = which < 3 ? sq_part(&S.p[57 + 2 * which], e) : kara_part(&S.p[57 + 6 + 3 * (which - 3)], e);
+    }
+    wsync();
+    // round B
+    if (L < 14) {
+        const fq* XX = S.v;
+        const fq* YY = S.v + 2;
+        const fq* ZZ = S.v + 4;
+        const fq* YZ = S.v + 6;
+        const fq* XY = S.v + 8;
+        // bz = b' Z^2 = 4 (1 + u) ZZ
+        fq bz[2], bz9[2], yp[2], ym[2];
+        bz[0] = fq_dbl(fq_dbl(fq_sub(ZZ[0], ZZ[1])));
+        bz[1] = fq_dbl(fq_dbl(fq_add(ZZ[0], ZZ[1])));
+        for (int e = 0; e < 2; e++) {
+            const fq b3 = fq_add(fq_dbl(bz[e]), bz[e]);
+            bz9[e] = fq_add(fq_dbl(b3), b3);
+            yp[e] = fq_add(YY[e], bz9[e]);
+            ym[e] = fq_sub(YY[e], bz9[e]);
+        }
+        fq x, y;
+        if (L < 2) { x = XX[L]; y = m3x; }
+        else if (L < 4) { x = YZ[L - 2]; y = y2; }
+        else if (L < 7) kara_ops(x, y, XY, ym, L - 4);
+        else if (L < 9) sq_ops(x, y, yp, L - 7);
+        else if (L < 11) sq_ops(x, y, bz, L - 9);
+        else kara_ops(x, y, YY, YZ, L - 11);
+        S.p[L] = fq_mul(x, y);
+    }
+    wsync();
+    if (L < 12) {
+        const int w = L >> 1, e = L & 1;
+        fq r;
+        if (w == 0) {                               // l0 = YY - 3 bz
+            const fq zz0 = S.v[4], zz1 = S.v[5];
+            const fq bze = fq_dbl(fq_dbl(e ? fq_add(zz0, zz1) : fq_sub(zz0, zz1)));
+            r = fq_sub(S.v[2 + e], fq_add(fq_dbl(bze), bze));
+            S.l[e] = r;
+        } else if (w == 1) {                        // l2 = m3x XX
+            S.l[2 + e] = S.p[e];
+        } else if (w == 2) {                        // l3 = y2 YZ
+            S.l[4 + e] = S.p[2 + e];
+        } else if (w == 3) {                        // X' = 2 XY (YY - 9 bz)
+            S.T[e] = fq_dbl(kara_part(&S.p[4], e));
+        } else if (w == 4) {                        // Y' = (YY + 9 bz)^2 - 108 bz^2
+            S.T[2 + e] = fq_sub(sq_part(&S.p[7], e), fq_mul_small(sq_part(&S.p[9], e), 108));
+        } else {                                    // Z' = 8 YY YZ
+            S.T[4 + e] = fq_dbl(fq_dbl(fq_dbl(kara_part(&S.p[11], e))));
+        }
+    }
+    wsync();
+    // round C: f^2 * line
+    for (int t = L; t < 54; t += 32) wm_line_products(S, S.g, t);
+    wsync();
+    if (L < 12) S.h[L] = wm_line_combine(S, L);
+    wsync();
+    if (L < 12) S.f[L] = S.h[L];
+    wsync();
+}
+
+FPG_NOINL void wm_add(WMill& S, const fq& mxP, const fq& yP) {
+    const int L = w_lane();
+    const fq* X = S.T;
+    const fq* Y = S.T + 2;
+    const fq* Z = S.T + 4;
+    const fq* xQ = S.Q;
+    const fq* yQ = S.Q + 2;
+    // round A: yQ Z, xQ Z
+    if (L < 6) {
+        fq x, y;
+        kara_ops(x, y, L < 3 ? yQ : xQ, Z, L % 3);
+        S.p[L] = fq_mul(x, y);
+    }
+    wsync();
+    if (L < 4) {                                    // theta = Y - yQ Z, lambda = X - xQ Z
+        const int e = L & 1;
+        S.v[L] = L < 2 ? fq_sub(Y[e], kara_part(&S.p[0], e)) : fq_sub(X[e], kara_part(&S.p[3], e));
+    }
+    wsync();
+    const fq* th = S.v;
+    const fq* la = S.v + 2;
+    // round B: theta xQ, lambda yQ, -theta xP, lambda yP, theta^2, lambda^2
+    if (L < 14) {
+        fq x, y;
+        if (L < 3) kara_ops(x, y, th, xQ, L);
+        else if (L < 6) kara_ops(x, y, la, yQ, L - 3);
+        else if (L < 8) { x = th[L - 6]; y = mxP; }
+        else if (L < 10) { x = la[L - 8]; y = yP; }
+        else if (L < 12) sq_ops(x, y, th, L - 10);
+        else sq_ops(x, y, la, L - 12);
+        S.p[L] = fq_mul(x, y);
+    }
+    wsync();
+    if (L < 10) {
+        const int w = L >> 1, e = L & 1;
+        if (w == 0) S.l[e] = fq_sub(kara_part(&S.p[0], e), kara_part(&S.p[3], e));
+        else if (w == 1) S.l[2 + e] = S.p[6 + e];
+        else if (w == 2) S.l[4 + e] = S.p[8 + e];
+        else if (w == 3) S.v[4 + e] = sq_part(&S.p[10], e);        // C = theta^2
+        else S.v[6 + e] = sq_part(&S.p[12], e);                     // D = lambda^2
+    }
+    wsync();
+    // round C: f * line (54) and E = D lambda, F = Z C, G = X D (9)
+    for (int t = L; t < 63; t += 32) {
+        if (t < 54) {
+            wm_line_products(S, S.f, t);
+        } else {
+            const int u = t - 54, which = u / 3;
+            fq x, y;
+            kara_ops(x, y, which == 0 ? S.v + 6 : (which == 1 ? Z : X), which == 0 ? la : (which == 1 ? S.v + 4 : S.v + 6),
+                     u % 3);
+            S.p[t] = fq_mul(x, y);
+        }
+    }
+    wsync();
+    if (L < 12) S.h[L] = wm_line_combine(S, L);
+    else if (L < 18) {                              // E, F, G
+        const int v = L - 12;
+        S.v[8 + v] = kara_part(&S.p[54 + 3 * (v >> 1)], v & 1);
+    }
+    wsync();
+    if (L < 12) S.f[L] = S.h[L];
+    // round D: lambda H, theta (G - H), Y E, Z E, with H = E + F - 2 G
+    const fq* E = S.v + 8;
+    const fq* Fv = S.v + 10;
+    const fq* G = S.v + 12;
+    if (L >= 16 && L < 28) {
+        const int u = L - 16, which = u / 3;
+        fq H[2], GH[2];
+        for (int e = 0; e < 2; e++) {
+            H[e] = fq_sub(fq_add(E[e], Fv[e]), fq_dbl(G[e]));
+            GH[e] = fq_sub(G[e], H[e]);
+        }
+        fq x, y;
+        kara_ops(x, y, which == 0 ? la : (which == 1 ? th : (which == 2 ? Y : Z)),
+                 which == 0 ? H : (which == 1 ? GH : E), u % 3);
+        S.p[u] = fq_mul(x, y);
+    }
+    wsync();
+    if (L < 6) {
+        const int w = L >> 1, e = L & 1;
+        fq r;
+        if (w == 0) r = kara_part(&S.p[0], e);
+        else if (w == 1) r = fq_sub(kara_part(&S.p[3], e), kara_part(&S.p[6], e));
+        else r = kara_part(&S.p[9], e);
+        S.h[L] = r;
+    }
+    wsync();
+    if (L < 6) S.T[L] = S.h[L];
+    wsync();
+}
+
+// S.f <- conj(f_{|x|,Q}(P)) in flat order; 1 when P or Q is the identity
+FPG_NOINL void w_miller(WMill& S, g1a P, g2a Q) {
+    const int L = w_lane();
+    const bool inf = g1a_is_inf(P) || g2a_is_inf(Q);
+    if (inf) {
+        P = g1_generator();
+        Q = g2_generator();
+    }
+    const fq m3x = fq_neg(fq_add(fq_dbl(P.x), P.x)), y2 = fq_dbl(P.y), mxP = fq_neg(P.x);
+    if (L < 12) {
+        fq one;
+        fq_one(one);
+        fq z;
+        fq_zero(z);
+        S.f[L] = L == 0 ? one : z;
+    }
+    if (L == 0) {
+        S.T[0] = Q.x.c0; S.T[1] = Q.x.c1; S.T[2] = Q.y.c0; S.T[3] = Q.y.c1;
+        fq_one(S.T[4]);
+        fq_zero(S.T[5]);
+        S.Q[0] = Q.x.c0; S.Q[1] = Q.x.c1; S.Q[2] = Q.y.c0; S.Q[3] = Q.y.c1;
+    }
+    wsync();
+    for (int i = 62; i >= 0; i--) {
+        wm_dbl(S, m3x, y2);
+        if ((BLS_X_ABS >> i) & 1) wm_add(S, mxP, P.y);
+    }
+    if (L < 12) {
+        fq one;
+        fq_one(one);
+        fq z;
+        fq_zero(z);
+        const fq v = ((L >> 1) & 1) ? fq_neg(S.f[L]) : S.f[L];       // conjugation (x < 0)
+        S.f[L] = inf ? (L == 0 ? one : z) : v;
+    }
+    wsync();
+}
