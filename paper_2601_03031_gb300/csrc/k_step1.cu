@@ -375,6 +375,108 @@ __global__ void __launch_bounds__(64) k_w_terms(const g2a* g2pow, const fr* q_ca
     out[t] = res;
 }
 
+// W terms with one warp per term (few terms: latency); results as Jacobian (X Z, Y Z^2, Z)
+__global__ void __launch_bounds__(128) k_w_terms_w(const g2a* g2pow, const fr* q_canon, uint32_t K, uint32_t R,
+                                                   g2j* out) {
+    __shared__ GEcW sm[4];
+    const int w = threadIdx.x >> 5, L = threadIdx.x & 31;
+    const uint64_t t = (uint64_t)blockIdx.x * 4 + w;
+    if (t >= (uint64_t)K * 2 * R) return;                     // warp-uniform
+    const uint32_t i = (uint32_t)(t % (2 * R));
+    const fr sc = q_canon[t];
+    if (i >= 2 * R - 1 || fr_is_zero(sc)) {
+        if (L == 0) {
+            g2j z;
+            jac_set_inf(z);
+            out[t] = z;
+        }
+        return;
+    }
+    const GPt<fq2> r = gecw_g2_mul_proj(sm[w], L, g2pow[i], sc.v);
+    __syncwarp();
+    if (L == 0) {
+        g2j o;
+        o.X = fq2_mul(r.X, r.Z);
+        o.Y = fq2_mul(r.Y, fq2_sqr(r.Z));
+        o.Z = r.Z;
+        out[t] = o;
+    }
+}
+
+// The fast-verification proof's quotient for one block per CTA (parallel form of k_kzg):
+//   P(X) = prod_j (1 + x_j^-1 X^(2^(l - j + 1))): the coefficient of X^m (m even) is the product of
+//   x_j^-1 over the bits l - j + 1 set in m, and 0 for odd m;
+//   q = (P(X) - P(z)) / (X - z): q_(i-1) = sum_{m >= i} P_m z^(m - i), by chunks of C indices: each
+//   thread runs its chunk's recurrence with a zero carry, one thread chains the chunk carries
+//   (carry of the chunk below = local top + z^len carry), then each chunk adds z^(hi - i) carry.
+constexpr int KZG_THREADS = 128, KZG_CHUNK = 32;
+__global__ void __launch_bounds__(KZG_THREADS) k_kzg_p(const g1a* A, const g2a* v, const uint8_t* xprev,
+                                                       const fr* xinv_all, uint32_t K, uint32_t R, int log_r,
+                                                       uint8_t* blocks, size_t bopen_len, fr* pcoef, fr* q_canon) {
+    __shared__ fr zpow[KZG_CHUNK + 1];
+    __shared__ fr carry[KZG_THREADS];
+    const uint32_t k = blockIdx.x;
+    const int T = threadIdx.x;
+    const uint32_t deg = 2 * R - 2;
+    fr* P = pcoef + (size_t)k * (deg + 1);
+    fr* q = q_canon + (size_t)k * (2 * R);
+    if (T == 0) {
+        uint8_t* tail = blocks + k * bopen_len + (size_t)log_r * ROUND_BYTES;
+        g1a_to_be(tail, A[(size_t)k * R]);
+        g2a_to_be(tail + G1_SER, v[(size_t)k * R]);
+        const fr z = hash_to_fr("FP-z", 4, xprev + k * 32, 32, tail + G1_SER, G2_SER, nullptr, 0);
+        fr_one(zpow[0]);
+        for (int c = 1; c <= KZG_CHUNK; c++) zpow[c] = fr_mul(zpow[c - 1], z);
+    }
+    for (uint32_t m = T; m <= deg; m += KZG_THREADS) {
+        fr c;
+        fr_one(c);
+        if (m & 1) {
+            fr_zero(c);
+        } else {
+            for (int j = 1; j <= log_r; j++)
+                if ((m >> (log_r - j + 1)) & 1) c = fr_mul(c, xinv_all[(size_t)k * log_r + (j - 1)]);
+        }
+        P[m] = c;
+    }
+    __syncthreads();
+    // indices i = 1 .. deg produce q_(i-1); chunk c covers i in [1 + c C, min(1 + (c + 1) C, deg + 1))
+    const uint32_t nchunks = (deg + KZG_CHUNK - 1) / KZG_CHUNK;
+    for (uint32_t c = T; c < nchunks; c += KZG_THREADS) {
+        const uint32_t lo = 1 + c * KZG_CHUNK, hi = min(lo + KZG_CHUNK, deg + 1);
+        fr acc;
+        fr_zero(acc);
+        for (uint32_t i = hi - 1; i >= lo; i--) {
+            acc = fr_add(P[i], fr_mul(zpow[1], acc));        // local q_(i-1) with zero carry from above
+            q[i - 1] = acc;
+        }
+        carry[c] = acc;                                       // local q_(lo-1)
+    }
+    __syncthreads();
+    if (T == 0) {
+        // true q_(lo_c - 1) = local_c + z^(hi_c - lo_c) q_(hi_c - 1), q_deg = 0 above the top chunk;
+        // carry[c] <- the true q_(hi_c - 1) that chunk c needs
+        fr above;
+        fr_zero(above);
+        for (int c = (int)nchunks - 1; c >= 0; c--) {
+            const uint32_t lo = 1 + c * KZG_CHUNK, hi = min(lo + KZG_CHUNK, deg + 1);
+            const fr local = carry[c];
+            carry[c] = above;
+            above = fr_add(local, fr_mul(zpow[hi - lo], above));
+        }
+    }
+    __syncthreads();
+    for (uint32_t c = T; c < nchunks; c += KZG_THREADS) {
+        const uint32_t lo = 1 + c * KZG_CHUNK, hi = min(lo + KZG_CHUNK, deg + 1);
+        const fr cin = carry[c];
+        for (uint32_t i = lo; i < hi; i++) q[i - 1] = fr_from_mont(fr_add(q[i - 1], fr_mul(zpow[hi - i], cin)));
+    }
+    if (T == 0) {
+        fr_zero(q[deg]);
+        fr_zero(q[deg + 1]);
+    }
+}
+
 void step1_init(const void* rows, const void* g2pow, uint32_t K, uint32_t R, void* A, void* v, void* bvec,
                 cudaStream_t s) {
     FP_KERNEL("k_step1_init", s, k_step1_init<<<grid_for((uint64_t)K * R), TPB, 0, s>>>((const g1a*)rows, (const g2a*)g2pow, K, R, (g1a*)A,
@@ -434,13 +536,26 @@ void step1_fold_g2(void* v, const void* xinv_mont, uint32_t K, uint32_t R, uint3
 }
 void step1_kzg(const void* A, const void* v, const void* xprev, const void* xinv_all, uint32_t K, uint32_t R,
                int log_r, void* blocks, size_t bopen_len, void* pcoef, void* q_canon, cudaStream_t s) {
-    FP_KERNEL("k_kzg", s, k_kzg<<<grid_for(K, 32), 32, 0, s>>>((const g1a*)A, (const g2a*)v, (const uint8_t*)xprev,
-                                         (const fr*)xinv_all, K, R, log_r, (uint8_t*)blocks, bopen_len,
-                                         (fr*)pcoef, (fr*)q_canon));
+    if ((2 * R - 2 + KZG_CHUNK - 1) / KZG_CHUNK > KZG_THREADS) {       // more chunks than one CTA chains
+        FP_KERNEL("k_kzg", s, k_kzg<<<grid_for(K, 32), 32, 0, s>>>((const g1a*)A, (const g2a*)v, (const uint8_t*)xprev,
+                                             (const fr*)xinv_all, K, R, log_r, (uint8_t*)blocks, bopen_len,
+                                             (fr*)pcoef, (fr*)q_canon));
+        return;
+    }
+    FP_KERNEL("k_kzg_p", s, k_kzg_p<<<K, KZG_THREADS, 0, s>>>((const g1a*)A, (const g2a*)v, (const uint8_t*)xprev,
+                                                             (const fr*)xinv_all, K, R, log_r, (uint8_t*)blocks,
+                                                             bopen_len, (fr*)pcoef, (fr*)q_canon));
 }
 void step1_w_terms(const void* g2pow, const void* q_canon, uint32_t K, uint32_t R, void* out, cudaStream_t s) {
-    FP_KERNEL("k_w_terms", s, k_w_terms<<<grid_for((uint64_t)K * 2 * R, 64), 64, 0, s>>>((const g2a*)g2pow, (const fr*)q_canon, K, R,
-                                                              (g2j*)out));
+    const uint64_t n = (uint64_t)K * 2 * R;
+    if (n <= 4096) {                    // few terms: a warp per term for latency
+        FP_KERNEL("k_w_terms_w", s, k_w_terms_w<<<(unsigned)((n + 3) / 4), 128, 0, s>>>((const g2a*)g2pow,
+                                                                                       (const fr*)q_canon, K, R,
+                                                                                       (g2j*)out));
+        return;
+    }
+    FP_KERNEL("k_w_terms", s, k_w_terms<<<grid_for(n, 64), 64, 0, s>>>((const g2a*)g2pow, (const fr*)q_canon, K, R,
+                                                                      (g2j*)out));
 }
 
 }  // namespace fpk
