@@ -49,10 +49,13 @@ def step_units(log_n: int, b: int, msm_window: int) -> dict:
     hs = [R >> j for j in range(1, lr + 1)]
     W = -(-129 // msm_window)
     return {
-        "k_final_exp_w": ("final_exp", 1 + 2 * K * lr),
-        "k_round_miller_w": ("miller_loop", sum(K * 2 * h for h in hs if K * 2 * h < 16384)),
+        "k_final_exp_c": ("final_exp", 1 + (2 * K * lr if 2 * K <= 256 else 0)),
+        "k_final_exp_w": ("final_exp", 2 * K * lr if 2 * K > 256 else 0),
+        "k_round_miller_c": ("miller_loop", sum(K * 2 * h for h in hs if K * 2 * h <= 1024)),
+        "k_round_miller_w": ("miller_loop", sum(K * 2 * h for h in hs if 1024 < K * 2 * h < 16384)),
         "k_step1_miller": ("miller_loop", sum(K * 2 * h for h in hs if K * 2 * h >= 16384)),
-        "k_commit_miller_w": ("miller_loop", R),
+        "k_commit_miller_c": ("miller_loop", R if R <= 1024 else 0),
+        "k_commit_miller_w": ("miller_loop", R if R > 1024 else 0),
         "k_sparse_g": ("g1_mul", sum(K * min(b, 2 * h) for h in hs)),
         "k_fold_w": (("g1_mul", "g2_mul"), sum(K * h for h in hs if K * h <= 4096)),
         "k_fold": (("g1_mul", "g2_mul"), sum(K * h for h in hs if K * h > 4096)),

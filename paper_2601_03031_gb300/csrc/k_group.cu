@@ -97,18 +97,11 @@ __global__ void k_g2_pair(const g2j* in, g2j* out, uint64_t n) {
     uint64_t i = gtid();
     if (i < n) out[i] = jac_add(in[2 * i], in[2 * i + 1]);
 }
-__global__ void k_fq12_pair(const fq12* in, fq12* out, uint64_t n) {
-    uint64_t i = gtid();
-    if (i < n) out[i] = fq12_mul(in[2 * i], in[2 * i + 1]);
-}
 void g1_pair_reduce(const void* in, void* out, uint64_t n, cudaStream_t s) {
     if (n) FP_KERNEL("k_g1_pair", s, k_g1_pair<<<grid_for(n), TPB, 0, s>>>((const g1j*)in, (g1j*)out, n));
 }
 void g2_pair_reduce(const void* in, void* out, uint64_t n, cudaStream_t s) {
     if (n) FP_KERNEL("k_g2_pair", s, k_g2_pair<<<grid_for(n, 64), 64, 0, s>>>((const g2j*)in, (g2j*)out, n));
-}
-void fq12_pair_reduce(const void* in, void* out, uint64_t n, cudaStream_t s) {
-    if (n) FP_KERNEL("k_fq12_pair", s, k_fq12_pair<<<grid_for(n, 64), 64, 0, s>>>((const fq12*)in, (fq12*)out, n));
 }
 
 __global__ void k_g1j_affine(const g1j* in, g1a* out, uint8_t* ser, size_t stride, uint64_t n) {

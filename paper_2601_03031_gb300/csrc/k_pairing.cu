@@ -63,8 +63,25 @@ __global__ void __launch_bounds__(128) k_final_exp_w(const fq12* in, uint32_t n,
     const uint64_t t = (uint64_t)blockIdx.x * 4 + w;
     if (t >= n) return;                                   // warp-uniform
     W12& W = sm[w];
-    w_from_tower(W.s[0], in[t]);
-    w_final_exp(W);
+    w_from_tower<1>(W.s[0], in[t]);
+    w_final_exp<1>(W);
+    if (L < 12) {
+        const int tp = w_tower_pos(L >> 1), e = L & 1;
+        const fq v = W.s[2][L];
+        if (out) reinterpret_cast<fq*>(&out[t])[2 * tp + e] = v;
+        if (ser) fq_to_be(ser + (t / per) * stride_a + (t % per) * stride_b + 96 * tp + 48 * e, v);
+    }
+}
+
+// one 128-thread block per final exponentiation (few of them: the 108 products of an Fq12
+// product take one round instead of four)
+__global__ void __launch_bounds__(128) k_final_exp_c(const fq12* in, uint32_t n, fq12* out, uint8_t* ser,
+                                                     uint32_t per, size_t stride_a, size_t stride_b) {
+    __shared__ W12 W;
+    const int L = threadIdx.x;
+    const uint64_t t = blockIdx.x;
+    w_from_tower<4>(W.s[0], in[t]);
+    w_final_exp<4>(W);
     if (L < 12) {
         const int tp = w_tower_pos(L >> 1), e = L & 1;
         const fq v = W.s[2][L];
@@ -75,9 +92,42 @@ __global__ void __launch_bounds__(128) k_final_exp_w(const fq12* in, uint32_t n,
 
 void final_exp_group(const void* in, uint32_t n, void* out, void* ser, uint32_t per, size_t stride_a,
                      size_t stride_b, cudaStream_t s) {
-    if (n) FP_KERNEL("k_final_exp_w", s, k_final_exp_w<<<(n + 3) / 4, 128, 0, s>>>((const fq12*)in, n, (fq12*)out,
-                                                                                  (uint8_t*)ser, per, stride_a,
-                                                                                  stride_b));
+    if (!n) return;
+    if (n <= 256) {
+        FP_KERNEL("k_final_exp_c", s, k_final_exp_c<<<n, 128, 0, s>>>((const fq12*)in, n, (fq12*)out, (uint8_t*)ser, per,
+                                                                     stride_a, stride_b));
+        return;
+    }
+    FP_KERNEL("k_final_exp_w", s, k_final_exp_w<<<(n + 3) / 4, 128, 0, s>>>((const fq12*)in, n, (fq12*)out,
+                                                                           (uint8_t*)ser, per, stride_a, stride_b));
+}
+
+// pairwise Fq12 products out[i] = in[2i] in[2i+1]: one 128-thread block per product when there are
+// few (latency), one thread per product otherwise
+__global__ void k_fq12_pair(const fq12* in, fq12* out, uint64_t n) {
+    uint64_t i = gtid();
+    if (i < n) out[i] = fq12_mul(in[2 * i], in[2 * i + 1]);
+}
+__global__ void __launch_bounds__(128) k_fq12_pair_c(const fq12* in, fq12* out) {
+    __shared__ W12 W;
+    const int L = threadIdx.x;
+    const uint64_t i = blockIdx.x;
+    if (L < 12) {
+        const int pos = 2 * w_tower_pos(L >> 1) + (L & 1);
+        W.s[0][L] = reinterpret_cast<const fq*>(&in[2 * i])[pos];
+        W.s[1][L] = reinterpret_cast<const fq*>(&in[2 * i + 1])[pos];
+    }
+    __syncthreads();
+    w_mul<4>(W, W.s[2], W.s[0], W.s[1]);
+    if (L < 12) reinterpret_cast<fq*>(&out[i])[2 * w_tower_pos(L >> 1) + (L & 1)] = W.s[2][L];
+}
+void fq12_pair_reduce(const void* in, void* out, uint64_t n, cudaStream_t s) {
+    if (!n) return;
+    if (n <= 2048) {
+        FP_KERNEL("k_fq12_pair_c", s, k_fq12_pair_c<<<(unsigned)n, 128, 0, s>>>((const fq12*)in, (fq12*)out));
+        return;
+    }
+    FP_KERNEL("k_fq12_pair", s, k_fq12_pair<<<grid_for(n, 64), 64, 0, s>>>((const fq12*)in, (fq12*)out, n));
 }
 
 // Miller loops, one warp per pair (warp12.cuh).  Pair t of Step 1 round h: t = (k, side, i) with
@@ -92,8 +142,8 @@ __global__ void __launch_bounds__(128) k_round_miller_w(const g1a* A, const g2a*
     const uint32_t r = (uint32_t)(t % (2 * h)), side = r / h, i = r % h;
     const g1a* Ak = A + k * R;
     const g2a* vk = v + k * R;
-    if (side == 0) w_miller(sm[w], Ak[h + i], vk[i]);
-    else w_miller(sm[w], Ak[i], vk[h + i]);
+    if (side == 0) w_miller<1>(sm[w], Ak[h + i], vk[i]);
+    else w_miller<1>(sm[w], Ak[i], vk[h + i]);
     if (L < 12) reinterpret_cast<fq*>(&out[t])[2 * w_tower_pos(L >> 1) + (L & 1)] = sm[w].f[L];
 }
 __global__ void __launch_bounds__(128) k_commit_miller_w(const g1a* rows, const g2a* g2pow, uint32_t R, fq12* out) {
@@ -101,11 +151,37 @@ __global__ void __launch_bounds__(128) k_commit_miller_w(const g1a* rows, const 
     const int w = threadIdx.x >> 5, L = threadIdx.x & 31;
     const uint64_t j = (uint64_t)blockIdx.x * 4 + w;
     if (j >= R) return;
-    w_miller(sm[w], rows[j], g2pow[2 * j]);
+    w_miller<1>(sm[w], rows[j], g2pow[2 * j]);
     if (L < 12) reinterpret_cast<fq*>(&out[j])[2 * w_tower_pos(L >> 1) + (L & 1)] = sm[w].f[L];
+}
+// the same with one 128-thread block per pair (fewer rounds per step)
+__global__ void __launch_bounds__(128) k_round_miller_c(const g1a* A, const g2a* v, uint32_t K, uint32_t R,
+                                                        uint32_t h, fq12* out) {
+    __shared__ WMill S;
+    const int L = threadIdx.x;
+    const uint64_t t = blockIdx.x;
+    const uint64_t k = t / (2 * h);
+    const uint32_t r = (uint32_t)(t % (2 * h)), side = r / h, i = r % h;
+    const g1a* Ak = A + k * R;
+    const g2a* vk = v + k * R;
+    if (side == 0) w_miller<4>(S, Ak[h + i], vk[i]);
+    else w_miller<4>(S, Ak[i], vk[h + i]);
+    if (L < 12) reinterpret_cast<fq*>(&out[t])[2 * w_tower_pos(L >> 1) + (L & 1)] = S.f[L];
+}
+__global__ void __launch_bounds__(128) k_commit_miller_c(const g1a* rows, const g2a* g2pow, fq12* out) {
+    __shared__ WMill S;
+    const int L = threadIdx.x;
+    const uint64_t j = blockIdx.x;
+    w_miller<4>(S, rows[j], g2pow[2 * j]);
+    if (L < 12) reinterpret_cast<fq*>(&out[j])[2 * w_tower_pos(L >> 1) + (L & 1)] = S.f[L];
 }
 void round_miller_w(const void* A, const void* v, uint32_t K, uint32_t R, uint32_t h, void* out, cudaStream_t s) {
     const uint64_t n = (uint64_t)K * 2 * h;
+    if (n <= 1024) {
+        FP_KERNEL("k_round_miller_c", s, k_round_miller_c<<<(unsigned)n, 128, 0, s>>>((const g1a*)A, (const g2a*)v, K, R,
+                                                                                     h, (fq12*)out));
+        return;
+    }
     FP_KERNEL("k_round_miller_w", s, k_round_miller_w<<<(unsigned)((n + 3) / 4), 128, 0, s>>>((const g1a*)A,
                                                                                              (const g2a*)v, K, R, h,
                                                                                              (fq12*)out));
@@ -127,6 +203,11 @@ void commit_miller(const void* rows, const void* g2pow, uint32_t R, void* out, c
         FP_KERNEL("k_commit_miller", s, k_commit_miller<<<grid_for(R, 64), 64, 0, s>>>((const g1a*)rows,
                                                                                        (const g2a*)g2pow, R,
                                                                                        (fq12*)out));
+        return;
+    }
+    if (R <= 1024) {
+        FP_KERNEL("k_commit_miller_c", s, k_commit_miller_c<<<R, 128, 0, s>>>((const g1a*)rows, (const g2a*)g2pow,
+                                                                             (fq12*)out));
         return;
     }
     FP_KERNEL("k_commit_miller_w", s, k_commit_miller_w<<<(R + 3) / 4, 128, 0, s>>>((const g1a*)rows,

@@ -232,7 +232,7 @@ __global__ void __launch_bounds__(128) k_fold_w(g1a* A, g2a* v, fr* bvec, const 
     const uint32_t i = (uint32_t)(t % h);
     const uint64_t lo = k * R + i, hi = k * R + h + i;
     fr_canon_words(kw, x_mont[k]);
-    const GPt<fq> r = gec_add(sm.g1[grp], lane, gec_g1_mul_proj(sm.g1[grp], lane, A[hi], kw),
+    const GPt<fq> r = gec_add(sm.g1[grp], lane, gec_g1_mul_proj_w2(sm.g1[grp], lane, A[hi], kw),
                               gec_from_affine_or_inf(A[lo].x, A[lo].y));
     g1a o;
     gec_to_affine(o.x, o.y, r);
@@ -263,7 +263,7 @@ __global__ void __launch_bounds__(128) k_sparse_g(const g1a* A, const fr* bvec, 
     const uint32_t p = sk <= 2 * h ? (uint32_t)(((uint64_t)(k0 + k) * b + t) % (2 * h)) : t;
     uint32_t kw[8];
     fr_canon_words(kw, bvec[k * R + p]);
-    const GPt<fq> r = gec_g1_mul_proj(sm[grp], lane, A[k * R + (p < h ? h + p : p - h)], kw);
+    const GPt<fq> r = gec_g1_mul_proj_w2(sm[grp], lane, A[k * R + (p < h ? h + p : p - h)], kw);
     __syncwarp();
     if (valid && lane == 0) {
         g1j o;                                                // (X : Y : Z) -> Jacobian (X Z, Y Z^2, Z)
@@ -300,6 +300,38 @@ __global__ void k_challenge(const uint8_t* blocks, size_t bopen_len, uint32_t K,
     xinv_mont[k] = xi;
     xinv_all[k * log_r + (j - 1)] = xi;
     fr_to_be(xp, x);
+}
+
+// the same with the two SHA-256 halves of HFr on two lanes of a warp per block (they are
+// independent); lane 0 finishes (a zero challenge falls back to the serial re-hash)
+__global__ void __launch_bounds__(64) k_challenge2(const uint8_t* blocks, size_t bopen_len, uint32_t K, int j,
+                                                   uint8_t* xprev, fr* x_mont, fr* xinv_mont, fr* xinv_all,
+                                                   int log_r) {
+    __shared__ uint8_t wide[2][64];
+    const int w = threadIdx.x >> 5, L = threadIdx.x & 31;
+    const uint64_t k = (uint64_t)blockIdx.x * 2 + w;
+    if (k >= K) return;                                       // warp-uniform
+    const uint8_t* rec = blocks + k * bopen_len + (size_t)(j - 1) * ROUND_BYTES;
+    uint8_t* xp = xprev + k * 32;
+    if (L < 2) {
+        sha256_ctx c;
+        sha256_init(c);
+        sha256_update(c, (const uint8_t*)"FP-x", 4);
+        sha256_byte(c, (uint8_t)L);
+        if (j > 1) sha256_update(c, xp, 32);
+        sha256_update(c, rec, ROUND_BYTES);
+        sha256_final(c, wide[w] + 32 * L);
+    }
+    __syncwarp();
+    if (L == 0) {
+        fr x = fr_from_be64(wide[w]);
+        if (fr_is_zero(x)) x = hash_to_fr_nonzero("FP-x", 4, xp, j > 1 ? 32 : 0, rec, ROUND_BYTES, nullptr, 0);
+        const fr xi = fr_inv(x);
+        x_mont[k] = x;
+        xinv_mont[k] = xi;
+        xinv_all[k * log_r + (j - 1)] = xi;
+        fr_to_be(xp, x);
+    }
 }
 
 // A_j = A_L o A_R^{x_j};  b_j = b_L + b_R / x_j
@@ -523,8 +555,9 @@ void step1_round_out_serial(const void* ml, const void* sp, uint32_t K, int j, v
 }
 void step1_challenge(void* blocks, size_t bopen_len, uint32_t K, int j, void* xprev, void* x_mont, void* xinv_mont,
                      void* xinv_all, int log_r, cudaStream_t s) {
-    FP_KERNEL("k_challenge", s, k_challenge<<<grid_for(K, 64), 64, 0, s>>>((const uint8_t*)blocks, bopen_len, K, j, (uint8_t*)xprev,
-                                               (fr*)x_mont, (fr*)xinv_mont, (fr*)xinv_all, log_r));
+    FP_KERNEL("k_challenge2", s, k_challenge2<<<(K + 1) / 2, 64, 0, s>>>((const uint8_t*)blocks, bopen_len, K, j,
+                                                                         (uint8_t*)xprev, (fr*)x_mont, (fr*)xinv_mont,
+                                                                         (fr*)xinv_all, log_r));
 }
 void step1_fold_g1(void* A, void* bvec, const void* x_mont, const void* xinv_mont, uint32_t K, uint32_t R,
                    uint32_t h, cudaStream_t s) {

@@ -490,8 +490,12 @@ fp_proofs* prove_impl(const fp_pp* pp, const fp_commit* cm, uint32_t b, uint32_t
             // final exponentiations, joined before the challenge
             cudaEvent_t ev_folded = new_event(), ev_sparse = new_event();
             step1_init(cm->rows, pp->g2pow, Kc, R, A, v, bvec, s1);
-            step1_stmt_hash(cm->C_ser, cm->rows_ser, k0, Kc, R, b, hstmt, s1);
-            step1_block_r(hstmt, k0, Kc, R, b, bvec, s1);
+            // the statement hashes and r_a only feed b: they run on s3 ahead of the first sparse terms
+            // while s1 starts the first round's Miller loops
+            check(cudaEventRecord(ev_folded, s1), "event");
+            check(cudaStreamWaitEvent(s3, ev_folded, 0), "wait");
+            step1_stmt_hash(cm->C_ser, cm->rows_ser, k0, Kc, R, b, hstmt, s3);
+            step1_block_r(hstmt, k0, Kc, R, b, bvec, s3);
             for (int j = 1; j <= lr; j++) {
                 const uint32_t h = R >> j;
                 check(cudaEventRecord(ev_folded, s1), "event");

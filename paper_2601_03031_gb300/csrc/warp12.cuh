@@ -9,8 +9,8 @@
 //   1. products: lane L computes products L, L + 32, ... of the operation's list,
 //   2. __syncwarp, then 12 (or 24) lanes form the output Fq components as sums of products,
 //   3. __syncwarp.
-// All 32 lanes run every operation (no lane-dependent synchronisation), so one warp handles one
-// Fq12 value at a time.
+// All lanes of an engine run every operation (no lane-dependent synchronisation).  An engine is one
+// warp (NW = 1) or one 128-thread block (NW = 4: a product's 108 Fq products take one round).
 //   product c = a b:        36 Fq2 products a_i b_j, each 3 Fq products (Karatsuba): 108
 //   cyclotomic squaring:    Granger-Scott, 3 Fq4 squarings of 7 Fq products each: 21
 //   Frobenius p / p^2:      20 / 10 Fq products by constants
@@ -23,8 +23,14 @@ struct W12 {
     fq h[24];           // partial sums
 };
 
-FPG_DEV void wsync() { __syncwarp(); }
-FPG_DEV int w_lane() { return (int)(threadIdx.x & 31); }
+// NW = 1: one engine per warp (__syncwarp); NW = 4: one engine per 128-thread block (__syncthreads)
+template <int NW>
+FPG_DEV void wsync() {
+    if (NW == 1) __syncwarp();
+    else __syncthreads();
+}
+template <int NW>
+FPG_DEV int w_lane() { return (int)(threadIdx.x & (32 * NW - 1)); }
 
 // tower position of flat coefficient k (0..5): even k -> c0.c(k/2), odd k -> c1.c(k/2)
 FPG_DEV int w_tower_pos(int k) { return (k & 1) ? 3 + (k >> 1) : (k >> 1); }
@@ -37,31 +43,34 @@ FPG_DEV fq fq_select(bool c, const fq& a, const fq& b) {
 }
 
 // dst (flat) <- f (tower order: six consecutive Fq2, each (c0, c1))
+template <int NW>
 FPG_DEV void w_from_tower(fq* dst, const fq12& f) {
-    const int L = w_lane();
+    const int L = w_lane<NW>();
     if (L < 12) dst[L] = reinterpret_cast<const fq*>(&f)[2 * w_tower_pos(L >> 1) + (L & 1)];
-    wsync();
+    wsync<NW>();
 }
+template <int NW>
 FPG_DEV void w_copy(fq* dst, const fq* src) {
-    const int L = w_lane();
-    wsync();
+    const int L = w_lane<NW>();
+    wsync<NW>();
     if (L < 12) dst[L] = src[L];
-    wsync();
+    wsync<NW>();
 }
 
 // out = a b (out may alias a or b)
+template <int NW>
 FPG_NOINL void w_mul(W12& W, fq* out, const fq* a, const fq* b) {
-    const int L = w_lane();
+    const int L = w_lane<NW>();
     fq zero;
     fq_zero(zero);
-    for (int t = L; t < 108; t += 32) {
+    for (int t = L; t < 108; t += 32 * NW) {
         const int q = t / 3, kind = t - 3 * q, i = q / 6, j = q - 6 * i;
         // kind 0: a_i.0 b_j.0, kind 1: a_i.1 b_j.1, kind 2: (a_i.0 + a_i.1)(b_j.0 + b_j.1)
         const fq x = fq_add(a[2 * i + (kind == 1)], kind == 2 ? a[2 * i + 1] : zero);
         const fq y = fq_add(b[2 * j + (kind == 1)], kind == 2 ? b[2 * j + 1] : zero);
         W.p[t] = fq_mul(x, y);
     }
-    wsync();
+    wsync<NW>();
     // lane L < 24: output component o = L % 12 (coefficient k, part e), terms i in [3 hf, 3 hf + 3)
     if (L < 24) {
         const int o = L % 12, hf = L / 12, k = o >> 1, e = o & 1;
@@ -80,9 +89,9 @@ FPG_NOINL void w_mul(W12& W, fq* out, const fq* a, const fq* b) {
         }
         W.h[L] = acc;
     }
-    wsync();
+    wsync<NW>();
     if (L < 12) out[L] = fq_add(W.h[L], W.h[L + 12]);
-    wsync();
+    wsync<NW>();
 }
 
 // out = a^2 for a in the cyclotomic subgroup (Granger-Scott).  Pairs (z_p, z_{p+3}), p = 0, 1, 2,
@@ -92,8 +101,9 @@ FPG_NOINL void w_mul(W12& W, fq* out, const fq* a, const fq* b) {
 // Products per pair (a = a0 + a1 u, b = b0 + b1 u): s1 = (a0 + a1)(a0 - a1), s2 = a0 a1,
 // t1 = (b0 + b1)(b0 - b1), t2 = b0 b1, k0 = a0 b0, k1 = a1 b1, k2 = (a0 + a1)(b0 + b1); then
 // a^2 = s1 + 2 s2 u, b^2 = t1 + 2 t2 u, a b = (k0 - k1) + (k2 - k0 - k1) u.
+template <int NW>
 FPG_NOINL void w_cyc_sqr(W12& W, fq* out, const fq* z) {
-    const int L = w_lane();
+    const int L = w_lane<NW>();
     if (L < 21) {
         const int p = L / 7, r = L - 7 * p;
         const fq a0 = z[2 * p], a1 = z[2 * p + 1], b0 = z[2 * p + 6], b1 = z[2 * p + 7];
@@ -109,7 +119,7 @@ FPG_NOINL void w_cyc_sqr(W12& W, fq* out, const fq* z) {
         fq y = (r == 0 || r == 2) ? ydiff : (r == 6 ? ysum : (r == 4 ? b0 : (r == 1 ? a1 : b1)));
         W.p[L] = fq_mul(x, y);
     }
-    wsync();
+    wsync<NW>();
     if (L < 12) {
         const int k = L >> 1, e = L & 1;
         // coefficient k -> (pair, kind): kind 0: 3A - 2z, 1: 3B + 2z, 2: 3 xi B + 2z
@@ -130,26 +140,28 @@ FPG_NOINL void w_cyc_sqr(W12& W, fq* out, const fq* z) {
         const fq z2 = fq_dbl(z[L]);
         W.h[L] = kind == 0 ? fq_sub(V3, z2) : fq_add(V3, z2);
     }
-    wsync();
+    wsync<NW>();
     if (L < 12) out[L] = W.h[L];
-    wsync();
+    wsync<NW>();
 }
 
 // out = conj(a) = a^(p^6): coefficients of odd k negated
+template <int NW>
 FPG_DEV void w_conj(fq* out, const fq* a) {
-    const int L = w_lane();
-    wsync();
+    const int L = w_lane<NW>();
+    wsync<NW>();
     if (L < 12) {
         const fq v = a[L];
         out[L] = ((L >> 1) & 1) ? fq_neg(v) : v;
     }
-    wsync();
+    wsync<NW>();
 }
 
 // out = a^p: coefficient k -> conj(a_k) gamma1_k (gamma1_0 = 1);
 // (x0 - x1 u)(g0 + g1 u) = (x0 g0 + x1 g1) + (x0 g1 - x1 g0) u
+template <int NW>
 FPG_NOINL void w_frob(W12& W, fq* out, const fq* a) {
-    const int L = w_lane();
+    const int L = w_lane<NW>();
     if (L < 20) {
         const int k = 1 + (L >> 2), r = L & 3;
         const fq2 g = frob1_coef(k);
@@ -157,7 +169,7 @@ FPG_NOINL void w_frob(W12& W, fq* out, const fq* a) {
         const fq y = (r == 0 || r == 3) ? g.c0 : g.c1;
         W.p[L] = fq_mul(x, y);
     }
-    wsync();
+    wsync<NW>();
     if (L < 12) {
         const int k = L >> 1, e = L & 1;
         fq v;
@@ -168,29 +180,31 @@ FPG_NOINL void w_frob(W12& W, fq* out, const fq* a) {
         }
         W.h[L] = v;
     }
-    wsync();
+    wsync<NW>();
     if (L < 12) out[L] = W.h[L];
-    wsync();
+    wsync<NW>();
 }
 
 // out = a^(p^2): coefficient k times gamma2_k in Fq (gamma2_0 = 1)
+template <int NW>
 FPG_NOINL void w_frob2(W12& W, fq* out, const fq* a) {
-    const int L = w_lane();
+    const int L = w_lane<NW>();
     if (L < 10) {
         const int k = 1 + (L >> 1);
         W.p[L] = fq_mul(a[2 * k + (L & 1)], frob2_coef(k));
     }
-    wsync();
+    wsync<NW>();
     if (L < 12) W.h[L] = L < 2 ? a[L] : W.p[L - 2];
-    wsync();
+    wsync<NW>();
     if (L < 12) out[L] = W.h[L];
-    wsync();
+    wsync<NW>();
 }
 
 // out = a^-1 (one lane, tower arithmetic)
+template <int NW>
 FPG_NOINL void w_inv(fq* out, const fq* a) {
-    const int L = w_lane();
-    wsync();
+    const int L = w_lane<NW>();
+    wsync<NW>();
     if (L == 0) {
         fq12 f;
         fq* fc = reinterpret_cast<fq*>(&f);
@@ -199,22 +213,24 @@ FPG_NOINL void w_inv(fq* out, const fq* a) {
         const fq* ic = reinterpret_cast<const fq*>(&fi);
         for (int o = 0; o < 12; o++) out[o] = ic[2 * w_tower_pos(o >> 1) + (o & 1)];
     }
-    wsync();
+    wsync<NW>();
 }
 
 // acc = base^e for base in the cyclotomic subgroup (e little-endian words, e > 0); acc != base
+template <int NW>
 FPG_NOINL void w_cyc_exp(W12& W, fq* acc, const fq* base, const uint32_t* e, int bits) {
     int i = bits - 1;
     while (i >= 0 && !((e[i >> 5] >> (i & 31)) & 1)) i--;
-    w_copy(acc, base);
+    w_copy<NW>(acc, base);
     for (i = i - 1; i >= 0; i--) {
-        w_cyc_sqr(W, acc, acc);
-        if ((e[i >> 5] >> (i & 31)) & 1) w_mul(W, acc, acc, base);
+        w_cyc_sqr<NW>(W, acc, acc);
+        if ((e[i >> 5] >> (i & 31)) & 1) w_mul<NW>(W, acc, acc, base);
     }
 }
 
 // slot 2 <- f^((p^12 - 1)/r) for f in slot 0 (slots 0..4 are used).  Easy part t = conj(f) f^-1,
 // g = t^(p^2) t; hard part g^d with d = h1 (x + p)(x^2 + p^2 - 1) + 1, h1 = (x - 1)^2 / 3, x < 0.
+template <int NW>
 FPG_NOINL void w_final_exp(W12& W) {
     fq* s0 = W.s[0];
     fq* s1 = W.s[1];
@@ -223,23 +239,23 @@ FPG_NOINL void w_final_exp(W12& W) {
     fq* s4 = W.s[4];
     const uint32_t xabs[2] = {(uint32_t)BLS_X_ABS, (uint32_t)(BLS_X_ABS >> 32)};
     const uint32_t h1[4] = {BLS_H1[0], BLS_H1[1], BLS_H1[2], BLS_H1[3]};
-    w_inv(s1, s0);                      // f^-1
-    w_conj(s0, s0);                     // conj(f)
-    w_mul(W, s2, s0, s1);               // t
-    w_frob2(W, s3, s2);
-    w_mul(W, s3, s3, s2);               // g = t^(p^2) t
-    w_cyc_exp(W, s4, s3, h1, 126);      // a = g^h1
-    w_cyc_exp(W, s0, s4, xabs, 64);     // a^|x|
-    w_conj(s0, s0);                     // a^x
-    w_frob(W, s1, s4);                  // a^p
-    w_mul(W, s0, s0, s1);               // b = a^(x + p)
-    w_cyc_exp(W, s1, s0, xabs, 64);
-    w_cyc_exp(W, s2, s1, xabs, 64);     // b^(x^2)
-    w_frob2(W, s1, s0);
-    w_mul(W, s2, s2, s1);               // b^(x^2 + p^2)
-    w_conj(s1, s0);
-    w_mul(W, s2, s2, s1);               // c = b^(x^2 + p^2 - 1)
-    w_mul(W, s2, s2, s3);               // c g
+    w_inv<NW>(s1, s0);                      // f^-1
+    w_conj<NW>(s0, s0);                     // conj(f)
+    w_mul<NW>(W, s2, s0, s1);               // t
+    w_frob2<NW>(W, s3, s2);
+    w_mul<NW>(W, s3, s3, s2);               // g = t^(p^2) t
+    w_cyc_exp<NW>(W, s4, s3, h1, 126);      // a = g^h1
+    w_cyc_exp<NW>(W, s0, s4, xabs, 64);     // a^|x|
+    w_conj<NW>(s0, s0);                     // a^x
+    w_frob<NW>(W, s1, s4);                  // a^p
+    w_mul<NW>(W, s0, s0, s1);               // b = a^(x + p)
+    w_cyc_exp<NW>(W, s1, s0, xabs, 64);
+    w_cyc_exp<NW>(W, s2, s1, xabs, 64);     // b^(x^2)
+    w_frob2<NW>(W, s1, s0);
+    w_mul<NW>(W, s2, s2, s1);               // b^(x^2 + p^2)
+    w_conj<NW>(s1, s0);
+    w_mul<NW>(W, s2, s2, s1);               // c = b^(x^2 + p^2 - 1)
+    w_mul<NW>(W, s2, s2, s3);               // c g
 }
 
 // ---------------------------------------------------------------------------------------
@@ -313,10 +329,11 @@ FPG_DEV fq wm_line_combine(const WMill& S, int o) {
     return acc;
 }
 
+template <int NW>
 FPG_NOINL void wm_dbl(WMill& S, const fq& m3x, const fq& y2) {
-    const int L = w_lane();
+    const int L = w_lane<NW>();
     // round A
-    for (int t = L; t < 69; t += 32) {
+    for (int t = L; t < 69; t += 32 * NW) {
         fq x, y;
         if (t < 12) {
             sq_ops(x, y, S.f + 2 * (t >> 1), t & 1);
@@ -333,7 +350,7 @@ FPG_NOINL void wm_dbl(WMill& S, const fq& m3x, const fq& y2) {
         }
         S.p[t] = fq_mul(x, y);
     }
-    wsync();
+    wsync<NW>();
     if (L < 12) {                                  // f^2, coefficient k, component e
         const int k = L >> 1, e = L & 1;
         fq acc;
@@ -359,7 +376,7 @@ FPG_NOINL void wm_dbl(WMill& S, const fq& m3x, const fq& y2) {
         const int v = L - 12, which = v >> 1, e = v & 1;
         S.v[v] = which < 3 ? sq_part(&S.p[57 + 2 * which], e) : kara_part(&S.p[57 + 6 + 3 * (which - 3)], e);
     }
-    wsync();
+    wsync<NW>();
     // round B
     if (L < 14) {
         const fq* XX = S.v;
@@ -386,7 +403,7 @@ FPG_NOINL void wm_dbl(WMill& S, const fq& m3x, const fq& y2) {
         else kara_ops(x, y, YY, YZ, L - 11);
         S.p[L] = fq_mul(x, y);
     }
-    wsync();
+    wsync<NW>();
     if (L < 12) {
         const int w = L >> 1, e = L & 1;
         fq r;
@@ -407,18 +424,19 @@ FPG_NOINL void wm_dbl(WMill& S, const fq& m3x, const fq& y2) {
             S.T[4 + e] = fq_dbl(fq_dbl(fq_dbl(kara_part(&S.p[11], e))));
         }
     }
-    wsync();
+    wsync<NW>();
     // round C: f^2 * line
-    for (int t = L; t < 54; t += 32) wm_line_products(S, S.g, t);
-    wsync();
+    for (int t = L; t < 54; t += 32 * NW) wm_line_products(S, S.g, t);
+    wsync<NW>();
     if (L < 12) S.h[L] = wm_line_combine(S, L);
-    wsync();
+    wsync<NW>();
     if (L < 12) S.f[L] = S.h[L];
-    wsync();
+    wsync<NW>();
 }
 
+template <int NW>
 FPG_NOINL void wm_add(WMill& S, const fq& mxP, const fq& yP) {
-    const int L = w_lane();
+    const int L = w_lane<NW>();
     const fq* X = S.T;
     const fq* Y = S.T + 2;
     const fq* Z = S.T + 4;
@@ -430,12 +448,12 @@ FPG_NOINL void wm_add(WMill& S, const fq& mxP, const fq& yP) {
         kara_ops(x, y, L < 3 ? yQ : xQ, Z, L % 3);
         S.p[L] = fq_mul(x, y);
     }
-    wsync();
+    wsync<NW>();
     if (L < 4) {                                    // theta = Y - yQ Z, lambda = X - xQ Z
         const int e = L & 1;
         S.v[L] = L < 2 ? fq_sub(Y[e], kara_part(&S.p[0], e)) : fq_sub(X[e], kara_part(&S.p[3], e));
     }
-    wsync();
+    wsync<NW>();
     const fq* th = S.v;
     const fq* la = S.v + 2;
     // round B: theta xQ, lambda yQ, -theta xP, lambda yP, theta^2, lambda^2
@@ -449,7 +467,7 @@ FPG_NOINL void wm_add(WMill& S, const fq& mxP, const fq& yP) {
         else sq_ops(x, y, la, L - 12);
         S.p[L] = fq_mul(x, y);
     }
-    wsync();
+    wsync<NW>();
     if (L < 10) {
         const int w = L >> 1, e = L & 1;
         if (w == 0) S.l[e] = fq_sub(kara_part(&S.p[0], e), kara_part(&S.p[3], e));
@@ -458,9 +476,9 @@ FPG_NOINL void wm_add(WMill& S, const fq& mxP, const fq& yP) {
         else if (w == 3) S.v[4 + e] = sq_part(&S.p[10], e);        // C = theta^2
         else S.v[6 + e] = sq_part(&S.p[12], e);                     // D = lambda^2
     }
-    wsync();
+    wsync<NW>();
     // round C: f * line (54) and E = D lambda, F = Z C, G = X D (9)
-    for (int t = L; t < 63; t += 32) {
+    for (int t = L; t < 63; t += 32 * NW) {
         if (t < 54) {
             wm_line_products(S, S.f, t);
         } else {
@@ -471,13 +489,13 @@ FPG_NOINL void wm_add(WMill& S, const fq& mxP, const fq& yP) {
             S.p[t] = fq_mul(x, y);
         }
     }
-    wsync();
+    wsync<NW>();
     if (L < 12) S.h[L] = wm_line_combine(S, L);
     else if (L < 18) {                              // E, F, G
         const int v = L - 12;
         S.v[8 + v] = kara_part(&S.p[54 + 3 * (v >> 1)], v & 1);
     }
-    wsync();
+    wsync<NW>();
     if (L < 12) S.f[L] = S.h[L];
     // round D: lambda H, theta (G - H), Y E, Z E, with H = E + F - 2 G
     const fq* E = S.v + 8;
@@ -495,7 +513,7 @@ FPG_NOINL void wm_add(WMill& S, const fq& mxP, const fq& yP) {
                  which == 0 ? H : (which == 1 ? GH : E), u % 3);
         S.p[u] = fq_mul(x, y);
     }
-    wsync();
+    wsync<NW>();
     if (L < 6) {
         const int w = L >> 1, e = L & 1;
         fq r;
@@ -504,14 +522,15 @@ FPG_NOINL void wm_add(WMill& S, const fq& mxP, const fq& yP) {
         else r = kara_part(&S.p[9], e);
         S.h[L] = r;
     }
-    wsync();
+    wsync<NW>();
     if (L < 6) S.T[L] = S.h[L];
-    wsync();
+    wsync<NW>();
 }
 
 // S.f <- conj(f_{|x|,Q}(P)) in flat order; 1 when P or Q is the identity
+template <int NW>
 FPG_NOINL void w_miller(WMill& S, g1a P, g2a Q) {
-    const int L = w_lane();
+    const int L = w_lane<NW>();
     const bool inf = g1a_is_inf(P) || g2a_is_inf(Q);
     if (inf) {
         P = g1_generator();
@@ -531,10 +550,10 @@ FPG_NOINL void w_miller(WMill& S, g1a P, g2a Q) {
         fq_zero(S.T[5]);
         S.Q[0] = Q.x.c0; S.Q[1] = Q.x.c1; S.Q[2] = Q.y.c0; S.Q[3] = Q.y.c1;
     }
-    wsync();
+    wsync<NW>();
     for (int i = 62; i >= 0; i--) {
-        wm_dbl(S, m3x, y2);
-        if ((BLS_X_ABS >> i) & 1) wm_add(S, mxP, P.y);
+        wm_dbl<NW>(S, m3x, y2);
+        if ((BLS_X_ABS >> i) & 1) wm_add<NW>(S, mxP, P.y);
     }
     if (L < 12) {
         fq one;
@@ -544,5 +563,5 @@ FPG_NOINL void w_miller(WMill& S, g1a P, g2a Q) {
         const fq v = ((L >> 1) & 1) ? fq_neg(S.f[L]) : S.f[L];       // conjugation (x < 0)
         S.f[L] = inf ? (L == 0 ? one : z) : v;
     }
-    wsync();
+    wsync<NW>();
 }
