@@ -116,15 +116,22 @@ void assemble(const ProofLayout& L, const void* rows_ser, const void* blocks, co
 size_t proof_len(const ProofLayout& L, uint64_t i);
 
 
-// ---- G1 multi-scalar multiplication (batched Pippenger; shape in msm.h)
-MsmShape msm_shape(uint64_t n, uint32_t nbatch, uint64_t npts, int c);
+// ---- multi-scalar multiplication (batched Pippenger; shape in msm.h).  G1: parts = 2, part_bits
+// = 129, fmul = 1; G2: parts = 4, part_bits = 65, fmul = 3.
+MsmShape msm_shape(uint64_t n, uint32_t nbatch, uint64_t npts, int c, int parts = 2, int part_bits = 129);
 size_t msm_scratch_bytes(const MsmShape& sh);
-int msm_window_model(uint64_t n, uint32_t nbatch);
+size_t msm_scratch_bytes_g2(const MsmShape& sh);
+int msm_window_model(uint64_t n, uint32_t nbatch, int parts = 2, int part_bits = 129, double fmul = 1.0);
 // bases: 2 npts affine G1 [P_i | -phi(P_i)]; k_canon: n nbatch x 8 u32; out_g1a / ser_out optional
 void msm_g1(const void* bases, const void* k_canon, const MsmShape& sh, void* scratch, void* out_g1a, void* ser_out,
             cudaStream_t s);
+// bases: 4 npts affine G2 [(-1)^h psi^h(Q_i)]; serialised result j at ser_out + j ser_stride
+void msm_g2(const void* bases, const void* k_canon, const MsmShape& sh, void* scratch, void* out_g2a, void* ser_out,
+            size_t ser_stride, cudaStream_t s);
 // bases table from n serialised points (err |= 1 on a bad point); or the second half from the first
 void msm_bases_load(const void* be96, uint64_t n, void* tab, uint32_t* err, cudaStream_t s);
 void msm_bases_endo(void* tab, uint64_t n, cudaStream_t s);
+// G2 bases table (4 n points) from nvalid <= n affine points, the rest identity
+void msm_bases_g2(const void* pts, uint64_t nvalid, uint64_t n, void* tab, cudaStream_t s);
 
 }  // namespace fpk

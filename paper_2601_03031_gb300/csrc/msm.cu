@@ -21,85 +21,101 @@
 // add-2008-s and dbl-2008-s-1 of the Explicit-Formulas Database (curve coefficient a = 0).
 #include <algorithm>
 #include <cmath>
+#include <type_traits>
 
 #include "group_ec.cuh"
 #include "k_common.cuh"
 
 namespace fpk {
 
-struct xyzz { fq X, Y, ZZ, ZZZ; };
+template <typename F> struct xyzz_t { F X, Y, ZZ, ZZZ; };
+using xyzz = xyzz_t<fq>;
 
-FPG_DEV void xyzz_inf(xyzz& p) { fq_zero(p.X); fq_zero(p.Y); fq_zero(p.ZZ); fq_zero(p.ZZZ); }
-FPG_DEV bool xyzz_is_inf(const xyzz& p) { return fq_is_zero(p.ZZ); }
+template <typename F> FPG_DEV void xyzz_inf(xyzz_t<F>& p) { f_set_zero(p.X); f_set_zero(p.Y); f_set_zero(p.ZZ); f_set_zero(p.ZZZ); }
+template <typename F> FPG_DEV bool xyzz_is_inf(const xyzz_t<F>& p) { return f_is_zero(p.ZZ); }
 
-FPG_NOINL xyzz xyzz_dbl(const xyzz& p) {
+template <typename F>
+FPG_NOINL xyzz_t<F> xyzz_dbl(const xyzz_t<F>& p) {
     if (xyzz_is_inf(p)) return p;
-    const fq U = fq_dbl(p.Y), V = fq_sqr(U), W = fq_mul(U, V), S = fq_mul(p.X, V);
-    const fq X2 = fq_sqr(p.X), M = fq_add(fq_dbl(X2), X2);
-    xyzz r;
-    r.X = fq_sub(fq_sqr(M), fq_dbl(S));
-    r.Y = fq_sub(fq_mul(M, fq_sub(S, r.X)), fq_mul(W, p.Y));
-    r.ZZ = fq_mul(V, p.ZZ);
-    r.ZZZ = fq_mul(W, p.ZZZ);
+    const F U = f_dbl(p.Y), V = f_sqr(U), W = f_mul(U, V), S = f_mul(p.X, V);
+    const F X2 = f_sqr(p.X), M = f_add(f_dbl(X2), X2);
+    xyzz_t<F> r;
+    r.X = f_sub(f_sqr(M), f_dbl(S));
+    r.Y = f_sub(f_mul(M, f_sub(S, r.X)), f_mul(W, p.Y));
+    r.ZZ = f_mul(V, p.ZZ);
+    r.ZZZ = f_mul(W, p.ZZZ);
     return r;
 }
-// 2 (x, y) for an affine point (y != 0 on this curve: no point of order 2)
-FPG_DEV xyzz xyzz_dbl_affine(const fq& x, const fq& y) {
-    const fq U = fq_dbl(y), V = fq_sqr(U), W = fq_mul(U, V), S = fq_mul(x, V);
-    const fq X2 = fq_sqr(x), M = fq_add(fq_dbl(X2), X2);
-    xyzz r;
-    r.X = fq_sub(fq_sqr(M), fq_dbl(S));
-    r.Y = fq_sub(fq_mul(M, fq_sub(S, r.X)), fq_mul(W, y));
+// 2 (x, y) for an affine point (y != 0 on these curves: no point of order 2)
+template <typename F>
+FPG_DEV xyzz_t<F> xyzz_dbl_affine(const F& x, const F& y) {
+    const F U = f_dbl(y), V = f_sqr(U), W = f_mul(U, V), S = f_mul(x, V);
+    const F X2 = f_sqr(x), M = f_add(f_dbl(X2), X2);
+    xyzz_t<F> r;
+    r.X = f_sub(f_sqr(M), f_dbl(S));
+    r.Y = f_sub(f_mul(M, f_sub(S, r.X)), f_mul(W, y));
     r.ZZ = V;
     r.ZZZ = W;
     return r;
 }
 // p + (x, y), the second point affine and not the identity
-FPG_NOINL xyzz xyzz_madd(const xyzz& p, const fq& x, const fq& y) {
-    xyzz r;
-    if (xyzz_is_inf(p)) { r.X = x; r.Y = y; fq_one(r.ZZ); fq_one(r.ZZZ); return r; }
-    const fq U2 = fq_mul(x, p.ZZ), S2 = fq_mul(y, p.ZZZ);
-    const fq P = fq_sub(U2, p.X), R = fq_sub(S2, p.Y);
-    if (fq_is_zero(P)) {
-        if (fq_is_zero(R)) return xyzz_dbl_affine(x, y);
+template <typename F>
+FPG_NOINL xyzz_t<F> xyzz_madd(const xyzz_t<F>& p, const F& x, const F& y) {
+    xyzz_t<F> r;
+    if (xyzz_is_inf(p)) { r.X = x; r.Y = y; f_set_one(r.ZZ); f_set_one(r.ZZZ); return r; }
+    const F U2 = f_mul(x, p.ZZ), S2 = f_mul(y, p.ZZZ);
+    const F P = f_sub(U2, p.X), R = f_sub(S2, p.Y);
+    if (f_is_zero(P)) {
+        if (f_is_zero(R)) return xyzz_dbl_affine(x, y);
         xyzz_inf(r);
         return r;
     }
-    const fq PP = fq_sqr(P), PPP = fq_mul(P, PP), Q = fq_mul(p.X, PP);
-    r.X = fq_sub(fq_sub(fq_sqr(R), PPP), fq_dbl(Q));
-    r.Y = fq_sub(fq_mul(R, fq_sub(Q, r.X)), fq_mul(p.Y, PPP));
-    r.ZZ = fq_mul(p.ZZ, PP);
-    r.ZZZ = fq_mul(p.ZZZ, PPP);
+    const F PP = f_sqr(P), PPP = f_mul(P, PP), Q = f_mul(p.X, PP);
+    r.X = f_sub(f_sub(f_sqr(R), PPP), f_dbl(Q));
+    r.Y = f_sub(f_mul(R, f_sub(Q, r.X)), f_mul(p.Y, PPP));
+    r.ZZ = f_mul(p.ZZ, PP);
+    r.ZZZ = f_mul(p.ZZZ, PPP);
     return r;
 }
-FPG_NOINL xyzz xyzz_add(const xyzz& p, const xyzz& q) {
+template <typename F>
+FPG_NOINL xyzz_t<F> xyzz_add(const xyzz_t<F>& p, const xyzz_t<F>& q) {
     if (xyzz_is_inf(p)) return q;
     if (xyzz_is_inf(q)) return p;
-    const fq U1 = fq_mul(p.X, q.ZZ), U2 = fq_mul(q.X, p.ZZ);
-    const fq S1 = fq_mul(p.Y, q.ZZZ), S2 = fq_mul(q.Y, p.ZZZ);
-    const fq P = fq_sub(U2, U1), R = fq_sub(S2, S1);
-    xyzz r;
-    if (fq_is_zero(P)) {
-        if (fq_is_zero(R)) return xyzz_dbl(p);
+    const F U1 = f_mul(p.X, q.ZZ), U2 = f_mul(q.X, p.ZZ);
+    const F S1 = f_mul(p.Y, q.ZZZ), S2 = f_mul(q.Y, p.ZZZ);
+    const F P = f_sub(U2, U1), R = f_sub(S2, S1);
+    xyzz_t<F> r;
+    if (f_is_zero(P)) {
+        if (f_is_zero(R)) return xyzz_dbl(p);
         xyzz_inf(r);
         return r;
     }
-    const fq PP = fq_sqr(P), PPP = fq_mul(P, PP), Q = fq_mul(U1, PP);
-    r.X = fq_sub(fq_sub(fq_sqr(R), PPP), fq_dbl(Q));
-    r.Y = fq_sub(fq_mul(R, fq_sub(Q, r.X)), fq_mul(S1, PPP));
-    r.ZZ = fq_mul(fq_mul(p.ZZ, q.ZZ), PP);
-    r.ZZZ = fq_mul(fq_mul(p.ZZZ, q.ZZZ), PPP);
+    const F PP = f_sqr(P), PPP = f_mul(P, PP), Q = f_mul(U1, PP);
+    r.X = f_sub(f_sub(f_sqr(R), PPP), f_dbl(Q));
+    r.Y = f_sub(f_mul(R, f_sub(Q, r.X)), f_mul(S1, PPP));
+    r.ZZ = f_mul(f_mul(p.ZZ, q.ZZ), PP);
+    r.ZZZ = f_mul(f_mul(p.ZZZ, q.ZZZ), PPP);
     return r;
 }
 // m p for m >= 1 (double-and-add from the top set bit)
-FPG_DEV xyzz xyzz_mul_small(const xyzz& p, uint32_t m) {
-    xyzz acc = p;
+template <typename F>
+FPG_DEV xyzz_t<F> xyzz_mul_small(const xyzz_t<F>& p, uint32_t m) {
+    xyzz_t<F> acc = p;
     for (int i = 30 - __clz(m); i >= 0; i--) {
         acc = xyzz_dbl(acc);
         if ((m >> i) & 1) acc = xyzz_add(acc, p);
     }
     return acc;
 }
+
+// affine point type, identity test and serialisation per group
+template <typename F> struct Aff;
+template <> struct Aff<fq> { using T = g1a; static constexpr size_t SER = G1_SER; };
+template <> struct Aff<fq2> { using T = g2a; static constexpr size_t SER = G2_SER; };
+FPG_DEV bool aff_is_inf(const g1a& p) { return g1a_is_inf(p); }
+FPG_DEV bool aff_is_inf(const g2a& p) { return g2a_is_inf(p); }
+FPG_DEV void aff_to_be(uint8_t* o, const g1a& p) { g1a_to_be(o, p); }
+FPG_DEV void aff_to_be(uint8_t* o, const g2a& p) { g2a_to_be(o, p); }
 
 // ---------------------------------------------------------------------------- digits
 FPG_DEV uint32_t win_bits(const uint32_t* a, int nw, int lo, int c) {
@@ -119,46 +135,72 @@ FPG_DEV void reduce_mod_r(uint32_t* k) {
     }
 }
 
-// calls emit(half, window, digit) for every non-zero signed digit of the GLV halves of k mod r
+// signed digits of one part a (nw words) over the shape's windows: emit(window, digit) for each
+// non-zero digit
 template <typename Emit>
-FPG_DEV void msm_digits(const fr& s, const MsmShape& sh, Emit&& emit) {
+FPG_DEV void part_digits(const uint32_t* a, int nw, const MsmShape& sh, Emit&& emit) {
+    int32_t carry = 0;
+    for (int w = 0; w < sh.W; w++) {
+        const int cw = sh.bits(w);
+        int32_t d = (int32_t)win_bits(a, nw, sh.lo(w), cw) + carry;
+        carry = d > (1 << (cw - 1));
+        if (carry) d -= 1 << cw;
+        if (d) emit(w, d);
+    }
+}
+
+// emit(part, window, digit) for every non-zero signed digit of the endomorphism parts of k mod r:
+// G1 (GLV): k = k0 + k1 |x|^2, parts below 2^128 (bases P, -phi(P));
+// G2 (GLS): k = d0 + d1 |x| + d2 |x|^2 + d3 |x|^3, parts below 2^64 (bases (-1)^h psi^h(Q))
+template <typename Emit>
+FPG_DEV void msm_digits_glv(const fr& s, const MsmShape& sh, Emit&& emit) {
     uint32_t k[8], k1[5], k0[4];
 #pragma unroll
     for (int i = 0; i < 8; i++) k[i] = s.v[i];
     reduce_mod_r(k);
     div_by_const<4, 5>(k1, k0, k, GLV_D, GLV_BARRETT);
-    for (int h = 0; h < 2; h++) {
-        const uint32_t* a = h ? k1 : k0;
-        const int nw = h ? 5 : 4;
-        int32_t carry = 0;
-        for (int w = 0; w < sh.W; w++) {
-            const int cw = sh.bits(w);
-            int32_t d = (int32_t)win_bits(a, nw, sh.lo(w), cw) + carry;
-            carry = d > (1 << (cw - 1));
-            if (carry) d -= 1 << cw;
-            if (d) emit(h, w, d);
-        }
+    part_digits(k0, 4, sh, [&](int w, int32_t d) { emit(0, w, d); });
+    part_digits(k1, 5, sh, [&](int w, int32_t d) { emit(1, w, d); });
+}
+template <typename Emit>
+FPG_DEV void msm_digits_gls(const fr& s, const MsmShape& sh, Emit&& emit) {
+    uint32_t k[8], q[7], d[2], t8[8];
+#pragma unroll
+    for (int i = 0; i < 8; i++) k[i] = s.v[i];
+    reduce_mod_r(k);
+    for (int h = 0; h < 3; h++) {
+        div_by_const<2, 7>(q, d, k, GLS_D, GLS_BARRETT);
+        part_digits(d, 2, sh, [&](int w, int32_t dd) { emit(h, w, dd); });
+        for (int i = 0; i < 8; i++) t8[i] = i < 7 ? q[i] : 0;
+        for (int i = 0; i < 8; i++) k[i] = t8[i];
     }
+    part_digits(k, 2, sh, [&](int w, int32_t dd) { emit(3, w, dd); });
 }
 
+template <typename F>
 __global__ void k_msm_count(const fr* k, MsmShape sh, uint32_t* counts) {
     const uint64_t t = gtid();
     if (t >= sh.n * sh.nbatch) return;
     const uint64_t base = (t / sh.n) * sh.KW;
-    msm_digits(k[t], sh, [&](int, int w, int32_t d) {
+    auto emit = [&](int, int w, int32_t d) {
         atomicAdd(&counts[base + sh.off(w) + (uint32_t)(d < 0 ? -d : d) - 1], 1u);
-    });
+    };
+    if constexpr (std::is_same<F, fq>::value) msm_digits_glv(k[t], sh, emit);
+    else msm_digits_gls(k[t], sh, emit);
 }
 
+template <typename F>
 __global__ void k_msm_scatter(const fr* k, MsmShape sh, uint32_t* cursor, uint32_t* list) {
     const uint64_t t = gtid();
     if (t >= sh.n * sh.nbatch) return;
     const uint64_t base = (t / sh.n) * sh.KW;
     const uint32_t pidx = (uint32_t)(t % sh.npts);
-    msm_digits(k[t], sh, [&](int h, int w, int32_t d) {
+    auto emit = [&](int h, int w, int32_t d) {
         const uint32_t pos = atomicAdd(&cursor[base + sh.off(w) + (uint32_t)(d < 0 ? -d : d) - 1], 1u);
-        list[pos] = (pidx + (h ? (uint32_t)sh.npts : 0u)) | (d < 0 ? 0x80000000u : 0u);
-    });
+        list[pos] = (pidx + (uint32_t)h * (uint32_t)sh.npts) | (d < 0 ? 0x80000000u : 0u);
+    };
+    if constexpr (std::is_same<F, fq>::value) msm_digits_glv(k[t], sh, emit);
+    else msm_digits_gls(k[t], sh, emit);
 }
 
 // ---------------------------------------------------------------------------- scan
@@ -202,32 +244,34 @@ static void exclusive_scan(const uint32_t* in, uint32_t* out, uint64_t n, uint32
 }
 
 // ---------------------------------------------------------------------------- buckets
-__global__ void __launch_bounds__(128) k_msm_bucket(const g1a* pts, MsmShape sh, const uint32_t* offsets,
-                                                    const uint32_t* counts, const uint32_t* list, xyzz* buckets) {
+template <typename F>
+__global__ void __launch_bounds__(128) k_msm_bucket(const typename Aff<F>::T* pts, MsmShape sh, const uint32_t* offsets,
+                                                    const uint32_t* counts, const uint32_t* list, xyzz_t<F>* buckets) {
     const uint64_t key = gtid();
     if (key >= sh.nkeys()) return;
     const uint32_t off = offsets[key], cnt = counts[key];
-    xyzz acc;
+    xyzz_t<F> acc;
     xyzz_inf(acc);
     for (uint32_t q = 0; q < cnt; q++) {
         const uint32_t e = list[off + q];
-        const g1a p = pts[e & 0x7fffffffu];
-        if (g1a_is_inf(p)) continue;
-        acc = xyzz_madd(acc, p.x, (e >> 31) ? fq_neg(p.y) : p.y);
+        const typename Aff<F>::T p = pts[e & 0x7fffffffu];
+        if (aff_is_inf(p)) continue;
+        acc = xyzz_madd(acc, p.x, (e >> 31) ? f_neg(p.y) : p.y);
     }
     buckets[key] = acc;
 }
 
 // segment s of window w of batch j: its L = B_w / S buckets b in [s L, (s + 1) L) give
 // sum_b (b + 1) B_b
-__global__ void __launch_bounds__(128) k_msm_segment(MsmShape sh, const xyzz* buckets, xyzz* segs) {
+template <typename F>
+__global__ void __launch_bounds__(128) k_msm_segment(MsmShape sh, const xyzz_t<F>* buckets, xyzz_t<F>* segs) {
     const uint64_t t = gtid();
     if (t >= sh.nsegs()) return;
     const uint64_t j = t / ((uint64_t)sh.W * sh.S);
     const int w = (int)((t / sh.S) % sh.W);
     const uint32_t s = (uint32_t)(t % sh.S), L = sh.buckets(w) / sh.S;
-    const xyzz* bk = buckets + j * sh.KW + sh.off(w) + (uint64_t)s * L;
-    xyzz run, acc;
+    const xyzz_t<F>* bk = buckets + j * sh.KW + sh.off(w) + (uint64_t)s * L;
+    xyzz_t<F> run, acc;
     xyzz_inf(run);
     xyzz_inf(acc);
     for (int b = (int)L - 1; b >= 0; b--) {
@@ -238,44 +282,49 @@ __global__ void __launch_bounds__(128) k_msm_segment(MsmShape sh, const xyzz* bu
     segs[t] = acc;
 }
 
-__global__ void k_msm_pair(const xyzz* in, xyzz* out, uint64_t n) {
+template <typename F>
+__global__ void k_msm_pair(const xyzz_t<F>* in, xyzz_t<F>* out, uint64_t n) {
     const uint64_t i = gtid();
     if (i < n) out[i] = xyzz_add(in[2 * i], in[2 * i + 1]);
 }
 
 // window sums to homogeneous projective (X ZZZ : Y ZZ : ZZ ZZZ), identity (0 : 1 : 0)
-__global__ void k_msm_to_proj(const xyzz* in, GPt<fq>* out, uint64_t n) {
+template <typename F>
+__global__ void k_msm_to_proj(const xyzz_t<F>* in, GPt<F>* out, uint64_t n) {
     const uint64_t i = gtid();
     if (i >= n) return;
-    const xyzz p = in[i];
-    GPt<fq> r;
+    const xyzz_t<F> p = in[i];
+    GPt<F> r;
     if (xyzz_is_inf(p)) {
-        r = gec_identity<fq>();
+        r = gec_identity<F>();
     } else {
-        r.X = fq_mul(p.X, p.ZZZ);
-        r.Y = fq_mul(p.Y, p.ZZ);
-        r.Z = fq_mul(p.ZZ, p.ZZZ);
+        r.X = f_mul(p.X, p.ZZZ);
+        r.Y = f_mul(p.Y, p.ZZ);
+        r.Z = f_mul(p.ZZ, p.ZZZ);
     }
     out[i] = r;
 }
 
-// per batch, on 8 lanes: sum_w 2^(lo_w) S_w by Horner from the top window, then affine
-__global__ void __launch_bounds__(64) k_msm_final(MsmShape sh, const GPt<fq>* win, g1a* out, uint8_t* ser) {
-    __shared__ GEc<fq> sm[8];
+// per batch, on 8 lanes: sum_w 2^(lo_w) S_w by Horner from the top window, then affine; the
+// serialised result of batch j goes to ser + j ser_stride
+template <typename F>
+__global__ void __launch_bounds__(64) k_msm_final(MsmShape sh, const GPt<F>* win, typename Aff<F>::T* out, uint8_t* ser,
+                                                  size_t ser_stride) {
+    __shared__ GEc<F> sm[8];
     const int grp = threadIdx.x >> 3, lane = threadIdx.x & 7;
     const uint64_t j0 = (uint64_t)blockIdx.x * 8 + grp;
     const bool valid = j0 < sh.nbatch;
     const uint64_t j = valid ? j0 : 0;                // idle groups repeat batch 0's work
-    GPt<fq> acc = win[j * sh.W + sh.W - 1];
+    GPt<F> acc = win[j * sh.W + sh.W - 1];
     for (int w = sh.W - 2; w >= 0; w--) {
         for (int q = 0; q < sh.bits(w); q++) acc = gec_dbl(sm[grp], lane, acc);
         acc = gec_add(sm[grp], lane, acc, win[j * sh.W + w]);
     }
-    g1a a;
+    typename Aff<F>::T a;
     gec_to_affine(a.x, a.y, acc);
     if (valid && lane == 0) {
         if (out) out[j] = a;
-        if (ser) g1a_to_be(ser + j * G1_SER, a);
+        if (ser) aff_to_be(ser + j * ser_stride, a);
     }
 }
 
@@ -344,15 +393,38 @@ void msm_bases_endo(void* tab, uint64_t n, cudaStream_t s) {
     if (n) FP_KERNEL("k_bases_endo", s, k_bases_endo<<<grid_for(n, 128), 128, 0, s>>>((g1a*)tab, n));
 }
 
+// G2 bases table for the GLS parts: tab[h n + i] = (-1)^h psi^h(Q_i) for h < 4; entries i >= nvalid
+// are the identity (padding)
+__global__ void k_bases_g2(const g2a* pts, uint64_t nvalid, uint64_t n, g2a* tab) {
+    const uint64_t i = gtid();
+    if (i >= n) return;
+    g2a b;
+    fq2_zero(b.x);
+    fq2_zero(b.y);
+    if (i < nvalid) b = pts[i];
+    const bool inf = g2a_is_inf(b);
+    for (int h = 0; h < 4; h++) {
+        if (h && !inf) b = g2_psi(b);
+        g2a o = b;
+        if ((h & 1) && !inf) o.y = fq2_neg(o.y);
+        tab[h * n + i] = o;
+    }
+}
+void msm_bases_g2(const void* pts, uint64_t nvalid, uint64_t n, void* tab, cudaStream_t s) {
+    if (n) FP_KERNEL("k_bases_g2", s, k_bases_g2<<<grid_for(n, 128), 128, 0, s>>>((const g2a*)pts, nvalid, n,
+                                                                                 (g2a*)tab));
+}
+
 // ---------------------------------------------------------------------------- shape and driver
-MsmShape msm_shape(uint64_t n, uint32_t nbatch, uint64_t npts, int c) {
+MsmShape msm_shape(uint64_t n, uint32_t nbatch, uint64_t npts, int c, int parts, int part_bits) {
     MsmShape sh;
     sh.n = n;
     sh.nbatch = nbatch;
     sh.npts = npts;
-    sh.W = (129 + c - 1) / c;
-    sh.c = (129 + sh.W - 1) / sh.W;                    // balanced widths: c or c - 1
-    sh.n_hi = 129 - sh.W * (sh.c - 1);
+    sh.H = parts;
+    sh.W = (part_bits + c - 1) / c;
+    sh.c = (part_bits + sh.W - 1) / sh.W;              // balanced widths: c or c - 1
+    sh.n_hi = part_bits - sh.W * (sh.c - 1);
     sh.KW = sh.off(sh.W);
     // segments of at least 4 buckets in the narrowest window, at most about 2^15 segment threads
     uint32_t S = sh.buckets(sh.W - 1);
@@ -362,34 +434,38 @@ MsmShape msm_shape(uint64_t n, uint32_t nbatch, uint64_t npts, int c) {
     return sh;
 }
 
-size_t msm_scratch_bytes(const MsmShape& sh) {
+template <typename F>
+static size_t scratch_bytes(const MsmShape& sh) {
     const uint64_t nk = sh.nkeys();
     auto r = [](size_t b) { return (b + 255) & ~(size_t)255; };
     size_t b = 3 * r(nk * 4) + r(scan_tmp_words(nk) * 4);
     b += r(sh.entries_max() * 4);
-    b += r(nk * sizeof(xyzz));
-    b += 2 * r(sh.nsegs() * sizeof(xyzz));
-    b += r((uint64_t)sh.nbatch * sh.W * sizeof(GPt<fq>));
+    b += r(nk * sizeof(xyzz_t<F>));
+    b += 2 * r(sh.nsegs() * sizeof(xyzz_t<F>));
+    b += r((uint64_t)sh.nbatch * sh.W * sizeof(GPt<F>));
     return b;
 }
+size_t msm_scratch_bytes(const MsmShape& sh) { return scratch_bytes<fq>(sh); }
+size_t msm_scratch_bytes_g2(const MsmShape& sh) { return scratch_bytes<fq2>(sh); }
 
 // Window size from a cost model: per phase the larger of the throughput time (about 1.9e10 Fq
-// products/s over the GPU) and the latency of one thread's dependent chain (about 1.3 us per
-// product); mixed addition 10 products, addition 14, group doubling/addition about 2 x 1.5.
-int msm_window_model(uint64_t n, uint32_t nbatch) {
-    const double tp = 1.0 / 1.9e10, lat = 2.7e-6;
+// products/s over the GPU) and the latency of one thread's dependent chain (about 2.7 us per
+// product); mixed addition 10 field products, addition 14, group doubling/addition about
+// 2 x 1.5 (fmul = Fq products per field product: 1 on G1, 3 on G2).
+int msm_window_model(uint64_t n, uint32_t nbatch, int parts, int part_bits, double fmul) {
+    const double tp = fmul / 1.9e10, lat = fmul * 2.7e-6;
     int best = 8;
     double bestt = 1e300;
     for (int c = 4; c <= 16; c++) {
-        const MsmShape sh = msm_shape(n, nbatch, n, c);
+        const MsmShape sh = msm_shape(n, nbatch, n, c, parts, part_bits);
         if (sh.c != c || sh.nkeys() > (1ull << 28) || sh.entries_max() > 0xffffffffull) continue;
-        const double entries = 2.0 * (double)n * nbatch * sh.W;
+        const double entries = (double)parts * n * nbatch * sh.W;
         const double per_bucket = entries / (double)sh.nkeys();
         const double t_bucket = std::max(entries * 10 * tp, per_bucket * 10 * lat);
         const double L = (double)(sh.buckets(0) / sh.S);
         const double t_seg = std::max((double)sh.nkeys() * 2 * 14 * tp, (2 * L + 1.5 * (c - 1)) * 14 * lat);
         const double t_pair = std::log2((double)sh.S) * 14 * lat;
-        const double t_final = 129.0 * 2 * 1.5 * lat;
+        const double t_final = (double)part_bits * 2 * 1.5 * lat;
         const double t = t_bucket + t_seg + t_pair + t_final;
         if (t < bestt) {
             bestt = t;
@@ -399,8 +475,10 @@ int msm_window_model(uint64_t n, uint32_t nbatch) {
     return best;
 }
 
-void msm_g1(const void* bases, const void* k_canon, const MsmShape& sh, void* scratch, void* out_g1a, void* ser_out,
-            cudaStream_t s) {
+template <typename F>
+static void msm_run(const void* bases, const void* k_canon, const MsmShape& sh, void* scratch, void* out_aff,
+                    void* ser_out, size_t ser_stride, cudaStream_t s) {
+    using X = xyzz_t<F>;
     const uint64_t nk = sh.nkeys(), nseg = sh.nsegs(), nwin = (uint64_t)sh.nbatch * sh.W;
     uint8_t* p = (uint8_t*)scratch;
     auto take = [&](size_t bytes) {
@@ -413,34 +491,45 @@ void msm_g1(const void* bases, const void* k_canon, const MsmShape& sh, void* sc
     uint32_t* cursor = (uint32_t*)take(nk * 4);
     uint32_t* scan_tmp = (uint32_t*)take(scan_tmp_words(nk) * 4);
     uint32_t* list = (uint32_t*)take(sh.entries_max() * 4);
-    xyzz* buckets = (xyzz*)take(nk * sizeof(xyzz));
-    xyzz* seg_a = (xyzz*)take(nseg * sizeof(xyzz));
-    xyzz* seg_b = (xyzz*)take(nseg * sizeof(xyzz));
-    GPt<fq>* proj = (GPt<fq>*)take(nwin * sizeof(GPt<fq>));
+    X* buckets = (X*)take(nk * sizeof(X));
+    X* seg_a = (X*)take(nseg * sizeof(X));
+    X* seg_b = (X*)take(nseg * sizeof(X));
+    GPt<F>* proj = (GPt<F>*)take(nwin * sizeof(GPt<F>));
     const uint64_t terms = sh.n * sh.nbatch;
     cudaMemsetAsync(counts, 0, nk * 4, s);
     if (terms) {
         FP_KERNEL("k_msm_count", s,
-                  k_msm_count<<<grid_for(terms, 128), 128, 0, s>>>((const fr*)k_canon, sh, counts));
+                  k_msm_count<F><<<grid_for(terms, 128), 128, 0, s>>>((const fr*)k_canon, sh, counts));
     }
     exclusive_scan(counts, offsets, nk, scan_tmp, s);
     cudaMemcpyAsync(cursor, offsets, nk * 4, cudaMemcpyDeviceToDevice, s);
     if (terms) {
         FP_KERNEL("k_msm_scatter", s,
-                  k_msm_scatter<<<grid_for(terms, 128), 128, 0, s>>>((const fr*)k_canon, sh, cursor, list));
+                  k_msm_scatter<F><<<grid_for(terms, 128), 128, 0, s>>>((const fr*)k_canon, sh, cursor, list));
     }
-    FP_KERNEL("k_msm_bucket", s, k_msm_bucket<<<grid_for(nk, 128), 128, 0, s>>>((const g1a*)bases, sh, offsets,
-                                                                               counts, list, buckets));
-    FP_KERNEL("k_msm_segment", s, k_msm_segment<<<grid_for(nseg, 128), 128, 0, s>>>(sh, buckets, seg_a));
-    xyzz* a = seg_a;
-    xyzz* b = seg_b;
+    FP_KERNEL("k_msm_bucket", s,
+              k_msm_bucket<F><<<grid_for(nk, 128), 128, 0, s>>>((const typename Aff<F>::T*)bases, sh, offsets, counts,
+                                                               list, buckets));
+    FP_KERNEL("k_msm_segment", s, k_msm_segment<F><<<grid_for(nseg, 128), 128, 0, s>>>(sh, buckets, seg_a));
+    X* a = seg_a;
+    X* b = seg_b;
     for (uint64_t m = nseg; m > nwin; m /= 2) {
-        FP_KERNEL("k_msm_pair", s, k_msm_pair<<<grid_for(m / 2, 128), 128, 0, s>>>(a, b, m / 2));
+        FP_KERNEL("k_msm_pair", s, k_msm_pair<F><<<grid_for(m / 2, 128), 128, 0, s>>>(a, b, m / 2));
         std::swap(a, b);
     }
-    FP_KERNEL("k_msm_to_proj", s, k_msm_to_proj<<<grid_for(nwin, 128), 128, 0, s>>>(a, proj, nwin));
-    FP_KERNEL("k_msm_final", s, k_msm_final<<<grid_for(sh.nbatch, 8), 64, 0, s>>>(sh, proj, (g1a*)out_g1a,
-                                                                                  (uint8_t*)ser_out));
+    FP_KERNEL("k_msm_to_proj", s, k_msm_to_proj<F><<<grid_for(nwin, 128), 128, 0, s>>>(a, proj, nwin));
+    FP_KERNEL("k_msm_final", s,
+              k_msm_final<F><<<grid_for(sh.nbatch, 8), 64, 0, s>>>(sh, proj, (typename Aff<F>::T*)out_aff,
+                                                                  (uint8_t*)ser_out, ser_stride));
+}
+
+void msm_g1(const void* bases, const void* k_canon, const MsmShape& sh, void* scratch, void* out_g1a, void* ser_out,
+            cudaStream_t s) {
+    msm_run<fq>(bases, k_canon, sh, scratch, out_g1a, ser_out, G1_SER, s);
+}
+void msm_g2(const void* bases, const void* k_canon, const MsmShape& sh, void* scratch, void* out_g2a, void* ser_out,
+            size_t ser_stride, cudaStream_t s) {
+    msm_run<fq2>(bases, k_canon, sh, scratch, out_g2a, ser_out, ser_stride, s);
 }
 
 }  // namespace fpk

@@ -1,8 +1,8 @@
-// Shape of the batched G1 multi-scalar multiplication (host and device).
+// Shape of the batched multi-scalar multiplications (host and device).
 //
-// Each scalar is reduced mod r and split by GLV into two halves below 2^128.  The 129 bits of a
-// half (one spare bit for the carry of the signed digits) are cut into W windows of nearly equal
-// width: the first n_hi windows have c bits, the others c - 1, so no window is left with a few
+// Each scalar is reduced mod r and split by the endomorphism: on G1 (GLV) into two parts below
+// 2^128, on G2 (GLS) into four parts below 2^64.  The bits of a part plus one spare bit for the
+// carry of the signed digits (129 or 65) are cut into W windows of nearly equal width: the first n_hi windows have c bits, the others c - 1, so no window is left with a few
 // high bits whose digits crowd into a few buckets.  Window w has B_w = 2^(c_w - 1) buckets, and
 // the buckets of one batch are laid out window after window (KW keys per batch).
 #pragma once
@@ -14,7 +14,8 @@ struct MsmShape {
     uint64_t n;         // terms per batch
     uint32_t nbatch;    // independent sums
     uint64_t npts;      // term i of batch j uses base (j n + i) mod npts
-    int c, W, n_hi;     // widest window, windows per half, windows of width c
+    int H;              // endomorphism parts per scalar (2 on G1, 4 on G2): bases table [H][npts]
+    int c, W, n_hi;     // widest window, windows per part, windows of width c
     uint32_t KW;        // buckets per batch, all windows
     uint32_t S;         // segments per window in the bucket reduction
     __host__ __device__ int bits(int w) const { return w < n_hi ? c : c - 1; }
@@ -25,7 +26,7 @@ struct MsmShape {
     }
     __host__ __device__ uint64_t nkeys() const { return (uint64_t)nbatch * KW; }
     __host__ __device__ uint64_t nsegs() const { return (uint64_t)nbatch * W * S; }
-    __host__ __device__ uint64_t entries_max() const { return 2ull * n * nbatch * W; }
+    __host__ __device__ uint64_t entries_max() const { return (uint64_t)H * n * nbatch * W; }
 };
 
 }  // namespace fpk

@@ -21,6 +21,7 @@ struct fp_pp {
     const fp_pp* parent = nullptr;  // views share the parent's tables (all but lam_tab)
     void* lam = nullptr;      // G1 affine, 2M - 1: Lambda_t at offset 2^t - 1
     void* lam_tab = nullptr;  // G1 affine, 2M: Lambda_{l_c} and its GLV partners (MSM bases)
+    void* g2w_tab = nullptr;  // G2 affine, 4 x 2R: (-1)^h psi^h(g2^{beta^i}) (W-proof MSM bases)
     void* g1beta = nullptr;   // G1 affine
     void* g2pow = nullptr;    // G2 affine, 2R - 1: g2^{beta^i}
     void* g2tau = nullptr;    // G2 affine, l_c
@@ -214,8 +215,10 @@ fp_status vc_setup(uint32_t log_n, uint32_t b, uint64_t seed, void* stream, fp_p
             check(cudaMemcpyAsync(pp->lam_tab, (uint8_t*)pp->lam + ((size_t)M - 1) * G1A_BYTES, (size_t)M * G1A_BYTES,
                                   cudaMemcpyDeviceToDevice, s), "D2D");
             msm_bases_endo(pp->lam_tab, M, s);
+            pp->g2w_tab = dalloc(8 * (size_t)R * G2A_BYTES, s);
             g1_gen_mul(beta_s, 1, pp->g1beta, s);
             g2_gen_mul(pow_s, 2 * R - 1, pp->g2pow, s);
+            msm_bases_g2(pp->g2pow, 2 * R - 1, 2 * R, pp->g2w_tab, s);
             g2_gen_mul(tau_s, log_c, pp->g2tau, s);
             check_launch("vc_setup kernels");
             // the trapdoor and its scalar tables are cleared before release
@@ -378,6 +381,8 @@ fp_status vc_pp_view(const fp_pp* pp, uint32_t log_n, fp_pp** out) {
             check(cudaMemcpyAsync(v->lam_tab, (uint8_t*)root->lam + ((size_t)M - 1) * G1A_BYTES, (size_t)M * G1A_BYTES,
                                   cudaMemcpyDeviceToDevice, s), "D2D");
             msm_bases_endo(v->lam_tab, M, s);
+            v->g2w_tab = dalloc(8 * (size_t)R * G2A_BYTES, s);
+            msm_bases_g2(v->g2pow, 2 * R - 1, 2 * R, v->g2w_tab, s);
             check_launch("vc_pp_view");
             check(cudaStreamSynchronize(s), "vc_pp_view");
         } catch (...) {
@@ -453,8 +458,18 @@ fp_proofs* prove_impl(const fp_pp* pp, const fp_commit* cm, uint32_t b, uint32_t
             void* sp2 = T((KR / 2 + 1) * G1J_BYTES);
             void* pcoef = T((size_t)Kc * (2 * R - 1) * FR_BYTES);
             void* q = T((size_t)Kc * 2 * R * FR_BYTES);
-            void* wt = T((size_t)Kc * 2 * R * G2J_BYTES);
-            void* wt2 = T(((size_t)Kc * R + 1) * G2J_BYTES);
+            // W proofs: one batched G2 MSM over the shared bases g2^{beta^i} when there are many
+            // terms, else one scalar multiplication per term and pairwise sums (latency)
+            const bool w_msm = (uint64_t)Kc * 2 * R > 4096;
+            void *wt = nullptr, *wt2 = nullptr, *wscr = nullptr;
+            MsmShape wsh{};
+            if (w_msm) {
+                wsh = msm_shape(2 * R, Kc, 2 * R, msm_window_model(2 * R, Kc, 4, 65, 3.0), 4, 65);
+                wscr = T(msm_scratch_bytes_g2(wsh));
+            } else {
+                wt = T((size_t)Kc * 2 * R * G2J_BYTES);
+                wt2 = T(((size_t)Kc * R + 1) * G2J_BYTES);
+            }
             const Streams st = streams(s);
             cudaStream_t s2 = st.lo, s1 = st.hi, s3 = st.sp;
             cudaEvent_t ev_fork = new_event(), ev_join = new_event(), ev_join1 = new_event();
@@ -512,9 +527,14 @@ fp_proofs* prove_impl(const fp_pp* pp, const fp_commit* cm, uint32_t b, uint32_t
                 step1_fold(A, v, bvec, x_mont, xinv_mont, Kc, R, h, s1);
             }
             step1_kzg(A, v, xprev, xinv_all, Kc, R, lr, blocks1, blen, pcoef, q, s1);
-            step1_w_terms(pp->g2pow, q, Kc, R, wt, s1);
-            void* wr = reduce_pairs(wt, wt2, (uint64_t)Kc * 2 * R, Kc, g2_pair_reduce, s1);
-            g2j_to_affine(wr, nullptr, (uint8_t*)blocks1 + (size_t)lr * ROUND_BYTES + G1_SER + G2_SER, blen, Kc, s1);
+            uint8_t* w_out = (uint8_t*)blocks1 + (size_t)lr * ROUND_BYTES + G1_SER + G2_SER;
+            if (w_msm) {
+                msm_g2(pp->g2w_tab, q, wsh, wscr, nullptr, w_out, blen, s1);
+            } else {
+                step1_w_terms(pp->g2pow, q, Kc, R, wt, s1);
+                void* wr = reduce_pairs(wt, wt2, (uint64_t)Kc * 2 * R, Kc, g2_pair_reduce, s1);
+                g2j_to_affine(wr, nullptr, w_out, blen, Kc, s1);
+            }
             check(cudaEventRecord(ev_join1, s1), "event");
             check(cudaStreamWaitEvent(s, ev_join1, 0), "join");
             cudaEventDestroy(ev_folded);
@@ -957,6 +977,7 @@ void fp_pp_free(fp_pp* pp) {
     if (!pp) return;
     cudaDeviceSynchronize();
     cudaFree(pp->lam_tab);
+    cudaFree(pp->g2w_tab);
     if (!pp->parent) {
         cudaFree(pp->lam); cudaFree(pp->g1beta); cudaFree(pp->g2pow); cudaFree(pp->g2tau);
     }
