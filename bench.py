@@ -59,7 +59,7 @@ def step_units(log_n: int, b: int, msm_window: int) -> dict:
         "k_sparse_g": ("g1_mul", sum(K * min(b, 2 * h) for h in hs)),
         "k_fold_w": (("g1_mul", "g2_mul"), sum(K * h for h in hs if K * h <= 4096)),
         "k_fold": (("g1_mul", "g2_mul"), sum(K * h for h in hs if K * h > 4096)),
-        "k_msm_bucket": ("msm_madd", 2 * R * M * W),
+        "k_msm_chunk": ("msm_madd", 2 * R * M * W),
         "k_w_terms": ("g2_mul", K * (2 * R - 2)),
         "k_pst_terms": ("g1_mul", M * lc // 2),
     }

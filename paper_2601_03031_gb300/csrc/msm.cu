@@ -11,7 +11,8 @@
 //      |d| - 1) selects a bucket; a negative digit negates the base.
 //   2. counting sort of the (base, window) entries by key: histogram with atomics, exclusive scan,
 //      scatter of base index | sign bit;
-//   3. one thread per bucket sums its bases with XYZZ mixed additions;
+//   3. bucket sums with XYZZ mixed additions, load-balanced: fixed-size chunks of the sorted entry
+//      list, one thread each, partial sums of runs that cross chunks added afterwards;
 //   4. bucket reduction sum_b (b + 1) B_b: the buckets of a window are cut into S segments;
 //      a thread per segment forms its running sums plus (start) x (segment sum), and the segment
 //      results are added pairwise;
@@ -190,14 +191,16 @@ __global__ void k_msm_count(const fr* k, MsmShape sh, uint32_t* counts) {
 }
 
 template <typename F>
-__global__ void k_msm_scatter(const fr* k, MsmShape sh, uint32_t* cursor, uint32_t* list) {
+__global__ void k_msm_scatter(const fr* k, MsmShape sh, uint32_t* cursor, uint32_t* list, uint32_t* keys) {
     const uint64_t t = gtid();
     if (t >= sh.n * sh.nbatch) return;
     const uint64_t base = (t / sh.n) * sh.KW;
     const uint32_t pidx = (uint32_t)(t % sh.npts);
     auto emit = [&](int h, int w, int32_t d) {
-        const uint32_t pos = atomicAdd(&cursor[base + sh.off(w) + (uint32_t)(d < 0 ? -d : d) - 1], 1u);
+        const uint32_t key = (uint32_t)(base + sh.off(w) + (uint32_t)(d < 0 ? -d : d) - 1);
+        const uint32_t pos = atomicAdd(&cursor[key], 1u);
         list[pos] = (pidx + (uint32_t)h * (uint32_t)sh.npts) | (d < 0 ? 0x80000000u : 0u);
+        keys[pos] = key;
     };
     if constexpr (std::is_same<F, fq>::value) msm_digits_glv(k[t], sh, emit);
     else msm_digits_gls(k[t], sh, emit);
@@ -244,21 +247,62 @@ static void exclusive_scan(const uint32_t* in, uint32_t* out, uint64_t n, uint32
 }
 
 // ---------------------------------------------------------------------------- buckets
+// Load-balanced bucket sums: the sorted entry list (E entries, E = end of the last key's run) is cut
+// into chunks of T consecutive entries, one thread each.  A thread sums each run of equal keys in its
+// chunk; a run that neither started in the previous chunk nor continues into the next is the whole
+// bucket and is stored there; the partial sum of a chunk's first run, when that run started
+// earlier, goes to head[c], and the partial of its last run, when it continues, to tail[c] (a
+// chunk inside one run stores it in head[c]).  k_msm_fixup then completes those buckets.
+// Buckets without entries stay the identity (zeroed by the caller).
 template <typename F>
-__global__ void __launch_bounds__(128) k_msm_bucket(const typename Aff<F>::T* pts, MsmShape sh, const uint32_t* offsets,
-                                                    const uint32_t* counts, const uint32_t* list, xyzz_t<F>* buckets) {
-    const uint64_t key = gtid();
-    if (key >= sh.nkeys()) return;
-    const uint32_t off = offsets[key], cnt = counts[key];
+__global__ void __launch_bounds__(128) k_msm_chunk(const typename Aff<F>::T* pts, const uint32_t* list,
+                                                   const uint32_t* keys, const uint32_t* offsets,
+                                                   const uint32_t* counts, uint64_t nk, uint32_t T,
+                                                   xyzz_t<F>* buckets, xyzz_t<F>* head, xyzz_t<F>* tail) {
+    const uint64_t c = gtid();
+    const uint64_t E = nk ? (uint64_t)offsets[nk - 1] + counts[nk - 1] : 0;
+    const uint64_t lo = c * T;
+    if (lo >= E) return;
+    const uint64_t hi = lo + T < E ? lo + T : E;
     xyzz_t<F> acc;
     xyzz_inf(acc);
-    for (uint32_t q = 0; q < cnt; q++) {
-        const uint32_t e = list[off + q];
+    uint64_t run0 = lo;
+    for (uint64_t i = lo; i < hi; i++) {
+        const uint32_t e = list[i];
         const typename Aff<F>::T p = pts[e & 0x7fffffffu];
-        if (aff_is_inf(p)) continue;
-        acc = xyzz_madd(acc, p.x, (e >> 31) ? f_neg(p.y) : p.y);
+        if (!aff_is_inf(p)) acc = xyzz_madd(acc, p.x, (e >> 31) ? f_neg(p.y) : p.y);
+        const uint32_t k = keys[i];
+        if (i + 1 == hi || keys[i + 1] != k) {                   // end of a run inside this chunk
+            const bool before = run0 == lo && lo > 0 && keys[lo - 1] == k;
+            const bool after = i + 1 == hi && hi < E && keys[hi] == k;
+            if (before) head[c] = acc;
+            else if (after) tail[c] = acc;
+            else buckets[k] = acc;
+            xyzz_inf(acc);
+            run0 = i + 1;
+        }
     }
-    buckets[key] = acc;
+}
+
+// buckets whose run starts in chunk c and continues: tail[c] plus the head partials of the chunks
+// that start inside the same run
+template <typename F>
+__global__ void k_msm_fixup(const uint32_t* keys, const uint32_t* offsets, const uint32_t* counts, uint64_t nk,
+                            uint32_t T, const xyzz_t<F>* head, const xyzz_t<F>* tail, xyzz_t<F>* buckets) {
+    const uint64_t c = gtid();
+    const uint64_t E = nk ? (uint64_t)offsets[nk - 1] + counts[nk - 1] : 0;
+    const uint64_t lo = c * T;
+    if (lo >= E) return;
+    const uint64_t hi = lo + T < E ? lo + T : E;
+    if (hi >= E) return;
+    const uint32_t k = keys[hi - 1];
+    if (keys[hi] != k) return;                                   // the last run ends in this chunk
+    // the run continues past chunk c; chunk c computes it only if it starts in chunk c
+    const uint32_t start = offsets[k];
+    if (start < lo) return;
+    xyzz_t<F> acc = tail[c];
+    for (uint64_t d = c + 1; d * T < E && keys[d * T] == k; d++) acc = xyzz_add(acc, head[d]);
+    buckets[k] = acc;
 }
 
 // segment s of window w of batch j: its L = B_w / S buckets b in [s L, (s + 1) L) give
@@ -434,13 +478,22 @@ MsmShape msm_shape(uint64_t n, uint32_t nbatch, uint64_t npts, int c, int parts,
     return sh;
 }
 
+// entries per chunk of the bucket pass: enough chunks to fill the GPU a few times over
+static uint32_t msm_chunk_len(const MsmShape& sh) {
+    const uint64_t e = sh.entries_max();
+    uint64_t T = (e + (1u << 17) - 1) >> 17;
+    return (uint32_t)(T < 8 ? 8 : T);
+}
+
 template <typename F>
 static size_t scratch_bytes(const MsmShape& sh) {
     const uint64_t nk = sh.nkeys();
     auto r = [](size_t b) { return (b + 255) & ~(size_t)255; };
+    const uint64_t nchunks = (sh.entries_max() + msm_chunk_len(sh) - 1) / msm_chunk_len(sh);
     size_t b = 3 * r(nk * 4) + r(scan_tmp_words(nk) * 4);
-    b += r(sh.entries_max() * 4);
+    b += 2 * r(sh.entries_max() * 4);
     b += r(nk * sizeof(xyzz_t<F>));
+    b += 2 * r(nchunks * sizeof(xyzz_t<F>));
     b += 2 * r(sh.nsegs() * sizeof(xyzz_t<F>));
     b += r((uint64_t)sh.nbatch * sh.W * sizeof(GPt<F>));
     return b;
@@ -491,7 +544,12 @@ static void msm_run(const void* bases, const void* k_canon, const MsmShape& sh, 
     uint32_t* cursor = (uint32_t*)take(nk * 4);
     uint32_t* scan_tmp = (uint32_t*)take(scan_tmp_words(nk) * 4);
     uint32_t* list = (uint32_t*)take(sh.entries_max() * 4);
+    uint32_t* keys = (uint32_t*)take(sh.entries_max() * 4);
+    const uint32_t T = msm_chunk_len(sh);
+    const uint64_t nchunks = (sh.entries_max() + T - 1) / T;
     X* buckets = (X*)take(nk * sizeof(X));
+    X* head = (X*)take(nchunks * sizeof(X));
+    X* tail = (X*)take(nchunks * sizeof(X));
     X* seg_a = (X*)take(nseg * sizeof(X));
     X* seg_b = (X*)take(nseg * sizeof(X));
     GPt<F>* proj = (GPt<F>*)take(nwin * sizeof(GPt<F>));
@@ -505,11 +563,17 @@ static void msm_run(const void* bases, const void* k_canon, const MsmShape& sh, 
     cudaMemcpyAsync(cursor, offsets, nk * 4, cudaMemcpyDeviceToDevice, s);
     if (terms) {
         FP_KERNEL("k_msm_scatter", s,
-                  k_msm_scatter<F><<<grid_for(terms, 128), 128, 0, s>>>((const fr*)k_canon, sh, cursor, list));
+                  k_msm_scatter<F><<<grid_for(terms, 128), 128, 0, s>>>((const fr*)k_canon, sh, cursor, list, keys));
     }
-    FP_KERNEL("k_msm_bucket", s,
-              k_msm_bucket<F><<<grid_for(nk, 128), 128, 0, s>>>((const typename Aff<F>::T*)bases, sh, offsets, counts,
-                                                               list, buckets));
+    cudaMemsetAsync(buckets, 0, nk * sizeof(X), s);
+    if (nchunks) {                                   // no terms: every bucket stays the identity
+        FP_KERNEL("k_msm_chunk", s,
+                  k_msm_chunk<F><<<grid_for(nchunks, 128), 128, 0, s>>>((const typename Aff<F>::T*)bases, list, keys,
+                                                                       offsets, counts, nk, T, buckets, head, tail));
+        FP_KERNEL("k_msm_fixup", s,
+                  k_msm_fixup<F><<<grid_for(nchunks, 128), 128, 0, s>>>(keys, offsets, counts, nk, T, head, tail,
+                                                                       buckets));
+    }
     FP_KERNEL("k_msm_segment", s, k_msm_segment<F><<<grid_for(nseg, 128), 128, 0, s>>>(sh, buckets, seg_a));
     X* a = seg_a;
     X* b = seg_b;
