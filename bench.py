@@ -53,7 +53,9 @@ def step_units(log_n: int, b: int, msm_window: int) -> dict:
         "k_final_exp_w": ("final_exp", 2 * K * lr if 2 * K > 256 else 0),
         "k_round_miller_c": ("miller_loop", sum(K * 2 * h for h in hs if K * 2 * h <= 1024)),
         "k_round_miller_w": ("miller_loop", sum(K * 2 * h for h in hs if 1024 < K * 2 * h < 16384)),
-        "k_step1_miller": ("miller_loop", sum(K * 2 * h for h in hs if K * 2 * h >= 16384)),
+        "k_step1_miller_multi": ("miller_loop", sum(K * 2 * h for h in hs if K * 2 * h >= 1 << 18 and h >= 4)),
+        "k_step1_miller": ("miller_loop", sum(K * 2 * h for h in hs
+                                              if K * 2 * h >= 16384 and not (K * 2 * h >= 1 << 18 and h >= 4))),
         "k_commit_miller_c": ("miller_loop", R if R <= 1024 else 0),
         "k_commit_miller_w": ("miller_loop", R if R > 1024 else 0),
         "k_sparse_g": ("g1_mul", sum(K * min(b, 2 * h) for h in hs)),

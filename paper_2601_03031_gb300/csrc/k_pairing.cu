@@ -25,6 +25,27 @@ __global__ void __launch_bounds__(64) k_step1_miller(const g1a* A, const g2a* v,
     out[t] = side == 0 ? miller_loop(Ak[h + i], vk[i]) : miller_loop(Ak[i], vk[h + i]);
 }
 
+// G consecutive pairs of the same (k, side) product in one multi-pair Miller loop; output t covers
+// pairs (k, side, i) with i in [G t', G t' + G), t = (k 2 + side) (h / G) + t'
+template <int G>
+__global__ void __launch_bounds__(64) k_step1_miller_multi(const g1a* A, const g2a* v, uint32_t K, uint32_t R,
+                                                           uint32_t h, fq12* out) {
+    const uint64_t t = gtid();
+    const uint32_t per = h / G;
+    if (t >= (uint64_t)K * 2 * per) return;
+    const uint64_t k = t / (2 * per);
+    const uint32_t r = (uint32_t)(t % (2 * per)), side = r / per, i0 = (r % per) * G;
+    const g1a* Ak = A + k * R;
+    const g2a* vk = v + k * R;
+    g1a P[G];
+    g2a Q[G];
+    for (int g = 0; g < G; g++) {
+        P[g] = side == 0 ? Ak[h + i0 + g] : Ak[i0 + g];
+        Q[g] = side == 0 ? vk[i0 + g] : vk[h + i0 + g];
+    }
+    out[t] = miller_loop_multi<G>(P, Q);
+}
+
 __global__ void __launch_bounds__(64) k_final_exp(const fq12* in, uint32_t n, size_t stride, fq12* out, uint8_t* ser,
                                                   size_t ser_stride) {
     uint64_t i = gtid();
@@ -214,7 +235,16 @@ void commit_miller(const void* rows, const void* g2pow, uint32_t R, void* out, c
                                                                                    (const g2a*)g2pow, R,
                                                                                    (fq12*)out));
 }
+// grouping pays once the grouped threads still fill the GPU several times over (2^16 threads)
+uint32_t step1_miller_group(uint64_t n, uint32_t h) { return (h >= 4 && n >= (1u << 18)) ? 4 : 1; }
 void step1_miller(const void* A, const void* v, uint32_t K, uint32_t R, uint32_t h, void* out, cudaStream_t s) {
+    if (step1_miller_group((uint64_t)K * 2 * h, h) == 4) {   // 4 pairs per thread share the squarings
+        const uint64_t n = (uint64_t)K * 2 * (h / 4);
+        FP_KERNEL("k_step1_miller_multi", s,
+                  k_step1_miller_multi<4><<<grid_for(n, 64), 64, 0, s>>>((const g1a*)A, (const g2a*)v, K, R, h,
+                                                                        (fq12*)out));
+        return;
+    }
     uint64_t n = (uint64_t)K * 2 * h;
     FP_KERNEL("k_step1_miller", s, k_step1_miller<<<grid_for(n, 64), 64, 0, s>>>((const g1a*)A, (const g2a*)v, K, R, h, (fq12*)out));
 }

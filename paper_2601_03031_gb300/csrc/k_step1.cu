@@ -602,13 +602,15 @@ void step1_round_terms(const void* A, const void* v, const void* bvec, uint32_t 
               k_round_terms_g<<<nb_ml + nb_sp, 64, 0, s>>>((const g1a*)A, (const g2a*)v, (const fr*)bvec, K, R, h,
                                                            nb_ml, (fq12*)ml_out, (g1j*)sp_out));
 }
-void step1_miller_g(const void* A, const void* v, uint32_t K, uint32_t R, uint32_t h, void* ml_out, cudaStream_t s) {
+uint64_t step1_miller_g(const void* A, const void* v, uint32_t K, uint32_t R, uint32_t h, void* ml_out,
+                        cudaStream_t s) {
     uint64_t n = (uint64_t)K * 2 * h;
-    if (n >= 16384) {          // enough pairs to fill the GPU one per thread: less work than 8-lane groups
+    if (n >= 16384) {          // enough pairs to fill the GPU with threads: less work than warps
         step1_miller(A, v, K, R, h, ml_out, s);
-        return;
+        return n / step1_miller_group(n, h);
     }
-    round_miller_w(A, v, K, R, h, ml_out, s);      // few pairs: one warp each, for latency
+    round_miller_w(A, v, K, R, h, ml_out, s);      // few pairs: one warp or block each, for latency
+    return n;
 }
 void step1_fold(void* A, void* v, void* bvec, const void* x_mont, const void* xinv_mont, uint32_t K, uint32_t R,
                 uint32_t h, cudaStream_t s) {

@@ -65,6 +65,9 @@ void step1_init(const void* rows_g1a, const void* g2pow, uint32_t K, uint32_t R,
 void step1_stmt_hash(const void* C_ser, const void* rows_ser, uint32_t k0, uint32_t K, uint32_t R, uint32_t b,
                      void* hstmt, cudaStream_t s);
 void step1_block_r(const void* hstmt, uint32_t k0, uint32_t K, uint32_t R, uint32_t b, void* bvec, cudaStream_t s);
+// one thread per step1_miller_group(h) pairs of a product (multi-pair Miller loop); the outputs are
+// the products over those groups, in pair order
+uint32_t step1_miller_group(uint64_t n, uint32_t h);
 void step1_miller(const void* A, const void* v, uint32_t K, uint32_t R, uint32_t h, void* out_fq12, cudaStream_t s);
 // the same Miller loops with one warp per pair (few pairs: latency)
 void round_miller_w(const void* A, const void* v, uint32_t K, uint32_t R, uint32_t h, void* out_fq12, cudaStream_t s);
@@ -74,7 +77,9 @@ void step1_sparse_terms(const void* A, const void* bvec, uint32_t k0, uint32_t K
                         void* out_g1j, cudaStream_t s);
 void step1_round_terms(const void* A, const void* v, const void* bvec, uint32_t K, uint32_t R, uint32_t h,
                        void* ml_out_fq12, void* sp_out_g1j, cudaStream_t s);
-void step1_miller_g(const void* A, const void* v, uint32_t K, uint32_t R, uint32_t h, void* ml_out, cudaStream_t s);
+// round j's Miller values (returns how many: K 2h, or fewer when pairs were grouped)
+uint64_t step1_miller_g(const void* A, const void* v, uint32_t K, uint32_t R, uint32_t h, void* ml_out,
+                        cudaStream_t s);
 void step1_g1_out(const void* sp_g1j, uint32_t K, int j, void* blocks, size_t bopen_len, cudaStream_t s);
 void step1_gt_out(const void* ml_fq12, uint32_t K, int j, void* blocks, size_t bopen_len, cudaStream_t s);
 void step1_fold(void* A, void* v, void* bvec, const void* x_mont, const void* xinv_mont, uint32_t K, uint32_t R,

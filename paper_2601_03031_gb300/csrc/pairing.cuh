@@ -86,6 +86,39 @@ FPG_NOINL fq12 miller_loop(const g1a& P, const g2a& Q) {
     return fq12_conj(f);
 }
 
+// prod_g conj(f_{|x|,Q_g}(P_g)) for G pairs in one loop: the squaring of f is shared by the pairs
+// (a product of Miller functions squares as one), each step multiplies in every pair's line
+template <int G>
+FPG_NOINL fq12 miller_loop_multi(const g1a* P, const g2a* Q) {
+    fq12 f;
+    fq12_one(f);
+    g2j T[G];
+    bool live[G];
+    for (int g = 0; g < G; g++) {
+        live[g] = !(g1a_is_inf(P[g]) || g2a_is_inf(Q[g]));
+        T[g] = g2_from_affine(Q[g]);
+    }
+    line3 l;
+    bool first = true;
+    for (int i = 62; i >= 0; i--) {
+        if (!first) f = fq12_sqr(f);
+        first = false;
+        for (int g = 0; g < G; g++) {
+            if (!live[g]) continue;
+            miller_dbl_step(T[g], l, P[g].x, P[g].y);
+            f = fq12_mul_line(f, l.l0, l.l2, l.l3);
+        }
+        if ((BLS_X_ABS >> i) & 1) {
+            for (int g = 0; g < G; g++) {
+                if (!live[g]) continue;
+                miller_add_step(T[g], l, Q[g].x, Q[g].y, P[g].x, P[g].y);
+                f = fq12_mul_line(f, l.l0, l.l2, l.l3);
+            }
+        }
+    }
+    return fq12_conj(f);
+}
+
 // a^e for a in the cyclotomic subgroup and a plain exponent given as little-endian 32-bit words
 FPG_NOINL fq12 cyclotomic_exp(const fq12& a, const uint32_t* e, int bits) {
     fq12 acc;

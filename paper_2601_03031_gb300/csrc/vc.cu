@@ -519,8 +519,8 @@ fp_proofs* prove_impl(const fp_pp* pp, const fp_commit* cm, uint32_t b, uint32_t
                 void* spr = reduce_pairs(sp, sp2, (uint64_t)Kc * 2 * h, (uint64_t)Kc * 2, g1_pair_reduce, s3);
                 step1_g1_out(spr, Kc, j, blocks1, blen, s3);
                 check(cudaEventRecord(ev_sparse, s3), "event");
-                step1_miller_g(A, v, Kc, R, h, ml, s1);
-                void* mlr = reduce_pairs(ml, ml2, (uint64_t)Kc * 2 * h, (uint64_t)Kc * 2, fq12_pair_reduce, s1);
+                const uint64_t nml = step1_miller_g(A, v, Kc, R, h, ml, s1);
+                void* mlr = reduce_pairs(ml, ml2, nml, (uint64_t)Kc * 2, fq12_pair_reduce, s1);
                 step1_gt_out(mlr, Kc, j, blocks1, blen, s1);
                 check(cudaStreamWaitEvent(s1, ev_sparse, 0), "wait");
                 step1_challenge(blocks1, blen, Kc, j, xprev, x_mont, xinv_mont, xinv_all, lr, s1);
