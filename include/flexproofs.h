@@ -95,6 +95,18 @@ fp_status vc_commit_get(const fp_commit* cm, uint8_t* gt576, uint8_t* rows);
  *   - the two-level Merkle tree, the fold tree (g_w, D_w for every node), the PST proofs of g*. */
 fp_status vc_prove_all(const fp_pp* pp, const fp_commit* cm, uint32_t b, void* stream, fp_proofs** out);
 
+/* VC.Verify of one proof on the GPU (Sec. 4.2 verification: the Merkle path to the Fiat-Shamir
+ * root and r_j, FC.BVerify of block k = (i / M) / b with the b_l shortcut of Sec. 4.3 and the fast
+ * verification of v_l (Sec. 3), and PST.Verify of column a = i mod M for D* and y* (Sec. 4.2,
+ * Eq. VerifierRand)).
+ *   C: 576-byte commitment; m_i: the claimed value, 4 little-endian uint64 (canonical Fr);
+ *   proof / len: the bytes of vc_proof_get (host pointers).
+ * Returns FP_OK if the proof verifies, FP_EVERIFY if it does not (a check fails, a serialised
+ * element is not canonical or not on its curve, m_i >= r, or len is not the proof length for (b, i)),
+ * FP_EINVAL for bad arguments.  Synchronises `stream`. */
+fp_status vc_verify(const fp_pp* pp, const uint8_t* C, uint32_t b, uint64_t i, const uint64_t m_i[4],
+                    const uint8_t* proof, size_t len, void* stream);
+
 /* OpenAll for several independent jobs at once (no counterpart in the paper: serving-side batching).
  * Job j proves jobs[j].cm (any size; commitments made with views of one SRS, or with separate
  * setups) with batch size jobs[j].b.  Every job runs on its own library stream, forked from and

@@ -20,7 +20,7 @@ EXPORTED = ["vc_setup", "vc_pp_export", "vc_pp_dims", "vc_commit", "vc_commit_ge
             "fp_profile_enable", "fp_profile_report", "fp_imad_probe", "vc_commit_rows_noalloc",
             "fp_g1_bases_from_scalars", "fp_g1_bases_load", "fp_g1_bases_count", "fp_g1_bases_free", "fp_msm_g1",
             "fp_msm_window", "fp_msm_autotune", "vc_prove_one", "vc_pp_view", "vc_commit_async",
-            "vc_commit_status", "vc_prove_all_batch"]
+            "vc_commit_status", "vc_prove_all_batch", "vc_verify"]
 
 
 class FlexProofsError(RuntimeError):
@@ -56,6 +56,7 @@ def load(path: str = LIB_PATH):
     L.vc_proof_get.argtypes = [vp, u64, vp, sz, ctypes.POINTER(sz)]
     L.vc_prove_one.argtypes = [vp, vp, u32, u64, vp, vp, sz, ctypes.POINTER(sz)]
     L.vc_pp_view.argtypes = [vp, u32, pp]
+    L.vc_verify.argtypes = [vp, vp, u32, u64, vp, vp, sz, vp]
     L.vc_commit_async.argtypes = [vp, vp, ctypes.c_int, vp, pp]
     L.vc_commit_status.argtypes = [vp]
     L.vc_prove_all_batch.argtypes = [u32, vp, ctypes.c_int, vp, vp]
@@ -261,6 +262,15 @@ def vc_prove_all_batch(jobs, use_graph: bool = False, stream=None) -> list:
     outs = (ctypes.c_void_p * max(1, n))()
     _check("vc_prove_all_batch", L.vc_prove_all_batch(n, arr, int(use_graph), _stream_ptr(stream), outs))
     return [Proofs(cm.pp, cm, b, handle=ctypes.c_void_p(outs[j])) for j, (cm, b) in enumerate(jobs)]
+
+
+def vc_verify(pp: PP, C: bytes, b: int, i: int, m_i: int, proof: bytes, stream=None) -> bool:
+    """VC.Verify of one proof on the GPU: True if it verifies (FP_OK), False if not (FP_EVERIFY)."""
+    limbs = (ctypes.c_uint64 * 4)(*[(m_i >> (64 * w)) & 0xFFFFFFFFFFFFFFFF for w in range(4)])
+    st = load().vc_verify(pp.h, C, b, i, limbs, proof, len(proof), _stream_ptr(stream))
+    if st not in (0, 5):
+        raise FlexProofsError("vc_verify", st)
+    return st == 0
 
 
 def vc_prove_one(pp: PP, cm: Commitment, b: int, i: int, stream=None) -> bytes:

@@ -139,4 +139,10 @@ void msm_bases_endo(void* tab, uint64_t n, cudaStream_t s);
 // G2 bases table (4 n points) from nvalid <= n affine points, the rest identity
 void msm_bases_g2(const void* pts, uint64_t nvalid, uint64_t n, void* tab, cudaStream_t s);
 
+// ---- VC.Verify of one proof (verify.cu); result word 0 = accepted
+size_t verify_scratch_bytes(uint32_t nk, int lr, int lc);
+void verify_one(const void* proof, const void* C_be, const void* mi_be, uint32_t nk, int lr, int lc, uint32_t b,
+                uint64_t i, uint32_t M, uint32_t k, uint32_t lo, const void* g1beta, const void* g2tau, void* scratch,
+                uint32_t* result, cudaStream_t s);
+
 }  // namespace fpk

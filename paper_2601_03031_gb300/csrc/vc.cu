@@ -677,6 +677,44 @@ fp_status vc_prove_all_batch(uint32_t njobs, const fp_job* jobs, int use_graph, 
     });
 }
 
+fp_status vc_verify(const fp_pp* pp, const uint8_t* C, uint32_t b, uint64_t i, const uint64_t m_i[4],
+                    const uint8_t* proof, size_t len, void* stream) {
+    if (!pp || !C || !m_i || !proof) return FP_EINVAL;
+    if (b < 1 || b > pp->R || i >= (uint64_t)pp->R * pp->M) return FP_EINVAL;
+    if (len != vc_proof_len(pp, b, i)) return FP_EVERIFY;
+    cudaStream_t s = (cudaStream_t)stream;
+    return guarded([&]() -> fp_status {
+        const uint32_t k = (uint32_t)(i / pp->M) / b, lo = k * b, nk = std::min(b, pp->R - lo);
+        const int lr = (int)pp->log_r, lc = (int)pp->log_c;
+        // proof | C | m_i (32 bytes big-endian), one host-to-device copy
+        std::vector<uint8_t> host(len + GT_SER + 32);
+        memcpy(host.data(), proof, len);
+        memcpy(host.data() + len, C, GT_SER);
+        for (int w = 0; w < 4; w++)
+            for (int q = 0; q < 8; q++) host[len + GT_SER + 8 * (3 - w) + q] = (uint8_t)(m_i[w] >> (56 - 8 * q));
+        void *dbuf = nullptr, *scr = nullptr, *res = nullptr;
+        uint32_t hres = 1;
+        try {
+            dbuf = dalloc(host.size(), s);
+            scr = dalloc(verify_scratch_bytes(nk, lr, lc), s);
+            res = dalloc(sizeof(uint32_t), s);
+            check(cudaMemcpyAsync(dbuf, host.data(), host.size(), cudaMemcpyHostToDevice, s), "H2D proof");
+            const uint8_t* d = (const uint8_t*)dbuf;
+            verify_one(d, d + len, d + len + GT_SER, nk, lr, lc, b, i, pp->M, k, lo, pp->g1beta, pp->g2tau, scr,
+                       (uint32_t*)res, s);
+            check_launch("vc_verify kernels");
+            check(cudaMemcpyAsync(&hres, res, sizeof hres, cudaMemcpyDeviceToHost, s), "D2H result");
+            dfree(dbuf, s); dfree(scr, s); dfree(res, s);
+            check(cudaStreamSynchronize(s), "vc_verify");
+        } catch (...) {
+            cudaStreamSynchronize(s);
+            dfree(dbuf, s); dfree(scr, s); dfree(res, s);
+            throw;
+        }
+        return hres ? FP_EVERIFY : FP_OK;
+    });
+}
+
 fp_status vc_prove_one(const fp_pp* pp, const fp_commit* cm, uint32_t b, uint64_t i, void* stream, uint8_t* out,
                        size_t cap, size_t* len) {
     if (!pp || !cm || !len || cm->pp != pp) return FP_EINVAL;

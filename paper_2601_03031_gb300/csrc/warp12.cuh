@@ -565,3 +565,27 @@ FPG_NOINL void w_miller(WMill& S, g1a P, g2a Q) {
     }
     wsync<NW>();
 }
+
+// acc = base^e for any base (e little-endian words, squarings as products); acc != base
+template <int NW>
+FPG_NOINL void w_exp(W12& W, fq* acc, const fq* base, const uint32_t* e, int bits) {
+    const int L = w_lane<NW>();
+    int i = bits - 1;
+    while (i >= 0 && !((e[i >> 5] >> (i & 31)) & 1)) i--;
+    if (i < 0) {                                   // e = 0: acc = 1
+        wsync<NW>();
+        if (L < 12) {
+            fq v;
+            if (L == 0) fq_one(v);
+            else fq_zero(v);
+            acc[L] = v;
+        }
+        wsync<NW>();
+        return;
+    }
+    w_copy<NW>(acc, base);
+    for (i = i - 1; i >= 0; i--) {
+        w_mul<NW>(W, acc, acc, acc);
+        if ((e[i >> 5] >> (i & 31)) & 1) w_mul<NW>(W, acc, acc, base);
+    }
+}

@@ -1,0 +1,83 @@
+"""vc_verify on the GPU against the oracle's verifier: honest proofs verify, tampered ones do not.
+
+Tampering covers every part of a proof: the claimed value m_i, a block commitment C_a, a GT and a
+G1 part of an FC round, the fast-verification proof W, a Merkle path digest, a sibling pair and a
+PST proof element; each must be rejected by both verifiers."""
+import pytest
+
+import oracle as O
+from paper_2601_03031_gb300 import inputs as I
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+if not torch.cuda.is_available():
+    pytest.skip("no CUDA device", allow_module_level=True)
+
+from paper_2601_03031_gb300 import _lib as F  # noqa: E402
+
+
+def setup(log_n, seed, b):
+    pp = F.PP(log_n, 1, seed)
+    m = I.vector(seed + 1, log_n)
+    cm = F.Commitment(pp, m)
+    C, _ = cm.get()
+    pf = F.Proofs(pp, cm, b)
+    return pp, O.PP(log_n, seed), I.to_ints(m), C, pf
+
+
+@pytest.mark.parametrize("log_n,b", [(4, 1), (5, 3), (6, 8)])
+def test_honest_proofs_verify(log_n, b):
+    pp, opp, vals, C, pf = setup(log_n, 31, b)
+    for i in range(0, pp.N, 3):
+        p = pf.proof(i)
+        assert F.vc_verify(pp, C, b, i, vals[i], p), i
+        assert O.verify(opp, C, b, i, vals[i], p, memo=False)
+
+
+def flip(p: bytes, off: int) -> bytes:
+    return p[:off] + bytes([p[off] ^ 1]) + p[off + 1:]
+
+
+def test_tampered_proofs_rejected():
+    log_n, b = 5, 2
+    pp, opp, vals, C, pf = setup(log_n, 32, b)
+    i = 13
+    p = pf.proof(i)
+    nk = b
+    lr, lc = pp.log_r, pp.log_c
+    fc = 96 * nk
+    path = fc + lr * 1344 + 96 + 192 + 192
+    sib = path + 32 * (lr + lc)
+    pst = sib + 128 * lr
+    cases = {
+        "m_i": (vals[i] + 1, p),
+        "C_a": (vals[i], flip(p, 47)),
+        "L_1.T": (vals[i], flip(p, fc + 100)),
+        "R_1.1": (vals[i], flip(p, fc + 576 + 96 + 576 + 95)),
+        "W": (vals[i], flip(p, path - 1)),
+        "path": (vals[i], flip(p, path + 3)),
+        "sibling": (vals[i], flip(p, sib + 100)),
+        "pst": (vals[i], flip(p, pst + 95)),
+    }
+    assert F.vc_verify(pp, C, b, i, vals[i], p)
+    for name, (mi, q) in cases.items():
+        assert not F.vc_verify(pp, C, b, i, mi, q), name
+        assert not O.verify(opp, C, b, i, mi, q, memo=False), name
+    assert not F.vc_verify(pp, C, b, i, vals[i], p[:-1])          # wrong length
+    assert not F.vc_verify(pp, C, b, i + 1, vals[i + 1], p)       # proof of another index
+    assert not F.vc_verify(pp, C, b, i, I.R_INT + vals[i], p)     # m_i >= r
+
+
+def test_verify_n16_sampled():
+    log_n, seed = 16, 0
+    pp = F.PP(log_n, 1, seed)
+    m = I.vector(seed + 1, log_n)
+    vals = I.to_ints(m)
+    cm = F.Commitment(pp, m)
+    C, _ = cm.get()
+    for b, i in ((256, 12345), (1, 65535)):
+        pf = F.Proofs(pp, cm, b)
+        p = pf.proof(i)
+        assert F.vc_verify(pp, C, b, i, vals[i], p)
+        assert not F.vc_verify(pp, C, b, i, vals[i] ^ 1, p)
