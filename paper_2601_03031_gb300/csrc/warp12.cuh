@@ -120,7 +120,31 @@ FPG_NOINL void w_cyc_sqr(W12& W, fq* out, const fq* z) {
         W.p[L] = fq_mul(x, y);
     }
     wsync<NW>();
-    if (L < 12) {
+    if (NW == 4) {
+        // A_p.re, A_p.im, B_p.re, B_p.im on warps 0, 1, 2, 3 (lane p of each), then the outputs
+        const int w = L >> 5, pl = L & 31;
+        if (pl < 3) {
+            const fq* m = &W.p[7 * pl];
+            fq v;
+            if (w == 0) v = fq_sub(fq_add(m[0], m[2]), fq_dbl(m[3]));
+            else if (w == 1) v = fq_add(fq_add(fq_dbl(m[1]), m[2]), fq_dbl(m[3]));
+            else if (w == 2) v = fq_dbl(fq_sub(m[4], m[5]));
+            else v = fq_dbl(fq_sub(m[6], fq_add(m[4], m[5])));
+            W.h[12 + 3 * w + pl] = v;
+        }
+        wsync<NW>();
+        if (L < 12) {
+            const int k = L >> 1, e = L & 1;
+            const int pair = (k == 0 || k == 3) ? 0 : (k == 2 || k == 5) ? 1 : 2;
+            const int kind = (k == 0 || k == 2 || k == 4) ? 0 : (k == 1 ? 2 : 1);
+            const fq* AB = &W.h[12];                  // [A.re | A.im | B.re | B.im] x 3 pairs
+            const fq bre = AB[6 + pair], bim = AB[9 + pair];
+            const fq V = kind == 0 ? AB[3 * e + pair] : (kind == 1 ? (e ? bim : bre) : (e ? fq_add(bre, bim) : fq_sub(bre, bim)));
+            const fq V3 = fq_add(fq_dbl(V), V);
+            const fq z2 = fq_dbl(z[L]);
+            W.h[L] = kind == 0 ? fq_sub(V3, z2) : fq_add(V3, z2);
+        }
+    } else if (L < 12) {
         const int k = L >> 1, e = L & 1;
         // coefficient k -> (pair, kind): kind 0: 3A - 2z, 1: 3B + 2z, 2: 3 xi B + 2z
         const int pair = (k == 0 || k == 3) ? 0 : (k == 2 || k == 5) ? 1 : 2;
@@ -284,6 +308,7 @@ struct WMill {
     fq v[16];       // round results: T products, line helpers
     fq l[6];        // line l0, l2, l3
     fq h[24];
+    fq tm[72];      // per-term partial sums of the combines (block-wide engine)
 };
 
 FPG_DEV void kara_ops(fq& x, fq& y, const fq* a, const fq* b, int kind) {
@@ -329,6 +354,16 @@ FPG_DEV fq wm_line_combine(const WMill& S, int o) {
     return acc;
 }
 
+// block-wide combine of f * line: lane L < 36 forms term L / 12 of output component L % 12
+FPG_DEV void wm_line_terms(WMill& S, int L) {
+    if (L < 36) {
+        const int o = L % 12, term = L / 12, k = o >> 1, e = o & 1;
+        const fq* m = &S.p[3 * (6 * term + k)];
+        S.tm[L] = twist_part(kara_part(m, 0), kara_part(m, 1), e, (term == 1 && k < 2) || (term == 2 && k < 3));
+    }
+}
+FPG_DEV fq wm_line_sum(const WMill& S, int o) { return fq_add(fq_add(S.tm[o], S.tm[12 + o]), S.tm[24 + o]); }
+
 template <int NW>
 FPG_NOINL void wm_dbl(WMill& S, const fq& m3x, const fq& y2) {
     const int L = w_lane<NW>();
@@ -351,7 +386,38 @@ FPG_NOINL void wm_dbl(WMill& S, const fq& m3x, const fq& y2) {
         S.p[t] = fq_mul(x, y);
     }
     wsync<NW>();
-    if (L < 12) {                                  // f^2, coefficient k, component e
+    if (NW == 4 && L < 72) {                       // f^2 terms: lane L -> component L % 12, term i = L / 12
+        const int o = L % 12, i = L / 12, k = o >> 1, e = o & 1;
+        int j = k - i;
+        if (j < 0) j += 6;
+        fq v;
+        fq_zero(v);
+        if (i <= j) {
+            fq re, im;
+            if (i == j) {
+                re = sq_part(&S.p[2 * i], 0);
+                im = sq_part(&S.p[2 * i], 1);
+            } else {
+                const int c = i * (11 - i) / 2 + (j - i - 1);
+                re = fq_dbl(kara_part(&S.p[12 + 3 * c], 0));
+                im = fq_dbl(kara_part(&S.p[12 + 3 * c], 1));
+            }
+            v = twist_part(re, im, e, i + j >= 6);
+        }
+        S.tm[L] = v;
+    }
+    if (NW == 4 && L >= 96 && L < 106) {           // XX, YY, ZZ, YZ, XY (re, im)
+        const int v = L - 96, which = v >> 1, e = v & 1;
+        S.v[v] = which < 3 ? sq_part(&S.p[57 + 2 * which], e) : kara_part(&S.p[57 + 6 + 3 * (which - 3)], e);
+    }
+    if (NW == 4) {
+        wsync<NW>();
+        if (L < 12) {
+            fq acc = S.tm[L];
+            for (int i = 1; i < 6; i++) acc = fq_add(acc, S.tm[12 * i + L]);
+            S.g[L] = acc;
+        }
+    } else if (L < 12) {                           // f^2, coefficient k, component e
         const int k = L >> 1, e = L & 1;
         fq acc;
         fq_zero(acc);
@@ -372,7 +438,7 @@ FPG_NOINL void wm_dbl(WMill& S, const fq& m3x, const fq& y2) {
             acc = fq_add(acc, twist_part(re, im, e, wrap));
         }
         S.g[L] = acc;
-    } else if (L < 22) {                           // XX, YY, ZZ, YZ, XY (re, im)
+    } else if (NW == 1 && L < 22) {                // XX, YY, ZZ, YZ, XY (re, im)
         const int v = L - 12, which = v >> 1, e = v & 1;
         S.v[v] = which < 3 ? sq_part(&S.p[57 + 2 * which], e) : kara_part(&S.p[57 + 6 + 3 * (which - 3)], e);
     }
@@ -428,9 +494,15 @@ FPG_NOINL void wm_dbl(WMill& S, const fq& m3x, const fq& y2) {
     // round C: f^2 * line
     for (int t = L; t < 54; t += 32 * NW) wm_line_products(S, S.g, t);
     wsync<NW>();
-    if (L < 12) S.h[L] = wm_line_combine(S, L);
-    wsync<NW>();
-    if (L < 12) S.f[L] = S.h[L];
+    if (NW == 4) {
+        wm_line_terms(S, L);
+        wsync<NW>();
+        if (L < 12) S.f[L] = wm_line_sum(S, L);
+    } else {
+        if (L < 12) S.h[L] = wm_line_combine(S, L);
+        wsync<NW>();
+        if (L < 12) S.f[L] = S.h[L];
+    }
     wsync<NW>();
 }
 
@@ -490,13 +562,23 @@ FPG_NOINL void wm_add(WMill& S, const fq& mxP, const fq& yP) {
         }
     }
     wsync<NW>();
-    if (L < 12) S.h[L] = wm_line_combine(S, L);
-    else if (L < 18) {                              // E, F, G
-        const int v = L - 12;
-        S.v[8 + v] = kara_part(&S.p[54 + 3 * (v >> 1)], v & 1);
+    if (NW == 4) {
+        wm_line_terms(S, L);
+        if (L >= 64 && L < 70) {                     // E, F, G
+            const int v = L - 64;
+            S.v[8 + v] = kara_part(&S.p[54 + 3 * (v >> 1)], v & 1);
+        }
+        wsync<NW>();
+        if (L < 12) S.f[L] = wm_line_sum(S, L);
+    } else {
+        if (L < 12) S.h[L] = wm_line_combine(S, L);
+        else if (L < 18) {                          // E, F, G
+            const int v = L - 12;
+            S.v[8 + v] = kara_part(&S.p[54 + 3 * (v >> 1)], v & 1);
+        }
+        wsync<NW>();
+        if (L < 12) S.f[L] = S.h[L];
     }
-    wsync<NW>();
-    if (L < 12) S.f[L] = S.h[L];
     // round D: lambda H, theta (G - H), Y E, Z E, with H = E + F - 2 G
     const fq* E = S.v + 8;
     const fq* Fv = S.v + 10;
