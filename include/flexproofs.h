@@ -107,6 +107,20 @@ fp_status vc_prove_all(const fp_pp* pp, const fp_commit* cm, uint32_t b, void* s
 fp_status vc_verify(const fp_pp* pp, const uint8_t* C, uint32_t b, uint64_t i, const uint64_t m_i[4],
                     const uint8_t* proof, size_t len, void* stream);
 
+/* VC.Verify of all N proofs of a vc_prove_all result at once.  ok[i] (host, N bytes, may be NULL)
+ * receives 1 if proof i -- the bytes vc_proof_get(pf, i) would return -- verifies for the claimed
+ * value m[i] against C, else 0: the same verdict as vc_verify(pp, C, b, i, m[i], proof i).
+ * *n_ok (may be NULL) receives the number accepted.  The verifiers of one block share pi_{C_k}
+ * and those of one column share pi*_a (Protocol 1, Steps 1 and 2), so each block's FC.BVerify runs
+ * once, and one PST.Verify per column serves every proof whose (root, D*, y*) equal those of the
+ * column's row-0 proof; any other proof (say, a wrong claimed value) gets a PST.Verify of its own.
+ *   C: 576-byte commitment (host); m: N x 4 little-endian uint64 claimed values, on the host
+ *   (on_device = 0) or the current device (on_device = 1); a value >= r fails its proof only.
+ *   flags: 0, or 1 = give every proof its own PST.Verify (no column sharing; slower, same verdicts).
+ * pf must come from pp (FP_EINVAL otherwise).  Orders itself after pf's work; synchronises `stream`. */
+fp_status vc_verify_all(const fp_pp* pp, const uint8_t* C, const uint64_t* m, int on_device, const fp_proofs* pf,
+                        int flags, void* stream, uint8_t* ok, uint64_t* n_ok);
+
 /* OpenAll for several independent jobs at once (no counterpart in the paper: serving-side batching).
  * Job j proves jobs[j].cm (any size; commitments made with views of one SRS, or with separate
  * setups) with batch size jobs[j].b.  Every job runs on its own library stream, forked from and

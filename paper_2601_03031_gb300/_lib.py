@@ -20,7 +20,7 @@ EXPORTED = ["vc_setup", "vc_pp_export", "vc_pp_dims", "vc_commit", "vc_commit_ge
             "fp_profile_enable", "fp_profile_report", "fp_imad_probe", "vc_commit_rows_noalloc",
             "fp_g1_bases_from_scalars", "fp_g1_bases_load", "fp_g1_bases_count", "fp_g1_bases_free", "fp_msm_g1",
             "fp_msm_window", "fp_msm_autotune", "vc_prove_one", "vc_pp_view", "vc_commit_async",
-            "vc_commit_status", "vc_prove_all_batch", "vc_verify"]
+            "vc_commit_status", "vc_prove_all_batch", "vc_verify", "vc_verify_all"]
 
 
 class FlexProofsError(RuntimeError):
@@ -57,6 +57,7 @@ def load(path: str = LIB_PATH):
     L.vc_prove_one.argtypes = [vp, vp, u32, u64, vp, vp, sz, ctypes.POINTER(sz)]
     L.vc_pp_view.argtypes = [vp, u32, pp]
     L.vc_verify.argtypes = [vp, vp, u32, u64, vp, vp, sz, vp]
+    L.vc_verify_all.argtypes = [vp, vp, vp, ctypes.c_int, vp, ctypes.c_int, vp, vp, ctypes.POINTER(u64)]
     L.vc_commit_async.argtypes = [vp, vp, ctypes.c_int, vp, pp]
     L.vc_commit_status.argtypes = [vp]
     L.vc_prove_all_batch.argtypes = [u32, vp, ctypes.c_int, vp, vp]
@@ -271,6 +272,26 @@ def vc_verify(pp: PP, C: bytes, b: int, i: int, m_i: int, proof: bytes, stream=N
     if st not in (0, 5):
         raise FlexProofsError("vc_verify", st)
     return st == 0
+
+
+def vc_verify_all(pf: "Proofs", C: bytes, m, each: bool = False, stream=None):
+    """VC.Verify of all N proofs of `pf` for the claimed values m (N x 4 uint64 limbs: numpy, or a
+    torch CUDA tensor of int64) against C.  Returns (ok: numpy bool array of N, number accepted).
+    each=True gives every proof its own PST check (no column sharing)."""
+    N = pf.pp.N
+    if hasattr(m, "data_ptr"):
+        assert m.is_cuda and m.is_contiguous() and m.numel() == 4 * N
+        ptr, dev, keep = m.data_ptr(), 1, m
+    else:
+        keep = np.ascontiguousarray(m, dtype=np.uint64)
+        assert keep.size == 4 * N
+        ptr, dev = keep.ctypes.data, 0
+    ok = np.zeros(N, np.uint8)
+    n_ok = ctypes.c_uint64()
+    _check("vc_verify_all", load().vc_verify_all(pf.pp.h, C, ptr, dev, pf.h, int(each), _stream_ptr(stream),
+                                                 ok.ctypes.data, ctypes.byref(n_ok)))
+    del keep
+    return ok.astype(bool), int(n_ok.value)
 
 
 def vc_prove_one(pp: PP, cm: Commitment, b: int, i: int, stream=None) -> bytes:

@@ -139,10 +139,17 @@ void msm_bases_endo(void* tab, uint64_t n, cudaStream_t s);
 // G2 bases table (4 n points) from nvalid <= n affine points, the rest identity
 void msm_bases_g2(const void* pts, uint64_t nvalid, uint64_t n, void* tab, cudaStream_t s);
 
-// ---- VC.Verify of one proof (verify.cu); result word 0 = accepted
-size_t verify_scratch_bytes(uint32_t nk, int lr, int lc);
+// ---- VC.Verify (verify.cu).  One proof: result word 0 = 0 if accepted.
+size_t verify_scratch_bytes(uint32_t b, int lr, int lc);
 void verify_one(const void* proof, const void* C_be, const void* mi_be, uint32_t nk, int lr, int lc, uint32_t b,
                 uint64_t i, uint32_t M, uint32_t k, uint32_t lo, const void* g1beta, const void* g2tau, void* scratch,
                 uint32_t* result, cudaStream_t s);
+// All N proofs of an OpenAll output (its shared pieces as stored by vc_prove_all) against the
+// claimed values m (device, N x 4 little-endian u64): ok_out (host, N bytes, may be null) gets 1
+// per accepted proof; returns the number accepted.  each = 1: no PST check is shared.  Synchronises.
+size_t verify_all_scratch_bytes(const ProofLayout& L);
+uint64_t verify_all(const ProofLayout& L, const void* C_be, const void* m, const void* rows_ser, const void* blocks,
+                    const void* row_tree, const void* top_tree, const void* D_ser, const void* g, const void* pst_ser,
+                    const void* g1beta, const void* g2tau, int each, void* scratch, void* ok_out, cudaStream_t s);
 
 }  // namespace fpk

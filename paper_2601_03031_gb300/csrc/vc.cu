@@ -696,7 +696,7 @@ fp_status vc_verify(const fp_pp* pp, const uint8_t* C, uint32_t b, uint64_t i, c
         uint32_t hres = 1;
         try {
             dbuf = dalloc(host.size(), s);
-            scr = dalloc(verify_scratch_bytes(nk, lr, lc), s);
+            scr = dalloc(verify_scratch_bytes(b, lr, lc), s);
             res = dalloc(sizeof(uint32_t), s);
             check(cudaMemcpyAsync(dbuf, host.data(), host.size(), cudaMemcpyHostToDevice, s), "H2D proof");
             const uint8_t* d = (const uint8_t*)dbuf;
@@ -712,6 +712,46 @@ fp_status vc_verify(const fp_pp* pp, const uint8_t* C, uint32_t b, uint64_t i, c
             throw;
         }
         return hres ? FP_EVERIFY : FP_OK;
+    });
+}
+
+fp_status vc_verify_all(const fp_pp* pp, const uint8_t* C, const uint64_t* m, int on_device, const fp_proofs* pf,
+                        int flags, void* stream, uint8_t* ok, uint64_t* n_ok) {
+    if (!pp || !C || !m || !pf || pf->pp != pp || (flags & ~1)) return FP_EINVAL;
+    cudaStream_t s = (cudaStream_t)stream;
+    return guarded([&]() -> fp_status {
+        const ProofLayout& L = pf->L;
+        const uint64_t N = (uint64_t)L.R * L.M;
+        void *dC = nullptr, *dm = nullptr, *scr = nullptr;
+        cudaEvent_t ready = nullptr;
+        try {
+            // the proof pieces are written on the handle's stream
+            check(cudaEventCreateWithFlags(&ready, cudaEventDisableTiming), "cudaEventCreate");
+            check(cudaEventRecord(ready, pf->stream), "cudaEventRecord");
+            check(cudaStreamWaitEvent(s, ready, 0), "cudaStreamWaitEvent");
+            dC = dalloc(GT_SER, s);
+            check(cudaMemcpyAsync(dC, C, GT_SER, cudaMemcpyHostToDevice, s), "H2D C");
+            const void* md = m;
+            if (!on_device) {
+                dm = dalloc(N * 32, s);
+                check(cudaMemcpyAsync(dm, m, N * 32, cudaMemcpyHostToDevice, s), "H2D m");
+                md = dm;
+            }
+            scr = dalloc(verify_all_scratch_bytes(L), s);
+            const uint64_t good = verify_all(L, dC, md, pf->rows_ser, pf->blocks, pf->row_tree, pf->top_tree, pf->D_ser,
+                                             pf->g, pf->pst_ser, pp->g1beta, pp->g2tau, flags & 1, scr, ok, s);
+            check_launch("vc_verify_all kernels");
+            dfree(dC, s); dfree(dm, s); dfree(scr, s);
+            check(cudaStreamSynchronize(s), "vc_verify_all");
+            cudaEventDestroy(ready);
+            if (n_ok) *n_ok = good;
+        } catch (...) {
+            cudaStreamSynchronize(s);
+            dfree(dC, s); dfree(dm, s); dfree(scr, s);
+            if (ready) cudaEventDestroy(ready);
+            throw;
+        }
+        return FP_OK;
     });
 }
 

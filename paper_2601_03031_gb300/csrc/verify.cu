@@ -1,32 +1,36 @@
-// VC.Verify of one proof on the GPU (Sec. 4.2, Protocol 1 verification; FC.BVerify of Sec. 3 with
-// the b_l shortcut of Sec. 4.3 and the fast verification of v_l; PST.Verify):
-//   1. transcript (one thread): statement hash of block k, x_j from L_j, R_j, z, P(z), the Merkle
-//      path from (i, m_i) and C_j to the root, r_j, y* = r_j m_i + sum y_w;
-//   2. C_0's G1 part sum_a r_a C_a and the rounds' x_j L_j.1 + x_j^-1 R_j.1 (one thread per term,
-//      pairwise sums), b_l = sum_a r_a prod_k x_k^-(bit l - k of a);
-//   3. the GT fold C L_1^x1 R_1^(1/x1) ... (one 128-thread block per exponentiation);
-//   4. pairings: e(A_l, v_l) against the folded C, e(g1^beta - z g1, W) e(-g1, v_l - P(z) g2) = 1,
-//      e(D* - y* g1, g2) prod_t e(-pi_t, g2^tau_t - a_t g2) = 1, and b_l A_l against the folded
-//      G1 part.
-// Every serialised element is decoded with its checks (canonical coordinates, on the curve);
-// a failed decode rejects the proof.
+// VC.Verify on the GPU (Sec. 4.2, Protocol 1 verification; FC.BVerify of Sec. 3 with the b_l
+// shortcut of Sec. 4.3 and the fast verification of v_l; PST.Verify), for one proof (verify_one)
+// and for all N proofs of an OpenAll output (verify_all).
+//
+// A proof of element i = j M + a (row j, column a, block k = j / b) consists of
+//   the block part:   the block's row commitments C_a and pi_{C_k} (the same for all of block k),
+//   the element part: the Merkle path of (i, m_i) and the fold-tree siblings (D_w, y_w),
+//   the column part:  the PST proof of g* at a (the same for all of column a).
+// Checks, in three groups:
+//   block:   statement hash, x_j, z, P(z); C_0's G1 part sum_a r_a C_a and the rounds'
+//            x_j L_j.1 + x_j^-1 R_j.1 (one thread per term, pairwise sums);
+//            b_l = sum_a r_a prod_k x_k^-(bit l - k of a); the GT fold C L_1^x1 R_1^(1/x1) ...
+//            (one 128-thread block per exponentiation); e(A_l, v_l) against the folded C,
+//            e(g1^beta - z g1, W) e(-g1, v_l - P(z) g2) = 1, and b_l A_l against the folded G1 part;
+//   element: the Merkle path to the root, r_j = H(root, j), D* = r_j C_j + sum_w D_w and
+//            y* = r_j m_i + sum_w y_w (Eq. VerifierRand and the Sub-protocol);
+//   PST:     e(D* - y* g1, g2) prod_t e(-pi_t, g2^tau_t - a_t g2) = 1 (PST.Verify at Bin(a)).
+// Every serialised element is decoded with its checks (canonical coordinates, on the curve); a
+// failed decode rejects the proof.  A proof is accepted iff no check of any group fails.
+//
+// verify_all runs each block check once per block (every proof of a block carries the same block
+// part) and one PST check per column for the proofs whose PST inputs (a, D*, y*) equal those of
+// the column's row-0 proof, which holds when the Merkle roots, the rows' D* and the y* agree.
+// Every other proof gets a PST check of its own, so each result is the one verify_one gives for
+// that proof's bytes.
+#include <algorithm>
+
 #include "k_common.cuh"
 #include "warp12.cuh"
 
 namespace fpk {
 
-struct VState {
-    uint32_t bad;
-    uint8_t hstmt[32];
-    fr x[32], xinv[32];            // Montgomery
-    fr z, Pz, rj, ys, bl;          // Montgomery
-    g1a Al, Cj;
-    g2a vl, W;
-    fq12 C;
-    g1j blA, zg, ysg, rjCj;
-    g2j Pzg;
-};
-
+// ------------------------------------------------------------------------------ decoding
 FPG_DEV bool fq_from_be48(const uint8_t* b, fq& out) {
     fq c;
     for (int w = 0; w < 12; w++) {
@@ -84,11 +88,327 @@ FPG_DEV bool fq12_decode(const uint8_t* b, fq12& f) {
     return true;
 }
 FPG_DEV g1j g1j_neg(const g1j& p) { g1j r = p; r.Y = fq_neg(p.Y); return r; }
-FPG_DEV bool jac_eq(const g1j& p, const g1j& q) {
-    const g1a a = g1_affine(p), b = g1_affine(q);
-    return fq_eq(a.x, b.x) && fq_eq(a.y, b.y);
+FPG_DEV bool g1a_same(const g1a& a, const g1a& b) { return fq_eq(a.x, b.x) && fq_eq(a.y, b.y); }
+FPG_DEV bool jac_eq(const g1j& p, const g1j& q) { return g1a_same(g1_affine(p), g1_affine(q)); }
+FPG_DEV bool fr_same(const fr& a, const fr& b) {
+    for (int w = 0; w < 8; w++)
+        if (a.v[w] != b.v[w]) return false;
+    return true;
+}
+FPG_DEV bool digest_same(const uint8_t* a, const uint8_t* b) {
+    for (int q = 0; q < 32; q++)
+        if (a[q] != b[q]) return false;
+    return true;
 }
 FPG_DEV g2a g2a_negate(const g2a& p) { return g2a_is_inf(p) ? p : g2a{p.x, fq2_neg(p.y)}; }
+// r_j = HFr("FP-rho", root || u32be(j))
+FPG_DEV fr row_rho(const uint8_t* root, uint32_t j) {
+    uint8_t rb[36];
+    for (int q = 0; q < 32; q++) rb[q] = root[q];
+    put_be32(rb + 32, j);
+    return hash_to_fr("FP-rho", 6, rb, 36, nullptr, 0, nullptr, 0);
+}
+// one step up a Merkle path: SHA256("FP-node" || left || right), cur the right child if `right`
+FPG_DEV void node_hash(uint8_t* cur, const uint8_t* sib, bool right) {
+    uint8_t buf[7 + 64];
+    for (int q = 0; q < 7; q++) buf[q] = (uint8_t)"FP-node"[q];
+    for (int q = 0; q < 32; q++) {
+        buf[7 + q] = right ? sib[q] : cur[q];
+        buf[39 + q] = right ? cur[q] : sib[q];
+    }
+    sha256(cur, buf, 7 + 64);
+}
+// element leaf SHA256("FP-leaf" || u64be(i) || m_i)
+FPG_DEV void leaf_hash(uint8_t* cur, uint64_t i, const uint8_t* mi_be) {
+    uint8_t buf[7 + 8 + 32];
+    for (int q = 0; q < 7; q++) buf[q] = (uint8_t)"FP-leaf"[q];
+    put_be64(buf + 7, i);
+    for (int q = 0; q < 32; q++) buf[15 + q] = mi_be[q];
+    sha256(cur, buf, sizeof buf);
+}
+// row leaf SHA256("FP-row" || s_j || C_j), s_j = cur
+FPG_DEV void row_leaf_hash(uint8_t* cur, const uint8_t* Cj_be) {
+    uint8_t buf[6 + 32 + 96];
+    for (int q = 0; q < 6; q++) buf[q] = (uint8_t)"FP-row"[q];
+    for (int q = 0; q < 32; q++) buf[6 + q] = cur[q];
+    for (int q = 0; q < 96; q++) buf[38 + q] = Cj_be[q];
+    sha256(cur, buf, sizeof buf);
+}
+
+// ------------------------------------------------------------------------------ block checks
+// FC.BVerify state of one block
+struct VBlk {
+    uint32_t bad;
+    uint8_t hstmt[32];
+    fr x[32], xinv[32];            // Montgomery
+    fr z, Pz, bl;                  // Montgomery
+    g1a Al;
+    g2a vl, W;
+    g1j blA, zg;
+    g2j Pzg;
+};
+
+// blocks q = 0 .. nb - 1 (block k0 + q): row commitments at blk + q blk_stride, pi_{C_k} at
+// fc + q fc_stride
+struct VSrc {
+    const uint8_t* blk;
+    size_t blk_stride;
+    const uint8_t* fc;
+    size_t fc_stride;
+    uint32_t k0, nb, b, R;
+    int lr;
+    __host__ __device__ uint32_t lo(uint32_t q) const { return (k0 + q) * b; }
+    __host__ __device__ uint32_t nk(uint32_t q) const { return lo(q) + b < R ? b : R - lo(q); }
+};
+
+__global__ void k_v_cdec(const uint8_t* C_be, fq12* Cd, uint32_t* cbad) {
+    if (gtid() != 0) return;
+    *cbad = fq12_decode(C_be, *Cd) ? 0u : 1u;
+}
+
+// statement hash, x_j and x_j^-1, A_l, v_l, W, z and P(z) = prod_j (1 + x_j^-1 z^(2^(l - j + 1)))
+__global__ void k_vb_transcript(VSrc S, const uint8_t* C_be, VBlk* st) {
+    const uint64_t q = gtid();
+    if (q >= S.nb) return;
+    VBlk& B = st[q];
+    const uint32_t k = S.k0 + (uint32_t)q, nk = S.nk((uint32_t)q);
+    const uint8_t* blk = S.blk + q * S.blk_stride;
+    const uint8_t* fc = S.fc + q * S.fc_stride;
+    const int lr = S.lr;
+    uint32_t bad = 0;
+    {
+        sha256_ctx c;
+        sha256_init(c);
+        sha256_update(c, C_be, 576);
+        uint8_t hdr[12];
+        put_be32(hdr, k); put_be32(hdr + 4, S.b); put_be32(hdr + 8, nk);
+        sha256_update(c, hdr, 12);
+        sha256_update(c, blk, 96 * nk);
+        sha256_final(c, B.hstmt);
+    }
+    uint8_t xprev[32];
+    for (int j = 1; j <= lr; j++) {
+        const uint8_t* rd = fc + (size_t)(j - 1) * ROUND_BYTES;
+        const fr x = hash_to_fr_nonzero("FP-x", 4, xprev, j > 1 ? 32 : 0, rd, ROUND_BYTES, nullptr, 0);
+        B.x[j - 1] = x;
+        B.xinv[j - 1] = fr_inv(x);
+        fr_to_be(xprev, x);
+    }
+    const uint8_t* tail = fc + (size_t)lr * ROUND_BYTES;
+    if (!g1_decode(tail, B.Al) || !g2_decode(tail + G1_SER, B.vl) || !g2_decode(tail + G1_SER + G2_SER, B.W))
+        bad |= 2;
+    const fr z = hash_to_fr("FP-z", 4, xprev, 32, tail + G1_SER, G2_SER, nullptr, 0);
+    B.z = z;
+    fr zp[34];
+    zp[0] = z;
+    for (int e = 1; e <= lr + 1; e++) zp[e] = fr_mul(zp[e - 1], zp[e - 1]);
+    fr one, Pz;
+    fr_one(one);
+    Pz = one;
+    for (int j = 1; j <= lr; j++) Pz = fr_mul(Pz, fr_add(one, fr_mul(B.xinv[j - 1], zp[lr - j + 1])));
+    B.Pz = Pz;
+    B.bad = bad;
+}
+
+// per block tpb term slots (a power of two): r_a C_a for its nk rows, then x_j L_j.1 and
+// x_j^-1 R_j.1; the b_l summands r_a prod_k x_k^-(bit l - k of a) at wt[q b + t].  Unused slots
+// keep the identity the caller cleared them to.
+__global__ void k_vb_terms(VSrc S, VBlk* st, uint32_t tpb, g1j* T, fr* wt) {
+    const uint64_t t = gtid();
+    if (t >= (uint64_t)S.nb * tpb) return;
+    const uint32_t q = (uint32_t)(t / tpb), u = (uint32_t)(t % tpb), nk = S.nk(q);
+    const int lr = S.lr;
+    if (u >= nk + 2 * (uint32_t)lr) return;
+    VBlk& B = st[q];
+    g1a P;
+    uint32_t kw[8];
+    if (u < nk) {
+        const uint32_t a = S.lo(q) + u;
+        if (!g1_decode(S.blk + q * S.blk_stride + 96 * (size_t)u, P)) atomicOr(&B.bad, 32u);
+        uint8_t buf[36];
+        for (int c = 0; c < 32; c++) buf[c] = B.hstmt[c];
+        put_be32(buf + 32, a);
+        const fr r = hash_to_fr("FP-r", 4, buf, 36, nullptr, 0, nullptr, 0);
+        fr w = r;
+        for (int kk = 1; kk <= lr; kk++)
+            if ((a >> (lr - kk)) & 1) w = fr_mul(w, B.xinv[kk - 1]);
+        wt[(size_t)q * S.b + u] = w;
+        fr_canon_words(kw, r);
+    } else {
+        const int v = (int)(u - nk), jj = v >> 1, side = v & 1;
+        const uint8_t* rd = S.fc + q * S.fc_stride + (size_t)jj * ROUND_BYTES;
+        if (!g1_decode(rd + (side ? GT_SER + G1_SER + GT_SER : GT_SER), P)) atomicOr(&B.bad, 64u);
+        fr_canon_words(kw, side ? B.xinv[jj] : B.x[jj]);
+    }
+    T[t] = g1_mul(P, kw);
+}
+
+__global__ void k_vb_scalars(VSrc S, const fr* wt, VBlk* st) {
+    const uint64_t q = gtid();
+    if (q >= S.nb) return;
+    fr s;
+    fr_zero(s);
+    const uint32_t nk = S.nk((uint32_t)q);
+    for (uint32_t u = 0; u < nk; u++) s = fr_add(s, wt[q * S.b + u]);
+    st[q].bl = s;
+}
+
+// per block: 0: b_l A_l, 1: z g1, 2: P(z) g2
+__global__ void k_vb_muls(VBlk* st, uint32_t nb) {
+    const uint64_t t = gtid();
+    if (t >= 3 * (uint64_t)nb) return;
+    VBlk& B = st[t / 3];
+    uint32_t kw[8];
+    switch (t % 3) {
+        case 0: fr_canon_words(kw, B.bl); B.blA = g1_mul(B.Al, kw); break;
+        case 1: fr_canon_words(kw, B.z); B.zg = g1_mul(g1_generator(), kw); break;
+        default: fr_canon_words(kw, B.Pz); B.Pzg = g2_mul(g2_generator(), kw); break;
+    }
+}
+
+// block q's pairs at 3q: (A_l, v_l), (g1^beta - z g1, W), (-g1, v_l - P(z) g2); and b_l A_l
+// against the folded G1 part c1[q]
+__global__ void k_vb_pairs(uint32_t nb, const g1a* g1beta, const g1j* c1, VBlk* st, g1a* P, g2a* Q) {
+    const uint64_t q = gtid();
+    if (q >= nb) return;
+    VBlk& B = st[q];
+    if (!jac_eq(c1[q], B.blA)) atomicOr(&B.bad, 128u);
+    P[3 * q] = B.Al;
+    Q[3 * q] = B.vl;
+    P[3 * q + 1] = g1_affine(g1_madd(g1j_neg(B.zg), g1beta[0]));
+    Q[3 * q + 1] = B.W;
+    P[3 * q + 2] = g1a_neg(g1_generator());
+    Q[3 * q + 2] = g2_affine(g2_madd(g2j{B.Pzg.X, fq2_neg(B.Pzg.Y), B.Pzg.Z}, B.vl));
+}
+
+// one 128-thread block per pair
+__global__ void __launch_bounds__(128) k_v_miller(const g1a* P, const g2a* Q, fq12* out) {
+    __shared__ WMill S;
+    const int L = threadIdx.x;
+    const uint64_t j = blockIdx.x;
+    w_miller<4>(S, P[j], Q[j]);
+    if (L < 12) reinterpret_cast<fq*>(&out[j])[2 * w_tower_pos(L >> 1) + (L & 1)] = S.f[L];
+}
+
+// L_j.T^(x_j) and R_j.T^(1/x_j) of block q at 2 lr q + 2 (j - 1) + side
+__global__ void __launch_bounds__(128) k_vb_gt(VSrc S, VBlk* st, fq12* out) {
+    __shared__ W12 W;
+    const int L = threadIdx.x;
+    const int per = 2 * S.lr;
+    const uint32_t q = blockIdx.x / per;
+    const int jj = (blockIdx.x % per) >> 1, side = blockIdx.x & 1;
+    VBlk& B = st[q];
+    const uint8_t* rd = S.fc + q * S.fc_stride + (size_t)jj * ROUND_BYTES + (side ? GT_SER + G1_SER : 0);
+    if (L < 12) {
+        const int pos = 2 * w_tower_pos(L >> 1) + (L & 1);
+        fq v;
+        if (!fq_from_be48(rd + 48 * pos, v)) {
+            atomicOr(&B.bad, 1024u);
+            fq_zero(v);
+        }
+        W.s[0][L] = v;
+    }
+    __syncthreads();
+    uint32_t kw[8];
+    fr_canon_words(kw, side ? B.xinv[jj] : B.x[jj]);
+    w_exp<4>(W, W.s[1], W.s[0], kw, 256);
+    if (L < 12) reinterpret_cast<fq*>(&out[blockIdx.x])[2 * w_tower_pos(L >> 1) + (L & 1)] = W.s[1][L];
+}
+
+// per block: the folded C, and the inputs of its two final exponentiations (e(A_l, v_l) and the
+// fast-verification product) at fe_in[2q], fe_in[2q + 1]
+__global__ void k_vb_prod(const fq12* ml, const fq12* ge, const fq12* Cd, uint32_t nb, int lr, fq12* fe_in,
+                          fq12* cT) {
+    const uint64_t q = gtid();
+    if (q >= nb) return;
+    fq12 c = *Cd;
+    for (int t = 0; t < 2 * lr; t++) c = fq12_mul(c, ge[q * 2 * lr + t]);
+    cT[q] = c;
+    fe_in[2 * q] = ml[3 * q];
+    fe_in[2 * q + 1] = fq12_mul(ml[3 * q + 1], ml[3 * q + 2]);
+}
+
+__global__ void k_vb_check(const fq12* fe_out, const fq12* cT, const uint32_t* cbad, const VBlk* st, uint32_t nb,
+                           uint32_t* res) {
+    const uint64_t q = gtid();
+    if (q >= nb) return;
+    fq12 one;
+    fq12_one(one);
+    uint32_t bad = st[q].bad | *cbad;
+    if (!fq12_eq(fe_out[2 * q], cT[q])) bad |= 2048;
+    if (!fq12_eq(fe_out[2 * q + 1], one)) bad |= 4096;
+    res[q] = bad;
+}
+
+// ------------------------------------------------------------------------------ PST checks
+// A PST job q checks e(E_q, g2) prod_t e(-pi_t, g2^tau_t - a_t g2) = 1 for column a_q, with
+// E_q = D* - y* g1.  pi_t comes from one proof's PST part (idx = l_c - 1 - t, contiguous) or from
+// the stored table of HyperEval proofs (level t at offset sum_{u<t} M / 2^(u+1), node a >> (t+1)).
+struct PiSrc {
+    const uint8_t* base;
+    int table;
+    uint32_t M;
+    int lc;
+    FPG_DEV const uint8_t* at(uint32_t a, int idx) const {
+        if (!table) return base + 96 * (size_t)idx;
+        const int t = lc - 1 - idx;
+        uint64_t off = 0;
+        for (int u = 0; u < t; u++) off += M >> (u + 1);
+        return base + (off + (a >> (t + 1))) * G1_SER;
+    }
+};
+
+// pairs of job q at (lc + 1) q: idx < lc: (-pi_idx, g2^tau_t - a_t g2); idx = lc: (E_q, g2)
+__global__ void k_vp_pairs(PiSrc pi, const uint32_t* job_a, uint32_t a0, const g1a* E, uint32_t nj,
+                           const g2a* g2tau, uint32_t* job_bad, g1a* P, g2a* Q) {
+    const uint64_t t = gtid();
+    const int lc = pi.lc;
+    if (t >= (uint64_t)nj * (lc + 1)) return;
+    const uint32_t q = (uint32_t)(t / (lc + 1));
+    const int idx = (int)(t % (lc + 1));
+    const uint32_t a = job_a ? job_a[q] : a0 + q;
+    if (idx == lc) {
+        P[t] = E[q];
+        Q[t] = g2_generator();
+        return;
+    }
+    const int tt = lc - 1 - idx;
+    g1a p;
+    if (!g1_decode(pi.at(a, idx), p)) atomicOr(&job_bad[q], 512u);
+    P[t] = g1a_neg(p);
+    g2a v = g2tau[tt];
+    if ((a >> tt) & 1) v = g2_affine(g2_madd(g2_from_affine(v), g2a_negate(g2_generator())));
+    Q[t] = v;
+}
+
+// out[q] = prod_{u < per} ml[per q + u]
+__global__ void k_vp_prod(const fq12* ml, uint32_t per, uint32_t nj, fq12* out) {
+    const uint64_t q = gtid();
+    if (q >= nj) return;
+    fq12 p = ml[q * per];
+    for (uint32_t u = 1; u < per; u++) p = fq12_mul(p, ml[q * per + u]);
+    out[q] = p;
+}
+
+// job q's result (decode failures | the pairing check) at res[idx ? idx[q0 + q] : q]
+__global__ void k_vp_check(const fq12* fe_out, const uint32_t* job_bad, uint32_t nj, const uint32_t* idx, uint32_t q0,
+                           uint32_t* res) {
+    const uint64_t q = gtid();
+    if (q >= nj) return;
+    fq12 one;
+    fq12_one(one);
+    uint32_t bad = job_bad[q];
+    if (!fq12_eq(fe_out[q], one)) bad |= 8192;
+    res[idx ? idx[q0 + q] : q] = bad;
+}
+
+// ------------------------------------------------------------------------------ one proof
+struct VElem {
+    uint32_t bad;
+    fr rj, ys;
+    g1a Cj;
+    g1j ysg, rjCj;
+};
 
 // offsets inside a proof of block size nk: block | pi_Ck | path | siblings | pst
 struct VLayout {
@@ -100,288 +420,457 @@ struct VLayout {
     __host__ __device__ size_t pst() const { return sib() + 128 * (size_t)lr; }
 };
 
-__global__ void k_v_transcript(const uint8_t* proof, const uint8_t* C_be, const uint8_t* mi_be, VLayout Ly, uint32_t b,
-                               uint64_t i, uint32_t M, uint32_t k, uint32_t lo, VState* st) {
+// Merkle path of (i, m_i) up the row tree, the row leaf with C_j, up the top tree; r_j; y*
+__global__ void k_v_elem(const uint8_t* proof, const uint8_t* mi_be, VLayout Ly, uint64_t i, uint32_t M, uint32_t lo,
+                         VElem* e) {
     if (gtid() != 0) return;
     uint32_t bad = 0;
-    const uint8_t* blk = proof;
-    const uint8_t* fc = proof + Ly.fc();
     const int lr = Ly.lr, lc = Ly.lc;
-    if (!fq12_decode(C_be, st->C)) bad |= 1;
-    // statement hash and the round challenges
-    {
-        sha256_ctx c;
-        sha256_init(c);
-        sha256_update(c, C_be, 576);
-        uint8_t hdr[12];
-        put_be32(hdr, k); put_be32(hdr + 4, b); put_be32(hdr + 8, Ly.nk);
-        sha256_update(c, hdr, 12);
-        sha256_update(c, blk, 96 * Ly.nk);
-        sha256_final(c, st->hstmt);
-    }
-    uint8_t xprev[32];
-    for (int j = 1; j <= lr; j++) {
-        const uint8_t* rd = fc + (size_t)(j - 1) * ROUND_BYTES;
-        const fr x = hash_to_fr_nonzero("FP-x", 4, xprev, j > 1 ? 32 : 0, rd, ROUND_BYTES, nullptr, 0);
-        st->x[j - 1] = x;
-        st->xinv[j - 1] = fr_inv(x);
-        fr_to_be(xprev, x);
-    }
-    const uint8_t* tail = fc + (size_t)lr * ROUND_BYTES;
-    if (!g1_decode(tail, st->Al) || !g2_decode(tail + G1_SER, st->vl) || !g2_decode(tail + G1_SER + G2_SER, st->W))
-        bad |= 2;
-    // z and P(z) = prod_j (1 + x_j^-1 z^(2^(l - j + 1)))
-    const fr z = hash_to_fr("FP-z", 4, xprev, 32, tail + G1_SER, G2_SER, nullptr, 0);
-    st->z = z;
-    fr zp[34];
-    zp[0] = z;
-    for (int e = 1; e <= lr + 1; e++) zp[e] = fr_mul(zp[e - 1], zp[e - 1]);
-    fr one, Pz;
-    fr_one(one);
-    Pz = one;
-    for (int j = 1; j <= lr; j++) Pz = fr_mul(Pz, fr_add(one, fr_mul(st->xinv[j - 1], zp[lr - j + 1])));
-    st->Pz = Pz;
-    // Merkle path: leaf of (i, m_i) up the row tree, the row leaf with C_j, up the top tree
     const uint32_t j = (uint32_t)(i / M), a = (uint32_t)(i % M);
+    const uint8_t* Cj_be = proof + 96 * (size_t)(j - lo);
     const uint8_t* path = proof + Ly.path();
-    uint8_t cur[32], buf[7 + 64 + 96];
-    for (int q = 0; q < 7; q++) buf[q] = (uint8_t)"FP-leaf"[q];
-    put_be64(buf + 7, i);
-    for (int q = 0; q < 32; q++) buf[15 + q] = mi_be[q];
-    sha256(cur, buf, 7 + 8 + 32);
-    for (int l = 0; l < lc + lr; l++) {
-        if (l == lc) {                                     // row leaf
-            for (int q = 0; q < 6; q++) buf[q] = (uint8_t)"FP-row"[q];
-            for (int q = 0; q < 32; q++) buf[6 + q] = cur[q];
-            for (int q = 0; q < 96; q++) buf[38 + q] = blk[96 * (size_t)(j - lo) + q];
-            sha256(cur, buf, 6 + 32 + 96);
-        }
-        const bool right = l < lc ? ((a >> l) & 1) : ((j >> (l - lc)) & 1);
-        for (int q = 0; q < 7; q++) buf[q] = (uint8_t)"FP-node"[q];
-        for (int q = 0; q < 32; q++) {
-            buf[7 + q] = right ? path[32 * l + q] : cur[q];
-            buf[39 + q] = right ? cur[q] : path[32 * l + q];
-        }
-        sha256(cur, buf, 7 + 64);
-    }
-    uint8_t rb[36];
-    for (int q = 0; q < 32; q++) rb[q] = cur[q];
-    put_be32(rb + 32, j);
-    st->rj = hash_to_fr("FP-rho", 6, rb, 36, nullptr, 0, nullptr, 0);
-    // y* = r_j m_i + sum_w y_w
+    uint8_t cur[32];
+    leaf_hash(cur, i, mi_be);
+    for (int l = 0; l < lc; l++) node_hash(cur, path + 32 * l, (a >> l) & 1);
+    row_leaf_hash(cur, Cj_be);
+    for (int l = 0; l < lr; l++) node_hash(cur, path + 32 * (lc + l), (j >> l) & 1);
+    e->rj = row_rho(cur, j);
     fr mi, ys;
     if (!fr_from_be32(mi_be, mi)) bad |= 4;
-    ys = fr_mul(st->rj, mi);
+    ys = fr_mul(e->rj, mi);
     const uint8_t* sib = proof + Ly.sib();
     for (int h = 0; h < lr; h++) {
         fr y;
         if (!fr_from_be32(sib + 128 * h + 96, y)) bad |= 8;
         ys = fr_add(ys, y);
     }
-    st->ys = ys;
-    if (!g1_decode(blk + 96 * (size_t)(j - lo), st->Cj)) bad |= 16;
-    st->bad = bad;
+    e->ys = ys;
+    if (!g1_decode(Cj_be, e->Cj)) bad |= 16;
+    e->bad = bad;
 }
 
-// terms of C_0's G1 part and the rounds' G1 parts (Jacobian), and the b_l summands
-__global__ void k_v_terms(const uint8_t* proof, VLayout Ly, uint32_t lo, VState* st, g1j* T, fr* wt) {
+// 0: y* g1, 1: r_j C_j
+__global__ void k_v_elem_muls(VElem* e) {
     const uint64_t t = gtid();
-    const uint32_t nk = Ly.nk;
-    const int lr = Ly.lr;
-    if (t >= nk + 2 * (uint64_t)lr) return;
-    g1a P;
+    if (t >= 2) return;
     uint32_t kw[8];
-    if (t < nk) {
-        const uint32_t a = lo + (uint32_t)t;
-        if (!g1_decode(proof + 96 * t, P)) atomicOr(&st->bad, 32u);
-        uint8_t buf[36];
-        for (int q = 0; q < 32; q++) buf[q] = st->hstmt[q];
-        put_be32(buf + 32, a);
-        const fr r = hash_to_fr("FP-r", 4, buf, 36, nullptr, 0, nullptr, 0);
-        fr w = r;
-        for (int kk = 1; kk <= lr; kk++)
-            if ((a >> (lr - kk)) & 1) w = fr_mul(w, st->xinv[kk - 1]);
-        wt[t] = w;
-        fr_canon_words(kw, r);
+    if (t == 0) {
+        fr_canon_words(kw, e->ys);
+        e->ysg = g1_mul(g1_generator(), kw);
     } else {
-        const int u = (int)(t - nk), jj = u >> 1, side = u & 1;
-        const uint8_t* rd = proof + Ly.fc() + (size_t)jj * ROUND_BYTES;
-        if (!g1_decode(rd + (side ? GT_SER + G1_SER + GT_SER : GT_SER), P)) atomicOr(&st->bad, 64u);
-        fr_canon_words(kw, side ? st->xinv[jj] : st->x[jj]);
-    }
-    T[t] = g1_mul(P, kw);
-}
-
-__global__ void k_v_scalars(const fr* wt, uint32_t nk, VState* st) {
-    if (gtid() != 0) return;
-    fr s;
-    fr_zero(s);
-    for (uint32_t t = 0; t < nk; t++) s = fr_add(s, wt[t]);
-    st->bl = s;
-}
-
-// 0: b_l A_l, 1: z g1, 2: y* g1, 3: r_j C_j, 4: P(z) g2
-__global__ void k_v_muls(VState* st) {
-    const uint64_t t = gtid();
-    if (t >= 5) return;
-    uint32_t kw[8];
-    switch (t) {
-        case 0: fr_canon_words(kw, st->bl); st->blA = g1_mul(st->Al, kw); break;
-        case 1: fr_canon_words(kw, st->z); st->zg = g1_mul(g1_generator(), kw); break;
-        case 2: fr_canon_words(kw, st->ys); st->ysg = g1_mul(g1_generator(), kw); break;
-        case 3: fr_canon_words(kw, st->rj); st->rjCj = g1_mul(st->Cj, kw); break;
-        default: fr_canon_words(kw, st->Pz); st->Pzg = g2_mul(g2_generator(), kw); break;
+        fr_canon_words(kw, e->rj);
+        e->rjCj = g1_mul(e->Cj, kw);
     }
 }
 
-// the pairs: 0 (A_l, v_l); 1 (g1^beta - z g1, W), 2 (-g1, v_l - P(z) g2); 3 (D* - y* g1, g2),
-// 4 + idx (-pi_idx, g2^tau_t - a_t g2) with t = l_c - 1 - idx; also b_l A_l == the folded G1 part
-__global__ void k_v_pairs(const uint8_t* proof, VLayout Ly, uint32_t a, const g1a* g1beta, const g2a* g2tau,
-                          const g1j* c1, VState* st, g1a* P, g2a* Q) {
+// E = D* - y* g1 with D* = r_j C_j + sum_w D_w
+__global__ void k_v_elem_E(const uint8_t* proof, VLayout Ly, VElem* e, g1a* E) {
     if (gtid() != 0) return;
-    const int lr = Ly.lr, lc = Ly.lc;
-    uint32_t bad = 0;
-    if (!jac_eq(c1[0], st->blA)) bad |= 128;
-    const g1a g1 = g1_generator();
-    const g2a g2 = g2_generator();
-    P[0] = st->Al;
-    Q[0] = st->vl;
-    P[1] = g1_affine(g1_madd(g1j_neg(st->zg), g1beta[0]));
-    Q[1] = st->W;
-    P[2] = g1a_neg(g1);
-    Q[2] = g2_affine(g2_madd(g2j{st->Pzg.X, fq2_neg(st->Pzg.Y), st->Pzg.Z}, st->vl));
-    g1j Ds = st->rjCj;
+    g1j Ds = e->rjCj;
     const uint8_t* sib = proof + Ly.sib();
-    for (int h = 0; h < lr; h++) {
+    for (int h = 0; h < Ly.lr; h++) {
         g1a D;
-        if (!g1_decode(sib + 128 * h, D)) bad |= 256;
+        if (!g1_decode(sib + 128 * h, D)) atomicOr(&e->bad, 256u);
         Ds = g1_madd(Ds, D);
     }
-    P[3] = g1_affine(jac_add(Ds, g1j_neg(st->ysg)));
-    Q[3] = g2;
-    const uint8_t* pst = proof + Ly.pst();
-    for (int idx = 0; idx < lc; idx++) {
-        const int t = lc - 1 - idx;
-        g1a pi;
-        if (!g1_decode(pst + 96 * idx, pi)) bad |= 512;
-        P[4 + idx] = g1a_neg(pi);
-        g2a q = g2tau[t];
-        if ((a >> t) & 1) q = g2_affine(g2_madd(g2_from_affine(q), g2a_negate(g2)));
-        Q[4 + idx] = q;
-    }
-    atomicOr(&st->bad, bad);
+    E[0] = g1_affine(jac_add(Ds, g1j_neg(e->ysg)));
 }
 
-__global__ void __launch_bounds__(128) k_v_miller(const g1a* P, const g2a* Q, fq12* out) {
-    __shared__ WMill S;
-    const int L = threadIdx.x;
-    const uint64_t j = blockIdx.x;
-    w_miller<4>(S, P[j], Q[j]);
-    if (L < 12) reinterpret_cast<fq*>(&out[j])[2 * w_tower_pos(L >> 1) + (L & 1)] = S.f[L];
-}
-
-// L_j.T^(x_j) (block 2 (j-1)) and R_j.T^(1/x_j) (block 2 (j-1) + 1)
-__global__ void __launch_bounds__(128) k_v_gt(const uint8_t* proof, VLayout Ly, VState* st, fq12* out) {
-    __shared__ W12 W;
-    const int L = threadIdx.x;
-    const int jj = blockIdx.x >> 1, side = blockIdx.x & 1;
-    const uint8_t* rd = proof + Ly.fc() + (size_t)jj * ROUND_BYTES + (side ? GT_SER + G1_SER : 0);
-    if (L < 12) {
-        const int pos = 2 * w_tower_pos(L >> 1) + (L & 1);
-        fq v;
-        if (!fq_from_be48(rd + 48 * pos, v)) {
-            atomicOr(&st->bad, 1024u);
-            fq_zero(v);
-        }
-        W.s[0][L] = v;
-    }
-    __syncthreads();
-    uint32_t kw[8];
-    fr_canon_words(kw, side ? st->xinv[jj] : st->x[jj]);
-    w_exp<4>(W, W.s[1], W.s[0], kw, 256);
-    if (L < 12) reinterpret_cast<fq*>(&out[blockIdx.x])[2 * w_tower_pos(L >> 1) + (L & 1)] = W.s[1][L];
-}
-
-// inputs of the three final exponentiations: e(A_l, v_l), the fast-verification product, the PST
-// product; and the folded C
-__global__ void k_v_prod(const fq12* ml, int np, const fq12* ge, int lr, VState* st, fq12* fe_in, fq12* cT) {
+__global__ void k_v_result(const uint32_t* blk_res, const VElem* e, const uint32_t* pst_res, uint32_t* result) {
     if (gtid() != 0) return;
-    fq12 c = st->C;
-    for (int t = 0; t < 2 * lr; t++) c = fq12_mul(c, ge[t]);
-    cT[0] = c;
-    fe_in[0] = ml[0];
-    fe_in[1] = fq12_mul(ml[1], ml[2]);
-    fq12 p = ml[3];
-    for (int t = 4; t < np; t++) p = fq12_mul(p, ml[t]);
-    fe_in[2] = p;
+    result[0] = blk_res[0] | e->bad | pst_res[0];
 }
 
-__global__ void k_v_check(const fq12* fe_out, const fq12* cT, VState* st, uint32_t* result) {
-    if (gtid() != 0) return;
-    fq12 one;
-    fq12_one(one);
-    uint32_t bad = st->bad;
-    if (!fq12_eq(fe_out[0], cT[0])) bad |= 2048;
-    if (!fq12_eq(fe_out[1], one)) bad |= 4096;
-    if (!fq12_eq(fe_out[2], one)) bad |= 8192;
-    result[0] = bad;
+namespace {
+
+// carves a scratch buffer into 256-byte aligned pieces (SizeArena: the same walk, sizes only)
+struct Arena {
+    uint8_t* p;
+    void* take(size_t bytes) {
+        uint8_t* r = p;
+        p += (bytes + 255) & ~(size_t)255;
+        return r;
+    }
+};
+struct SizeArena {
+    size_t n = 0;
+    void* take(size_t bytes) {
+        n += (bytes + 255) & ~(size_t)255;
+        return nullptr;
+    }
+};
+
+uint32_t pow2_at_least(uint64_t n) {
+    uint32_t p = 1;
+    while (p < n) p <<= 1;
+    return p;
 }
+
+// scratch of the checks of nb blocks of size b
+template <class A>
+struct BlockBufs {
+    VBlk* st; g1j* T; g1j* T2; fr* wt; g1a* P; g2a* Q; fq12* ml; fq12* ge; fq12* fe_in; fq12* fe_out; fq12* cT;
+    uint32_t* res;
+    BlockBufs(A& ar, uint32_t nb, uint32_t b, int lr) {
+        const uint64_t tpb = pow2_at_least(b + 2 * (uint64_t)lr);
+        st = (VBlk*)ar.take(nb * sizeof(VBlk));
+        T = (g1j*)ar.take(nb * tpb * G1J_BYTES);
+        T2 = (g1j*)ar.take((nb * tpb / 2 + 1) * G1J_BYTES);
+        wt = (fr*)ar.take((size_t)nb * b * FR_BYTES);
+        P = (g1a*)ar.take(3 * (size_t)nb * G1A_BYTES);
+        Q = (g2a*)ar.take(3 * (size_t)nb * G2A_BYTES);
+        ml = (fq12*)ar.take(3 * (size_t)nb * FQ12_BYTES);
+        ge = (fq12*)ar.take(2 * (size_t)lr * nb * FQ12_BYTES);
+        fe_in = (fq12*)ar.take(2 * (size_t)nb * FQ12_BYTES);
+        fe_out = (fq12*)ar.take(2 * (size_t)nb * FQ12_BYTES);
+        cT = (fq12*)ar.take((size_t)nb * FQ12_BYTES);
+        res = (uint32_t*)ar.take((size_t)nb * 4);
+    }
+};
+
+// scratch of nj PST jobs with lc + 1 pairs each
+template <class A>
+struct JobBufs {
+    g1a* E; uint32_t* a; uint32_t* bad; g1a* P; g2a* Q; fq12* ml; fq12* fe_in; fq12* fe_out;
+    JobBufs(A& ar, uint32_t nj, int lc) {
+        const size_t np = (size_t)nj * (lc + 1);
+        E = (g1a*)ar.take((size_t)nj * G1A_BYTES);
+        a = (uint32_t*)ar.take((size_t)nj * 4);
+        bad = (uint32_t*)ar.take((size_t)nj * 4);
+        P = (g1a*)ar.take(np * G1A_BYTES);
+        Q = (g2a*)ar.take(np * G2A_BYTES);
+        ml = (fq12*)ar.take(np * FQ12_BYTES);
+        fe_in = (fq12*)ar.take((size_t)nj * FQ12_BYTES);
+        fe_out = (fq12*)ar.take((size_t)nj * FQ12_BYTES);
+    }
+};
+
+// the block checks up to their pairs (at Bb.P / Bb.Q, three per block)
+template <class A>
+void block_checks_front(const VSrc& S, const uint8_t* C_be, const g1a* g1beta, BlockBufs<A>& Bb, cudaStream_t s) {
+    const uint32_t tpb = pow2_at_least(S.b + 2 * (uint64_t)S.lr);
+    const uint64_t nt = (uint64_t)S.nb * tpb;
+    cudaMemsetAsync(Bb.T, 0, nt * G1J_BYTES, s);
+    FP_KERNEL("k_vb_transcript", s, k_vb_transcript<<<grid_for(S.nb, 32), 32, 0, s>>>(S, C_be, Bb.st));
+    FP_KERNEL("k_vb_terms", s, k_vb_terms<<<grid_for(nt, 64), 64, 0, s>>>(S, Bb.st, tpb, Bb.T, Bb.wt));
+    g1j* x = Bb.T;
+    g1j* y = Bb.T2;
+    for (uint64_t n = nt; n > S.nb; n /= 2) {            // per-block sums: tpb is a power of two
+        g1_pair_reduce(x, y, n / 2, s);
+        std::swap(x, y);
+    }
+    FP_KERNEL("k_vb_scalars", s, k_vb_scalars<<<grid_for(S.nb, 64), 64, 0, s>>>(S, Bb.wt, Bb.st));
+    FP_KERNEL("k_vb_muls", s, k_vb_muls<<<grid_for(3 * (uint64_t)S.nb, 64), 64, 0, s>>>(Bb.st, S.nb));
+    FP_KERNEL("k_vb_pairs", s, k_vb_pairs<<<grid_for(S.nb, 64), 64, 0, s>>>(S.nb, g1beta, x, Bb.st, Bb.P, Bb.Q));
+}
+
+// verify_one's scratch: the block's buffers, the element state, and the pairs of the block's
+// three and the PST job's lc + 1 checks (one Miller launch for all)
+template <class A>
+struct OneBufs {
+    fq12* Cd; uint32_t* cbad; VElem* e; BlockBufs<A> Bb; g1a* P; g2a* Q; fq12* ml; fq12* fe_in; fq12* fe_out;
+    g1a* E; uint32_t* job_bad; uint32_t* pst_res;
+    OneBufs(A& ar, uint32_t b, int lr, int lc)
+        : Cd((fq12*)ar.take(FQ12_BYTES)), cbad((uint32_t*)ar.take(4)), e((VElem*)ar.take(sizeof(VElem))),
+          Bb(ar, 1, b, lr) {
+        const int np = 3 + lc + 1;
+        P = (g1a*)ar.take((size_t)np * G1A_BYTES);
+        Q = (g2a*)ar.take((size_t)np * G2A_BYTES);
+        ml = (fq12*)ar.take((size_t)np * FQ12_BYTES);
+        fe_in = (fq12*)ar.take(3 * FQ12_BYTES);
+        fe_out = (fq12*)ar.take(3 * FQ12_BYTES);
+        E = (g1a*)ar.take(G1A_BYTES);
+        job_bad = (uint32_t*)ar.take(4);
+        pst_res = (uint32_t*)ar.take(4);
+        Bb.P = P;
+        Bb.Q = Q;
+        Bb.ml = ml;
+    }
+};
+
+}  // namespace
 
 void verify_one(const void* proof, const void* C_be, const void* mi_be, uint32_t nk, int lr, int lc, uint32_t b,
                 uint64_t i, uint32_t M, uint32_t k, uint32_t lo, const void* g1beta, const void* g2tau, void* scratch,
                 uint32_t* result, cudaStream_t s) {
     const VLayout Ly{nk, lr, lc};
-    const uint64_t nterms = nk + 2 * (uint64_t)lr;
-    uint64_t n1 = 1;
-    while (n1 < nterms) n1 <<= 1;
-    const int np = 4 + lc;
-    uint8_t* p = (uint8_t*)scratch;
-    auto take = [&](size_t bytes) {
-        uint8_t* r = p;
-        p += (bytes + 255) & ~(size_t)255;
-        return (void*)r;
-    };
-    VState* st = (VState*)take(sizeof(VState));
-    g1j* T = (g1j*)take(n1 * G1J_BYTES);
-    g1j* T2 = (g1j*)take((n1 / 2 + 1) * G1J_BYTES);
-    fr* wt = (fr*)take((size_t)nk * FR_BYTES);
-    g1a* P = (g1a*)take((size_t)np * G1A_BYTES);
-    g2a* Q = (g2a*)take((size_t)np * G2A_BYTES);
-    fq12* ml = (fq12*)take((size_t)np * FQ12_BYTES);
-    fq12* ge = (fq12*)take(2 * (size_t)lr * FQ12_BYTES);
-    fq12* fe_in = (fq12*)take(3 * FQ12_BYTES);
-    fq12* fe_out = (fq12*)take(3 * FQ12_BYTES);
-    fq12* cT = (fq12*)take(FQ12_BYTES);
-    cudaMemsetAsync(T, 0, n1 * G1J_BYTES, s);
     const uint8_t* pr = (const uint8_t*)proof;
-    FP_KERNEL("k_v_transcript", s, k_v_transcript<<<1, 32, 0, s>>>(pr, (const uint8_t*)C_be, (const uint8_t*)mi_be, Ly,
-                                                                   b, i, M, k, lo, st));
-    FP_KERNEL("k_v_terms", s, k_v_terms<<<grid_for(nterms, 64), 64, 0, s>>>(pr, Ly, lo, st, T, wt));
-    g1j* a = T;
-    g1j* bb = T2;
-    for (uint64_t n = n1; n > 1; n /= 2) {
-        g1_pair_reduce(a, bb, n / 2, s);
-        std::swap(a, bb);
-    }
-    FP_KERNEL("k_v_scalars", s, k_v_scalars<<<1, 32, 0, s>>>(wt, nk, st));
-    FP_KERNEL("k_v_muls", s, k_v_muls<<<1, 32, 0, s>>>(st));
-    FP_KERNEL("k_v_pairs", s, k_v_pairs<<<1, 32, 0, s>>>(pr, Ly, (uint32_t)(i % M), (const g1a*)g1beta,
-                                                         (const g2a*)g2tau, a, st, P, Q));
-    FP_KERNEL("k_v_miller", s, k_v_miller<<<np, 128, 0, s>>>(P, Q, ml));
-    FP_KERNEL("k_v_gt", s, k_v_gt<<<2 * lr, 128, 0, s>>>(pr, Ly, st, ge));
-    FP_KERNEL("k_v_prod", s, k_v_prod<<<1, 32, 0, s>>>(ml, np, ge, lr, st, fe_in, cT));
-    final_exp_group(fe_in, 3, fe_out, nullptr, 1, 0, 0, s);
-    FP_KERNEL("k_v_check", s, k_v_check<<<1, 32, 0, s>>>(fe_out, cT, st, result));
+    const VSrc S{pr, 0, pr + Ly.fc(), 0, k, 1, b, lo + nk, lr};   // R = lo + nk gives nk(0) = nk
+    Arena ar{(uint8_t*)scratch};
+    OneBufs<Arena> O(ar, b, lr, lc);
+    const int np = 3 + lc + 1;
+    cudaMemsetAsync(O.job_bad, 0, 4, s);
+    FP_KERNEL("k_v_cdec", s, k_v_cdec<<<1, 32, 0, s>>>((const uint8_t*)C_be, O.Cd, O.cbad));
+    FP_KERNEL("k_v_elem", s, k_v_elem<<<1, 32, 0, s>>>(pr, (const uint8_t*)mi_be, Ly, i, M, lo, O.e));
+    block_checks_front(S, (const uint8_t*)C_be, (const g1a*)g1beta, O.Bb, s);
+    FP_KERNEL("k_v_elem_muls", s, k_v_elem_muls<<<1, 32, 0, s>>>(O.e));
+    FP_KERNEL("k_v_elem_E", s, k_v_elem_E<<<1, 32, 0, s>>>(pr, Ly, O.e, O.E));
+    const PiSrc pi{pr + Ly.pst(), 0, M, lc};
+    FP_KERNEL("k_vp_pairs", s, k_vp_pairs<<<1, 32, 0, s>>>(pi, nullptr, (uint32_t)(i % M), O.E, 1,
+                                                           (const g2a*)g2tau, O.job_bad, O.P + 3, O.Q + 3));
+    FP_KERNEL("k_v_miller", s, k_v_miller<<<np, 128, 0, s>>>(O.P, O.Q, O.ml));
+    FP_KERNEL("k_vb_gt", s, k_vb_gt<<<2 * lr, 128, 0, s>>>(S, O.Bb.st, O.Bb.ge));
+    FP_KERNEL("k_vb_prod", s, k_vb_prod<<<1, 32, 0, s>>>(O.ml, O.Bb.ge, O.Cd, 1, lr, O.fe_in, O.Bb.cT));
+    FP_KERNEL("k_vp_prod", s, k_vp_prod<<<1, 32, 0, s>>>(O.ml + 3, lc + 1, 1, O.fe_in + 2));
+    final_exp_group(O.fe_in, 3, O.fe_out, nullptr, 1, 0, 0, s);
+    FP_KERNEL("k_vb_check", s, k_vb_check<<<1, 32, 0, s>>>(O.fe_out, O.Bb.cT, O.cbad, O.Bb.st, 1, O.Bb.res));
+    FP_KERNEL("k_vp_check", s, k_vp_check<<<1, 32, 0, s>>>(O.fe_out + 2, O.job_bad, 1, nullptr, 0, O.pst_res));
+    FP_KERNEL("k_v_result", s, k_v_result<<<1, 32, 0, s>>>(O.Bb.res, O.e, O.pst_res, result));
 }
 
-size_t verify_scratch_bytes(uint32_t nk, int lr, int lc) {
-    uint64_t n1 = 1;
-    while (n1 < nk + 2 * (uint64_t)lr) n1 <<= 1;
-    const int np = 4 + lc;
-    auto r = [](size_t b) { return (b + 255) & ~(size_t)255; };
-    return r(sizeof(VState)) + r(n1 * G1J_BYTES) + r((n1 / 2 + 1) * G1J_BYTES) + r((size_t)nk * FR_BYTES) +
-           r((size_t)np * G1A_BYTES) + r((size_t)np * G2A_BYTES) + r((size_t)np * FQ12_BYTES) +
-           r(2 * (size_t)lr * FQ12_BYTES) + 2 * r(3 * FQ12_BYTES) + r(FQ12_BYTES) + 256;
+size_t verify_scratch_bytes(uint32_t b, int lr, int lc) {
+    SizeArena ar;
+    OneBufs<SizeArena> O(ar, b, lr, lc);
+    (void)O;
+    return ar.n + 256;
+}
+
+// ------------------------------------------------------------------------------ all proofs
+// Merkle root of every proof (from the stored trees) and the range check of its claimed m_i
+// (N x 4 little-endian u64)
+__global__ void k_va_paths(ProofLayout L, const uint64_t* m, const uint8_t* row_tree, const uint8_t* top_tree,
+                           const uint8_t* rows_ser, uint8_t* roots, uint8_t* mbad) {
+    const uint64_t i = gtid();
+    if (i >= (uint64_t)L.R * L.M) return;
+    const uint32_t j = (uint32_t)(i / L.M), a = (uint32_t)(i % L.M);
+    uint8_t mi_be[32];
+    uint64_t limb[4];
+    for (int w = 0; w < 4; w++) limb[w] = m[4 * i + w];
+    for (int w = 0; w < 4; w++) put_be64(mi_be + 8 * (3 - w), limb[w]);
+    fr c;
+    for (int w = 0; w < 4; w++) {
+        c.v[2 * w] = (uint32_t)limb[w];
+        c.v[2 * w + 1] = (uint32_t)(limb[w] >> 32);
+    }
+    mbad[i] = mp::lt<8>(c.v, FR_P) ? 0 : 1;
+    uint8_t cur[32];
+    leaf_hash(cur, i, mi_be);
+    const uint8_t* rt = row_tree + (size_t)j * (2 * (size_t)L.M - 1) * 32;
+    for (int l = 0; l < L.log_c; l++) node_hash(cur, rt + 32 * (tree_off(L.M, l) + ((a >> l) ^ 1)), (a >> l) & 1);
+    row_leaf_hash(cur, rows_ser + 96 * (size_t)j);
+    for (int l = 0; l < L.log_r; l++)
+        node_hash(cur, top_tree + 32 * (tree_off(L.R, l) + ((j >> l) ^ 1)), (j >> l) & 1);
+    for (int q = 0; q < 32; q++) roots[32 * i + q] = cur[q];
+}
+
+// per row, with the root of proof 0: r_j and D*_j = r_j C_j + sum_w D_w (affine)
+__global__ void k_va_rows(ProofLayout L, const uint8_t* roots, const uint8_t* rows_ser, const uint8_t* D_ser, fr* rj,
+                          g1a* Dstar, uint32_t* row_bad) {
+    const uint64_t j = gtid();
+    if (j >= L.R) return;
+    uint32_t bad = 0;
+    const fr r = row_rho(roots, (uint32_t)j);
+    rj[j] = r;
+    g1a Cj;
+    if (!g1_decode(rows_ser + 96 * j, Cj)) bad |= 16;
+    uint32_t kw[8];
+    fr_canon_words(kw, r);
+    g1j Ds = g1_mul(Cj, kw);
+    for (int h = 0; h < L.log_r; h++) {
+        g1a D;
+        if (!g1_decode(D_ser + G1_SER * (tree_off(L.R, h) + ((j >> h) ^ 1)), D)) bad |= 256;
+        Ds = g1_madd(Ds, D);
+    }
+    Dstar[j] = g1_affine(Ds);
+    row_bad[j] = bad;
+}
+
+// y* = r_j m_i + sum_w g_w[a] of every proof, r_j from the proof's own root
+__global__ void k_va_y(ProofLayout L, const uint64_t* m, const uint8_t* roots, const fr* rj, const fr* g,
+                       const uint8_t* mbad, fr* ys) {
+    const uint64_t i = gtid();
+    if (i >= (uint64_t)L.R * L.M) return;
+    const uint32_t j = (uint32_t)(i / L.M), a = (uint32_t)(i % L.M);
+    const fr r = digest_same(roots + 32 * i, roots) ? rj[j] : row_rho(roots + 32 * i, j);
+    fr mi;
+    fr_zero(mi);
+    if (!mbad[i]) {
+        for (int w = 0; w < 4; w++) {
+            const uint64_t v = m[4 * i + w];
+            mi.v[2 * w] = (uint32_t)v;
+            mi.v[2 * w + 1] = (uint32_t)(v >> 32);
+        }
+        mi = fr_to_mont(mi);
+    }
+    fr y = fr_mul(r, mi);
+    for (int h = 0; h < L.log_r; h++) y = fr_add(y, g[(tree_off(L.R, h) + ((j >> h) ^ 1)) * L.M + a]);
+    ys[i] = y;
+}
+
+// a proof shares its column's PST check when its root and the root of the column's row-0 proof
+// are proof 0's, its row's D* is row 0's, and its y* is the row-0 proof's; the others are listed
+__global__ void k_va_class(ProofLayout L, const uint8_t* roots, const g1a* Dstar, const fr* ys, int each,
+                           uint8_t* shared, uint32_t* irr, uint32_t* nirr) {
+    const uint64_t i = gtid();
+    if (i >= (uint64_t)L.R * L.M) return;
+    const uint32_t j = (uint32_t)(i / L.M), a = (uint32_t)(i % L.M);
+    const bool sh = !each && digest_same(roots + 32 * i, roots) && digest_same(roots + 32 * (uint64_t)a, roots) &&
+                    g1a_same(Dstar[j], Dstar[0]) && fr_same(ys[i], ys[a]);
+    shared[i] = sh;
+    if (!sh) irr[atomicAdd(nirr, 1u)] = (uint32_t)i;
+}
+
+// column jobs: E_a = D*_0 - y*_a g1
+__global__ void k_va_colE(const g1a* Dstar, const fr* ys, uint32_t M, g1a* E) {
+    const uint64_t a = gtid();
+    if (a >= M) return;
+    uint32_t kw[8];
+    fr_canon_words(kw, ys[a]);
+    E[a] = g1_affine(g1_madd(g1j_neg(g1_mul(g1_generator(), kw)), Dstar[0]));
+}
+
+// jobs of the listed proofs irr[q0 .. q0 + nj): E = r_j C_j + sum_w D_w - y* g1, r_j from the
+// proof's own root
+__global__ void k_va_irrE(ProofLayout L, const uint32_t* irr, uint32_t q0, uint32_t nj, const uint8_t* roots,
+                          const fr* ys, const uint8_t* rows_ser, const uint8_t* D_ser, g1a* E, uint32_t* job_a) {
+    const uint64_t q = gtid();
+    if (q >= nj) return;
+    const uint64_t i = irr[q0 + q];
+    const uint32_t j = (uint32_t)(i / L.M);
+    job_a[q] = (uint32_t)(i % L.M);
+    g1a Cj;
+    g1_decode(rows_ser + 96 * (size_t)j, Cj);         // a bad C_j or D_w fails the row's check
+    uint32_t kw[8];
+    fr_canon_words(kw, row_rho(roots + 32 * i, j));
+    g1j Ds = g1_mul(Cj, kw);
+    for (int h = 0; h < L.log_r; h++) {
+        g1a D;
+        g1_decode(D_ser + G1_SER * (tree_off(L.R, h) + ((j >> h) ^ 1)), D);
+        Ds = g1_madd(Ds, D);
+    }
+    fr_canon_words(kw, ys[i]);
+    E[q] = g1_affine(jac_add(Ds, g1j_neg(g1_mul(g1_generator(), kw))));
+}
+
+__global__ void k_va_result(ProofLayout L, const uint32_t* blk_res, const uint32_t* row_bad, const uint8_t* mbad,
+                            const uint8_t* shared, const uint32_t* col_res, const uint32_t* irr_res, uint8_t* ok,
+                            unsigned long long* n_ok) {
+    const uint64_t i = gtid();
+    bool good = false;
+    if (i < (uint64_t)L.R * L.M) {
+        const uint32_t j = (uint32_t)(i / L.M), a = (uint32_t)(i % L.M);
+        const uint32_t bad = blk_res[j / L.b] | row_bad[j] | mbad[i] | (shared[i] ? col_res[a] : irr_res[i]);
+        good = bad == 0;
+        ok[i] = good;
+    }
+    const unsigned mask = __ballot_sync(0xffffffffu, good);
+    if ((threadIdx.x & 31) == 0 && mask) atomicAdd(n_ok, (unsigned long long)__popc(mask));
+}
+
+namespace {
+
+template <class A>
+struct AllBufs {
+    fq12* Cd; uint32_t* cbad; uint8_t* roots; uint8_t* mbad; fr* ys; uint8_t* shared; fr* rj; g1a* Dstar;
+    uint32_t* row_bad; uint32_t* irr; uint32_t* nirr; uint32_t* col_res; uint32_t* irr_res; uint8_t* ok;
+    unsigned long long* n_ok;
+    AllBufs(A& ar, const ProofLayout& L) {
+        const uint64_t N = (uint64_t)L.R * L.M;
+        Cd = (fq12*)ar.take(FQ12_BYTES);
+        cbad = (uint32_t*)ar.take(4);
+        roots = (uint8_t*)ar.take(32 * N);
+        mbad = (uint8_t*)ar.take(N);
+        ys = (fr*)ar.take(N * FR_BYTES);
+        shared = (uint8_t*)ar.take(N);
+        rj = (fr*)ar.take((size_t)L.R * FR_BYTES);
+        Dstar = (g1a*)ar.take((size_t)L.R * G1A_BYTES);
+        row_bad = (uint32_t*)ar.take((size_t)L.R * 4);
+        irr = (uint32_t*)ar.take(N * 4);
+        nirr = (uint32_t*)ar.take(8);
+        col_res = (uint32_t*)ar.take((size_t)L.M * 4);
+        irr_res = (uint32_t*)ar.take(N * 4);
+        ok = (uint8_t*)ar.take(N);
+        n_ok = (unsigned long long*)ar.take(8);
+    }
+};
+
+// PST jobs per launch chain: all M columns at once, and the other proofs in chunks of this size
+uint32_t verify_all_chunk(const ProofLayout& L) { return L.M > 8192 ? L.M : 8192; }
+
+// the PST checks of nj jobs whose E (and column, if job_a) are in J; results at
+// res[idx ? idx[q0 + q] : q]
+template <class A>
+void pst_jobs(const ProofLayout& L, JobBufs<A>& J, uint32_t nj, const uint32_t* job_a, const uint8_t* pst_ser,
+              const g2a* g2tau, const uint32_t* idx, uint32_t q0, uint32_t* res, cudaStream_t s) {
+    const int lc = L.log_c;
+    const uint64_t np = (uint64_t)nj * (lc + 1);
+    const PiSrc pi{pst_ser, 1, L.M, lc};
+    cudaMemsetAsync(J.bad, 0, (size_t)nj * 4, s);
+    FP_KERNEL("k_vp_pairs", s, k_vp_pairs<<<grid_for(np, 64), 64, 0, s>>>(pi, job_a, 0, J.E, nj, g2tau, J.bad, J.P,
+                                                                        J.Q));
+    FP_KERNEL("k_v_miller", s, k_v_miller<<<(unsigned)np, 128, 0, s>>>(J.P, J.Q, J.ml));
+    FP_KERNEL("k_vp_prod", s, k_vp_prod<<<grid_for(nj, 64), 64, 0, s>>>(J.ml, lc + 1, nj, J.fe_in));
+    final_exp_group(J.fe_in, nj, J.fe_out, nullptr, 1, 0, 0, s);
+    FP_KERNEL("k_vp_check", s, k_vp_check<<<grid_for(nj, 64), 64, 0, s>>>(J.fe_out, J.bad, nj, idx, q0, res));
+}
+
+}  // namespace
+
+size_t verify_all_scratch_bytes(const ProofLayout& L) {
+    SizeArena ar;
+    AllBufs<SizeArena> Ab(ar, L);
+    BlockBufs<SizeArena> Bb(ar, L.K, L.b, L.log_r);
+    JobBufs<SizeArena> J(ar, verify_all_chunk(L), L.log_c);
+    (void)Ab; (void)Bb; (void)J;
+    return ar.n + 256;
+}
+
+uint64_t verify_all(const ProofLayout& L, const void* C_be, const void* m, const void* rows_ser, const void* blocks,
+                    const void* row_tree, const void* top_tree, const void* D_ser, const void* g, const void* pst_ser,
+                    const void* g1beta, const void* g2tau, int each, void* scratch, void* ok_out, cudaStream_t s) {
+    const uint64_t N = (uint64_t)L.R * L.M;
+    Arena ar{(uint8_t*)scratch};
+    AllBufs<Arena> Ab(ar, L);
+    BlockBufs<Arena> Bb(ar, L.K, L.b, L.log_r);
+    const uint32_t chunk = verify_all_chunk(L);
+    JobBufs<Arena> J(ar, chunk, L.log_c);
+    const uint8_t* Cb = (const uint8_t*)C_be;
+    const uint8_t* rs = (const uint8_t*)rows_ser;
+    const uint8_t* Ds = (const uint8_t*)D_ser;
+    const uint8_t* ps = (const uint8_t*)pst_ser;
+    cudaMemsetAsync(Ab.nirr, 0, 8, s);
+    cudaMemsetAsync(Ab.n_ok, 0, 8, s);
+    // the checks of all K blocks
+    const VSrc S{rs, (size_t)L.b * G1_SER, (const uint8_t*)blocks, L.bopen_len, 0, L.K, L.b, L.R, L.log_r};
+    FP_KERNEL("k_v_cdec", s, k_v_cdec<<<1, 32, 0, s>>>(Cb, Ab.Cd, Ab.cbad));
+    block_checks_front(S, Cb, (const g1a*)g1beta, Bb, s);
+    FP_KERNEL("k_v_miller", s, k_v_miller<<<3 * L.K, 128, 0, s>>>(Bb.P, Bb.Q, Bb.ml));
+    FP_KERNEL("k_vb_gt", s, k_vb_gt<<<2 * L.log_r * L.K, 128, 0, s>>>(S, Bb.st, Bb.ge));
+    FP_KERNEL("k_vb_prod", s, k_vb_prod<<<grid_for(L.K, 64), 64, 0, s>>>(Bb.ml, Bb.ge, Ab.Cd, L.K, L.log_r, Bb.fe_in,
+                                                                       Bb.cT));
+    final_exp_group(Bb.fe_in, 2 * L.K, Bb.fe_out, nullptr, 1, 0, 0, s);
+    FP_KERNEL("k_vb_check", s, k_vb_check<<<grid_for(L.K, 64), 64, 0, s>>>(Bb.fe_out, Bb.cT, Ab.cbad, Bb.st, L.K,
+                                                                         Bb.res));
+    // element checks and the sharing classes
+    const uint64_t* md = (const uint64_t*)m;
+    FP_KERNEL("k_va_paths", s, k_va_paths<<<grid_for(N, 64), 64, 0, s>>>(L, md, (const uint8_t*)row_tree,
+                                                                       (const uint8_t*)top_tree, rs, Ab.roots,
+                                                                       Ab.mbad));
+    FP_KERNEL("k_va_rows", s, k_va_rows<<<grid_for(L.R, 64), 64, 0, s>>>(L, Ab.roots, rs, Ds, Ab.rj, Ab.Dstar,
+                                                                       Ab.row_bad));
+    FP_KERNEL("k_va_y", s, k_va_y<<<grid_for(N), TPB, 0, s>>>(L, md, Ab.roots, Ab.rj, (const fr*)g, Ab.mbad, Ab.ys));
+    FP_KERNEL("k_va_class", s, k_va_class<<<grid_for(N), TPB, 0, s>>>(L, Ab.roots, Ab.Dstar, Ab.ys, each, Ab.shared,
+                                                                      Ab.irr, Ab.nirr));
+    // one PST check per column
+    FP_KERNEL("k_va_colE", s, k_va_colE<<<grid_for(L.M, 64), 64, 0, s>>>(Ab.Dstar, Ab.ys, L.M, J.E));
+    pst_jobs(L, J, L.M, nullptr, ps, (const g2a*)g2tau, nullptr, 0, Ab.col_res, s);
+    // and one for each proof outside the shared classes
+    uint32_t nirr = 0;
+    cudaMemcpyAsync(&nirr, Ab.nirr, 4, cudaMemcpyDeviceToHost, s);
+    cudaStreamSynchronize(s);
+    for (uint32_t q0 = 0; q0 < nirr; q0 += chunk) {
+        const uint32_t nj = std::min(chunk, nirr - q0);
+        FP_KERNEL("k_va_irrE", s, k_va_irrE<<<grid_for(nj, 64), 64, 0, s>>>(L, Ab.irr, q0, nj, Ab.roots, Ab.ys, rs,
+                                                                          Ds, J.E, J.a));
+        pst_jobs(L, J, nj, J.a, ps, (const g2a*)g2tau, Ab.irr, q0, Ab.irr_res, s);
+    }
+    FP_KERNEL("k_va_result", s, k_va_result<<<grid_for(N), TPB, 0, s>>>(L, Bb.res, Ab.row_bad, Ab.mbad, Ab.shared,
+                                                                        Ab.col_res, Ab.irr_res, Ab.ok, Ab.n_ok));
+    unsigned long long n_ok = 0;
+    if (ok_out) cudaMemcpyAsync(ok_out, Ab.ok, N, cudaMemcpyDeviceToHost, s);
+    cudaMemcpyAsync(&n_ok, Ab.n_ok, 8, cudaMemcpyDeviceToHost, s);
+    cudaStreamSynchronize(s);
+    return n_ok;
 }
 
 }  // namespace fpk

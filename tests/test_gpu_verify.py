@@ -81,3 +81,71 @@ def test_verify_n16_sampled():
         p = pf.proof(i)
         assert F.vc_verify(pp, C, b, i, vals[i], p)
         assert not F.vc_verify(pp, C, b, i, vals[i] ^ 1, p)
+
+
+def limbs_of(v: int):
+    return [(v >> (64 * w)) & 0xFFFFFFFFFFFFFFFF for w in range(4)]
+
+
+@pytest.mark.parametrize("log_n,b", [(4, 1), (5, 3), (7, 4), (10, 1)])
+def test_verify_all_matches_single_and_oracle(log_n, b):
+    """vc_verify_all over all N proofs: honest values all verify; wrong claimed values (proof 0,
+    whose root is the sharing reference, a row-0 proof that is a column's reference, others, and
+    a value >= r) fail exactly where vc_verify and the oracle's verifier fail, with and without
+    column sharing."""
+    import numpy as np
+    pp, opp, vals, C, pf = setup(log_n, 41, b)
+    N, M = pp.N, pp.M
+    m = np.array([limbs_of(v) for v in vals], np.uint64)
+    ok, n = F.vc_verify_all(pf, C, m)
+    assert n == N and ok.all()
+    bad = {0, 1, M + 2, N - 1, N // 2 + 3}
+    claimed = list(vals)
+    for i in bad:
+        claimed[i] = (vals[i] + 1) % I.R_INT
+    claimed[N // 2 + 3] = vals[N // 2 + 3] + I.R_INT          # not canonical
+    m2 = np.array([limbs_of(v) for v in claimed], np.uint64)
+    ok2, n2 = F.vc_verify_all(pf, C, m2)
+    assert set(np.nonzero(~ok2)[0].tolist()) == bad and n2 == N - len(bad)
+    ok3, n3 = F.vc_verify_all(pf, C, m2, each=True)
+    assert (ok3 == ok2).all() and n3 == n2
+    for i in sorted(bad | {2, M, N - 2}):
+        p = pf.proof(i)
+        assert F.vc_verify(pp, C, b, i, claimed[i], p) == ok2[i], i
+    for i in (0, 2, N - 1):
+        assert O.verify(opp, C, b, i, claimed[i], pf.proof(i), memo=False) == ok2[i], i
+
+
+def test_verify_all_wrong_commitment_and_device_values():
+    import numpy as np
+    log_n, b = 6, 2
+    pp, opp, vals, C, pf = setup(log_n, 42, b)
+    m = np.array([limbs_of(v) for v in vals], np.uint64)
+    other = F.Commitment(pp, I.vector(99, log_n))
+    C2, _ = other.get()
+    ok, n = F.vc_verify_all(pf, C2, m)
+    assert n == 0 and not ok.any()
+    md = torch.from_numpy(m.view(np.int64)).cuda()
+    ok, n = F.vc_verify_all(pf, C, md)
+    assert n == pp.N and ok.all()
+
+
+@pytest.mark.parametrize("b", [256, 1])
+def test_verify_all_n16(b):
+    """N = 2^16: every proof verifies; two wrong values fail, and only those."""
+    import numpy as np
+    log_n, seed = 16, 0
+    pp = F.PP(log_n, 1, seed)
+    m = I.vector(seed + 1, log_n)
+    cm = F.Commitment(pp, m)
+    C, _ = cm.get()
+    pf = F.Proofs(pp, cm, b)
+    ok, n = F.vc_verify_all(pf, C, m)
+    assert n == pp.N and ok.all()
+    m2 = m.copy()
+    m2[777, 0] ^= 1
+    m2[65535, 1] ^= 4
+    ok2, n2 = F.vc_verify_all(pf, C, m2)
+    assert n2 == pp.N - 2 and not ok2[777] and not ok2[65535]
+    vals = I.to_ints(m2)
+    assert not F.vc_verify(pp, C, b, 777, vals[777], pf.proof(777))
