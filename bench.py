@@ -178,6 +178,30 @@ def proveall_sweep(F, I, torch, np, stream, flush, b_values, seed: int) -> dict:
     return out
 
 
+def verify_sweep(F, I, torch, np, cases, seed: int) -> dict:
+    """vc_verify_all: every proof of one ProveAll output verified against the claimed values
+    (device-resident), host wall time of the synchronous call, median of 3 after one warm-up."""
+    out = {}
+    for log_n, b in cases:
+        pp = F.PP(log_n, 1, seed)
+        m = I.vector(seed + 1, log_n)
+        cm = F.Commitment(pp, m)
+        C, _ = cm.get()
+        pf = F.Proofs(pp, cm, b)
+        md = torch.from_numpy(m.view(np.int64).copy()).cuda()
+        torch.cuda.synchronize()
+        F.vc_verify_all(pf, C, md)
+        ts, n = [], 0
+        for _ in range(3):
+            t0 = time.perf_counter()
+            _, n = F.vc_verify_all(pf, C, md)
+            ts.append(time.perf_counter() - t0)
+        s = sorted(ts)[1]
+        out[f"n2^{log_n}_b={b}"] = {"proofs_per_s": pp.N / s, "ms": s * 1e3, "accepted": n, "N": pp.N}
+        del pf, cm, pp
+    return out
+
+
 def batched_workload(F, I, torch, np) -> dict:
     """64 jobs, log N uniform in 8..18 by seed, b = min(R, nearestpow2(log^2 N)), one SRS for 2^18
     resident: one vc_prove_all_batch captured as a CUDA graph vs the same jobs as concurrent job
@@ -513,6 +537,7 @@ def main():
                                              [int(x) for x in args.b_sweep.split(",") if x], args.seed),
             "msm_g1": msm_sweep(F, I, torch, np, stream, flush,
                                 [int(x) for x in args.msm_sweep.split(",") if x], args.seed),
+            "verify_all": verify_sweep(F, I, torch, np, [(16, 256), (20, 1), (20, 1024)], args.seed),
             "batched_64_jobs": batched_workload(F, I, torch, np),
             "served": served_workload(F, I, torch, np, args.served_requests),
         }

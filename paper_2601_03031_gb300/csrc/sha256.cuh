@@ -15,9 +15,16 @@ FPG_DEV uint32_t sha_rotr(uint32_t x, int n) { return (x >> n) | (x << (32 - n))
 
 FPG_NOINL void sha256_compress(uint32_t* h, const uint8_t* blk) {
     uint32_t w[16];
+    if (((uintptr_t)blk & 3) == 0) {                  // word loads, byte-swapped to big-endian
+        const uint32_t* b4 = reinterpret_cast<const uint32_t*>(blk);
 #pragma unroll
-    for (int t = 0; t < 16; t++)
-        w[t] = ((uint32_t)blk[4 * t] << 24) | ((uint32_t)blk[4 * t + 1] << 16) | ((uint32_t)blk[4 * t + 2] << 8) | blk[4 * t + 3];
+        for (int t = 0; t < 16; t++) w[t] = __byte_perm(b4[t], 0, 0x0123);
+    } else {
+#pragma unroll
+        for (int t = 0; t < 16; t++)
+            w[t] = ((uint32_t)blk[4 * t] << 24) | ((uint32_t)blk[4 * t + 1] << 16) | ((uint32_t)blk[4 * t + 2] << 8) |
+                   blk[4 * t + 3];
+    }
     uint32_t a = h[0], b = h[1], c = h[2], d = h[3], e = h[4], f = h[5], g = h[6], hh = h[7];
 #pragma unroll
     for (int t = 0; t < 64; t++) {
@@ -47,11 +54,25 @@ FPG_DEV void sha256_init(sha256_ctx& c) {
     c.nbuf = 0;
     c.total = 0;
 }
+// whole 64-byte blocks of the input are compressed in place; only partial blocks are buffered
 FPG_DEV void sha256_update(sha256_ctx& c, const uint8_t* data, uint32_t n) {
     c.total += n;
-    for (uint32_t i = 0; i < n; i++) {
-        c.buf[c.nbuf++] = data[i];
-        if (c.nbuf == 64) { sha256_compress(c.h, c.buf); c.nbuf = 0; }
+    while (n) {
+        if (c.nbuf == 0 && n >= 64) {
+            sha256_compress(c.h, data);
+            data += 64;
+            n -= 64;
+            continue;
+        }
+        const uint32_t take = min(64u - c.nbuf, n);
+        for (uint32_t i = 0; i < take; i++) c.buf[c.nbuf + i] = data[i];
+        c.nbuf += take;
+        data += take;
+        n -= take;
+        if (c.nbuf == 64) {
+            sha256_compress(c.h, c.buf);
+            c.nbuf = 0;
+        }
     }
 }
 FPG_DEV void sha256_byte(sha256_ctx& c, uint8_t b) { sha256_update(c, &b, 1); }

@@ -8,7 +8,7 @@
 //   the column part:  the PST proof of g* at a (the same for all of column a).
 // Checks, in three groups:
 //   block:   statement hash, x_j, z, P(z); C_0's G1 part sum_a r_a C_a and the rounds'
-//            x_j L_j.1 + x_j^-1 R_j.1 (one thread per term, pairwise sums);
+//            x_j L_j.1 + x_j^-1 R_j.1 (one 8-lane group per term, pairwise sums);
 //            b_l = sum_a r_a prod_k x_k^-(bit l - k of a); the GT fold C L_1^x1 R_1^(1/x1) ...
 //            (one 128-thread block per exponentiation); e(A_l, v_l) against the folded C,
 //            e(g1^beta - z g1, W) e(-g1, v_l - P(z) g2) = 1, and b_l A_l against the folded G1 part;
@@ -25,6 +25,7 @@
 // that proof's bytes.
 #include <algorithm>
 
+#include "group_ec.cuh"
 #include "k_common.cuh"
 #include "warp12.cuh"
 
@@ -101,6 +102,27 @@ FPG_DEV bool digest_same(const uint8_t* a, const uint8_t* b) {
     return true;
 }
 FPG_DEV g2a g2a_negate(const g2a& p) { return g2a_is_inf(p) ? p : g2a{p.x, fq2_neg(p.y)}; }
+// homogeneous projective (X : Y : Z) -> Jacobian (X Z, Y Z^2, Z)
+FPG_DEV g1j proj_to_jac(const GPt<fq>& r) {
+    g1j o;
+    o.X = fq_mul(r.X, r.Z);
+    o.Y = fq_mul(r.Y, fq_sqr(r.Z));
+    o.Z = r.Z;
+    return o;
+}
+FPG_DEV g2j proj_to_jac(const GPt<fq2>& r) {
+    g2j o;
+    o.X = fq2_mul(r.X, r.Z);
+    o.Y = fq2_mul(r.Y, fq2_sqr(r.Z));
+    o.Z = r.Z;
+    return o;
+}
+// k P on one 8-lane group (GLV, 2-bit joint windows); every lane of the group must call it
+FPG_DEV g1j g1_mul8(GEc<fq>& sm, int lane, const g1a& P, const fr& k_mont) {
+    uint32_t kw[8];
+    fr_canon_words(kw, k_mont);
+    return proj_to_jac(gec_g1_mul_proj_w2(sm, lane, P, kw));
+}
 // r_j = HFr("FP-rho", root || u32be(j))
 FPG_DEV fr row_rho(const uint8_t* root, uint32_t j) {
     uint8_t rb[36];
@@ -211,36 +233,50 @@ __global__ void k_vb_transcript(VSrc S, const uint8_t* C_be, VBlk* st) {
 }
 
 // per block tpb term slots (a power of two): r_a C_a for its nk rows, then x_j L_j.1 and
-// x_j^-1 R_j.1; the b_l summands r_a prod_k x_k^-(bit l - k of a) at wt[q b + t].  Unused slots
-// keep the identity the caller cleared them to.
-__global__ void k_vb_terms(VSrc S, VBlk* st, uint32_t tpb, g1j* T, fr* wt) {
-    const uint64_t t = gtid();
-    if (t >= (uint64_t)S.nb * tpb) return;
-    const uint32_t q = (uint32_t)(t / tpb), u = (uint32_t)(t % tpb), nk = S.nk(q);
+// x_j^-1 R_j.1; the b_l summands r_a prod_k x_k^-(bit l - k of a) at wt[q b + t].  One 8-lane
+// group per slot (16 per block); unused slots keep the identity the caller cleared them to.
+__global__ void __launch_bounds__(128) k_vb_terms(VSrc S, VBlk* st, uint32_t tpb, g1j* T, fr* wt) {
+    __shared__ GEc<fq> sm[16];
+    const int grp = threadIdx.x >> 3, lane = threadIdx.x & 7;
+    const uint64_t t = (uint64_t)blockIdx.x * 16 + grp;
     const int lr = S.lr;
-    if (u >= nk + 2 * (uint32_t)lr) return;
-    VBlk& B = st[q];
-    g1a P;
-    uint32_t kw[8];
-    if (u < nk) {
-        const uint32_t a = S.lo(q) + u;
-        if (!g1_decode(S.blk + q * S.blk_stride + 96 * (size_t)u, P)) atomicOr(&B.bad, 32u);
-        uint8_t buf[36];
-        for (int c = 0; c < 32; c++) buf[c] = B.hstmt[c];
-        put_be32(buf + 32, a);
-        const fr r = hash_to_fr("FP-r", 4, buf, 36, nullptr, 0, nullptr, 0);
-        fr w = r;
-        for (int kk = 1; kk <= lr; kk++)
-            if ((a >> (lr - kk)) & 1) w = fr_mul(w, B.xinv[kk - 1]);
-        wt[(size_t)q * S.b + u] = w;
-        fr_canon_words(kw, r);
-    } else {
-        const int v = (int)(u - nk), jj = v >> 1, side = v & 1;
-        const uint8_t* rd = S.fc + q * S.fc_stride + (size_t)jj * ROUND_BYTES;
-        if (!g1_decode(rd + (side ? GT_SER + G1_SER + GT_SER : GT_SER), P)) atomicOr(&B.bad, 64u);
-        fr_canon_words(kw, side ? B.xinv[jj] : B.x[jj]);
+    uint32_t q = 0, u = 0, nk = 0;
+    bool valid = t < (uint64_t)S.nb * tpb;
+    if (valid) {
+        q = (uint32_t)(t / tpb);
+        u = (uint32_t)(t % tpb);
+        nk = S.nk(q);
+        valid = u < nk + 2 * (uint32_t)lr;
     }
-    T[t] = g1_mul(P, kw);
+    g1a P;                                             // identity and k = 0 for the idle groups
+    fq_zero(P.x);
+    fq_zero(P.y);
+    fr k;
+    fr_zero(k);
+    if (valid) {
+        VBlk& B = st[q];
+        if (u < nk) {
+            const uint32_t a = S.lo(q) + u;
+            if (!g1_decode(S.blk + q * S.blk_stride + 96 * (size_t)u, P) && lane == 0) atomicOr(&B.bad, 32u);
+            uint8_t buf[36];
+            for (int c = 0; c < 32; c++) buf[c] = B.hstmt[c];
+            put_be32(buf + 32, a);
+            k = hash_to_fr("FP-r", 4, buf, 36, nullptr, 0, nullptr, 0);
+            if (lane == 0) {
+                fr w = k;
+                for (int kk = 1; kk <= lr; kk++)
+                    if ((a >> (lr - kk)) & 1) w = fr_mul(w, B.xinv[kk - 1]);
+                wt[(size_t)q * S.b + u] = w;
+            }
+        } else {
+            const int v = (int)(u - nk), jj = v >> 1, side = v & 1;
+            const uint8_t* rd = S.fc + q * S.fc_stride + (size_t)jj * ROUND_BYTES;
+            if (!g1_decode(rd + (side ? GT_SER + G1_SER + GT_SER : GT_SER), P) && lane == 0) atomicOr(&B.bad, 64u);
+            k = side ? B.xinv[jj] : B.x[jj];
+        }
+    }
+    const g1j r = g1_mul8(sm[grp], lane, P, k);
+    if (valid && lane == 0) T[t] = r;
 }
 
 __global__ void k_vb_scalars(VSrc S, const fr* wt, VBlk* st) {
@@ -253,16 +289,35 @@ __global__ void k_vb_scalars(VSrc S, const fr* wt, VBlk* st) {
     st[q].bl = s;
 }
 
-// per block: 0: b_l A_l, 1: z g1, 2: P(z) g2
-__global__ void k_vb_muls(VBlk* st, uint32_t nb) {
-    const uint64_t t = gtid();
-    if (t >= 3 * (uint64_t)nb) return;
-    VBlk& B = st[t / 3];
-    uint32_t kw[8];
-    switch (t % 3) {
-        case 0: fr_canon_words(kw, B.bl); B.blA = g1_mul(B.Al, kw); break;
-        case 1: fr_canon_words(kw, B.z); B.zg = g1_mul(g1_generator(), kw); break;
-        default: fr_canon_words(kw, B.Pz); B.Pzg = g2_mul(g2_generator(), kw); break;
+// per block: P(z) g2 on one warp (the first nb2 CTAs, four blocks each), b_l A_l and z g1 on
+// 8-lane groups (16 per CTA)
+union VMulSmem {
+    GEcW g2[4];
+    GEc<fq> g1[16];
+};
+__global__ void __launch_bounds__(128) k_vb_muls(VBlk* st, uint32_t nb, uint32_t nb2) {
+    __shared__ VMulSmem sm;
+    if (blockIdx.x < nb2) {
+        const int w = threadIdx.x >> 5, L = threadIdx.x & 31;
+        const uint64_t q = (uint64_t)blockIdx.x * 4 + w;
+        if (q >= nb) return;                                  // warp-uniform
+        VBlk& B = st[q];
+        uint32_t kw[8];
+        fr_canon_words(kw, B.Pz);
+        const GPt<fq2> r = gecw_g2_mul_proj(sm.g2[w], L, g2_generator(), kw);
+        if (L == 0) B.Pzg = proj_to_jac(r);
+        return;
+    }
+    const int grp = threadIdx.x >> 3, lane = threadIdx.x & 7;
+    const uint64_t t0 = (uint64_t)(blockIdx.x - nb2) * 16 + grp;
+    const bool valid = t0 < 2 * (uint64_t)nb;
+    const uint64_t t = valid ? t0 : 0;
+    VBlk& B = st[t >> 1];
+    const bool zg = t & 1;
+    const g1j r = g1_mul8(sm.g1[grp], lane, zg ? g1_generator() : B.Al, zg ? B.z : B.bl);
+    if (valid && lane == 0) {
+        if (zg) B.zg = r;
+        else B.blA = r;
     }
 }
 
@@ -449,17 +504,15 @@ __global__ void k_v_elem(const uint8_t* proof, const uint8_t* mi_be, VLayout Ly,
     e->bad = bad;
 }
 
-// 0: y* g1, 1: r_j C_j
-__global__ void k_v_elem_muls(VElem* e) {
-    const uint64_t t = gtid();
-    if (t >= 2) return;
-    uint32_t kw[8];
-    if (t == 0) {
-        fr_canon_words(kw, e->ys);
-        e->ysg = g1_mul(g1_generator(), kw);
-    } else {
-        fr_canon_words(kw, e->rj);
-        e->rjCj = g1_mul(e->Cj, kw);
+// group 0: y* g1, group 1: r_j C_j (groups 2 and 3 idle)
+__global__ void __launch_bounds__(32) k_v_elem_muls(VElem* e) {
+    __shared__ GEc<fq> sm[4];
+    const int grp = threadIdx.x >> 3, lane = threadIdx.x & 7;
+    const bool yg = grp == 0;
+    const g1j r = g1_mul8(sm[grp], lane, yg ? g1_generator() : e->Cj, yg ? e->ys : e->rj);
+    if (lane == 0 && grp < 2) {
+        if (yg) e->ysg = r;
+        else e->rjCj = r;
     }
 }
 
@@ -552,7 +605,7 @@ void block_checks_front(const VSrc& S, const uint8_t* C_be, const g1a* g1beta, B
     const uint64_t nt = (uint64_t)S.nb * tpb;
     cudaMemsetAsync(Bb.T, 0, nt * G1J_BYTES, s);
     FP_KERNEL("k_vb_transcript", s, k_vb_transcript<<<grid_for(S.nb, 32), 32, 0, s>>>(S, C_be, Bb.st));
-    FP_KERNEL("k_vb_terms", s, k_vb_terms<<<grid_for(nt, 64), 64, 0, s>>>(S, Bb.st, tpb, Bb.T, Bb.wt));
+    FP_KERNEL("k_vb_terms", s, k_vb_terms<<<grid_for(nt, 16), 128, 0, s>>>(S, Bb.st, tpb, Bb.T, Bb.wt));
     g1j* x = Bb.T;
     g1j* y = Bb.T2;
     for (uint64_t n = nt; n > S.nb; n /= 2) {            // per-block sums: tpb is a power of two
@@ -560,7 +613,8 @@ void block_checks_front(const VSrc& S, const uint8_t* C_be, const g1a* g1beta, B
         std::swap(x, y);
     }
     FP_KERNEL("k_vb_scalars", s, k_vb_scalars<<<grid_for(S.nb, 64), 64, 0, s>>>(S, Bb.wt, Bb.st));
-    FP_KERNEL("k_vb_muls", s, k_vb_muls<<<grid_for(3 * (uint64_t)S.nb, 64), 64, 0, s>>>(Bb.st, S.nb));
+    const uint32_t nb2 = (S.nb + 3) / 4;
+    FP_KERNEL("k_vb_muls", s, k_vb_muls<<<nb2 + grid_for(2 * (uint64_t)S.nb, 16), 128, 0, s>>>(Bb.st, S.nb, nb2));
     FP_KERNEL("k_vb_pairs", s, k_vb_pairs<<<grid_for(S.nb, 64), 64, 0, s>>>(S.nb, g1beta, x, Bb.st, Bb.P, Bb.Q));
 }
 
@@ -653,24 +707,27 @@ __global__ void k_va_paths(ProofLayout L, const uint64_t* m, const uint8_t* row_
     for (int q = 0; q < 32; q++) roots[32 * i + q] = cur[q];
 }
 
-// per row, with the root of proof 0: r_j and D*_j = r_j C_j + sum_w D_w (affine)
-__global__ void k_va_rows(ProofLayout L, const uint8_t* roots, const uint8_t* rows_ser, const uint8_t* D_ser, fr* rj,
-                          g1a* Dstar, uint32_t* row_bad) {
-    const uint64_t j = gtid();
-    if (j >= L.R) return;
-    uint32_t bad = 0;
-    const fr r = row_rho(roots, (uint32_t)j);
-    rj[j] = r;
+// per row, with the root of proof 0: r_j and D*_j = r_j C_j + sum_w D_w (affine); one 8-lane
+// group per row
+__global__ void __launch_bounds__(128) k_va_rows(ProofLayout L, const uint8_t* roots, const uint8_t* rows_ser,
+                                                 const uint8_t* D_ser, fr* rj, g1a* Dstar, uint32_t* row_bad) {
+    __shared__ GEc<fq> sm[16];
+    const int grp = threadIdx.x >> 3, lane = threadIdx.x & 7;
+    const uint64_t j0 = (uint64_t)blockIdx.x * 16 + grp;
+    const bool valid = j0 < L.R;
+    const uint32_t j = valid ? (uint32_t)j0 : 0;
+    const fr r = row_rho(roots, j);
     g1a Cj;
-    if (!g1_decode(rows_ser + 96 * j, Cj)) bad |= 16;
-    uint32_t kw[8];
-    fr_canon_words(kw, r);
-    g1j Ds = g1_mul(Cj, kw);
+    const bool cok = g1_decode(rows_ser + 96 * (size_t)j, Cj);
+    g1j Ds = g1_mul8(sm[grp], lane, Cj, r);
+    if (!valid || lane != 0) return;
+    uint32_t bad = cok ? 0u : 16u;
     for (int h = 0; h < L.log_r; h++) {
         g1a D;
         if (!g1_decode(D_ser + G1_SER * (tree_off(L.R, h) + ((j >> h) ^ 1)), D)) bad |= 256;
         Ds = g1_madd(Ds, D);
     }
+    rj[j] = r;
     Dstar[j] = g1_affine(Ds);
     row_bad[j] = bad;
 }
@@ -710,36 +767,41 @@ __global__ void k_va_class(ProofLayout L, const uint8_t* roots, const g1a* Dstar
     if (!sh) irr[atomicAdd(nirr, 1u)] = (uint32_t)i;
 }
 
-// column jobs: E_a = D*_0 - y*_a g1
-__global__ void k_va_colE(const g1a* Dstar, const fr* ys, uint32_t M, g1a* E) {
-    const uint64_t a = gtid();
-    if (a >= M) return;
-    uint32_t kw[8];
-    fr_canon_words(kw, ys[a]);
-    E[a] = g1_affine(g1_madd(g1j_neg(g1_mul(g1_generator(), kw)), Dstar[0]));
+// column jobs: E_a = D*_0 - y*_a g1, one 8-lane group each
+__global__ void __launch_bounds__(128) k_va_colE(const g1a* Dstar, const fr* ys, uint32_t M, g1a* E) {
+    __shared__ GEc<fq> sm[16];
+    const int grp = threadIdx.x >> 3, lane = threadIdx.x & 7;
+    const uint64_t a0 = (uint64_t)blockIdx.x * 16 + grp;
+    const bool valid = a0 < M;
+    const uint64_t a = valid ? a0 : 0;
+    const g1j yg = g1_mul8(sm[grp], lane, g1_generator(), ys[a]);
+    if (valid && lane == 0) E[a] = g1_affine(g1_madd(g1j_neg(yg), Dstar[0]));
 }
 
 // jobs of the listed proofs irr[q0 .. q0 + nj): E = r_j C_j + sum_w D_w - y* g1, r_j from the
-// proof's own root
-__global__ void k_va_irrE(ProofLayout L, const uint32_t* irr, uint32_t q0, uint32_t nj, const uint8_t* roots,
-                          const fr* ys, const uint8_t* rows_ser, const uint8_t* D_ser, g1a* E, uint32_t* job_a) {
-    const uint64_t q = gtid();
-    if (q >= nj) return;
+// proof's own root; one 8-lane group each
+__global__ void __launch_bounds__(128) k_va_irrE(ProofLayout L, const uint32_t* irr, uint32_t q0, uint32_t nj,
+                                                 const uint8_t* roots, const fr* ys, const uint8_t* rows_ser,
+                                                 const uint8_t* D_ser, g1a* E, uint32_t* job_a) {
+    __shared__ GEc<fq> sm[16];
+    const int grp = threadIdx.x >> 3, lane = threadIdx.x & 7;
+    const uint64_t q0g = (uint64_t)blockIdx.x * 16 + grp;
+    const bool valid = q0g < nj;
+    const uint64_t q = valid ? q0g : 0;
     const uint64_t i = irr[q0 + q];
     const uint32_t j = (uint32_t)(i / L.M);
-    job_a[q] = (uint32_t)(i % L.M);
     g1a Cj;
     g1_decode(rows_ser + 96 * (size_t)j, Cj);         // a bad C_j or D_w fails the row's check
-    uint32_t kw[8];
-    fr_canon_words(kw, row_rho(roots + 32 * i, j));
-    g1j Ds = g1_mul(Cj, kw);
+    g1j Ds = g1_mul8(sm[grp], lane, Cj, row_rho(roots + 32 * i, j));
+    const g1j yg = g1_mul8(sm[grp], lane, g1_generator(), ys[i]);
+    if (!valid || lane != 0) return;
     for (int h = 0; h < L.log_r; h++) {
         g1a D;
         g1_decode(D_ser + G1_SER * (tree_off(L.R, h) + ((j >> h) ^ 1)), D);
         Ds = g1_madd(Ds, D);
     }
-    fr_canon_words(kw, ys[i]);
-    E[q] = g1_affine(jac_add(Ds, g1j_neg(g1_mul(g1_generator(), kw))));
+    job_a[q] = (uint32_t)(i % L.M);
+    E[q] = g1_affine(jac_add(Ds, g1j_neg(yg)));
 }
 
 __global__ void k_va_result(ProofLayout L, const uint32_t* blk_res, const uint32_t* row_bad, const uint8_t* mbad,
@@ -846,13 +908,13 @@ uint64_t verify_all(const ProofLayout& L, const void* C_be, const void* m, const
     FP_KERNEL("k_va_paths", s, k_va_paths<<<grid_for(N, 64), 64, 0, s>>>(L, md, (const uint8_t*)row_tree,
                                                                        (const uint8_t*)top_tree, rs, Ab.roots,
                                                                        Ab.mbad));
-    FP_KERNEL("k_va_rows", s, k_va_rows<<<grid_for(L.R, 64), 64, 0, s>>>(L, Ab.roots, rs, Ds, Ab.rj, Ab.Dstar,
+    FP_KERNEL("k_va_rows", s, k_va_rows<<<grid_for(L.R, 16), 128, 0, s>>>(L, Ab.roots, rs, Ds, Ab.rj, Ab.Dstar,
                                                                        Ab.row_bad));
     FP_KERNEL("k_va_y", s, k_va_y<<<grid_for(N), TPB, 0, s>>>(L, md, Ab.roots, Ab.rj, (const fr*)g, Ab.mbad, Ab.ys));
     FP_KERNEL("k_va_class", s, k_va_class<<<grid_for(N), TPB, 0, s>>>(L, Ab.roots, Ab.Dstar, Ab.ys, each, Ab.shared,
                                                                       Ab.irr, Ab.nirr));
     // one PST check per column
-    FP_KERNEL("k_va_colE", s, k_va_colE<<<grid_for(L.M, 64), 64, 0, s>>>(Ab.Dstar, Ab.ys, L.M, J.E));
+    FP_KERNEL("k_va_colE", s, k_va_colE<<<grid_for(L.M, 16), 128, 0, s>>>(Ab.Dstar, Ab.ys, L.M, J.E));
     pst_jobs(L, J, L.M, nullptr, ps, (const g2a*)g2tau, nullptr, 0, Ab.col_res, s);
     // and one for each proof outside the shared classes
     uint32_t nirr = 0;
@@ -860,7 +922,7 @@ uint64_t verify_all(const ProofLayout& L, const void* C_be, const void* m, const
     cudaStreamSynchronize(s);
     for (uint32_t q0 = 0; q0 < nirr; q0 += chunk) {
         const uint32_t nj = std::min(chunk, nirr - q0);
-        FP_KERNEL("k_va_irrE", s, k_va_irrE<<<grid_for(nj, 64), 64, 0, s>>>(L, Ab.irr, q0, nj, Ab.roots, Ab.ys, rs,
+        FP_KERNEL("k_va_irrE", s, k_va_irrE<<<grid_for(nj, 16), 128, 0, s>>>(L, Ab.irr, q0, nj, Ab.roots, Ab.ys, rs,
                                                                           Ds, J.E, J.a));
         pst_jobs(L, J, nj, J.a, ps, (const g2a*)g2tau, Ab.irr, q0, Ab.irr_res, s);
     }
