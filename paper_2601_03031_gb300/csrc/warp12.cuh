@@ -121,29 +121,38 @@ FPG_NOINL void w_cyc_sqr(W12& W, fq* out, const fq* z) {
     }
     wsync<NW>();
     if (NW == 4) {
-        // A_p.re, A_p.im, B_p.re, B_p.im on warps 0, 1, 2, 3 (lane p of each), then the outputs
+        // each output from its pair's products in one step, one formula per warp (no divergence):
+        //   warp 0: c0, c2, c4 real parts  3 (s1 + t1 - 2 t2) - 2 z
+        //   warp 1: c0, c2, c4 imag parts  3 (t1 + 2 (s2 + t2)) - 2 z
+        //   warp 2: c3.re, c5.re  3 (2 (k0 - k1)) + 2 z;  c1.re = 3 (2 (2 k0 - k2)) + 2 z
+        //   warp 3: c3.im, c5.im  3 (2 (k2 - k0 - k1)) + 2 z;  c1.im = 3 (2 (k2 - 2 k1)) + 2 z
         const int w = L >> 5, pl = L & 31;
         if (pl < 3) {
             const fq* m = &W.p[7 * pl];
-            fq v;
-            if (w == 0) v = fq_sub(fq_add(m[0], m[2]), fq_dbl(m[3]));
-            else if (w == 1) v = fq_add(fq_add(fq_dbl(m[1]), m[2]), fq_dbl(m[3]));
-            else if (w == 2) v = fq_dbl(fq_sub(m[4], m[5]));
-            else v = fq_dbl(fq_sub(m[6], fq_add(m[4], m[5])));
-            W.h[12 + 3 * w + pl] = v;
+            int o;
+            fq V;
+            if (w == 0) {
+                o = 4 * pl;
+                V = fq_sub(fq_add(m[0], m[2]), fq_dbl(m[3]));
+            } else if (w == 1) {
+                o = 4 * pl + 1;
+                V = fq_add(m[2], fq_dbl(fq_add(m[1], m[3])));
+            } else if (w == 2) {
+                o = pl == 2 ? 2 : 6 + 4 * pl;
+                const fq k0 = m[4];
+                const fq u = pl == 2 ? fq_dbl(k0) : k0;
+                V = fq_dbl(fq_sub(u, pl == 2 ? m[6] : m[5]));
+            } else {
+                o = pl == 2 ? 3 : 7 + 4 * pl;
+                const fq y = pl == 2 ? fq_dbl(m[5]) : fq_add(m[4], m[5]);
+                V = fq_dbl(fq_sub(m[6], y));
+            }
+            const fq V3 = fq_add(fq_dbl(V), V);
+            const fq z2 = fq_dbl(z[o]);
+            out[o] = w < 2 ? fq_sub(V3, z2) : fq_add(V3, z2);
         }
         wsync<NW>();
-        if (L < 12) {
-            const int k = L >> 1, e = L & 1;
-            const int pair = (k == 0 || k == 3) ? 0 : (k == 2 || k == 5) ? 1 : 2;
-            const int kind = (k == 0 || k == 2 || k == 4) ? 0 : (k == 1 ? 2 : 1);
-            const fq* AB = &W.h[12];                  // [A.re | A.im | B.re | B.im] x 3 pairs
-            const fq bre = AB[6 + pair], bim = AB[9 + pair];
-            const fq V = kind == 0 ? AB[3 * e + pair] : (kind == 1 ? (e ? bim : bre) : (e ? fq_add(bre, bim) : fq_sub(bre, bim)));
-            const fq V3 = fq_add(fq_dbl(V), V);
-            const fq z2 = fq_dbl(z[L]);
-            W.h[L] = kind == 0 ? fq_sub(V3, z2) : fq_add(V3, z2);
-        }
+        return;
     } else if (L < 12) {
         const int k = L >> 1, e = L & 1;
         // coefficient k -> (pair, kind): kind 0: 3A - 2z, 1: 3B + 2z, 2: 3 xi B + 2z
@@ -224,18 +233,16 @@ FPG_NOINL void w_frob2(W12& W, fq* out, const fq* a) {
     wsync<NW>();
 }
 
-// out = a^-1 (one lane, tower arithmetic)
+// a <- a^-1 for a in Fq2 (flat coefficient 0; the others are zero), on one lane
 template <int NW>
-FPG_NOINL void w_inv(fq* out, const fq* a) {
+FPG_NOINL void w_inv_fq2(fq* a) {
     const int L = w_lane<NW>();
     wsync<NW>();
     if (L == 0) {
-        fq12 f;
-        fq* fc = reinterpret_cast<fq*>(&f);
-        for (int o = 0; o < 12; o++) fc[2 * w_tower_pos(o >> 1) + (o & 1)] = a[o];
-        const fq12 fi = fq12_inv(f);
-        const fq* ic = reinterpret_cast<const fq*>(&fi);
-        for (int o = 0; o < 12; o++) out[o] = ic[2 * w_tower_pos(o >> 1) + (o & 1)];
+        const fq2 v{a[0], a[1]};
+        const fq2 vi = fq2_inv(v);
+        a[0] = vi.c0;
+        a[1] = vi.c1;
     }
     wsync<NW>();
 }
@@ -254,6 +261,9 @@ FPG_NOINL void w_cyc_exp(W12& W, fq* acc, const fq* base, const uint32_t* e, int
 
 // slot 2 <- f^((p^12 - 1)/r) for f in slot 0 (slots 0..4 are used).  Easy part t = conj(f) f^-1,
 // g = t^(p^2) t; hard part g^d with d = h1 (x + p)(x^2 + p^2 - 1) + 1, h1 = (x - 1)^2 / 3, x < 0.
+// The inverse goes through norms: n = f conj(f) lies in Fq6, u = n^(p^2) n^(p^4), and n u is the
+// norm of n to Fq2, so f^-1 = conj(f) / n = conj(f) u / (n u) and t = conj(f)^2 u (n u)^-1: six
+// lane-parallel Fq12 products, two Frobenius maps and one Fq2 inversion on one lane.
 template <int NW>
 FPG_NOINL void w_final_exp(W12& W) {
     fq* s0 = W.s[0];
@@ -263,9 +273,16 @@ FPG_NOINL void w_final_exp(W12& W) {
     fq* s4 = W.s[4];
     const uint32_t xabs[2] = {(uint32_t)BLS_X_ABS, (uint32_t)(BLS_X_ABS >> 32)};
     const uint32_t h1[4] = {BLS_H1[0], BLS_H1[1], BLS_H1[2], BLS_H1[3]};
-    w_inv<NW>(s1, s0);                      // f^-1
-    w_conj<NW>(s0, s0);                     // conj(f)
-    w_mul<NW>(W, s2, s0, s1);               // t
+    w_conj<NW>(s1, s0);                     // c = conj(f)
+    w_mul<NW>(W, s2, s0, s1);               // n = f c, in Fq6
+    w_frob2<NW>(W, s3, s2);
+    w_frob2<NW>(W, s4, s3);
+    w_mul<NW>(W, s3, s3, s4);               // u = n^(p^2 + p^4)
+    w_mul<NW>(W, s4, s2, s3);               // n u, in Fq2
+    w_inv_fq2<NW>(s4);
+    w_mul<NW>(W, s2, s1, s1);
+    w_mul<NW>(W, s2, s2, s3);
+    w_mul<NW>(W, s2, s2, s4);               // t = c^2 u (n u)^-1 = conj(f) f^-1
     w_frob2<NW>(W, s3, s2);
     w_mul<NW>(W, s3, s3, s2);               // g = t^(p^2) t
     w_cyc_exp<NW>(W, s4, s3, h1, 126);      // a = g^h1
