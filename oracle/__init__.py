@@ -52,6 +52,11 @@ def lib():
             vp = ctypes.c_void_p
             L.or_setup.restype = vp
             L.or_setup.argtypes = [ctypes.c_uint32, ctypes.c_uint64]
+            L.or_setup_split.restype = vp
+            L.or_setup_split.argtypes = [ctypes.c_uint32, ctypes.c_uint32, ctypes.c_uint64]
+            L.or_segment_proof_len.restype = ctypes.c_size_t
+            L.or_segment_proof_len.argtypes = [vp, ctypes.c_uint32, ctypes.c_uint32]
+            L.or_verify_segment.argtypes = [vp, vp, ctypes.c_uint32, ctypes.c_uint32, vp, vp, ctypes.c_size_t]
             L.or_pp_free.argtypes = [vp]
             L.or_pp_bytes.restype = ctypes.c_size_t
             L.or_pp_bytes.argtypes = [vp, vp]
@@ -234,10 +239,14 @@ def splitmix_fr(seed: int, n: int) -> list[int]:
 
 # --------------------------------------------------------------------------- protocol
 class PP:
-    """VC.Setup output (Eq. vcpp) held by the oracle."""
+    """VC.Setup output (Eq. vcpp) held by the oracle.  log_r (default floor(log_n / 2)) sets the
+    number of segments R = 2^log_r, each of M = N / R elements (OpenAll for sub-arrays, Sec. 4.4)."""
 
-    def __init__(self, log_n: int, seed: int):
-        self.h = lib().or_setup(log_n, seed)
+    def __init__(self, log_n: int, seed: int, log_r: int | None = None):
+        if log_r is None:
+            self.h = lib().or_setup(log_n, seed)
+        else:
+            self.h = lib().or_setup_split(log_r, log_n - log_r, seed)
         if not self.h:
             raise ValueError("or_setup failed")
         info = (ctypes.c_uint32 * 4)()
@@ -266,6 +275,9 @@ class PP:
 
     def proof_len(self, b: int, k: int) -> int:
         return lib().or_proof_len(self.h, b, k)
+
+    def segment_proof_len(self, b: int, k: int) -> int:
+        return lib().or_segment_proof_len(self.h, b, k)
 
 
 def commit(pp: PP, m_limbs: bytes):
@@ -346,6 +358,21 @@ def verify(pp: PP, C: bytes, b: int, i: int, m_i: int, proof: bytes, memo: bool 
     """VC.Verify.  With memo=True identical FC.BVerify / PST.Verify sub-checks (same block, same
     column, byte-identical inputs) are answered from a cache keyed by a hash of those inputs."""
     return bool(lib().or_verify(pp.h, C, b, i, m_i.to_bytes(32, "big"), proof, len(proof), int(memo)))
+
+
+def segment_proof(pp: PP, rows: bytes, prover: "Prover", j: int) -> bytes:
+    """OpenAll for sub-arrays (Sec. 4.4): the proof of segment j is its block's row commitments and
+    pi_{C_k} from Step 1 (prover.blocks() must have run for block k = j // b)."""
+    b = prover.b
+    k = j // b
+    lo, hi = k * b, min((k + 1) * b, pp.R)
+    return rows[96 * lo: 96 * hi] + prover.block_bytes(k)
+
+
+def verify_segment(pp: PP, C: bytes, b: int, j: int, m_j_limbs: bytes, proof: bytes) -> bool:
+    """Verifier V_j of OpenAll for sub-arrays: C_j recomputed from m_j (M x 4 little-endian u64)
+    must be the block's entry j, and FC.BVerify of the block must accept."""
+    return bool(lib().or_verify_segment(pp.h, C, b, j, m_j_limbs, proof, len(proof)))
 
 
 def verify_many(pp: PP, C: bytes, b: int, items, threads: int | None = None) -> list[bool]:

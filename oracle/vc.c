@@ -108,12 +108,15 @@ static void eq_weight(fe* w, const or_pp* pp, int t, u32 c) {
 }
 
 /* VC.Setup (Eq. vcpp): pp_PC for l_c variables (Lambda tables, g2^tau) and pp_FC of size R
- * with the faster-verification extras (all g2^{beta^i}, i < 2R - 1, and g1^beta). */
-or_pp* or_setup(u32 log_n, u64 seed) {
+ * with the faster-verification extras (all g2^{beta^i}, i < 2R - 1, and g1^beta).  R = 2^l_R
+ * segments of M = 2^l_c elements (OpenAll for sub-arrays, Sec. 4.4, partitions m into any number
+ * of equal segments); or_setup takes l_R = floor(n/2).  The trapdoor stream draws beta, then
+ * tau_0, tau_1, ...: the tables of a smaller split are prefixes of a larger split's. */
+or_pp* or_setup_split(u32 log_r, u32 log_c, u64 seed) {
     if (or_init()) return NULL;
-    if (log_n < 2 || log_n > 26) return NULL;
+    if (log_r < 1 || log_c < 1 || log_r > 13 || log_r + log_c > 26) return NULL;
     or_pp* pp = (or_pp*)calloc(1, sizeof *pp);
-    pp->log_n = (int)log_n; pp->log_r = (int)log_n / 2; pp->log_c = (int)log_n - pp->log_r;
+    pp->log_n = (int)(log_r + log_c); pp->log_r = (int)log_r; pp->log_c = (int)log_c;
     pp->R = 1u << pp->log_r; pp->M = 1u << pp->log_c; pp->seed = seed;
     splitmix s = {seed ^ 0x5eed5eedull};
     u64 l[4];
@@ -135,6 +138,10 @@ or_pp* or_setup(u32 log_n, u64 seed) {
     pp->g2tau = (g2*)calloc((size_t)pp->log_c + 1, sizeof(g2));
     for (int t = 0; t < pp->log_c; t++) g2_mul(&pp->g2tau[t], &G2_GEN, &pp->tau[t]);
     return pp;
+}
+or_pp* or_setup(u32 log_n, u64 seed) {
+    if (log_n < 2 || log_n > 26) return NULL;
+    return or_setup_split(log_n / 2, log_n - log_n / 2, seed);
 }
 void or_pp_free(or_pp* pp) {
     if (!pp) return;
@@ -578,30 +585,16 @@ int or_prove_one(const or_pp* pp, const u64* m, const u8* C, const u8* rows, u32
     return 0;
 }
 
-/* ------------------------------------------------------------------------------
- * VC.Verify (Protocol 1 verifier steps; the combination D* = r_j C_j + sum D_w,
- * y* = r_j m_i + sum y_w of Appendix C; FC.BVerify with the b_l shortcut of Eq. b_l and the
- * faster-verification check; PST.Verify).  Returns 1 if the proof is accepted, 0 if not.
- * ------------------------------------------------------------------------------ */
-int or_verify(const or_pp* pp, const u8* C, u32 b, u64 i, const u8 mi_be[32], const u8* proof, size_t len, int use_memo) {
-    const u32 R = pp->R, M = pp->M; const int lr = pp->log_r, lc = pp->log_c;
-    if (b < 1 || b > R || i >= (u64)R * M) return 0;
-    u32 j = (u32)(i / M), a = (u32)(i % M), k = j / b;
-    if (len != or_proof_len(pp, b, k)) return 0;
-    fe mi; if (f_from_be(&FR, &mi, mi_be, 32)) return 0;
-    u32 lo = k * b, hi = (k + 1) * b < R ? (k + 1) * b : R, nk = hi - lo;
-    const u8* blk = proof;
-    const u8* fc = blk + 96 * (size_t)nk;
-    const u8* path = fc + or_bopen_len(pp);
-    const u8* sib = path + 32 * (size_t)pp->log_n;
-    const u8* pst = sib + 128 * (size_t)lr;
+/* FC.BVerify of block k (Sec. 3, with the b_l shortcut of Sec. 4.3 and the faster-verification
+ * check of v_l) for the block's row commitments Ca (decoded from blk) and pi_{C_k} at fc.
+ * Returns 1 if accepted.  The memo key covers every input, the split included. */
+static int fc_bverify(const or_pp* pp, const fq12* Cgp, const u8* C, u32 b, u32 k, const u8* blk, const g1* Ca,
+                      u32 nk, const u8* fc, int use_memo) {
+    const u32 R = pp->R; const int lr = pp->log_r;
+    const u32 lo = k * b;
+    const fq12 Cg = *Cgp;
     int ok = 1;
-    fq12 Cg; if (fq12_from_bytes(&Cg, C)) return 0;
-
-    /* --- FC.BVerify --- */
-    g1* Ca = (g1*)malloc(nk * sizeof(g1));
-    for (u32 t = 0; t < nk; t++) if (g1_from_bytes(&Ca[t], blk + 96 * (size_t)t)) { free(Ca); return 0; }
-    u32 pid[4] = {(u32)pp->log_n, (u32)pp->seed, (u32)(pp->seed >> 32), b};
+    u32 pid[5] = {(u32)pp->log_n, (u32)pp->seed, (u32)(pp->seed >> 32), b, (u32)pp->log_r};
     u8 hdr[576 + 4]; memcpy(hdr, C, 576); be32(hdr + 576, k);
     u8 bkey[32]; int cached = 0, cval = 0;
     if (use_memo) {
@@ -671,6 +664,33 @@ int or_verify(const or_pp* pp, const u8* C, u32 b, u64 i, const u8 mi_be[32], co
         free(rr);
         if (use_memo) memo_put(bkey, ok);
     }
+    return ok;
+}
+
+/* ------------------------------------------------------------------------------
+ * VC.Verify (Protocol 1 verifier steps; the combination D* = r_j C_j + sum D_w,
+ * y* = r_j m_i + sum y_w of Appendix C; FC.BVerify with the b_l shortcut of Eq. b_l and the
+ * faster-verification check; PST.Verify).  Returns 1 if the proof is accepted, 0 if not.
+ * ------------------------------------------------------------------------------ */
+int or_verify(const or_pp* pp, const u8* C, u32 b, u64 i, const u8 mi_be[32], const u8* proof, size_t len, int use_memo) {
+    const u32 R = pp->R, M = pp->M; const int lr = pp->log_r, lc = pp->log_c;
+    if (b < 1 || b > R || i >= (u64)R * M) return 0;
+    u32 j = (u32)(i / M), a = (u32)(i % M), k = j / b;
+    if (len != or_proof_len(pp, b, k)) return 0;
+    fe mi; if (f_from_be(&FR, &mi, mi_be, 32)) return 0;
+    u32 lo = k * b, hi = (k + 1) * b < R ? (k + 1) * b : R, nk = hi - lo;
+    const u8* blk = proof;
+    const u8* fc = blk + 96 * (size_t)nk;
+    const u8* path = fc + or_bopen_len(pp);
+    const u8* sib = path + 32 * (size_t)pp->log_n;
+    const u8* pst = sib + 128 * (size_t)lr;
+    fq12 Cg; if (fq12_from_bytes(&Cg, C)) return 0;
+    u32 pid[5] = {(u32)pp->log_n, (u32)pp->seed, (u32)(pp->seed >> 32), b, (u32)pp->log_r};
+
+    /* --- FC.BVerify --- */
+    g1* Ca = (g1*)malloc(nk * sizeof(g1));
+    for (u32 t = 0; t < nk; t++) if (g1_from_bytes(&Ca[t], blk + 96 * (size_t)t)) { free(Ca); return 0; }
+    int ok = fc_bverify(pp, &Cg, C, b, k, blk, Ca, nk, fc, use_memo);
     if (!ok) { free(Ca); return 0; }
     g1 Cj = Ca[j - lo];
     free(Ca);
@@ -721,4 +741,34 @@ int or_verify(const or_pp* pp, const u8* C, u32 b, u64 i, const u8 mi_be[32], co
     int res = fq12_eq(&el, &er) ? 1 : 0;
     if (use_memo) memo_put(pkey, res);
     return res;
+}
+
+/* ------------------------------------------------------------------------------
+ * OpenAll for sub-arrays (Sec. 4.4): the proof for segment j is its block's row commitments
+ * (C_a)_{a in S_k} and pi_{C_k} (Step 1 only).  Verifier V_j recomputes C_j from its segment m_j
+ * (the MLE commitment of m_j, as in VC.Commit) and checks it against the block's entry, then runs
+ * FC.BVerify of the block.  m_j: M x 4 little-endian u64.  Returns 1 if accepted, 0 if not.
+ * ------------------------------------------------------------------------------ */
+size_t or_segment_proof_len(const or_pp* pp, u32 b, u32 k) {
+    u32 lo = k * b, hi = (k + 1) * b < pp->R ? (k + 1) * b : pp->R;
+    return 96 * (size_t)(hi - lo) + or_bopen_len(pp);
+}
+int or_verify_segment(const or_pp* pp, const u8* C, u32 b, u32 j, const u64* m_j, const u8* proof, size_t len) {
+    const u32 R = pp->R, M = pp->M;
+    if (b < 1 || b > R || j >= R) return 0;
+    const u32 k = j / b, lo = k * b, hi = (k + 1) * b < R ? (k + 1) * b : R, nk = hi - lo;
+    if (len != or_segment_proof_len(pp, b, k)) return 0;
+    fe* mm = (fe*)malloc(M * sizeof(fe));
+    if (load_m(mm, m_j, M)) { free(mm); return 0; }
+    const g1* L = LAM(pp, pp->log_c);
+    g1 Cj; g1_set_inf(&Cj);
+    for (u32 a = 0; a < M; a++) { g1 t; g1_mul(&t, &L[a], &mm[a]); g1_add(&Cj, &Cj, &t); }
+    free(mm);
+    fq12 Cg; if (fq12_from_bytes(&Cg, C)) return 0;
+    g1* Ca = (g1*)malloc(nk * sizeof(g1));
+    for (u32 t = 0; t < nk; t++) if (g1_from_bytes(&Ca[t], proof + 96 * (size_t)t)) { free(Ca); return 0; }
+    int ok = g1_eq(&Ca[j - lo], &Cj);
+    if (ok) ok = fc_bverify(pp, &Cg, C, b, k, proof, Ca, nk, proof + 96 * (size_t)nk, 0);
+    free(Ca);
+    return ok;
 }
