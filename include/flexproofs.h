@@ -59,12 +59,23 @@ typedef enum {
  * The trapdoor never leaves the device and is discarded before returning. */
 fp_status vc_setup(uint32_t log_n, uint32_t b, uint64_t seed, void* stream, fp_pp** out);
 
+/* VC.Setup for N = R M split into R = 2^log_r segments of M = 2^log_c elements (OpenAll for
+ * sub-arrays, Sec. 4.4, partitions m into any number of equal segments; vc_setup is the split
+ * log_r = floor(log_n / 2)).  Same trapdoor stream as vc_setup, so every table is a prefix of the
+ * tables of any setup with at least as many rows and columns.  1 <= log_r <= 13, 1 <= log_c,
+ * log_r + log_c <= 26; b in [1, R].  Every call that takes an fp_pp works on any split. */
+fp_status vc_setup_split(uint32_t log_r, uint32_t log_c, uint32_t b, uint64_t seed, void* stream, fp_pp** out);
+
 /* A view of `pp` for a smaller size 2^log_n (2 <= log_n <= pp's): the same trapdoor, so every table
  * of the smaller setup is a prefix of the larger one's (Lambda_t for t <= l_c, g2^{beta^i} for
  * i < 2R - 1, g2^{tau_t} for t < l_c) and the view shares them; it owns only a small MSM table
  * (2M points).  One resident SRS then serves jobs of every smaller N.  The view must be freed
  * (fp_pp_free) before its parent.  Synchronises the legacy default stream. */
 fp_status vc_pp_view(const fp_pp* pp, uint32_t log_n, fp_pp** out);
+
+/* vc_pp_view for any split: log_r <= the parent's log_r and log_c <= the parent's log_c
+ * (FP_EINVAL otherwise). */
+fp_status vc_pp_view_split(const fp_pp* pp, uint32_t log_r, uint32_t log_c, fp_pp** out);
 
 /* Serialised public parameters (synchronises): Lambda (2M-1) x 96 || g1^beta 96 ||
  * g2^{beta^i} (2R-1) x 192 || g2^{tau_t} l_c x 192.  *len receives the size; out may be NULL to
@@ -140,6 +151,32 @@ fp_status vc_prove_all_batch(uint32_t njobs, const fp_job* jobs, int use_graph, 
  * work).  i >= N or b out of range gives FP_EINVAL.  Synchronises `stream`. */
 fp_status vc_prove_one(const fp_pp* pp, const fp_commit* cm, uint32_t b, uint64_t i, void* stream, uint8_t* out,
                        size_t cap, size_t* len);
+
+/* OpenAll for sub-arrays (Sec. 4.4): VC.Commit made the R segment commitments C_j, and Step 1
+ * alone proves that C_j is the j-th element of the committed vector for the segments of blocks
+ * k0 .. k0 + nblocks - 1 (nblocks = 0: every block from k0 on), b segments per block.  The
+ * handle holds those blocks' pi_{C_k}; vc_segment_proof_get reads a segment's proof from it.
+ * Element proofs (vc_proof_get, vc_proofs_export, vc_verify_all) are refused on it (FP_EINVAL).
+ * Enqueues only, like vc_prove_all. */
+fp_status vc_open_segments(const fp_pp* pp, const fp_commit* cm, uint32_t b, uint32_t k0, uint32_t nblocks,
+                           void* stream, fp_proofs** out);
+
+/* Byte length of segment j's proof under batch size b: the block's row commitments (C_a)_{a in S_k}
+ * (96 B each) || pi_{C_k}, k = j / b.  0 for bad arguments.  No device work. */
+size_t vc_segment_proof_len(const fp_pp* pp, uint32_t b, uint32_t j);
+
+/* Segment j's proof (host, synchronises) from a vc_open_segments or vc_prove_all handle; the same
+ * bytes are the prefix of every element proof of segment j.  FP_EINVAL if j's block was not
+ * opened or cap is too small (out = NULL queries *len). */
+fp_status vc_segment_proof_get(const fp_proofs* pf, uint32_t j, uint8_t* out, size_t cap, size_t* len);
+
+/* Verifier V_j of OpenAll for sub-arrays, on the GPU: C_j recomputed from the segment m_j (M x 4
+ * little-endian uint64 on the host; the MLE commitment of VC.Commit) must equal the block's entry
+ * for j, and FC.BVerify of the block (b_l shortcut, fast verification of v_l) must accept.
+ * FP_OK if both hold, FP_EVERIFY if not (also for a value of m_j >= r, a wrong length or a
+ * malformed element), FP_EINVAL for bad arguments.  Synchronises `stream`. */
+fp_status vc_verify_segment(const fp_pp* pp, const uint8_t* C, uint32_t b, uint32_t j, const uint64_t* m_j,
+                            const uint8_t* proof, size_t len, void* stream);
 
 /* Byte length of proof i under batch size b (no device work). */
 size_t vc_proof_len(const fp_pp* pp, uint32_t b, uint64_t i);

@@ -20,7 +20,9 @@ EXPORTED = ["vc_setup", "vc_pp_export", "vc_pp_dims", "vc_commit", "vc_commit_ge
             "fp_profile_enable", "fp_profile_report", "fp_imad_probe", "vc_commit_rows_noalloc",
             "fp_g1_bases_from_scalars", "fp_g1_bases_load", "fp_g1_bases_count", "fp_g1_bases_free", "fp_msm_g1",
             "fp_msm_window", "fp_msm_autotune", "vc_prove_one", "vc_pp_view", "vc_commit_async",
-            "vc_commit_status", "vc_prove_all_batch", "vc_verify", "vc_verify_all"]
+            "vc_commit_status", "vc_prove_all_batch", "vc_verify", "vc_verify_all", "vc_setup_split",
+            "vc_pp_view_split", "vc_open_segments", "vc_segment_proof_len", "vc_segment_proof_get",
+            "vc_verify_segment"]
 
 
 class FlexProofsError(RuntimeError):
@@ -58,6 +60,13 @@ def load(path: str = LIB_PATH):
     L.vc_pp_view.argtypes = [vp, u32, pp]
     L.vc_verify.argtypes = [vp, vp, u32, u64, vp, vp, sz, vp]
     L.vc_verify_all.argtypes = [vp, vp, vp, ctypes.c_int, vp, ctypes.c_int, vp, vp, ctypes.POINTER(u64)]
+    L.vc_setup_split.argtypes = [u32, u32, u32, u64, vp, pp]
+    L.vc_pp_view_split.argtypes = [vp, u32, u32, pp]
+    L.vc_open_segments.argtypes = [vp, vp, u32, u32, u32, vp, pp]
+    L.vc_segment_proof_len.argtypes = [vp, u32, u32]
+    L.vc_segment_proof_len.restype = sz
+    L.vc_segment_proof_get.argtypes = [vp, u32, vp, sz, ctypes.POINTER(sz)]
+    L.vc_verify_segment.argtypes = [vp, vp, u32, u32, vp, vp, sz, vp]
     L.vc_commit_async.argtypes = [vp, vp, ctypes.c_int, vp, pp]
     L.vc_commit_status.argtypes = [vp]
     L.vc_prove_all_batch.argtypes = [u32, vp, ctypes.c_int, vp, vp]
@@ -106,14 +115,22 @@ def _stream_ptr(stream) -> int | None:
 
 class PP:
     """Handle of vc_setup's device-resident public parameters (or, with parent=, a vc_pp_view of a
-    larger setup for size 2^log_n)."""
+    larger setup for size 2^log_n).  log_r (default floor(log_n / 2)) splits N into R = 2^log_r
+    segments of M = N / R elements (vc_setup_split / vc_pp_view_split)."""
 
-    def __init__(self, log_n: int, b: int = 1, seed: int = 0, stream=None, parent: "PP | None" = None):
+    def __init__(self, log_n: int, b: int = 1, seed: int = 0, stream=None, parent: "PP | None" = None,
+                 log_r: int | None = None):
         L = load()
         h = ctypes.c_void_p()
         if parent is not None:
-            _check("vc_pp_view", L.vc_pp_view(parent.h, log_n, ctypes.byref(h)))
+            if log_r is None:
+                _check("vc_pp_view", L.vc_pp_view(parent.h, log_n, ctypes.byref(h)))
+            else:
+                _check("vc_pp_view_split", L.vc_pp_view_split(parent.h, log_r, log_n - log_r, ctypes.byref(h)))
             self.parent = parent                     # keeps the parent alive while the view lives
+        elif log_r is not None:
+            _check("vc_setup_split", L.vc_setup_split(log_r, log_n - log_r, b, seed, _stream_ptr(stream),
+                                                      ctypes.byref(h)))
         else:
             _check("vc_setup", L.vc_setup(log_n, b, seed, _stream_ptr(stream), ctypes.byref(h)))
         self.h = h
@@ -135,8 +152,11 @@ class PP:
     def proof_len(self, b: int, i: int) -> int:
         return load().vc_proof_len(self.h, b, i)
 
-    def view(self, log_n: int) -> "PP":
-        return PP(log_n, parent=self)
+    def view(self, log_n: int, log_r: int | None = None) -> "PP":
+        return PP(log_n, parent=self, log_r=log_r)
+
+    def segment_proof_len(self, b: int, j: int) -> int:
+        return load().vc_segment_proof_len(self.h, b, j)
 
     def __del__(self):
         if getattr(self, "h", None) and _lib is not None:
@@ -193,6 +213,14 @@ class Proofs:
         h = ctypes.c_void_p()
         _check("vc_prove_all", L.vc_prove_all(pp.h, cm.h, b, _stream_ptr(stream), ctypes.byref(h)))
         self.h = h
+
+    def segment_proof(self, j: int) -> bytes:
+        """Segment j's proof (OpenAll for sub-arrays): its block's row commitments and pi_{C_k}."""
+        n = self.pp.segment_proof_len(self.b, j)
+        buf = ctypes.create_string_buffer(n)
+        ln = ctypes.c_size_t()
+        _check("vc_segment_proof_get", load().vc_segment_proof_get(self.h, j, buf, n, ctypes.byref(ln)))
+        return buf.raw[: ln.value]
 
     def proof(self, i: int) -> bytes:
         n = self.pp.proof_len(self.b, i)
@@ -292,6 +320,24 @@ def vc_verify_all(pf: "Proofs", C: bytes, m, each: bool = False, stream=None):
                                                  ok.ctypes.data, ctypes.byref(n_ok)))
     del keep
     return ok.astype(bool), int(n_ok.value)
+
+
+def vc_open_segments(pp: PP, cm: Commitment, b: int, k0: int = 0, nblocks: int = 0, stream=None) -> "Proofs":
+    """OpenAll for sub-arrays: Step 1 only, for blocks k0 .. k0 + nblocks - 1 (0: all from k0)."""
+    h = ctypes.c_void_p()
+    _check("vc_open_segments", load().vc_open_segments(pp.h, cm.h, b, k0, nblocks, _stream_ptr(stream),
+                                                       ctypes.byref(h)))
+    return Proofs(pp, cm, b, handle=h)
+
+
+def vc_verify_segment(pp: PP, C: bytes, b: int, j: int, m_j, proof: bytes, stream=None) -> bool:
+    """Verifier V_j of OpenAll for sub-arrays on the GPU (m_j: M x 4 uint64 limbs)."""
+    arr = np.ascontiguousarray(m_j, dtype=np.uint64)
+    assert arr.size == 4 * pp.M
+    st = load().vc_verify_segment(pp.h, C, b, j, arr.ctypes.data, proof, len(proof), _stream_ptr(stream))
+    if st not in (0, 5):
+        raise FlexProofsError("vc_verify_segment", st)
+    return st == 0
 
 
 def vc_prove_one(pp: PP, cm: Commitment, b: int, i: int, stream=None) -> bytes:

@@ -144,6 +144,10 @@ size_t verify_scratch_bytes(uint32_t b, int lr, int lc);
 void verify_one(const void* proof, const void* C_be, const void* mi_be, uint32_t nk, int lr, int lc, uint32_t b,
                 uint64_t i, uint32_t M, uint32_t k, uint32_t lo, const void* g1beta, const void* g2tau, void* scratch,
                 uint32_t* result, cudaStream_t s);
+// FC.BVerify of one block: blk = its nk row commitments, fc = pi_{C_k}; result word 0 = 0 if accepted
+size_t verify_block_scratch_bytes(uint32_t b, int lr);
+void verify_block(const void* blk, const void* fc, const void* C_be, uint32_t nk, int lr, uint32_t b, uint32_t k,
+                  uint32_t lo, const void* g1beta, void* scratch, uint32_t* result, cudaStream_t s);
 // All N proofs of an OpenAll output (its shared pieces as stored by vc_prove_all) against the
 // claimed values m (device, N x 4 little-endian u64): ok_out (host, N bytes, may be null) gets 1
 // per accepted proof; returns the number accepted.  each = 1: no PST check is shared.  Synchronises.

@@ -62,6 +62,8 @@ struct fp_proofs {
     void* D_ser = nullptr;     // (2R - 1) x 96
     void* pst_ser = nullptr;   // (M - 1) x 96
     cudaStream_t stream;
+    bool step2 = true;         // false: Step 1 only (OpenAll for sub-arrays), no element proofs
+    uint32_t k0 = 0, nopen = 0;   // blocks [k0, k0 + nopen) hold their pi_{C_k}
 };
 
 namespace {
@@ -192,7 +194,12 @@ const char* fp_last_error(void) { return g_last_error.c_str(); }
 
 fp_status vc_setup(uint32_t log_n, uint32_t b, uint64_t seed, void* stream, fp_pp** out) {
     if (!out || log_n < 2 || log_n > 26) return FP_EINVAL;
-    const uint32_t log_r = log_n / 2, log_c = log_n - log_r, R = 1u << log_r, M = 1u << log_c;
+    return vc_setup_split(log_n / 2, log_n - log_n / 2, b, seed, stream, out);
+}
+
+fp_status vc_setup_split(uint32_t log_r, uint32_t log_c, uint32_t b, uint64_t seed, void* stream, fp_pp** out) {
+    if (!out || log_r < 1 || log_c < 1 || log_r > 13 || log_r + log_c > 26) return FP_EINVAL;
+    const uint32_t log_n = log_r + log_c, R = 1u << log_r, M = 1u << log_c;
     if (b < 1 || b > R) return FP_EINVAL;
     cudaStream_t s = (cudaStream_t)stream;
     return guarded([&]() -> fp_status {
@@ -366,9 +373,15 @@ fp_status vc_commit_status(const fp_commit* cm) {
 
 fp_status vc_pp_view(const fp_pp* pp, uint32_t log_n, fp_pp** out) {
     if (!pp || !out || log_n < 2 || log_n > pp->log_n) return FP_EINVAL;
+    return vc_pp_view_split(pp, log_n / 2, log_n - log_n / 2, out);
+}
+
+fp_status vc_pp_view_split(const fp_pp* pp, uint32_t log_r, uint32_t log_c, fp_pp** out) {
+    if (!pp || !out || log_r < 1 || log_c < 1) return FP_EINVAL;
     const fp_pp* root = pp->parent ? pp->parent : pp;
+    if (log_r > root->log_r || log_c > root->log_c) return FP_EINVAL;
     return guarded([&]() -> fp_status {
-        const uint32_t log_r = log_n / 2, log_c = log_n - log_r, R = 1u << log_r, M = 1u << log_c;
+        const uint32_t log_n = log_r + log_c, R = 1u << log_r, M = 1u << log_c;
         fp_pp* v = new fp_pp{log_n, log_r, log_c, R, M};
         v->parent = root;
         v->lam = root->lam;                 // Lambda_t for t <= l_c are the same prefix levels
@@ -412,7 +425,7 @@ namespace {
 // OpenAll's work with Step 1 restricted to the blocks [k0, k0 + Kc) (all blocks: k0 = 0, Kc = K):
 // their records are written at their places in the K-block array; Step 2 runs in full.
 fp_proofs* prove_impl(const fp_pp* pp, const fp_commit* cm, uint32_t b, uint32_t k0, uint32_t Kc, cudaStream_t s,
-                      bool track_use = true) {
+                      bool track_use = true, bool with_step2 = true) {
     const uint32_t R = pp->R, M = pp->M;
     {
         const int lr = (int)pp->log_r, lc = (int)pp->log_c;
@@ -420,6 +433,9 @@ fp_proofs* prove_impl(const fp_pp* pp, const fp_commit* cm, uint32_t b, uint32_t
         fp_proofs* pf = new fp_proofs{pp};
         pf->stream = s;
         pf->L = ProofLayout{R, M, b, K, (int)pp->log_n, lr, lc, bopen_len(pp->log_r)};
+        pf->step2 = with_step2;
+        pf->k0 = k0;
+        pf->nopen = Kc;
         const size_t blen = pf->L.bopen_len;
         uint8_t* blocks1 = nullptr;
         std::vector<void*> tmp;
@@ -432,16 +448,19 @@ fp_proofs* prove_impl(const fp_pp* pp, const fp_commit* cm, uint32_t b, uint32_t
             pf->blocks = dalloc(K * blen, s);
             blocks1 = (uint8_t*)pf->blocks + (size_t)k0 * blen;
             // Step 2 depends only on the commitment: it runs on a second stream, concurrently with Step 1
-            pf->row_tree = dalloc((size_t)R * (2 * M - 1) * DIGEST, s);
-            pf->top_tree = dalloc((2 * (size_t)R - 1) * DIGEST, s);
-            pf->rj = dalloc(R * FR_BYTES, s);
-            pf->g = dalloc((2 * (size_t)R - 1) * M * FR_BYTES, s);
-            pf->D = dalloc((2 * (size_t)R - 1) * G1A_BYTES, s);
-            pf->D_ser = dalloc((2 * (size_t)R - 1) * G1_SER, s);
-            pf->pst_ser = dalloc(((size_t)M - 1) * G1_SER, s);
             const uint64_t half = M / 2;
-            void* pt = T((size_t)lc * half * G1J_BYTES);
-            void* pt2 = T((half / 2 + 1) * G1J_BYTES);
+            void *pt = nullptr, *pt2 = nullptr;
+            if (with_step2) {
+                pf->row_tree = dalloc((size_t)R * (2 * M - 1) * DIGEST, s);
+                pf->top_tree = dalloc((2 * (size_t)R - 1) * DIGEST, s);
+                pf->rj = dalloc(R * FR_BYTES, s);
+                pf->g = dalloc((2 * (size_t)R - 1) * M * FR_BYTES, s);
+                pf->D = dalloc((2 * (size_t)R - 1) * G1A_BYTES, s);
+                pf->D_ser = dalloc((2 * (size_t)R - 1) * G1_SER, s);
+                pf->pst_ser = dalloc(((size_t)M - 1) * G1_SER, s);
+                pt = T((size_t)lc * half * G1J_BYTES);
+                pt2 = T((half / 2 + 1) * G1J_BYTES);
+            }
             // every buffer is allocated (stream-ordered on s) before the fork to the internal streams
             const uint64_t KR = (uint64_t)Kc * R;
             void* A = T(KR * G1A_BYTES);
@@ -477,26 +496,28 @@ fp_proofs* prove_impl(const fp_pp* pp, const fp_commit* cm, uint32_t b, uint32_t
             check(cudaStreamWaitEvent(s2, ev_fork, 0), "wait");
             check(cudaStreamWaitEvent(s1, ev_fork, 0), "wait");
             // ---------------- Step 2: Merkle tree, randomise, fold tree, HyperEval (stream s2)
-            step2_leaves(cm->m_canon, R, M, pf->row_tree, s2);
-            for (int l = 1; l <= lc; l++) tree_level(pf->row_tree, R, M, l, s2);
-            step2_row_leaves(pf->row_tree, cm->rows_ser, R, M, pf->top_tree, s2);
-            for (int l = 1; l <= lr; l++) tree_level(pf->top_tree, 1, R, l, s2);
-            step2_rj(pf->top_tree, R, pf->rj, s2);
-            step2_randomize(cm->m_mont, pf->rj, R, M, pf->g, s2);
-            step2_d0(cm->rows, pf->rj, R, pf->D, s2);
-            for (int h = 1; h <= lr; h++) {
-                step2_fold_g(pf->g, R, M, h, s2);
-                step2_fold_d(pf->D, R, h, s2);
-            }
-            g1a_serialize(pf->D, pf->D_ser, G1_SER, 2 * (uint64_t)R - 1, s2);
-            step2_pst_terms(pf->g, pp->lam, R, M, lc, pt, s2);
-            size_t pst_off = 0;
-            for (int t = 0; t < lc; t++) {
-                void* lvl = (uint8_t*)pt + (size_t)t * half * G1J_BYTES;
-                uint64_t nseg = half >> t;
-                void* res = reduce_pairs(lvl, pt2, half, nseg, g1_pair_reduce, s2);
-                g1j_to_affine(res, nullptr, (uint8_t*)pf->pst_ser + pst_off * G1_SER, G1_SER, nseg, s2);
-                pst_off += nseg;
+            if (with_step2) {
+                step2_leaves(cm->m_canon, R, M, pf->row_tree, s2);
+                for (int l = 1; l <= lc; l++) tree_level(pf->row_tree, R, M, l, s2);
+                step2_row_leaves(pf->row_tree, cm->rows_ser, R, M, pf->top_tree, s2);
+                for (int l = 1; l <= lr; l++) tree_level(pf->top_tree, 1, R, l, s2);
+                step2_rj(pf->top_tree, R, pf->rj, s2);
+                step2_randomize(cm->m_mont, pf->rj, R, M, pf->g, s2);
+                step2_d0(cm->rows, pf->rj, R, pf->D, s2);
+                for (int h = 1; h <= lr; h++) {
+                    step2_fold_g(pf->g, R, M, h, s2);
+                    step2_fold_d(pf->D, R, h, s2);
+                }
+                g1a_serialize(pf->D, pf->D_ser, G1_SER, 2 * (uint64_t)R - 1, s2);
+                step2_pst_terms(pf->g, pp->lam, R, M, lc, pt, s2);
+                size_t pst_off = 0;
+                for (int t = 0; t < lc; t++) {
+                    void* lvl = (uint8_t*)pt + (size_t)t * half * G1J_BYTES;
+                    uint64_t nseg = half >> t;
+                    void* res = reduce_pairs(lvl, pt2, half, nseg, g1_pair_reduce, s2);
+                    g1j_to_affine(res, nullptr, (uint8_t*)pf->pst_ser + pst_off * G1_SER, G1_SER, nseg, s2);
+                    pst_off += nseg;
+                }
             }
             check(cudaEventRecord(ev_join, s2), "event");
 
@@ -717,7 +738,7 @@ fp_status vc_verify(const fp_pp* pp, const uint8_t* C, uint32_t b, uint64_t i, c
 
 fp_status vc_verify_all(const fp_pp* pp, const uint8_t* C, const uint64_t* m, int on_device, const fp_proofs* pf,
                         int flags, void* stream, uint8_t* ok, uint64_t* n_ok) {
-    if (!pp || !C || !m || !pf || pf->pp != pp || (flags & ~1)) return FP_EINVAL;
+    if (!pp || !C || !m || !pf || pf->pp != pp || (flags & ~1) || !pf->step2 || pf->nopen != pf->L.K) return FP_EINVAL;
     cudaStream_t s = (cudaStream_t)stream;
     return guarded([&]() -> fp_status {
         const ProofLayout& L = pf->L;
@@ -755,6 +776,95 @@ fp_status vc_verify_all(const fp_pp* pp, const uint8_t* C, const uint64_t* m, in
     });
 }
 
+fp_status vc_open_segments(const fp_pp* pp, const fp_commit* cm, uint32_t b, uint32_t k0, uint32_t nblocks,
+                           void* stream, fp_proofs** out) {
+    if (!pp || !cm || !out || cm->pp != pp) return FP_EINVAL;
+    if (b < 1 || b > pp->R) return FP_EINVAL;
+    const uint32_t K = (pp->R + b - 1) / b;
+    if (k0 >= K) return FP_EINVAL;
+    if (nblocks == 0) nblocks = K - k0;
+    if (nblocks > K - k0) return FP_EINVAL;
+    return guarded([&]() -> fp_status {
+        *out = prove_impl(pp, cm, b, k0, nblocks, (cudaStream_t)stream, true, false);
+        return FP_OK;
+    });
+}
+
+size_t vc_segment_proof_len(const fp_pp* pp, uint32_t b, uint32_t j) {
+    if (!pp || b < 1 || b > pp->R || j >= pp->R) return 0;
+    const uint32_t lo = (j / b) * b, nk = std::min(b, pp->R - lo);
+    return (size_t)nk * G1_SER + bopen_len(pp->log_r);
+}
+
+fp_status vc_segment_proof_get(const fp_proofs* pf, uint32_t j, uint8_t* out, size_t cap, size_t* len) {
+    if (!pf || !len) return FP_EINVAL;
+    const ProofLayout& L = pf->L;
+    if (j >= L.R) return FP_EINVAL;
+    const uint32_t k = j / L.b, lo = k * L.b, nk = std::min(L.b, L.R - lo);
+    if (k < pf->k0 || k >= pf->k0 + pf->nopen) return FP_EINVAL;
+    const size_t need = (size_t)nk * G1_SER + L.bopen_len;
+    *len = need;
+    if (!out) return FP_OK;
+    if (cap < need) return FP_EINVAL;
+    return guarded([&]() -> fp_status {
+        cudaStream_t s = pf->stream;
+        check(cudaMemcpyAsync(out, (const uint8_t*)pf->rows_ser + (size_t)lo * G1_SER, (size_t)nk * G1_SER,
+                              cudaMemcpyDeviceToHost, s), "D2H block");
+        check(cudaMemcpyAsync(out + (size_t)nk * G1_SER, (const uint8_t*)pf->blocks + (size_t)k * L.bopen_len,
+                              L.bopen_len, cudaMemcpyDeviceToHost, s), "D2H pi_Ck");
+        check(cudaStreamSynchronize(s), "vc_segment_proof_get");
+        return FP_OK;
+    });
+}
+
+fp_status vc_verify_segment(const fp_pp* pp, const uint8_t* C, uint32_t b, uint32_t j, const uint64_t* m_j,
+                            const uint8_t* proof, size_t len, void* stream) {
+    if (!pp || !C || !m_j || !proof) return FP_EINVAL;
+    if (b < 1 || b > pp->R || j >= pp->R) return FP_EINVAL;
+    if (len != vc_segment_proof_len(pp, b, j)) return FP_EVERIFY;
+    cudaStream_t s = (cudaStream_t)stream;
+    return guarded([&]() -> fp_status {
+        const uint32_t M = pp->M, k = j / b, lo = k * b, nk = std::min(b, pp->R - lo);
+        const int lr = (int)pp->log_r;
+        const MsmShape sh = msm_shape(M, 1, M, fp_msm_window(M, 1));
+        // proof | C | m_j, one host-to-device copy
+        const size_t mbytes = (size_t)M * 32;
+        std::vector<uint8_t> host(len + GT_SER + mbytes);
+        memcpy(host.data(), proof, len);
+        memcpy(host.data() + len, C, GT_SER);
+        memcpy(host.data() + len + GT_SER, m_j, mbytes);
+        void *dbuf = nullptr, *vscr = nullptr, *mscr = nullptr, *mc = nullptr, *mm = nullptr, *cj = nullptr,
+             *out = nullptr;
+        uint32_t hout[2 + 24] = {};
+        try {
+            dbuf = dalloc(host.size(), s);
+            vscr = dalloc(verify_block_scratch_bytes(b, lr), s);
+            mscr = dalloc(msm_scratch_bytes(sh), s);
+            mc = dalloc(mbytes, s);
+            mm = dalloc(mbytes, s);
+            cj = dalloc(G1A_BYTES, s);
+            out = dalloc(sizeof hout, s);         // [block result, range error, C_j serialised (96 B)]
+            check(cudaMemsetAsync(out, 0, sizeof hout, s), "memset");
+            check(cudaMemcpyAsync(dbuf, host.data(), host.size(), cudaMemcpyHostToDevice, s), "H2D");
+            const uint8_t* d = (const uint8_t*)dbuf;
+            uint32_t* o = (uint32_t*)out;
+            load_vector(d + len + GT_SER, M, mc, mm, o + 1, s);
+            msm_g1(pp->lam_tab, mc, sh, mscr, cj, o + 2, s);       // C_j from m_j (VC.Commit's row MSM)
+            verify_block(d, d + (size_t)nk * G1_SER, d + len, nk, lr, b, k, lo, pp->g1beta, vscr, o, s);
+            check_launch("vc_verify_segment kernels");
+            check(cudaMemcpyAsync(hout, out, sizeof hout, cudaMemcpyDeviceToHost, s), "D2H");
+            dfree(dbuf, s); dfree(vscr, s); dfree(mscr, s); dfree(mc, s); dfree(mm, s); dfree(cj, s); dfree(out, s);
+            check(cudaStreamSynchronize(s), "vc_verify_segment");
+        } catch (...) {
+            cudaStreamSynchronize(s);
+            dfree(dbuf, s); dfree(vscr, s); dfree(mscr, s); dfree(mc, s); dfree(mm, s); dfree(cj, s); dfree(out, s);
+            throw;
+        }
+        const bool same = memcmp(hout + 2, proof + (size_t)(j - lo) * G1_SER, G1_SER) == 0;
+        return (hout[0] == 0 && hout[1] == 0 && same) ? FP_OK : FP_EVERIFY;
+    });
+}
+
 fp_status vc_prove_one(const fp_pp* pp, const fp_commit* cm, uint32_t b, uint64_t i, void* stream, uint8_t* out,
                        size_t cap, size_t* len) {
     if (!pp || !cm || !len || cm->pp != pp) return FP_EINVAL;
@@ -780,10 +890,12 @@ size_t vc_proof_len(const fp_pp* pp, uint32_t b, uint64_t i) {
 }
 
 fp_status vc_proofs_export(const fp_proofs* pf, uint64_t i0, uint64_t count, uint8_t* out, size_t cap, size_t* len) {
-    if (!pf || !len) return FP_EINVAL;
+    if (!pf || !len || !pf->step2) return FP_EINVAL;
     const ProofLayout& L = pf->L;
     const uint64_t N = (uint64_t)L.R * L.M;
     if (count == 0 || i0 >= N || count > N - i0) return FP_EINVAL;
+    const uint64_t ka = (i0 / L.M) / L.b, kb = ((i0 + count - 1) / L.M) / L.b;
+    if (ka < pf->k0 || kb >= (uint64_t)pf->k0 + pf->nopen) return FP_EINVAL;
     size_t total = 0;
     for (uint64_t q = 0; q < count; q++) total += proof_len(L, i0 + q);
     *len = total;
@@ -807,7 +919,7 @@ fp_status vc_proof_get(const fp_proofs* pf, uint64_t i, uint8_t* out, size_t cap
 }
 
 fp_status vc_proofs_state(const fp_proofs* pf, uint8_t* out, size_t cap, size_t* len) {
-    if (!pf || !len) return FP_EINVAL;
+    if (!pf || !len || !pf->step2) return FP_EINVAL;
     const ProofLayout& L = pf->L;
     const size_t parts[6] = {(size_t)L.K * L.bopen_len, (size_t)L.R * (2 * L.M - 1) * DIGEST,
                              (2 * (size_t)L.R - 1) * DIGEST, (2 * (size_t)L.R - 1) * G1_SER,
@@ -831,7 +943,7 @@ fp_status vc_proofs_state(const fp_proofs* pf, uint8_t* out, size_t cap, size_t*
 }
 
 fp_status vc_proofs_step2_parts(const fp_proofs* pf, uint8_t* root, uint8_t* rj, uint8_t* gstar, uint8_t* dstar) {
-    if (!pf) return FP_EINVAL;
+    if (!pf || !pf->step2) return FP_EINVAL;
     const ProofLayout& L = pf->L;
     return guarded([&]() -> fp_status {
         cudaStream_t s = pf->stream;

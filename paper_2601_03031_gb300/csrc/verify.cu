@@ -679,6 +679,38 @@ size_t verify_scratch_bytes(uint32_t b, int lr, int lc) {
     return ar.n + 256;
 }
 
+// FC.BVerify of one block on its own (the segment verifier of OpenAll for sub-arrays): result
+// word 0 = 0 if the block check accepts
+namespace {
+template <class A>
+struct BlockOnlyBufs {
+    fq12* Cd; uint32_t* cbad; BlockBufs<A> Bb;
+    BlockOnlyBufs(A& ar, uint32_t b, int lr)
+        : Cd((fq12*)ar.take(FQ12_BYTES)), cbad((uint32_t*)ar.take(4)), Bb(ar, 1, b, lr) {}
+};
+}  // namespace
+
+size_t verify_block_scratch_bytes(uint32_t b, int lr) {
+    SizeArena ar;
+    BlockOnlyBufs<SizeArena> O(ar, b, lr);
+    (void)O;
+    return ar.n + 256;
+}
+
+void verify_block(const void* blk, const void* fc, const void* C_be, uint32_t nk, int lr, uint32_t b, uint32_t k,
+                  uint32_t lo, const void* g1beta, void* scratch, uint32_t* result, cudaStream_t s) {
+    const VSrc S{(const uint8_t*)blk, 0, (const uint8_t*)fc, 0, k, 1, b, lo + nk, lr};
+    Arena ar{(uint8_t*)scratch};
+    BlockOnlyBufs<Arena> O(ar, b, lr);
+    FP_KERNEL("k_v_cdec", s, k_v_cdec<<<1, 32, 0, s>>>((const uint8_t*)C_be, O.Cd, O.cbad));
+    block_checks_front(S, (const uint8_t*)C_be, (const g1a*)g1beta, O.Bb, s);
+    FP_KERNEL("k_v_miller", s, k_v_miller<<<3, 128, 0, s>>>(O.Bb.P, O.Bb.Q, O.Bb.ml));
+    FP_KERNEL("k_vb_gt", s, k_vb_gt<<<2 * lr, 128, 0, s>>>(S, O.Bb.st, O.Bb.ge));
+    FP_KERNEL("k_vb_prod", s, k_vb_prod<<<1, 32, 0, s>>>(O.Bb.ml, O.Bb.ge, O.Cd, 1, lr, O.Bb.fe_in, O.Bb.cT));
+    final_exp_group(O.Bb.fe_in, 2, O.Bb.fe_out, nullptr, 1, 0, 0, s);
+    FP_KERNEL("k_vb_check", s, k_vb_check<<<1, 32, 0, s>>>(O.Bb.fe_out, O.Bb.cT, O.cbad, O.Bb.st, 1, result));
+}
+
 // ------------------------------------------------------------------------------ all proofs
 // Merkle root of every proof (from the stored trees) and the range check of its claimed m_i
 // (N x 4 little-endian u64)
