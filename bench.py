@@ -132,6 +132,7 @@ def parse():
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-sweeps", action="store_true", help="skip the N=2^20 b sweep and the MSM sweep")
+    ap.add_argument("--fc-only", action="store_true", help="only the FC microbenchmark (one JSON line)")
     ap.add_argument("--msm-sweep", default="12,14,16,18,20,22,24", help="log2 sizes of the MSM sweep")
     ap.add_argument("--b-sweep", default="1,16,256,1024", help="b values of the N=2^20 ProveAll sweep")
     ap.add_argument("--served-requests", type=int, default=100, help="requests of the served trace replayed")
@@ -199,6 +200,88 @@ def verify_sweep(F, I, torch, np, cases, seed: int) -> dict:
         s = sorted(ts)[1]
         out[f"n2^{log_n}_b={b}"] = {"proofs_per_s": pp.N / s, "ms": s * 1e3, "accepted": n, "N": pp.N}
         del pf, cm, pp
+    return out
+
+
+def fc_microbench(F, I, torch, np, seed: int) -> dict:
+    """The FC scheme alone (Table tb:fc and the batch-opening/verification figures), as OpenAll for
+    sub-arrays on a split with R = n segments of M = 2 elements: FC.Commit = VC.Commit (two-term
+    row MSMs, then the n-pair FC commitment), FC.BOpen-t = Step 1 on one block of t segments,
+    t x FC.BOpen-1 = t blocks of one segment (one batched call, and t single calls), FC.BVerify-t =
+    the segment verifier on a block of t.  Device time (CUDA events) for Commit and BOpen, host
+    wall time for the synchronous verifier; median of 3 after one warm-up."""
+    s = torch.cuda.Stream()
+
+    def dev_ms(fn):
+        fn()
+        torch.cuda.synchronize()
+        ts = []
+        for _ in range(3):
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(s)
+            fn()
+            b.record(s)
+            b.synchronize()
+            ts.append(a.elapsed_time(b))
+        return sorted(ts)[1]
+
+    def wall_ms(fn):
+        fn()
+        ts = []
+        for _ in range(3):
+            t0 = time.perf_counter()
+            fn()
+            ts.append((time.perf_counter() - t0) * 1e3)
+        return sorted(ts)[1]
+
+    out = {"table": {}, "batch_open_n2^12": {}}
+    for log_r in (8, 9, 10, 11, 12):
+        pp = F.PP(log_r + 1, 1, seed, s, log_r=log_r)
+        m = I.vector(seed + 1, log_r + 1)
+        m_dev = torch.from_numpy(m.view(np.int64).copy()).cuda()
+        keep = []
+
+        def commit():
+            keep.append(F.Commitment(pp, m_dev, s))
+            if len(keep) > 2:
+                keep.pop(0)
+        row = {"commit_ms": dev_ms(commit)}
+        cm = F.Commitment(pp, m_dev, s)
+        C, _ = cm.get(rows=False)
+        for t in (1, 32):
+            hold = []
+
+            def bopen():
+                hold.append(F.vc_open_segments(pp, cm, t, 0, 1, s))
+                if len(hold) > 2:
+                    hold.pop(0)
+            row[f"bopen_t{t}_ms"] = dev_ms(bopen)
+            seg = F.vc_open_segments(pp, cm, t, 0, 1, s)
+            proof = seg.segment_proof(0)
+            assert F.vc_verify_segment(pp, C, t, 0, m[0:2], proof, s)
+            row[f"bverify_t{t}_ms"] = wall_ms(lambda: F.vc_verify_segment(pp, C, t, 0, m[0:2], proof, s))
+        row["pi_y_bytes"] = 1344 * log_r + 480
+        out["table"][f"n=2^{log_r}"] = row
+        if log_r == 12:
+            one = row["bopen_t1_ms"]
+            for t in (16, 32, 64, 128, 256, 512):
+                hold = []
+
+                def batch_t():
+                    hold.append(F.vc_open_segments(pp, cm, t, 0, 1, s))
+                    if len(hold) > 2:
+                        hold.pop(0)
+
+                def t_single():
+                    hold.append(F.vc_open_segments(pp, cm, 1, 0, t, s))
+                    if len(hold) > 2:
+                        hold.pop(0)
+                out["batch_open_n2^12"][f"t={t}"] = {
+                    "bopen_t_ms": dev_ms(batch_t),
+                    "t_x_bopen1_one_call_ms": dev_ms(t_single),
+                    "t_x_bopen1_sequential_ms": t * one,
+                }
+        del cm, pp
     return out
 
 
@@ -417,6 +500,11 @@ def main():
     from paper_2601_03031_gb300 import _lib as F
     from paper_2601_03031_gb300 import inputs as I
 
+    if args.fc_only:
+        res = fc_microbench(F, I, torch, np, args.seed)
+        if rank == 0:
+            print(json.dumps({"metric": "FC.BOpen ms (Table tb:fc)", "n_gpus": world, "fc_microbench": res}))
+        return
     if args.msm_only:
         stream = torch.cuda.current_stream()
         flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
@@ -538,6 +626,7 @@ def main():
             "msm_g1": msm_sweep(F, I, torch, np, stream, flush,
                                 [int(x) for x in args.msm_sweep.split(",") if x], args.seed),
             "verify_all": verify_sweep(F, I, torch, np, [(16, 256), (20, 1), (20, 1024)], args.seed),
+            "fc_microbench": fc_microbench(F, I, torch, np, args.seed),
             "batched_64_jobs": batched_workload(F, I, torch, np),
             "served": served_workload(F, I, torch, np, args.served_requests),
         }

@@ -477,9 +477,10 @@ fp_proofs* prove_impl(const fp_pp* pp, const fp_commit* cm, uint32_t b, uint32_t
             void* sp2 = T((KR / 2 + 1) * G1J_BYTES);
             void* pcoef = T((size_t)Kc * (2 * R - 1) * FR_BYTES);
             void* q = T((size_t)Kc * 2 * R * FR_BYTES);
-            // W proofs: one batched G2 MSM over the shared bases g2^{beta^i} when there are many
-            // terms, else one scalar multiplication per term and pairwise sums (latency)
-            const bool w_msm = (uint64_t)Kc * 2 * R > 4096;
+            // W proofs: one batched G2 MSM over the shared bases g2^{beta^i} when many blocks share
+            // them, else one scalar multiplication per term and pairwise sums (with few batches the
+            // MSM's bucket reduction runs nearly serially per window)
+            const bool w_msm = (uint64_t)Kc * 2 * R > 4096 && Kc >= 8;
             void *wt = nullptr, *wt2 = nullptr, *wscr = nullptr;
             MsmShape wsh{};
             if (w_msm) {
