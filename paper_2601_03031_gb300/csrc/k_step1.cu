@@ -362,39 +362,6 @@ __global__ void __launch_bounds__(64) k_fold_g2(g2a* v, const fr* xinv_mont, uin
     v[lo] = g2_affine(s);
 }
 
-// A_l, v_l into the record; z = HFr("FP-z", x_l || v_l);
-// P(X) = prod_{j=1..l} (1 + x_j^{-1} X^{2^{l-j+1}}) expanded densely (degree 2R - 2);
-// q = (P - P(z)) / (X - z) by synthetic division, stored canonical and zero-padded to 2R terms.
-__global__ void k_kzg(const g1a* A, const g2a* v, const uint8_t* xprev, const fr* xinv_all, uint32_t K, uint32_t R,
-                      int log_r, uint8_t* blocks, size_t bopen_len, fr* pcoef, fr* q_canon) {
-    uint64_t k = gtid();
-    if (k >= K) return;
-    uint8_t* tail = blocks + k * bopen_len + (size_t)log_r * ROUND_BYTES;
-    g1a_to_be(tail, A[k * R]);
-    g2a_to_be(tail + G1_SER, v[k * R]);
-    fr z = hash_to_fr("FP-z", 4, xprev + k * 32, 32, tail + G1_SER, G2_SER, nullptr, 0);
-    const uint32_t deg = 2 * R - 2;
-    fr* P = pcoef + k * (deg + 1);
-    for (uint32_t d = 0; d <= deg; d++) fr_zero(P[d]);
-    fr_one(P[0]);
-    uint32_t cur = 0;
-    for (int j = 1; j <= log_r; j++) {
-        uint32_t e = 1u << (log_r - j + 1);
-        fr xi = xinv_all[k * log_r + (j - 1)];
-        for (int d = (int)cur; d >= 0; d--) P[d + e] = fr_add(P[d + e], fr_mul(P[d], xi));
-        cur += e;
-    }
-    fr* q = q_canon + k * (2 * R);
-    fr qi = P[deg];                       // q_{deg-1}
-    q[deg - 1] = fr_from_mont(qi);
-    for (int i = (int)deg - 1; i >= 1; i--) {
-        qi = fr_add(P[i], fr_mul(z, qi));  // q_{i-1} = P_i + z q_i
-        q[i - 1] = fr_from_mont(qi);
-    }
-    fr_zero(q[deg]);
-    fr_zero(q[deg + 1]);
-}
-
 // W = sum_i q_i g2^{beta^i}: one term per (k, i < 2R), padding terms are zero
 __global__ void __launch_bounds__(64) k_w_terms(const g2a* g2pow, const fr* q_canon, uint32_t K, uint32_t R, g2j* out) {
     uint64_t t = gtid();
@@ -435,17 +402,19 @@ __global__ void __launch_bounds__(128) k_w_terms_w(const g2a* g2pow, const fr* q
     }
 }
 
-// The fast-verification proof's quotient for one block per CTA (parallel form of k_kzg):
+// The fast-verification proof of v_l, one block per CTA: A_l and v_l go into the block's record,
+// z = HFr("FP-z", x_l || v_l), and the quotient coefficients, stored canonical and zero-padded to 2R:
 //   P(X) = prod_j (1 + x_j^-1 X^(2^(l - j + 1))): the coefficient of X^m (m even) is the product of
 //   x_j^-1 over the bits l - j + 1 set in m, and 0 for odd m;
 //   q = (P(X) - P(z)) / (X - z): q_(i-1) = sum_{m >= i} P_m z^(m - i), by chunks of C indices: each
 //   thread runs its chunk's recurrence with a zero carry, one thread chains the chunk carries
 //   (carry of the chunk below = local top + z^len carry), then each chunk adds z^(hi - i) carry.
-constexpr int KZG_THREADS = 128, KZG_CHUNK = 32;
+constexpr int KZG_THREADS = 128, KZG_CHUNK_MAX = 128;   // chunk length C <= KZG_CHUNK_MAX, one chunk per thread
 __global__ void __launch_bounds__(KZG_THREADS) k_kzg_p(const g1a* A, const g2a* v, const uint8_t* xprev,
                                                        const fr* xinv_all, uint32_t K, uint32_t R, int log_r,
-                                                       uint8_t* blocks, size_t bopen_len, fr* pcoef, fr* q_canon) {
-    __shared__ fr zpow[KZG_CHUNK + 1];
+                                                       uint8_t* blocks, size_t bopen_len, fr* pcoef, fr* q_canon,
+                                                       uint32_t C) {
+    __shared__ fr zpow[KZG_CHUNK_MAX + 1];
     __shared__ fr carry[KZG_THREADS];
     const uint32_t k = blockIdx.x;
     const int T = threadIdx.x;
@@ -458,7 +427,7 @@ __global__ void __launch_bounds__(KZG_THREADS) k_kzg_p(const g1a* A, const g2a* 
         g2a_to_be(tail + G1_SER, v[(size_t)k * R]);
         const fr z = hash_to_fr("FP-z", 4, xprev + k * 32, 32, tail + G1_SER, G2_SER, nullptr, 0);
         fr_one(zpow[0]);
-        for (int c = 1; c <= KZG_CHUNK; c++) zpow[c] = fr_mul(zpow[c - 1], z);
+        for (uint32_t c = 1; c <= C; c++) zpow[c] = fr_mul(zpow[c - 1], z);
     }
     for (uint32_t m = T; m <= deg; m += KZG_THREADS) {
         fr c;
@@ -473,9 +442,9 @@ __global__ void __launch_bounds__(KZG_THREADS) k_kzg_p(const g1a* A, const g2a* 
     }
     __syncthreads();
     // indices i = 1 .. deg produce q_(i-1); chunk c covers i in [1 + c C, min(1 + (c + 1) C, deg + 1))
-    const uint32_t nchunks = (deg + KZG_CHUNK - 1) / KZG_CHUNK;
+    const uint32_t nchunks = (deg + C - 1) / C;
     for (uint32_t c = T; c < nchunks; c += KZG_THREADS) {
-        const uint32_t lo = 1 + c * KZG_CHUNK, hi = min(lo + KZG_CHUNK, deg + 1);
+        const uint32_t lo = 1 + c * C, hi = min(lo + C, deg + 1);
         fr acc;
         fr_zero(acc);
         for (uint32_t i = hi - 1; i >= lo; i--) {
@@ -491,7 +460,7 @@ __global__ void __launch_bounds__(KZG_THREADS) k_kzg_p(const g1a* A, const g2a* 
         fr above;
         fr_zero(above);
         for (int c = (int)nchunks - 1; c >= 0; c--) {
-            const uint32_t lo = 1 + c * KZG_CHUNK, hi = min(lo + KZG_CHUNK, deg + 1);
+            const uint32_t lo = 1 + c * C, hi = min(lo + C, deg + 1);
             const fr local = carry[c];
             carry[c] = above;
             above = fr_add(local, fr_mul(zpow[hi - lo], above));
@@ -499,7 +468,7 @@ __global__ void __launch_bounds__(KZG_THREADS) k_kzg_p(const g1a* A, const g2a* 
     }
     __syncthreads();
     for (uint32_t c = T; c < nchunks; c += KZG_THREADS) {
-        const uint32_t lo = 1 + c * KZG_CHUNK, hi = min(lo + KZG_CHUNK, deg + 1);
+        const uint32_t lo = 1 + c * C, hi = min(lo + C, deg + 1);
         const fr cin = carry[c];
         for (uint32_t i = lo; i < hi; i++) q[i - 1] = fr_from_mont(fr_add(q[i - 1], fr_mul(zpow[hi - i], cin)));
     }
@@ -569,15 +538,13 @@ void step1_fold_g2(void* v, const void* xinv_mont, uint32_t K, uint32_t R, uint3
 }
 void step1_kzg(const void* A, const void* v, const void* xprev, const void* xinv_all, uint32_t K, uint32_t R,
                int log_r, void* blocks, size_t bopen_len, void* pcoef, void* q_canon, cudaStream_t s) {
-    if ((2 * R - 2 + KZG_CHUNK - 1) / KZG_CHUNK > KZG_THREADS) {       // more chunks than one CTA chains
-        FP_KERNEL("k_kzg", s, k_kzg<<<grid_for(K, 32), 32, 0, s>>>((const g1a*)A, (const g2a*)v, (const uint8_t*)xprev,
-                                             (const fr*)xinv_all, K, R, log_r, (uint8_t*)blocks, bopen_len,
-                                             (fr*)pcoef, (fr*)q_canon));
-        return;
-    }
+    // chunks of C >= 32 coefficients, at most one per thread: C <= KZG_CHUNK_MAX for 2R - 2 <= 2^14
+    const uint32_t deg = 2 * R - 2;
+    uint32_t C = (deg + KZG_THREADS - 1) / KZG_THREADS;
+    if (C < 32) C = 32;
     FP_KERNEL("k_kzg_p", s, k_kzg_p<<<K, KZG_THREADS, 0, s>>>((const g1a*)A, (const g2a*)v, (const uint8_t*)xprev,
                                                              (const fr*)xinv_all, K, R, log_r, (uint8_t*)blocks,
-                                                             bopen_len, (fr*)pcoef, (fr*)q_canon));
+                                                             bopen_len, (fr*)pcoef, (fr*)q_canon, C));
 }
 void step1_w_terms(const void* g2pow, const void* q_canon, uint32_t K, uint32_t R, void* out, cudaStream_t s) {
     const uint64_t n = (uint64_t)K * 2 * R;

@@ -113,3 +113,20 @@ def test_full_openall_on_other_splits(log_r, log_c, b):
     assert pf.export(0, pp.N) == b"".join(pr.proof(i) for i in range(pp.N))
     ok, n = F.vc_verify_all(pf, C, m)
     assert n == pp.N and ok.all()
+
+
+def test_fc_opening_at_4096_rows():
+    """R = 4096 (FC length of the microbenchmark's largest n): the quotient of the fast-verification
+    proof runs in chunks longer than the default; both verifiers accept the first and last segments."""
+    log_r, log_c, b, seed = 12, 1, 1, 61
+    pp = F.PP(log_r + log_c, 1, seed, log_r=log_r)
+    opp = O.PP(log_r + log_c, seed, log_r=log_r)
+    m = I.vector(seed + 1, log_r + log_c)
+    cm = F.Commitment(pp, m)
+    C, rows = cm.get()
+    assert (C, rows) == O.commit(opp, m.tobytes())
+    for j in (0, pp.R - 1):
+        p = F.vc_open_segments(pp, cm, b, j // b, 1).segment_proof(j)
+        mj = m[2 * j:2 * j + 2]
+        assert F.vc_verify_segment(pp, C, b, j, mj, p)
+        assert O.verify_segment(opp, C, b, j, mj.tobytes(), p)
