@@ -40,6 +40,30 @@ FQ_MULS = {
 }
 
 
+def _cyc_exp_rounds(e: int) -> int:
+    """Product rounds of a square-and-multiply exponentiation by e (squarings + multiplications)."""
+    return (e.bit_length() - 1) + (bin(e).count("1") - 1)
+
+
+X_ABS = 0xd201000000010000                   # |x| of BLS12-381 (x < 0)
+H1 = (X_ABS + 1) ** 2 // 3                   # h1 = (x - 1)^2 / 3
+# Sequential Fq-product rounds on one launch's critical path in the lane-parallel engines: every
+# round waits for one dependent Montgomery product, so rounds x the measured product latency is a
+# lower bound on the launch time (the linear combinations between rounds and the one-lane
+# binary-gcd inversions are left out, so the bound is optimistic).
+CRITICAL_ROUNDS = {
+    # easy part 8 rounds (n, two Frobenius^2, u, n u, c^2, c^2 u, t) + 5 products of the Fq2 inverse,
+    # g 2, hard part h1 and 3 |x| cyclotomic exponentiations + 6 Frobenius / product rounds
+    "k_final_exp_c": 8 + 5 + 2 + _cyc_exp_rounds(H1) + 3 * _cyc_exp_rounds(X_ABS) + 6,
+    # 63 doubling steps of 3 rounds, 5 addition steps of 4
+    "k_round_miller_c": 63 * 3 + 5 * 4,
+    # G1 by 8-lane groups, 2-bit joint GLV windows: 13 table formulas + 64 x (2 doublings + 1 addition),
+    # 2 phases each, then the addition of A_L and the conversion (longer than the warp G2 chain)
+    "k_fold_w": (13 + 64 * 3) * 2 + 2 + 3,
+    "k_sparse_g": (13 + 64 * 3) * 2 + 2,
+}
+
+
 def step_units(log_n: int, b: int, msm_window: int) -> dict:
     """Per kernel: (unit, units processed per step) for one Commit + OpenAll step."""
     lr = log_n // 2
@@ -606,6 +630,16 @@ def main():
                 "units_per_step": n_units, "unit_op": unit, "launches_per_step": launches_per_step,
                 "avg_launch_ms": avg_ms,
                 "peak_source": "measured: fp_imad_probe on this GPU in this run"}
+    lat = None
+    if name in CRITICAL_ROUNDS and kms > 0:
+        t_ns = F.fq_mul_latency_ns()
+        rounds = CRITICAL_ROUNDS[name]
+        avg_ms = kms / cnt
+        bound_ms = rounds * t_ns * 1e-6
+        lat = {"kernel": name, "critical_rounds": rounds, "fq_mul_ns": t_ns, "bound_ms": bound_ms,
+               "achieved_ms": avg_ms, "frac": bound_ms / avg_ms,
+               "note": "sequential Fq-product rounds on the launch's critical path x measured latency of "
+                       "one dependent product (fp_fq_mul_latency); combines and inversions excluded"}
     share = {k: round(v[1] / (total_ms if total_ms else 1), 4) for k, v in
              sorted(prof.items(), key=lambda kv: -kv[1][1])[:8]}
 
@@ -645,6 +679,7 @@ def main():
                    "note": "value counts Commit + OpenAll per step; OpenAll alone is the paper's ProveAll time"},
         "gpu_launches": launches,
         "roofline": roof,
+        "latency_roofline": lat,
         "kernel_share": share,
         "clocks": clk.summary(),
         "cpu_baseline": cpu,

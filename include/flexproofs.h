@@ -273,6 +273,11 @@ size_t fp_profile_report(char* out, size_t cap);
  * fp_status code. */
 int fp_imad_probe(double* ops_per_s, double* ms);
 
+/* Measured latency of one Fq Montgomery product on one lane (a chain of dependent products on the
+ * current device, CUDA-event timed), in ns: the unit of the latency bound of the lane-parallel
+ * engines, whose every round waits for one product.  Returns a fp_status code. */
+int fp_fq_mul_latency(double* ns_per_product);
+
 const char* fp_strerror(fp_status s);
 /* Text of the last CUDA error seen by this thread's calls (empty if none). */
 const char* fp_last_error(void);

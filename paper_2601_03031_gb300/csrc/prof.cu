@@ -10,6 +10,7 @@
 #include <vector>
 
 #include "../../include/flexproofs.h"
+#include "fp.cuh"
 #include "kernels.h"
 
 namespace fpk {
@@ -127,5 +128,35 @@ extern "C" int fp_imad_probe(double* ops_per_s, double* ms_out) {
     if (e != cudaSuccess) return 3;
     *ops_per_s = (double)blocks * threads * iters * 8 / (ms * 1e-3);
     if (ms_out) *ms_out = ms;
+    return 0;
+}
+
+// one lane, n dependent Montgomery products in Fq: the latency that bounds the lane-parallel engines
+// (every round of a Miller step, cyclotomic squaring or group formula waits for one such product)
+__global__ void k_fq_mul_chain(uint32_t n, uint32_t* sink) {
+    if (threadIdx.x != 0) return;
+    fq a, b;
+    fq_from_const(a, FQ_R2);
+    fq_from_const(b, FQ_R3);
+    for (uint32_t i = 0; i < n; i++) a = fq_mul(a, b);
+    if (a.v[0] == 0x12345678u) sink[0] = a.v[1];
+}
+
+extern "C" int fp_fq_mul_latency(double* ns_per_product) {
+    uint32_t* sink = nullptr;
+    if (cudaMalloc(&sink, 4) != cudaSuccess) return 2;
+    const uint32_t n = 4096;
+    cudaEvent_t a, b;
+    cudaEventCreate(&a); cudaEventCreate(&b);
+    k_fq_mul_chain<<<1, 32>>>(64, sink);                 // warm-up
+    cudaEventRecord(a);
+    k_fq_mul_chain<<<1, 32>>>(n, sink);
+    cudaEventRecord(b);
+    cudaError_t e = cudaEventSynchronize(b);
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, a, b);
+    cudaEventDestroy(a); cudaEventDestroy(b); cudaFree(sink);
+    if (e != cudaSuccess) return 3;
+    *ns_per_product = (double)ms * 1e6 / n;
     return 0;
 }
