@@ -57,6 +57,10 @@ def lib():
             L.or_segment_proof_len.restype = ctypes.c_size_t
             L.or_segment_proof_len.argtypes = [vp, ctypes.c_uint32, ctypes.c_uint32]
             L.or_verify_segment.argtypes = [vp, vp, ctypes.c_uint32, ctypes.c_uint32, vp, vp, ctypes.c_size_t]
+            L.or_eval_proof_len.restype = ctypes.c_size_t
+            L.or_eval_proof_len.argtypes = [vp]
+            L.or_eval_prove.argtypes = [vp, vp, vp, vp, vp, vp]
+            L.or_eval_verify.argtypes = [vp, vp, vp, vp, ctypes.c_size_t]
             L.or_pp_free.argtypes = [vp]
             L.or_pp_bytes.restype = ctypes.c_size_t
             L.or_pp_bytes.argtypes = [vp, vp]
@@ -373,6 +377,23 @@ def verify_segment(pp: PP, C: bytes, b: int, j: int, m_j_limbs: bytes, proof: by
     """Verifier V_j of OpenAll for sub-arrays: C_j recomputed from m_j (M x 4 little-endian u64)
     must be the block's entry j, and FC.BVerify of the block must accept."""
     return bool(lib().or_verify_segment(pp.h, C, b, j, m_j_limbs, proof, len(proof)))
+
+
+def _point_bytes(pp: PP, r) -> bytes:
+    assert len(r) == pp.log_n
+    return b"".join(int(v).to_bytes(32, "big") for v in r)
+
+
+def eval_prove(pp: PP, m_limbs: bytes, C: bytes, rows: bytes, r) -> bytes:
+    """Evaluation proof of the committed vector's multilinear extension at r = (r_0 .. r_{log N - 1})
+    (Sec. 4.4): y || C_F || pi_FC || pi_PST."""
+    o = _buf(lib().or_eval_proof_len(pp.h))
+    _call(lib().or_eval_prove, pp.h, m_limbs, C, rows, _point_bytes(pp, r), o)
+    return o.raw
+
+
+def eval_verify(pp: PP, C: bytes, r, proof: bytes) -> bool:
+    return bool(lib().or_eval_verify(pp.h, C, _point_bytes(pp, r), proof, len(proof)))
 
 
 def verify_many(pp: PP, C: bytes, b: int, items, threads: int | None = None) -> list[bool]:

@@ -229,21 +229,10 @@ static void block_challenges(fe* r_out, const u8* C, const u8* rows, u32 R, u32 
     *nk_out = nk;
 }
 
-int or_bopen(const or_pp* pp, const u8* C_bytes, const u8* rows_bytes, u32 b, u32 k, u8* out, int check_invariant) {
+/* FC.BOpen rounds, y's opening and the faster-verification proof for the combined vector bv (R
+ * entries) over A = the row commitments, v_i = g2^{beta^{2i}}; A, v, bv are consumed. */
+static int fc_bopen_core(const or_pp* pp, const u8* C_bytes, g1* A, g2* v, fe* bv, u8* out, int check_invariant) {
     const u32 R = pp->R; const int lr = pp->log_r;
-    if (b < 1 || b > R || k * b >= R) return -1;
-    g1* A = (g1*)malloc(R * sizeof(g1));
-    g2* v = (g2*)malloc(R * sizeof(g2));
-    fe* bv = (fe*)calloc(R, sizeof(fe));
-    fe* rr = (fe*)malloc(b * sizeof(fe));
-    for (u32 i = 0; i < R; i++) {
-        if (g1_from_bytes(&A[i], rows_bytes + 96 * (size_t)i)) { free(A); free(v); free(bv); free(rr); return -2; }
-        v[i] = pp->g2pow[2 * i];
-    }
-    u32 nk;
-    block_challenges(rr, C_bytes, rows_bytes, R, b, k, &nk);
-    for (u32 a = 0; a < nk; a++) bv[k * b + a] = rr[a];
-
     /* invariant state: C_0 = (C, y) with y = <A, b> */
     fq12 invT; g1 inv1;
     if (check_invariant) {
@@ -327,8 +316,27 @@ int or_bopen(const or_pp* pp, const u8* C_bytes, const u8* rows_bytes, u32 b, u3
     for (u32 i = 0; i < deg; i++) { g2 t; g2_mul(&t, &pp->g2pow[i], &q[i]); g2_add(&W, &W, &t); }
     g2_to_bytes(o, &W); o += 192;
     (void)xs;
-    free(P); free(q); free(A); free(v); free(bv); free(rr);
+    free(P); free(q);
     return bad ? 1 : 0;
+}
+
+int or_bopen(const or_pp* pp, const u8* C_bytes, const u8* rows_bytes, u32 b, u32 k, u8* out, int check_invariant) {
+    const u32 R = pp->R;
+    if (b < 1 || b > R || k * b >= R) return -1;
+    g1* A = (g1*)malloc(R * sizeof(g1));
+    g2* v = (g2*)malloc(R * sizeof(g2));
+    fe* bv = (fe*)calloc(R, sizeof(fe));
+    fe* rr = (fe*)malloc(b * sizeof(fe));
+    for (u32 i = 0; i < R; i++) {
+        if (g1_from_bytes(&A[i], rows_bytes + 96 * (size_t)i)) { free(A); free(v); free(bv); free(rr); return -2; }
+        v[i] = pp->g2pow[2 * i];
+    }
+    u32 nk;
+    block_challenges(rr, C_bytes, rows_bytes, R, b, k, &nk);
+    for (u32 a = 0; a < nk; a++) bv[k * b + a] = rr[a];
+    int rc = fc_bopen_core(pp, C_bytes, A, v, bv, out, check_invariant);
+    free(A); free(v); free(bv); free(rr);
+    return rc;
 }
 
 /* ------------------------------------------------------------------------------
@@ -585,12 +593,71 @@ int or_prove_one(const or_pp* pp, const u64* m, const u8* C, const u8* rows, u32
     return 0;
 }
 
+/* FC.BVerify checks after C_0 = (C, c1) and the weights rr of positions lo .. lo + n - 1 are known:
+ * the rounds' folds of C_0, b_l from the weights (Eq. b_l), e(A_l, v_l) and b_l A_l against the
+ * folded C_0, and the faster-verification check of v_l.  Returns 1 if accepted. */
+static int fc_bverify_core(const or_pp* pp, const fq12* Cg, g1 c1, const fe* rr, u32 lo, u32 n, const u8* fc) {
+    const int lr = pp->log_r;
+    int ok = 1;
+    fq12 cT = *Cg;
+    u8 xprev[32]; size_t xl = 0;
+    fe xinv[32];
+    for (int jj = 1; jj <= lr; jj++) {
+        const u8* rd = fc + 1344 * (size_t)(jj - 1);
+        fq12 LT, RT; g1 L1, R1;
+        if (fq12_from_bytes(&LT, rd) || g1_from_bytes(&L1, rd + 576) ||
+            fq12_from_bytes(&RT, rd + 672) || g1_from_bytes(&R1, rd + 1248)) { ok = 0; break; }
+        u8 tr[32 + 1344]; memcpy(tr, xprev, xl); memcpy(tr + xl, rd, 1344);
+        fe x; hfr_nonzero(&x, "FP-x", tr, xl + 1344);
+        fe xi; f_inv(&FR, &xi, &x); xinv[jj - 1] = xi;
+        fr_to_bytes(xprev, &x); xl = 32;
+        fq12 t1, t2; fq12_pow_fr(&t1, &LT, &x); fq12_pow_fr(&t2, &RT, &xi);
+        fq12_mul(&cT, &cT, &t1); fq12_mul(&cT, &cT, &t2);      /* L^x o C o R^{1/x} */
+        g1 s1, s2; g1_mul(&s1, &L1, &x); g1_mul(&s2, &R1, &xi);
+        g1_add(&c1, &c1, &s1); g1_add(&c1, &c1, &s2);
+    }
+    if (ok) {
+        const u8* tail = fc + 1344 * (size_t)lr;
+        g1 Al; g2 vl, W;
+        if (g1_from_bytes(&Al, tail) || g2_from_bytes(&vl, tail + 96) || g2_from_bytes(&W, tail + 288)) ok = 0;
+        if (ok) {
+            /* b_l = sum_a r_a prod_k (1/x_k)^{a_{l-k}} (Eq. b_l) */
+            fe bl; f_zero(&bl);
+            for (u32 t = 0; t < n; t++) {
+                u32 aa = lo + t; fe w = rr[t];
+                for (int kk = 1; kk <= lr; kk++) if ((aa >> (lr - kk)) & 1) f_mul(&FR, &w, &w, &xinv[kk - 1]);
+                f_add(&FR, &bl, &bl, &w);
+            }
+            fq12 eAv; pairing(&eAv, &Al, &vl);
+            g1 bA; g1_mul(&bA, &Al, &bl);
+            if (!fq12_eq(&eAv, &cT) || !g1_eq(&bA, &c1)) ok = 0;
+            /* v_l check: e(g1^beta - z g1, W) = e(g1, v_l - P(z) g2) */
+            u8 zb[32 + 192]; memcpy(zb, xprev, 32); memcpy(zb + 32, tail + 96, 192);
+            fe z; hfr(&z, "FP-z", zb, sizeof zb);
+            fe Pz = FR.one, zp = z;                 /* zp runs through z^(2^e) */
+            fe zpow[34]; zpow[0] = z;
+            for (int e = 1; e <= lr + 1; e++) f_mul(&FR, &zpow[e], &zpow[e - 1], &zpow[e - 1]);
+            for (int jj = 1; jj <= lr; jj++) {
+                fe t; f_mul(&FR, &t, &xinv[jj - 1], &zpow[lr - jj + 1]);
+                f_add(&FR, &t, &t, &FR.one);
+                f_mul(&FR, &Pz, &Pz, &t);
+            }
+            (void)zp;
+            g1 lhsP, zg; g1_mul(&zg, &G1_GEN, &z); g1_neg(&zg, &zg); g1_add(&lhsP, &pp->g1beta, &zg);
+            g2 rhsQ, pg; g2_mul(&pg, &G2_GEN, &Pz); g2_neg(&pg, &pg); g2_add(&rhsQ, &vl, &pg);
+            fq12 e1, e2; pairing(&e1, &lhsP, &W); pairing(&e2, &G1_GEN, &rhsQ);
+            if (!fq12_eq(&e1, &e2)) ok = 0;
+        }
+    }
+    return ok;
+}
+
 /* FC.BVerify of block k (Sec. 3, with the b_l shortcut of Sec. 4.3 and the faster-verification
  * check of v_l) for the block's row commitments Ca (decoded from blk) and pi_{C_k} at fc.
  * Returns 1 if accepted.  The memo key covers every input, the split included. */
 static int fc_bverify(const or_pp* pp, const fq12* Cgp, const u8* C, u32 b, u32 k, const u8* blk, const g1* Ca,
                       u32 nk, const u8* fc, int use_memo) {
-    const u32 R = pp->R; const int lr = pp->log_r;
+    const u32 R = pp->R;
     const u32 lo = k * b;
     const fq12 Cg = *Cgp;
     int ok = 1;
@@ -610,57 +677,9 @@ static int fc_bverify(const or_pp* pp, const fq12* Cgp, const u8* C, u32 b, u32 
         block_challenges(rr, C, rows_view, R, b, k, &nk2);
         free(rows_view);
         /* C_0 = (C, y), y = prod_a C_a^{r_a} (Eq. comy) */
-        fq12 cT = Cg; g1 c1; g1_set_inf(&c1);
-        for (u32 t = 0; t < nk; t++) { g1 s; g1_mul(&s, &Ca[t], &rr[t]); g1_add(&c1, &c1, &s); }
-        u8 xprev[32]; size_t xl = 0;
-        fe xinv[32];
-        for (int jj = 1; jj <= lr; jj++) {
-            const u8* rd = fc + 1344 * (size_t)(jj - 1);
-            fq12 LT, RT; g1 L1, R1;
-            if (fq12_from_bytes(&LT, rd) || g1_from_bytes(&L1, rd + 576) ||
-                fq12_from_bytes(&RT, rd + 672) || g1_from_bytes(&R1, rd + 1248)) { ok = 0; break; }
-            u8 tr[32 + 1344]; memcpy(tr, xprev, xl); memcpy(tr + xl, rd, 1344);
-            fe x; hfr_nonzero(&x, "FP-x", tr, xl + 1344);
-            fe xi; f_inv(&FR, &xi, &x); xinv[jj - 1] = xi;
-            fr_to_bytes(xprev, &x); xl = 32;
-            fq12 t1, t2; fq12_pow_fr(&t1, &LT, &x); fq12_pow_fr(&t2, &RT, &xi);
-            fq12_mul(&cT, &cT, &t1); fq12_mul(&cT, &cT, &t2);      /* L^x o C o R^{1/x} */
-            g1 s1, s2; g1_mul(&s1, &L1, &x); g1_mul(&s2, &R1, &xi);
-            g1_add(&c1, &c1, &s1); g1_add(&c1, &c1, &s2);
-        }
-        if (ok) {
-            const u8* tail = fc + 1344 * (size_t)lr;
-            g1 Al; g2 vl, W;
-            if (g1_from_bytes(&Al, tail) || g2_from_bytes(&vl, tail + 96) || g2_from_bytes(&W, tail + 288)) ok = 0;
-            if (ok) {
-                /* b_l = sum_a r_a prod_k (1/x_k)^{a_{l-k}} (Eq. b_l) */
-                fe bl; f_zero(&bl);
-                for (u32 t = 0; t < nk; t++) {
-                    u32 aa = lo + t; fe w = rr[t];
-                    for (int kk = 1; kk <= lr; kk++) if ((aa >> (lr - kk)) & 1) f_mul(&FR, &w, &w, &xinv[kk - 1]);
-                    f_add(&FR, &bl, &bl, &w);
-                }
-                fq12 eAv; pairing(&eAv, &Al, &vl);
-                g1 bA; g1_mul(&bA, &Al, &bl);
-                if (!fq12_eq(&eAv, &cT) || !g1_eq(&bA, &c1)) ok = 0;
-                /* v_l check: e(g1^beta - z g1, W) = e(g1, v_l - P(z) g2) */
-                u8 zb[32 + 192]; memcpy(zb, xprev, 32); memcpy(zb + 32, tail + 96, 192);
-                fe z; hfr(&z, "FP-z", zb, sizeof zb);
-                fe Pz = FR.one, zp = z;                 /* zp runs through z^(2^e) */
-                fe zpow[34]; zpow[0] = z;
-                for (int e = 1; e <= lr + 1; e++) f_mul(&FR, &zpow[e], &zpow[e - 1], &zpow[e - 1]);
-                for (int jj = 1; jj <= lr; jj++) {
-                    fe t; f_mul(&FR, &t, &xinv[jj - 1], &zpow[lr - jj + 1]);
-                    f_add(&FR, &t, &t, &FR.one);
-                    f_mul(&FR, &Pz, &Pz, &t);
-                }
-                (void)zp;
-                g1 lhsP, zg; g1_mul(&zg, &G1_GEN, &z); g1_neg(&zg, &zg); g1_add(&lhsP, &pp->g1beta, &zg);
-                g2 rhsQ, pg; g2_mul(&pg, &G2_GEN, &Pz); g2_neg(&pg, &pg); g2_add(&rhsQ, &vl, &pg);
-                fq12 e1, e2; pairing(&e1, &lhsP, &W); pairing(&e2, &G1_GEN, &rhsQ);
-                if (!fq12_eq(&e1, &e2)) ok = 0;
-            }
-        }
+        g1 c1; g1_set_inf(&c1);
+        for (u32 t = 0; t < nk; t++) { g1 sm; g1_mul(&sm, &Ca[t], &rr[t]); g1_add(&c1, &c1, &sm); }
+        ok = fc_bverify_core(pp, &Cg, c1, rr, lo, nk, fc);
         free(rr);
         if (use_memo) memo_put(bkey, ok);
     }
@@ -771,4 +790,127 @@ int or_verify_segment(const or_pp* pp, const u8* C, u32 b, u32 j, const u64* m_j
     if (ok) ok = fc_bverify(pp, &Cg, C, b, k, proof, Ca, nk, proof + 96 * (size_t)nk, 0);
     free(Ca);
     return ok;
+}
+
+/* ------------------------------------------------------------------------------
+ * Evaluation proof of f_m at a point r (Sec. 4.4, "Compatibility with a family of zkSNARKs"),
+ * r = (r_0 .. r_{log N - 1}) with variable k <-> bit k of i = j M + a, so the column variables
+ * r_R = (r_0 .. r_{l_c - 1}) and the row variables r_L = (r_{l_c} .. r_{log N - 1}):
+ *   T_j = prod_{s < l_R} (j_s r_{l_c + s} + (1 - j_s)(1 - r_{l_c + s}))   (T_{j, log mu}(r_L))
+ *   F = sum_j T_j f_j (a table over the M columns), y = F(r_R) = f_m(r)  (Eq. fANDfj)
+ *   step 1: C_F = prod_j C_j^{T_j};
+ *   step 2: FC.BOpen(C, C, {b^(0) = T}, {y_0 = C_F}) with t = 1: r_0 = HFr("FP-r", SHA256(stmt) ||
+ *           u32be(0)), stmt = "FP-eval" || C || u32be(log N) || r_0 .. r_{log N - 1} || C_F, b = r_0 T;
+ *   step 3: PST.Eval(F, r_R): for t = l_c - 1 .. 0, q_t[c] = F[2^t + c] - F[c] (c < 2^t),
+ *           pi_t = sum_c q_t[c] Lambda_t[c], then F[c] <- F[c] + r_t q_t[c].
+ * Proof: y (32) || C_F (96) || pi_FC (or_bopen_len) || pi_{l_c-1} .. pi_0 (96 each).
+ * The verifier checks FC.BVerify with C_0 = (C, C_F^{r_0}) and weights r_0 T, and
+ * e(C_F - y g1, g2) = prod_t e(pi_t, g2^{tau_t} - r_t g2).
+ * ------------------------------------------------------------------------------ */
+size_t or_eval_proof_len(const or_pp* pp) { return 32 + 96 + or_bopen_len(pp) + 96 * (size_t)pp->log_c; }
+
+static int load_point(fe* r, const or_pp* pp, const u8* r_be) {
+    for (int k = 0; k < pp->log_n; k++)
+        if (f_from_be(&FR, &r[k], r_be + 32 * (size_t)k, 32)) return -1;
+    return 0;
+}
+static void eval_weights(fe* T, const or_pp* pp, const fe* r) {
+    for (u32 j = 0; j < pp->R; j++) {
+        fe acc = FR.one;
+        for (int s = 0; s < pp->log_r; s++) {
+            fe f = r[pp->log_c + s];
+            if (!((j >> s) & 1)) f_sub(&FR, &f, &FR.one, &f);
+            f_mul(&FR, &acc, &acc, &f);
+        }
+        T[j] = acc;
+    }
+}
+static void eval_r0(fe* r0, const or_pp* pp, const u8* C, const u8* r_be, const u8* CF_bytes) {
+    size_t sl = 7 + 576 + 4 + 32 * (size_t)pp->log_n + 96;
+    u8* stmt = (u8*)malloc(sl);
+    size_t o = 0;
+    memcpy(stmt + o, "FP-eval", 7); o += 7;
+    memcpy(stmt + o, C, 576); o += 576;
+    be32(stmt + o, (u32)pp->log_n); o += 4;
+    memcpy(stmt + o, r_be, 32 * (size_t)pp->log_n); o += 32 * (size_t)pp->log_n;
+    memcpy(stmt + o, CF_bytes, 96);
+    u8 buf[36];
+    sha256(buf, stmt, sl);
+    free(stmt);
+    be32(buf + 32, 0);
+    hfr(r0, "FP-r", buf, 36);
+}
+
+int or_eval_prove(const or_pp* pp, const u64* m, const u8* C, const u8* rows_bytes, const u8* r_be, u8* out) {
+    const u32 R = pp->R, M = pp->M; const int lc = pp->log_c;
+    const size_t N = (size_t)R * M;
+    fe r[32];
+    if (load_point(r, pp, r_be)) return -1;
+    fe* mm = (fe*)malloc(N * sizeof(fe));
+    if (load_m(mm, m, N)) { free(mm); return -1; }
+    fe* T = (fe*)malloc(R * sizeof(fe));
+    eval_weights(T, pp, r);
+    fe* F = (fe*)calloc(M, sizeof(fe));
+    for (u32 a = 0; a < M; a++)
+        for (u32 j = 0; j < R; j++) { fe w; f_mul(&FR, &w, &T[j], &mm[(size_t)j * M + a]); f_add(&FR, &F[a], &F[a], &w); }
+    g1* A = (g1*)malloc(R * sizeof(g1));
+    g2* v = (g2*)malloc(R * sizeof(g2));
+    g1 CF; g1_set_inf(&CF);
+    for (u32 j = 0; j < R; j++) {
+        if (g1_from_bytes(&A[j], rows_bytes + 96 * (size_t)j)) { free(mm); free(T); free(F); free(A); free(v); return -2; }
+        v[j] = pp->g2pow[2 * j];
+        g1 t; g1_mul(&t, &A[j], &T[j]); g1_add(&CF, &CF, &t);
+    }
+    u8* o = out + 32;
+    g1_to_bytes(o, &CF); o += 96;
+    fe r0; eval_r0(&r0, pp, C, r_be, out + 32);
+    fe* bv = (fe*)malloc(R * sizeof(fe));
+    for (u32 j = 0; j < R; j++) f_mul(&FR, &bv[j], &r0, &T[j]);
+    fc_bopen_core(pp, C, A, v, bv, o, 0);
+    o += or_bopen_len(pp);
+    for (int t = lc - 1; t >= 0; t--) {
+        const u32 w = 1u << t;
+        g1 acc; g1_set_inf(&acc);
+        for (u32 c = 0; c < w; c++) {
+            fe q; f_sub(&FR, &q, &F[w + c], &F[c]);
+            g1 tt; g1_mul(&tt, &LAM(pp, t)[c], &q); g1_add(&acc, &acc, &tt);
+            fe s; f_mul(&FR, &s, &r[t], &q); f_add(&FR, &F[c], &F[c], &s);
+        }
+        g1_to_bytes(o, &acc); o += 96;
+    }
+    fr_to_bytes(out, &F[0]);
+    free(mm); free(T); free(F); free(A); free(v); free(bv);
+    return 0;
+}
+
+int or_eval_verify(const or_pp* pp, const u8* C, const u8* r_be, const u8* proof, size_t len) {
+    const u32 R = pp->R; const int lc = pp->log_c;
+    if (len != or_eval_proof_len(pp)) return 0;
+    fe r[32];
+    if (load_point(r, pp, r_be)) return 0;
+    fe y; if (f_from_be(&FR, &y, proof, 32)) return 0;
+    g1 CF; if (g1_from_bytes(&CF, proof + 32)) return 0;
+    fq12 Cg; if (fq12_from_bytes(&Cg, C)) return 0;
+    fe* T = (fe*)malloc(R * sizeof(fe));
+    eval_weights(T, pp, r);
+    fe r0; eval_r0(&r0, pp, C, r_be, proof + 32);
+    for (u32 j = 0; j < R; j++) f_mul(&FR, &T[j], &T[j], &r0);
+    g1 c1; g1_mul(&c1, &CF, &r0);
+    int ok = fc_bverify_core(pp, &Cg, c1, T, 0, R, proof + 128);
+    free(T);
+    if (!ok) return 0;
+    /* PST.Verify at r_R */
+    const u8* pst = proof + 128 + or_bopen_len(pp);
+    g1 lhsP, yg; g1_mul(&yg, &G1_GEN, &y); g1_neg(&yg, &yg); g1_add(&lhsP, &CF, &yg);
+    fq12 lhs; pairing(&lhs, &lhsP, &G2_GEN);
+    fq12 rhs; int first = 1;
+    for (int idx = 0; idx < lc; idx++) {
+        const int t = lc - 1 - idx;
+        g1 pi; if (g1_from_bytes(&pi, pst + 96 * (size_t)idx)) return 0;
+        g2 rg, Q; g2_mul(&rg, &G2_GEN, &r[t]); g2_neg(&rg, &rg); g2_add(&Q, &pp->g2tau[t], &rg);
+        fq12 e; pairing(&e, &pi, &Q);
+        if (first) { rhs = e; first = 0; } else fq12_mul(&rhs, &rhs, &e);
+    }
+    if (first) fq12_one(&rhs);
+    return fq12_eq(&lhs, &rhs);
 }
