@@ -178,6 +178,22 @@ fp_status vc_segment_proof_get(const fp_proofs* pf, uint32_t j, uint8_t* out, si
 fp_status vc_verify_segment(const fp_pp* pp, const uint8_t* C, uint32_t b, uint32_t j, const uint64_t* m_j,
                             const uint8_t* proof, size_t len, void* stream);
 
+/* Evaluation proof of the committed vector's multilinear extension f_m at a point (Sec. 4.4,
+ * "Compatibility with a family of zkSNARKs", Eq. fANDfj), for zkSNARKs that encode their inputs
+ * as multilinear polynomials.  r: log_n field elements r_0 .. r_{log N - 1}, 32 bytes big-endian
+ * canonical each (host); variable k pairs with bit k of i = j M + a, so r_0 .. r_{l_c - 1} are the
+ * column variables r_R and the rest the row variables r_L.  With T_j = eq(j, r_L) and
+ * F = sum_j T_j f_j, the proof (host, *len = vc_eval_proof_len bytes; out = NULL queries *len) is
+ *   y = f_m(r) (32) || C_F = prod_j C_j^{T_j} (96) || the FC proof of C_F = <C, T> (FC.BOpen with
+ *   t = 1: r_0 = HFr("FP-r", SHA256("FP-eval" || C || u32be(log N) || r || C_F) || u32be(0)),
+ *   b = r_0 T; the layout of pi_{C_k}) || PST.Eval(F, r_R): pi_{l_c-1} .. pi_0 (96 each).
+ * A verifier checks FC.BVerify with C_0 = (C, C_F^{r_0}) and weights r_0 T, and
+ * e(C_F - y g1, g2) = prod_t e(pi_t, g2^{tau_t} - r_t g2).  FP_ERANGE if an r_k >= r.
+ * Synchronises `stream`. */
+size_t vc_eval_proof_len(const fp_pp* pp);
+fp_status vc_eval_prove(const fp_pp* pp, const fp_commit* cm, const uint8_t* r, void* stream, uint8_t* out,
+                        size_t cap, size_t* len);
+
 /* Byte length of proof i under batch size b (no device work). */
 size_t vc_proof_len(const fp_pp* pp, uint32_t b, uint64_t i);
 

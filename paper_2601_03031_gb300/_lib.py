@@ -22,7 +22,7 @@ EXPORTED = ["vc_setup", "vc_pp_export", "vc_pp_dims", "vc_commit", "vc_commit_ge
             "fp_msm_window", "fp_msm_autotune", "vc_prove_one", "vc_pp_view", "vc_commit_async",
             "vc_commit_status", "vc_prove_all_batch", "vc_verify", "vc_verify_all", "vc_setup_split",
             "vc_pp_view_split", "vc_open_segments", "vc_segment_proof_len", "vc_segment_proof_get",
-            "vc_verify_segment"]
+            "vc_verify_segment", "vc_eval_proof_len", "vc_eval_prove"]
 
 
 class FlexProofsError(RuntimeError):
@@ -67,6 +67,9 @@ def load(path: str = LIB_PATH):
     L.vc_segment_proof_len.restype = sz
     L.vc_segment_proof_get.argtypes = [vp, u32, vp, sz, ctypes.POINTER(sz)]
     L.vc_verify_segment.argtypes = [vp, vp, u32, u32, vp, vp, sz, vp]
+    L.vc_eval_proof_len.argtypes = [vp]
+    L.vc_eval_proof_len.restype = sz
+    L.vc_eval_prove.argtypes = [vp, vp, vp, vp, vp, sz, ctypes.POINTER(sz)]
     L.vc_commit_async.argtypes = [vp, vp, ctypes.c_int, vp, pp]
     L.vc_commit_status.argtypes = [vp]
     L.vc_prove_all_batch.argtypes = [u32, vp, ctypes.c_int, vp, vp]
@@ -339,6 +342,19 @@ def vc_verify_segment(pp: PP, C: bytes, b: int, j: int, m_j, proof: bytes, strea
     if st not in (0, 5):
         raise FlexProofsError("vc_verify_segment", st)
     return st == 0
+
+
+def vc_eval_prove(pp: PP, cm: Commitment, r, stream=None) -> bytes:
+    """Evaluation proof of the committed vector's multilinear extension at r = (r_0 .. r_{log N - 1})
+    (canonical Fr integers): y || C_F || pi_FC || pi_PST."""
+    assert len(r) == pp.log_n
+    rb = b"".join(int(v).to_bytes(32, "big") for v in r)
+    L = load()
+    n = L.vc_eval_proof_len(pp.h)
+    buf = ctypes.create_string_buffer(n)
+    ln = ctypes.c_size_t()
+    _check("vc_eval_prove", L.vc_eval_prove(pp.h, cm.h, rb, _stream_ptr(stream), buf, n, ctypes.byref(ln)))
+    return buf.raw[: ln.value]
 
 
 def vc_prove_one(pp: PP, cm: Commitment, b: int, i: int, stream=None) -> bytes:

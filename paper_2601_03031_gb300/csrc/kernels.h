@@ -139,6 +139,15 @@ void msm_bases_endo(void* tab, uint64_t n, cudaStream_t s);
 // G2 bases table (4 n points) from nvalid <= n affine points, the rest identity
 void msm_bases_g2(const void* pts, uint64_t nvalid, uint64_t n, void* tab, cudaStream_t s);
 
+// ---- evaluation proof at a point (eval.cu)
+void eval_point(const void* r_be, int log_n, void* r_mont, uint32_t* err, cudaStream_t s);
+void eval_weights(const void* r_mont, int log_r, int log_c, void* T_mont, void* T_canon, cudaStream_t s);
+void eval_ftable(const void* m_mont, const void* T_mont, uint32_t R, uint32_t M, void* F, cudaStream_t s);
+void eval_bvec(const void* C_ser, const void* r_be, int log_n, const void* CF_ser, const void* T_mont, uint32_t R,
+               void* r0, void* bvec, cudaStream_t s);
+void eval_pst_fold(void* F, const void* r_mont, int log_c, void* q, void* y_out, cudaStream_t s);
+void eval_pst_terms(const void* q, const void* lam, uint32_t M, void* out, cudaStream_t s);
+
 // ---- VC.Verify (verify.cu).  One proof: result word 0 = 0 if accepted.
 size_t verify_scratch_bytes(uint32_t b, int lr, int lc);
 void verify_one(const void* proof, const void* C_be, const void* mi_be, uint32_t nk, int lr, int lc, uint32_t b,

@@ -422,6 +422,83 @@ fp_status vc_commit_get(const fp_commit* cm, uint8_t* gt576, uint8_t* rows) {
 }  // extern "C"
 
 namespace {
+// Step 1's device buffers for Kc blocks of R rows: FC.BOpen state (A, v, b per block), the round
+// outputs, the challenges and the fast-verification proof of v_l
+struct Step1Bufs {
+    void *A, *v, *bvec, *xprev, *x_mont, *xinv_mont, *xinv_all, *ml, *ml2, *sp, *sp2, *pcoef, *q;
+    void *wt = nullptr, *wt2 = nullptr, *wscr = nullptr;
+    MsmShape wsh{};
+    bool w_msm = false;
+};
+template <class Alloc>
+Step1Bufs step1_bufs(const fp_pp* pp, uint32_t Kc, Alloc&& T) {
+    const uint32_t R = pp->R;
+    const uint64_t KR = (uint64_t)Kc * R;
+    Step1Bufs B;
+    B.A = T(KR * G1A_BYTES);
+    B.v = T(KR * G2A_BYTES);
+    B.bvec = T(KR * FR_BYTES);
+    B.xprev = T(Kc * 32);
+    B.x_mont = T(Kc * FR_BYTES);
+    B.xinv_mont = T(Kc * FR_BYTES);
+    B.xinv_all = T((size_t)Kc * pp->log_r * FR_BYTES);
+    B.ml = T(KR * FQ12_BYTES);
+    B.ml2 = T((KR / 2 + 1) * FQ12_BYTES);
+    B.sp = T(KR * G1J_BYTES);
+    B.sp2 = T((KR / 2 + 1) * G1J_BYTES);
+    B.pcoef = T((size_t)Kc * (2 * R - 1) * FR_BYTES);
+    B.q = T((size_t)Kc * 2 * R * FR_BYTES);
+    // W proofs: one batched G2 MSM over the shared bases g2^{beta^i} when many blocks share them,
+    // else one scalar multiplication per term and pairwise sums (with few batches the MSM's bucket
+    // reduction runs nearly serially per window)
+    B.w_msm = KR * 2 > 4096 && Kc >= 8;
+    if (B.w_msm) {
+        B.wsh = msm_shape(2 * R, Kc, 2 * R, msm_window_model(2 * R, Kc, 4, 65, 3.0), 4, 65);
+        B.wscr = T(msm_scratch_bytes_g2(B.wsh));
+    } else {
+        B.wt = T((size_t)Kc * 2 * R * G2J_BYTES);
+        B.wt2 = T(((size_t)Kc * R + 1) * G2J_BYTES);
+    }
+    return B;
+}
+
+// FC.BOpen rounds (Sec. 3, Eq. folding) and the fast-verification proof of v_l for the Kc blocks
+// k0 .. k0 + Kc - 1 of size b, whose combined vectors are in B.bvec (their support is the block):
+// the round chain on s1, each round's G1 parts on s3 (joined before the challenge); the records go
+// to blocks1 (stride blen).  s3 must already be ordered after whatever filled B.bvec.
+void step1_rounds(const fp_pp* pp, uint32_t k0, uint32_t Kc, uint32_t b, const Step1Bufs& B, uint8_t* blocks1,
+                  size_t blen, cudaStream_t s1, cudaStream_t s3) {
+    const uint32_t R = pp->R;
+    const int lr = (int)pp->log_r;
+    cudaEvent_t ev_folded = new_event(), ev_sparse = new_event();
+    for (int j = 1; j <= lr; j++) {
+        const uint32_t h = R >> j;
+        check(cudaEventRecord(ev_folded, s1), "event");
+        check(cudaStreamWaitEvent(s3, ev_folded, 0), "wait");
+        step1_sparse_terms(B.A, B.bvec, k0, Kc, R, h, b, B.sp, s3);
+        void* spr = reduce_pairs(B.sp, B.sp2, (uint64_t)Kc * 2 * h, (uint64_t)Kc * 2, g1_pair_reduce, s3);
+        step1_g1_out(spr, Kc, j, blocks1, blen, s3);
+        check(cudaEventRecord(ev_sparse, s3), "event");
+        const uint64_t nml = step1_miller_g(B.A, B.v, Kc, R, h, B.ml, s1);
+        void* mlr = reduce_pairs(B.ml, B.ml2, nml, (uint64_t)Kc * 2, fq12_pair_reduce, s1);
+        step1_gt_out(mlr, Kc, j, blocks1, blen, s1);
+        check(cudaStreamWaitEvent(s1, ev_sparse, 0), "wait");
+        step1_challenge(blocks1, blen, Kc, j, B.xprev, B.x_mont, B.xinv_mont, B.xinv_all, lr, s1);
+        step1_fold(B.A, B.v, B.bvec, B.x_mont, B.xinv_mont, Kc, R, h, s1);
+    }
+    step1_kzg(B.A, B.v, B.xprev, B.xinv_all, Kc, R, lr, blocks1, blen, B.pcoef, B.q, s1);
+    uint8_t* w_out = blocks1 + (size_t)lr * ROUND_BYTES + G1_SER + G2_SER;
+    if (B.w_msm) {
+        msm_g2(pp->g2w_tab, B.q, B.wsh, B.wscr, nullptr, w_out, blen, s1);
+    } else {
+        step1_w_terms(pp->g2pow, B.q, Kc, R, B.wt, s1);
+        void* wr = reduce_pairs(B.wt, B.wt2, (uint64_t)Kc * 2 * R, Kc, g2_pair_reduce, s1);
+        g2j_to_affine(wr, nullptr, w_out, blen, Kc, s1);
+    }
+    cudaEventDestroy(ev_folded);
+    cudaEventDestroy(ev_sparse);
+}
+
 // OpenAll's work with Step 1 restricted to the blocks [k0, k0 + Kc) (all blocks: k0 = 0, Kc = K):
 // their records are written at their places in the K-block array; Step 2 runs in full.
 fp_proofs* prove_impl(const fp_pp* pp, const fp_commit* cm, uint32_t b, uint32_t k0, uint32_t Kc, cudaStream_t s,
@@ -462,34 +539,8 @@ fp_proofs* prove_impl(const fp_pp* pp, const fp_commit* cm, uint32_t b, uint32_t
                 pt2 = T((half / 2 + 1) * G1J_BYTES);
             }
             // every buffer is allocated (stream-ordered on s) before the fork to the internal streams
-            const uint64_t KR = (uint64_t)Kc * R;
-            void* A = T(KR * G1A_BYTES);
-            void* v = T(KR * G2A_BYTES);
-            void* bvec = T(KR * FR_BYTES);
+            const Step1Bufs B = step1_bufs(pp, Kc, T);
             void* hstmt = T(Kc * DIGEST);
-            void* xprev = T(Kc * 32);
-            void* x_mont = T(Kc * FR_BYTES);
-            void* xinv_mont = T(Kc * FR_BYTES);
-            void* xinv_all = T((size_t)Kc * lr * FR_BYTES);
-            void* ml = T(KR * FQ12_BYTES);
-            void* ml2 = T((KR / 2 + 1) * FQ12_BYTES);
-            void* sp = T(KR * G1J_BYTES);
-            void* sp2 = T((KR / 2 + 1) * G1J_BYTES);
-            void* pcoef = T((size_t)Kc * (2 * R - 1) * FR_BYTES);
-            void* q = T((size_t)Kc * 2 * R * FR_BYTES);
-            // W proofs: one batched G2 MSM over the shared bases g2^{beta^i} when many blocks share
-            // them, else one scalar multiplication per term and pairwise sums (with few batches the
-            // MSM's bucket reduction runs nearly serially per window)
-            const bool w_msm = (uint64_t)Kc * 2 * R > 4096 && Kc >= 8;
-            void *wt = nullptr, *wt2 = nullptr, *wscr = nullptr;
-            MsmShape wsh{};
-            if (w_msm) {
-                wsh = msm_shape(2 * R, Kc, 2 * R, msm_window_model(2 * R, Kc, 4, 65, 3.0), 4, 65);
-                wscr = T(msm_scratch_bytes_g2(wsh));
-            } else {
-                wt = T((size_t)Kc * 2 * R * G2J_BYTES);
-                wt2 = T(((size_t)Kc * R + 1) * G2J_BYTES);
-            }
             const Streams st = streams(s);
             cudaStream_t s2 = st.lo, s1 = st.hi, s3 = st.sp;
             cudaEvent_t ev_fork = new_event(), ev_join = new_event(), ev_join1 = new_event();
@@ -525,42 +576,18 @@ fp_proofs* prove_impl(const fp_pp* pp, const fp_commit* cm, uint32_t b, uint32_t
             // ---------------- Step 1: FC.BOpen on every block (Protocol 1, Step 1)
             // round chain on s1; each round's sparse G1 terms on s3, overlapping its Miller loops and
             // final exponentiations, joined before the challenge
-            cudaEvent_t ev_folded = new_event(), ev_sparse = new_event();
-            step1_init(cm->rows, pp->g2pow, Kc, R, A, v, bvec, s1);
+            cudaEvent_t ev_init = new_event();
+            step1_init(cm->rows, pp->g2pow, Kc, R, B.A, B.v, B.bvec, s1);
             // the statement hashes and r_a only feed b: they run on s3 ahead of the first sparse terms
             // while s1 starts the first round's Miller loops
-            check(cudaEventRecord(ev_folded, s1), "event");
-            check(cudaStreamWaitEvent(s3, ev_folded, 0), "wait");
+            check(cudaEventRecord(ev_init, s1), "event");
+            check(cudaStreamWaitEvent(s3, ev_init, 0), "wait");
             step1_stmt_hash(cm->C_ser, cm->rows_ser, k0, Kc, R, b, hstmt, s3);
-            step1_block_r(hstmt, k0, Kc, R, b, bvec, s3);
-            for (int j = 1; j <= lr; j++) {
-                const uint32_t h = R >> j;
-                check(cudaEventRecord(ev_folded, s1), "event");
-                check(cudaStreamWaitEvent(s3, ev_folded, 0), "wait");
-                step1_sparse_terms(A, bvec, k0, Kc, R, h, b, sp, s3);
-                void* spr = reduce_pairs(sp, sp2, (uint64_t)Kc * 2 * h, (uint64_t)Kc * 2, g1_pair_reduce, s3);
-                step1_g1_out(spr, Kc, j, blocks1, blen, s3);
-                check(cudaEventRecord(ev_sparse, s3), "event");
-                const uint64_t nml = step1_miller_g(A, v, Kc, R, h, ml, s1);
-                void* mlr = reduce_pairs(ml, ml2, nml, (uint64_t)Kc * 2, fq12_pair_reduce, s1);
-                step1_gt_out(mlr, Kc, j, blocks1, blen, s1);
-                check(cudaStreamWaitEvent(s1, ev_sparse, 0), "wait");
-                step1_challenge(blocks1, blen, Kc, j, xprev, x_mont, xinv_mont, xinv_all, lr, s1);
-                step1_fold(A, v, bvec, x_mont, xinv_mont, Kc, R, h, s1);
-            }
-            step1_kzg(A, v, xprev, xinv_all, Kc, R, lr, blocks1, blen, pcoef, q, s1);
-            uint8_t* w_out = (uint8_t*)blocks1 + (size_t)lr * ROUND_BYTES + G1_SER + G2_SER;
-            if (w_msm) {
-                msm_g2(pp->g2w_tab, q, wsh, wscr, nullptr, w_out, blen, s1);
-            } else {
-                step1_w_terms(pp->g2pow, q, Kc, R, wt, s1);
-                void* wr = reduce_pairs(wt, wt2, (uint64_t)Kc * 2 * R, Kc, g2_pair_reduce, s1);
-                g2j_to_affine(wr, nullptr, w_out, blen, Kc, s1);
-            }
+            step1_block_r(hstmt, k0, Kc, R, b, B.bvec, s3);
+            step1_rounds(pp, k0, Kc, b, B, blocks1, blen, s1, s3);
             check(cudaEventRecord(ev_join1, s1), "event");
             check(cudaStreamWaitEvent(s, ev_join1, 0), "join");
-            cudaEventDestroy(ev_folded);
-            cudaEventDestroy(ev_sparse);
+            cudaEventDestroy(ev_init);
             cudaEventDestroy(ev_join1);
             check_launch("step 1 kernels");
             check(cudaStreamWaitEvent(s, ev_join, 0), "join");
@@ -774,6 +801,93 @@ fp_status vc_verify_all(const fp_pp* pp, const uint8_t* C, const uint64_t* m, in
             throw;
         }
         return FP_OK;
+    });
+}
+
+size_t vc_eval_proof_len(const fp_pp* pp) {
+    if (!pp) return 0;
+    return 32 + G1_SER + bopen_len(pp->log_r) + G1_SER * (size_t)pp->log_c;
+}
+
+fp_status vc_eval_prove(const fp_pp* pp, const fp_commit* cm, const uint8_t* r, void* stream, uint8_t* out,
+                        size_t cap, size_t* len) {
+    if (!pp || !cm || !r || !len || cm->pp != pp) return FP_EINVAL;
+    const size_t need = vc_eval_proof_len(pp);
+    *len = need;
+    if (!out) return FP_OK;
+    if (cap < need) return FP_EINVAL;
+    cudaStream_t s = (cudaStream_t)stream;
+    return guarded([&]() -> fp_status {
+        const uint32_t R = pp->R, M = pp->M;
+        const int lr = (int)pp->log_r, lc = (int)pp->log_c, ln = (int)pp->log_n;
+        const size_t blen = bopen_len(pp->log_r);
+        const uint64_t half = M / 2 ? M / 2 : 1;
+        const MsmShape sh = msm_shape(R, 1, R, fp_msm_window(R, 1));
+        std::vector<void*> tmp;
+        auto T = [&](size_t bytes) { void* p = dalloc(bytes, s); tmp.push_back(p); return p; };
+        uint32_t herr = 0;
+        try {
+            if (cm->done) check(cudaStreamWaitEvent(s, cm->done, 0), "wait");
+            uint8_t* proof = (uint8_t*)T(need);                 // y | C_F | pi_FC | pi_PST
+            void* r_be = T(32 * (size_t)ln);
+            void* r_mont = T((size_t)ln * FR_BYTES);
+            uint32_t* err = (uint32_t*)T(4);
+            void* Tm = T((size_t)R * FR_BYTES);
+            void* Tc = T((size_t)R * FR_BYTES);
+            void* F = T((size_t)M * FR_BYTES);
+            void* q = T((size_t)M * FR_BYTES);
+            void* tab = T(2 * (size_t)R * G1A_BYTES);
+            void* mscr = T(msm_scratch_bytes(sh));
+            void* r0 = T(FR_BYTES);
+            void* terms = T((size_t)(lc ? lc : 1) * half * G1J_BYTES);
+            void* terms2 = T((half / 2 + 1) * G1J_BYTES);
+            const Step1Bufs B = step1_bufs(pp, 1, T);
+            const Streams st = streams(s);
+            cudaStream_t s1 = st.hi, s3 = st.sp;
+            cudaEvent_t ev_fork = new_event(), ev_bvec = new_event(), ev_join = new_event();
+            check(cudaEventRecord(ev_fork, s), "event");
+            check(cudaStreamWaitEvent(s1, ev_fork, 0), "wait");
+            check(cudaMemsetAsync(err, 0, 4, s1), "memset");
+            check(cudaMemcpyAsync(r_be, r, 32 * (size_t)ln, cudaMemcpyHostToDevice, s1), "H2D r");
+            eval_point(r_be, ln, r_mont, err, s1);
+            eval_weights(r_mont, lr, lc, Tm, Tc, s1);
+            // step 1: C_F = sum_j T_j C_j over the row commitments (and their GLV partners)
+            check(cudaMemcpyAsync(tab, cm->rows, (size_t)R * G1A_BYTES, cudaMemcpyDeviceToDevice, s1), "D2D");
+            msm_bases_endo(tab, R, s1);
+            msm_g1(tab, Tc, sh, mscr, nullptr, proof + 32, s1);
+            // step 2: FC.BOpen of <C, T> with t = 1 through the Step-1 round chain (one block of R rows)
+            step1_init(cm->rows, pp->g2pow, 1, R, B.A, B.v, B.bvec, s1);
+            eval_bvec(cm->C_ser, r_be, ln, proof + 32, Tm, R, r0, B.bvec, s1);
+            check(cudaEventRecord(ev_bvec, s1), "event");
+            check(cudaStreamWaitEvent(s3, ev_bvec, 0), "wait");
+            step1_rounds(pp, 0, 1, R, B, proof + 128, blen, s1, s3);
+            // step 3: PST.Eval of F = sum_j T_j f_j at r_R
+            eval_ftable(cm->m_mont, Tm, R, M, F, s1);
+            eval_pst_fold(F, r_mont, lc, q, proof, s1);
+            if (lc) {
+                check(cudaMemsetAsync(terms, 0, (size_t)lc * half * G1J_BYTES, s1), "memset");
+                eval_pst_terms(q, pp->lam, M, terms, s1);
+                for (int t = 0; t < lc; t++) {
+                    void* lvl = (uint8_t*)terms + (size_t)t * half * G1J_BYTES;
+                    void* res = reduce_pairs(lvl, terms2, half, 1, g1_pair_reduce, s1);
+                    g1j_to_affine(res, nullptr, proof + 128 + blen + G1_SER * (size_t)(lc - 1 - t), G1_SER, 1, s1);
+                }
+            }
+            check_launch("vc_eval_prove kernels");
+            check(cudaMemcpyAsync(out, proof, need, cudaMemcpyDeviceToHost, s1), "D2H proof");
+            check(cudaMemcpyAsync(&herr, err, 4, cudaMemcpyDeviceToHost, s1), "D2H err");
+            check(cudaEventRecord(ev_join, s1), "event");
+            check(cudaStreamWaitEvent(s, ev_join, 0), "join");
+            for (void* p : tmp) cudaFreeAsync(p, s);
+            tmp.clear();
+            cudaEventDestroy(ev_fork); cudaEventDestroy(ev_bvec); cudaEventDestroy(ev_join);
+            check(cudaStreamSynchronize(s), "vc_eval_prove");
+        } catch (...) {
+            for (void* p : tmp) cudaFreeAsync(p, s);
+            cudaStreamSynchronize(s);
+            throw;
+        }
+        return herr ? FP_ERANGE : FP_OK;
     });
 }
 

@@ -1,0 +1,72 @@
+"""Evaluation proof at a point (Sec. 4.4, "Compatibility with a family of zkSNARKs") on the GPU
+against the oracle: proof bytes equal for several splits and points (the FC part runs through the
+Step-1 round chain with a dense b), y at Boolean points equals the element, the oracle's verifier
+accepts the GPU proof, and out-of-range coordinates are rejected."""
+import random
+
+import pytest
+
+import oracle as O
+from paper_2601_03031_gb300 import inputs as I
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+if not torch.cuda.is_available():
+    pytest.skip("no CUDA device", allow_module_level=True)
+
+from paper_2601_03031_gb300 import _lib as F  # noqa: E402
+
+
+def point(seed, n):
+    rnd = random.Random(seed)
+    return [rnd.randrange(I.R_INT) for _ in range(n)]
+
+
+@pytest.mark.parametrize("log_n,log_r", [(4, 2), (5, 2), (7, 3), (6, 5), (8, 1), (10, 5)])
+def test_eval_proof_equals_oracle(log_n, log_r):
+    seed = 71 + log_n
+    pp = F.PP(log_n, 1, seed, log_r=log_r)
+    opp = O.PP(log_n, seed, log_r=log_r)
+    m = I.vector(seed + 1, log_n)
+    cm = F.Commitment(pp, m)
+    C, rows = cm.get()
+    for ps in (1, 2):
+        r = point(seed * 10 + ps, log_n)
+        got = F.vc_eval_prove(pp, cm, r)
+        assert got == O.eval_prove(opp, m.tobytes(), C, rows, r)
+        assert O.eval_verify(opp, C, r, got)
+
+
+def test_eval_boolean_points_and_range():
+    log_n, seed = 6, 81
+    pp = F.PP(log_n, 1, seed)
+    m = I.vector(seed + 1, log_n)
+    vals = I.to_ints(m)
+    cm = F.Commitment(pp, m)
+    for i in (0, 9, 63):
+        r = [(i >> k) & 1 for k in range(log_n)]
+        assert int.from_bytes(F.vc_eval_prove(pp, cm, r)[:32], "big") == vals[i]
+    bad = point(5, log_n)
+    bad[2] = I.R_INT
+    with pytest.raises(F.FlexProofsError) as e:
+        F.vc_eval_prove(pp, cm, bad)
+    assert e.value.status == 6
+
+
+def test_eval_n16():
+    log_n, seed = 16, 0
+    pp = F.PP(log_n, 1, seed)
+    opp = O.PP(log_n, seed)
+    m = I.vector(seed + 1, log_n)
+    cm = F.Commitment(pp, m)
+    C, rows = cm.get()
+    r = point(123, log_n)
+    got = F.vc_eval_prove(pp, cm, r)
+    assert O.eval_verify(opp, C, r, got)
+    # y against the multilinear extension evaluated by folding the vector on the host
+    vals = I.to_ints(m)
+    cur = vals
+    for k in range(log_n):
+        cur = [(cur[2 * c] + r[k] * (cur[2 * c + 1] - cur[2 * c])) % I.R_INT for c in range(len(cur) // 2)]
+    assert int.from_bytes(got[:32], "big") == cur[0]
