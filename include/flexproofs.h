@@ -194,6 +194,13 @@ size_t vc_eval_proof_len(const fp_pp* pp);
 fp_status vc_eval_prove(const fp_pp* pp, const fp_commit* cm, const uint8_t* r, void* stream, uint8_t* out,
                         size_t cap, size_t* len);
 
+/* The verifier of vc_eval_prove's proof on the GPU: FC.BVerify of C_F = <C, T> (b_l shortcut, fast
+ * verification of v_l) and PST.Verify of y at r_R.  C: 576-byte commitment, r as for vc_eval_prove,
+ * proof / len: host bytes.  FP_OK if both hold, FP_EVERIFY if not (also for a wrong length, an
+ * r_k >= r, y >= r or a malformed element), FP_EINVAL for bad arguments.  Synchronises `stream`. */
+fp_status vc_eval_verify(const fp_pp* pp, const uint8_t* C, const uint8_t* r, const uint8_t* proof, size_t len,
+                         void* stream);
+
 /* Byte length of proof i under batch size b (no device work). */
 size_t vc_proof_len(const fp_pp* pp, uint32_t b, uint64_t i);
 

@@ -22,7 +22,7 @@ EXPORTED = ["vc_setup", "vc_pp_export", "vc_pp_dims", "vc_commit", "vc_commit_ge
             "fp_msm_window", "fp_msm_autotune", "vc_prove_one", "vc_pp_view", "vc_commit_async",
             "vc_commit_status", "vc_prove_all_batch", "vc_verify", "vc_verify_all", "vc_setup_split",
             "vc_pp_view_split", "vc_open_segments", "vc_segment_proof_len", "vc_segment_proof_get",
-            "vc_verify_segment", "vc_eval_proof_len", "vc_eval_prove"]
+            "vc_verify_segment", "vc_eval_proof_len", "vc_eval_prove", "vc_eval_verify"]
 
 
 class FlexProofsError(RuntimeError):
@@ -70,6 +70,7 @@ def load(path: str = LIB_PATH):
     L.vc_eval_proof_len.argtypes = [vp]
     L.vc_eval_proof_len.restype = sz
     L.vc_eval_prove.argtypes = [vp, vp, vp, vp, vp, sz, ctypes.POINTER(sz)]
+    L.vc_eval_verify.argtypes = [vp, vp, vp, vp, sz, vp]
     L.vc_commit_async.argtypes = [vp, vp, ctypes.c_int, vp, pp]
     L.vc_commit_status.argtypes = [vp]
     L.vc_prove_all_batch.argtypes = [u32, vp, ctypes.c_int, vp, vp]
@@ -355,6 +356,16 @@ def vc_eval_prove(pp: PP, cm: Commitment, r, stream=None) -> bytes:
     ln = ctypes.c_size_t()
     _check("vc_eval_prove", L.vc_eval_prove(pp.h, cm.h, rb, _stream_ptr(stream), buf, n, ctypes.byref(ln)))
     return buf.raw[: ln.value]
+
+
+def vc_eval_verify(pp: PP, C: bytes, r, proof: bytes, stream=None) -> bool:
+    """GPU verifier of vc_eval_prove's proof at r."""
+    assert len(r) == pp.log_n
+    rb = b"".join(int(v).to_bytes(32, "big") for v in r)
+    st = load().vc_eval_verify(pp.h, C, rb, proof, len(proof), _stream_ptr(stream))
+    if st not in (0, 5):
+        raise FlexProofsError("vc_eval_verify", st)
+    return st == 0
 
 
 def vc_prove_one(pp: PP, cm: Commitment, b: int, i: int, stream=None) -> bytes:

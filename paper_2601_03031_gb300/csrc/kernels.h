@@ -157,6 +157,11 @@ void verify_one(const void* proof, const void* C_be, const void* mi_be, uint32_t
 size_t verify_block_scratch_bytes(uint32_t b, int lr);
 void verify_block(const void* blk, const void* fc, const void* C_be, uint32_t nk, int lr, uint32_t b, uint32_t k,
                   uint32_t lo, const void* g1beta, void* scratch, uint32_t* result, cudaStream_t s);
+// The evaluation proof at r (proof = y | C_F | pi_FC | pi_PST, r log_n x 32 B big-endian); result
+// word 0 = 0 if accepted
+size_t verify_eval_scratch_bytes(uint32_t R, int lr, int lc, int log_n);
+void verify_eval(const void* proof, const void* C_be, const void* r_be, int log_n, int lr, int lc, uint32_t R,
+                 const void* g1beta, const void* g2tau, void* scratch, uint32_t* result, cudaStream_t s);
 // All N proofs of an OpenAll output (its shared pieces as stored by vc_prove_all) against the
 // claimed values m (device, N x 4 little-endian u64): ok_out (host, N bytes, may be null) gets 1
 // per accepted proof; returns the number accepted.  each = 1: no PST check is shared.  Synchronises.

@@ -891,6 +891,41 @@ fp_status vc_eval_prove(const fp_pp* pp, const fp_commit* cm, const uint8_t* r, 
     });
 }
 
+fp_status vc_eval_verify(const fp_pp* pp, const uint8_t* C, const uint8_t* r, const uint8_t* proof, size_t len,
+                         void* stream) {
+    if (!pp || !C || !r || !proof) return FP_EINVAL;
+    if (len != vc_eval_proof_len(pp)) return FP_EVERIFY;
+    cudaStream_t s = (cudaStream_t)stream;
+    return guarded([&]() -> fp_status {
+        const int ln = (int)pp->log_n;
+        // proof | C | r, one host-to-device copy
+        std::vector<uint8_t> host(len + GT_SER + 32 * (size_t)ln);
+        memcpy(host.data(), proof, len);
+        memcpy(host.data() + len, C, GT_SER);
+        memcpy(host.data() + len + GT_SER, r, 32 * (size_t)ln);
+        void *dbuf = nullptr, *scr = nullptr, *res = nullptr;
+        uint32_t hres = 1;
+        try {
+            dbuf = dalloc(host.size(), s);
+            scr = dalloc(verify_eval_scratch_bytes(pp->R, (int)pp->log_r, (int)pp->log_c, ln), s);
+            res = dalloc(sizeof(uint32_t), s);
+            check(cudaMemcpyAsync(dbuf, host.data(), host.size(), cudaMemcpyHostToDevice, s), "H2D");
+            const uint8_t* d = (const uint8_t*)dbuf;
+            verify_eval(d, d + len, d + len + GT_SER, ln, (int)pp->log_r, (int)pp->log_c, pp->R, pp->g1beta,
+                        pp->g2tau, scr, (uint32_t*)res, s);
+            check_launch("vc_eval_verify kernels");
+            check(cudaMemcpyAsync(&hres, res, sizeof hres, cudaMemcpyDeviceToHost, s), "D2H result");
+            dfree(dbuf, s); dfree(scr, s); dfree(res, s);
+            check(cudaStreamSynchronize(s), "vc_eval_verify");
+        } catch (...) {
+            cudaStreamSynchronize(s);
+            dfree(dbuf, s); dfree(scr, s); dfree(res, s);
+            throw;
+        }
+        return hres ? FP_EVERIFY : FP_OK;
+    });
+}
+
 fp_status vc_open_segments(const fp_pp* pp, const fp_commit* cm, uint32_t b, uint32_t k0, uint32_t nblocks,
                            void* stream, fp_proofs** out) {
     if (!pp || !cm || !out || cm->pp != pp) return FP_EINVAL;

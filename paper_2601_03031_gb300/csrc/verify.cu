@@ -198,7 +198,7 @@ __global__ void k_vb_transcript(VSrc S, const uint8_t* C_be, VBlk* st) {
     const uint8_t* fc = S.fc + q * S.fc_stride;
     const int lr = S.lr;
     uint32_t bad = 0;
-    {
+    if (S.blk) {                                       // the evaluation proof has no block statement
         sha256_ctx c;
         sha256_init(c);
         sha256_update(c, C_be, 576);
@@ -709,6 +709,177 @@ void verify_block(const void* blk, const void* fc, const void* C_be, uint32_t nk
     FP_KERNEL("k_vb_prod", s, k_vb_prod<<<1, 32, 0, s>>>(O.Bb.ml, O.Bb.ge, O.Cd, 1, lr, O.Bb.fe_in, O.Bb.cT));
     final_exp_group(O.Bb.fe_in, 2, O.Bb.fe_out, nullptr, 1, 0, 0, s);
     FP_KERNEL("k_vb_check", s, k_vb_check<<<1, 32, 0, s>>>(O.Bb.fe_out, O.Bb.cT, O.cbad, O.Bb.st, 1, result));
+}
+
+// ------------------------------------------------------------------------------ evaluation proof
+// Verifier of the evaluation proof at r (Sec. 4.4): FC.BVerify with C_0 = (C, r_0 C_F) and the
+// weights w = r_0 T (one block of all R rows, no block statement), then PST.Verify at r_R:
+// e(C_F - y g1, g2) prod_t e(-pi_t, g2^{tau_t} - r_t g2) = 1.  Proof: y | C_F | pi_FC | pi_PST.
+
+// y (canonical) and C_F (on the curve) from the proof; bad |= 1 on a failed decode
+__global__ void k_ve_decode(const uint8_t* proof, fr* y, g1a* CF, uint32_t* bad) {
+    if (gtid() != 0) return;
+    if (!fr_from_be32(proof, *y) || !g1_decode(proof + 32, *CF)) atomicOr(bad, 1u);
+}
+
+// slot 0: r_0 C_F; slots 1 .. 2 l_R: x_j L_j.1 and x_j^-1 R_j.1 (one 8-lane group each)
+__global__ void __launch_bounds__(128) k_ve_terms(VSrc S, VBlk* st, const g1a* CF, const fr* r0, uint32_t tpb,
+                                                  g1j* T) {
+    __shared__ GEc<fq> sm[16];
+    const int grp = threadIdx.x >> 3, lane = threadIdx.x & 7;
+    const uint64_t u = (uint64_t)blockIdx.x * 16 + grp;
+    const int lr = S.lr;
+    const bool valid = u < 1 + 2 * (uint64_t)lr && u < tpb;
+    VBlk& B = st[0];
+    g1a P;
+    fq_zero(P.x);
+    fq_zero(P.y);
+    fr k;
+    fr_zero(k);
+    if (valid && u == 0) {
+        P = *CF;
+        k = *r0;
+    } else if (valid) {
+        const int v = (int)(u - 1), jj = v >> 1, side = v & 1;
+        const uint8_t* rd = S.fc + (size_t)jj * ROUND_BYTES;
+        if (!g1_decode(rd + (side ? GT_SER + G1_SER + GT_SER : GT_SER), P) && lane == 0) atomicOr(&B.bad, 64u);
+        k = side ? B.xinv[jj] : B.x[jj];
+    }
+    const g1j r = g1_mul8(sm[grp], lane, P, k);
+    if (valid && lane == 0) T[u] = r;
+}
+
+// b_l summands w_a prod_k x_k^-(bit l - k of a), a < R
+__global__ void k_ve_wt(VSrc S, const VBlk* st, const fr* w, fr* wt) {
+    const uint64_t a = gtid();
+    if (a >= S.R) return;
+    fr v = w[a];
+    for (int kk = 1; kk <= S.lr; kk++)
+        if ((a >> (S.lr - kk)) & 1) v = fr_mul(v, st[0].xinv[kk - 1]);
+    wt[a] = v;
+}
+
+// E = C_F - y g1 on one 8-lane group
+__global__ void __launch_bounds__(32) k_ve_E(const g1a* CF, const fr* y, g1a* E) {
+    __shared__ GEc<fq> sm[4];
+    const int grp = threadIdx.x >> 3, lane = threadIdx.x & 7;
+    const g1j yg = g1_mul8(sm[grp], lane, g1_generator(), *y);
+    if (threadIdx.x == 0) *E = g1_affine(g1_madd(g1j_neg(yg), *CF));
+}
+
+// PST pairs at r: idx < l_c: (-pi_idx, g2^{tau_t} - r_t g2), t = l_c - 1 - idx (r_t g2 on one warp);
+// idx = l_c: (E, g2)
+__global__ void __launch_bounds__(32) k_ve_pst_pairs(const uint8_t* pst, const fr* r_mont, const g2a* g2tau, int lc,
+                                                     const g1a* E, uint32_t* bad, g1a* P, g2a* Q) {
+    __shared__ GEcW sm;
+    const int idx = blockIdx.x, L = threadIdx.x;
+    if (idx == lc) {
+        if (L == 0) {
+            P[idx] = *E;
+            Q[idx] = g2_generator();
+        }
+        return;
+    }
+    const int t = lc - 1 - idx;
+    uint32_t kw[8];
+    fr_canon_words(kw, r_mont[t]);
+    const GPt<fq2> rg = gecw_g2_mul_proj(sm, L, g2_generator(), kw);
+    if (L == 0) {
+        g1a p;
+        if (!g1_decode(pst + 96 * (size_t)idx, p)) atomicOr(bad, 512u);
+        P[idx] = g1a_neg(p);
+        g2a ra;
+        gec_to_affine(ra.x, ra.y, rg);
+        Q[idx] = g2_affine(g2_madd(g2_from_affine(g2tau[t]), g2a_negate(ra)));
+    }
+}
+
+__global__ void k_ve_result(const uint32_t* blk_res, const uint32_t* pst_res, const uint32_t* dec_bad,
+                            const uint32_t* err, uint32_t* result) {
+    if (gtid() != 0) return;
+    result[0] = blk_res[0] | pst_res[0] | dec_bad[0] | err[0];
+}
+
+namespace {
+template <class A>
+struct EvalBufs {
+    fq12* Cd; uint32_t* cbad; BlockBufs<A> Bb; fr* r_mont; uint32_t* err; fr* Tm; fr* Tc; fr* w; fr* r0; fr* y;
+    g1a* CF; g1a* E; uint32_t* dec_bad; g1a* P; g2a* Q; fq12* ml; fq12* fe_in; fq12* fe_out; uint32_t* blk_res;
+    uint32_t* pst_res;
+    EvalBufs(A& ar, uint32_t R, int lr, int lc, int log_n)
+        : Cd((fq12*)ar.take(FQ12_BYTES)), cbad((uint32_t*)ar.take(4)), Bb(ar, 1, R, lr) {
+        r_mont = (fr*)ar.take((size_t)log_n * FR_BYTES);
+        err = (uint32_t*)ar.take(4);
+        Tm = (fr*)ar.take((size_t)R * FR_BYTES);
+        Tc = (fr*)ar.take((size_t)R * FR_BYTES);
+        w = (fr*)ar.take((size_t)R * FR_BYTES);
+        r0 = (fr*)ar.take(FR_BYTES);
+        y = (fr*)ar.take(FR_BYTES);
+        CF = (g1a*)ar.take(G1A_BYTES);
+        E = (g1a*)ar.take(G1A_BYTES);
+        dec_bad = (uint32_t*)ar.take(4);
+        P = (g1a*)ar.take((size_t)(lc + 1) * G1A_BYTES);
+        Q = (g2a*)ar.take((size_t)(lc + 1) * G2A_BYTES);
+        ml = (fq12*)ar.take((size_t)(lc + 1) * FQ12_BYTES);
+        fe_in = (fq12*)ar.take(FQ12_BYTES);
+        fe_out = (fq12*)ar.take(FQ12_BYTES);
+        blk_res = (uint32_t*)ar.take(4);
+        pst_res = (uint32_t*)ar.take(4);
+    }
+};
+}  // namespace
+
+size_t verify_eval_scratch_bytes(uint32_t R, int lr, int lc, int log_n) {
+    SizeArena ar;
+    EvalBufs<SizeArena> Eb(ar, R, lr, lc, log_n);
+    (void)Eb;
+    return ar.n + 256;
+}
+
+void verify_eval(const void* proof, const void* C_be, const void* r_be, int log_n, int lr, int lc, uint32_t R,
+                 const void* g1beta, const void* g2tau, void* scratch, uint32_t* result, cudaStream_t s) {
+    const uint8_t* pr = (const uint8_t*)proof;
+    const size_t blen = (size_t)lr * ROUND_BYTES + G1_SER + 2 * G2_SER;
+    const VSrc S{nullptr, 0, pr + 128, 0, 0, 1, R, R, lr};
+    Arena ar{(uint8_t*)scratch};
+    EvalBufs<Arena> O(ar, R, lr, lc, log_n);
+    cudaMemsetAsync(O.err, 0, 4, s);
+    cudaMemsetAsync(O.dec_bad, 0, 4, s);
+    eval_point(r_be, log_n, O.r_mont, O.err, s);
+    eval_weights(O.r_mont, lr, lc, O.Tm, O.Tc, s);
+    FP_KERNEL("k_ve_decode", s, k_ve_decode<<<1, 32, 0, s>>>(pr, O.y, O.CF, O.dec_bad));
+    eval_bvec(C_be, r_be, log_n, pr + 32, O.Tm, R, O.r0, O.w, s);          // r_0 and w = r_0 T
+    FP_KERNEL("k_v_cdec", s, k_v_cdec<<<1, 32, 0, s>>>((const uint8_t*)C_be, O.Cd, O.cbad));
+    // FC.BVerify front: transcript, the G1 part of C_0 and the rounds, b_l, the three pairs
+    const uint32_t tpb = pow2_at_least(1 + 2 * (uint64_t)lr);
+    cudaMemsetAsync(O.Bb.T, 0, (size_t)tpb * G1J_BYTES, s);
+    FP_KERNEL("k_vb_transcript", s, k_vb_transcript<<<1, 32, 0, s>>>(S, (const uint8_t*)C_be, O.Bb.st));
+    FP_KERNEL("k_ve_terms", s, k_ve_terms<<<grid_for(tpb, 16), 128, 0, s>>>(S, O.Bb.st, O.CF, O.r0, tpb, O.Bb.T));
+    FP_KERNEL("k_ve_wt", s, k_ve_wt<<<grid_for(R, 64), 64, 0, s>>>(S, O.Bb.st, O.w, O.Bb.wt));
+    g1j* x = O.Bb.T;
+    g1j* yb = O.Bb.T2;
+    for (uint64_t n = tpb; n > 1; n /= 2) {
+        g1_pair_reduce(x, yb, n / 2, s);
+        std::swap(x, yb);
+    }
+    FP_KERNEL("k_vb_scalars", s, k_vb_scalars<<<1, 64, 0, s>>>(S, O.Bb.wt, O.Bb.st));
+    FP_KERNEL("k_vb_muls", s, k_vb_muls<<<2, 128, 0, s>>>(O.Bb.st, 1, 1));
+    FP_KERNEL("k_vb_pairs", s, k_vb_pairs<<<1, 64, 0, s>>>(1, (const g1a*)g1beta, x, O.Bb.st, O.Bb.P, O.Bb.Q));
+    FP_KERNEL("k_v_miller", s, k_v_miller<<<3, 128, 0, s>>>(O.Bb.P, O.Bb.Q, O.Bb.ml));
+    FP_KERNEL("k_vb_gt", s, k_vb_gt<<<2 * lr, 128, 0, s>>>(S, O.Bb.st, O.Bb.ge));
+    FP_KERNEL("k_vb_prod", s, k_vb_prod<<<1, 32, 0, s>>>(O.Bb.ml, O.Bb.ge, O.Cd, 1, lr, O.Bb.fe_in, O.Bb.cT));
+    final_exp_group(O.Bb.fe_in, 2, O.Bb.fe_out, nullptr, 1, 0, 0, s);
+    FP_KERNEL("k_vb_check", s, k_vb_check<<<1, 32, 0, s>>>(O.Bb.fe_out, O.Bb.cT, O.cbad, O.Bb.st, 1, O.blk_res));
+    // PST.Verify at r_R
+    FP_KERNEL("k_ve_E", s, k_ve_E<<<1, 32, 0, s>>>(O.CF, O.y, O.E));
+    FP_KERNEL("k_ve_pst_pairs", s, k_ve_pst_pairs<<<lc + 1, 32, 0, s>>>(pr + 128 + blen, O.r_mont, (const g2a*)g2tau,
+                                                                       lc, O.E, O.dec_bad, O.P, O.Q));
+    FP_KERNEL("k_v_miller", s, k_v_miller<<<lc + 1, 128, 0, s>>>(O.P, O.Q, O.ml));
+    FP_KERNEL("k_vp_prod", s, k_vp_prod<<<1, 32, 0, s>>>(O.ml, lc + 1, 1, O.fe_in));
+    final_exp_group(O.fe_in, 1, O.fe_out, nullptr, 1, 0, 0, s);
+    cudaMemsetAsync(O.pst_res, 0, 4, s);
+    FP_KERNEL("k_vp_check", s, k_vp_check<<<1, 32, 0, s>>>(O.fe_out, O.pst_res, 1, nullptr, 0, O.pst_res));
+    FP_KERNEL("k_ve_result", s, k_ve_result<<<1, 32, 0, s>>>(O.blk_res, O.pst_res, O.dec_bad, O.err, result));
 }
 
 // ------------------------------------------------------------------------------ all proofs

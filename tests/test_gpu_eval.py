@@ -1,7 +1,7 @@
 """Evaluation proof at a point (Sec. 4.4, "Compatibility with a family of zkSNARKs") on the GPU
 against the oracle: proof bytes equal for several splits and points (the FC part runs through the
-Step-1 round chain with a dense b), y at Boolean points equals the element, the oracle's verifier
-accepts the GPU proof, and out-of-range coordinates are rejected."""
+Step-1 round chain with a dense b), y at Boolean points equals the element, the oracle's and the
+GPU verifier accept it and agree on every tampered part, and out-of-range coordinates are rejected."""
 import random
 
 import pytest
@@ -36,6 +36,7 @@ def test_eval_proof_equals_oracle(log_n, log_r):
         got = F.vc_eval_prove(pp, cm, r)
         assert got == O.eval_prove(opp, m.tobytes(), C, rows, r)
         assert O.eval_verify(opp, C, r, got)
+        assert F.vc_eval_verify(pp, C, r, got)
 
 
 def test_eval_boolean_points_and_range():
@@ -70,3 +71,35 @@ def test_eval_n16():
     for k in range(log_n):
         cur = [(cur[2 * c] + r[k] * (cur[2 * c + 1] - cur[2 * c])) % I.R_INT for c in range(len(cur) // 2)]
     assert int.from_bytes(got[:32], "big") == cur[0]
+
+
+def test_eval_verifier_rejections_agree_with_oracle():
+    log_n, log_r, seed = 7, 3, 91
+    pp = F.PP(log_n, 1, seed, log_r=log_r)
+    opp = O.PP(log_n, seed, log_r=log_r)
+    m = I.vector(seed + 1, log_n)
+    cm = F.Commitment(pp, m)
+    C, rows = cm.get()
+    r = point(17, log_n)
+    proof = F.vc_eval_prove(pp, cm, r)
+    assert F.vc_eval_verify(pp, C, r, proof)
+    blen = 1344 * log_r + 480
+    y = int.from_bytes(proof[:32], "big")
+    cases = {"y": ((y + 1) % I.R_INT).to_bytes(32, "big") + proof[32:]}
+    for name, off in (("C_F", 100), ("L_1.T", 128 + 40), ("R_1.1", 128 + 576 + 96 + 576 + 90),
+                      ("W", 128 + blen - 3), ("pi", 128 + blen + 95), ("pi_0", len(proof) - 1)):
+        t = bytearray(proof)
+        t[off] ^= 1
+        cases[name] = bytes(t)
+    for name, q in cases.items():
+        assert not F.vc_eval_verify(pp, C, r, q), name
+        assert not O.eval_verify(opp, C, r, q), name
+    r2 = list(r)
+    r2[log_n - 1] = (r2[log_n - 1] + 1) % I.R_INT
+    assert not F.vc_eval_verify(pp, C, r2, proof)
+    other_C = F.Commitment(pp, I.vector(5, log_n)).get()[0]
+    assert not F.vc_eval_verify(pp, other_C, r, proof)
+    assert not F.vc_eval_verify(pp, C, r, proof[:-1])
+    big = list(r)
+    big[0] = I.R_INT
+    assert not F.vc_eval_verify(pp, C, big, proof)
