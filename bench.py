@@ -309,6 +309,36 @@ def fc_microbench(F, I, torch, np, seed: int) -> dict:
     return out
 
 
+def eval_sweep(F, I, torch, np, cases, seed: int) -> dict:
+    """Evaluation proof of the committed vector's multilinear extension at a random point (prover and
+    GPU verifier, host wall time of the synchronous calls, median of 3 after one warm-up)."""
+    import random
+    out = {}
+    for log_n in cases:
+        pp = F.PP(log_n, 1, seed)
+        m = I.vector(seed + 1, log_n)
+        cm = F.Commitment(pp, m)
+        C, _ = cm.get(rows=False)
+        rnd = random.Random(seed + log_n)
+        r = [rnd.randrange(I.R_INT) for _ in range(log_n)]
+
+        def wall(fn):
+            fn()
+            ts = []
+            for _ in range(3):
+                t0 = time.perf_counter()
+                fn()
+                ts.append((time.perf_counter() - t0) * 1e3)
+            return sorted(ts)[1]
+        proof = F.vc_eval_prove(pp, cm, r)
+        assert F.vc_eval_verify(pp, C, r, proof)
+        out[f"n2^{log_n}"] = {"prove_ms": wall(lambda: F.vc_eval_prove(pp, cm, r)),
+                              "verify_ms": wall(lambda: F.vc_eval_verify(pp, C, r, proof)),
+                              "proof_bytes": len(proof)}
+        del cm, pp
+    return out
+
+
 def batched_workload(F, I, torch, np) -> dict:
     """64 jobs, log N uniform in 8..18 by seed, b = min(R, nearestpow2(log^2 N)), one SRS for 2^18
     resident: one vc_prove_all_batch captured as a CUDA graph vs the same jobs as concurrent job
@@ -661,6 +691,7 @@ def main():
                                 [int(x) for x in args.msm_sweep.split(",") if x], args.seed),
             "verify_all": verify_sweep(F, I, torch, np, [(16, 256), (20, 1), (20, 1024)], args.seed),
             "fc_microbench": fc_microbench(F, I, torch, np, args.seed),
+            "eval_proof": eval_sweep(F, I, torch, np, [16, 20], args.seed),
             "batched_64_jobs": batched_workload(F, I, torch, np),
             "served": served_workload(F, I, torch, np, args.served_requests),
         }
