@@ -10,7 +10,10 @@
 // joint double-and-add over a table of subset sums that always adds (the empty subset is the
 // identity), so all groups of a warp run the same instruction stream.
 #pragma once
-#include "group12.cuh"
+#include "pairing.cuh"
+
+// barrier of the lanes of a warp (the groups of a warp run the same instruction stream)
+FPG_DEV void gsync() { __syncwarp(); }
 
 template <typename F> struct GPt { F X, Y, Z; };
 template <typename F> struct GEc {

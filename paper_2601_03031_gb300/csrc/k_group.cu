@@ -157,16 +157,7 @@ __global__ void k_load_vector(const fr* m, uint64_t n, fr* canon, fr* mont, uint
     canon[i] = c;
     mont[i] = fr_to_mont(c);
 }
-__global__ void k_commit_terms(const fr* m_canon, const g1a* lam, uint64_t n, uint32_t M, g1j* out) {
-    uint64_t i = gtid();
-    if (i >= n) return;
-    out[i] = g1_mul(lam[i % M], m_canon[i].v);
-}
 void load_vector(const void* m, uint64_t n, void* canon, void* mont, uint32_t* err, cudaStream_t s) {
     FP_KERNEL("k_load_vector", s, k_load_vector<<<grid_for(n), TPB, 0, s>>>((const fr*)m, n, (fr*)canon, (fr*)mont, err));
 }
-void commit_terms(const void* m_canon, const void* lam, uint64_t n, uint32_t M, void* out, cudaStream_t s) {
-    FP_KERNEL("k_commit_terms", s, k_commit_terms<<<grid_for(n, 64), 64, 0, s>>>((const fr*)m_canon, (const g1a*)lam, n, M, (g1j*)out));
-}
-
 }  // namespace fpk

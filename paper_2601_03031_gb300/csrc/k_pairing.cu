@@ -1,5 +1,4 @@
 // Batched Miller loops and final exponentiations.
-#include "group12.cuh"
 #include "k_common.cuh"
 #include "warp12.cuh"
 
@@ -44,35 +43,6 @@ __global__ void __launch_bounds__(64) k_step1_miller_multi(const g1a* A, const g
         Q[g] = side == 0 ? vk[i0 + g] : vk[h + i0 + g];
     }
     out[t] = miller_loop_multi<G>(P, Q);
-}
-
-__global__ void __launch_bounds__(64) k_final_exp(const fq12* in, uint32_t n, size_t stride, fq12* out, uint8_t* ser,
-                                                  size_t ser_stride) {
-    uint64_t i = gtid();
-    if (i >= n) return;
-    fq12 e = final_exp(in[i * stride]);
-    if (out) out[i] = e;
-    if (ser) fq12_to_be(ser + i * ser_stride, e);
-}
-
-// Final exponentiations with one group of 8 lanes per element (group12.cuh).  Element t is written
-// serialised at ser + (t / per) * stride_a + (t % per) * stride_b (and to out[t] if out != null).
-// Groups past n repeat element 0 without storing, so every lane of a warp runs the same code.
-__global__ void __launch_bounds__(64) k_final_exp_g(const fq12* in, uint32_t n, fq12* out, uint8_t* ser,
-                                                    uint32_t per, size_t stride_a, size_t stride_b) {
-    __shared__ fq2 xb[8][8], yb[8][8];
-    const int grp = threadIdx.x >> 3, lane = threadIdx.x & 7;
-    const uint64_t t = (uint64_t)blockIdx.x * 8 + grp;
-    const bool valid = t < n;
-    const G12 g{lane, xb[grp]};
-    const fq2 e = g_final_exp(g, yb[grp], g_load(in[valid ? t : 0], lane));
-    if (!valid || lane >= 6) return;
-    if (out) g_store(out[t], lane, e);
-    if (ser) {
-        uint8_t* o = ser + (t / per) * stride_a + (t % per) * stride_b + 96 * g_tower_pos(lane);
-        fq_to_be(o, e.c0);
-        fq_to_be(o + 48, e.c1);
-    }
 }
 
 // one warp per final exponentiation (warp12.cuh): value t's result goes to out[t] and/or its
@@ -208,17 +178,6 @@ void round_miller_w(const void* A, const void* v, uint32_t K, uint32_t R, uint32
                                                                                              (fq12*)out));
 }
 
-// FC.Commit's Miller loops on 8-lane groups: pair j = (C_j, v_j)
-__global__ void __launch_bounds__(64) k_commit_miller_g(const g1a* rows, const g2a* g2pow, uint32_t R, fq12* out) {
-    __shared__ GMill sm[8];
-    const int grp = threadIdx.x >> 3, lane = threadIdx.x & 7;
-    const uint64_t j0 = (uint64_t)blockIdx.x * 8 + grp;
-    const bool valid = j0 < R;
-    const uint64_t j = valid ? j0 : 0;
-    const fq2 f = g_miller(sm[grp], lane, rows[j], g2pow[2 * j]);
-    if (valid) g_store(out[j], lane, f);
-}
-
 void commit_miller(const void* rows, const void* g2pow, uint32_t R, void* out, cudaStream_t s) {
     if ((uint64_t)R * 32 > 16384 * 32) {           // many pairs: one thread each does less work in total
         FP_KERNEL("k_commit_miller", s, k_commit_miller<<<grid_for(R, 64), 64, 0, s>>>((const g1a*)rows,
@@ -248,10 +207,4 @@ void step1_miller(const void* A, const void* v, uint32_t K, uint32_t R, uint32_t
     uint64_t n = (uint64_t)K * 2 * h;
     FP_KERNEL("k_step1_miller", s, k_step1_miller<<<grid_for(n, 64), 64, 0, s>>>((const g1a*)A, (const g2a*)v, K, R, h, (fq12*)out));
 }
-void final_exp_batch(const void* in, uint32_t n, size_t stride, void* out, void* ser, size_t ser_stride,
-                     cudaStream_t s) {
-    if (n) FP_KERNEL("k_final_exp", s, k_final_exp<<<grid_for(n, 64), 64, 0, s>>>((const fq12*)in, n, stride, (fq12*)out, (uint8_t*)ser,
-                                                       ser_stride));
-}
-
 }  // namespace fpk

@@ -47,90 +47,6 @@ __global__ void k_block_r(const uint8_t* hstmt, uint32_t k0, uint32_t K, uint32_
     bvec[(size_t)kl * R + a] = hash_to_fr("FP-r", 4, buf, 36, nullptr, 0, nullptr, 0);
 }
 
-// L_j.1 = <A_R, b_L>, R_j.1 = <A_L, b_R>: one term per (k, side, i)
-__global__ void __launch_bounds__(64) k_sparse_terms(const g1a* A, const fr* bvec, uint32_t K, uint32_t R, uint32_t h,
-                                                     g1j* out) {
-    uint64_t t = gtid();
-    if (t >= (uint64_t)K * 2 * h) return;
-    uint64_t k = t / (2 * h);
-    uint32_t r = (uint32_t)(t % (2 * h)), side = r / h, i = r % h;
-    fr sc = bvec[k * R + (side == 0 ? i : h + i)];
-    g1j res;
-    if (fr_is_zero(sc)) {
-        jac_set_inf(res);
-    } else {
-        uint32_t kw[8];
-        fr_canon_words(kw, sc);
-        res = g1_mul(A[k * R + (side == 0 ? h + i : i)], kw);
-    }
-    out[t] = res;
-}
-
-// Round j's two independent batches in one launch: blocks [0, nb_ml) run the Miller loops of
-// k_step1_miller's pairs, the remaining blocks the sparse G1 terms of k_sparse_terms.
-__global__ void __launch_bounds__(64) k_round_terms(const g1a* A, const g2a* v, const fr* bvec, uint32_t K,
-                                                    uint32_t R, uint32_t h, uint32_t nb_ml, fq12* ml_out,
-                                                    g1j* sp_out) {
-    const bool ml = blockIdx.x < nb_ml;
-    uint64_t t = (uint64_t)(ml ? blockIdx.x : blockIdx.x - nb_ml) * blockDim.x + threadIdx.x;
-    if (t >= (uint64_t)K * 2 * h) return;
-    uint64_t k = t / (2 * h);
-    uint32_t r = (uint32_t)(t % (2 * h)), side = r / h, i = r % h;
-    const g1a* Ak = A + k * R;
-    if (ml) {
-        const g2a* vk = v + k * R;
-        ml_out[t] = side == 0 ? miller_loop(Ak[h + i], vk[i]) : miller_loop(Ak[i], vk[h + i]);
-        return;
-    }
-    fr sc = bvec[k * R + (side == 0 ? i : h + i)];
-    g1j res;
-    if (fr_is_zero(sc)) {
-        jac_set_inf(res);
-    } else {
-        uint32_t kw[8];
-        fr_canon_words(kw, sc);
-        res = g1_mul(Ak[side == 0 ? h + i : i], kw);
-    }
-    sp_out[t] = res;
-}
-
-// Round j's two independent batches in one launch, Miller loops on 8-lane groups: blocks
-// [0, nb_ml) hold 8 pairs each (one group per pair, group12.cuh), the remaining blocks the sparse G1
-// terms (one thread each).  Pair t = (k, side, i) as in k_step1_miller.
-__global__ void __launch_bounds__(64) k_round_terms_g(const g1a* A, const g2a* v, const fr* bvec, uint32_t K,
-                                                      uint32_t R, uint32_t h, uint32_t nb_ml, fq12* ml_out,
-                                                      g1j* sp_out) {
-    __shared__ GMill sm[8];
-    const uint64_t n = (uint64_t)K * 2 * h;
-    if (blockIdx.x < nb_ml) {
-        const int grp = threadIdx.x >> 3, lane = threadIdx.x & 7;
-        const uint64_t t0 = (uint64_t)blockIdx.x * 8 + grp;
-        const bool valid = t0 < n;
-        const uint64_t t = valid ? t0 : 0;
-        const uint64_t k = t / (2 * h);
-        const uint32_t r = (uint32_t)(t % (2 * h)), side = r / h, i = r % h;
-        const g1a* Ak = A + k * R;
-        const g2a* vk = v + k * R;
-        const fq2 f = side == 0 ? g_miller(sm[grp], lane, Ak[h + i], vk[i]) : g_miller(sm[grp], lane, Ak[i], vk[h + i]);
-        if (valid) g_store(ml_out[t], lane, f);
-        return;
-    }
-    uint64_t t = (uint64_t)(blockIdx.x - nb_ml) * blockDim.x + threadIdx.x;
-    if (t >= n) return;
-    uint64_t k = t / (2 * h);
-    uint32_t r = (uint32_t)(t % (2 * h)), side = r / h, i = r % h;
-    fr sc = bvec[k * R + (side == 0 ? i : h + i)];
-    g1j res;
-    if (fr_is_zero(sc)) {
-        jac_set_inf(res);
-    } else {
-        uint32_t kw[8];
-        fr_canon_words(kw, sc);
-        res = g1_mul(A[k * R + (side == 0 ? h + i : i)], kw);
-    }
-    sp_out[t] = res;
-}
-
 // Both folds of round j in one launch: blocks [0, nb_g2) fold v, the remaining blocks fold A and b.
 __global__ void __launch_bounds__(64) k_fold(g1a* A, g2a* v, fr* bvec, const fr* x_mont, const fr* xinv_mont,
                                              uint32_t K, uint32_t R, uint32_t h, uint32_t nb_g2) {
@@ -151,7 +67,7 @@ __global__ void __launch_bounds__(64) k_fold(g1a* A, g2a* v, fr* bvec, const fr*
     }
 }
 
-// the G1 parts of round j's record (the GT parts are written by k_final_exp_g)
+// the G1 parts of round j's record (the GT parts are written by the final exponentiation)
 __global__ void __launch_bounds__(64) k_round_g1_out(const g1j* sp, uint32_t K, int j, uint8_t* blocks,
                                                      size_t bopen_len) {
     uint64_t t = gtid();
@@ -166,38 +82,6 @@ union FoldSmem {
     GEc<fq2> g2[8];
     GEc<fq> g1[8];
 };
-__global__ void __launch_bounds__(64) k_fold_grp(g1a* A, g2a* v, fr* bvec, const fr* x_mont, const fr* xinv_mont,
-                                                 uint32_t K, uint32_t R, uint32_t h, uint32_t nb2) {
-    __shared__ FoldSmem sm;
-    const int grp = threadIdx.x >> 3, lane = threadIdx.x & 7;
-    const bool g2 = blockIdx.x < nb2;
-    const uint64_t t0 = (uint64_t)(g2 ? blockIdx.x : blockIdx.x - nb2) * 8 + grp;
-    const bool valid = t0 < (uint64_t)K * h;
-    const uint64_t t = valid ? t0 : 0;
-    const uint64_t k = t / h;
-    const uint32_t i = (uint32_t)(t % h);
-    const uint64_t lo = k * R + i, hi = k * R + h + i;
-    uint32_t kw[8];
-    if (g2) {
-        fr_canon_words(kw, xinv_mont[k]);
-        const GPt<fq2> r = gec_add(sm.g2[grp], lane, gec_g2_mul_proj(sm.g2[grp], lane, v[hi], kw),
-                                   gec_from_affine_or_inf(v[lo].x, v[lo].y));
-        g2a o;
-        gec_to_affine(o.x, o.y, r);
-        if (valid && lane == 0) v[lo] = o;
-    } else {
-        fr_canon_words(kw, x_mont[k]);
-        const GPt<fq> r = gec_add(sm.g1[grp], lane, gec_g1_mul_proj(sm.g1[grp], lane, A[hi], kw),
-                                  gec_from_affine_or_inf(A[lo].x, A[lo].y));
-        g1a o;
-        gec_to_affine(o.x, o.y, r);
-        if (valid && lane == 0) {
-            A[lo] = o;
-            bvec[lo] = fr_add(bvec[lo], fr_mul(bvec[hi], xinv_mont[k]));
-        }
-    }
-}
-
 // Both folds of round j for few points: blocks [0, nb2) fold 4 points of v each (one warp per point,
 // group_ec.cuh GEcW), the remaining blocks 16 points of A (8-lane groups) and the entries of b.
 union FoldSmemW {
@@ -274,34 +158,6 @@ __global__ void __launch_bounds__(128) k_sparse_g(const g1a* A, const fr* bvec, 
     }
 }
 
-// after the reductions: GT = final exponentiation of the Miller product, G1 part to affine;
-// written to round j's record of block k: L_j.T | L_j.1 | R_j.T | R_j.1
-__global__ void __launch_bounds__(64) k_round_out(const fq12* ml, const g1j* sp, uint32_t K, int j, uint8_t* blocks,
-                                                  size_t bopen_len) {
-    uint64_t t = gtid();
-    if (t >= (uint64_t)K * 2) return;
-    uint64_t k = t >> 1;
-    uint32_t side = (uint32_t)(t & 1);
-    uint8_t* rec = blocks + k * bopen_len + (size_t)(j - 1) * ROUND_BYTES + side * (GT_SER + G1_SER);
-    fq12_to_be(rec, final_exp(ml[t]));
-    g1a_to_be(rec + GT_SER, g1_affine(sp[t]));
-}
-
-// x_j = HFr'("FP-x", x_{j-1} || L_j || R_j) (x_0 empty), re-hashed while 0; x_j^{-1}
-__global__ void k_challenge(const uint8_t* blocks, size_t bopen_len, uint32_t K, int j, uint8_t* xprev, fr* x_mont,
-                            fr* xinv_mont, fr* xinv_all, int log_r) {
-    uint64_t k = gtid();
-    if (k >= K) return;
-    const uint8_t* rec = blocks + k * bopen_len + (size_t)(j - 1) * ROUND_BYTES;
-    uint8_t* xp = xprev + k * 32;
-    fr x = hash_to_fr_nonzero("FP-x", 4, xp, j > 1 ? 32 : 0, rec, ROUND_BYTES, nullptr, 0);
-    fr xi = fr_inv(x);
-    x_mont[k] = x;
-    xinv_mont[k] = xi;
-    xinv_all[k * log_r + (j - 1)] = xi;
-    fr_to_be(xp, x);
-}
-
 // the same with the two SHA-256 halves of HFr on two lanes of a warp per block (they are
 // independent); lane 0 finishes (a zero challenge falls back to the serial re-hash)
 __global__ void __launch_bounds__(64) k_challenge2(const uint8_t* blocks, size_t bopen_len, uint32_t K, int j,
@@ -332,34 +188,6 @@ __global__ void __launch_bounds__(64) k_challenge2(const uint8_t* blocks, size_t
         xinv_all[k * log_r + (j - 1)] = xi;
         fr_to_be(xp, x);
     }
-}
-
-// A_j = A_L o A_R^{x_j};  b_j = b_L + b_R / x_j
-__global__ void __launch_bounds__(64) k_fold_g1(g1a* A, fr* bvec, const fr* x_mont, const fr* xinv_mont, uint32_t K,
-                                                uint32_t R, uint32_t h) {
-    uint64_t t = gtid();
-    if (t >= (uint64_t)K * h) return;
-    uint64_t k = t / h;
-    uint32_t i = (uint32_t)(t % h);
-    uint64_t lo = k * R + i, hi = k * R + h + i;
-    uint32_t kw[8];
-    fr_canon_words(kw, x_mont[k]);
-    g1j s = g1_madd(g1_mul(A[hi], kw), A[lo]);
-    A[lo] = g1_affine(s);
-    bvec[lo] = fr_add(bvec[lo], fr_mul(bvec[hi], xinv_mont[k]));
-}
-
-// v_j = v_L o v_R^{1/x_j}
-__global__ void __launch_bounds__(64) k_fold_g2(g2a* v, const fr* xinv_mont, uint32_t K, uint32_t R, uint32_t h) {
-    uint64_t t = gtid();
-    if (t >= (uint64_t)K * h) return;
-    uint64_t k = t / h;
-    uint32_t i = (uint32_t)(t % h);
-    uint64_t lo = k * R + i, hi = k * R + h + i;
-    uint32_t kw[8];
-    fr_canon_words(kw, xinv_mont[k]);
-    g2j s = g2_madd(g2_mul(v[hi], kw), v[lo]);
-    v[lo] = g2_affine(s);
 }
 
 // W = sum_i q_i g2^{beta^i}: one term per (k, i < 2R), padding terms are zero
@@ -499,15 +327,6 @@ void step1_sparse_terms(const void* A, const void* bvec, uint32_t k0, uint32_t K
     FP_KERNEL("k_sparse_g", s, k_sparse_g<<<(unsigned)(((uint64_t)K * cmax + 15) / 16), 128, 0, s>>>(
                                    (const g1a*)A, (const fr*)bvec, k0, K, R, h, b, cmax, (g1j*)out));
 }
-void step1_round_out(const void* ml, const void* sp, uint32_t K, int j, void* blocks, size_t bopen_len,
-                     cudaStream_t s) {
-    // GT parts: one 8-lane group per final exponentiation; G1 parts: one thread each
-    final_exp_group(ml, 2 * K, nullptr, (uint8_t*)blocks + (size_t)(j - 1) * ROUND_BYTES, 2, bopen_len,
-                    GT_SER + G1_SER, s);
-    FP_KERNEL("k_round_g1_out", s, k_round_g1_out<<<grid_for((uint64_t)K * 2, 64), 64, 0, s>>>((const g1j*)sp, K, j,
-                                                                                          (uint8_t*)blocks,
-                                                                                          bopen_len));
-}
 void step1_gt_out(const void* ml, uint32_t K, int j, void* blocks, size_t bopen_len, cudaStream_t s) {
     final_exp_group(ml, 2 * K, nullptr, (uint8_t*)blocks + (size_t)(j - 1) * ROUND_BYTES, 2, bopen_len,
                     GT_SER + G1_SER, s);
@@ -517,24 +336,11 @@ void step1_g1_out(const void* sp, uint32_t K, int j, void* blocks, size_t bopen_
                                                                                           (uint8_t*)blocks,
                                                                                           bopen_len));
 }
-void step1_round_out_serial(const void* ml, const void* sp, uint32_t K, int j, void* blocks, size_t bopen_len,
-                            cudaStream_t s) {
-    FP_KERNEL("k_round_out", s, k_round_out<<<grid_for((uint64_t)K * 2, 64), 64, 0, s>>>((const fq12*)ml, (const g1j*)sp, K, j,
-                                                            (uint8_t*)blocks, bopen_len));
-}
 void step1_challenge(void* blocks, size_t bopen_len, uint32_t K, int j, void* xprev, void* x_mont, void* xinv_mont,
                      void* xinv_all, int log_r, cudaStream_t s) {
     FP_KERNEL("k_challenge2", s, k_challenge2<<<(K + 1) / 2, 64, 0, s>>>((const uint8_t*)blocks, bopen_len, K, j,
                                                                          (uint8_t*)xprev, (fr*)x_mont, (fr*)xinv_mont,
                                                                          (fr*)xinv_all, log_r));
-}
-void step1_fold_g1(void* A, void* bvec, const void* x_mont, const void* xinv_mont, uint32_t K, uint32_t R,
-                   uint32_t h, cudaStream_t s) {
-    FP_KERNEL("k_fold_g1", s, k_fold_g1<<<grid_for((uint64_t)K * h, 64), 64, 0, s>>>((g1a*)A, (fr*)bvec, (const fr*)x_mont,
-                                                          (const fr*)xinv_mont, K, R, h));
-}
-void step1_fold_g2(void* v, const void* xinv_mont, uint32_t K, uint32_t R, uint32_t h, cudaStream_t s) {
-    FP_KERNEL("k_fold_g2", s, k_fold_g2<<<grid_for((uint64_t)K * h, 64), 64, 0, s>>>((g2a*)v, (const fr*)xinv_mont, K, R, h));
 }
 void step1_kzg(const void* A, const void* v, const void* xprev, const void* xinv_all, uint32_t K, uint32_t R,
                int log_r, void* blocks, size_t bopen_len, void* pcoef, void* q_canon, cudaStream_t s) {
@@ -561,14 +367,6 @@ void step1_w_terms(const void* g2pow, const void* q_canon, uint32_t K, uint32_t 
 }  // namespace fpk
 
 namespace fpk {
-void step1_round_terms(const void* A, const void* v, const void* bvec, uint32_t K, uint32_t R, uint32_t h,
-                       void* ml_out, void* sp_out, cudaStream_t s) {
-    uint64_t n = (uint64_t)K * 2 * h;
-    uint32_t nb_ml = (uint32_t)((n + 7) / 8), nb_sp = grid_for(n, 64);
-    FP_KERNEL("k_round_terms_g", s,
-              k_round_terms_g<<<nb_ml + nb_sp, 64, 0, s>>>((const g1a*)A, (const g2a*)v, (const fr*)bvec, K, R, h,
-                                                           nb_ml, (fq12*)ml_out, (g1j*)sp_out));
-}
 uint64_t step1_miller_g(const void* A, const void* v, uint32_t K, uint32_t R, uint32_t h, void* ml_out,
                         cudaStream_t s) {
     uint64_t n = (uint64_t)K * 2 * h;

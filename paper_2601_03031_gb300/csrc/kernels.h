@@ -49,14 +49,10 @@ void fr_serialize(const void* fr_mont, uint64_t n, void* out, cudaStream_t s);
 
 // ---- commit
 void load_vector(const void* m_limbs, uint64_t n, void* m_canon, void* m_mont, uint32_t* err, cudaStream_t s);
-// out[i] = m_canon[i] * lam[i mod M]  (row MSM terms)
-void commit_terms(const void* m_canon, const void* lam, uint64_t n, uint32_t M, void* out_g1j, cudaStream_t s);
 // out[j] = ML(rows[j], g2pow[2 j])
 void commit_miller(const void* rows_g1a, const void* g2pow, uint32_t R, void* out_fq12, cudaStream_t s);
 void final_exp_group(const void* in_fq12, uint32_t n, void* out_fq12, void* ser, uint32_t per, size_t stride_a,
                      size_t stride_b, cudaStream_t s);
-void final_exp_batch(const void* in_fq12, uint32_t n, size_t in_stride_elems, void* out_fq12, void* ser_out,
-                     size_t ser_stride, cudaStream_t s);
 
 // ---- Step 1 (FC.BOpen for all blocks at once)
 void step1_init(const void* rows_g1a, const void* g2pow, uint32_t K, uint32_t R, void* A, void* v, void* bvec,
@@ -75,8 +71,6 @@ void round_miller_w(const void* A, const void* v, uint32_t K, uint32_t R, uint32
 // dense per-block layout
 void step1_sparse_terms(const void* A, const void* bvec, uint32_t k0, uint32_t K, uint32_t R, uint32_t h, uint32_t b,
                         void* out_g1j, cudaStream_t s);
-void step1_round_terms(const void* A, const void* v, const void* bvec, uint32_t K, uint32_t R, uint32_t h,
-                       void* ml_out_fq12, void* sp_out_g1j, cudaStream_t s);
 // round j's Miller values (returns how many: K 2h, or fewer when pairs were grouped)
 uint64_t step1_miller_g(const void* A, const void* v, uint32_t K, uint32_t R, uint32_t h, void* ml_out,
                         cudaStream_t s);
@@ -84,13 +78,8 @@ void step1_g1_out(const void* sp_g1j, uint32_t K, int j, void* blocks, size_t bo
 void step1_gt_out(const void* ml_fq12, uint32_t K, int j, void* blocks, size_t bopen_len, cudaStream_t s);
 void step1_fold(void* A, void* v, void* bvec, const void* x_mont, const void* xinv_mont, uint32_t K, uint32_t R,
                 uint32_t h, cudaStream_t s);
-void step1_round_out(const void* ml_fq12, const void* sp_g1j, uint32_t K, int j, void* blocks, size_t bopen_len,
-                     cudaStream_t s);
 void step1_challenge(void* blocks, size_t bopen_len, uint32_t K, int j, void* xprev, void* x_mont, void* xinv_mont,
                      void* xinv_all, int log_r, cudaStream_t s);
-void step1_fold_g1(void* A, void* bvec, const void* x_mont, const void* xinv_mont, uint32_t K, uint32_t R,
-                   uint32_t h, cudaStream_t s);
-void step1_fold_g2(void* v, const void* xinv_mont, uint32_t K, uint32_t R, uint32_t h, cudaStream_t s);
 void step1_kzg(const void* A, const void* v, const void* xprev, const void* xinv_all, uint32_t K, uint32_t R,
                int log_r, void* blocks, size_t bopen_len, void* pcoef, void* q_canon, cudaStream_t s);
 void step1_w_terms(const void* g2pow, const void* q_canon, uint32_t K, uint32_t R, void* out_g2j, cudaStream_t s);
