@@ -65,3 +65,39 @@ def test_msm_window_model_and_argument_checks():
     out = ctypes.c_void_p()
     assert lib.fp_g1_bases_from_scalars(None, 5, 0, None, ctypes.byref(out)) == 1   # NULL scalars, n > 0
     assert lib.fp_g1_bases_from_scalars(None, 1 << 30, 0, None, ctypes.byref(out)) == 1
+
+
+def test_new_entry_points_reject_bad_arguments_without_device_work():
+    """The segment, evaluation and batch-verification entry points check their arguments on the host
+    (null handles, out-of-range splits) before any CUDA call."""
+    from paper_2601_03031_gb300 import build as B
+    lib = ctypes.CDLL(B.build())
+    vp, u32, u64 = ctypes.c_void_p, ctypes.c_uint32, ctypes.c_uint64
+    out = ctypes.c_void_p()
+    lib.vc_setup_split.argtypes = [u32, u32, u32, u64, vp, vp]
+    assert lib.vc_setup_split(0, 4, 1, 0, None, ctypes.byref(out)) == 1      # log_r < 1
+    assert lib.vc_setup_split(4, 0, 1, 0, None, ctypes.byref(out)) == 1      # log_c < 1
+    assert lib.vc_setup_split(14, 4, 1, 0, None, ctypes.byref(out)) == 1     # log_r > 13
+    assert lib.vc_setup_split(13, 14, 1, 0, None, ctypes.byref(out)) == 1    # N > 2^26
+    assert lib.vc_setup_split(3, 3, 9, 0, None, ctypes.byref(out)) == 1      # b > R
+    lib.vc_pp_view_split.argtypes = [vp, u32, u32, vp]
+    assert lib.vc_pp_view_split(None, 2, 2, ctypes.byref(out)) == 1
+    lib.vc_open_segments.argtypes = [vp, vp, u32, u32, u32, vp, vp]
+    assert lib.vc_open_segments(None, None, 1, 0, 0, None, ctypes.byref(out)) == 1
+    lib.vc_segment_proof_len.argtypes = [vp, u32, u32]
+    lib.vc_segment_proof_len.restype = ctypes.c_size_t
+    assert lib.vc_segment_proof_len(None, 1, 0) == 0
+    lib.vc_segment_proof_get.argtypes = [vp, u32, vp, ctypes.c_size_t, vp]
+    ln = ctypes.c_size_t()
+    assert lib.vc_segment_proof_get(None, 0, None, 0, ctypes.byref(ln)) == 1
+    lib.vc_verify_segment.argtypes = [vp, vp, u32, u32, vp, vp, ctypes.c_size_t, vp]
+    assert lib.vc_verify_segment(None, None, 1, 0, None, None, 0, None) == 1
+    lib.vc_eval_proof_len.argtypes = [vp]
+    lib.vc_eval_proof_len.restype = ctypes.c_size_t
+    assert lib.vc_eval_proof_len(None) == 0
+    lib.vc_eval_prove.argtypes = [vp, vp, vp, vp, vp, ctypes.c_size_t, vp]
+    assert lib.vc_eval_prove(None, None, None, None, None, 0, ctypes.byref(ln)) == 1
+    lib.vc_eval_verify.argtypes = [vp, vp, vp, vp, ctypes.c_size_t, vp]
+    assert lib.vc_eval_verify(None, None, None, None, 0, None) == 1
+    lib.vc_verify_all.argtypes = [vp, vp, vp, ctypes.c_int, vp, ctypes.c_int, vp, vp, vp]
+    assert lib.vc_verify_all(None, None, None, 0, None, 0, None, None, None) == 1
