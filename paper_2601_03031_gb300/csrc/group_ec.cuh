@@ -15,17 +15,26 @@
 // barrier of the lanes of a warp (the groups of a warp run the same instruction stream)
 FPG_DEV void gsync() { __syncwarp(); }
 
+// The formulas' additions are called out of line: inlined, the linear combinations of a doubling
+// and an addition outgrow the instruction cache, and instruction fetch then stalls every lane.
+static __device__ __noinline__ fq e_add(fq a, fq b) { return fq_add(a, b); }
+static __device__ __noinline__ fq e_sub(fq a, fq b) { return fq_sub(a, b); }
+static __device__ __noinline__ fq e_dbl(fq a) { return fq_dbl(a); }
+static __device__ __noinline__ fq2 e_add(fq2 a, fq2 b) { return fq2_add(a, b); }
+static __device__ __noinline__ fq2 e_sub(fq2 a, fq2 b) { return fq2_sub(a, b); }
+static __device__ __noinline__ fq2 e_dbl(fq2 a) { return fq2_dbl(a); }
+
 template <typename F> struct GPt { F X, Y, Z; };
 template <typename F> struct GEc {
     F sc[8];          // products of the current phase
     GPt<F> tab[16];   // subset sums of the split bases
 };
 
-FPG_DEV fq f_b3(const fq& a) {            // 3 b = 12 on G1
+static __device__ __noinline__ fq f_b3(fq a) {            // 3 b = 12 on G1
     const fq t = fq_add(fq_dbl(a), a);
     return fq_dbl(fq_dbl(t));
 }
-FPG_DEV fq2 f_b3(const fq2& a) {          // 3 b' = 12 (1 + u) on the twist
+static __device__ __noinline__ fq2 f_b3(fq2 a) {          // 3 b' = 12 (1 + u) on the twist
     const fq2 x = fq2_mul_xi(a);
     const fq2 t = fq2_add(fq2_dbl(x), x);
     return fq2_dbl(fq2_dbl(t));
@@ -54,19 +63,19 @@ FPG_NOINL GPt<F> gec_add(GEc<F>& sm, int lane, const GPt<F>& P, const GPt<F>& Q)
         case 0: a = P.X; b = Q.X; break;
         case 1: a = P.Y; b = Q.Y; break;
         case 2: a = P.Z; b = Q.Z; break;
-        case 3: a = f_add(P.X, P.Y); b = f_add(Q.X, Q.Y); break;
-        case 4: a = f_add(P.Y, P.Z); b = f_add(Q.Y, Q.Z); break;
-        default: a = f_add(P.X, P.Z); b = f_add(Q.X, Q.Z); break;
+        case 3: a = e_add(P.X, P.Y); b = e_add(Q.X, Q.Y); break;
+        case 4: a = e_add(P.Y, P.Z); b = e_add(Q.Y, Q.Z); break;
+        default: a = e_add(P.X, P.Z); b = e_add(Q.X, Q.Z); break;
     }
     gec_phase(sm, lane, a, b);
     const F t0 = sm.sc[0], t1 = sm.sc[1], t2 = sm.sc[2];
-    const F t3 = f_sub(sm.sc[3], f_add(t0, t1));
-    const F t4 = f_sub(sm.sc[4], f_add(t1, t2));
-    const F y3 = f_b3(f_sub(sm.sc[5], f_add(t0, t2)));
-    const F x3 = f_add(f_dbl(t0), t0);
+    const F t3 = e_sub(sm.sc[3], e_add(t0, t1));
+    const F t4 = e_sub(sm.sc[4], e_add(t1, t2));
+    const F y3 = f_b3(e_sub(sm.sc[5], e_add(t0, t2)));
+    const F x3 = e_add(e_dbl(t0), t0);
     const F bt2 = f_b3(t2);
-    const F z3 = f_add(t1, bt2);
-    const F u1 = f_sub(t1, bt2);
+    const F z3 = e_add(t1, bt2);
+    const F u1 = e_sub(t1, bt2);
     switch (lane) {
         case 0: a = t4; b = y3; break;
         case 1: a = t3; b = u1; break;
@@ -77,9 +86,9 @@ FPG_NOINL GPt<F> gec_add(GEc<F>& sm, int lane, const GPt<F>& P, const GPt<F>& Q)
     }
     gec_phase(sm, lane, a, b);
     GPt<F> r;
-    r.X = f_sub(sm.sc[1], sm.sc[0]);
-    r.Y = f_add(sm.sc[3], sm.sc[2]);
-    r.Z = f_add(sm.sc[5], sm.sc[4]);
+    r.X = e_sub(sm.sc[1], sm.sc[0]);
+    r.Y = e_add(sm.sc[3], sm.sc[2]);
+    r.Z = e_add(sm.sc[5], sm.sc[4]);
     return r;
 }
 
@@ -95,10 +104,10 @@ FPG_NOINL GPt<F> gec_dbl(GEc<F>& sm, int lane, const GPt<F>& P) {
     }
     gec_phase(sm, lane, a, b);
     const F t0 = sm.sc[0], t1 = sm.sc[1], xy = sm.sc[3];
-    const F z8 = f_dbl(f_dbl(f_dbl(t0)));
+    const F z8 = e_dbl(e_dbl(e_dbl(t0)));
     const F bt2 = f_b3(sm.sc[2]);
-    const F y3a = f_add(t0, bt2);
-    const F t0p = f_sub(t0, f_add(f_dbl(bt2), bt2));
+    const F y3a = e_add(t0, bt2);
+    const F t0p = e_sub(t0, e_add(e_dbl(bt2), bt2));
     switch (lane) {
         case 0: a = bt2; b = z8; break;
         case 1: a = t1; b = z8; break;
@@ -107,8 +116,8 @@ FPG_NOINL GPt<F> gec_dbl(GEc<F>& sm, int lane, const GPt<F>& P) {
     }
     gec_phase(sm, lane, a, b);
     GPt<F> r;
-    r.X = f_dbl(sm.sc[3]);
-    r.Y = f_add(sm.sc[0], sm.sc[2]);
+    r.X = e_dbl(sm.sc[3]);
+    r.Y = e_add(sm.sc[0], sm.sc[2]);
     r.Z = sm.sc[1];
     return r;
 }
@@ -260,19 +269,19 @@ FPG_NOINL GPt<fq2> gecw_add(GEcW& sm, int L, const GPt<fq2>& P, const GPt<fq2>& 
             case 0: a = P.X; b = Q.X; break;
             case 1: a = P.Y; b = Q.Y; break;
             case 2: a = P.Z; b = Q.Z; break;
-            case 3: a = f_add(P.X, P.Y); b = f_add(Q.X, Q.Y); break;
-            case 4: a = f_add(P.Y, P.Z); b = f_add(Q.Y, Q.Z); break;
-            default: a = f_add(P.X, P.Z); b = f_add(Q.X, Q.Z); break;
+            case 3: a = e_add(P.X, P.Y); b = e_add(Q.X, Q.Y); break;
+            case 4: a = e_add(P.Y, P.Z); b = e_add(Q.Y, Q.Z); break;
+            default: a = e_add(P.X, P.Z); b = e_add(Q.X, Q.Z); break;
         }
     });
     const fq2 t0 = sm.sc[0], t1 = sm.sc[1], t2 = sm.sc[2];
-    const fq2 t3 = f_sub(sm.sc[3], f_add(t0, t1));
-    const fq2 t4 = f_sub(sm.sc[4], f_add(t1, t2));
-    const fq2 y3 = f_b3(f_sub(sm.sc[5], f_add(t0, t2)));
-    const fq2 x3 = f_add(f_dbl(t0), t0);
+    const fq2 t3 = e_sub(sm.sc[3], e_add(t0, t1));
+    const fq2 t4 = e_sub(sm.sc[4], e_add(t1, t2));
+    const fq2 y3 = f_b3(e_sub(sm.sc[5], e_add(t0, t2)));
+    const fq2 x3 = e_add(e_dbl(t0), t0);
     const fq2 bt2 = f_b3(t2);
-    const fq2 z3 = f_add(t1, bt2);
-    const fq2 u1 = f_sub(t1, bt2);
+    const fq2 z3 = e_add(t1, bt2);
+    const fq2 u1 = e_sub(t1, bt2);
     gecw_phase(sm, L, [&](int q, fq2& a, fq2& b) {
         switch (q) {
             case 0: a = t4; b = y3; break;
@@ -284,9 +293,9 @@ FPG_NOINL GPt<fq2> gecw_add(GEcW& sm, int L, const GPt<fq2>& P, const GPt<fq2>& 
         }
     });
     GPt<fq2> r;
-    r.X = f_sub(sm.sc[1], sm.sc[0]);
-    r.Y = f_add(sm.sc[3], sm.sc[2]);
-    r.Z = f_add(sm.sc[5], sm.sc[4]);
+    r.X = e_sub(sm.sc[1], sm.sc[0]);
+    r.Y = e_add(sm.sc[3], sm.sc[2]);
+    r.Z = e_add(sm.sc[5], sm.sc[4]);
     return r;
 }
 
@@ -301,10 +310,10 @@ FPG_NOINL GPt<fq2> gecw_dbl(GEcW& sm, int L, const GPt<fq2>& P) {
         }
     });
     const fq2 t0 = sm.sc[0], t1 = sm.sc[1], xy = sm.sc[3];
-    const fq2 z8 = f_dbl(f_dbl(f_dbl(t0)));
+    const fq2 z8 = e_dbl(e_dbl(e_dbl(t0)));
     const fq2 bt2 = f_b3(sm.sc[2]);
-    const fq2 y3a = f_add(t0, bt2);
-    const fq2 t0p = f_sub(t0, f_add(f_dbl(bt2), bt2));
+    const fq2 y3a = e_add(t0, bt2);
+    const fq2 t0p = e_sub(t0, e_add(e_dbl(bt2), bt2));
     gecw_phase(sm, L, [&](int q, fq2& a, fq2& b) {
         switch (q) {
             case 0: a = bt2; b = z8; break;
@@ -314,8 +323,8 @@ FPG_NOINL GPt<fq2> gecw_dbl(GEcW& sm, int L, const GPt<fq2>& P) {
         }
     });
     GPt<fq2> r;
-    r.X = f_dbl(sm.sc[3]);
-    r.Y = f_add(sm.sc[0], sm.sc[2]);
+    r.X = e_dbl(sm.sc[3]);
+    r.Y = e_add(sm.sc[0], sm.sc[2]);
     r.Z = sm.sc[1];
     return r;
 }
