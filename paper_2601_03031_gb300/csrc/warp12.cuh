@@ -322,7 +322,7 @@ struct WMill {
     fq g[12];       // f^2
     fq T[6];        // X, Y, Z
     fq Q[4];        // xQ, yQ
-    fq v[16];       // round results: T products, line helpers
+    fq v[28];       // round results: T products, line helpers; 16..27 round B's operands (block engine)
     fq l[6];        // line l0, l2, l3
     fq h[24];
     fq tm[72];      // per-term partial sums of the combines (block-wide engine)
@@ -433,6 +433,24 @@ FPG_NOINL void wm_dbl(WMill& S, const fq& m3x, const fq& y2) {
             fq acc = S.tm[L];
             for (int i = 1; i < 6; i++) acc = fq_add(acc, S.tm[12 * i + L]);
             S.g[L] = acc;
+        } else if (L >= 96 && L < 108) {
+            // beside the sums, warp 3 forms round B's operands from ZZ and YY (re, im each):
+            // 16: bz = b' ZZ = 4 (1 + u) ZZ, 18: YY - 9 bz, 20: YY + 9 bz, 22: l0 = YY - 3 bz,
+            // 24: 6 bz, 26: 18 bz (so that (6 bz)(18 bz) = 108 bz^2 is a product of round B)
+            const int u = L - 96, e = u & 1, kind = u >> 1;
+            const fq zr = S.p[61], zi = fq_dbl(S.p[62]);
+            const fq bze = fq_dbl(fq_dbl(e ? fq_add(zr, zi) : fq_sub(zr, zi)));
+            const fq yy = e ? fq_dbl(S.p[60]) : S.p[59];
+            const fq b3 = fq_add(fq_dbl(bze), bze);
+            const fq b9 = fq_add(fq_dbl(b3), b3);
+            fq r;
+            if (kind == 0) r = bze;
+            else if (kind == 1) r = fq_sub(yy, b9);
+            else if (kind == 2) r = fq_add(yy, b9);
+            else if (kind == 3) r = fq_sub(yy, b3);
+            else if (kind == 4) r = fq_dbl(b3);
+            else r = fq_add(fq_dbl(b3), fq_dbl(fq_dbl(b3)));
+            S.v[16 + u] = r;
         }
     } else if (L < 12) {                           // f^2, coefficient k, component e
         const int k = L >> 1, e = L & 1;
@@ -461,50 +479,79 @@ FPG_NOINL void wm_dbl(WMill& S, const fq& m3x, const fq& y2) {
     }
     wsync<NW>();
     // round B
-    if (L < 14) {
-        const fq* XX = S.v;
-        const fq* YY = S.v + 2;
-        const fq* ZZ = S.v + 4;
-        const fq* YZ = S.v + 6;
-        const fq* XY = S.v + 8;
-        // bz = b' Z^2 = 4 (1 + u) ZZ
-        fq bz[2], bz9[2], yp[2], ym[2];
-        bz[0] = fq_dbl(fq_dbl(fq_sub(ZZ[0], ZZ[1])));
-        bz[1] = fq_dbl(fq_dbl(fq_add(ZZ[0], ZZ[1])));
-        for (int e = 0; e < 2; e++) {
-            const fq b3 = fq_add(fq_dbl(bz[e]), bz[e]);
-            bz9[e] = fq_add(fq_dbl(b3), b3);
-            yp[e] = fq_add(YY[e], bz9[e]);
-            ym[e] = fq_sub(YY[e], bz9[e]);
+    if (NW == 4) {
+        if (L < 15) {
+            const fq* XX = S.v;
+            const fq* YY = S.v + 2;
+            const fq* YZ = S.v + 6;
+            const fq* XY = S.v + 8;
+            fq x, y;
+            if (L < 2) { x = XX[L]; y = m3x; }
+            else if (L < 4) { x = YZ[L - 2]; y = y2; }
+            else if (L < 7) kara_ops(x, y, XY, S.v + 18, L - 4);        // XY (YY - 9 bz)
+            else if (L < 9) sq_ops(x, y, S.v + 20, L - 7);              // (YY + 9 bz)^2
+            else if (L < 12) kara_ops(x, y, S.v + 24, S.v + 26, L - 9); // 108 bz^2
+            else kara_ops(x, y, YY, YZ, L - 12);                        // YY YZ
+            S.p[L] = fq_mul(x, y);
         }
-        fq x, y;
-        if (L < 2) { x = XX[L]; y = m3x; }
-        else if (L < 4) { x = YZ[L - 2]; y = y2; }
-        else if (L < 7) kara_ops(x, y, XY, ym, L - 4);
-        else if (L < 9) sq_ops(x, y, yp, L - 7);
-        else if (L < 11) sq_ops(x, y, bz, L - 9);
-        else kara_ops(x, y, YY, YZ, L - 11);
-        S.p[L] = fq_mul(x, y);
-    }
-    wsync<NW>();
-    if (L < 12) {
-        const int w = L >> 1, e = L & 1;
-        fq r;
-        if (w == 0) {                               // l0 = YY - 3 bz
-            const fq zz0 = S.v[4], zz1 = S.v[5];
-            const fq bze = fq_dbl(fq_dbl(e ? fq_add(zz0, zz1) : fq_sub(zz0, zz1)));
-            r = fq_sub(S.v[2 + e], fq_add(fq_dbl(bze), bze));
-            S.l[e] = r;
-        } else if (w == 1) {                        // l2 = m3x XX
-            S.l[2 + e] = S.p[e];
-        } else if (w == 2) {                        // l3 = y2 YZ
-            S.l[4 + e] = S.p[2 + e];
-        } else if (w == 3) {                        // X' = 2 XY (YY - 9 bz)
-            S.T[e] = fq_dbl(kara_part(&S.p[4], e));
-        } else if (w == 4) {                        // Y' = (YY + 9 bz)^2 - 108 bz^2
-            S.T[2 + e] = fq_sub(sq_part(&S.p[7], e), fq_mul_small(sq_part(&S.p[9], e), 108));
-        } else {                                    // Z' = 8 YY YZ
-            S.T[4 + e] = fq_dbl(fq_dbl(fq_dbl(kara_part(&S.p[11], e))));
+        wsync<NW>();
+        // the line (warp 0) and 2T (X' on warp 1, Y' on warp 2, Z' on warp 3)
+        const int w = L >> 5, pl = L & 31;
+        if (w == 0 && pl < 6) {
+            const int e = pl & 1, which = pl >> 1;                      // l0 = YY - 3 bz, l2, l3
+            S.l[pl] = which == 0 ? S.v[22 + e] : S.p[2 * (which - 1) + e];
+        } else if (w > 0 && pl < 2) {
+            const int e = pl;
+            if (w == 1) S.T[e] = fq_dbl(kara_part(&S.p[4], e));
+            else if (w == 2) S.T[2 + e] = fq_sub(sq_part(&S.p[7], e), kara_part(&S.p[9], e));
+            else S.T[4 + e] = fq_dbl(fq_dbl(fq_dbl(kara_part(&S.p[12], e))));
+        }
+    } else {
+        if (L < 14) {
+            const fq* XX = S.v;
+            const fq* YY = S.v + 2;
+            const fq* ZZ = S.v + 4;
+            const fq* YZ = S.v + 6;
+            const fq* XY = S.v + 8;
+            // bz = b' Z^2 = 4 (1 + u) ZZ
+            fq bz[2], bz9[2], yp[2], ym[2];
+            bz[0] = fq_dbl(fq_dbl(fq_sub(ZZ[0], ZZ[1])));
+            bz[1] = fq_dbl(fq_dbl(fq_add(ZZ[0], ZZ[1])));
+            for (int e = 0; e < 2; e++) {
+                const fq b3 = fq_add(fq_dbl(bz[e]), bz[e]);
+                bz9[e] = fq_add(fq_dbl(b3), b3);
+                yp[e] = fq_add(YY[e], bz9[e]);
+                ym[e] = fq_sub(YY[e], bz9[e]);
+            }
+            fq x, y;
+            if (L < 2) { x = XX[L]; y = m3x; }
+            else if (L < 4) { x = YZ[L - 2]; y = y2; }
+            else if (L < 7) kara_ops(x, y, XY, ym, L - 4);
+            else if (L < 9) sq_ops(x, y, yp, L - 7);
+            else if (L < 11) sq_ops(x, y, bz, L - 9);
+            else kara_ops(x, y, YY, YZ, L - 11);
+            S.p[L] = fq_mul(x, y);
+        }
+        wsync<NW>();
+        if (L < 12) {
+            const int w = L >> 1, e = L & 1;
+            fq r;
+            if (w == 0) {                               // l0 = YY - 3 bz
+                const fq zz0 = S.v[4], zz1 = S.v[5];
+                const fq bze = fq_dbl(fq_dbl(e ? fq_add(zz0, zz1) : fq_sub(zz0, zz1)));
+                r = fq_sub(S.v[2 + e], fq_add(fq_dbl(bze), bze));
+                S.l[e] = r;
+            } else if (w == 1) {                        // l2 = m3x XX
+                S.l[2 + e] = S.p[e];
+            } else if (w == 2) {                        // l3 = y2 YZ
+                S.l[4 + e] = S.p[2 + e];
+            } else if (w == 3) {                        // X' = 2 XY (YY - 9 bz)
+                S.T[e] = fq_dbl(kara_part(&S.p[4], e));
+            } else if (w == 4) {                        // Y' = (YY + 9 bz)^2 - 108 bz^2
+                S.T[2 + e] = fq_sub(sq_part(&S.p[7], e), fq_mul_small(sq_part(&S.p[9], e), 108));
+            } else {                                    // Z' = 8 YY YZ
+                S.T[4 + e] = fq_dbl(fq_dbl(fq_dbl(kara_part(&S.p[11], e))));
+            }
         }
     }
     wsync<NW>();
