@@ -51,6 +51,14 @@ def closed_form(s, k):
     return O.g1_mul(O.g1_gen(), sum(a * b for a, b in zip(s, k)) % R)
 
 
+def closed_form_np(s_np, k_np):
+    """closed_form for n x 4 little-endian uint64 arrays, read element by element from the bytes."""
+    ms, mk = memoryview(s_np.tobytes()), memoryview(k_np.tobytes())
+    fb = int.from_bytes
+    dot = sum(fb(ms[o:o + 32], "little") * fb(mk[o:o + 32], "little") for o in range(0, len(ms), 32))
+    return O.g1_mul(O.g1_gen(), dot % R)
+
+
 def neg_point(p: bytes) -> bytes:
     if p == bytes(96):
         return p
@@ -148,9 +156,19 @@ def test_msm_device_path_matches_host():
     assert bytes(out.cpu().numpy()) == F.msm_g1(bases, k, nb, 0)
 
 
-@pytest.mark.parametrize("log_n", [12, 16, 20])
+def test_msm_naive_n4096():
+    """2^12 terms (the smallest size of the MSM sweep, autotuned window) against the oracle's naive
+    per-term double-and-add MSM."""
+    n = 1 << 12
+    pts = oracle_points(13, n)
+    k = base_scalars(14, n)
+    bases = F.G1Bases(scalars=limbs(base_scalars(13, n)))
+    assert F.msm_g1(bases, limbs(k), 1, 0) == O.g1_msm(b"".join(pts), list(k))
+
+
+@pytest.mark.parametrize("log_n", [12, 16, 20, 24])
 def test_msm_closed_form_large(log_n):
-    """Sizes of the MSM sweep; the autotuner's choice is exercised at 2^16."""
+    """Sizes of the MSM sweep (2^24: its largest); the autotuner's choice is exercised at 2^16."""
     n = 1 << log_n
     s_np = I.fr_uniform(70 + log_n, n)
     k_np = I.fr_uniform(80 + log_n, n)
@@ -162,4 +180,4 @@ def test_msm_closed_form_large(log_n):
     out = torch.zeros(96, dtype=torch.uint8, device="cuda")
     F.msm_g1(bases, kd, 1, 0, None, out)
     torch.cuda.synchronize()
-    assert bytes(out.cpu().numpy()) == closed_form(I.to_ints(s_np), I.to_ints(k_np))
+    assert bytes(out.cpu().numpy()) == closed_form_np(s_np, k_np)

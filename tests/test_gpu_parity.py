@@ -2,11 +2,13 @@
 
 There is no floating point anywhere in the method, so the tolerance is zero: public parameters,
 commitments and every proof byte must be identical.  Small cases compare everything; the
-N = 2^16 cases (the benchmark workload) compare all shared Step-2 state and sampled Step-1
-blocks / proofs, and check commitments against the trapdoor closed form.
+N = 2^16 and N = 2^20 cases compare all shared Step-2 state and sampled Step-1 blocks / proofs,
+and check commitments against the trapdoor closed form.
 """
 import functools
+import os
 import random
+from concurrent.futures import ThreadPoolExecutor
 
 import numpy as np
 import pytest
@@ -167,9 +169,10 @@ def test_n16_commit_closed_form(dist):
     assert cm.get() == row_closed_form(opp, I.to_ints(m))
 
 
-@pytest.mark.parametrize("b,blocks", [(256, [0]), (1, [0, 77, 255])])
-def test_n16_prove_all_sampled(b, blocks):
-    pp, opp, m, cm = n16("uniform")
+@pytest.mark.parametrize("b,blocks,dist", [(256, [0], "uniform"), (1, [0, 77, 255], "uniform"), (256, [0], "u32"),
+                                          (1, [0, 255], "u32")])
+def test_n16_prove_all_sampled(b, blocks, dist):
+    pp, opp, m, cm = n16(dist)
     C, rows = cm.get()
     pf = F.Proofs(pp, cm, b)
     pr = O.Prover(opp, m.tobytes(), C, rows, b)
@@ -214,3 +217,62 @@ def test_prove_one_n16_sampled():
         assert O.verify(opp, C, b, i, vals[i], one)
     with pytest.raises(F.FlexProofsError):
         F.vc_prove_one(pp, cm, 1, pp.N)
+
+
+# ------------------------------------------------------------------ N = 2^20, b = 1024, 256, 16, 1
+# Sampled Step-1 blocks per b (first, interior and last blocks; K = 1, 4, 64, 1024).
+N20_BLOCKS = {1024: [0], 256: [3], 16: [0, 37, 63], 1: [0, 511, 1023]}
+
+
+@functools.lru_cache(maxsize=None)
+def n20():
+    log_n, seed = 20, 0
+    pp, opp = gpu_pp(log_n, seed), oracle_pp(log_n, seed)
+    m = vec(log_n, seed + 1)
+    return pp, opp, m, F.Commitment(pp, m)
+
+
+@functools.lru_cache(maxsize=None)
+def n20_oracle():
+    """Oracle provers for every b: Step 2 in full and Step 1 on the sampled blocks, run on host
+    threads (each call releases the GIL; the jobs write disjoint parts of the provers)."""
+    pp, opp, m, cm = n20()
+    C, rows = cm.get()
+    provers = {b: O.Prover(opp, m.tobytes(), C, rows, b) for b in N20_BLOCKS}
+    jobs = [p.step2 for p in provers.values()]
+    jobs += [functools.partial(provers[b].block, k) for b, ks in N20_BLOCKS.items() for k in ks]
+    with ThreadPoolExecutor(max_workers=os.cpu_count() or 1) as ex:
+        for f in [ex.submit(j) for j in jobs]:
+            f.result()
+    return provers
+
+
+def test_n20_setup_and_commit_closed_form():
+    pp, opp, m, cm = n20()
+    assert pp.export() == opp.to_bytes()
+    assert cm.get() == row_closed_form(opp, I.to_ints(m))
+
+
+@pytest.mark.parametrize("b", sorted(N20_BLOCKS, reverse=True))
+def test_n20_prove_all_sampled(b):
+    """OpenAll at N = 2^20 in the benchmark's launch configuration: Step-2 state equal to the
+    oracle's, sampled proofs of the sampled blocks byte-identical and accepted by the oracle's
+    verifier, and every one of the 2^20 proofs accepted by the GPU batch verifier."""
+    pp, opp, m, cm = n20()
+    C, rows = cm.get()
+    pr = n20_oracle()[b]
+    pf = F.Proofs(pp, cm, b)
+    assert pf.step2_parts() == pr.step2_parts()
+    rnd = random.Random(b)
+    vals = I.to_ints(m)
+    items = []
+    for k in N20_BLOCKS[b]:
+        j = k * b + rnd.randrange(min(b, pp.R - k * b))
+        for a in (0, rnd.randrange(pp.M), pp.M - 1):
+            i = j * pp.M + a
+            e = pr.proof(i)
+            assert pf.proof(i) == e, i
+            items.append((i, vals[i], e))
+    assert all(O.verify_many(opp, C, b, items))
+    ok, n_ok = F.vc_verify_all(pf, C, m)
+    assert n_ok == pp.N and ok.all()
