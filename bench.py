@@ -60,8 +60,17 @@ CRITICAL_ROUNDS = {
     # G1 by 8-lane groups, 2-bit joint GLV windows: 13 table formulas + 64 x (2 doublings + 1 addition),
     # 2 phases each, then the addition of A_L and the conversion (longer than the warp G2 chain)
     "k_fold_w": (13 + 64 * 3) * 2 + 2 + 3,
+    # split folds: the G1 half chain (13 table formulas + 32 x (2 doublings + 1 addition)), the sum of
+    # the halves and the addition of A_L, 2 phases each, then the conversion (the G2 half chain:
+    # 11 + 32 x 2 + 2 formulas, is shorter)
+    "k_fold_s": (13 + 32 * 3 + 2) * 2 + 3,
+    # shifted bases beside the round: 64 G1 doublings of 2 phases, then the conversion
+    "k_fold_pre": 64 * 2 + 3,
     "k_sparse_g": (13 + 64 * 3) * 2 + 2,
 }
+
+
+FOLD_SPLIT_MAX = 256          # rounds with at most this many fold points use the split folds
 
 
 def step_units(log_n: int, b: int, msm_window: int) -> dict:
@@ -83,7 +92,8 @@ def step_units(log_n: int, b: int, msm_window: int) -> dict:
         "k_commit_miller_c": ("miller_loop", R if R <= 1024 else 0),
         "k_commit_miller_w": ("miller_loop", R if R > 1024 else 0),
         "k_sparse_g": ("g1_mul", sum(K * min(b, 2 * h) for h in hs)),
-        "k_fold_w": (("g1_mul", "g2_mul"), sum(K * h for h in hs if K * h <= 4096)),
+        "k_fold_s": (("g1_mul", "g2_mul"), sum(K * h for h in hs if K * h <= FOLD_SPLIT_MAX)),
+        "k_fold_w": (("g1_mul", "g2_mul"), sum(K * h for h in hs if FOLD_SPLIT_MAX < K * h <= 4096)),
         "k_fold": (("g1_mul", "g2_mul"), sum(K * h for h in hs if K * h > 4096)),
         "k_msm_chunk": ("msm_madd", 2 * R * M * W),
         "k_w_terms": ("g2_mul", K * (2 * R - 2)),

@@ -329,9 +329,9 @@ FPG_NOINL GPt<fq2> gecw_dbl(GEcW& sm, int L, const GPt<fq2>& P) {
     return r;
 }
 
-// k Q on G2 for a canonical k < r (GLS, as gec_g2_mul_proj), on one warp
-FPG_NOINL GPt<fq2> gecw_g2_mul_proj(GEcW& sm, int L, const g2a& Q, const uint32_t* k) {
-    uint32_t q1[7], q2[7], q3[7], d[4][2];
+// GLS digits of a canonical k < r: k = sum_i d_i |x|^i with 64-bit d_i (two words each)
+FPG_DEV void gls_digits(uint32_t (*d)[2], const uint32_t* k) {
+    uint32_t q1[7], q2[7], q3[7];
     div_by_const<2, 7>(q1, d[0], k, GLS_D, GLS_BARRETT);
     uint32_t t8[8];
     for (int i = 0; i < 8; i++) t8[i] = i < 7 ? q1[i] : 0;
@@ -340,6 +340,10 @@ FPG_NOINL GPt<fq2> gecw_g2_mul_proj(GEcW& sm, int L, const g2a& Q, const uint32_
     div_by_const<2, 7>(q3, d[2], t8, GLS_D, GLS_BARRETT);
     d[3][0] = q3[0];
     d[3][1] = q3[1];
+}
+
+// sm.tab[s] = sum_{i in s} (-1)^i psi^i(Q) for s < 16, on one warp
+FPG_DEV void gecw_g2_table(GEcW& sm, int L, const g2a& Q) {
     const bool inf = g2a_is_inf(Q);
     g2a b = Q;
     GPt<fq2> B[4];
@@ -362,8 +366,13 @@ FPG_NOINL GPt<fq2> gecw_g2_mul_proj(GEcW& sm, int L, const g2a& Q, const uint32_
         if (L == 0) sm.tab[s] = r;
         __syncwarp();
     }
+}
+
+// joint double-and-add over bits i0 + n - 1 .. i0 of the four digits on the table above:
+// sum_i 2^(i - i0) sum_j bit_i(d_j) (-1)^j psi^j(Q)
+FPG_DEV GPt<fq2> gecw_g2_bits(GEcW& sm, int L, const uint32_t (*d)[2], int i0, int n) {
     GPt<fq2> acc = gec_identity<fq2>();
-    for (int i = 63; i >= 0; i--) {
+    for (int i = i0 + n - 1; i >= i0; i--) {
         acc = gecw_dbl(sm, L, acc);
         const int s = bit_of(d[0], i) | (bit_of(d[1], i) << 1) | (bit_of(d[2], i) << 2) | (bit_of(d[3], i) << 3);
         acc = gecw_add(sm, L, acc, sm.tab[s]);
@@ -371,12 +380,33 @@ FPG_NOINL GPt<fq2> gecw_g2_mul_proj(GEcW& sm, int L, const g2a& Q, const uint32_
     return acc;
 }
 
-// k P on G1 for a canonical k < r with 2-bit joint windows of the GLV halves: table
-// tab[a + 4 b] = a P + b (-phi(P)) for a, b < 4, then 64 steps of two doublings and one addition
-// (384 formula phases instead of 512 for the bit-by-bit ladder)
-FPG_NOINL GPt<fq> gec_g1_mul_proj_w2(GEc<fq>& sm, int lane, const g1a& P, const uint32_t* k) {
-    uint32_t k1[5], k0[4];
-    div_by_const<4, 5>(k1, k0, k, GLV_D, GLV_BARRETT);
+// k Q on G2 for a canonical k < r (GLS, as gec_g2_mul_proj), on one warp
+FPG_NOINL GPt<fq2> gecw_g2_mul_proj(GEcW& sm, int L, const g2a& Q, const uint32_t* k) {
+    uint32_t d[4][2];
+    gls_digits(d, k);
+    gecw_g2_table(sm, L, Q);
+    return gecw_g2_bits(sm, L, d, 0, 64);
+}
+
+// Half of k Q on G2, on one warp: half 0 takes the low 32 bits of each GLS digit on the bases of
+// Q; half 1 the high 32 bits on the bases of Q2 = 2^32 Q (computed beforehand), so that
+// k Q = half 0 + half 1 and each half is a chain of 32 steps instead of 64.
+FPG_NOINL GPt<fq2> gecw_g2_mul_half(GEcW& sm, int L, const g2a& Qh, const uint32_t* k, int half) {
+    uint32_t d[4][2];
+    gls_digits(d, k);
+    gecw_g2_table(sm, L, Qh);
+    return gecw_g2_bits(sm, L, d, 32 * half, 32);
+}
+
+// 2^n Q (affine in, projective out) by n complete doublings, on one warp
+FPG_NOINL GPt<fq2> gecw_g2_dbl_n(GEcW& sm, int L, const g2a& Q, int n) {
+    GPt<fq2> acc = gec_from_affine_or_inf(Q.x, Q.y);
+    for (int i = 0; i < n; i++) acc = gecw_dbl(sm, L, acc);
+    return acc;
+}
+
+// tab[a + 4 b] = a P + b (-phi(P)) for a, b < 4 on an 8-lane group
+FPG_DEV void gec_g1_w2_table(GEc<fq>& sm, int lane, const g1a& P) {
     fq om;
     fq_from_const(om, GLV_OMEGA);
     const bool inf = g1a_is_inf(P);
@@ -401,12 +431,44 @@ FPG_NOINL GPt<fq> gec_g1_mul_proj_w2(GEc<fq>& sm, int lane, const g1a& P, const 
             gsync();
         }
     }
+}
+
+// Horner over the 2-bit joint windows w = w0 + n - 1 .. w0 of the GLV halves (window w: bits 2w,
+// 2w + 1 of k0 and k1) on the table above: two doublings and one addition per window
+FPG_DEV GPt<fq> gec_g1_w2_windows(GEc<fq>& sm, int lane, const uint32_t* k0, const uint32_t* k1, int w0, int n) {
     GPt<fq> acc = gec_identity<fq>();
-    for (int i = 63; i >= 0; i--) {
+    for (int i = w0 + n - 1; i >= w0; i--) {
         acc = gec_dbl(sm, lane, gec_dbl(sm, lane, acc));
         const int a = (k0[i >> 4] >> (2 * (i & 15))) & 3;
         const int bb = (k1[i >> 4] >> (2 * (i & 15))) & 3;
         acc = gec_add(sm, lane, acc, sm.tab[a + 4 * bb]);
     }
+    return acc;
+}
+
+// k P on G1 for a canonical k < r with 2-bit joint windows of the GLV halves: table
+// tab[a + 4 b] = a P + b (-phi(P)) for a, b < 4, then 64 steps of two doublings and one addition
+// (384 formula phases instead of 512 for the bit-by-bit ladder)
+FPG_NOINL GPt<fq> gec_g1_mul_proj_w2(GEc<fq>& sm, int lane, const g1a& P, const uint32_t* k) {
+    uint32_t k1[5], k0[4];
+    div_by_const<4, 5>(k1, k0, k, GLV_D, GLV_BARRETT);
+    gec_g1_w2_table(sm, lane, P);
+    return gec_g1_w2_windows(sm, lane, k0, k1, 0, 64);
+}
+
+// Half of k P on G1, on an 8-lane group: half 0 takes windows 0 .. 31 (bits 0 .. 63 of each GLV
+// half) on the bases of P; half 1 windows 32 .. 63 on the bases of P2 = 2^64 P (computed
+// beforehand), so that k P = half 0 + half 1 and each half is a chain of 32 steps instead of 64.
+FPG_NOINL GPt<fq> gec_g1_mul_half(GEc<fq>& sm, int lane, const g1a& Ph, const uint32_t* k, int half) {
+    uint32_t k1[5], k0[4];
+    div_by_const<4, 5>(k1, k0, k, GLV_D, GLV_BARRETT);
+    gec_g1_w2_table(sm, lane, Ph);
+    return gec_g1_w2_windows(sm, lane, k0, k1, 32 * half, 32);
+}
+
+// 2^n P (affine in, projective out) by n complete doublings, on an 8-lane group
+FPG_NOINL GPt<fq> gec_g1_dbl_n(GEc<fq>& sm, int lane, const g1a& P, int n) {
+    GPt<fq> acc = gec_from_affine_or_inf(P.x, P.y);
+    for (int i = 0; i < n; i++) acc = gec_dbl(sm, lane, acc);
     return acc;
 }

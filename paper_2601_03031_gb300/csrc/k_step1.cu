@@ -127,6 +127,99 @@ __global__ void __launch_bounds__(128) k_fold_w(g1a* A, g2a* v, fr* bvec, const 
     }
 }
 
+// Split folds for few points.  The scalar multiplications x_j A[h + i] and x_j^-1 v[h + i] are the
+// longest chain of a round after the challenge; the bases are known one round earlier, so
+// k_fold_pre, run beside the round's Miller loops and final exponentiations, forms
+// A2[t] = 2^64 A[h + i] and v2[t] = 2^32 v[h + i] (affine), and k_fold_s then runs each
+// multiplication as two chains of half the length: the low halves of the GLV / GLS digits on the
+// original bases, the high halves on the shifted ones (group_ec.cuh, *_mul_half), followed by
+// their sum and the addition of A[i] (v[i]).  Point t = (k, i < h) as in k_fold_w.
+__global__ void __launch_bounds__(128) k_fold_pre(const g1a* A, const g2a* v, g1a* A2, g2a* v2, uint32_t K,
+                                                  uint32_t R, uint32_t h, uint32_t nb2) {
+    __shared__ FoldSmemW sm;
+    if (blockIdx.x < nb2) {
+        const int w = threadIdx.x >> 5, L = threadIdx.x & 31;
+        const uint64_t t = (uint64_t)blockIdx.x * 4 + w;
+        if (t >= (uint64_t)K * h) return;                     // warp-uniform
+        const uint64_t hi = (t / h) * R + h + (uint32_t)(t % h);
+        const GPt<fq2> r = gecw_g2_dbl_n(sm.g2[w], L, v[hi], 32);
+        g2a o;
+        gec_to_affine(o.x, o.y, r);
+        if (L == 0) v2[t] = o;
+        return;
+    }
+    const int grp = threadIdx.x >> 3, lane = threadIdx.x & 7;
+    const uint64_t t0 = (uint64_t)(blockIdx.x - nb2) * 16 + grp;
+    const bool valid = t0 < (uint64_t)K * h;
+    const uint64_t t = valid ? t0 : 0;
+    const uint64_t hi = (t / h) * R + h + (uint32_t)(t % h);
+    const GPt<fq> r = gec_g1_dbl_n(sm.g1[grp], lane, A[hi], 64);
+    g1a o;
+    gec_to_affine(o.x, o.y, r);
+    if (valid && lane == 0) A2[t] = o;
+}
+
+// G2: two warps per point (blocks [0, nb2), two points each); G1: two 8-lane groups of one warp per
+// point (8 points per block).  Both chains of a point add their partial sums (each keeps the
+// same instruction stream; the half-0 chain stores the result).
+struct FoldSmemS {
+    union {
+        GEcW g2[4];
+        GEc<fq> g1[16];
+    } e;
+    union {
+        GPt<fq2> g2[4];
+        GPt<fq> g1[16];
+    } part;
+};
+__global__ void __launch_bounds__(128) k_fold_s(g1a* A, g2a* v, fr* bvec, const g1a* A2, const g2a* v2,
+                                                const fr* x_mont, const fr* xinv_mont, uint32_t K, uint32_t R,
+                                                uint32_t h, uint32_t nb2) {
+    __shared__ FoldSmemS sm;
+    uint32_t kw[8];
+    if (blockIdx.x < nb2) {
+        const int w = threadIdx.x >> 5, L = threadIdx.x & 31, half = w & 1;
+        const uint64_t t0 = (uint64_t)blockIdx.x * 2 + (w >> 1);
+        const bool valid = t0 < (uint64_t)K * h;
+        const uint64_t t = valid ? t0 : 0;                    // every warp reaches the barrier below
+        const uint64_t k = t / h;
+        const uint32_t i = (uint32_t)(t % h);
+        const uint64_t lo = k * R + i, hi = k * R + h + i;
+        fr_canon_words(kw, xinv_mont[k]);
+        const GPt<fq2> part = gecw_g2_mul_half(sm.e.g2[w], L, half ? v2[t] : v[hi], kw, half);
+        if (L == 0) sm.part.g2[w] = part;
+        __syncthreads();
+        GPt<fq2> r = gecw_add(sm.e.g2[w], L, part, sm.part.g2[w ^ 1]);
+        r = gecw_add(sm.e.g2[w], L, r, gec_from_affine_or_inf(v[lo].x, v[lo].y));
+        g2a o;
+        gec_to_affine(o.x, o.y, r);
+        __syncthreads();                                      // v[lo] read by both warps before the store
+        if (valid && half == 0 && L == 0) v[lo] = o;
+        return;
+    }
+    const int grp = threadIdx.x >> 3, lane = threadIdx.x & 7, half = grp & 1;
+    const uint64_t t0 = (uint64_t)(blockIdx.x - nb2) * 8 + (grp >> 1);
+    const bool valid = t0 < (uint64_t)K * h;
+    const uint64_t t = valid ? t0 : 0;
+    const uint64_t k = t / h;
+    const uint32_t i = (uint32_t)(t % h);
+    const uint64_t lo = k * R + i, hi = k * R + h + i;
+    fr_canon_words(kw, x_mont[k]);
+    const GPt<fq> part = gec_g1_mul_half(sm.e.g1[grp], lane, half ? A2[t] : A[hi], kw, half);
+    gsync();
+    if (lane == 0) sm.part.g1[grp] = part;
+    gsync();
+    GPt<fq> r = gec_add(sm.e.g1[grp], lane, part, sm.part.g1[grp ^ 1]);
+    r = gec_add(sm.e.g1[grp], lane, r, gec_from_affine_or_inf(A[lo].x, A[lo].y));
+    g1a o;
+    gec_to_affine(o.x, o.y, r);
+    gsync();                                                  // A[lo] read by both groups before the store
+    if (valid && half == 0 && lane == 0) {
+        A[lo] = o;
+        bvec[lo] = fr_add(bvec[lo], fr_mul(bvec[hi], xinv_mont[k]));
+    }
+}
+
 // L_j.1 and R_j.1 terms at the support of b only, one 8-lane group per term, for the blocks
 // k0 .. k0 + K - 1 (local index k - k0).  Block k's vector b is
 // non-zero only at its statement indices S_k = [k b, k b + |S_k|) folded mod the current length 2h:
@@ -377,8 +470,21 @@ uint64_t step1_miller_g(const void* A, const void* v, uint32_t K, uint32_t R, ui
     round_miller_w(A, v, K, R, h, ml_out, s);      // few pairs: one warp or block each, for latency
     return n;
 }
+void step1_fold_pre(const void* A, const void* v, void* A2, void* v2, uint32_t K, uint32_t R, uint32_t h,
+                    cudaStream_t s) {
+    const uint32_t n = K * h, nb2 = (n + 3) / 4, nb1 = (n + 15) / 16;
+    FP_KERNEL("k_fold_pre", s, k_fold_pre<<<nb2 + nb1, 128, 0, s>>>((const g1a*)A, (const g2a*)v, (g1a*)A2, (g2a*)v2,
+                                                                    K, R, h, nb2));
+}
 void step1_fold(void* A, void* v, void* bvec, const void* x_mont, const void* xinv_mont, uint32_t K, uint32_t R,
-                uint32_t h, cudaStream_t s) {
+                uint32_t h, const void* A2, const void* v2, cudaStream_t s) {
+    if (A2 && (uint64_t)K * h <= FOLD_SPLIT_MAX) {     // shifted bases ready: half-length chains
+        const uint32_t n = K * h, nb2 = (n + 1) / 2, nb1 = (n + 7) / 8;
+        FP_KERNEL("k_fold_s", s, k_fold_s<<<nb2 + nb1, 128, 0, s>>>((g1a*)A, (g2a*)v, (fr*)bvec, (const g1a*)A2,
+                                                                  (const g2a*)v2, (const fr*)x_mont,
+                                                                  (const fr*)xinv_mont, K, R, h, nb2));
+        return;
+    }
     if ((uint64_t)K * h <= 4096) {      // few points: a warp per G2 point, an 8-lane group per G1 point
         const uint32_t nb2 = (uint32_t)(((uint64_t)K * h + 3) / 4), nb1 = (uint32_t)(((uint64_t)K * h + 15) / 16);
         FP_KERNEL("k_fold_w", s, k_fold_w<<<nb2 + nb1, 128, 0, s>>>((g1a*)A, (g2a*)v, (fr*)bvec, (const fr*)x_mont,

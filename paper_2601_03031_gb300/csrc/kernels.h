@@ -76,8 +76,13 @@ uint64_t step1_miller_g(const void* A, const void* v, uint32_t K, uint32_t R, ui
                         cudaStream_t s);
 void step1_g1_out(const void* sp_g1j, uint32_t K, int j, void* blocks, size_t bopen_len, cudaStream_t s);
 void step1_gt_out(const void* ml_fq12, uint32_t K, int j, void* blocks, size_t bopen_len, cudaStream_t s);
+// Round j's folds.  With A2 / v2 (2^64 A[h + i] and 2^32 v[h + i] from step1_fold_pre, at most
+// FOLD_SPLIT_MAX points) each scalar multiplication runs as two half-length chains.
+constexpr uint32_t FOLD_SPLIT_MAX = 256;
+void step1_fold_pre(const void* A, const void* v, void* A2, void* v2, uint32_t K, uint32_t R, uint32_t h,
+                    cudaStream_t s);
 void step1_fold(void* A, void* v, void* bvec, const void* x_mont, const void* xinv_mont, uint32_t K, uint32_t R,
-                uint32_t h, cudaStream_t s);
+                uint32_t h, const void* A2, const void* v2, cudaStream_t s);
 void step1_challenge(void* blocks, size_t bopen_len, uint32_t K, int j, void* xprev, void* x_mont, void* xinv_mont,
                      void* xinv_all, int log_r, cudaStream_t s);
 void step1_kzg(const void* A, const void* v, const void* xprev, const void* xinv_all, uint32_t K, uint32_t R,

@@ -127,13 +127,13 @@ void* reduce_pairs(void* a, void* b, uint64_t n, uint64_t target, Red red, cudaS
 
 size_t bopen_len(uint32_t log_r) { return (size_t)log_r * ROUND_BYTES + G1_SER + 2 * G2_SER; }
 
-// Internal non-blocking streams: OpenAll's latency-bound Step 1 runs on two high-priority streams
-// (the round chain, and the sparse G1 terms that overlap it), the throughput-bound Step 2 on a
-// low-priority stream; all are forked from and joined back to the caller's stream with events
+// Internal non-blocking streams: OpenAll's latency-bound Step 1 runs on three high-priority
+// streams (the round chain, and beside it the sparse G1 terms and the shifted fold bases), the
+// throughput-bound Step 2 on a low-priority stream; all are forked from and joined back to the caller's stream with events
 // created per call.  Each caller stream (per device) gets its own set, so calls on different caller
 // streams run concurrently; past 256 caller streams the sets are shared (still correct, less
 // concurrent).
-struct Streams { cudaStream_t hi = nullptr, sp = nullptr, lo = nullptr; };
+struct Streams { cudaStream_t hi = nullptr, sp = nullptr, pre = nullptr, lo = nullptr; };
 struct StreamKey { int dev; cudaStream_t user; Streams set; };
 std::vector<StreamKey> g_sets;
 std::mutex g_aux_mu;
@@ -143,6 +143,7 @@ Streams make_set() {
     check(cudaDeviceGetStreamPriorityRange(&lo, &hi), "priority range");
     check(cudaStreamCreateWithPriority(&a.hi, cudaStreamNonBlocking, hi), "cudaStreamCreate");
     check(cudaStreamCreateWithPriority(&a.sp, cudaStreamNonBlocking, hi), "cudaStreamCreate");
+    check(cudaStreamCreateWithPriority(&a.pre, cudaStreamNonBlocking, hi), "cudaStreamCreate");
     check(cudaStreamCreateWithPriority(&a.lo, cudaStreamNonBlocking, lo), "cudaStreamCreate");
     return a;
 }
@@ -426,6 +427,7 @@ namespace {
 // outputs, the challenges and the fast-verification proof of v_l
 struct Step1Bufs {
     void *A, *v, *bvec, *xprev, *x_mont, *xinv_mont, *xinv_all, *ml, *ml2, *sp, *sp2, *pcoef, *q;
+    void *A2, *v2;                       // shifted fold bases of rounds with few points
     void *wt = nullptr, *wt2 = nullptr, *wscr = nullptr;
     MsmShape wsh{};
     bool w_msm = false;
@@ -448,6 +450,8 @@ Step1Bufs step1_bufs(const fp_pp* pp, uint32_t Kc, Alloc&& T) {
     B.sp2 = T((KR / 2 + 1) * G1J_BYTES);
     B.pcoef = T((size_t)Kc * (2 * R - 1) * FR_BYTES);
     B.q = T((size_t)Kc * 2 * R * FR_BYTES);
+    B.A2 = T((size_t)FOLD_SPLIT_MAX * G1A_BYTES);
+    B.v2 = T((size_t)FOLD_SPLIT_MAX * G2A_BYTES);
     // W proofs: one batched G2 MSM over the shared bases g2^{beta^i} when many blocks share them,
     // else one scalar multiplication per term and pairwise sums (with few batches the MSM's bucket
     // reduction runs nearly serially per window)
@@ -464,16 +468,23 @@ Step1Bufs step1_bufs(const fp_pp* pp, uint32_t Kc, Alloc&& T) {
 
 // FC.BOpen rounds (Sec. 3, Eq. folding) and the fast-verification proof of v_l for the Kc blocks
 // k0 .. k0 + Kc - 1 of size b, whose combined vectors are in B.bvec (their support is the block):
-// the round chain on s1, each round's G1 parts on s3 (joined before the challenge); the records go
-// to blocks1 (stride blen).  s3 must already be ordered after whatever filled B.bvec.
+// the round chain on s1, each round's G1 parts on s3 (joined before the challenge) and, in rounds
+// with few points, the shifted fold bases on s4 (joined before the fold); the records go to
+// blocks1 (stride blen).  s3 must already be ordered after whatever filled B.bvec.
 void step1_rounds(const fp_pp* pp, uint32_t k0, uint32_t Kc, uint32_t b, const Step1Bufs& B, uint8_t* blocks1,
-                  size_t blen, cudaStream_t s1, cudaStream_t s3) {
+                  size_t blen, cudaStream_t s1, cudaStream_t s3, cudaStream_t s4) {
     const uint32_t R = pp->R;
     const int lr = (int)pp->log_r;
-    cudaEvent_t ev_folded = new_event(), ev_sparse = new_event();
+    cudaEvent_t ev_folded = new_event(), ev_sparse = new_event(), ev_pre = new_event();
     for (int j = 1; j <= lr; j++) {
         const uint32_t h = R >> j;
         check(cudaEventRecord(ev_folded, s1), "event");
+        const bool split = (uint64_t)Kc * h <= FOLD_SPLIT_MAX;
+        if (split) {
+            check(cudaStreamWaitEvent(s4, ev_folded, 0), "wait");
+            step1_fold_pre(B.A, B.v, B.A2, B.v2, Kc, R, h, s4);
+            check(cudaEventRecord(ev_pre, s4), "event");
+        }
         check(cudaStreamWaitEvent(s3, ev_folded, 0), "wait");
         step1_sparse_terms(B.A, B.bvec, k0, Kc, R, h, b, B.sp, s3);
         void* spr = reduce_pairs(B.sp, B.sp2, (uint64_t)Kc * 2 * h, (uint64_t)Kc * 2, g1_pair_reduce, s3);
@@ -484,7 +495,9 @@ void step1_rounds(const fp_pp* pp, uint32_t k0, uint32_t Kc, uint32_t b, const S
         step1_gt_out(mlr, Kc, j, blocks1, blen, s1);
         check(cudaStreamWaitEvent(s1, ev_sparse, 0), "wait");
         step1_challenge(blocks1, blen, Kc, j, B.xprev, B.x_mont, B.xinv_mont, B.xinv_all, lr, s1);
-        step1_fold(B.A, B.v, B.bvec, B.x_mont, B.xinv_mont, Kc, R, h, s1);
+        if (split) check(cudaStreamWaitEvent(s1, ev_pre, 0), "wait");
+        step1_fold(B.A, B.v, B.bvec, B.x_mont, B.xinv_mont, Kc, R, h, split ? B.A2 : nullptr,
+                   split ? B.v2 : nullptr, s1);
     }
     step1_kzg(B.A, B.v, B.xprev, B.xinv_all, Kc, R, lr, blocks1, blen, B.pcoef, B.q, s1);
     uint8_t* w_out = blocks1 + (size_t)lr * ROUND_BYTES + G1_SER + G2_SER;
@@ -497,6 +510,7 @@ void step1_rounds(const fp_pp* pp, uint32_t k0, uint32_t Kc, uint32_t b, const S
     }
     cudaEventDestroy(ev_folded);
     cudaEventDestroy(ev_sparse);
+    cudaEventDestroy(ev_pre);
 }
 
 // OpenAll's work with Step 1 restricted to the blocks [k0, k0 + Kc) (all blocks: k0 = 0, Kc = K):
@@ -584,7 +598,7 @@ fp_proofs* prove_impl(const fp_pp* pp, const fp_commit* cm, uint32_t b, uint32_t
             check(cudaStreamWaitEvent(s3, ev_init, 0), "wait");
             step1_stmt_hash(cm->C_ser, cm->rows_ser, k0, Kc, R, b, hstmt, s3);
             step1_block_r(hstmt, k0, Kc, R, b, B.bvec, s3);
-            step1_rounds(pp, k0, Kc, b, B, blocks1, blen, s1, s3);
+            step1_rounds(pp, k0, Kc, b, B, blocks1, blen, s1, s3, st.pre);
             check(cudaEventRecord(ev_join1, s1), "event");
             check(cudaStreamWaitEvent(s, ev_join1, 0), "join");
             cudaEventDestroy(ev_init);
@@ -860,7 +874,7 @@ fp_status vc_eval_prove(const fp_pp* pp, const fp_commit* cm, const uint8_t* r, 
             eval_bvec(cm->C_ser, r_be, ln, proof + 32, Tm, R, r0, B.bvec, s1);
             check(cudaEventRecord(ev_bvec, s1), "event");
             check(cudaStreamWaitEvent(s3, ev_bvec, 0), "wait");
-            step1_rounds(pp, 0, 1, R, B, proof + 128, blen, s1, s3);
+            step1_rounds(pp, 0, 1, R, B, proof + 128, blen, s1, s3, st.pre);
             // step 3: PST.Eval of F = sum_j T_j f_j at r_R
             eval_ftable(cm->m_mont, Tm, R, M, F, s1);
             eval_pst_fold(F, r_mont, lc, q, proof, s1);
