@@ -60,12 +60,13 @@ CRITICAL_ROUNDS = {
     # G1 by 8-lane groups, 2-bit joint GLV windows: 13 table formulas + 64 x (2 doublings + 1 addition),
     # 2 phases each, then the addition of A_L and the conversion (longer than the warp G2 chain)
     "k_fold_w": (13 + 64 * 3) * 2 + 2 + 3,
-    # split folds: the G1 half chain (13 table formulas + 32 x (2 doublings + 1 addition)), the sum of
-    # the halves and the addition of A_L, 2 phases each, then the conversion (the G2 half chain:
-    # 11 + 32 x 2 + 2 formulas, is shorter)
-    "k_fold_s": (13 + 32 * 3 + 2) * 2 + 3,
-    # shifted bases beside the round: 64 G1 doublings of 2 phases, then the conversion
-    "k_fold_pre": 64 * 2 + 3,
+    # split folds in four parts (rounds of at most 128 points): the G1 quarter chain (13 table
+    # formulas + 16 x (2 doublings + 1 addition)), two levels of sums of the parts and the addition of
+    # A_L, 2 phases each, then the conversion (the G2 quarter chain, 11 + 16 x 2 + 3 formulas, is
+    # shorter)
+    "k_fold_s": (13 + 16 * 3 + 2 + 1) * 2 + 3,
+    # shifted bases beside the round: 3 x 32 G1 doublings of 2 phases, each followed by a conversion
+    "k_fold_pre": 96 * 2 + 3 * 3,
     "k_sparse_g": (13 + 64 * 3) * 2 + 2,
 }
 

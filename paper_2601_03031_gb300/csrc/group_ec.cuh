@@ -388,19 +388,19 @@ FPG_NOINL GPt<fq2> gecw_g2_mul_proj(GEcW& sm, int L, const g2a& Q, const uint32_
     return gecw_g2_bits(sm, L, d, 0, 64);
 }
 
-// Half of k Q on G2, on one warp: half 0 takes the low 32 bits of each GLS digit on the bases of
-// Q; half 1 the high 32 bits on the bases of Q2 = 2^32 Q (computed beforehand), so that
-// k Q = half 0 + half 1 and each half is a chain of 32 steps instead of 64.
-FPG_NOINL GPt<fq2> gecw_g2_mul_half(GEcW& sm, int L, const g2a& Qh, const uint32_t* k, int half) {
+// Part `part` of NP of k Q on G2, on one warp: bits [part 64/NP, (part + 1) 64/NP) of the four GLS
+// digits on the bases of Qp = 2^(64 part / NP) Q (computed beforehand), so that k Q is the sum of
+// the NP parts and each part is a chain of 64/NP steps instead of 64.
+template <int NP>
+FPG_NOINL GPt<fq2> gecw_g2_mul_part(GEcW& sm, int L, const g2a& Qp, const uint32_t* k, int part) {
     uint32_t d[4][2];
     gls_digits(d, k);
-    gecw_g2_table(sm, L, Qh);
-    return gecw_g2_bits(sm, L, d, 32 * half, 32);
+    gecw_g2_table(sm, L, Qp);
+    return gecw_g2_bits(sm, L, d, part * (64 / NP), 64 / NP);
 }
 
-// 2^n Q (affine in, projective out) by n complete doublings, on one warp
-FPG_NOINL GPt<fq2> gecw_g2_dbl_n(GEcW& sm, int L, const g2a& Q, int n) {
-    GPt<fq2> acc = gec_from_affine_or_inf(Q.x, Q.y);
+// 2^n P by n complete doublings, on one warp
+FPG_NOINL GPt<fq2> gecw_g2_dbl_n(GEcW& sm, int L, GPt<fq2> acc, int n) {
     for (int i = 0; i < n; i++) acc = gecw_dbl(sm, L, acc);
     return acc;
 }
@@ -456,19 +456,19 @@ FPG_NOINL GPt<fq> gec_g1_mul_proj_w2(GEc<fq>& sm, int lane, const g1a& P, const 
     return gec_g1_w2_windows(sm, lane, k0, k1, 0, 64);
 }
 
-// Half of k P on G1, on an 8-lane group: half 0 takes windows 0 .. 31 (bits 0 .. 63 of each GLV
-// half) on the bases of P; half 1 windows 32 .. 63 on the bases of P2 = 2^64 P (computed
-// beforehand), so that k P = half 0 + half 1 and each half is a chain of 32 steps instead of 64.
-FPG_NOINL GPt<fq> gec_g1_mul_half(GEc<fq>& sm, int lane, const g1a& Ph, const uint32_t* k, int half) {
+// Part `part` of NP of k P on G1, on an 8-lane group: 2-bit windows [part 64/NP, (part + 1) 64/NP)
+// of the GLV halves on the bases of Pp = 2^(128 part / NP) P (computed beforehand), so that k P is
+// the sum of the NP parts and each part is a chain of 64/NP steps instead of 64.
+template <int NP>
+FPG_NOINL GPt<fq> gec_g1_mul_part(GEc<fq>& sm, int lane, const g1a& Pp, const uint32_t* k, int part) {
     uint32_t k1[5], k0[4];
     div_by_const<4, 5>(k1, k0, k, GLV_D, GLV_BARRETT);
-    gec_g1_w2_table(sm, lane, Ph);
-    return gec_g1_w2_windows(sm, lane, k0, k1, 32 * half, 32);
+    gec_g1_w2_table(sm, lane, Pp);
+    return gec_g1_w2_windows(sm, lane, k0, k1, part * (64 / NP), 64 / NP);
 }
 
-// 2^n P (affine in, projective out) by n complete doublings, on an 8-lane group
-FPG_NOINL GPt<fq> gec_g1_dbl_n(GEc<fq>& sm, int lane, const g1a& P, int n) {
-    GPt<fq> acc = gec_from_affine_or_inf(P.x, P.y);
+// 2^n P by n complete doublings, on an 8-lane group
+FPG_NOINL GPt<fq> gec_g1_dbl_n(GEc<fq>& sm, int lane, GPt<fq> acc, int n) {
     for (int i = 0; i < n; i++) acc = gec_dbl(sm, lane, acc);
     return acc;
 }

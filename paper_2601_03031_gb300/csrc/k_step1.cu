@@ -129,92 +129,106 @@ __global__ void __launch_bounds__(128) k_fold_w(g1a* A, g2a* v, fr* bvec, const 
 
 // Split folds for few points.  The scalar multiplications x_j A[h + i] and x_j^-1 v[h + i] are the
 // longest chain of a round after the challenge; the bases are known one round earlier, so
-// k_fold_pre, run beside the round's Miller loops and final exponentiations, forms
-// A2[t] = 2^64 A[h + i] and v2[t] = 2^32 v[h + i] (affine), and k_fold_s then runs each
-// multiplication as two chains of half the length: the low halves of the GLV / GLS digits on the
-// original bases, the high halves on the shifted ones (group_ec.cuh, *_mul_half), followed by
-// their sum and the addition of A[i] (v[i]).  Point t = (k, i < h) as in k_fold_w.
+// k_fold_pre, run beside the round's Miller loops and final exponentiations, forms the shifted
+// bases 2^(128 p / NP) A[h + i] and 2^(64 p / NP) v[h + i] for p = 1 .. NP - 1 (affine, at
+// A2[(p - 1) FOLD_SPLIT_MAX + t]), and k_fold_s then runs each multiplication as NP chains of 1/NP
+// of the length, part p on the p-th shifted bases (group_ec.cuh, *_mul_part), followed by a tree
+// sum of the parts and the addition of A[i] (v[i]).  Point t = (k, i < h) as in k_fold_w.
+template <int NP>
 __global__ void __launch_bounds__(128) k_fold_pre(const g1a* A, const g2a* v, g1a* A2, g2a* v2, uint32_t K,
                                                   uint32_t R, uint32_t h, uint32_t nb2) {
     __shared__ FoldSmemW sm;
-    if (blockIdx.x < nb2) {
+    if (blockIdx.x < nb2) {                                   // one warp per G2 point
         const int w = threadIdx.x >> 5, L = threadIdx.x & 31;
         const uint64_t t = (uint64_t)blockIdx.x * 4 + w;
         if (t >= (uint64_t)K * h) return;                     // warp-uniform
         const uint64_t hi = (t / h) * R + h + (uint32_t)(t % h);
-        const GPt<fq2> r = gecw_g2_dbl_n(sm.g2[w], L, v[hi], 32);
-        g2a o;
-        gec_to_affine(o.x, o.y, r);
-        if (L == 0) v2[t] = o;
+        GPt<fq2> acc = gec_from_affine_or_inf(v[hi].x, v[hi].y);
+        for (int p = 1; p < NP; p++) {
+            acc = gecw_g2_dbl_n(sm.g2[w], L, acc, 64 / NP);
+            g2a o;
+            gec_to_affine(o.x, o.y, acc);
+            if (L == 0) v2[(p - 1) * FOLD_SPLIT_MAX + t] = o;
+        }
         return;
     }
-    const int grp = threadIdx.x >> 3, lane = threadIdx.x & 7;
+    const int grp = threadIdx.x >> 3, lane = threadIdx.x & 7;   // one 8-lane group per G1 point
     const uint64_t t0 = (uint64_t)(blockIdx.x - nb2) * 16 + grp;
     const bool valid = t0 < (uint64_t)K * h;
     const uint64_t t = valid ? t0 : 0;
     const uint64_t hi = (t / h) * R + h + (uint32_t)(t % h);
-    const GPt<fq> r = gec_g1_dbl_n(sm.g1[grp], lane, A[hi], 64);
-    g1a o;
-    gec_to_affine(o.x, o.y, r);
-    if (valid && lane == 0) A2[t] = o;
+    GPt<fq> acc = gec_from_affine_or_inf(A[hi].x, A[hi].y);
+    for (int p = 1; p < NP; p++) {
+        acc = gec_g1_dbl_n(sm.g1[grp], lane, acc, 128 / NP);
+        g1a o;
+        gec_to_affine(o.x, o.y, acc);
+        if (valid && lane == 0) A2[(p - 1) * FOLD_SPLIT_MAX + t] = o;
+    }
 }
 
-// G2: two warps per point (blocks [0, nb2), two points each); G1: two 8-lane groups of one warp per
-// point (8 points per block).  Both chains of a point add their partial sums (each keeps the
-// same instruction stream; the half-0 chain stores the result).
+// G2: NP warps per point (blocks [0, nb2), 4 / NP points each); G1: NP 8-lane groups of one warp per
+// point (16 / NP points per block).  The parts of a point are summed pairwise (every chain keeps the
+// same instruction stream and ends with the whole sum; part 0 stores the result).
 struct FoldSmemS {
     union {
         GEcW g2[4];
         GEc<fq> g1[16];
     } e;
     union {
-        GPt<fq2> g2[4];
-        GPt<fq> g1[16];
+        GPt<fq2> g2[2][4];
+        GPt<fq> g1[2][16];
     } part;
 };
+template <int NP>
 __global__ void __launch_bounds__(128) k_fold_s(g1a* A, g2a* v, fr* bvec, const g1a* A2, const g2a* v2,
                                                 const fr* x_mont, const fr* xinv_mont, uint32_t K, uint32_t R,
                                                 uint32_t h, uint32_t nb2) {
     __shared__ FoldSmemS sm;
     uint32_t kw[8];
     if (blockIdx.x < nb2) {
-        const int w = threadIdx.x >> 5, L = threadIdx.x & 31, half = w & 1;
-        const uint64_t t0 = (uint64_t)blockIdx.x * 2 + (w >> 1);
+        const int w = threadIdx.x >> 5, L = threadIdx.x & 31, part = w % NP;
+        const uint64_t t0 = (uint64_t)blockIdx.x * (4 / NP) + w / NP;
         const bool valid = t0 < (uint64_t)K * h;
-        const uint64_t t = valid ? t0 : 0;                    // every warp reaches the barrier below
+        const uint64_t t = valid ? t0 : 0;                    // every warp reaches the barriers below
         const uint64_t k = t / h;
         const uint32_t i = (uint32_t)(t % h);
         const uint64_t lo = k * R + i, hi = k * R + h + i;
         fr_canon_words(kw, xinv_mont[k]);
-        const GPt<fq2> part = gecw_g2_mul_half(sm.e.g2[w], L, half ? v2[t] : v[hi], kw, half);
-        if (L == 0) sm.part.g2[w] = part;
-        __syncthreads();
-        GPt<fq2> r = gecw_add(sm.e.g2[w], L, part, sm.part.g2[w ^ 1]);
-        r = gecw_add(sm.e.g2[w], L, r, gec_from_affine_or_inf(v[lo].x, v[lo].y));
+        GPt<fq2> acc = gecw_g2_mul_part<NP>(sm.e.g2[w], L, part ? v2[(part - 1) * FOLD_SPLIT_MAX + t] : v[hi], kw,
+                                            part);
+        for (int sh = 1, b = 0; sh < NP; sh <<= 1, b ^= 1) {
+            if (L == 0) sm.part.g2[b][w] = acc;
+            __syncthreads();
+            acc = gecw_add(sm.e.g2[w], L, acc, sm.part.g2[b][w ^ sh]);
+        }
+        acc = gecw_add(sm.e.g2[w], L, acc, gec_from_affine_or_inf(v[lo].x, v[lo].y));
         g2a o;
-        gec_to_affine(o.x, o.y, r);
-        __syncthreads();                                      // v[lo] read by both warps before the store
-        if (valid && half == 0 && L == 0) v[lo] = o;
+        gec_to_affine(o.x, o.y, acc);
+        __syncthreads();                                      // v[lo] read by every part before the store
+        if (valid && part == 0 && L == 0) v[lo] = o;
         return;
     }
-    const int grp = threadIdx.x >> 3, lane = threadIdx.x & 7, half = grp & 1;
-    const uint64_t t0 = (uint64_t)(blockIdx.x - nb2) * 8 + (grp >> 1);
+    const int grp = threadIdx.x >> 3, lane = threadIdx.x & 7, part = grp % NP;
+    const uint64_t t0 = (uint64_t)(blockIdx.x - nb2) * (16 / NP) + grp / NP;
     const bool valid = t0 < (uint64_t)K * h;
     const uint64_t t = valid ? t0 : 0;
     const uint64_t k = t / h;
     const uint32_t i = (uint32_t)(t % h);
     const uint64_t lo = k * R + i, hi = k * R + h + i;
     fr_canon_words(kw, x_mont[k]);
-    const GPt<fq> part = gec_g1_mul_half(sm.e.g1[grp], lane, half ? A2[t] : A[hi], kw, half);
-    gsync();
-    if (lane == 0) sm.part.g1[grp] = part;
-    gsync();
-    GPt<fq> r = gec_add(sm.e.g1[grp], lane, part, sm.part.g1[grp ^ 1]);
-    r = gec_add(sm.e.g1[grp], lane, r, gec_from_affine_or_inf(A[lo].x, A[lo].y));
+    GPt<fq> acc = gec_g1_mul_part<NP>(sm.e.g1[grp], lane, part ? A2[(part - 1) * FOLD_SPLIT_MAX + t] : A[hi], kw,
+                                      part);
+    for (int sh = 1, b = 0; sh < NP; sh <<= 1, b ^= 1) {
+        gsync();
+        if (lane == 0) sm.part.g1[b][grp] = acc;
+        gsync();
+        acc = gec_add(sm.e.g1[grp], lane, acc, sm.part.g1[b][grp ^ sh]);
+    }
+    acc = gec_add(sm.e.g1[grp], lane, acc, gec_from_affine_or_inf(A[lo].x, A[lo].y));
     g1a o;
-    gec_to_affine(o.x, o.y, r);
-    gsync();                                                  // A[lo] read by both groups before the store
-    if (valid && half == 0 && lane == 0) {
+    gec_to_affine(o.x, o.y, acc);
+    gsync();                                                  // A[lo] read by every part before the store
+    if (valid && part == 0 && lane == 0) {
         A[lo] = o;
         bvec[lo] = fr_add(bvec[lo], fr_mul(bvec[hi], xinv_mont[k]));
     }
@@ -470,19 +484,35 @@ uint64_t step1_miller_g(const void* A, const void* v, uint32_t K, uint32_t R, ui
     round_miller_w(A, v, K, R, h, ml_out, s);      // few pairs: one warp or block each, for latency
     return n;
 }
+// parts per fold multiplication for n points: 4 while the 4 n warps of the G2 chains and n warps of
+// the G1 chains fit the GPU at once, else 2
+static int fold_parts(uint64_t n) { return n <= FOLD_SPLIT4_MAX ? 4 : 2; }
 void step1_fold_pre(const void* A, const void* v, void* A2, void* v2, uint32_t K, uint32_t R, uint32_t h,
                     cudaStream_t s) {
     const uint32_t n = K * h, nb2 = (n + 3) / 4, nb1 = (n + 15) / 16;
-    FP_KERNEL("k_fold_pre", s, k_fold_pre<<<nb2 + nb1, 128, 0, s>>>((const g1a*)A, (const g2a*)v, (g1a*)A2, (g2a*)v2,
-                                                                    K, R, h, nb2));
+    if (fold_parts(n) == 4)
+        FP_KERNEL("k_fold_pre", s, k_fold_pre<4><<<nb2 + nb1, 128, 0, s>>>((const g1a*)A, (const g2a*)v, (g1a*)A2,
+                                                                           (g2a*)v2, K, R, h, nb2));
+    else
+        FP_KERNEL("k_fold_pre", s, k_fold_pre<2><<<nb2 + nb1, 128, 0, s>>>((const g1a*)A, (const g2a*)v, (g1a*)A2,
+                                                                           (g2a*)v2, K, R, h, nb2));
 }
 void step1_fold(void* A, void* v, void* bvec, const void* x_mont, const void* xinv_mont, uint32_t K, uint32_t R,
                 uint32_t h, const void* A2, const void* v2, cudaStream_t s) {
-    if (A2 && (uint64_t)K * h <= FOLD_SPLIT_MAX) {     // shifted bases ready: half-length chains
-        const uint32_t n = K * h, nb2 = (n + 1) / 2, nb1 = (n + 7) / 8;
-        FP_KERNEL("k_fold_s", s, k_fold_s<<<nb2 + nb1, 128, 0, s>>>((g1a*)A, (g2a*)v, (fr*)bvec, (const g1a*)A2,
-                                                                  (const g2a*)v2, (const fr*)x_mont,
-                                                                  (const fr*)xinv_mont, K, R, h, nb2));
+    if (A2 && (uint64_t)K * h <= FOLD_SPLIT_MAX) {     // shifted bases ready: shorter chains
+        const uint32_t n = K * h;
+        const int np = fold_parts(n);
+        const uint32_t nb2 = (n * np + 3) / 4, nb1 = (n * np + 15) / 16;
+        if (np == 4)
+            FP_KERNEL("k_fold_s", s, k_fold_s<4><<<nb2 + nb1, 128, 0, s>>>((g1a*)A, (g2a*)v, (fr*)bvec,
+                                                                         (const g1a*)A2, (const g2a*)v2,
+                                                                         (const fr*)x_mont, (const fr*)xinv_mont,
+                                                                         K, R, h, nb2));
+        else
+            FP_KERNEL("k_fold_s", s, k_fold_s<2><<<nb2 + nb1, 128, 0, s>>>((g1a*)A, (g2a*)v, (fr*)bvec,
+                                                                         (const g1a*)A2, (const g2a*)v2,
+                                                                         (const fr*)x_mont, (const fr*)xinv_mont,
+                                                                         K, R, h, nb2));
         return;
     }
     if ((uint64_t)K * h <= 4096) {      // few points: a warp per G2 point, an 8-lane group per G1 point

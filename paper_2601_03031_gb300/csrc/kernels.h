@@ -76,9 +76,10 @@ uint64_t step1_miller_g(const void* A, const void* v, uint32_t K, uint32_t R, ui
                         cudaStream_t s);
 void step1_g1_out(const void* sp_g1j, uint32_t K, int j, void* blocks, size_t bopen_len, cudaStream_t s);
 void step1_gt_out(const void* ml_fq12, uint32_t K, int j, void* blocks, size_t bopen_len, cudaStream_t s);
-// Round j's folds.  With A2 / v2 (2^64 A[h + i] and 2^32 v[h + i] from step1_fold_pre, at most
-// FOLD_SPLIT_MAX points) each scalar multiplication runs as two half-length chains.
-constexpr uint32_t FOLD_SPLIT_MAX = 256;
+// Round j's folds.  With A2 / v2 (the shifted bases from step1_fold_pre: 3 FOLD_SPLIT_MAX points
+// each, for rounds of at most FOLD_SPLIT_MAX points) each scalar multiplication runs as four chains
+// of a quarter of the length (at most FOLD_SPLIT4_MAX points) or two of half the length.
+constexpr uint32_t FOLD_SPLIT_MAX = 256, FOLD_SPLIT4_MAX = 128;
 void step1_fold_pre(const void* A, const void* v, void* A2, void* v2, uint32_t K, uint32_t R, uint32_t h,
                     cudaStream_t s);
 void step1_fold(void* A, void* v, void* bvec, const void* x_mont, const void* xinv_mont, uint32_t K, uint32_t R,

@@ -450,8 +450,8 @@ Step1Bufs step1_bufs(const fp_pp* pp, uint32_t Kc, Alloc&& T) {
     B.sp2 = T((KR / 2 + 1) * G1J_BYTES);
     B.pcoef = T((size_t)Kc * (2 * R - 1) * FR_BYTES);
     B.q = T((size_t)Kc * 2 * R * FR_BYTES);
-    B.A2 = T((size_t)FOLD_SPLIT_MAX * G1A_BYTES);
-    B.v2 = T((size_t)FOLD_SPLIT_MAX * G2A_BYTES);
+    B.A2 = T((size_t)3 * FOLD_SPLIT_MAX * G1A_BYTES);
+    B.v2 = T((size_t)3 * FOLD_SPLIT_MAX * G2A_BYTES);
     // W proofs: one batched G2 MSM over the shared bases g2^{beta^i} when many blocks share them,
     // else one scalar multiplication per term and pairwise sums (with few batches the MSM's bucket
     // reduction runs nearly serially per window)
