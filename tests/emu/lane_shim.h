@@ -1,0 +1,77 @@
+// Host build of the device arithmetic headers, for CPU tests of the lane-parallel engines: each
+// lane of a warp (or block) is a host thread, __syncwarp / __syncthreads are a barrier over all of
+// them, and the PTX carry-chain primitives are written with 64-bit host arithmetic (one carry flag
+// per thread).  Test infrastructure only; the library never uses it.
+#pragma once
+#include <barrier>
+#include <cstdint>
+#include <cstring>
+#include <thread>
+
+#define __device__
+#define __forceinline__ inline
+#define __noinline__
+#define __constant__ static const
+#define __global__
+#define FPG_PRIMITIVES_EXTERNAL 1
+#define FPG_DEV static inline
+#define FPG_NOINL static
+
+static inline int __clz(unsigned x) { return x ? __builtin_clz(x) : 32; }
+
+namespace ptx {
+static thread_local uint32_t cc;   // the carry flag of the calling lane
+static inline uint32_t add_cc(uint32_t a, uint32_t b) {
+    const uint64_t s = (uint64_t)a + b;
+    cc = (uint32_t)(s >> 32);
+    return (uint32_t)s;
+}
+static inline uint32_t addc_cc(uint32_t a, uint32_t b) {
+    const uint64_t s = (uint64_t)a + b + cc;
+    cc = (uint32_t)(s >> 32);
+    return (uint32_t)s;
+}
+static inline uint32_t addc(uint32_t a, uint32_t b) { return (uint32_t)((uint64_t)a + b + cc); }
+static inline uint32_t sub_cc(uint32_t a, uint32_t b) {
+    const uint64_t s = (uint64_t)a - b;
+    cc = (uint32_t)(s >> 32) & 1;
+    return (uint32_t)s;
+}
+static inline uint32_t subc_cc(uint32_t a, uint32_t b) {
+    const uint64_t s = (uint64_t)a - b - cc;
+    cc = (uint32_t)(s >> 32) & 1;
+    return (uint32_t)s;
+}
+static inline uint32_t subc(uint32_t a, uint32_t b) { return (uint32_t)((uint64_t)a - b - cc); }
+static inline uint32_t mad_lo_cc(uint32_t a, uint32_t b, uint32_t c) {
+    const uint64_t s = (uint64_t)(uint32_t)((uint64_t)a * b) + c;
+    cc = (uint32_t)(s >> 32);
+    return (uint32_t)s;
+}
+static inline uint32_t madc_lo_cc(uint32_t a, uint32_t b, uint32_t c) {
+    const uint64_t s = (uint64_t)(uint32_t)((uint64_t)a * b) + c + cc;
+    cc = (uint32_t)(s >> 32);
+    return (uint32_t)s;
+}
+static inline uint32_t mad_hi_cc(uint32_t a, uint32_t b, uint32_t c) {
+    const uint64_t s = (((uint64_t)a * b) >> 32) + c;
+    cc = (uint32_t)(s >> 32);
+    return (uint32_t)s;
+}
+static inline uint32_t madc_hi_cc(uint32_t a, uint32_t b, uint32_t c) {
+    const uint64_t s = (((uint64_t)a * b) >> 32) + c + cc;
+    cc = (uint32_t)(s >> 32);
+    return (uint32_t)s;
+}
+}  // namespace ptx
+
+static inline uint32_t __funnelshift_r(uint32_t lo, uint32_t hi, unsigned s) {
+    return (uint32_t)((((uint64_t)hi << 32) | lo) >> (s & 31));
+}
+static inline uint32_t __umulhi(uint32_t a, uint32_t b) { return (uint32_t)(((uint64_t)a * b) >> 32); }
+
+static std::barrier<>* g_lanes = nullptr;   // all lanes of the emulated launch
+static inline void __syncwarp(unsigned = 0xffffffffu) { g_lanes->arrive_and_wait(); }
+static inline void __syncthreads() { g_lanes->arrive_and_wait(); }
+struct LaneIdx { unsigned x; };
+static thread_local LaneIdx threadIdx;

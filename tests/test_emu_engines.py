@@ -1,0 +1,120 @@
+"""The lane-parallel device engines, compiled for the host and checked against the oracle (no GPU).
+
+`tests/emu/engines.cpp` includes the CUDA engine headers (warp12.cuh, group_ec.cuh) through a shim
+(`tests/emu/lane_shim.h`) that runs every lane of a warp or block as a host thread, with the
+warp/block barriers as one barrier over all of them and the PTX carry-chain primitives in 64-bit
+host arithmetic.  The same source the GPU runs is thus checked on the CPU, exactly:
+- the Miller loop on a warp and on a 128-thread block: its final exponentiation (by the oracle)
+  equals the oracle's pairing (line scalings vanish under it, so the Miller values themselves may
+  differ);
+- the final exponentiation on a warp and on a block against the oracle's plain square-and-multiply
+  by (p^12 - 1)/r;
+- G1 scalar multiplication on an 8-lane group (GLV, 2-bit joint windows) and G2 on a warp (GLS),
+  whole and split in 2 and 4 parts on shifted bases 2^(128 p / NP) P and 2^(64 p / NP) Q formed by
+  the engines' own doublings (Step 1's split folds), against the oracle's double-and-add, for edge
+  and random scalars and the identity.
+"""
+import ctypes
+import os
+import random
+import shutil
+import subprocess
+
+import pytest
+
+import oracle as O
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+CSRC = os.path.join(os.path.dirname(HERE), "paper_2601_03031_gb300", "csrc")
+
+
+@pytest.fixture(scope="module")
+def emu(tmp_path_factory):
+    gxx = shutil.which("g++")
+    if not gxx:
+        pytest.skip("g++ not available")
+    lib = str(tmp_path_factory.mktemp("emu") / "libengines.so")
+    subprocess.check_call([gxx, "-std=c++20", "-O1", "-shared", "-fPIC", f"-I{CSRC}", "-o", lib,
+                           os.path.join(HERE, "emu", "engines.cpp")])
+    L = ctypes.CDLL(lib)
+    for n in ("emu_miller", "emu_final_exp", "emu_g1_mul", "emu_g1_dbl_n", "emu_g2_mul", "emu_g2_dbl_n"):
+        getattr(L, n).restype = None
+    return L
+
+
+R = O.const_r()
+
+
+def words(k: int):
+    return (ctypes.c_uint32 * 8)(*[(k >> (32 * i)) & 0xFFFFFFFF for i in range(8)])
+
+
+def g1_mul(L, P, k, np_=1, part=0):
+    o = ctypes.create_string_buffer(96)
+    L.emu_g1_mul(P, words(k), np_, part, o)
+    return o.raw
+
+
+def g2_mul(L, Q, k, np_=1, part=0):
+    o = ctypes.create_string_buffer(192)
+    L.emu_g2_mul(Q, words(k), np_, part, o)
+    return o.raw
+
+
+@pytest.mark.parametrize("nw", [1, 4])
+def test_miller_loop_then_final_exp_is_the_pairing(emu, nw):
+    rnd = random.Random(nw)
+    for _ in range(2):
+        P = O.g1_mul(O.g1_gen(), rnd.randrange(1, R))
+        Q = O.g2_mul(O.g2_gen(), rnd.randrange(1, R))
+        f = ctypes.create_string_buffer(576)
+        emu.emu_miller(nw, P, Q, f)
+        assert O.final_exp(f.raw) == O.pairing(P, Q)
+
+
+@pytest.mark.parametrize("nw", [1, 4])
+def test_final_exp(emu, nw):
+    rnd = random.Random(10 + nw)
+    for _ in range(2):
+        f = O.miller(O.g1_mul(O.g1_gen(), rnd.randrange(1, R)), O.g2_mul(O.g2_gen(), rnd.randrange(1, R)))
+        o = ctypes.create_string_buffer(576)
+        emu.emu_final_exp(nw, f, o)
+        assert o.raw == O.final_exp(f)
+
+
+def test_g1_scalar_mul_whole_and_split(emu):
+    rnd = random.Random(21)
+    P = O.g1_mul(O.g1_gen(), rnd.randrange(1, R))
+    for k in (0, 1, 2, R - 1, rnd.randrange(R), rnd.randrange(R)):
+        e = O.g1_mul(P, k)
+        assert g1_mul(emu, P, k) == e, k
+        for np_ in (2, 4):
+            acc, base = bytes(96), P
+            for part in range(np_):
+                if part:
+                    o = ctypes.create_string_buffer(96)
+                    emu.emu_g1_dbl_n(base, 128 // np_, o)
+                    base = o.raw
+                    assert base == O.g1_mul(P, 1 << (128 * part // np_))
+                acc = O.g1_add(acc, g1_mul(emu, base, k, np_, part))
+            assert acc == e, (k, np_)
+    assert g1_mul(emu, bytes(96), rnd.randrange(R), 4, 1) == bytes(96)
+
+
+def test_g2_scalar_mul_whole_and_split(emu):
+    rnd = random.Random(22)
+    Q = O.g2_mul(O.g2_gen(), rnd.randrange(1, R))
+    for k in (0, 1, 2, R - 1, rnd.randrange(R), rnd.randrange(R)):
+        e = O.g2_mul(Q, k)
+        assert g2_mul(emu, Q, k) == e, k
+        for np_ in (2, 4):
+            acc, base = bytes(192), Q
+            for part in range(np_):
+                if part:
+                    o = ctypes.create_string_buffer(192)
+                    emu.emu_g2_dbl_n(base, 64 // np_, o)
+                    base = o.raw
+                    assert base == O.g2_mul(Q, 1 << (64 * part // np_))
+                acc = O.g2_add(acc, g2_mul(emu, base, k, np_, part))
+            assert acc == e, (k, np_)
+    assert g2_mul(emu, bytes(192), rnd.randrange(R), 2, 1) == bytes(192)
