@@ -73,6 +73,12 @@ CRITICAL_ROUNDS = {
 
 FOLD_SPLIT_MAX = 256          # rounds with at most this many fold points use the split folds
 
+# DRAM bytes per launch (dram__bytes_read.sum + dram__bytes_write.sum) from the ncu captures summarised
+# under profiles/, keyed by (log N, b, kernel), for kernels unchanged since their capture
+NCU_TRAFFIC = {
+    (16, 256, "k_final_exp_c"): (89e3, "profiles/k_final_exp_c_n16_b256.md"),
+}
+
 
 def step_units(log_n: int, b: int, msm_window: int) -> dict:
     """Per kernel: (unit, units processed per step) for one Commit + OpenAll step."""
@@ -705,7 +711,9 @@ def main():
         ops_launch = ops_step / launches_per_step
         achieved = ops_launch / (avg_ms * 1e-3)
         roof = {"bound": "alu", "kernel": name, "achieved": achieved / 1e12, "peak": peak / 1e12,
-                "unit": "Tops/s (32-bit multiply-add lane ops)", "frac": achieved / peak, "traffic": None,
+                "unit": "Tops/s (32-bit multiply-add lane ops)", "frac": achieved / peak,
+                "traffic": NCU_TRAFFIC.get((log_n, b, name), (None,))[0],
+                "traffic_source": NCU_TRAFFIC.get((log_n, b, name), (None, None))[1],
                 "units_per_step": n_units, "unit_op": unit, "launches_per_step": launches_per_step,
                 "avg_launch_ms": avg_ms,
                 "peak_source": "measured: fp_imad_probe on this GPU in this run"}
