@@ -590,6 +590,28 @@ def run_reference(args):
     print(json.dumps(line))
 
 
+# ------------------------------------------------------------------------- replicas (N > 1)
+def replica_seed(seed: int, rank: int) -> int:
+    """Seed of rank `rank`'s vector: every replica proves its own vector."""
+    return seed + 1 + rank
+
+
+def slowest_rank_ms(total_ms: float, world: int, dist=None, device="cpu") -> float:
+    """The timed region's length over all ranks (max): the job ends with its slowest replica."""
+    if world <= 1:
+        return total_ms
+    import torch
+    t = torch.tensor([total_ms], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    dist.barrier()
+    return float(t.item())
+
+
+def job_proofs_per_s(world: int, N: int, ms_per_step: float) -> float:
+    """Whole-job throughput: all ranks' proofs per step over the slowest rank's step time."""
+    return world * N / (ms_per_step * 1e-3)
+
+
 # --------------------------------------------------------------------------------- GPU arm
 def main():
     args = parse()
@@ -629,7 +651,7 @@ def main():
     N = 1 << log_n
     stream = torch.cuda.current_stream()
     pp = F.PP(log_n, b, args.seed, stream)
-    m = I.vector(args.seed + 1 + rank, log_n)
+    m = I.vector(replica_seed(args.seed, rank), log_n)
     m_dev = torch.from_numpy(m.view(np.int64).copy()).cuda()
     flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")     # > 129 MB L2
 
@@ -666,13 +688,9 @@ def main():
     total_ms = sum(a.elapsed_time(b_) for a, b_ in ev)
     commit_ms = sum(a.elapsed_time(mid) for (a, _), mid in zip(ev, mids)) / args.steps
     openall_ms = sum(mid.elapsed_time(b_) for (_, b_), mid in zip(ev, mids)) / args.steps
-    if world > 1:
-        t = torch.tensor([total_ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_ms = float(t.item())
-        dist.barrier()
+    total_ms = slowest_rank_ms(total_ms, world, dist, "cuda")
     ms_per_step = total_ms / args.steps
-    value = world * N / (ms_per_step * 1e-3)
+    value = job_proofs_per_s(world, N, ms_per_step)
 
     # end-to-end through the C ABI with host buffers: H2D of m from pinned memory inside vc_commit,
     # D2H of the shared proof state (the OpenAll result) into pinned memory
