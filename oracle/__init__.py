@@ -103,6 +103,10 @@ def lib():
             L.or_sha256.argtypes = [vp, ctypes.c_size_t, vp]
             L.or_hfr.argtypes = [c_u8p, vp, ctypes.c_size_t, vp]
             L.or_splitmix_fr.argtypes = [ctypes.c_uint64, ctypes.c_uint32, vp]
+            L.or_ops_reset.argtypes = []
+            L.or_ops_reset.restype = None
+            L.or_ops_get.argtypes = [vp]
+            L.or_ops_get.restype = None
             rc = L.or_status()
             if rc != 0:
                 raise RuntimeError(f"oracle constant derivation failed: {rc}")
@@ -132,6 +136,19 @@ def const_r() -> int:
 def const_final_exp() -> int:
     b = _buf(4 * 160); n = lib().or_const(2, b)
     return int.from_bytes(b.raw[: 4 * n], "little")
+
+
+# --------------------------------------------------------------------------- operation counts
+def ops_reset() -> None:
+    """Zero the counters of Miller loops, final exponentiations and G1 / G2 scalar multiplications."""
+    lib().or_ops_reset()
+
+
+def ops() -> dict:
+    """Operations since the last ops_reset() (all threads)."""
+    a = (ctypes.c_uint64 * 4)()
+    lib().or_ops_get(a)
+    return {"miller": a[0], "final_exp": a[1], "g1_mul": a[2], "g2_mul": a[3]}
 
 
 # --------------------------------------------------------------------------- fields

@@ -99,7 +99,13 @@ void g1_mul(g1* r, const g1* p, const fe* k) {
     u64 l[FE_LIMBS] = {0}; f_to_canon(&FR, l, k);
     g1_mul_limbs(r, p, l);
 }
+static u64 OR_OPS[OR_OP_KINDS];
+void or_op_count(int kind) { __atomic_fetch_add(&OR_OPS[kind], 1, __ATOMIC_RELAXED); }
+void or_ops_reset(void) { for (int i = 0; i < OR_OP_KINDS; i++) __atomic_store_n(&OR_OPS[i], 0, __ATOMIC_RELAXED); }
+void or_ops_get(u64 out[OR_OP_KINDS]) { for (int i = 0; i < OR_OP_KINDS; i++) out[i] = __atomic_load_n(&OR_OPS[i], __ATOMIC_RELAXED); }
+
 void g1_mul_limbs(g1* r, const g1* p, const u64 l[4]) {
+    or_op_count(OR_OP_G1_MUL);
     g1 acc; g1_set_inf(&acc);
     for (int i = 255; i >= 0; i--) {
         g1_dbl(&acc, &acc);
@@ -208,6 +214,7 @@ void g2_mul(g2* r, const g2* p, const fe* k) {
     g2_mul_limbs(r, p, l);
 }
 void g2_mul_limbs(g2* r, const g2* p, const u64 l[4]) {
+    or_op_count(OR_OP_G2_MUL);
     g2 acc; g2_set_inf(&acc);
     for (int i = 255; i >= 0; i--) {
         g2_dbl(&acc, &acc);
@@ -278,6 +285,7 @@ static void line_mul(fq12* f, const fq2* lam, const fq2* xT, const fq2* yT, cons
 }
 
 void miller_loop(fq12* f, const g1* P, const g2* Q) {
+    or_op_count(OR_OP_MILLER);
     fq12_one(f);
     if (g1_is_inf(P) || g2_is_inf(Q)) return;
     fe xP, yP; g1_affine(&xP, &yP, P);
@@ -316,7 +324,10 @@ void miller_loop(fq12* f, const g1* P, const g2* Q) {
     fq12_conj(f, f);
 }
 
-void final_exp(fq12* r, const fq12* f) { fq12_pow_words(r, f, OR_EXP_FINAL, OR_EXP_FINAL_WORDS); }
+void final_exp(fq12* r, const fq12* f) {
+    or_op_count(OR_OP_FINAL_EXP);
+    fq12_pow_words(r, f, OR_EXP_FINAL, OR_EXP_FINAL_WORDS);
+}
 
 void pairing(fq12* r, const g1* P, const g2* Q) {
     fq12 f; miller_loop(&f, P, Q); final_exp(r, &f);

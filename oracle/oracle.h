@@ -59,6 +59,15 @@ int  or_init(void);                                     /* 0 on success */
 extern u32 OR_EXP_FINAL[160];                           /* (p^12-1)/r, little-endian 32-bit words */
 extern int OR_EXP_FINAL_WORDS;
 
+/* --- operation counters ---------------------------------------------------------
+ * Miller loops, final exponentiations and G1 / G2 scalar multiplications since the last reset,
+ * over all threads: the efficiency statements of Sec. 3 (pairings and exponentiations per
+ * algorithm) are checked against them. */
+enum { OR_OP_MILLER = 0, OR_OP_FINAL_EXP = 1, OR_OP_G1_MUL = 2, OR_OP_G2_MUL = 3, OR_OP_KINDS = 4 };
+void or_op_count(int kind);
+void or_ops_reset(void);
+void or_ops_get(u64 out[OR_OP_KINDS]);
+
 /* --- field ------------------------------------------------------------------- */
 void f_add(const field* F, fe* c, const fe* a, const fe* b);
 void f_sub(const field* F, fe* c, const fe* a, const fe* b);

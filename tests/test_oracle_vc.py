@@ -181,3 +181,21 @@ def test_proof_size_formula_reproduces_paper_tables():
     for log_n, b in [(4, 1), (4, 4), (6, 8)]:
         pp = O.PP(log_n, 1) if log_n != 4 else setup(4)[0]
         assert pp.proof_len(b, 0) == ref.proof_size(b, log_n, g1=96, g2=192, gt=576, fr=32)
+
+
+@pytest.mark.parametrize("log_n,b,k", [(4, 1, 2), (5, 3, 1), (6, 8, 0)])
+def test_operation_counts_match_fc_efficiency(log_n, b, k):
+    """Sec. 3's efficiency statements with n = R (the FC length).  FC.Commit takes n pairings (R
+    Miller loops, one final exponentiation for their product) after the N G1 exponentiations of the
+    row commitments.  FC.BOpen takes 2n pairings for the GT parts of L_j, R_j (2(R - 1) Miller loops,
+    two final exponentiations per round), 2n G1 exponentiations for their G1 parts, n in G1 and n in
+    G2 for the rescaling (R - 1 each) and 2n in G2 for the proof of v_l (2R - 2 terms)."""
+    pp = O.PP(log_n, 3)
+    m = I.vector(103, log_n).tobytes()
+    R, M, lr = pp.R, pp.M, pp.R.bit_length() - 1
+    O.ops_reset()
+    C, rows = O.commit(pp, m)
+    assert O.ops() == {"miller": R, "final_exp": 1, "g1_mul": R * M, "g2_mul": 0}
+    O.ops_reset()
+    O.bopen(pp, C, rows, b, k)
+    assert O.ops() == {"miller": 2 * (R - 1), "final_exp": 2 * lr, "g1_mul": 3 * (R - 1), "g2_mul": 3 * (R - 1)}
