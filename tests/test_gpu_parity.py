@@ -220,8 +220,10 @@ def test_prove_one_n16_sampled():
 
 
 # ------------------------------------------------------------------ N = 2^20, b = 1024, 256, 16, 1
-# Sampled Step-1 blocks per b (first, interior and last blocks; K = 1, 4, 64, 1024).
-N20_BLOCKS = {1024: [0], 256: [3], 16: [0, 37, 63], 1: [0, 511, 1023]}
+# Step-1 blocks compared per b (K = 1, 4, 64, 1024 blocks): every block at b >= 256, eight spread
+# over the 64 at b = 16 and 32 spread over the 1024 at b = 1 (first and last included).
+N20_BLOCKS = {1024: [0], 256: [0, 1, 2, 3], 16: [9 * i for i in range(8)],
+              1: [round(i * 1023 / 31) for i in range(32)]}
 
 
 @functools.lru_cache(maxsize=None)
