@@ -122,26 +122,6 @@ FPG_NOINL GPt<F> gec_dbl(GEc<F>& sm, int lane, const GPt<F>& P) {
     return r;
 }
 
-// table of subset sums tab[s] = sum_{i in s} B_i for s < 2^nb (tab[0] = identity); every lane holds
-// the same B_i and the same results, lane 0 stores them
-template <typename F>
-FPG_DEV void gec_table(GEc<F>& sm, int lane, const GPt<F>* B, int nb) {
-    gsync();
-    if (lane == 0) {
-        sm.tab[0] = gec_identity<F>();
-        for (int i = 0; i < nb; i++) sm.tab[1 << i] = B[i];
-    }
-    gsync();
-    for (int s = 3; s < (1 << nb); s++) {
-        if (!(s & (s - 1))) continue;                          // single bases are already in place
-        const int top = 31 - __clz(s);
-        const GPt<F> r = gec_add(sm, lane, sm.tab[s & ~(1 << top)], sm.tab[1 << top]);
-        gsync();
-        if (lane == 0) sm.tab[s] = r;
-        gsync();
-    }
-}
-
 template <typename F>
 FPG_DEV GPt<F> gec_from_affine(const F& x, const F& y) {
     GPt<F> r;
@@ -156,65 +136,6 @@ FPG_DEV void gec_to_affine(F& x, F& y, const GPt<F>& P) {
     const F zi = f_inv(P.Z);
     x = f_mul(P.X, zi);
     y = f_mul(P.Y, zi);
-}
-
-// k P on G1 for a canonical k < r (GLV: k = k0 + k1 |x|^2, bases P and -phi(P)), projective
-FPG_NOINL GPt<fq> gec_g1_mul_proj(GEc<fq>& sm, int lane, const g1a& P, const uint32_t* k) {
-    uint32_t k1[5], k0[4];
-    div_by_const<4, 5>(k1, k0, k, GLV_D, GLV_BARRETT);
-    fq om;
-    fq_from_const(om, GLV_OMEGA);
-    const bool inf = g1a_is_inf(P);
-    GPt<fq> B[2];
-    B[0] = inf ? gec_identity<fq>() : gec_from_affine(P.x, P.y);
-    B[1] = inf ? gec_identity<fq>() : gec_from_affine(fq_mul(P.x, om), fq_neg(P.y));
-    gec_table(sm, lane, B, 2);
-    GPt<fq> acc = gec_identity<fq>();
-    for (int i = 127; i >= 0; i--) {
-        acc = gec_dbl(sm, lane, acc);
-        const int s = bit_of(k0, i) | (bit_of(k1, i) << 1);
-        acc = gec_add(sm, lane, acc, sm.tab[s]);
-    }
-    return acc;
-}
-FPG_DEV g1a gec_g1_mul(GEc<fq>& sm, int lane, const g1a& P, const uint32_t* k) {
-    g1a r;
-    gec_to_affine(r.x, r.y, gec_g1_mul_proj(sm, lane, P, k));
-    return r;
-}
-
-// k Q on G2 for a canonical k < r (GLS: base-|x| digits, bases (-1)^i psi^i(Q)), projective
-FPG_NOINL GPt<fq2> gec_g2_mul_proj(GEc<fq2>& sm, int lane, const g2a& Q, const uint32_t* k) {
-    uint32_t q1[7], q2[7], q3[7], d[4][2];
-    div_by_const<2, 7>(q1, d[0], k, GLS_D, GLS_BARRETT);
-    uint32_t t8[8];
-    for (int i = 0; i < 8; i++) t8[i] = i < 7 ? q1[i] : 0;
-    div_by_const<2, 7>(q2, d[1], t8, GLS_D, GLS_BARRETT);
-    for (int i = 0; i < 8; i++) t8[i] = i < 7 ? q2[i] : 0;
-    div_by_const<2, 7>(q3, d[2], t8, GLS_D, GLS_BARRETT);
-    d[3][0] = q3[0];
-    d[3][1] = q3[1];
-    const bool inf = g2a_is_inf(Q);
-    g2a b = Q;
-    GPt<fq2> B[4];
-    for (int i = 0; i < 4; i++) {
-        if (i) b = g2_psi(b);
-        const fq2 y = (i & 1) ? fq2_neg(b.y) : b.y;
-        B[i] = inf ? gec_identity<fq2>() : gec_from_affine(b.x, y);
-    }
-    gec_table(sm, lane, B, 4);
-    GPt<fq2> acc = gec_identity<fq2>();
-    for (int i = 63; i >= 0; i--) {
-        acc = gec_dbl(sm, lane, acc);
-        const int s = bit_of(d[0], i) | (bit_of(d[1], i) << 1) | (bit_of(d[2], i) << 2) | (bit_of(d[3], i) << 3);
-        acc = gec_add(sm, lane, acc, sm.tab[s]);
-    }
-    return acc;
-}
-FPG_DEV g2a gec_g2_mul(GEc<fq2>& sm, int lane, const g2a& Q, const uint32_t* k) {
-    g2a r;
-    gec_to_affine(r.x, r.y, gec_g2_mul_proj(sm, lane, Q, k));
-    return r;
 }
 
 template <typename F>
@@ -380,7 +301,7 @@ FPG_DEV GPt<fq2> gecw_g2_bits(GEcW& sm, int L, const uint32_t (*d)[2], int i0, i
     return acc;
 }
 
-// k Q on G2 for a canonical k < r (GLS, as gec_g2_mul_proj), on one warp
+// k Q on G2 for a canonical k < r (GLS: base-|x| digits, bases (-1)^i psi^i(Q)), on one warp
 FPG_NOINL GPt<fq2> gecw_g2_mul_proj(GEcW& sm, int L, const g2a& Q, const uint32_t* k) {
     uint32_t d[4][2];
     gls_digits(d, k);

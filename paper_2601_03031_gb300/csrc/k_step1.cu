@@ -76,12 +76,6 @@ __global__ void __launch_bounds__(64) k_round_g1_out(const g1j* sp, uint32_t K, 
     g1a_to_be(rec + GT_SER, g1_affine(sp[t]));
 }
 
-// Both folds of round j on 8-lane groups (group_ec.cuh): blocks [0, nb2) fold 8 points of v each,
-// the remaining blocks 8 points of A (and the matching entries of b).  Point t = (k, i < h).
-union FoldSmem {
-    GEc<fq2> g2[8];
-    GEc<fq> g1[8];
-};
 // Both folds of round j for few points: blocks [0, nb2) fold 4 points of v each (one warp per point,
 // group_ec.cuh GEcW), the remaining blocks 16 points of A (8-lane groups) and the entries of b.
 union FoldSmemW {
