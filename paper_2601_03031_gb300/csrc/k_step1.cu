@@ -162,7 +162,10 @@ __global__ void __launch_bounds__(128) k_fold_pre(const g1a* A, const g2a* v, g1
 
 // G2: NP warps per point (blocks [0, nb2), 4 / NP points each); G1: NP 8-lane groups of one warp per
 // point (16 / NP points per block).  The parts of a point are summed pairwise (every chain keeps the
-// same instruction stream and ends with the whole sum; part 0 stores the result).
+// same instruction stream and ends with the whole sum; part 0 stores the result).  Chains past the
+// last point recompute point 0 and store nothing; their read of A[lo] / v[lo] may meet point 0's
+// store from another block, which only changes the discarded result (the arithmetic is bounded for
+// any input).
 struct FoldSmemS {
     union {
         GEcW g2[4];
