@@ -2,6 +2,7 @@
 round invariant, brute force (ProveOne), verification, tamper rejection and the paper's
 proof-size formula."""
 import functools
+import os
 import random
 
 import pytest
@@ -165,18 +166,32 @@ def test_out_of_range_scalar_rejected():
         O.commit(pp, m.tobytes())
 
 
+def paper_proof_sizes():
+    """The proof sizes printed in Tables tb:fc and tb:vc (tests/golden/paper_proof_sizes.txt)."""
+    fc, vc = [], []
+    with open(os.path.join(os.path.dirname(__file__), "golden", "paper_proof_sizes.txt")) as f:
+        for line in f:
+            w = line.split()
+            if not w or w[0].startswith("#"):
+                continue
+            if w[0] == "fc":
+                fc.append((int(w[1]), float(w[2])))
+            else:
+                vc.append((int(w[1]), int(w[2]), float(w[3])))
+    return fc, vc
+
+
 def test_proof_size_formula_reproduces_paper_tables():
     # BN_SNARK1 sizes: G1 32, G2 64, GT 384, Fr 32, digest 32 (Sec. 5, Tables tb:fc and tb:vc)
     bn = dict(g1=32, g2=64, gt=384, fr=32)
     kib = lambda v: round(v / 1024, 2)
-    fp_2logn = [8.91, 10, 11.09, 12.19, 13.28]
-    fp_log2n = [15.91, 19, 22.34, 25.94, 29.78]
-    for idx, n in enumerate([16, 18, 20, 22, 24]):
-        assert kib(ref.proof_size(2 * n, n, **bn)) == fp_2logn[idx]
-        assert kib(ref.proof_size(n * n, n, **bn)) == fp_log2n[idx]
+    fc, vc = paper_proof_sizes()
+    assert len(fc) == 5 and len(vc) == 10
+    for log_n, b, exp in vc:
+        assert kib(ref.proof_size(b, log_n, **bn)) == exp, (log_n, b)
     # FC proof alone (Table tb:fc): 2 log n GT + (2 log n + 1) G1 + 2 G2
-    for n, exp in zip([8, 9, 10, 11, 12], [6.66, 7.47, 8.28, 9.09, 9.91]):
-        assert kib(2 * n * 384 + (2 * n + 1) * 32 + 2 * 64) == exp
+    for n, exp in fc:
+        assert kib(2 * n * 384 + (2 * n + 1) * 32 + 2 * 64) == exp, n
     # and the oracle's byte layout is that formula with BLS12-381 sizes (tower: l = l_R = l_c)
     for log_n, b in [(4, 1), (4, 4), (6, 8)]:
         pp = O.PP(log_n, 1) if log_n != 4 else setup(4)[0]
