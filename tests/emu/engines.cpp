@@ -1,11 +1,12 @@
 // Host entry points over the lane-parallel device engines (warp12.cuh: Miller loop and final
-// exponentiation on a warp or a 128-thread block; group_ec.cuh: G1 scalar multiplication on an
+// exponentiation on a warp or a 128-thread block; gt_exp.cuh: exponentiation in GT; group_ec.cuh: G1 scalar multiplication on an
 // 8-lane group, G2 on a warp, and the parts of the split folds).  Points and field elements cross as
 // canonical big-endian bytes (G1 96, G2 192, Fq12 576 in the tower order of the serialisation),
 // scalars as 8 little-endian 32-bit words.  Test infrastructure only.
 #include "lane_shim.h"
 #include "warp12.cuh"
 #include "group_ec.cuh"
+#include "gt_exp.cuh"
 
 #include <vector>
 
@@ -45,6 +46,7 @@ void lanes(int n, Fn fn) {
 }
 W12 g_w;
 WMill g_m;
+WGt g_gt;
 GEc<fq> g_g1;
 GEcW g_g2;
 }  // namespace
@@ -65,6 +67,17 @@ void emu_final_exp(int nw, const uint8_t* f_be, uint8_t* out) {
     else lanes(32, [&] { w_from_tower<1>(g_w.s[0], in); w_final_exp<1>(g_w); });
     fq12 r;
     to_tower(r, g_w.s[2]);
+    fq12_to_be(out, r);
+}
+// bits [i0, i0 + n) of the Frobenius split of g^c (g in GT, c < r as 8 little-endian words)
+void emu_gt_pow(int nw, const uint8_t* g_be, const uint32_t* c, int i0, int n, uint8_t* out) {
+    const fq12 in = be_fq12(g_be);
+    if (nw == 4)
+        lanes(128, [&] { w_from_tower<4>(g_gt.w.s[0], in); w_gt_pow_bits<4>(g_gt, g_gt.w.s[1], g_gt.w.s[0], c, i0, n); });
+    else
+        lanes(32, [&] { w_from_tower<1>(g_gt.w.s[0], in); w_gt_pow_bits<1>(g_gt, g_gt.w.s[1], g_gt.w.s[0], c, i0, n); });
+    fq12 r;
+    to_tower(r, g_gt.w.s[1]);
     fq12_to_be(out, r);
 }
 // k P on an 8-lane group: np = 1 the whole multiplication, else part `part` of np on the base P

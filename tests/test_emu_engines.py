@@ -9,6 +9,8 @@ host arithmetic.  The same source the GPU runs is thus checked on the CPU, exact
   differ);
 - the final exponentiation on a warp and on a block against the oracle's plain square-and-multiply
   by (p^12 - 1)/r;
+- exponentiation in GT by the Frobenius split of the exponent (gt_exp.cuh), whole and in parts,
+  against the oracle's square-and-multiply;
 - G1 scalar multiplication on an 8-lane group (GLV, 2-bit joint windows) and G2 on a warp (GLS),
   whole and split in 2 and 4 parts on shifted bases 2^(128 p / NP) P and 2^(64 p / NP) Q formed by
   the engines' own doublings (Step 1's split folds), against the oracle's double-and-add, for edge
@@ -37,7 +39,8 @@ def emu(tmp_path_factory):
     subprocess.check_call([gxx, "-std=c++20", "-O1", "-shared", "-fPIC", f"-I{CSRC}", "-o", lib,
                            os.path.join(HERE, "emu", "engines.cpp")])
     L = ctypes.CDLL(lib)
-    for n in ("emu_miller", "emu_final_exp", "emu_g1_mul", "emu_g1_dbl_n", "emu_g2_mul", "emu_g2_dbl_n"):
+    for n in ("emu_miller", "emu_final_exp", "emu_gt_pow", "emu_g1_mul", "emu_g1_dbl_n", "emu_g2_mul",
+              "emu_g2_dbl_n"):
         getattr(L, n).restype = None
     return L
 
@@ -80,6 +83,25 @@ def test_final_exp(emu, nw):
         o = ctypes.create_string_buffer(576)
         emu.emu_final_exp(nw, f, o)
         assert o.raw == O.final_exp(f)
+
+
+@pytest.mark.parametrize("nw", [1, 4])
+def test_gt_exponentiation_by_frobenius_split(emu, nw):
+    """g^c by the base-|x| digits of c on the Frobenius powers of g, whole and in 4 parts of 16 digit
+    bits on the bases g^(2^(16 p)), against the oracle's square-and-multiply."""
+    rnd = random.Random(30 + nw)
+    g = O.pairing(O.g1_mul(O.g1_gen(), rnd.randrange(1, R)), O.g2_mul(O.g2_gen(), rnd.randrange(1, R)))
+    for c in (0, 1, R - 1, rnd.randrange(R)):
+        o = ctypes.create_string_buffer(576)
+        emu.emu_gt_pow(nw, g, words(c), 0, 64, o)
+        assert o.raw == O.fq12_pow(g, c), c
+    c = rnd.randrange(R)
+    acc = O.fq12_pow(g, 0)
+    for part in range(4):
+        o = ctypes.create_string_buffer(576)
+        emu.emu_gt_pow(nw, O.fq12_pow(g, 1 << (16 * part)), words(c), 16 * part, 16, o)
+        acc = O.fq12_mul(acc, o.raw)
+    assert acc == O.fq12_pow(g, c)
 
 
 def test_g1_scalar_mul_whole_and_split(emu):
