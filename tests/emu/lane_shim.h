@@ -70,8 +70,15 @@ static inline uint32_t __funnelshift_r(uint32_t lo, uint32_t hi, unsigned s) {
 }
 static inline uint32_t __umulhi(uint32_t a, uint32_t b) { return (uint32_t)(((uint64_t)a * b) >> 32); }
 
+// kernels: one block at a time, its shared variables as statics, blockIdx per lane thread
+#define __shared__ static
+#define __launch_bounds__(...)
+static inline uint32_t min(uint32_t a, uint32_t b) { return a < b ? a : b; }
+
 static std::barrier<>* g_lanes = nullptr;   // all lanes of the emulated launch
 static inline void __syncwarp(unsigned = 0xffffffffu) { g_lanes->arrive_and_wait(); }
 static inline void __syncthreads() { g_lanes->arrive_and_wait(); }
 struct LaneIdx { unsigned x; };
 static thread_local LaneIdx threadIdx;
+static thread_local LaneIdx blockIdx;
+static const LaneIdx blockDim{128};
