@@ -441,8 +441,8 @@ Step1Bufs step1_bufs(const fp_pp* pp, uint32_t Kc, Alloc&& T) {
     B.v = T(KR * G2A_BYTES);
     B.bvec = T(KR * FR_BYTES);
     B.xprev = T(Kc * 32);
-    B.x_mont = T(Kc * FR_BYTES);
-    B.xinv_mont = T(Kc * FR_BYTES);
+    B.x_mont = T(2 * Kc * FR_BYTES);        // two rounds' challenges (the look-ahead schedule alternates)
+    B.xinv_mont = T(2 * Kc * FR_BYTES);
     B.xinv_all = T((size_t)Kc * pp->log_r * FR_BYTES);
     B.ml = T(KR * FQ12_BYTES);
     B.ml2 = T((KR / 2 + 1) * FQ12_BYTES);
@@ -464,6 +464,32 @@ Step1Bufs step1_bufs(const fp_pp* pp, uint32_t Kc, Alloc&& T) {
         B.wt2 = T(((size_t)Kc * R + 1) * G2J_BYTES);
     }
     return B;
+}
+
+// Look-ahead buffers (lookahead.cuh) for Kc blocks of R rows: a snapshot of round j-1's state, the
+// Miller values by class and their pairwise products (8 Kc h2 <= 2 Kc R), the final exponentiations
+// and affine G1 sums of two rounds in flight, the GT powers, the G1 terms (6 Kc 4 h2 <= 6 Kc R) and
+// their pairwise sums
+struct LaBufs {
+    void *A, *v, *bvec, *ml, *ml2, *fe[2], *pw, *sp, *sp2, *acc[2];
+};
+template <class Alloc>
+LaBufs la_bufs(const fp_pp* pp, uint32_t Kc, Alloc&& T) {
+    const uint64_t KR = (uint64_t)Kc * pp->R;
+    LaBufs L;
+    L.A = T(KR * G1A_BYTES);
+    L.v = T(KR * G2A_BYTES);
+    L.bvec = T(KR * FR_BYTES);
+    L.ml = T(2 * KR * FQ12_BYTES);
+    L.ml2 = T((KR + 1) * FQ12_BYTES);
+    for (int i = 0; i < 2; i++) {
+        L.fe[i] = T((size_t)8 * Kc * FQ12_BYTES);
+        L.acc[i] = T((size_t)6 * Kc * G1A_BYTES);
+    }
+    L.pw = T((size_t)4 * Kc * FQ12_BYTES);
+    L.sp = T(6 * KR * G1J_BYTES);
+    L.sp2 = T((3 * KR + 1) * G1J_BYTES);
+    return L;
 }
 
 // FC.BOpen rounds (Sec. 3, Eq. folding) and the fast-verification proof of v_l for the Kc blocks
@@ -511,6 +537,109 @@ void step1_rounds(const fp_pp* pp, uint32_t k0, uint32_t Kc, uint32_t b, const S
     cudaEventDestroy(ev_folded);
     cudaEventDestroy(ev_sparse);
     cudaEventDestroy(ev_pre);
+}
+
+// The rounds with look-ahead (lookahead.cuh): round 1 as in step1_rounds; for j >= 2 round j's record
+// comes from round j-1's state (snapshotted on sL as soon as round j-2's fold has produced it, then
+// its Miller loops, final exponentiations and G1 sums) and x_{j-1} (GT exponentiations and the G1
+// multiplications on the challenge stream s1), while round j-1's fold runs on sF.  Challenges
+// alternate between two buffers (B.x_mont, B.xinv_mont hold 2 Kc entries) so that a fold still
+// reading x_{j-1} never meets x_j.  Streams: s1 challenges, s3 round 1's sparse G1 terms, s4 the
+// shifted fold bases, sL the look-ahead, sF the folds; s3 must already be ordered after whatever
+// filled B.bvec, s1 after B.A and B.v.
+[[maybe_unused]] void step1_rounds_la(const fp_pp* pp, uint32_t k0, uint32_t Kc, uint32_t b, const Step1Bufs& B,
+                                      const LaBufs& L, uint8_t* blocks1, size_t blen, cudaStream_t s1,
+                                      cudaStream_t s3, cudaStream_t s4, cudaStream_t sL, cudaStream_t sF) {
+    const uint32_t R = pp->R;
+    const int lr = (int)pp->log_r;
+    const uint64_t KR = (uint64_t)Kc * R;
+    auto xm = [&](int j) { return (uint8_t*)B.x_mont + (size_t)(j & 1) * Kc * FR_BYTES; };
+    auto xim = [&](int j) { return (uint8_t*)B.xinv_mont + (size_t)(j & 1) * Kc * FR_BYTES; };
+    std::vector<cudaEvent_t> evs;
+    auto ev = [&]() { evs.push_back(new_event()); return evs.back(); };
+    auto wait = [&](cudaStream_t st, cudaEvent_t e) { check(cudaStreamWaitEvent(st, e, 0), "wait"); };
+    auto rec = [&](cudaStream_t st) { cudaEvent_t e = ev(); check(cudaEventRecord(e, st), "event"); return e; };
+    std::vector<cudaEvent_t> ev_S(lr + 2, nullptr), ev_snap(lr + 2, nullptr), ev_la(lr + 2, nullptr),
+        ev_pre(lr + 2, nullptr), ev_x(lr + 2, nullptr);
+
+    // round j's look-ahead from the state S_{j-1} (ready on sL)
+    auto lookahead = [&](int j) {
+        const uint32_t h2 = R >> j;
+        check(cudaMemcpyAsync(L.A, B.A, KR * G1A_BYTES, cudaMemcpyDeviceToDevice, sL), "D2D");
+        check(cudaMemcpyAsync(L.v, B.v, KR * G2A_BYTES, cudaMemcpyDeviceToDevice, sL), "D2D");
+        check(cudaMemcpyAsync(L.bvec, B.bvec, KR * FR_BYTES, cudaMemcpyDeviceToDevice, sL), "D2D");
+        ev_snap[j] = rec(sL);
+        la_miller(L.A, L.v, Kc, R, h2, L.ml, sL);
+        void* mlr = reduce_pairs(L.ml, L.ml2, (uint64_t)Kc * 8 * h2, (uint64_t)Kc * 8, fq12_pair_reduce, sL);
+        final_exp_group(mlr, 8 * Kc, L.fe[j & 1], nullptr, 1, 0, 0, sL);
+        la_sparse(L.A, L.bvec, k0, Kc, R, h2, b, L.sp, sL);
+        void* spr = reduce_pairs(L.sp, L.sp2, (uint64_t)Kc * 24 * h2, (uint64_t)Kc * 6, g1_pair_reduce, sL);
+        g1j_to_affine(spr, L.acc[j & 1], nullptr, 0, (uint64_t)Kc * 6, sL);
+        ev_la[j] = rec(sL);
+    };
+    // round j's fold on sF (after x_j, the shifted bases and the snapshot of S_j for round j + 1)
+    auto fold = [&](int j) {
+        const uint32_t h = R >> j;
+        const bool split = (uint64_t)Kc * h <= FOLD_SPLIT_MAX;
+        wait(sF, ev_x[j]);
+        if (split) wait(sF, ev_pre[j]);
+        if (j + 1 <= lr) wait(sF, ev_snap[j + 1]);
+        step1_fold(B.A, B.v, B.bvec, xm(j), xim(j), Kc, R, h, split ? B.A2 : nullptr, split ? B.v2 : nullptr, sF);
+        ev_S[j + 1] = rec(sF);
+    };
+    auto fold_pre = [&](int j, cudaEvent_t ready) {
+        const uint32_t h = R >> j;
+        if ((uint64_t)Kc * h > FOLD_SPLIT_MAX) return;
+        wait(s4, ready);
+        step1_fold_pre(B.A, B.v, B.A2, B.v2, Kc, R, h, s4);
+        ev_pre[j] = rec(s4);
+    };
+
+    cudaEvent_t ev_a = rec(s1), ev_b = rec(s3);     // S_1: A, v (s1) and b (s3)
+    if (lr >= 2) {
+        wait(sL, ev_a);
+        wait(sL, ev_b);
+        lookahead(2);
+    }
+    fold_pre(1, ev_a);
+    {   // round 1, direct
+        const uint32_t h = R >> 1;
+        step1_sparse_terms(B.A, B.bvec, k0, Kc, R, h, b, B.sp, s3);
+        void* spr = reduce_pairs(B.sp, B.sp2, (uint64_t)Kc * 2 * h, (uint64_t)Kc * 2, g1_pair_reduce, s3);
+        step1_g1_out(spr, Kc, 1, blocks1, blen, s3);
+        cudaEvent_t ev_sp = rec(s3);
+        const uint64_t nml = step1_miller_g(B.A, B.v, Kc, R, h, B.ml, s1);
+        void* mlr = reduce_pairs(B.ml, B.ml2, nml, (uint64_t)Kc * 2, fq12_pair_reduce, s1);
+        step1_gt_out(mlr, Kc, 1, blocks1, blen, s1);
+        wait(s1, ev_sp);
+        step1_challenge(blocks1, blen, Kc, 1, B.xprev, xm(1), xim(1), B.xinv_all, lr, s1);
+        ev_x[1] = rec(s1);
+    }
+    fold(1);
+    for (int j = 2; j <= lr; j++) {
+        if (j + 1 <= lr) {
+            wait(sL, ev_S[j]);
+            lookahead(j + 1);
+        }
+        fold_pre(j, ev_S[j]);
+        wait(s1, ev_la[j]);
+        la_gt(L.fe[j & 1], xm(j - 1), xim(j - 1), Kc, L.pw, s1);
+        la_out(L.fe[j & 1], L.pw, L.acc[j & 1], xm(j - 1), xim(j - 1), Kc, j, blocks1, blen, s1);
+        step1_challenge(blocks1, blen, Kc, j, B.xprev, xm(j), xim(j), B.xinv_all, lr, s1);
+        ev_x[j] = rec(s1);
+        fold(j);
+    }
+    wait(s1, ev_S[lr + 1]);
+    step1_kzg(B.A, B.v, B.xprev, B.xinv_all, Kc, R, lr, blocks1, blen, B.pcoef, B.q, s1);
+    uint8_t* w_out = blocks1 + (size_t)lr * ROUND_BYTES + G1_SER + G2_SER;
+    if (B.w_msm) {
+        msm_g2(pp->g2w_tab, B.q, B.wsh, B.wscr, nullptr, w_out, blen, s1);
+    } else {
+        step1_w_terms(pp->g2pow, B.q, Kc, R, B.wt, s1);
+        void* wr = reduce_pairs(B.wt, B.wt2, (uint64_t)Kc * 2 * R, Kc, g2_pair_reduce, s1);
+        g2j_to_affine(wr, nullptr, w_out, blen, Kc, s1);
+    }
+    for (cudaEvent_t e : evs) cudaEventDestroy(e);
 }
 
 // OpenAll's work with Step 1 restricted to the blocks [k0, k0 + Kc) (all blocks: k0 = 0, Kc = K):
