@@ -59,7 +59,7 @@ def direct_round(A, v, b, x, h2):
     return LT + L1 + RT + R1
 
 
-@pytest.mark.parametrize("K,R,h2,k0,bsz", [(2, 8, 2, 0, 3), (1, 16, 1, 1, 5)])
+@pytest.mark.parametrize("K,R,h2,k0,bsz", [(2, 4, 1, 0, 3), (1, 16, 2, 1, 5)])
 def test_lookahead_round_equals_direct_round(la, K, R, h2, k0, bsz):
     rnd = random.Random(K * 1000 + R * 10 + h2)
     h = 2 * h2
