@@ -17,18 +17,23 @@ void la_sparse(const void* A, const void* bvec, uint32_t k0, uint32_t K, uint32_
     FP_KERNEL("k_la_sparse", s, k_la_sparse<<<(unsigned)(((uint64_t)2 * K * cmax + 15) / 16), 128, 0, s>>>(
                                     (const g1a*)A, (const fr*)bvec, k0, K, R, h2, b, cmax, (g1j*)out));
 }
-void la_gt(const void* fe, const void* x_mont, const void* xinv_mont, uint32_t K, void* pw, cudaStream_t s) {
-    FP_KERNEL("k_la_gt_c", s, k_la_gt_c<<<4 * K, 128, 0, s>>>((const fq12*)fe, (const fr*)x_mont, (const fr*)xinv_mont,
-                                                             (fq12*)pw));
+void la_pre(const void* fe, const void* acc, uint32_t K, void* gpre, void* acc2, cudaStream_t s) {
+    FP_KERNEL("k_la_gt_pre", s, k_la_gt_pre<<<4 * K, 128, 0, s>>>((const fq12*)fe, (fq12*)gpre));
+    FP_KERNEL("k_la_g1_pre", s, k_la_g1_pre<<<(4 * K + 15) / 16, 128, 0, s>>>((const g1a*)acc, K, (g1a*)acc2));
 }
-void la_out(const void* fe, const void* pw, const void* acc, const void* x_mont, const void* xinv_mont, uint32_t K,
-            int j, void* blocks, size_t bopen_len, cudaStream_t s) {
+void la_gt(const void* fe, const void* gpre, const void* x_mont, const void* xinv_mont, uint32_t K, void* pwp,
+           cudaStream_t s) {
+    FP_KERNEL("k_la_gt_c", s, k_la_gt_c<<<16 * K, 128, 0, s>>>((const fq12*)fe, (const fq12*)gpre,
+                                                              (const fr*)x_mont, (const fr*)xinv_mont, (fq12*)pwp));
+}
+void la_out(const void* fe, const void* pwp, const void* acc, const void* acc2, const void* x_mont,
+            const void* xinv_mont, uint32_t K, int j, void* blocks, size_t bopen_len, cudaStream_t s) {
     uint8_t* rec = (uint8_t*)blocks + (size_t)(j - 1) * ROUND_BYTES;
-    FP_KERNEL("k_la_gt_out", s, k_la_gt_out<<<2 * K, 128, 0, s>>>((const fq12*)fe, (const fq12*)pw, rec, bopen_len,
+    FP_KERNEL("k_la_gt_out", s, k_la_gt_out<<<2 * K, 128, 0, s>>>((const fq12*)fe, (const fq12*)pwp, rec, bopen_len,
                                                                  GT_SER + G1_SER));
-    FP_KERNEL("k_la_g1_out", s, k_la_g1_out<<<(4 * K + 15) / 16, 128, 0, s>>>((const g1a*)acc, (const fr*)x_mont,
-                                                                              (const fr*)xinv_mont, K, rec + GT_SER,
-                                                                              bopen_len, GT_SER + G1_SER));
+    FP_KERNEL("k_la_g1_out", s, k_la_g1_out<<<K, 128, 0, s>>>((const g1a*)acc, (const g1a*)acc2, (const fr*)x_mont,
+                                                             (const fr*)xinv_mont, K, rec + GT_SER, bopen_len,
+                                                             GT_SER + G1_SER));
 }
 
 }  // namespace fpk

@@ -85,15 +85,19 @@ void step1_fold_pre(const void* A, const void* v, void* A2, void* v2, uint32_t K
 void step1_fold(void* A, void* v, void* bvec, const void* x_mont, const void* xinv_mont, uint32_t K, uint32_t R,
                 uint32_t h, const void* A2, const void* v2, cudaStream_t s);
 // Look-ahead rounds (lookahead.cuh): round j's record from round j-1's state (half-length h = 2 h2)
-// and challenge.  la_miller: the 8 K h2 Miller values by class (then pairwise products to 8 K and their
-// final exponentiations); la_sparse: the 6 K (4 h2) G1 terms (then pairwise sums to 6 K, affine);
-// after the challenge la_gt (4 K exponentiations in GT) and la_out (round j's record).
+// and challenge.  Before the challenge: la_miller (the 8 K h2 Miller values by class; then pairwise
+// products to 8 K and their final exponentiations, fe), la_sparse (the 6 K (4 h2) G1 terms; then
+// pairwise sums to 6 K, affine, acc), la_pre (the shifted bases of the 4-part GT exponentiations and
+// G1 multiplications: gpre 12 K Fq12, acc2 12 K G1).  After it: la_gt (the 16 K exponentiation
+// parts, pwp) and la_out (round j's record).
 void la_miller(const void* A, const void* v, uint32_t K, uint32_t R, uint32_t h2, void* out_fq12, cudaStream_t s);
 void la_sparse(const void* A, const void* bvec, uint32_t k0, uint32_t K, uint32_t R, uint32_t h2, uint32_t b,
                void* out_g1j, cudaStream_t s);
-void la_gt(const void* fe_fq12, const void* x_mont, const void* xinv_mont, uint32_t K, void* pw_fq12, cudaStream_t s);
-void la_out(const void* fe_fq12, const void* pw_fq12, const void* acc_g1a, const void* x_mont, const void* xinv_mont,
-            uint32_t K, int j, void* blocks, size_t bopen_len, cudaStream_t s);
+void la_pre(const void* fe_fq12, const void* acc_g1a, uint32_t K, void* gpre_fq12, void* acc2_g1a, cudaStream_t s);
+void la_gt(const void* fe_fq12, const void* gpre_fq12, const void* x_mont, const void* xinv_mont, uint32_t K,
+           void* pwp_fq12, cudaStream_t s);
+void la_out(const void* fe_fq12, const void* pwp_fq12, const void* acc_g1a, const void* acc2_g1a, const void* x_mont,
+            const void* xinv_mont, uint32_t K, int j, void* blocks, size_t bopen_len, cudaStream_t s);
 void step1_challenge(void* blocks, size_t bopen_len, uint32_t K, int j, void* xprev, void* x_mont, void* xinv_mont,
                      void* xinv_all, int log_r, cudaStream_t s);
 void step1_kzg(const void* A, const void* v, const void* xprev, const void* xinv_all, uint32_t K, uint32_t R,

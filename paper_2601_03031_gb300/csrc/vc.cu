@@ -467,11 +467,11 @@ Step1Bufs step1_bufs(const fp_pp* pp, uint32_t Kc, Alloc&& T) {
 }
 
 // Look-ahead buffers (lookahead.cuh) for Kc blocks of R rows: a snapshot of round j-1's state, the
-// Miller values by class and their pairwise products (8 Kc h2 <= 2 Kc R), the final exponentiations
-// and affine G1 sums of two rounds in flight, the GT powers, the G1 terms (6 Kc 4 h2 <= 6 Kc R) and
-// their pairwise sums
+// Miller values by class and their pairwise products (8 Kc h2 <= 2 Kc R), the final exponentiations,
+// affine G1 sums and shifted bases of two rounds in flight, the exponentiation parts, the G1 terms
+// (6 Kc 4 h2 <= 6 Kc R) and their pairwise sums
 struct LaBufs {
-    void *A, *v, *bvec, *ml, *ml2, *fe[2], *pw, *sp, *sp2, *acc[2];
+    void *A, *v, *bvec, *ml, *ml2, *fe[2], *gpre[2], *acc[2], *acc2[2], *pwp, *sp, *sp2;
 };
 template <class Alloc>
 LaBufs la_bufs(const fp_pp* pp, uint32_t Kc, Alloc&& T) {
@@ -484,9 +484,11 @@ LaBufs la_bufs(const fp_pp* pp, uint32_t Kc, Alloc&& T) {
     L.ml2 = T((KR + 1) * FQ12_BYTES);
     for (int i = 0; i < 2; i++) {
         L.fe[i] = T((size_t)8 * Kc * FQ12_BYTES);
+        L.gpre[i] = T((size_t)12 * Kc * FQ12_BYTES);
         L.acc[i] = T((size_t)6 * Kc * G1A_BYTES);
+        L.acc2[i] = T((size_t)12 * Kc * G1A_BYTES);
     }
-    L.pw = T((size_t)4 * Kc * FQ12_BYTES);
+    L.pwp = T((size_t)16 * Kc * FQ12_BYTES);
     L.sp = T(6 * KR * G1J_BYTES);
     L.sp2 = T((3 * KR + 1) * G1J_BYTES);
     return L;
@@ -575,6 +577,7 @@ void step1_rounds(const fp_pp* pp, uint32_t k0, uint32_t Kc, uint32_t b, const S
         la_sparse(L.A, L.bvec, k0, Kc, R, h2, b, L.sp, sL);
         void* spr = reduce_pairs(L.sp, L.sp2, (uint64_t)Kc * 24 * h2, (uint64_t)Kc * 6, g1_pair_reduce, sL);
         g1j_to_affine(spr, L.acc[j & 1], nullptr, 0, (uint64_t)Kc * 6, sL);
+        la_pre(L.fe[j & 1], L.acc[j & 1], Kc, L.gpre[j & 1], L.acc2[j & 1], sL);
         ev_la[j] = rec(sL);
     };
     // round j's fold on sF (after x_j, the shifted bases and the snapshot of S_j for round j + 1)
@@ -623,8 +626,8 @@ void step1_rounds(const fp_pp* pp, uint32_t k0, uint32_t Kc, uint32_t b, const S
         }
         fold_pre(j, ev_S[j]);
         wait(s1, ev_la[j]);
-        la_gt(L.fe[j & 1], xm(j - 1), xim(j - 1), Kc, L.pw, s1);
-        la_out(L.fe[j & 1], L.pw, L.acc[j & 1], xm(j - 1), xim(j - 1), Kc, j, blocks1, blen, s1);
+        la_gt(L.fe[j & 1], L.gpre[j & 1], xm(j - 1), xim(j - 1), Kc, L.pwp, s1);
+        la_out(L.fe[j & 1], L.pwp, L.acc[j & 1], L.acc2[j & 1], xm(j - 1), xim(j - 1), Kc, j, blocks1, blen, s1);
         step1_challenge(blocks1, blen, Kc, j, B.xprev, xm(j), xim(j), B.xinv_all, lr, s1);
         ev_x[j] = rec(s1);
         fold(j);

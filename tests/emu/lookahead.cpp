@@ -57,7 +57,7 @@ extern "C" void emu_la_round(uint32_t K, uint32_t R, uint32_t h2, uint32_t k0, u
     }
     for (uint32_t k = 0; k < K; k++) { xm[k] = be_fr(x_be + 32 * k); xim[k] = fr_inv(xm[k]); }
     // pairings: Miller loops, products per class, final exponentiations
-    std::vector<fq12> ml((size_t)K * 8 * h2), fe((size_t)K * 8), pw((size_t)K * 4);
+    std::vector<fq12> ml((size_t)K * 8 * h2), fe((size_t)K * 8);
     grid((uint64_t)K * 8 * h2, [&] { k_la_miller_c(A.data(), v.data(), R, h2, ml.data()); });
     for (uint32_t c = 0; c < K * 8; c++) {                 // (the engines' final exponentiation is
         fq12 prod = ml[(size_t)c * h2];                      // checked on its own elsewhere)
@@ -77,11 +77,15 @@ extern "C" void emu_la_round(uint32_t K, uint32_t R, uint32_t h2, uint32_t k0, u
         for (uint32_t p = 1; p < 2 * h; p++) s = jac_add(s, terms[(size_t)c * 2 * h + p]);
         acc[c] = g1_affine(s);
     }
-    // after the challenge
+    // the shifted bases, then after the challenge the parts and the record
+    std::vector<fq12> gpre((size_t)K * 12), pwp((size_t)K * 16);
+    std::vector<g1a> acc2((size_t)K * 12);
+    grid((uint64_t)K * 4, [&] { k_la_gt_pre(fe.data(), gpre.data()); });
+    grid(((uint64_t)4 * K + 15) / 16, [&] { k_la_g1_pre(acc.data(), K, acc2.data()); });
     const size_t GT = 576, G1 = 96, stride_side = GT + G1, stride_k = 2 * (GT + G1);
-    grid((uint64_t)K * 4, [&] { k_la_gt_c(fe.data(), xm.data(), xim.data(), pw.data()); });
-    grid((uint64_t)K * 2, [&] { k_la_gt_out(fe.data(), pw.data(), rec_out, stride_k, stride_side); });
-    grid(((uint64_t)4 * K + 15) / 16, [&] {
-        k_la_g1_out(acc.data(), xm.data(), xim.data(), K, rec_out + GT, stride_k, stride_side);
+    grid((uint64_t)K * 16, [&] { k_la_gt_c(fe.data(), gpre.data(), xm.data(), xim.data(), pwp.data()); });
+    grid((uint64_t)K * 2, [&] { k_la_gt_out(fe.data(), pwp.data(), rec_out, stride_k, stride_side); });
+    grid((uint64_t)K, [&] {
+        k_la_g1_out(acc.data(), acc2.data(), xm.data(), xim.data(), K, rec_out + GT, stride_k, stride_side);
     });
 }
