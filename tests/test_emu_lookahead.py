@@ -1,5 +1,7 @@
 """The look-ahead round kernels (lookahead.cuh) compiled for the host and checked against a direct
-round computed with the oracle's group operations (no GPU).
+round computed with the oracle's group operations (no GPU).  Cases: two blocks covering all four
+quadrants of b's support; a stride beyond the live state with two pairs per class; a block larger
+than the live state (b dense over it, as in a late round or the evaluation proof).
 
 From a state A, v, b of round j-1 (length 2h per block) and its challenge x, the kernels produce
 round j's record L_j.T, L_j.1, R_j.T, R_j.1 without folding first; the reference folds
@@ -59,7 +61,7 @@ def direct_round(A, v, b, x, h2):
     return LT + L1 + RT + R1
 
 
-@pytest.mark.parametrize("K,R,h2,k0,bsz", [(2, 4, 1, 0, 3), (1, 16, 2, 1, 5)])
+@pytest.mark.parametrize("K,R,h2,k0,bsz", [(2, 4, 1, 0, 3), (1, 16, 2, 1, 5), (1, 16, 1, 0, 16)])
 def test_lookahead_round_equals_direct_round(la, K, R, h2, k0, bsz):
     rnd = random.Random(K * 1000 + R * 10 + h2)
     h = 2 * h2
