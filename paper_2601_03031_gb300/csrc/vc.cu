@@ -5,6 +5,7 @@
 
 #include <algorithm>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <mutex>
 #include <string>
@@ -133,7 +134,7 @@ size_t bopen_len(uint32_t log_r) { return (size_t)log_r * ROUND_BYTES + G1_SER +
 // created per call.  Each caller stream (per device) gets its own set, so calls on different caller
 // streams run concurrently; past 256 caller streams the sets are shared (still correct, less
 // concurrent).
-struct Streams { cudaStream_t hi = nullptr, sp = nullptr, pre = nullptr, lo = nullptr; };
+struct Streams { cudaStream_t hi = nullptr, sp = nullptr, pre = nullptr, la = nullptr, fold = nullptr, lo = nullptr; };
 struct StreamKey { int dev; cudaStream_t user; Streams set; };
 std::vector<StreamKey> g_sets;
 std::mutex g_aux_mu;
@@ -144,6 +145,8 @@ Streams make_set() {
     check(cudaStreamCreateWithPriority(&a.hi, cudaStreamNonBlocking, hi), "cudaStreamCreate");
     check(cudaStreamCreateWithPriority(&a.sp, cudaStreamNonBlocking, hi), "cudaStreamCreate");
     check(cudaStreamCreateWithPriority(&a.pre, cudaStreamNonBlocking, hi), "cudaStreamCreate");
+    check(cudaStreamCreateWithPriority(&a.la, cudaStreamNonBlocking, hi), "cudaStreamCreate");
+    check(cudaStreamCreateWithPriority(&a.fold, cudaStreamNonBlocking, hi), "cudaStreamCreate");
     check(cudaStreamCreateWithPriority(&a.lo, cudaStreamNonBlocking, lo), "cudaStreamCreate");
     return a;
 }
@@ -549,9 +552,9 @@ void step1_rounds(const fp_pp* pp, uint32_t k0, uint32_t Kc, uint32_t b, const S
 // reading x_{j-1} never meets x_j.  Streams: s1 challenges, s3 round 1's sparse G1 terms, s4 the
 // shifted fold bases, sL the look-ahead, sF the folds; s3 must already be ordered after whatever
 // filled B.bvec, s1 after B.A and B.v.
-[[maybe_unused]] void step1_rounds_la(const fp_pp* pp, uint32_t k0, uint32_t Kc, uint32_t b, const Step1Bufs& B,
-                                      const LaBufs& L, uint8_t* blocks1, size_t blen, cudaStream_t s1,
-                                      cudaStream_t s3, cudaStream_t s4, cudaStream_t sL, cudaStream_t sF) {
+void step1_rounds_la(const fp_pp* pp, uint32_t k0, uint32_t Kc, uint32_t b, const Step1Bufs& B,
+                     const LaBufs& L, uint8_t* blocks1, size_t blen, cudaStream_t s1, cudaStream_t s3,
+                     cudaStream_t s4, cudaStream_t sL, cudaStream_t sF) {
     const uint32_t R = pp->R;
     const int lr = (int)pp->log_r;
     const uint64_t KR = (uint64_t)Kc * R;
@@ -645,6 +648,17 @@ void step1_rounds(const fp_pp* pp, uint32_t k0, uint32_t Kc, uint32_t b, const S
     for (cudaEvent_t e : evs) cudaEventDestroy(e);
 }
 
+// Step 1 with look-ahead rounds when FP_LOOKAHEAD=1 is set in the environment and the blocks are few
+// (K R <= 4096: the look-ahead runs four times a round's Miller loops beside the chain); the records
+// are the same, the chain of dependent launches shorter.  Off by default.
+bool lookahead_on(uint32_t Kc, uint32_t R, int log_r) {
+    static const bool env = [] {
+        const char* e = getenv("FP_LOOKAHEAD");
+        return e && e[0] == '1';
+    }();
+    return env && log_r >= 2 && (uint64_t)Kc * R <= 4096;
+}
+
 // OpenAll's work with Step 1 restricted to the blocks [k0, k0 + Kc) (all blocks: k0 = 0, Kc = K):
 // their records are written at their places in the K-block array; Step 2 runs in full.
 fp_proofs* prove_impl(const fp_pp* pp, const fp_commit* cm, uint32_t b, uint32_t k0, uint32_t Kc, cudaStream_t s,
@@ -686,6 +700,8 @@ fp_proofs* prove_impl(const fp_pp* pp, const fp_commit* cm, uint32_t b, uint32_t
             }
             // every buffer is allocated (stream-ordered on s) before the fork to the internal streams
             const Step1Bufs B = step1_bufs(pp, Kc, T);
+            const bool la = lookahead_on(Kc, R, lr);
+            const LaBufs L = la ? la_bufs(pp, Kc, T) : LaBufs{};
             void* hstmt = T(Kc * DIGEST);
             const Streams st = streams(s);
             cudaStream_t s2 = st.lo, s1 = st.hi, s3 = st.sp;
@@ -730,7 +746,8 @@ fp_proofs* prove_impl(const fp_pp* pp, const fp_commit* cm, uint32_t b, uint32_t
             check(cudaStreamWaitEvent(s3, ev_init, 0), "wait");
             step1_stmt_hash(cm->C_ser, cm->rows_ser, k0, Kc, R, b, hstmt, s3);
             step1_block_r(hstmt, k0, Kc, R, b, B.bvec, s3);
-            step1_rounds(pp, k0, Kc, b, B, blocks1, blen, s1, s3, st.pre);
+            if (la) step1_rounds_la(pp, k0, Kc, b, B, L, blocks1, blen, s1, s3, st.pre, st.la, st.fold);
+            else step1_rounds(pp, k0, Kc, b, B, blocks1, blen, s1, s3, st.pre);
             check(cudaEventRecord(ev_join1, s1), "event");
             check(cudaStreamWaitEvent(s, ev_join1, 0), "join");
             cudaEventDestroy(ev_init);
@@ -988,6 +1005,8 @@ fp_status vc_eval_prove(const fp_pp* pp, const fp_commit* cm, const uint8_t* r, 
             void* terms = T((size_t)(lc ? lc : 1) * half * G1J_BYTES);
             void* terms2 = T((half / 2 + 1) * G1J_BYTES);
             const Step1Bufs B = step1_bufs(pp, 1, T);
+            const bool la = lookahead_on(1, R, (int)pp->log_r);
+            const LaBufs L = la ? la_bufs(pp, 1, T) : LaBufs{};
             const Streams st = streams(s);
             cudaStream_t s1 = st.hi, s3 = st.sp;
             cudaEvent_t ev_fork = new_event(), ev_bvec = new_event(), ev_join = new_event();
@@ -1006,7 +1025,8 @@ fp_status vc_eval_prove(const fp_pp* pp, const fp_commit* cm, const uint8_t* r, 
             eval_bvec(cm->C_ser, r_be, ln, proof + 32, Tm, R, r0, B.bvec, s1);
             check(cudaEventRecord(ev_bvec, s1), "event");
             check(cudaStreamWaitEvent(s3, ev_bvec, 0), "wait");
-            step1_rounds(pp, 0, 1, R, B, proof + 128, blen, s1, s3, st.pre);
+            if (la) step1_rounds_la(pp, 0, 1, R, B, L, proof + 128, blen, s1, s3, st.pre, st.la, st.fold);
+            else step1_rounds(pp, 0, 1, R, B, proof + 128, blen, s1, s3, st.pre);
             // step 3: PST.Eval of F = sum_j T_j f_j at r_R
             eval_ftable(cm->m_mont, Tm, R, M, F, s1);
             eval_pst_fold(F, r_mont, lc, q, proof, s1);
