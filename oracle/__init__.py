@@ -13,8 +13,11 @@ Parity status per function (the pins live in ``tests/test_oracle_*.py``):
     from-the-definition Miller function in pure Python.
   - PST / FC / VC: pinned by trapdoor closed forms, the FC round invariant, brute-force
     ProveOne, every proof verifying, tamper rejection and the paper's proof-size formula.
-  - Absolute bytes of Fiat-Shamir outputs (x_j, r_j, the proofs): parity unpinned beyond
-    self-consistency -- they depend on readings of hash encodings the paper leaves open.
+  - Absolute bytes of Fiat-Shamir and Merkle outputs (r_a, x_j, z, every digest, r_j, every
+    proof byte): pinned by an independent pure-Python re-derivation from hashlib, HFr and the
+    known discrete logarithms (tests/test_oracle_transcript.py), which also checks that changing
+    any one encoding reading is detected.  The readings themselves are choices where the paper
+    leaves the random oracles and the Merkle instantiation open.
 """
 from __future__ import annotations
 
