@@ -213,9 +213,19 @@ fp_status vc_proof_get(const fp_proofs* pf, uint64_t i, uint8_t* out, size_t cap
  * lengths differ only for the last, truncated block; *len receives the total byte count. */
 fp_status vc_proofs_export(const fp_proofs* pf, uint64_t i0, uint64_t count, uint8_t* out, size_t cap, size_t* len);
 
-/* Device-to-host copy of the shared proof state (synchronises), the compact result of OpenAll:
- * all blocks' pi_{C_k}, every Merkle digest, every fold-tree node (D_w, g_w) and the PST proofs.
- * *len receives the size; out may be NULL to query it. */
+/* Device-to-host copy of the shared proof state (synchronises), the compact result of OpenAll
+ * (Protocol 1 Steps 1 and 2 with the Sub-protocol and HyperEval, Sec. 4.2); every element proof is
+ * a selection of these bytes.  Layout, all canonical big-endian, concatenated in this order:
+ *   K x bopen_len   pi_{C_k} of every block k (zeros for blocks a vc_open_segments call did not open)
+ *   R x (2M-1) x 32 the per-row Merkle trees, each leaves first, then every parent level in turn
+ *                   (level l of a tree over n leaves at offset 2n - 2n/2^l)
+ *   (2R-1) x 32     the tree over the row leaves, same level layout (the root last)
+ *   R x 32          r_j
+ *   (2R-1) x 96     D_w for every fold-tree node w (same node order: level h node s at 2R - 2R/2^h + s)
+ *   (2R-1) x M x 32 g_w for every node, in that node order
+ *   (M-1) x 96      HyperEval's PST quotient commitments, level t = 0 .. l_c-1, prefix p at
+ *                   sum_{s<t} M/2^(s+1) + p
+ * *len receives the size; out may be NULL to query it.  FP_EINVAL for a handle without Step 2. */
 fp_status vc_proofs_state(const fp_proofs* pf, uint8_t* out, size_t cap, size_t* len);
 
 /* Pieces for parity checks (synchronise): the Merkle root (32 B), r_j (R x 32 B), g* (M x 32 B)

@@ -84,6 +84,8 @@ def lib():
             L.or_proof_len.argtypes = [vp, ctypes.c_uint32, ctypes.c_uint32]
             L.or_prover_proof.argtypes = [vp, ctypes.c_uint64, vp, ctypes.c_size_t, vp]
             L.or_prover_step2_parts.argtypes = [vp, vp, vp, vp, vp]
+            L.or_prover_state.restype = ctypes.c_size_t
+            L.or_prover_state.argtypes = [vp, vp]
             L.or_prove_one.argtypes = [vp, vp, vp, vp, ctypes.c_uint32, ctypes.c_uint64, vp, ctypes.c_size_t, vp]
             L.or_verify.argtypes = [vp, vp, ctypes.c_uint32, ctypes.c_uint64, vp, vp, ctypes.c_size_t, ctypes.c_int]
             L.or_const.argtypes = [ctypes.c_int, vp]
@@ -361,6 +363,15 @@ class Prover:
         root = _buf(32); rj = _buf(32 * self.pp.R); gs = _buf(32 * self.pp.M); ds = _buf(96)
         lib().or_prover_step2_parts(self.h, root, rj, gs, ds)
         return root.raw, rj.raw, gs.raw, ds.raw
+
+    def state(self) -> bytes:
+        """All shared proof state (block records, Merkle trees, r_j, D_w, g_w, PST quotients) in the
+        layout of the GPU library's state export; blocks not run are zeros."""
+        n = lib().or_prover_state(self.h, None)
+        o = _buf(n)
+        if lib().or_prover_state(self.h, o) != n:
+            raise ValueError("or_prover_state: Step 2 has not run")
+        return o.raw
 
     def proof(self, i: int) -> bytes:
         k = (i // self.pp.M) // self.b

@@ -509,6 +509,28 @@ int or_prover_proof(const or_prover* P, u64 i, u8* out, size_t cap, size_t* len)
     return 0;
 }
 
+/* The whole shared proof state in one byte string (test access; the layout of the GPU library's
+ * state export): K block records (zeros for blocks not run) || R row trees || the top tree || r_j ||
+ * D_w for every fold-tree node || g_w for every node || the PST quotient commitments.  Returns the
+ * size; out may be NULL to query it. */
+size_t or_prover_state(const or_prover* P, u8* out) {
+    const or_pp* pp = P->pp; const u32 R = pp->R, M = pp->M;
+    const size_t nb = (size_t)P->K * or_bopen_len(pp), nrt = (size_t)R * (2 * M - 1) * 32, ntt = (2 * (size_t)R - 1) * 32;
+    const size_t nw = 2 * (size_t)R - 1;
+    const size_t total = nb + nrt + ntt + 32 * (size_t)R + 96 * nw + 32 * nw * M + 96 * ((size_t)M - 1);
+    if (!out) return total;
+    if (!P->step2_done) return 0;
+    u8* o = out;
+    memcpy(o, P->blocks, nb); o += nb;
+    memcpy(o, P->row_tree, nrt); o += nrt;
+    memcpy(o, P->top_tree, ntt); o += ntt;
+    for (u32 j = 0; j < R; j++) { fr_to_bytes(o, &P->rj[j]); o += 32; }
+    for (size_t w = 0; w < nw; w++) { g1_to_bytes(o, &P->D[w]); o += 96; }
+    for (size_t q = 0; q < nw * M; q++) { fr_to_bytes(o, &P->gt[q]); o += 32; }
+    for (u32 q = 0; q + 1 < M; q++) { g1_to_bytes(o, &P->pst[q]); o += 96; }
+    return total;
+}
+
 /* digest of the whole shared proof state (Merkle root, r_j, fold tables, D, PST) for tests */
 void or_prover_step2_parts(const or_prover* P, u8* root, u8* rj, u8* gstar, u8* dstar) {
     const u32 R = P->pp->R, M = P->pp->M;

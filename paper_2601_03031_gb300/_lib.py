@@ -242,6 +242,14 @@ class Proofs:
         _check("vc_proofs_export", L.vc_proofs_export(self.h, i0, count, buf, ln.value, ctypes.byref(ln)))
         return buf.raw
 
+    def state(self) -> bytes:
+        """The shared proof state as bytes (layout in include/flexproofs.h, vc_proofs_state)."""
+        n = self.state_size()
+        buf = ctypes.create_string_buffer(n)
+        ln = ctypes.c_size_t()
+        _check("vc_proofs_state", load().vc_proofs_state(self.h, buf, n, ctypes.byref(ln)))
+        return buf.raw
+
     def state_size(self) -> int:
         ln = ctypes.c_size_t()
         _check("vc_proofs_state", load().vc_proofs_state(self.h, None, 0, ctypes.byref(ln)))

@@ -1237,10 +1237,10 @@ fp_status vc_proof_get(const fp_proofs* pf, uint64_t i, uint8_t* out, size_t cap
 fp_status vc_proofs_state(const fp_proofs* pf, uint8_t* out, size_t cap, size_t* len) {
     if (!pf || !len || !pf->step2) return FP_EINVAL;
     const ProofLayout& L = pf->L;
-    const size_t parts[6] = {(size_t)L.K * L.bopen_len, (size_t)L.R * (2 * L.M - 1) * DIGEST,
-                             (2 * (size_t)L.R - 1) * DIGEST, (2 * (size_t)L.R - 1) * G1_SER,
-                             (2 * (size_t)L.R - 1) * L.M * FR_BYTES, ((size_t)L.M - 1) * G1_SER};
-    const void* src[6] = {pf->blocks, pf->row_tree, pf->top_tree, pf->D_ser, pf->g, pf->pst_ser};
+    const uint64_t ng = (2 * (uint64_t)L.R - 1) * L.M;
+    const size_t parts[7] = {(size_t)L.K * L.bopen_len, (size_t)L.R * (2 * L.M - 1) * DIGEST,
+                             (2 * (size_t)L.R - 1) * DIGEST, (size_t)L.R * 32, (2 * (size_t)L.R - 1) * G1_SER,
+                             ng * 32, ((size_t)L.M - 1) * G1_SER};
     size_t total = 0;
     for (size_t p : parts) total += p;
     *len = total;
@@ -1248,11 +1248,19 @@ fp_status vc_proofs_state(const fp_proofs* pf, uint8_t* out, size_t cap, size_t*
     if (cap < total) return FP_EINVAL;
     return guarded([&]() -> fp_status {
         cudaStream_t s = pf->stream;
+        // r_j and the fold tables leave in the exchanged encoding (canonical big-endian)
+        void* d = dalloc(parts[3] + parts[5], s);
+        fr_serialize(pf->rj, L.R, d, s);
+        fr_serialize(pf->g, ng, (uint8_t*)d + parts[3], s);
+        check_launch("vc_proofs_state");
+        const void* src[7] = {pf->blocks, pf->row_tree, pf->top_tree, d, pf->D_ser, (uint8_t*)d + parts[3],
+                              pf->pst_ser};
         size_t off = 0;
-        for (int q = 0; q < 6; q++) {
+        for (int q = 0; q < 7; q++) {
             check(cudaMemcpyAsync(out + off, src[q], parts[q], cudaMemcpyDeviceToHost, s), "D2H state");
             off += parts[q];
         }
+        dfree(d, s);
         check(cudaStreamSynchronize(s), "vc_proofs_state");
         return FP_OK;
     });

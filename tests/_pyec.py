@@ -10,7 +10,7 @@ from __future__ import annotations
 import functools
 
 from tests import _pypairing as pyp
-from tests._pyref import P, R
+from tests._pyref import P, R, mle_eval
 
 # ---------------------------------------------------------------- Fq2 = Fq[u]/(u^2 + 1)
 
@@ -141,3 +141,11 @@ class Groups:
             Px, Py = self.g1
             self._gt = pyp.pairing_tower((Px, Py), self.g2)
         return pyp.to_tower_bytes(pyp.power(self._gt, s % R))
+
+
+def commit_closed_form(grp: Groups, beta: int, tau: list[int], nrows: int, M: int, m: list[int]):
+    """VC.Commit from the trapdoor: C_j = g1^{f_j(tau)} and C = e(g1, g2)^{sum_j f_j(tau) beta^{2j}},
+    f_j the multilinear extension of row j (Eqs. genCi and genC).  Returns (C, rows) as bytes."""
+    f = [mle_eval(m[j * M:(j + 1) * M], tau) for j in range(nrows)]
+    rows = b"".join(grp.G1(v) for v in f)
+    return grp.GT(sum(f[j] * pow(beta, 2 * j, R) for j in range(nrows))), rows

@@ -6,6 +6,7 @@ import pytest
 
 import oracle as O
 from paper_2601_03031_gb300 import inputs as I
+from tests import _state
 
 pytestmark = pytest.mark.gpu
 
@@ -66,11 +67,12 @@ def test_batch_equals_single_calls_and_oracle(use_graph):
         ln, m = sizes[j], vecs[j]
         cm, b = jobs[j]
         opp = O.PP(ln, seed)
-        C, rows = cm.get()
-        assert (C, rows) == O.commit(opp, m.tobytes())
+        C, rows = O.commit(opp, m.tobytes())
+        assert cm.get() == (C, rows)
         pr = O.Prover(opp, m.tobytes(), C, rows, b)
         pr.blocks()
         pr.step2()
+        _state.assert_equal(state(outs[j]), pr.state(), cm.pp.R, cm.pp.M, pr.K, opp.log_r)
         assert outs[j].export(0, cm.pp.N) == b"".join(pr.proof(i) for i in range(cm.pp.N))
 
 
@@ -96,9 +98,11 @@ def test_batched_workload_64_jobs_sampled():
     ln, cm, b = jobs_spec[j]["log_n"], jobs[j][0], jobs[j][1]
     opp = O.PP(ln, 4)
     m = I.vector(jobs_spec[j]["seed"], ln)
-    C, rows = cm.get()
+    C, rows = O.commit(opp, m.tobytes())
+    assert cm.get() == (C, rows)
     pr = O.Prover(opp, m.tobytes(), C, rows, b)
     pr.blocks([0])
     pr.step2()
+    _state.assert_equal(state(outs[j]), pr.state(), cm.pp.R, cm.pp.M, pr.K, opp.log_r, [0])
     for i in (0, 7, cm.pp.M - 1):
         assert outs[j].proof(i) == pr.proof(i)

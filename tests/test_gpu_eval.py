@@ -8,6 +8,7 @@ import pytest
 
 import oracle as O
 from paper_2601_03031_gb300 import inputs as I
+from tests import _pyec
 
 pytestmark = pytest.mark.gpu
 
@@ -30,7 +31,8 @@ def test_eval_proof_equals_oracle(log_n, log_r):
     opp = O.PP(log_n, seed, log_r=log_r)
     m = I.vector(seed + 1, log_n)
     cm = F.Commitment(pp, m)
-    C, rows = cm.get()
+    C, rows = O.commit(opp, m.tobytes())
+    assert cm.get() == (C, rows)
     for ps in (1, 2):
         r = point(seed * 10 + ps, log_n)
         got = F.vc_eval_prove(pp, cm, r)
@@ -61,7 +63,10 @@ def test_eval_n16():
     opp = O.PP(log_n, seed)
     m = I.vector(seed + 1, log_n)
     cm = F.Commitment(pp, m)
-    C, rows = cm.get()
+    beta, tau = opp.trapdoor()
+    C, rows = _pyec.commit_closed_form(_pyec.Groups(O.g1_gen(), O.g2_gen()), beta, tau, opp.R, opp.M,
+                                       I.to_ints(m))
+    assert cm.get() == (C, rows)
     r = point(123, log_n)
     got = F.vc_eval_prove(pp, cm, r)
     assert O.eval_verify(opp, C, r, got)
@@ -79,7 +84,8 @@ def test_eval_verifier_rejections_agree_with_oracle():
     opp = O.PP(log_n, seed, log_r=log_r)
     m = I.vector(seed + 1, log_n)
     cm = F.Commitment(pp, m)
-    C, rows = cm.get()
+    C, rows = O.commit(opp, m.tobytes())
+    assert cm.get() == (C, rows)
     r = point(17, log_n)
     proof = F.vc_eval_prove(pp, cm, r)
     assert F.vc_eval_verify(pp, C, r, proof)

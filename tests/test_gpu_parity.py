@@ -16,6 +16,7 @@ import pytest
 import oracle as O
 from paper_2601_03031_gb300 import inputs as I
 from tests import _pyref as ref
+from tests import _pyec, _state
 
 pytestmark = pytest.mark.gpu
 
@@ -73,6 +74,7 @@ def test_prove_all_every_proof(log_n, b):
     pr.blocks()
     pr.step2()
     assert pf.step2_parts() == pr.step2_parts()
+    _state.assert_equal(pf.state(), pr.state(), pp.R, pp.M, pr.K, opp.log_r)
     got = pf.export(0, pp.N)
     exp = b"".join(pr.proof(i) for i in range(pp.N))
     assert got == exp
@@ -86,12 +88,13 @@ def test_config1_n1024_b1_all_proofs_and_verify():
     pp, opp = F.PP(log_n, b, seed), O.PP(log_n, seed)
     m = I.vector(seed, log_n)
     cm = F.Commitment(pp, m)
-    C, rows = cm.get()
-    assert (C, rows) == O.commit(opp, m.tobytes())
+    C, rows = O.commit(opp, m.tobytes())
+    assert cm.get() == (C, rows)
     pf = F.Proofs(pp, cm, b)
     pr = O.Prover(opp, m.tobytes(), C, rows, b)
     pr.blocks()
     pr.step2()
+    _state.assert_equal(pf.state(), pr.state(), pp.R, pp.M, pr.K, opp.log_r)
     got = pf.export(0, pp.N)
     off = 0
     vals = I.to_ints(m)
@@ -112,11 +115,12 @@ def test_empty_and_degenerate_vectors():
     for m in (np.zeros((16, 4), np.uint64), np.eye(1, 16, 9, dtype=np.uint64).reshape(16, 1) * np.array([5, 0, 0, 0], np.uint64)):
         m = np.ascontiguousarray(m, dtype=np.uint64)
         cm = F.Commitment(pp, m)
-        C, rows = cm.get()
-        assert (C, rows) == O.commit(opp, m.tobytes())
+        C, rows = O.commit(opp, m.tobytes())
+        assert cm.get() == (C, rows)
         pf = F.Proofs(pp, cm, b)
         pr = O.Prover(opp, m.tobytes(), C, rows, b)
         pr.blocks(); pr.step2()
+        _state.assert_equal(pf.state(), pr.state(), pp.R, pp.M, pr.K, opp.log_r)
         assert pf.export(0, 16) == b"".join(pr.proof(i) for i in range(16))
 
 
@@ -140,45 +144,47 @@ def test_device_input_matches_host_input():
 
 # ------------------------------------------------------------------ N = 2^16 (benchmark workload)
 def row_closed_form(opp, m_ints):
+    """(C, rows) from the oracle's trapdoor by the closed form, in pure Python (tests._pyec)."""
     beta, tau = opp.trapdoor()
-    g1 = O.g1_gen()
-    R, M = opp.R, opp.M
-    rows = []
-    fj = []
-    for j in range(R):
-        f = ref.mle_eval(m_ints[j * M:(j + 1) * M], tau)
-        fj.append(f)
-        rows.append(O.g1_mul(g1, f))
-    s = sum(fj[j] * pow(beta, 2 * j, ref.R) for j in range(R)) % ref.R
-    C = O.fq12_pow(O.pairing(g1, O.g2_gen()), s)
-    return C, b"".join(rows)
+    return _pyec.commit_closed_form(groups(), beta, tau, opp.R, opp.M, m_ints)
+
+
+@functools.lru_cache(maxsize=None)
+def groups():
+    return _pyec.Groups(O.g1_gen(), O.g2_gen())
 
 
 @functools.lru_cache(maxsize=None)
 def n16(dist):
+    """GPU commitment of the N = 2^16 vector, and the oracle side's commitment from the trapdoor
+    closed form (the oracle's inputs never come from the GPU)."""
     log_n, seed = 16, 0
     pp, opp = gpu_pp(log_n, seed), oracle_pp(log_n, seed)
     m = vec(log_n, seed + 1, dist)
     cm = F.Commitment(pp, m)
-    return pp, opp, m, cm
+    return pp, opp, m, cm, row_closed_form(opp, I.to_ints(m))
 
 
 @pytest.mark.parametrize("dist", ["uniform", "u32"])
 def test_n16_commit_closed_form(dist):
-    pp, opp, m, cm = n16(dist)
-    assert cm.get() == row_closed_form(opp, I.to_ints(m))
+    pp, opp, m, cm, exp = n16(dist)
+    assert cm.get() == exp
 
 
-@pytest.mark.parametrize("b,blocks,dist", [(256, [0], "uniform"), (1, [0, 77, 255], "uniform"), (256, [0], "u32"),
-                                          (1, [0, 255], "u32")])
+@pytest.mark.parametrize("b,blocks,dist", [(256, [0], "uniform"), (1, [0, 77, 128, 255], "uniform"),
+                                          (256, [0], "u32"), (1, [0, 255], "u32")])
 def test_n16_prove_all_sampled(b, blocks, dist):
-    pp, opp, m, cm = n16(dist)
-    C, rows = cm.get()
+    """OpenAll at N = 2^16 in the benchmark's launch configuration: the whole shared state (every
+    Merkle digest, r_j, every fold-tree node D_w and g_w, every PST quotient commitment) equal to
+    the oracle's, the block records of the oracle's blocks (all of them at b = 256), and sampled
+    proofs byte-identical and accepted by the oracle's verifier."""
+    pp, opp, m, cm, (C, rows) = n16(dist)
     pf = F.Proofs(pp, cm, b)
     pr = O.Prover(opp, m.tobytes(), C, rows, b)
     pr.blocks(blocks)
     pr.step2()
     assert pf.step2_parts() == pr.step2_parts()
+    _state.assert_equal(pf.state(), pr.state(), pp.R, pp.M, pr.K, opp.log_r, blocks)
     rnd = random.Random(5)
     vals = I.to_ints(m)
     for k in blocks:
@@ -198,7 +204,7 @@ def test_prove_one_equals_oracle_brute_force_and_prove_all(log_n, b):
     pp, opp = gpu_pp(log_n, seed), oracle_pp(log_n, seed)
     m = vec(log_n, seed + 1)
     cm = F.Commitment(pp, m)
-    C, rows = cm.get()
+    C, rows = O.commit(opp, m.tobytes())
     pf = F.Proofs(pp, cm, b)
     for i in range(pp.N):
         one = F.vc_prove_one(pp, cm, b, i)
@@ -208,8 +214,7 @@ def test_prove_one_equals_oracle_brute_force_and_prove_all(log_n, b):
 
 
 def test_prove_one_n16_sampled():
-    pp, opp, m, cm = n16("uniform")
-    C, rows = cm.get()
+    pp, opp, m, cm, (C, rows) = n16("uniform")
     vals = I.to_ints(m)
     for b, i in ((256, 12345), (1, 65535), (16, 40000)):
         one = F.vc_prove_one(pp, cm, b, i)
@@ -231,15 +236,14 @@ def n20():
     log_n, seed = 20, 0
     pp, opp = gpu_pp(log_n, seed), oracle_pp(log_n, seed)
     m = vec(log_n, seed + 1)
-    return pp, opp, m, F.Commitment(pp, m)
+    return pp, opp, m, F.Commitment(pp, m), row_closed_form(opp, I.to_ints(m))
 
 
 @functools.lru_cache(maxsize=None)
 def n20_oracle():
     """Oracle provers for every b: Step 2 in full and Step 1 on the sampled blocks, run on host
     threads (each call releases the GIL; the jobs write disjoint parts of the provers)."""
-    pp, opp, m, cm = n20()
-    C, rows = cm.get()
+    pp, opp, m, cm, (C, rows) = n20()
     provers = {b: O.Prover(opp, m.tobytes(), C, rows, b) for b in N20_BLOCKS}
     jobs = [p.step2 for p in provers.values()]
     jobs += [functools.partial(provers[b].block, k) for b, ks in N20_BLOCKS.items() for k in ks]
@@ -250,9 +254,9 @@ def n20_oracle():
 
 
 def test_n20_setup_and_commit_closed_form():
-    pp, opp, m, cm = n20()
+    pp, opp, m, cm, exp = n20()
     assert pp.export() == opp.to_bytes()
-    assert cm.get() == row_closed_form(opp, I.to_ints(m))
+    assert cm.get() == exp
 
 
 @pytest.mark.parametrize("b", sorted(N20_BLOCKS, reverse=True))
@@ -260,11 +264,11 @@ def test_n20_prove_all_sampled(b):
     """OpenAll at N = 2^20 in the benchmark's launch configuration: Step-2 state equal to the
     oracle's, sampled proofs of the sampled blocks byte-identical and accepted by the oracle's
     verifier, and every one of the 2^20 proofs accepted by the GPU batch verifier."""
-    pp, opp, m, cm = n20()
-    C, rows = cm.get()
+    pp, opp, m, cm, (C, rows) = n20()
     pr = n20_oracle()[b]
     pf = F.Proofs(pp, cm, b)
     assert pf.step2_parts() == pr.step2_parts()
+    _state.assert_equal(pf.state(), pr.state(), pp.R, pp.M, pr.K, opp.log_r, N20_BLOCKS[b])
     rnd = random.Random(b)
     vals = I.to_ints(m)
     items = []

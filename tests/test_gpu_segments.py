@@ -7,6 +7,7 @@ import pytest
 
 import oracle as O
 from paper_2601_03031_gb300 import inputs as I
+from tests import _state
 
 pytestmark = pytest.mark.gpu
 
@@ -46,7 +47,8 @@ def test_segment_proofs_equal_oracle_and_verify(log_r, log_c, b):
     opp = O.PP(log_n, seed, log_r=log_r)
     m = I.vector(seed + 1, log_n)
     cm = F.Commitment(pp, m)
-    C, rows = cm.get()
+    C, rows = O.commit(opp, m.tobytes())
+    assert cm.get() == (C, rows)
     seg = F.vc_open_segments(pp, cm, b)
     pr = O.Prover(opp, m.tobytes(), C, rows, b)
     pr.blocks()
@@ -65,9 +67,11 @@ def test_segment_block_range_and_rejections():
     log_r, log_c, b, seed = 4, 3, 2, 41
     log_n = log_r + log_c
     pp = F.PP(log_n, 1, seed, log_r=log_r)
+    opp = O.PP(log_n, seed, log_r=log_r)
     m = I.vector(seed + 1, log_n)
     cm = F.Commitment(pp, m)
-    C, rows = cm.get()
+    C, rows = O.commit(opp, m.tobytes())
+    assert cm.get() == (C, rows)
     full = F.vc_open_segments(pp, cm, b)
     part = F.vc_open_segments(pp, cm, b, 3, 2)    # blocks 3 and 4: segments 6 .. 9
     for j in range(6, 10):
@@ -89,7 +93,6 @@ def test_segment_block_range_and_rejections():
     assert not F.vc_verify_segment(pp, C, b, j, big, p)
     assert not F.vc_verify_segment(pp, C, b, j - 1, mj, p)
     assert not F.vc_verify_segment(pp, C, b, j, mj, p[:-1])
-    opp = O.PP(log_n, seed, log_r=log_r)
     for off in (40, 96 * 2 + 10, 96 * 2 + 576 + 95, len(p) - 2):
         t = bytearray(p)
         t[off] ^= 1
@@ -105,11 +108,13 @@ def test_full_openall_on_other_splits(log_r, log_c, b):
     opp = O.PP(log_n, seed, log_r=log_r)
     m = I.vector(seed + 1, log_n)
     cm = F.Commitment(pp, m)
-    C, rows = cm.get()
+    C, rows = O.commit(opp, m.tobytes())
+    assert cm.get() == (C, rows)
     pf = F.Proofs(pp, cm, b)
     pr = O.Prover(opp, m.tobytes(), C, rows, b)
     pr.blocks()
     pr.step2()
+    _state.assert_equal(pf.state(), pr.state(), pp.R, pp.M, pr.K, opp.log_r)
     assert pf.export(0, pp.N) == b"".join(pr.proof(i) for i in range(pp.N))
     ok, n = F.vc_verify_all(pf, C, m)
     assert n == pp.N and ok.all()
@@ -123,8 +128,8 @@ def test_fc_opening_at_4096_rows():
     opp = O.PP(log_r + log_c, seed, log_r=log_r)
     m = I.vector(seed + 1, log_r + log_c)
     cm = F.Commitment(pp, m)
-    C, rows = cm.get()
-    assert (C, rows) == O.commit(opp, m.tobytes())
+    C, rows = O.commit(opp, m.tobytes())
+    assert cm.get() == (C, rows)
     for j in (0, pp.R - 1):
         p = F.vc_open_segments(pp, cm, b, j // b, 1).segment_proof(j)
         mj = m[2 * j:2 * j + 2]

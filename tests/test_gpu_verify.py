@@ -18,19 +18,27 @@ from paper_2601_03031_gb300 import _lib as F  # noqa: E402
 
 
 def setup(log_n, seed, b):
+    """GPU proofs, and the oracle's commitment and prover for the same vector: the oracle's
+    verifier is only ever handed the oracle's own inputs (equal bytes, asserted)."""
     pp = F.PP(log_n, 1, seed)
+    opp = O.PP(log_n, seed)
     m = I.vector(seed + 1, log_n)
     cm = F.Commitment(pp, m)
-    C, _ = cm.get()
+    C, rows = O.commit(opp, m.tobytes())
+    assert cm.get() == (C, rows)
     pf = F.Proofs(pp, cm, b)
-    return pp, O.PP(log_n, seed), I.to_ints(m), C, pf
+    pr = O.Prover(opp, m.tobytes(), C, rows, b)
+    pr.blocks()
+    pr.step2()
+    return pp, opp, I.to_ints(m), C, pf, pr
 
 
 @pytest.mark.parametrize("log_n,b", [(4, 1), (5, 3), (6, 8)])
 def test_honest_proofs_verify(log_n, b):
-    pp, opp, vals, C, pf = setup(log_n, 31, b)
+    pp, opp, vals, C, pf, pr = setup(log_n, 31, b)
     for i in range(0, pp.N, 3):
-        p = pf.proof(i)
+        p = pr.proof(i)
+        assert pf.proof(i) == p, i
         assert F.vc_verify(pp, C, b, i, vals[i], p), i
         assert O.verify(opp, C, b, i, vals[i], p, memo=False)
 
@@ -41,9 +49,10 @@ def flip(p: bytes, off: int) -> bytes:
 
 def test_tampered_proofs_rejected():
     log_n, b = 5, 2
-    pp, opp, vals, C, pf = setup(log_n, 32, b)
+    pp, opp, vals, C, pf, pr = setup(log_n, 32, b)
     i = 13
-    p = pf.proof(i)
+    p = pr.proof(i)
+    assert pf.proof(i) == p
     nk = b
     lr, lc = pp.log_r, pp.log_c
     fc = 96 * nk
@@ -75,7 +84,7 @@ def test_verify_n16_sampled():
     m = I.vector(seed + 1, log_n)
     vals = I.to_ints(m)
     cm = F.Commitment(pp, m)
-    C, _ = cm.get()
+    C, _ = cm.get()                  # GPU values into the GPU verifier only
     for b, i in ((256, 12345), (1, 65535)):
         pf = F.Proofs(pp, cm, b)
         p = pf.proof(i)
@@ -94,7 +103,7 @@ def test_verify_all_matches_single_and_oracle(log_n, b):
     a value >= r) fail exactly where vc_verify and the oracle's verifier fail, with and without
     column sharing."""
     import numpy as np
-    pp, opp, vals, C, pf = setup(log_n, 41, b)
+    pp, opp, vals, C, pf, pr = setup(log_n, 41, b)
     N, M = pp.N, pp.M
     m = np.array([limbs_of(v) for v in vals], np.uint64)
     ok, n = F.vc_verify_all(pf, C, m)
@@ -113,13 +122,14 @@ def test_verify_all_matches_single_and_oracle(log_n, b):
         p = pf.proof(i)
         assert F.vc_verify(pp, C, b, i, claimed[i], p) == ok2[i], i
     for i in (0, 2, N - 1):
-        assert O.verify(opp, C, b, i, claimed[i], pf.proof(i), memo=False) == ok2[i], i
+        assert pf.proof(i) == pr.proof(i)
+        assert O.verify(opp, C, b, i, claimed[i], pr.proof(i), memo=False) == ok2[i], i
 
 
 def test_verify_all_wrong_commitment_and_device_values():
     import numpy as np
     log_n, b = 6, 2
-    pp, opp, vals, C, pf = setup(log_n, 42, b)
+    pp, opp, vals, C, pf, pr = setup(log_n, 42, b)
     m = np.array([limbs_of(v) for v in vals], np.uint64)
     other = F.Commitment(pp, I.vector(99, log_n))
     C2, _ = other.get()
@@ -138,7 +148,7 @@ def test_verify_all_n16(b):
     pp = F.PP(log_n, 1, seed)
     m = I.vector(seed + 1, log_n)
     cm = F.Commitment(pp, m)
-    C, _ = cm.get()
+    C, _ = cm.get()                  # GPU values into the GPU verifier only
     pf = F.Proofs(pp, cm, b)
     ok, n = F.vc_verify_all(pf, C, m)
     assert n == pp.N and ok.all()

@@ -16,7 +16,7 @@ non-interactive"):
     P(X) = prod_j (1 + x_j^{-1} X^{2^{l_R - j + 1}});
   * leaves SHA256("FP-leaf" || u64be(i) || m_i), nodes SHA256("FP-node" || left || right), row
     leaves SHA256("FP-row" || s_j || C_j), r_j = HFr("FP-rho", root || u32be(j));
-  * proof = block (C_a) || pi_{C_k} || path (row tree leaf-up, then the row tree, leaf-up) ||
+  * proof = block (C_a) || pi_{C_k} || path (row tree leaf-up, then the tree over the rows) ||
     sibling pairs (D_w, g_w[a]) leaf-up || (pi_{l_c - 1} .. pi_0).
 Each mutation test changes one reading and checks that the re-derivation then disagrees with the
 oracle, so a plausible slip in any of them (little-endian integers, swapped node children, a
@@ -263,3 +263,28 @@ def test_a_changed_reading_is_detected(rd):
     pp, m, C, rows, pr, beta, tau = case(log_n, b)
     d = derive(log_n, b, rd)
     assert any(pr.proof(i) != d.proof(i) for i in range(pp.N))
+
+
+@pytest.mark.parametrize("log_n,b", CASES)
+def test_state_export_layout(log_n, b):
+    """The oracle's whole-state export (the layout the GPU library's state export shares) holds the
+    re-derived block records, Merkle trees level by level, r_j, every fold-tree node and the PST
+    quotient commitments, in the documented order."""
+    from tests import _state
+    pp, m, C, rows, pr, beta, tau = case(log_n, b)
+    d = derive(log_n, b)
+    st = _state.split(pr.state(), pp.R, pp.M, d.K, d.lr)
+    assert st["blocks"] == b"".join(d.blocks)
+    assert st["row_trees"] == b"".join(b"".join(b"".join(lv) for lv in t) for t in d.row_trees)
+    assert st["top_tree"] == b"".join(b"".join(lv) for lv in d.top)
+    assert st["r_j"] == b"".join(v.to_bytes(32, "big") for v in d.rj)
+    nodes = [(h, s) for h in range(d.lr + 1) for s in range(pp.R >> h)]
+    assert st["D_w"] == b"".join(d.D(h, s) for h, s in nodes)
+    assert st["g_w"] == b"".join(v.to_bytes(32, "big") for h, s in nodes for v in d.g[h][s])
+    pst = b""
+    for t in range(d.lc):
+        w = 1 << t
+        for p in range(pp.M >> (t + 1)):
+            Q = [(d.gstar[(2 * p + 1) * w + c] - d.gstar[2 * p * w + c]) % RR for c in range(w)]
+            pst += d.grp.G1(mle_eval(Q, d.tau[:t]) if t else Q[0])
+    assert st["pst"] == pst
