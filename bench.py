@@ -73,10 +73,10 @@ CRITICAL_ROUNDS = {
 
 FOLD_SPLIT_MAX = 256          # rounds with at most this many fold points use the split folds
 
-# DRAM bytes per launch (dram__bytes_read.sum + dram__bytes_write.sum) from the ncu captures summarised
-# under profiles/, keyed by (log N, b, kernel), for kernels unchanged since their capture
+# DRAM bytes per launch (dram__bytes_read.sum + dram__bytes_write.sum) from one ncu capture of the
+# kernel at this workload, keyed by (log N, b, kernel); an entry is removed when its kernel changes
 NCU_TRAFFIC = {
-    (16, 256, "k_final_exp_c"): (89e3, "profiles/k_final_exp_c_n16_b256.md"),
+    (16, 256, "k_final_exp_c"): 89e3,
 }
 
 
@@ -177,6 +177,15 @@ def parse():
     ap.add_argument("--msm-sweep", default="12,14,16,18,20,22,24", help="log2 sizes of the MSM sweep")
     ap.add_argument("--b-sweep", default="1,16,256,1024", help="b values of the N=2^20 ProveAll sweep")
     ap.add_argument("--served-requests", type=int, default=100, help="requests of the served trace replayed")
+    ap.add_argument("--served-rate", type=float, default=200.0, help="offered rate of the served trace (req/s)")
+    ap.add_argument("--served-only", action="store_true",
+                    help="only the served workload: the trace at --served-rate (served and sequential) and the "
+                         "rate sweep (one JSON line)")
+    ap.add_argument("--served-rates", default="2,4,6,8,12,16", help="offered rates of the served rate sweep")
+    ap.add_argument("--sweep-requests", type=int, default=150, help="requests per point of the rate sweep")
+    ap.add_argument("--batched-only", action="store_true", help="only the 64-job batched workload (one JSON line)")
+    ap.add_argument("--schedule", default="direct", choices=["direct", "lookahead"],
+                    help="Step-1 round schedule (fp_set_schedule)")
     ap.add_argument("--msm-only", type=int, default=0, metavar="LOG_N",
                     help="time only the standalone G1 MSM of 2^LOG_N points (profiling runs)")
     return ap.parse_args()
@@ -250,7 +259,8 @@ def fc_microbench(F, I, torch, np, seed: int) -> dict:
     row MSMs, then the n-pair FC commitment), FC.BOpen-t = Step 1 on one block of t segments,
     t x FC.BOpen-1 = t blocks of one segment (one batched call, and t single calls), FC.BVerify-t =
     the segment verifier on a block of t.  Device time (CUDA events) for Commit and BOpen, host
-    wall time for the synchronous verifier; median of 3 after one warm-up."""
+    wall time for the synchronous verifier (FC.BVerify-t against t calls of FC.BVerify-1 on t
+    segments at n = 2^12, the batch-verification figure); median of 3 after one warm-up."""
     s = torch.cuda.Stream()
 
     def dev_ms(fn):
@@ -275,7 +285,7 @@ def fc_microbench(F, I, torch, np, seed: int) -> dict:
             ts.append((time.perf_counter() - t0) * 1e3)
         return sorted(ts)[1]
 
-    out = {"table": {}, "batch_open_n2^12": {}}
+    out = {"table": {}, "batch_open_n2^12": {}, "batch_verify_n2^12": {}}
     for log_r in (8, 9, 10, 11, 12):
         pp = F.PP(log_r + 1, 1, seed, s, log_r=log_r)
         m = I.vector(seed + 1, log_r + 1)
@@ -305,6 +315,19 @@ def fc_microbench(F, I, torch, np, seed: int) -> dict:
         out["table"][f"n=2^{log_r}"] = row
         if log_r == 12:
             one = row["bopen_t1_ms"]
+            ones = F.vc_open_segments(pp, cm, 1, 0, 512, s)       # FC.BOpen-1 of segments 0 .. 511
+            proofs1 = [ones.segment_proof(j) for j in range(512)]
+            for t in (16, 32, 64, 128, 256, 512):
+                blk = F.vc_open_segments(pp, cm, t, 0, 1, s).segment_proof(0)
+                assert F.vc_verify_segment(pp, C, t, 0, m[0:2], blk, s)
+
+                t0 = time.perf_counter()                            # t calls, timed once
+                for j in range(t):
+                    assert F.vc_verify_segment(pp, C, 1, j, m[2 * j:2 * j + 2], proofs1[j], s)
+                out["batch_verify_n2^12"][f"t={t}"] = {
+                    "bverify_t_ms": wall_ms(lambda: F.vc_verify_segment(pp, C, t, 0, m[0:2], blk, s)),
+                    "t_x_bverify1_ms": (time.perf_counter() - t0) * 1e3,
+                }
             for t in (16, 32, 64, 128, 256, 512):
                 hold = []
 
@@ -386,23 +409,34 @@ def batched_workload(F, I, torch, np) -> dict:
             ts.append(time.perf_counter() - t0)
             del r
         return min(ts)
-    t_graph = run(lambda: F.vc_prove_all_batch(jobs, use_graph=True, stream=s), 3, 2)
+    phases = []
+
+    def graph_call():
+        r = F.vc_prove_all_batch(jobs, use_graph=True, stream=s)
+        phases.append(F.batch_last_times())
+        return r
+    t_graph = run(graph_call, 3, 2)
+    ph = min(phases[-3:], key=lambda p: p["capture_ms"] + p["instantiate_ms"] + p["run_ms"])
     t_streams = run(lambda: F.vc_prove_all_batch(jobs, use_graph=False, stream=s), 3, 1)
     t_seq = run(lambda: [F.Proofs(cm.pp, cm, b, s) for cm, b in jobs], 1, 1)
     return {"jobs": 64, "log_n": sorted(sp["log_n"] for sp in spec), "total_proofs": total,
             "timing": "host wall clock around the call, after synchronize, best of runs",
-            "graph": {"ms": t_graph * 1e3, "proofs_per_s": total / t_graph},
+            "graph": {"ms": t_graph * 1e3, "proofs_per_s": total / t_graph, "phases_ms": ph,
+                      "proofs_per_s_graph_run_only": total / (ph["run_ms"] * 1e-3) if ph["run_ms"] else None},
             "streams": {"ms": t_streams * 1e3, "proofs_per_s": total / t_streams},
             "sequential": {"ms": t_seq * 1e3, "proofs_per_s": total / t_seq}}
 
 
-def served_workload(F, I, torch, np, nreq: int) -> dict:
-    """Poisson trace (seed 5, 200 req/s, log N uniform 10..20, b uniform {1, 16, 256} clamped to R),
-    its first nreq requests replayed in real time through the serving loop; against sequential
-    plain calls on the same trace (each request's measured solo time, queued in arrival order)."""
-    from paper_2601_03031_gb300 import serve as S
-    trace = I.poisson_trace(5, 2000, 200.0, 10, 20, (1, 16, 256))[:nreq]
-    vecs = [I.vector(r["seed"], r["log_n"]) for r in trace]
+def _pct(a, q):
+    a = sorted(a)
+    return a[min(len(a) - 1, int(q * len(a)))] if a else None
+
+
+def _served_run(F, I, torch, np, S, trace, vecs, check_solo: int = 0) -> dict:
+    """Replay `trace` in real time through the continuous-batching server; latency = arrival to
+    proof state in host memory.  The sustained load is completed requests / (last completion -
+    first arrival); the backlog is the number of requests waiting or running when the last one
+    arrives."""
     srv = S.Server(log_n_max=20, seed=0, slots=32)
     for ln in range(10, 21):
         srv.view(ln)
@@ -415,35 +449,81 @@ def served_workload(F, I, torch, np, nreq: int) -> dict:
         if r["t"] > now:
             time.sleep(r["t"] - now)
         futs.append(srv.submit(m, r["b"], t_arrival=t0 + r["t"]))
+    t_last = t0 + trace[-1]["t"]
     res = [f.result() for f in futs]
-    span = max(q.t_done for q in res) - t0
     peak = srv.peak_running
     srv.close()
-    total = sum(1 << r["log_n"] for r in trace)
-
-    def pct(a, q):
-        a = sorted(a)
-        return a[min(len(a) - 1, int(q * len(a)))]
+    span = max(q.t_done for q in res) - t0
+    backlog = sum(1 for q in res if q.t_done > t_last)
     lat = [q.latency for q in res]
-    durs = []
+    half = len(res) // 2
+    out = {"requests": len(res), "offered_req_per_s": len(res) / max(trace[-1]["t"], 1e-9),
+           "sustained_req_per_s": len(res) / span, "span_s": span,
+           "proofs_per_s": sum(1 << r["log_n"] for r in trace) / span,
+           "p50_ms": _pct(lat, 0.5) * 1e3, "p99_ms": _pct(lat, 0.99) * 1e3,
+           "second_half_p50_ms": _pct(lat[half:], 0.5) * 1e3,
+           "backlog_at_last_arrival": backlog, "peak_concurrent_jobs": peak}
+    if check_solo:
+        for q in range(0, len(res), max(1, len(res) // check_solo)):
+            r = trace[q]
+            C, rows, state = S.solo(srv.view(r["log_n"]), vecs[q], r["b"])
+            assert state == res[q].state and C == res[q].C, "served result differs from its solo run"
+    return out
+
+
+def _sequential_run(F, I, torch, np, S, srv_views, trace, vecs) -> dict:
+    """The same trace through plain synchronous calls, one request at a time in arrival order
+    (vc_commit, vc_prove_all, the proof state copied to the host), replayed in real time."""
+    t0 = time.perf_counter()
+    lat, t_end = [], t0
     for r, m in zip(trace, vecs):
-        pp = srv.view(r["log_n"])
-        torch.cuda.synchronize()
-        a = time.perf_counter()
-        C, rows, state = S.solo(pp, m, r["b"])
-        durs.append(time.perf_counter() - a)
-        if len(durs) % 10 == 1:
-            assert state == res[len(durs) - 1].state, "served result differs from its solo run"
-    fin, seq_lat = 0.0, []
-    for r, d in zip(trace, durs):
-        fin = max(fin, r["t"]) + d
-        seq_lat.append(fin - r["t"])
-    return {"requests": nreq, "trace": "poisson seed 5, 200 req/s, log N 10..20, b in {1,16,256}",
-            "latency": "arrival to proof state in host memory",
-            "served": {"p50_ms": pct(lat, 0.5) * 1e3, "p99_ms": pct(lat, 0.99) * 1e3,
-                       "proofs_per_s": total / span, "span_s": span, "peak_concurrent_jobs": peak},
-            "sequential": {"p50_ms": pct(seq_lat, 0.5) * 1e3, "p99_ms": pct(seq_lat, 0.99) * 1e3,
-                           "proofs_per_s": total / fin, "span_s": fin}}
+        now = time.perf_counter() - t0
+        if r["t"] > now:
+            time.sleep(r["t"] - now)
+        S.solo(srv_views[r["log_n"]], m, r["b"])
+        t_end = time.perf_counter()
+        lat.append(t_end - (t0 + r["t"]))
+    span = t_end - t0
+    return {"requests": len(trace), "sustained_req_per_s": len(trace) / span, "span_s": span,
+            "proofs_per_s": sum(1 << r["log_n"] for r in trace) / span,
+            "p50_ms": _pct(lat, 0.5) * 1e3, "p99_ms": _pct(lat, 0.99) * 1e3}
+
+
+def served_workload(F, I, torch, np, nreq: int, rate: float = 200.0, sequential: bool = True) -> dict:
+    """Poisson trace (seed 5, log N uniform 10..20, b uniform {1, 16, 256} clamped to R) at `rate`
+    requests/s, its first nreq requests replayed in real time through the serving loop, and (when
+    `sequential`) through plain synchronous calls one at a time, also in real time."""
+    from paper_2601_03031_gb300 import serve as S
+    trace = I.poisson_trace(5, 2000, rate, 10, 20, (1, 16, 256))[:nreq]
+    vecs = [I.vector(r["seed"], r["log_n"]) for r in trace]
+    out = {"trace": f"poisson seed 5, {rate:g} req/s, log N 10..20, b in {{1,16,256}}",
+           "latency": "arrival to proof state in host memory",
+           "served": _served_run(F, I, torch, np, S, trace, vecs, check_solo=10)}
+    if sequential:
+        views = {}
+        base = F.PP(20, 1, 0)
+        for ln in range(10, 21):
+            views[ln] = base if ln == 20 else base.view(ln)
+        out["sequential"] = _sequential_run(F, I, torch, np, S, views, trace, vecs)
+    return out
+
+
+def served_rate_sweep(F, I, torch, np, nreq: int, rates) -> dict:
+    """The served trace's request mix at several offered rates (same sizes, seeds and order; arrival
+    times from the Poisson stream at each rate): the highest rate whose sustained load keeps up with
+    the offered load (within 10 %) and whose backlog at the last arrival stays within the 32 slots."""
+    from paper_2601_03031_gb300 import serve as S
+    out, best = {}, None
+    for rate in rates:
+        trace = I.poisson_trace(5, 2000, rate, 10, 20, (1, 16, 256))[:nreq]
+        vecs = [I.vector(r["seed"], r["log_n"]) for r in trace]
+        r = _served_run(F, I, torch, np, S, trace, vecs)
+        r["bounded"] = r["sustained_req_per_s"] >= 0.9 * r["offered_req_per_s"] and r["backlog_at_last_arrival"] <= 32
+        out[f"{rate:g}_req_per_s"] = r
+        if r["bounded"]:
+            best = rate
+    out["highest_bounded_rate_req_per_s"] = best
+    return out
 
 
 def msm_sweep(F, I, torch, np, stream, flush, logs, seed: int) -> dict:
@@ -464,15 +544,22 @@ def msm_sweep(F, I, torch, np, stream, flush, logs, seed: int) -> dict:
 
 
 # --------------------------------------------------------------------------------- oracle arm
-def oracle_sample(log_n: int, b: int, seed: int, other_rows: bool = False):
-    """Time the CPU oracle on a bounded sample of the workload; return (seconds per full step,
-    description).  Sample: Commit's row MSMs for a few rows (scaled to R rows), its Miller loops for
-    a few rows (scaled) plus the final exponentiation, FC.BOpen for one block (scaled to all
-    ceil(R/b) blocks), and Step 2 in full.  The oracle's rows for the sample come from its own
-    trapdoor closed form, which it knows from its setup."""
+def oracle_sample(log_n: int, b: int, seed: int, other_rows: bool = False, threads: int | None = None):
+    """Time the CPU oracle, as it stands, on a bounded sample of one Commit + OpenAll step, on
+    `threads` host threads (default: every core); return (sample seconds, estimated seconds of the
+    full step on the same threads, description, per-part seconds).
+
+    Sample: Commit's row MSMs and Miller loops on one row per thread at once (scaled to R rows),
+    the final exponentiation, FC.BOpen on min(K, threads) blocks at once (scaled to all K =
+    ceil(R/b) blocks; the oracle runs one block on one thread), and Step 2 in full (one thread).  The
+    oracle's rows for the sample come from its own trapdoor closed form, which it knows from its
+    setup."""
+    from concurrent.futures import ThreadPoolExecutor
+
     import oracle as O
     from paper_2601_03031_gb300 import inputs as I
 
+    threads = threads or os.cpu_count() or 1
     r_mod = I.R_INT
 
     def mle_eval(table, tau):       # f(tau) for the multilinear extension, x_s <-> bit s
@@ -495,33 +582,35 @@ def oracle_sample(log_n: int, b: int, seed: int, other_rows: bool = False):
     s = sum(fj[j] * pow(beta, 2 * j, r_mod) for j in range(R)) % r_mod
     C = O.fq12_pow(O.pairing(g1, O.g2_gen()), s)
     lam_top = pp.to_bytes()[96 * (M - 1): 96 * (2 * M - 1)]
-    t = {}
-    srows = min(R, 4)
-    t0 = time.perf_counter()
-    for j in range(srows):
-        O.g1_msm(lam_top, vals[j * M:(j + 1) * M])
-    t["commit_msm"] = (time.perf_counter() - t0) * R / srows
-    t0 = time.perf_counter()
     v0 = pp.to_bytes()[96 * (2 * M): 96 * (2 * M) + 192]
-    for j in range(srows):
-        f = O.miller(rows[96 * j:96 * j + 96], v0)
-    t["commit_miller"] = (time.perf_counter() - t0) * R / srows
-    t0 = time.perf_counter()
-    O.final_exp(f)
-    t["commit_final_exp"] = time.perf_counter() - t0
-    t0 = time.perf_counter()
-    O.bopen(pp, C, rows, b, 0)
-    t["step1"] = (time.perf_counter() - t0) * K
+    t, scale = {}, {}
+    srows = min(R, threads)
+    nblk = min(K, threads)
+    with ThreadPoolExecutor(max_workers=threads) as ex:
+        t0 = time.perf_counter()
+        list(ex.map(lambda j: O.g1_msm(lam_top, vals[j * M:(j + 1) * M]), range(srows)))
+        t["commit_msm"], scale["commit_msm"] = time.perf_counter() - t0, R / srows
+        t0 = time.perf_counter()
+        fs = list(ex.map(lambda j: O.miller(rows[96 * j:96 * j + 96], v0), range(srows)))
+        t["commit_miller"], scale["commit_miller"] = time.perf_counter() - t0, R / srows
+        t0 = time.perf_counter()
+        O.final_exp(fs[0])
+        t["commit_final_exp"], scale["commit_final_exp"] = time.perf_counter() - t0, 1.0
+        t0 = time.perf_counter()
+        list(ex.map(lambda k: O.bopen(pp, C, rows, b, k), range(nblk)))
+        t["step1"], scale["step1"] = time.perf_counter() - t0, K / nblk
     pr = O.Prover(pp, m.tobytes(), C, rows, b)
     t0 = time.perf_counter()
     pr.step2()
-    t["step2"] = time.perf_counter() - t0
-    total = sum(t.values())
+    t["step2"], scale["step2"] = time.perf_counter() - t0, 1.0
+    sample_s = sum(t.values())
+    full_s = sum(t[k] * scale[k] for k in t)
+    desc = (f"N=2^{log_n}, b={b} on {threads} host threads: commit MSM and Miller loops timed on {srows}/{R} rows "
+            f"(one per thread, scaled x{R / srows:g}) + 1 final exp; FC.BOpen timed on {nblk} of {K} blocks "
+            f"(one per thread, scaled x{K / nblk:g}); Step 2 in full on one thread; {sample_s:.1f} s of sampled "
+            f"work per step, full step estimated at {full_s:.1f} s")
     if not other_rows:
-        desc = (f"N=2^{log_n}, b={b}: commit MSM timed on {srows}/{R} rows and its Miller loops on {srows}/{R} "
-                f"rows (+1 final exp), scaled x{R // srows}; FC.BOpen timed on 1 of {K} blocks, scaled x{K}; "
-                f"Step 2 timed in full; 1 thread")
-        return total, desc, t
+        return sample_s, full_s, desc, t
     # the other rows, timed on the same kind of sample (not part of the step total)
     other = {}
     pr.block(0)
@@ -555,36 +644,78 @@ def oracle_sample(log_n: int, b: int, seed: int, other_rows: bool = False):
     assert O.verify_segment(fpp, fC, 1, 0, mj, seg)
     other["fc_bverify_n2^8_t1_s"] = time.perf_counter() - t0
     t["other_rows"] = other
-    desc = (f"N=2^{log_n}, b={b}: commit MSM timed on {srows}/{R} rows and its Miller loops on {srows}/{R} "
-            f"rows (+1 final exp), scaled x{R // srows}; FC.BOpen timed on 1 of {K} blocks, scaled x{K}; "
-            f"Step 2 timed in full; 1 thread")
-    return total, desc, t
+    return sample_s, full_s, desc, t
+
+
+def fc_oracle_table(seed: int, threads: int | None = None) -> dict:
+    """The CPU oracle's FC scheme alone (Table tb:fc) on the same R = n, M = 2 splits as the GPU rows:
+    FC.Commit (the oracle's VC.Commit on the split), FC.BOpen-1 and FC.BVerify-1 for n = 2^8 .. 2^10,
+    FC.BOpen-32 and FC.BVerify-32 at n = 2^8; each call single-threaded and timed on its own thread,
+    the calls spread over the host cores.  n = 2^11, 2^12 are not run (FC.BOpen is linear in n)."""
+    from concurrent.futures import ThreadPoolExecutor
+
+    import oracle as O
+    from paper_2601_03031_gb300 import inputs as I
+
+    threads = threads or os.cpu_count() or 1
+    cases = {}
+    for log_r in (8, 9, 10):
+        fpp = O.PP(log_r + 1, seed, log_r=log_r)
+        mb = I.vector(seed + 1, log_r + 1).tobytes()
+        cases[log_r] = (fpp, mb)
+
+    def timed(fn):
+        t0 = time.perf_counter()
+        r = fn()
+        return time.perf_counter() - t0, r
+
+    def row(log_r):
+        fpp, mb = cases[log_r]
+        out = {}
+        out["commit_s"], (C, rows) = timed(lambda: O.commit(fpp, mb))
+        for t in ((1, 32) if log_r == 8 else (1,)):
+            out[f"bopen_t{t}_s"], (proof, _) = timed(lambda: O.bopen(fpp, C, rows, t, 0))
+            seg = rows[0:96 * t] + proof
+            out[f"bverify_t{t}_s"], ok = timed(lambda: O.verify_segment(fpp, C, t, 0, mb[0:64], seg))
+            assert ok
+        return log_r, out
+
+    with ThreadPoolExecutor(max_workers=threads) as ex:
+        res = dict(ex.map(row, (8, 9, 10)))
+    return {f"n=2^{k}": v for k, v in sorted(res.items())} | {
+        "note": "oracle as it stands, one thread per call; n = 2^11, 2^12 not run"}
 
 
 def run_reference(args):
+    """The oracle as it stands on the host cores: each step is one bounded sample of the step
+    (oracle_sample); ms_per_step is the sample's own wall time and value the full-step rate the
+    sample estimates (N / estimated full-step seconds)."""
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return
     import oracle as O
     O.lib()
     N = 1 << args.log_n
+    threads = os.cpu_count() or 1
     for _ in range(args.warmup):
-        pass      # the oracle has no warm-up effects worth a full sample; warm-up steps are not re-run
-    per_step = []
+        pass      # the oracle has no warm-up effects worth a sample; warm-up steps are not re-run
+    samples, fulls = [], []
     desc = ""
     for _ in range(max(1, args.steps)):
-        total, desc, _parts = oracle_sample(args.log_n, args.b, args.seed)
-        per_step.append(total)
-    step_s = sum(per_step) / len(per_step)
-    value = N / step_s
+        sample_s, full_s, desc, _parts = oracle_sample(args.log_n, args.b, args.seed, threads=threads)
+        samples.append(sample_s)
+        fulls.append(full_s)
+    value = N / (sum(fulls) / len(fulls))
+    ms = 1e3 * sum(samples) / len(samples)
     line = {
         "impl": "reference", "metric": "ProveAll proofs/s (Commit + OpenAll)", "value": value,
         "unit": "proofs/s", "n_gpus": 0, "steps": args.steps, "warmup": args.warmup,
-        "ms_per_step": 1e3 * step_s, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "ms_per_step": ms, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": "u32 limbs (exact Fq/Fr arithmetic)", "data": "synthetic",
         "config": {"workload": f"ProveAll N=2^{args.log_n} b={args.b} uniform Fr, BLS12-381", "log_n": args.log_n,
-                   "b": args.b},
-        "cpu_baseline": {"value": value, "unit": "proofs/s", "cores": 1, "kind": "oracle", "sample": desc},
+                   "b": args.b, "step": "one bounded sample of the Commit + OpenAll step (see cpu_baseline.sample)"},
+        "cpu_baseline": {"value": value, "unit": "proofs/s", "cores": threads, "kind": "oracle", "sample": desc,
+                         "estimated_full_step_s": sum(fulls) / len(fulls)},
         "e2e": {"value": value, "unit": "proofs/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line))
@@ -630,11 +761,35 @@ def main():
 
     from paper_2601_03031_gb300 import _lib as F
     from paper_2601_03031_gb300 import inputs as I
+    F.set_schedule(args.schedule)
 
     if args.fc_only:
         res = fc_microbench(F, I, torch, np, args.seed)
         if rank == 0:
-            print(json.dumps({"metric": "FC.BOpen ms (Table tb:fc)", "n_gpus": world, "fc_microbench": res}))
+            line = {"metric": "FC.BOpen ms (Table tb:fc)", "n_gpus": world, "fc_microbench": res}
+            if not args.no_cpu_baseline:
+                line["fc_oracle"] = fc_oracle_table(args.seed)
+            print(json.dumps(line))
+        return
+    if args.batched_only:
+        res = batched_workload(F, I, torch, np)
+        if rank == 0:
+            print(json.dumps({"metric": "batched ProveAll proofs/s", "value": res["graph"]["proofs_per_s"],
+                              "unit": "proofs/s", "n_gpus": world,
+                              "config": {"workload": "64 ProveAll jobs, log N uniform 8..18 (seed 4), b = min(R, "
+                                                     "nearest power of two to log^2 N), one SRS for 2^18"},
+                              "batched_64_jobs": res}))
+        return
+    if args.served_only:
+        res = served_workload(F, I, torch, np, args.served_requests, args.served_rate)
+        sweep = served_rate_sweep(F, I, torch, np, args.sweep_requests,
+                                  [float(x) for x in args.served_rates.split(",") if x])
+        if rank == 0:
+            print(json.dumps({"metric": "served p50/p99 latency and proofs/s", "n_gpus": world,
+                              "config": {"workload": f"served Poisson trace, first {args.served_requests} requests "
+                                                     f"at {args.served_rate:g} req/s; rate sweep of "
+                                                     f"{args.sweep_requests} requests per rate"},
+                              "served_trace": res, "rate_sweep": sweep}))
         return
     if args.msm_only:
         stream = torch.cuda.current_stream()
@@ -730,8 +885,9 @@ def main():
         achieved = ops_launch / (avg_ms * 1e-3)
         roof = {"bound": "alu", "kernel": name, "achieved": achieved / 1e12, "peak": peak / 1e12,
                 "unit": "Tops/s (32-bit multiply-add lane ops)", "frac": achieved / peak,
-                "traffic": NCU_TRAFFIC.get((log_n, b, name), (None,))[0],
-                "traffic_source": NCU_TRAFFIC.get((log_n, b, name), (None, None))[1],
+                "traffic": NCU_TRAFFIC.get((log_n, b, name)),
+                "traffic_source": "ncu dram__bytes_read.sum + dram__bytes_write.sum, one capture of this kernel"
+                                  if (log_n, b, name) in NCU_TRAFFIC else None,
                 "units_per_step": n_units, "unit_op": unit, "launches_per_step": launches_per_step,
                 "avg_launch_ms": avg_ms,
                 "peak_source": "measured: fp_imad_probe on this GPU in this run"}
@@ -751,9 +907,10 @@ def main():
     cpu = None
     if not args.no_cpu_baseline:
         try:
-            cpu_s, desc, parts = oracle_sample(log_n, b, args.seed, other_rows=True)
-            cpu = {"value": N / cpu_s, "unit": "proofs/s", "cores": 1, "kind": "oracle", "sample": desc,
-                   "seconds_per_step_scaled": cpu_s,
+            threads = os.cpu_count() or 1
+            sample_s, cpu_s, desc, parts = oracle_sample(log_n, b, args.seed, other_rows=True, threads=threads)
+            cpu = {"value": N / cpu_s, "unit": "proofs/s", "cores": threads, "kind": "oracle", "sample": desc,
+                   "sample_s": sample_s, "estimated_full_step_s": cpu_s,
                    "other_rows": dict(parts.get("other_rows", {}),
                                       note="one thread each: VC.Verify of one proof (N = 2^%d, b = %d, no "
                                            "sharing), the evaluation proof at a random point (prove, verify), "
@@ -772,7 +929,7 @@ def main():
             "fc_microbench": fc_microbench(F, I, torch, np, args.seed),
             "eval_proof": eval_sweep(F, I, torch, np, [16, 20], args.seed),
             "batched_64_jobs": batched_workload(F, I, torch, np),
-            "served": served_workload(F, I, torch, np, args.served_requests),
+            "served": served_workload(F, I, torch, np, args.served_requests, args.served_rate),
         }
 
     line = {
@@ -781,7 +938,8 @@ def main():
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": "u32 limbs (exact Fq/Fr arithmetic)", "data": "synthetic",
         "config": {"workload": f"ProveAll N=2^{log_n} b={b} uniform Fr, BLS12-381", "log_n": log_n, "b": b,
-                   "parallelism": f"replicas x{world}", "l2": "flushed (256 MB write) before every timed step"},
+                   "parallelism": f"replicas x{world}", "l2": "flushed (256 MB write) before every timed step",
+                   "step1_schedule": args.schedule},
         "e2e": {"value": N / e2e_s, "unit": "proofs/s", "h2d_bytes_per_step": N * 32,
                 "d2h_bytes_per_step": int(state.numel())},
         "phases": {"commit_ms": commit_ms, "openall_ms": openall_ms,

@@ -144,6 +144,10 @@ typedef struct {
     uint32_t b;
 } fp_job;
 fp_status vc_prove_all_batch(uint32_t njobs, const fp_job* jobs, int use_graph, void* stream, fp_proofs** outs);
+/* Host wall-clock phases of this thread's last vc_prove_all_batch call with use_graph = 1, in ms:
+ * enqueueing every job's launches into the capture, instantiating the graph, and launching it
+ * until `stream` completes (zeros after a call without a graph).  Any pointer may be NULL. */
+fp_status fp_batch_last_times(double* capture_ms, double* instantiate_ms, double* run_ms);
 
 /* One proof pi_i alone (the same bytes as vc_proof_get of vc_prove_all's result): Step 1 for the
  * block of i only (FC.BOpen on S_k, k = (i / M) / b), Step 2 in full (it is O(N) either way), then
@@ -291,6 +295,22 @@ fp_status fp_msm_autotune(const fp_g1_bases* P, const uint64_t* k_dev, uint64_t 
 void fp_pp_free(fp_pp* pp);
 void fp_commit_free(fp_commit* cm);
 void fp_proofs_free(fp_proofs* pf);
+
+/* Step-1 round schedule of FC.BOpen (Sec. 3, Eq. folding) used by every later call that opens blocks
+ * (vc_prove_all, vc_prove_one, vc_prove_all_batch, vc_open_segments, vc_eval_prove); the proofs are
+ * byte-identical under every schedule, only the order of the device work differs.
+ *   FP_SCHEDULE_DIRECT     (default) round j's pairings after round j-1's fold, one round after
+ *                          another.
+ *   FP_SCHEDULE_LOOKAHEAD  round j's pairings from round j-1's state before its challenge is known,
+ *                          by bilinearity (e(A_L + x A_R, v_L + v_R / x) expanded), so that after
+ *                          each challenge only GT exponentiations by x^(+-1) remain on the chain; it
+ *                          runs four times a round's Miller loops and final exponentiations beside
+ *                          the chain, and on GB300 it is slower than the direct rounds for every
+ *                          measured size (kept as an option).
+ * A process-wide setting, read when a call enqueues its work.  FP_EINVAL for another value. */
+typedef enum { FP_SCHEDULE_DIRECT = 0, FP_SCHEDULE_LOOKAHEAD = 1 } fp_schedule;
+fp_status fp_set_schedule(int schedule);
+int fp_get_schedule(void);
 
 /* ---- diagnostics (no counterpart in the paper: bookkeeping for measurement) ----
  * fp_launch_count: number of CUDA kernel launches this library has made in this process.

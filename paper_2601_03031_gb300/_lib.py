@@ -22,7 +22,10 @@ EXPORTED = ["vc_setup", "vc_pp_export", "vc_pp_dims", "vc_commit", "vc_commit_ge
             "fp_msm_window", "fp_msm_autotune", "vc_prove_one", "vc_pp_view", "vc_commit_async",
             "vc_commit_status", "vc_prove_all_batch", "vc_verify", "vc_verify_all", "vc_setup_split",
             "vc_pp_view_split", "vc_open_segments", "vc_segment_proof_len", "vc_segment_proof_get",
-            "vc_verify_segment", "vc_eval_proof_len", "vc_eval_prove", "vc_eval_verify"]
+            "vc_verify_segment", "vc_eval_proof_len", "vc_eval_prove", "vc_eval_verify", "fp_set_schedule",
+            "fp_get_schedule", "fp_batch_last_times"]
+
+SCHEDULES = {"direct": 0, "lookahead": 1}
 
 
 class FlexProofsError(RuntimeError):
@@ -101,6 +104,9 @@ def load(path: str = LIB_PATH):
     L.fp_msm_window.argtypes = [u64, u32]
     L.fp_msm_window.restype = ctypes.c_int
     L.fp_msm_autotune.argtypes = [vp, vp, u64, u32, vp, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_double)]
+    L.fp_set_schedule.argtypes = [ctypes.c_int]
+    L.fp_get_schedule.restype = ctypes.c_int
+    L.fp_batch_last_times.argtypes = [ctypes.POINTER(ctypes.c_double)] * 3
     _lib = L
     return L
 
@@ -108,6 +114,24 @@ def load(path: str = LIB_PATH):
 def _check(fn: str, st: int):
     if st != 0:
         raise FlexProofsError(fn, st)
+
+
+def set_schedule(name: str) -> None:
+    """Step-1 round schedule for later calls: "direct" (default) or "lookahead" (fp_set_schedule);
+    proofs are identical under every schedule."""
+    _check("fp_set_schedule", load().fp_set_schedule(SCHEDULES[name]))
+
+
+def batch_last_times() -> dict:
+    """Host phases (ms) of this thread's last graph-captured vc_prove_all_batch call."""
+    v = [ctypes.c_double() for _ in range(3)]
+    _check("fp_batch_last_times", load().fp_batch_last_times(*[ctypes.byref(x) for x in v]))
+    return {"capture_ms": v[0].value, "instantiate_ms": v[1].value, "run_ms": v[2].value}
+
+
+def get_schedule() -> str:
+    v = load().fp_get_schedule()
+    return next(k for k, q in SCHEDULES.items() if q == v)
 
 
 def _stream_ptr(stream) -> int | None:

@@ -12,8 +12,7 @@ void la_miller(const void* A, const void* v, uint32_t K, uint32_t R, uint32_t h2
 }
 void la_sparse(const void* A, const void* bvec, uint32_t k0, uint32_t K, uint32_t R, uint32_t h2, uint32_t b,
                void* out, cudaStream_t s) {
-    const uint32_t cmax = std::min(b, 4 * h2);
-    cudaMemsetAsync(out, 0, (size_t)K * 6 * 4 * h2 * G1J_BYTES, s);
+    const uint32_t cmax = std::min(b, 4 * h2);     // out (K 6 4 h2 Jacobian) zeroed by the caller
     FP_KERNEL("k_la_sparse", s, k_la_sparse<<<(unsigned)(((uint64_t)2 * K * cmax + 15) / 16), 128, 0, s>>>(
                                     (const g1a*)A, (const fr*)bvec, k0, K, R, h2, b, cmax, (g1j*)out));
 }

@@ -87,7 +87,7 @@ void step1_fold(void* A, void* v, void* bvec, const void* x_mont, const void* xi
 // Look-ahead rounds (lookahead.cuh): round j's record from round j-1's state (half-length h = 2 h2)
 // and challenge.  Before the challenge: la_miller (the 8 K h2 Miller values by class; then pairwise
 // products to 8 K and their final exponentiations, fe), la_sparse (the 6 K (4 h2) G1 terms; then
-// pairwise sums to 6 K, affine, acc), la_pre (the shifted bases of the 4-part GT exponentiations and
+// pairwise sums to 6 K, affine, acc; the caller zeroes out_g1j first), la_pre (the shifted bases of the 4-part GT exponentiations and
 // G1 multiplications: gpre 12 K Fq12, acc2 12 K G1).  After it: la_gt (the 16 K exponentiation
 // parts, pwp) and la_out (round j's record).
 void la_miller(const void* A, const void* v, uint32_t K, uint32_t R, uint32_t h2, void* out_fq12, cudaStream_t s);

@@ -7,6 +7,8 @@
 #include <cstdio>
 #include <cstdlib>
 #include <cstring>
+#include <atomic>
+#include <chrono>
 #include <mutex>
 #include <string>
 #include <utility>
@@ -134,7 +136,9 @@ size_t bopen_len(uint32_t log_r) { return (size_t)log_r * ROUND_BYTES + G1_SER +
 // created per call.  Each caller stream (per device) gets its own set, so calls on different caller
 // streams run concurrently; past 256 caller streams the sets are shared (still correct, less
 // concurrent).
-struct Streams { cudaStream_t hi = nullptr, sp = nullptr, pre = nullptr, la = nullptr, fold = nullptr, lo = nullptr; };
+struct Streams {
+    cudaStream_t hi = nullptr, sp = nullptr, pre = nullptr, la[2] = {nullptr, nullptr}, fold = nullptr, lo = nullptr;
+};
 struct StreamKey { int dev; cudaStream_t user; Streams set; };
 std::vector<StreamKey> g_sets;
 std::mutex g_aux_mu;
@@ -145,7 +149,8 @@ Streams make_set() {
     check(cudaStreamCreateWithPriority(&a.hi, cudaStreamNonBlocking, hi), "cudaStreamCreate");
     check(cudaStreamCreateWithPriority(&a.sp, cudaStreamNonBlocking, hi), "cudaStreamCreate");
     check(cudaStreamCreateWithPriority(&a.pre, cudaStreamNonBlocking, hi), "cudaStreamCreate");
-    check(cudaStreamCreateWithPriority(&a.la, cudaStreamNonBlocking, hi), "cudaStreamCreate");
+    check(cudaStreamCreateWithPriority(&a.la[0], cudaStreamNonBlocking, hi), "cudaStreamCreate");
+    check(cudaStreamCreateWithPriority(&a.la[1], cudaStreamNonBlocking, hi), "cudaStreamCreate");
     check(cudaStreamCreateWithPriority(&a.fold, cudaStreamNonBlocking, hi), "cudaStreamCreate");
     check(cudaStreamCreateWithPriority(&a.lo, cudaStreamNonBlocking, lo), "cudaStreamCreate");
     return a;
@@ -469,31 +474,32 @@ Step1Bufs step1_bufs(const fp_pp* pp, uint32_t Kc, Alloc&& T) {
     return B;
 }
 
-// Look-ahead buffers (lookahead.cuh) for Kc blocks of R rows: a snapshot of round j-1's state, the
-// Miller values by class and their pairwise products (8 Kc h2 <= 2 Kc R), the final exponentiations,
-// affine G1 sums and shifted bases of two rounds in flight, the exponentiation parts, the G1 terms
-// (6 Kc 4 h2 <= 6 Kc R) and their pairwise sums
+// Look-ahead buffers (lookahead.cuh) for Kc blocks of R rows, one set per parity of the round (two
+// rounds' look-aheads run at once, on two streams): a snapshot of round j-1's state, the Miller
+// values by class and their pairwise products (8 Kc h2 <= 2 Kc R), the final exponentiations, affine
+// G1 sums and shifted bases, the G1 terms (6 Kc 4 h2 <= 6 Kc R) and their pairwise sums; and the
+// exponentiation parts, used on the challenge stream only
 struct LaBufs {
-    void *A, *v, *bvec, *ml, *ml2, *fe[2], *gpre[2], *acc[2], *acc2[2], *pwp, *sp, *sp2;
+    void *A[2], *v[2], *bvec[2], *ml[2], *ml2[2], *fe[2], *gpre[2], *acc[2], *acc2[2], *sp[2], *sp2[2], *pwp;
 };
 template <class Alloc>
 LaBufs la_bufs(const fp_pp* pp, uint32_t Kc, Alloc&& T) {
     const uint64_t KR = (uint64_t)Kc * pp->R;
     LaBufs L;
-    L.A = T(KR * G1A_BYTES);
-    L.v = T(KR * G2A_BYTES);
-    L.bvec = T(KR * FR_BYTES);
-    L.ml = T(2 * KR * FQ12_BYTES);
-    L.ml2 = T((KR + 1) * FQ12_BYTES);
     for (int i = 0; i < 2; i++) {
+        L.A[i] = T(KR * G1A_BYTES);
+        L.v[i] = T(KR * G2A_BYTES);
+        L.bvec[i] = T(KR * FR_BYTES);
+        L.ml[i] = T(2 * KR * FQ12_BYTES);
+        L.ml2[i] = T((KR + 1) * FQ12_BYTES);
         L.fe[i] = T((size_t)8 * Kc * FQ12_BYTES);
         L.gpre[i] = T((size_t)12 * Kc * FQ12_BYTES);
         L.acc[i] = T((size_t)6 * Kc * G1A_BYTES);
         L.acc2[i] = T((size_t)12 * Kc * G1A_BYTES);
+        L.sp[i] = T(6 * KR * G1J_BYTES);
+        L.sp2[i] = T((3 * KR + 1) * G1J_BYTES);
     }
     L.pwp = T((size_t)16 * Kc * FQ12_BYTES);
-    L.sp = T(6 * KR * G1J_BYTES);
-    L.sp2 = T((3 * KR + 1) * G1J_BYTES);
     return L;
 }
 
@@ -545,16 +551,19 @@ void step1_rounds(const fp_pp* pp, uint32_t k0, uint32_t Kc, uint32_t b, const S
 }
 
 // The rounds with look-ahead (lookahead.cuh): round 1 as in step1_rounds; for j >= 2 round j's record
-// comes from round j-1's state (snapshotted on sL as soon as round j-2's fold has produced it, then
-// its Miller loops, final exponentiations and G1 sums) and x_{j-1} (GT exponentiations and the G1
-// multiplications on the challenge stream s1), while round j-1's fold runs on sF.  Challenges
-// alternate between two buffers (B.x_mont, B.xinv_mont hold 2 Kc entries) so that a fold still
-// reading x_{j-1} never meets x_j.  Streams: s1 challenges, s3 round 1's sparse G1 terms, s4 the
-// shifted fold bases, sL the look-ahead, sF the folds; s3 must already be ordered after whatever
-// filled B.bvec, s1 after B.A and B.v.
+// comes from round j-1's state S_{j-1} and x_{j-1}.  Round j's look-ahead (a snapshot of S_{j-1}, then
+// its Miller loops, final exponentiations, G1 sums and shifted bases) starts as soon as round j-2's
+// fold has produced S_{j-1}, on look-ahead stream j mod 2 with the buffers of that parity, so the
+// look-aheads of consecutive rounds overlap; once x_{j-1} is known only the GT exponentiations by
+// x_{j-1}^(+-1), the G1 multiplications and the challenge remain, on the challenge stream s1.  Round
+// j-1's fold runs on sF after x_{j-1} and round j's snapshot.  Challenges alternate between two
+// buffers (B.x_mont, B.xinv_mont hold 2 Kc entries); a fold still reading x_{j-1} never meets x_{j+1},
+// because x_{j+1} waits for round j+1's look-ahead, which waits for that fold.  Streams: s1 challenges,
+// s3 round 1's sparse G1 terms, s4 the shifted fold bases, sL[0..1] the look-aheads, sF the folds;
+// s3 must already be ordered after whatever filled B.bvec, s1 after B.A and B.v.
 void step1_rounds_la(const fp_pp* pp, uint32_t k0, uint32_t Kc, uint32_t b, const Step1Bufs& B,
                      const LaBufs& L, uint8_t* blocks1, size_t blen, cudaStream_t s1, cudaStream_t s3,
-                     cudaStream_t s4, cudaStream_t sL, cudaStream_t sF) {
+                     cudaStream_t s4, const cudaStream_t* sL, cudaStream_t sF) {
     const uint32_t R = pp->R;
     const int lr = (int)pp->log_r;
     const uint64_t KR = (uint64_t)Kc * R;
@@ -567,21 +576,24 @@ void step1_rounds_la(const fp_pp* pp, uint32_t k0, uint32_t Kc, uint32_t b, cons
     std::vector<cudaEvent_t> ev_S(lr + 2, nullptr), ev_snap(lr + 2, nullptr), ev_la(lr + 2, nullptr),
         ev_pre(lr + 2, nullptr), ev_x(lr + 2, nullptr);
 
-    // round j's look-ahead from the state S_{j-1} (ready on sL)
+    // round j's look-ahead from the state S_{j-1} (the caller has ordered sL[j & 1] after it)
     auto lookahead = [&](int j) {
+        const int q = j & 1;
+        const cudaStream_t st = sL[q];
         const uint32_t h2 = R >> j;
-        check(cudaMemcpyAsync(L.A, B.A, KR * G1A_BYTES, cudaMemcpyDeviceToDevice, sL), "D2D");
-        check(cudaMemcpyAsync(L.v, B.v, KR * G2A_BYTES, cudaMemcpyDeviceToDevice, sL), "D2D");
-        check(cudaMemcpyAsync(L.bvec, B.bvec, KR * FR_BYTES, cudaMemcpyDeviceToDevice, sL), "D2D");
-        ev_snap[j] = rec(sL);
-        la_miller(L.A, L.v, Kc, R, h2, L.ml, sL);
-        void* mlr = reduce_pairs(L.ml, L.ml2, (uint64_t)Kc * 8 * h2, (uint64_t)Kc * 8, fq12_pair_reduce, sL);
-        final_exp_group(mlr, 8 * Kc, L.fe[j & 1], nullptr, 1, 0, 0, sL);
-        la_sparse(L.A, L.bvec, k0, Kc, R, h2, b, L.sp, sL);
-        void* spr = reduce_pairs(L.sp, L.sp2, (uint64_t)Kc * 24 * h2, (uint64_t)Kc * 6, g1_pair_reduce, sL);
-        g1j_to_affine(spr, L.acc[j & 1], nullptr, 0, (uint64_t)Kc * 6, sL);
-        la_pre(L.fe[j & 1], L.acc[j & 1], Kc, L.gpre[j & 1], L.acc2[j & 1], sL);
-        ev_la[j] = rec(sL);
+        check(cudaMemcpyAsync(L.A[q], B.A, KR * G1A_BYTES, cudaMemcpyDeviceToDevice, st), "D2D");
+        check(cudaMemcpyAsync(L.v[q], B.v, KR * G2A_BYTES, cudaMemcpyDeviceToDevice, st), "D2D");
+        check(cudaMemcpyAsync(L.bvec[q], B.bvec, KR * FR_BYTES, cudaMemcpyDeviceToDevice, st), "D2D");
+        ev_snap[j] = rec(st);
+        la_miller(L.A[q], L.v[q], Kc, R, h2, L.ml[q], st);
+        void* mlr = reduce_pairs(L.ml[q], L.ml2[q], (uint64_t)Kc * 8 * h2, (uint64_t)Kc * 8, fq12_pair_reduce, st);
+        final_exp_group(mlr, 8 * Kc, L.fe[q], nullptr, 1, 0, 0, st);
+        check(cudaMemsetAsync(L.sp[q], 0, (size_t)Kc * 6 * 4 * h2 * G1J_BYTES, st), "memset");
+        la_sparse(L.A[q], L.bvec[q], k0, Kc, R, h2, b, L.sp[q], st);
+        void* spr = reduce_pairs(L.sp[q], L.sp2[q], (uint64_t)Kc * 24 * h2, (uint64_t)Kc * 6, g1_pair_reduce, st);
+        g1j_to_affine(spr, L.acc[q], nullptr, 0, (uint64_t)Kc * 6, st);
+        la_pre(L.fe[q], L.acc[q], Kc, L.gpre[q], L.acc2[q], st);
+        ev_la[j] = rec(st);
     };
     // round j's fold on sF (after x_j, the shifted bases and the snapshot of S_j for round j + 1)
     auto fold = [&](int j) {
@@ -603,8 +615,8 @@ void step1_rounds_la(const fp_pp* pp, uint32_t k0, uint32_t Kc, uint32_t b, cons
 
     cudaEvent_t ev_a = rec(s1), ev_b = rec(s3);     // S_1: A, v (s1) and b (s3)
     if (lr >= 2) {
-        wait(sL, ev_a);
-        wait(sL, ev_b);
+        wait(sL[0], ev_a);
+        wait(sL[0], ev_b);
         lookahead(2);
     }
     fold_pre(1, ev_a);
@@ -624,7 +636,7 @@ void step1_rounds_la(const fp_pp* pp, uint32_t k0, uint32_t Kc, uint32_t b, cons
     fold(1);
     for (int j = 2; j <= lr; j++) {
         if (j + 1 <= lr) {
-            wait(sL, ev_S[j]);
+            wait(sL[(j + 1) & 1], ev_S[j]);
             lookahead(j + 1);
         }
         fold_pre(j, ev_S[j]);
@@ -648,16 +660,9 @@ void step1_rounds_la(const fp_pp* pp, uint32_t k0, uint32_t Kc, uint32_t b, cons
     for (cudaEvent_t e : evs) cudaEventDestroy(e);
 }
 
-// Step 1 with look-ahead rounds when FP_LOOKAHEAD=1 is set in the environment and the blocks are few
-// (K R <= 4096: the look-ahead runs four times a round's Miller loops beside the chain); the records
-// are the same, the chain of dependent launches shorter.  Off by default.
-bool lookahead_on(uint32_t Kc, uint32_t R, int log_r) {
-    static const bool env = [] {
-        const char* e = getenv("FP_LOOKAHEAD");
-        return e && e[0] == '1';
-    }();
-    return env && log_r >= 2 && (uint64_t)Kc * R <= 4096;
-}
+// Step-1 schedule of the library (fp_set_schedule); the records are the same either way
+std::atomic<int> g_schedule{FP_SCHEDULE_DIRECT};
+bool lookahead_on(int log_r) { return g_schedule.load(std::memory_order_relaxed) == FP_SCHEDULE_LOOKAHEAD && log_r >= 2; }
 
 // OpenAll's work with Step 1 restricted to the blocks [k0, k0 + Kc) (all blocks: k0 = 0, Kc = K):
 // their records are written at their places in the K-block array; Step 2 runs in full.
@@ -700,7 +705,7 @@ fp_proofs* prove_impl(const fp_pp* pp, const fp_commit* cm, uint32_t b, uint32_t
             }
             // every buffer is allocated (stream-ordered on s) before the fork to the internal streams
             const Step1Bufs B = step1_bufs(pp, Kc, T);
-            const bool la = lookahead_on(Kc, R, lr);
+            const bool la = lookahead_on(lr);
             const LaBufs L = la ? la_bufs(pp, Kc, T) : LaBufs{};
             void* hstmt = T(Kc * DIGEST);
             const Streams st = streams(s);
@@ -778,6 +783,13 @@ fp_proofs* prove_impl(const fp_pp* pp, const fp_commit* cm, uint32_t b, uint32_t
 
 extern "C" {
 
+fp_status fp_set_schedule(int schedule) {
+    if (schedule != FP_SCHEDULE_DIRECT && schedule != FP_SCHEDULE_LOOKAHEAD) return FP_EINVAL;
+    g_schedule.store(schedule, std::memory_order_relaxed);
+    return FP_OK;
+}
+int fp_get_schedule(void) { return g_schedule.load(std::memory_order_relaxed); }
+
 fp_status vc_prove_all(const fp_pp* pp, const fp_commit* cm, uint32_t b, void* stream, fp_proofs** out) {
     if (!pp || !cm || !out || cm->pp != pp) return FP_EINVAL;
     if (b < 1 || b > pp->R) return FP_EINVAL;
@@ -788,6 +800,19 @@ fp_status vc_prove_all(const fp_pp* pp, const fp_commit* cm, uint32_t b, void* s
 }
 
 }  // extern "C"
+
+namespace {
+// host wall-clock phases of this thread's last vc_prove_all_batch call (fp_batch_last_times)
+struct BatchTimes { double capture_ms = 0, instantiate_ms = 0, run_ms = 0; };
+thread_local BatchTimes g_batch_times;
+}  // namespace
+
+extern "C" fp_status fp_batch_last_times(double* capture_ms, double* instantiate_ms, double* run_ms) {
+    if (capture_ms) *capture_ms = g_batch_times.capture_ms;
+    if (instantiate_ms) *instantiate_ms = g_batch_times.instantiate_ms;
+    if (run_ms) *run_ms = g_batch_times.run_ms;
+    return FP_OK;
+}
 
 namespace {
 // library-owned streams for the jobs of a batch (0 .. 63) and a graph-capture origin (64), per
@@ -814,6 +839,11 @@ extern "C" {
 
 fp_status vc_prove_all_batch(uint32_t njobs, const fp_job* jobs, int use_graph, void* stream, fp_proofs** outs) {
     if (!jobs || !outs) return njobs ? FP_EINVAL : FP_OK;
+    g_batch_times = BatchTimes{};
+    const auto t_start = std::chrono::steady_clock::now();
+    auto ms_since = [](std::chrono::steady_clock::time_point a) {
+        return std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - a).count();
+    };
     for (uint32_t j = 0; j < njobs; j++) {
         const fp_commit* cm = jobs[j].cm;
         if (!cm || jobs[j].b < 1 || jobs[j].b > cm->pp->R) return FP_EINVAL;
@@ -853,12 +883,17 @@ fp_status vc_prove_all_batch(uint32_t njobs, const fp_job* jobs, int use_graph, 
             if (use_graph) {
                 capturing = false;
                 check(cudaStreamEndCapture(s, &graph), "cudaStreamEndCapture");
+                g_batch_times.capture_ms = ms_since(t_start);
+                const auto t_inst = std::chrono::steady_clock::now();
                 check(cudaGraphInstantiate(&exec, graph, 0), "cudaGraphInstantiate");
+                g_batch_times.instantiate_ms = ms_since(t_inst);
                 s = launch;
                 for (uint32_t j = 0; j < njobs; j++)
                     if (jobs[j].cm->done) check(cudaStreamWaitEvent(s, jobs[j].cm->done, 0), "wait");
+                const auto t_run = std::chrono::steady_clock::now();
                 check(cudaGraphLaunch(exec, s), "cudaGraphLaunch");
                 check(cudaStreamSynchronize(s), "vc_prove_all_batch");
+                g_batch_times.run_ms = ms_since(t_run);
                 cudaGraphExecDestroy(exec);
                 cudaGraphDestroy(graph);
                 exec = nullptr;
@@ -1005,7 +1040,7 @@ fp_status vc_eval_prove(const fp_pp* pp, const fp_commit* cm, const uint8_t* r, 
             void* terms = T((size_t)(lc ? lc : 1) * half * G1J_BYTES);
             void* terms2 = T((half / 2 + 1) * G1J_BYTES);
             const Step1Bufs B = step1_bufs(pp, 1, T);
-            const bool la = lookahead_on(1, R, (int)pp->log_r);
+            const bool la = lookahead_on((int)pp->log_r);
             const LaBufs L = la ? la_bufs(pp, 1, T) : LaBufs{};
             const Streams st = streams(s);
             cudaStream_t s1 = st.hi, s3 = st.sp;

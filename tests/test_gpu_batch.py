@@ -48,7 +48,7 @@ def test_commit_async_status():
 
 
 @pytest.mark.parametrize("use_graph", [False, True])
-def test_batch_equals_single_calls_and_oracle(use_graph):
+def test_batch_equals_single_calls_and_oracle(use_graph, schedule):
     seed = 17
     parent = F.PP(10, 1, seed)
     sizes = [4, 5, 6, 7, 8, 10, 4, 9, 6, 5]
@@ -76,7 +76,7 @@ def test_batch_equals_single_calls_and_oracle(use_graph):
         assert outs[j].export(0, cm.pp.N) == b"".join(pr.proof(i) for i in range(cm.pp.N))
 
 
-def test_batched_workload_64_jobs_sampled():
+def test_batched_workload_64_jobs_sampled(schedule):
     """64 jobs, log N uniform in 8..18 by seed, b = min(R, nearestpow2(log^2 N)), one SRS for 2^18:
     the graph-captured batch equals single calls (shared state of every job), and the smallest
     job's proofs equal the oracle's."""

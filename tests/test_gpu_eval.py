@@ -25,7 +25,7 @@ def point(seed, n):
 
 
 @pytest.mark.parametrize("log_n,log_r", [(4, 2), (5, 2), (7, 3), (6, 5), (8, 1), (10, 5)])
-def test_eval_proof_equals_oracle(log_n, log_r):
+def test_eval_proof_equals_oracle(log_n, log_r, schedule):
     seed = 71 + log_n
     pp = F.PP(log_n, 1, seed, log_r=log_r)
     opp = O.PP(log_n, seed, log_r=log_r)
@@ -57,7 +57,7 @@ def test_eval_boolean_points_and_range():
     assert e.value.status == 6
 
 
-def test_eval_n16():
+def test_eval_n16(schedule):
     log_n, seed = 16, 0
     pp = F.PP(log_n, 1, seed)
     opp = O.PP(log_n, seed)

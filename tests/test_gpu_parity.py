@@ -64,7 +64,7 @@ def test_commit_parity(log_n, dist):
 
 
 @pytest.mark.parametrize("log_n,b", [(2, 1), (2, 2), (4, 1), (4, 3), (4, 4), (5, 1), (5, 3), (5, 4)])
-def test_prove_all_every_proof(log_n, b):
+def test_prove_all_every_proof(log_n, b, schedule):
     seed = 7
     pp, opp = gpu_pp(log_n, seed), oracle_pp(log_n, seed)
     m = vec(log_n, seed + 1)
@@ -82,7 +82,7 @@ def test_prove_all_every_proof(log_n, b):
     assert all(O.verify_many(opp, C, b, [(i, vals[i], pr.proof(i)) for i in range(pp.N)]))
 
 
-def test_config1_n1024_b1_all_proofs_and_verify():
+def test_config1_n1024_b1_all_proofs_and_verify(schedule):
     """N = 2^10, b = 1, seed 0: every one of the 1024 proofs equals the oracle's and verifies."""
     log_n, seed, b = 10, 0, 1
     pp, opp = F.PP(log_n, b, seed), O.PP(log_n, seed)
@@ -108,7 +108,7 @@ def test_config1_n1024_b1_all_proofs_and_verify():
     assert all(O.verify_many(opp, C, b, items))
 
 
-def test_empty_and_degenerate_vectors():
+def test_empty_and_degenerate_vectors(schedule):
     """All-zero vector (identity rows, e(O, .) = 1) and a single non-zero entry."""
     log_n, seed, b = 4, 3, 2
     pp, opp = gpu_pp(log_n, seed), oracle_pp(log_n, seed)
@@ -173,7 +173,7 @@ def test_n16_commit_closed_form(dist):
 
 @pytest.mark.parametrize("b,blocks,dist", [(256, [0], "uniform"), (1, [0, 77, 128, 255], "uniform"),
                                           (256, [0], "u32"), (1, [0, 255], "u32")])
-def test_n16_prove_all_sampled(b, blocks, dist):
+def test_n16_prove_all_sampled(b, blocks, dist, schedule):
     """OpenAll at N = 2^16 in the benchmark's launch configuration: the whole shared state (every
     Merkle digest, r_j, every fold-tree node D_w and g_w, every PST quotient commitment) equal to
     the oracle's, the block records of the oracle's blocks (all of them at b = 256), and sampled
@@ -197,7 +197,7 @@ def test_n16_prove_all_sampled(b, blocks, dist):
 
 
 @pytest.mark.parametrize("log_n,b", [(4, 1), (5, 3), (6, 8)])
-def test_prove_one_equals_oracle_brute_force_and_prove_all(log_n, b):
+def test_prove_one_equals_oracle_brute_force_and_prove_all(log_n, b, schedule):
     """vc_prove_one (Step 1 on the index's block only) against the oracle's brute-force
     single-index prover and against vc_prove_all's proof, for every index of a ragged layout."""
     seed = 9
@@ -213,7 +213,7 @@ def test_prove_one_equals_oracle_brute_force_and_prove_all(log_n, b):
             assert one == O.prove_one(opp, m.tobytes(), C, rows, b, i), i
 
 
-def test_prove_one_n16_sampled():
+def test_prove_one_n16_sampled(schedule):
     pp, opp, m, cm, (C, rows) = n16("uniform")
     vals = I.to_ints(m)
     for b, i in ((256, 12345), (1, 65535), (16, 40000)):
@@ -259,14 +259,19 @@ def test_n20_setup_and_commit_closed_form():
     assert cm.get() == exp
 
 
-@pytest.mark.parametrize("b", sorted(N20_BLOCKS, reverse=True))
-def test_n20_prove_all_sampled(b):
+@pytest.mark.parametrize("b,sched", [(1024, "direct"), (1024, "lookahead"), (256, "direct"), (256, "lookahead"),
+                                     (16, "direct"), (1, "direct")])
+def test_n20_prove_all_sampled(b, sched):
     """OpenAll at N = 2^20 in the benchmark's launch configuration: Step-2 state equal to the
     oracle's, sampled proofs of the sampled blocks byte-identical and accepted by the oracle's
     verifier, and every one of the 2^20 proofs accepted by the GPU batch verifier."""
     pp, opp, m, cm, (C, rows) = n20()
     pr = n20_oracle()[b]
-    pf = F.Proofs(pp, cm, b)
+    F.set_schedule(sched)
+    try:
+        pf = F.Proofs(pp, cm, b)
+    finally:
+        F.set_schedule("direct")
     assert pf.step2_parts() == pr.step2_parts()
     _state.assert_equal(pf.state(), pr.state(), pp.R, pp.M, pr.K, opp.log_r, N20_BLOCKS[b])
     rnd = random.Random(b)

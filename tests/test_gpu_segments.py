@@ -41,7 +41,7 @@ def test_split_views_equal_fresh_setups():
 
 
 @pytest.mark.parametrize("log_r,log_c,b", [(4, 2, 3), (5, 1, 1), (1, 5, 2), (3, 4, 8)])
-def test_segment_proofs_equal_oracle_and_verify(log_r, log_c, b):
+def test_segment_proofs_equal_oracle_and_verify(log_r, log_c, b, schedule):
     log_n, seed = log_r + log_c, 31
     pp = F.PP(log_n, 1, seed, log_r=log_r)
     opp = O.PP(log_n, seed, log_r=log_r)
@@ -63,7 +63,7 @@ def test_segment_proofs_equal_oracle_and_verify(log_r, log_c, b):
         seg.proof(0)                              # no element proofs without Step 2
 
 
-def test_segment_block_range_and_rejections():
+def test_segment_block_range_and_rejections(schedule):
     log_r, log_c, b, seed = 4, 3, 2, 41
     log_n = log_r + log_c
     pp = F.PP(log_n, 1, seed, log_r=log_r)
@@ -101,7 +101,7 @@ def test_segment_block_range_and_rejections():
 
 
 @pytest.mark.parametrize("log_r,log_c,b", [(5, 2, 3), (1, 6, 1), (4, 1, 16)])
-def test_full_openall_on_other_splits(log_r, log_c, b):
+def test_full_openall_on_other_splits(log_r, log_c, b, schedule):
     """Every element proof on splits with R > M or R = 2 equals the oracle's; all verify."""
     log_n, seed = log_r + log_c, 51
     pp = F.PP(log_n, 1, seed, log_r=log_r)

@@ -54,3 +54,20 @@ def test_noalloc_limits_and_range():
     assert e.value.status == 6
     good = I.vector(3, 4)                      # the status word is cleared by the next call
     assert rows_via_noalloc(pp, good, None) == rows_via_commit(pp, good)
+
+
+def test_noalloc_allocates_no_device_memory():
+    """The device's free memory is the same before and after further calls (inputs, outputs and
+    torch's caching allocator all set up beforehand; the first call did the one-time set-up)."""
+    log_n = 14
+    pp = F.PP(log_n, 1, 5)
+    stream = torch.cuda.current_stream()
+    m_dev = torch.from_numpy(np.ascontiguousarray(I.vector(31, log_n)).view(np.int64).copy()).cuda()
+    out = torch.zeros(96 * pp.R, dtype=torch.uint8, device="cuda")
+    F.vc_commit_rows_noalloc(pp, m_dev, out, stream)
+    torch.cuda.synchronize()
+    free0 = torch.cuda.mem_get_info()[0]
+    for _ in range(3):
+        F.vc_commit_rows_noalloc(pp, m_dev, out, stream)
+    torch.cuda.synchronize()
+    assert torch.cuda.mem_get_info()[0] == free0
