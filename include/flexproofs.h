@@ -309,6 +309,43 @@ void fp_proofs_free(fp_proofs* pf);
  *                          measured size (kept as an option).
  * A process-wide setting, read when a call enqueues its work.  FP_EINVAL for another value. */
 typedef enum { FP_SCHEDULE_DIRECT = 0, FP_SCHEDULE_LOOKAHEAD = 1 } fp_schedule;
+
+/* Engine choice by size (no counterpart in the paper: how the device work is laid out).  Each launch
+ * runs its pairings, final exponentiations, fold points or terms either on a latency engine (one
+ * 128-thread block or one warp per item: shortest chain, few items) or on a throughput engine (one
+ * thread per item: least total work, many items); every engine computes the same values, so these
+ * limits change which kernels run and how fast, never the bytes.  Counts are per launch.
+ *   miller_block_max / miller_warp_max   Step-1 Miller loops: <= block_max a block each, <= warp_max
+ *                                        a warp each, above a thread each (default 1024 / 16383)
+ *   miller_group_min                     from this many (and h >= 4), a thread runs 4 pairs of one
+ *                                        product with shared squarings (default 2^18)
+ *   commit_block_max / commit_warp_max   Commit's R Miller loops, the same way (default 1024 / 16384)
+ *   fe_block_max / fe_warp_max           final exponentiations: block / warp / thread (256 / 2^32-1)
+ *   pair_block_max                       pairwise Fq12 products: <= a block each, above a thread (2048)
+ *   fold_warp_max                        fold points of rounds beyond the split folds (more than 256
+ *                                        points): <= a warp (G2) and 8 lanes (G1) each, above a thread
+ *                                        (4096)
+ *   wterm_warp_max                       terms of the v_l proof W when not by MSM: <= a warp each,
+ *                                        above a thread (4096)
+ *   msm_chunks                           MSM bucket pass: about this many chunks of the sorted entry
+ *                                        list, one thread each (2^17; > 0)
+ *   msm_segment_threads                  MSM bucket reduction: at most about this many segment
+ *                                        threads (2^15; > 0)
+ * A process-wide setting read when a call enqueues its work (set it between calls: a call enqueued
+ * concurrently may see either setting).  fp_set_engine_limits(NULL) restores the defaults;
+ * FP_EINVAL for a zero msm_chunks or msm_segment_threads. */
+typedef struct {
+    uint32_t miller_block_max, miller_warp_max, miller_group_min;
+    uint32_t commit_block_max, commit_warp_max;
+    uint32_t fe_block_max, fe_warp_max;
+    uint32_t pair_block_max;
+    uint32_t fold_warp_max;
+    uint32_t wterm_warp_max;
+    uint32_t msm_chunks, msm_segment_threads;
+} fp_engine_limits;
+fp_status fp_engine_limits_default(fp_engine_limits* out);
+fp_status fp_set_engine_limits(const fp_engine_limits* lim);
+fp_status fp_get_engine_limits(fp_engine_limits* out);
 fp_status fp_set_schedule(int schedule);
 int fp_get_schedule(void);
 

@@ -23,7 +23,16 @@ EXPORTED = ["vc_setup", "vc_pp_export", "vc_pp_dims", "vc_commit", "vc_commit_ge
             "vc_commit_status", "vc_prove_all_batch", "vc_verify", "vc_verify_all", "vc_setup_split",
             "vc_pp_view_split", "vc_open_segments", "vc_segment_proof_len", "vc_segment_proof_get",
             "vc_verify_segment", "vc_eval_proof_len", "vc_eval_prove", "vc_eval_verify", "fp_set_schedule",
-            "fp_get_schedule", "fp_batch_last_times"]
+            "fp_get_schedule", "fp_batch_last_times", "fp_engine_limits_default", "fp_set_engine_limits",
+            "fp_get_engine_limits"]
+
+LIMIT_FIELDS = ["miller_block_max", "miller_warp_max", "miller_group_min", "commit_block_max", "commit_warp_max",
+                "fe_block_max", "fe_warp_max", "pair_block_max", "fold_warp_max", "wterm_warp_max", "msm_chunks",
+                "msm_segment_threads"]
+
+
+class _Limits(ctypes.Structure):
+    _fields_ = [(f, ctypes.c_uint32) for f in LIMIT_FIELDS]
 
 SCHEDULES = {"direct": 0, "lookahead": 1}
 
@@ -107,6 +116,8 @@ def load(path: str = LIB_PATH):
     L.fp_set_schedule.argtypes = [ctypes.c_int]
     L.fp_get_schedule.restype = ctypes.c_int
     L.fp_batch_last_times.argtypes = [ctypes.POINTER(ctypes.c_double)] * 3
+    for n in ("fp_engine_limits_default", "fp_set_engine_limits", "fp_get_engine_limits"):
+        getattr(L, n).argtypes = [ctypes.POINTER(_Limits)]
     _lib = L
     return L
 
@@ -127,6 +138,33 @@ def batch_last_times() -> dict:
     v = [ctypes.c_double() for _ in range(3)]
     _check("fp_batch_last_times", load().fp_batch_last_times(*[ctypes.byref(x) for x in v]))
     return {"capture_ms": v[0].value, "instantiate_ms": v[1].value, "run_ms": v[2].value}
+
+
+def default_engine_limits() -> dict:
+    lim = _Limits()
+    _check("fp_engine_limits_default", load().fp_engine_limits_default(ctypes.byref(lim)))
+    return {f: getattr(lim, f) for f in LIMIT_FIELDS}
+
+
+def engine_limits() -> dict:
+    """The current engine-choice limits (fp_get_engine_limits)."""
+    lim = _Limits()
+    _check("fp_get_engine_limits", load().fp_get_engine_limits(ctypes.byref(lim)))
+    return {f: getattr(lim, f) for f in LIMIT_FIELDS}
+
+
+def set_engine_limits(limits: dict | None = None) -> None:
+    """Set the engine-choice limits for later calls (fp_set_engine_limits): fields not given keep
+    their defaults; None restores every default."""
+    if limits is None:
+        _check("fp_set_engine_limits", load().fp_set_engine_limits(None))
+        return
+    unknown = set(limits) - set(LIMIT_FIELDS)
+    if unknown:
+        raise ValueError(f"unknown engine limits: {sorted(unknown)}")
+    vals = dict(default_engine_limits(), **limits)
+    lim = _Limits(**{f: min(int(vals[f]), 0xFFFFFFFF) for f in LIMIT_FIELDS})
+    _check("fp_set_engine_limits", load().fp_set_engine_limits(ctypes.byref(lim)))
 
 
 def get_schedule() -> str:

@@ -81,10 +81,30 @@ __global__ void __launch_bounds__(128) k_final_exp_c(const fq12* in, uint32_t n,
     }
 }
 
+// one thread per final exponentiation (many of them: the least work in total)
+__global__ void k_final_exp_t(const fq12* in, uint32_t n, fq12* out, uint8_t* ser, uint32_t per, size_t stride_a,
+                              size_t stride_b) {
+    const uint64_t t = gtid();
+    if (t >= n) return;
+    const fq12 r = final_exp(in[t]);
+    if (out) out[t] = r;
+    if (ser) {
+        const fq* c = reinterpret_cast<const fq*>(&r);
+        for (int q = 0; q < 12; q++) fq_to_be(ser + (t / per) * stride_a + (t % per) * stride_b + 48 * q, c[q]);
+    }
+}
+
 void final_exp_group(const void* in, uint32_t n, void* out, void* ser, uint32_t per, size_t stride_a,
                      size_t stride_b, cudaStream_t s) {
     if (!n) return;
-    if (n <= 256) {
+    const EngineLimits lim = engine_limits();
+    if (n > lim.fe_warp_max && n > lim.fe_block_max) {
+        FP_KERNEL("k_final_exp_t", s, k_final_exp_t<<<grid_for(n, 64), 64, 0, s>>>((const fq12*)in, n, (fq12*)out,
+                                                                                  (uint8_t*)ser, per, stride_a,
+                                                                                  stride_b));
+        return;
+    }
+    if (n <= lim.fe_block_max) {
         FP_KERNEL("k_final_exp_c", s, k_final_exp_c<<<n, 128, 0, s>>>((const fq12*)in, n, (fq12*)out, (uint8_t*)ser, per,
                                                                      stride_a, stride_b));
         return;
@@ -114,7 +134,7 @@ __global__ void __launch_bounds__(128) k_fq12_pair_c(const fq12* in, fq12* out) 
 }
 void fq12_pair_reduce(const void* in, void* out, uint64_t n, cudaStream_t s) {
     if (!n) return;
-    if (n <= 2048) {
+    if (n <= engine_limits().pair_block_max) {
         FP_KERNEL("k_fq12_pair_c", s, k_fq12_pair_c<<<(unsigned)n, 128, 0, s>>>((const fq12*)in, (fq12*)out));
         return;
     }
@@ -168,7 +188,7 @@ __global__ void __launch_bounds__(128) k_commit_miller_c(const g1a* rows, const 
 }
 void round_miller_w(const void* A, const void* v, uint32_t K, uint32_t R, uint32_t h, void* out, cudaStream_t s) {
     const uint64_t n = (uint64_t)K * 2 * h;
-    if (n <= 1024) {
+    if (n <= engine_limits().miller_block_max) {
         FP_KERNEL("k_round_miller_c", s, k_round_miller_c<<<(unsigned)n, 128, 0, s>>>((const g1a*)A, (const g2a*)v, K, R,
                                                                                      h, (fq12*)out));
         return;
@@ -179,13 +199,14 @@ void round_miller_w(const void* A, const void* v, uint32_t K, uint32_t R, uint32
 }
 
 void commit_miller(const void* rows, const void* g2pow, uint32_t R, void* out, cudaStream_t s) {
-    if ((uint64_t)R * 32 > 16384 * 32) {           // many pairs: one thread each does less work in total
+    const EngineLimits lim = engine_limits();
+    if (R > lim.commit_warp_max && R > lim.commit_block_max) {   // many pairs: one thread each, less work
         FP_KERNEL("k_commit_miller", s, k_commit_miller<<<grid_for(R, 64), 64, 0, s>>>((const g1a*)rows,
                                                                                        (const g2a*)g2pow, R,
                                                                                        (fq12*)out));
         return;
     }
-    if (R <= 1024) {
+    if (R <= lim.commit_block_max) {
         FP_KERNEL("k_commit_miller_c", s, k_commit_miller_c<<<R, 128, 0, s>>>((const g1a*)rows, (const g2a*)g2pow,
                                                                              (fq12*)out));
         return;
@@ -195,9 +216,12 @@ void commit_miller(const void* rows, const void* g2pow, uint32_t R, void* out, c
                                                                                    (fq12*)out));
 }
 // grouping pays once the grouped threads still fill the GPU several times over (2^16 threads)
-uint32_t step1_miller_group(uint64_t n, uint32_t h) { return (h >= 4 && n >= (1u << 18)) ? 4 : 1; }
-void step1_miller(const void* A, const void* v, uint32_t K, uint32_t R, uint32_t h, void* out, cudaStream_t s) {
-    if (step1_miller_group((uint64_t)K * 2 * h, h) == 4) {   // 4 pairs per thread share the squarings
+uint32_t step1_miller_group(uint64_t n, uint32_t h, const EngineLimits& lim) {
+    return (h >= 4 && n >= lim.miller_group_min) ? 4 : 1;
+}
+void step1_miller(const void* A, const void* v, uint32_t K, uint32_t R, uint32_t h, uint32_t group, void* out,
+                  cudaStream_t s) {
+    if (group == 4) {                                   // 4 pairs per thread share the squarings
         const uint64_t n = (uint64_t)K * 2 * (h / 4);
         FP_KERNEL("k_step1_miller_multi", s,
                   k_step1_miller_multi<4><<<grid_for(n, 64), 64, 0, s>>>((const g1a*)A, (const g2a*)v, K, R, h,

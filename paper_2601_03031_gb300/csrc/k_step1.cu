@@ -458,7 +458,7 @@ void step1_kzg(const void* A, const void* v, const void* xprev, const void* xinv
 }
 void step1_w_terms(const void* g2pow, const void* q_canon, uint32_t K, uint32_t R, void* out, cudaStream_t s) {
     const uint64_t n = (uint64_t)K * 2 * R;
-    if (n <= 4096) {                    // few terms: a warp per term for latency
+    if (n <= engine_limits().wterm_warp_max) {      // few terms: a warp per term for latency
         FP_KERNEL("k_w_terms_w", s, k_w_terms_w<<<(unsigned)((n + 3) / 4), 128, 0, s>>>((const g2a*)g2pow,
                                                                                        (const fr*)q_canon, K, R,
                                                                                        (g2j*)out));
@@ -474,9 +474,11 @@ namespace fpk {
 uint64_t step1_miller_g(const void* A, const void* v, uint32_t K, uint32_t R, uint32_t h, void* ml_out,
                         cudaStream_t s) {
     uint64_t n = (uint64_t)K * 2 * h;
-    if (n >= 16384) {          // enough pairs to fill the GPU with threads: less work than warps
-        step1_miller(A, v, K, R, h, ml_out, s);
-        return n / step1_miller_group(n, h);
+    const EngineLimits lim = engine_limits();
+    if (n > lim.miller_warp_max && n > lim.miller_block_max) {   // many pairs: threads, less work than warps
+        const uint32_t group = step1_miller_group(n, h, lim);
+        step1_miller(A, v, K, R, h, group, ml_out, s);
+        return n / group;
     }
     round_miller_w(A, v, K, R, h, ml_out, s);      // few pairs: one warp or block each, for latency
     return n;
@@ -512,7 +514,7 @@ void step1_fold(void* A, void* v, void* bvec, const void* x_mont, const void* xi
                                                                          K, R, h, nb2));
         return;
     }
-    if ((uint64_t)K * h <= 4096) {      // few points: a warp per G2 point, an 8-lane group per G1 point
+    if ((uint64_t)K * h <= engine_limits().fold_warp_max) {   // few points: a warp per G2 point, 8 lanes per G1
         const uint32_t nb2 = (uint32_t)(((uint64_t)K * h + 3) / 4), nb1 = (uint32_t)(((uint64_t)K * h + 15) / 16);
         FP_KERNEL("k_fold_w", s, k_fold_w<<<nb2 + nb1, 128, 0, s>>>((g1a*)A, (g2a*)v, (fr*)bvec, (const fr*)x_mont,
                                                                   (const fr*)xinv_mont, K, R, h, nb2));

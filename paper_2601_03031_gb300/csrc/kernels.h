@@ -20,6 +20,27 @@ void prof_end(cudaStream_t s);
         fpk::prof_end(stream);       \
     } while (0)
 
+// Engine choice by size: the launchers pick a latency engine (one 128-thread block or one warp per
+// pairing, final exponentiation or point) for few items and a throughput engine (one thread each)
+// for many.  The limits are process-wide (fp_set_engine_limits); every decision reads them once, and
+// every engine computes the same values, so a limit changes which kernels run, never the bytes.
+struct EngineLimits {
+    uint32_t miller_block_max = 1024;       // Step-1 Miller loops per launch: <= this, a block each
+    uint32_t miller_warp_max = 16383;       //   <= this, a warp each; above, a thread each
+    uint32_t miller_group_min = 1u << 18;   //   from this many (h >= 4), 4 pairs of a product per thread
+    uint32_t commit_block_max = 1024;       // Commit's Miller loops: <= this, a block each
+    uint32_t commit_warp_max = 16384;       //   <= this, a warp each; above, a thread each
+    uint32_t fe_block_max = 256;            // final exponentiations per launch: <= this, a block each
+    uint32_t fe_warp_max = 0xffffffffu;     //   <= this, a warp each; above, a thread each
+    uint32_t pair_block_max = 2048;         // pairwise Fq12 products: <= this, a block each; above, a thread
+    uint32_t fold_warp_max = 4096;          // fold points (beyond the split folds): <= this, a warp / 8 lanes
+                                            //   per point; above, a thread per point
+    uint32_t wterm_warp_max = 4096;         // W terms: <= this, a warp per term; above, a thread per term
+    uint32_t msm_chunks = 1u << 17;         // MSM bucket pass: about this many chunks of the entry list
+    uint32_t msm_segment_threads = 1u << 15;  // MSM bucket reduction: at most about this many segments
+};
+EngineLimits engine_limits();              // a snapshot of the current limits
+
 constexpr size_t FR_BYTES = 32;     // fr: 8 x u32, Montgomery or canonical as documented
 constexpr size_t G1A_BYTES = 96;    // affine G1, Montgomery, (0,0) = identity
 constexpr size_t G1J_BYTES = 144;   // Jacobian G1
@@ -63,8 +84,9 @@ void step1_stmt_hash(const void* C_ser, const void* rows_ser, uint32_t k0, uint3
 void step1_block_r(const void* hstmt, uint32_t k0, uint32_t K, uint32_t R, uint32_t b, void* bvec, cudaStream_t s);
 // one thread per step1_miller_group(h) pairs of a product (multi-pair Miller loop); the outputs are
 // the products over those groups, in pair order
-uint32_t step1_miller_group(uint64_t n, uint32_t h);
-void step1_miller(const void* A, const void* v, uint32_t K, uint32_t R, uint32_t h, void* out_fq12, cudaStream_t s);
+uint32_t step1_miller_group(uint64_t n, uint32_t h, const EngineLimits& lim);
+void step1_miller(const void* A, const void* v, uint32_t K, uint32_t R, uint32_t h, uint32_t group, void* out_fq12,
+                  cudaStream_t s);
 // the same Miller loops with one warp per pair (few pairs: latency)
 void round_miller_w(const void* A, const void* v, uint32_t K, uint32_t R, uint32_t h, void* out_fq12, cudaStream_t s);
 // L_j.1 / R_j.1 terms at the support of the b vectors of blocks k0 .. k0 + K - 1 (blocks of size b),

@@ -471,25 +471,25 @@ MsmShape msm_shape(uint64_t n, uint32_t nbatch, uint64_t npts, int c, int parts,
     sh.n_hi = part_bits - sh.W * (sh.c - 1);
     sh.KW = sh.off(sh.W);
     // segments of at least 4 buckets in the narrowest window, at most about 2^15 segment threads
+    // at most about lim.msm_segment_threads segment threads; entries per chunk of the bucket pass
+    // so that there are about lim.msm_chunks chunks (enough to fill the GPU a few times over), >= 8
+    const EngineLimits lim = engine_limits();
+    const uint64_t seg_cap = lim.msm_segment_threads ? lim.msm_segment_threads : 1;
     uint32_t S = sh.buckets(sh.W - 1);
     while (S > 1 && sh.buckets(sh.W - 1) / S < 4) S >>= 1;
-    while (S > 1 && (uint64_t)nbatch * sh.W * S > (1u << 15)) S >>= 1;
+    while (S > 1 && (uint64_t)nbatch * sh.W * S > seg_cap) S >>= 1;
     sh.S = S;
+    const uint64_t chunks = lim.msm_chunks ? lim.msm_chunks : 1;
+    const uint64_t T = (sh.entries_max() + chunks - 1) / chunks;
+    sh.T = (uint32_t)std::min<uint64_t>(std::max<uint64_t>(T, 8), 1u << 30);
     return sh;
-}
-
-// entries per chunk of the bucket pass: enough chunks to fill the GPU a few times over
-static uint32_t msm_chunk_len(const MsmShape& sh) {
-    const uint64_t e = sh.entries_max();
-    uint64_t T = (e + (1u << 17) - 1) >> 17;
-    return (uint32_t)(T < 8 ? 8 : T);
 }
 
 template <typename F>
 static size_t scratch_bytes(const MsmShape& sh) {
     const uint64_t nk = sh.nkeys();
     auto r = [](size_t b) { return (b + 255) & ~(size_t)255; };
-    const uint64_t nchunks = (sh.entries_max() + msm_chunk_len(sh) - 1) / msm_chunk_len(sh);
+    const uint64_t nchunks = (sh.entries_max() + sh.T - 1) / sh.T;
     size_t b = 3 * r(nk * 4) + r(scan_tmp_words(nk) * 4);
     b += 2 * r(sh.entries_max() * 4);
     b += r(nk * sizeof(xyzz_t<F>));
@@ -545,7 +545,7 @@ static void msm_run(const void* bases, const void* k_canon, const MsmShape& sh, 
     uint32_t* scan_tmp = (uint32_t*)take(scan_tmp_words(nk) * 4);
     uint32_t* list = (uint32_t*)take(sh.entries_max() * 4);
     uint32_t* keys = (uint32_t*)take(sh.entries_max() * 4);
-    const uint32_t T = msm_chunk_len(sh);
+    const uint32_t T = sh.T;
     const uint64_t nchunks = (sh.entries_max() + T - 1) / T;
     X* buckets = (X*)take(nk * sizeof(X));
     X* head = (X*)take(nchunks * sizeof(X));

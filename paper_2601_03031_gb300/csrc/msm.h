@@ -18,6 +18,7 @@ struct MsmShape {
     int c, W, n_hi;     // widest window, windows per part, windows of width c
     uint32_t KW;        // buckets per batch, all windows
     uint32_t S;         // segments per window in the bucket reduction
+    uint32_t T;         // sorted bucket entries per chunk of the bucket pass (one thread each)
     __host__ __device__ int bits(int w) const { return w < n_hi ? c : c - 1; }
     __host__ __device__ int lo(int w) const { return w <= n_hi ? w * c : n_hi * c + (w - n_hi) * (c - 1); }
     __host__ __device__ uint32_t buckets(int w) const { return 1u << (bits(w) - 1); }

@@ -181,7 +181,16 @@ cudaEvent_t new_event() {
 
 }  // namespace
 
+namespace {
+std::mutex g_limits_mu;
+fpk::EngineLimits g_limits;
+}  // namespace
+
 namespace fpk {
+EngineLimits engine_limits() {
+    std::lock_guard<std::mutex> lk(g_limits_mu);
+    return g_limits;
+}
 const void* pp_lambda_top(const fp_pp* pp) { return (const uint8_t*)pp->lam + ((size_t)pp->M - 1) * G1A_BYTES; }
 }  // namespace fpk
 
@@ -782,6 +791,30 @@ fp_proofs* prove_impl(const fp_pp* pp, const fp_commit* cm, uint32_t b, uint32_t
 }  // namespace
 
 extern "C" {
+
+static_assert(sizeof(fp_engine_limits) == sizeof(fpk::EngineLimits), "engine limits layout");
+fp_status fp_engine_limits_default(fp_engine_limits* out) {
+    if (!out) return FP_EINVAL;
+    const fpk::EngineLimits d;
+    std::memcpy(out, &d, sizeof d);
+    return FP_OK;
+}
+fp_status fp_set_engine_limits(const fp_engine_limits* lim) {
+    fpk::EngineLimits v;
+    if (lim) {
+        std::memcpy(&v, lim, sizeof v);
+        if (!v.msm_chunks || !v.msm_segment_threads) return FP_EINVAL;
+    }
+    std::lock_guard<std::mutex> lk(g_limits_mu);
+    g_limits = v;
+    return FP_OK;
+}
+fp_status fp_get_engine_limits(fp_engine_limits* out) {
+    if (!out) return FP_EINVAL;
+    const fpk::EngineLimits v = fpk::engine_limits();
+    std::memcpy(out, &v, sizeof v);
+    return FP_OK;
+}
 
 fp_status fp_set_schedule(int schedule) {
     if (schedule != FP_SCHEDULE_DIRECT && schedule != FP_SCHEDULE_LOOKAHEAD) return FP_EINVAL;

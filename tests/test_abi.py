@@ -101,3 +101,29 @@ def test_new_entry_points_reject_bad_arguments_without_device_work():
     assert lib.vc_eval_verify(None, None, None, None, 0, None) == 1
     lib.vc_verify_all.argtypes = [vp, vp, vp, ctypes.c_int, vp, ctypes.c_int, vp, vp, vp]
     assert lib.vc_verify_all(None, None, None, 0, None, 0, None, None, None) == 1
+
+
+def test_engine_limits_and_schedule_settings_on_the_host():
+    """The process-wide settings need no device: defaults, partial updates, invalid values refused."""
+    from paper_2601_03031_gb300 import build as B
+    B.build()
+    from paper_2601_03031_gb300 import _lib as F
+    d = F.default_engine_limits()
+    assert d["miller_block_max"] == 1024 and d["fe_block_max"] == 256 and d["msm_chunks"] == 1 << 17
+    try:
+        F.set_engine_limits({"fe_block_max": 0, "fold_warp_max": 7})
+        cur = F.engine_limits()
+        assert cur["fe_block_max"] == 0 and cur["fold_warp_max"] == 7 and cur["miller_block_max"] == 1024
+        with pytest.raises(F.FlexProofsError):
+            F.set_engine_limits({"msm_chunks": 0})
+        with pytest.raises(ValueError):
+            F.set_engine_limits({"no_such_limit": 1})
+        F.set_engine_limits(None)
+        assert F.engine_limits() == d
+        assert F.get_schedule() == "direct"
+        F.set_schedule("lookahead")
+        assert F.get_schedule() == "lookahead"
+        assert F.load().fp_set_schedule(7) == 1
+    finally:
+        F.set_engine_limits(None)
+        F.set_schedule("direct")
