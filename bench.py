@@ -37,6 +37,10 @@ FQ_MULS = {
     "g1_mul": 2000,          # GLV: 128 Jacobian doublings (7) + ~96 mixed additions (11)
     "g2_mul": 3300,          # GLS: 64 doublings + ~60 mixed additions over Fq2, 15-point table
     "msm_madd": 10,          # XYZZ mixed addition (8M + 2S), one per bucket entry
+    # one pair of a 4-pair multi-Miller loop: the 62 Fq12 squarings (36 Fq products each) are shared
+    # by the 4 pairs, so a pair costs 7135 - 3/4 x 62 x 36
+    "miller_loop_multi4": 7135 - 3 * 62 * 36 // 4,
+    "g2_msm_madd": 30,       # XYZZ mixed addition over Fq2 (8M + 2S), 3 Fq products per Fq2 product
 }
 
 
@@ -80,7 +84,7 @@ NCU_TRAFFIC = {
 }
 
 
-def step_units(log_n: int, b: int, msm_window: int) -> dict:
+def step_units(log_n: int, b: int, msm_window: int, msm_window_g2: int = 16) -> dict:
     """Per kernel: (unit, units processed per step) for one Commit + OpenAll step."""
     lr = log_n // 2
     lc = log_n - lr
@@ -88,12 +92,14 @@ def step_units(log_n: int, b: int, msm_window: int) -> dict:
     K = (R + b - 1) // b
     hs = [R >> j for j in range(1, lr + 1)]
     W = -(-129 // msm_window)
+    W2 = -(-65 // msm_window_g2)
+    w_msm = K * R * 2 > 4096 and K >= 8         # the W proofs by one batched G2 MSM
     return {
         "k_final_exp_c": ("final_exp", 1 + (2 * K * lr if 2 * K <= 256 else 0)),
         "k_final_exp_w": ("final_exp", 2 * K * lr if 2 * K > 256 else 0),
         "k_round_miller_c": ("miller_loop", sum(K * 2 * h for h in hs if K * 2 * h <= 1024)),
         "k_round_miller_w": ("miller_loop", sum(K * 2 * h for h in hs if 1024 < K * 2 * h < 16384)),
-        "k_step1_miller_multi": ("miller_loop", sum(K * 2 * h for h in hs if K * 2 * h >= 1 << 18 and h >= 4)),
+        "k_step1_miller_multi": ("miller_loop_multi4", sum(K * 2 * h for h in hs if K * 2 * h >= 1 << 18 and h >= 4)),
         "k_step1_miller": ("miller_loop", sum(K * 2 * h for h in hs
                                               if K * 2 * h >= 16384 and not (K * 2 * h >= 1 << 18 and h >= 4))),
         "k_commit_miller_c": ("miller_loop", R if R <= 1024 else 0),
@@ -103,7 +109,9 @@ def step_units(log_n: int, b: int, msm_window: int) -> dict:
         "k_fold_w": (("g1_mul", "g2_mul"), sum(K * h for h in hs if FOLD_SPLIT_MAX < K * h <= 4096)),
         "k_fold": (("g1_mul", "g2_mul"), sum(K * h for h in hs if K * h > 4096)),
         "k_msm_chunk": ("msm_madd", 2 * R * M * W),
-        "k_w_terms": ("g2_mul", K * (2 * R - 2)),
+        "k_msm_chunk_g2": ("g2_msm_madd", 4 * 2 * R * K * W2 if w_msm else 0),
+        "k_w_terms": ("g2_mul", K * (2 * R - 2) if not w_msm and K * 2 * R > 4096 else 0),
+        "k_w_terms_w": ("g2_mul", K * (2 * R - 2) if not w_msm and K * 2 * R <= 4096 else 0),
         "k_pst_terms": ("g1_mul", M * lc // 2),
     }
 
@@ -885,28 +893,41 @@ def main():
             dist.destroy_process_group()
         return
 
-    # roofline of the dominant kernel (integer multiply-add pipe)
+    # roofline of the dominant kernel (integer multiply-add pipe), and of every kernel with a unit count
     peak = F.imad_peak()
-    units = step_units(log_n, b, F.msm_window(pp.M, pp.R))
-    dom = max(prof.items(), key=lambda kv: kv[1][1]) if prof else ("", (0, 0.0))
-    name, (cnt, kms) = dom
-    roof = None
-    if name in units and kms > 0 and units[name][1] > 0:
-        unit, n_units = units[name]
+    units = step_units(log_n, b, F.msm_window(pp.M, pp.R), F.msm_window_g2(2 * pp.R, -(-pp.R // b)))
+
+    def kernel_roof(kname, cnt, kms):
+        if kname not in units or kms <= 0 or units[kname][1] <= 0:
+            return None
+        unit, n_units = units[kname]
         per_unit = sum(FQ_MULS[u] for u in (unit if isinstance(unit, tuple) else (unit,)))
         ops_step = n_units * per_unit * FQ_MUL_IMAD
         launches_per_step = cnt / args.steps
         avg_ms = kms / cnt
-        ops_launch = ops_step / launches_per_step
-        achieved = ops_launch / (avg_ms * 1e-3)
-        roof = {"bound": "alu", "kernel": name, "achieved": achieved / 1e12, "peak": peak / 1e12,
-                "unit": "Tops/s (32-bit multiply-add lane ops)", "frac": achieved / peak,
+        achieved = ops_step / launches_per_step / (avg_ms * 1e-3)
+        return {"achieved": achieved / 1e12, "frac": achieved / peak, "units_per_step": n_units, "unit_op": unit,
+                "launches_per_step": launches_per_step, "avg_launch_ms": avg_ms}
+
+    dom = max(prof.items(), key=lambda kv: kv[1][1]) if prof else ("", (0, 0.0))
+    name, (cnt, kms) = dom
+    roof = None
+    r = kernel_roof(name, cnt, kms)
+    if r:
+        roof = {"bound": "alu", "kernel": name, "achieved": r["achieved"], "peak": peak / 1e12,
+                "unit": "Tops/s (32-bit multiply-add lane ops)", "frac": r["frac"],
                 "traffic": NCU_TRAFFIC.get((log_n, b, name)),
                 "traffic_source": "ncu dram__bytes_read.sum + dram__bytes_write.sum, one capture of this kernel"
                                   if (log_n, b, name) in NCU_TRAFFIC else None,
-                "units_per_step": n_units, "unit_op": unit, "launches_per_step": launches_per_step,
-                "avg_launch_ms": avg_ms,
+                "units_per_step": r["units_per_step"], "unit_op": r["unit_op"],
+                "launches_per_step": r["launches_per_step"], "avg_launch_ms": r["avg_launch_ms"],
                 "peak_source": "measured: fp_imad_probe on this GPU in this run"}
+    roof_all = {}
+    for kname, (kc, kt) in prof.items():
+        r = kernel_roof(kname, kc, kt)
+        if r:
+            roof_all[kname] = {"frac": round(r["frac"], 4), "avg_launch_ms": round(r["avg_launch_ms"], 4),
+                               "units_per_step": r["units_per_step"], "unit_op": r["unit_op"]}
     lat = None
     if name in CRITICAL_ROUNDS and kms > 0:
         t_ns = F.fq_mul_latency_ns()
@@ -963,6 +984,7 @@ def main():
                    "note": "value counts Commit + OpenAll per step; OpenAll alone is the paper's ProveAll time"},
         "gpu_launches": launches,
         "roofline": roof,
+        "roofline_kernels": roof_all,
         "latency_roofline": lat,
         "kernel_share": share,
         "clocks": clk.summary(),

@@ -286,6 +286,10 @@ fp_status fp_msm_g1(const fp_g1_bases* P, const uint64_t* k, uint64_t n, uint32_
  * that shape, else a cost model (per-phase throughput and per-thread latency of the field
  * products). */
 int fp_msm_window(uint64_t n, uint32_t nbatch);
+/* Window of the G2 MSM that forms the v_l proofs W of many blocks (OpenAll Step 1, "Faster
+ * verification" of Sec. 3): nbatch sums of n terms, each scalar in four 64-bit GLS parts; the cost
+ * model's choice (the launch-name suffix of its kernels is _g2). */
+int fp_msm_window_g2(uint64_t n, uint32_t nbatch);
 /* Times fp_msm_g1 on `stream` for windows around the model's choice with the given device
  * scalars (n * nbatch), keeps the fastest for (n, nbatch), and returns it (and its time in ms if
  * best_ms != NULL).  Synchronises. */

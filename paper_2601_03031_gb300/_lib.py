@@ -24,7 +24,7 @@ EXPORTED = ["vc_setup", "vc_pp_export", "vc_pp_dims", "vc_commit", "vc_commit_ge
             "vc_pp_view_split", "vc_open_segments", "vc_segment_proof_len", "vc_segment_proof_get",
             "vc_verify_segment", "vc_eval_proof_len", "vc_eval_prove", "vc_eval_verify", "fp_set_schedule",
             "fp_get_schedule", "fp_batch_last_times", "fp_engine_limits_default", "fp_set_engine_limits",
-            "fp_get_engine_limits"]
+            "fp_get_engine_limits", "fp_msm_window_g2"]
 
 LIMIT_FIELDS = ["miller_block_max", "miller_warp_max", "miller_group_min", "commit_block_max", "commit_warp_max",
                 "fe_block_max", "fe_warp_max", "pair_block_max", "fold_warp_max", "wterm_warp_max", "msm_chunks",
@@ -112,6 +112,8 @@ def load(path: str = LIB_PATH):
     L.fp_msm_g1.argtypes = [vp, vp, u64, u32, ctypes.c_int, ctypes.c_int, vp, vp]
     L.fp_msm_window.argtypes = [u64, u32]
     L.fp_msm_window.restype = ctypes.c_int
+    L.fp_msm_window_g2.argtypes = [u64, u32]
+    L.fp_msm_window_g2.restype = ctypes.c_int
     L.fp_msm_autotune.argtypes = [vp, vp, u64, u32, vp, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_double)]
     L.fp_set_schedule.argtypes = [ctypes.c_int]
     L.fp_get_schedule.restype = ctypes.c_int
@@ -549,6 +551,10 @@ def msm_g1(bases: G1Bases, k, nbatch: int = 1, window: int = 0, stream=None, out
 
 def msm_window(n: int, nbatch: int = 1) -> int:
     return int(load().fp_msm_window(n, nbatch))
+
+
+def msm_window_g2(n: int, nbatch: int = 1) -> int:
+    return int(load().fp_msm_window_g2(n, nbatch))
 
 
 def msm_autotune(bases: G1Bases, k_dev, nbatch: int = 1, stream=None):

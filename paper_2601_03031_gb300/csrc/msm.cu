@@ -532,6 +532,7 @@ template <typename F>
 static void msm_run(const void* bases, const void* k_canon, const MsmShape& sh, void* scratch, void* out_aff,
                     void* ser_out, size_t ser_stride, cudaStream_t s) {
     using X = xyzz_t<F>;
+    constexpr bool g2 = std::is_same<F, fq2>::value;     // launch names: G2 launches end in _g2
     const uint64_t nk = sh.nkeys(), nseg = sh.nsegs(), nwin = (uint64_t)sh.nbatch * sh.W;
     uint8_t* p = (uint8_t*)scratch;
     auto take = [&](size_t bytes) {
@@ -556,33 +557,33 @@ static void msm_run(const void* bases, const void* k_canon, const MsmShape& sh, 
     const uint64_t terms = sh.n * sh.nbatch;
     cudaMemsetAsync(counts, 0, nk * 4, s);
     if (terms) {
-        FP_KERNEL("k_msm_count", s,
+        FP_KERNEL(g2 ? "k_msm_count_g2" : "k_msm_count", s,
                   k_msm_count<F><<<grid_for(terms, 128), 128, 0, s>>>((const fr*)k_canon, sh, counts));
     }
     exclusive_scan(counts, offsets, nk, scan_tmp, s);
     cudaMemcpyAsync(cursor, offsets, nk * 4, cudaMemcpyDeviceToDevice, s);
     if (terms) {
-        FP_KERNEL("k_msm_scatter", s,
+        FP_KERNEL(g2 ? "k_msm_scatter_g2" : "k_msm_scatter", s,
                   k_msm_scatter<F><<<grid_for(terms, 128), 128, 0, s>>>((const fr*)k_canon, sh, cursor, list, keys));
     }
     cudaMemsetAsync(buckets, 0, nk * sizeof(X), s);
     if (nchunks) {                                   // no terms: every bucket stays the identity
-        FP_KERNEL("k_msm_chunk", s,
+        FP_KERNEL(g2 ? "k_msm_chunk_g2" : "k_msm_chunk", s,
                   k_msm_chunk<F><<<grid_for(nchunks, 128), 128, 0, s>>>((const typename Aff<F>::T*)bases, list, keys,
                                                                        offsets, counts, nk, T, buckets, head, tail));
-        FP_KERNEL("k_msm_fixup", s,
+        FP_KERNEL(g2 ? "k_msm_fixup_g2" : "k_msm_fixup", s,
                   k_msm_fixup<F><<<grid_for(nchunks, 128), 128, 0, s>>>(keys, offsets, counts, nk, T, head, tail,
                                                                        buckets));
     }
-    FP_KERNEL("k_msm_segment", s, k_msm_segment<F><<<grid_for(nseg, 128), 128, 0, s>>>(sh, buckets, seg_a));
+    FP_KERNEL(g2 ? "k_msm_segment_g2" : "k_msm_segment", s, k_msm_segment<F><<<grid_for(nseg, 128), 128, 0, s>>>(sh, buckets, seg_a));
     X* a = seg_a;
     X* b = seg_b;
     for (uint64_t m = nseg; m > nwin; m /= 2) {
-        FP_KERNEL("k_msm_pair", s, k_msm_pair<F><<<grid_for(m / 2, 128), 128, 0, s>>>(a, b, m / 2));
+        FP_KERNEL(g2 ? "k_msm_pair_g2" : "k_msm_pair", s, k_msm_pair<F><<<grid_for(m / 2, 128), 128, 0, s>>>(a, b, m / 2));
         std::swap(a, b);
     }
-    FP_KERNEL("k_msm_to_proj", s, k_msm_to_proj<F><<<grid_for(nwin, 128), 128, 0, s>>>(a, proj, nwin));
-    FP_KERNEL("k_msm_final", s,
+    FP_KERNEL(g2 ? "k_msm_to_proj_g2" : "k_msm_to_proj", s, k_msm_to_proj<F><<<grid_for(nwin, 128), 128, 0, s>>>(a, proj, nwin));
+    FP_KERNEL(g2 ? "k_msm_final_g2" : "k_msm_final", s,
               k_msm_final<F><<<grid_for(sh.nbatch, 8), 64, 0, s>>>(sh, proj, (typename Aff<F>::T*)out_aff,
                                                                   (uint8_t*)ser_out, ser_stride));
 }

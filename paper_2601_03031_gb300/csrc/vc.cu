@@ -474,7 +474,7 @@ Step1Bufs step1_bufs(const fp_pp* pp, uint32_t Kc, Alloc&& T) {
     // reduction runs nearly serially per window)
     B.w_msm = KR * 2 > 4096 && Kc >= 8;
     if (B.w_msm) {
-        B.wsh = msm_shape(2 * R, Kc, 2 * R, msm_window_model(2 * R, Kc, 4, 65, 3.0), 4, 65);
+        B.wsh = msm_shape(2 * R, Kc, 2 * R, fp_msm_window_g2(2 * R, Kc), 4, 65);
         B.wscr = T(msm_scratch_bytes_g2(B.wsh));
     } else {
         B.wt = T((size_t)Kc * 2 * R * G2J_BYTES);
@@ -1459,6 +1459,8 @@ void msm_enqueue(const fp_g1_bases* P, const void* k_dev, const MsmShape& sh, vo
 }  // namespace
 
 extern "C" {
+
+int fp_msm_window_g2(uint64_t n, uint32_t nbatch) { return msm_window_model(n, nbatch, 4, 65, 3.0); }
 
 int fp_msm_window(uint64_t n, uint32_t nbatch) {
     const int t = tuned_window(n, nbatch);
