@@ -229,6 +229,16 @@ FPG_DEV fq fq_sqr(const fq& a) { return fq_mul(a, a); }
 FPG_DEV fq fq_add(const fq& a, const fq& b) { fq r; mp::mod_add<12>(r.v, a.v, b.v, FQ_P); return r; }
 FPG_DEV fq fq_sub(const fq& a, const fq& b) { fq r; mp::mod_sub<12>(r.v, a.v, b.v, FQ_P); return r; }
 FPG_DEV fq fq_dbl(const fq& a) { return fq_add(a, a); }
+// c ? a : b by per-limb masks.  The lane-parallel engines form every operand this way: lanes of one
+// warp that chose between whole field elements by a branch would take divergent paths, which the
+// warp runs one after another.
+FPG_DEV fq fq_select(bool c, const fq& a, const fq& b) {
+    const uint32_t m = 0u - (uint32_t)c;
+    fq r;
+#pragma unroll
+    for (int j = 0; j < 12; j++) r.v[j] = (a.v[j] & m) | (b.v[j] & ~m);
+    return r;
+}
 FPG_DEV fq fq_neg(const fq& a) { fq z; fq_zero(z); return fq_sub(z, a); }
 FPG_DEV bool fq_is_zero(const fq& a) { return mp::is_zero<12>(a.v); }
 FPG_DEV bool fq_eq(const fq& a, const fq& b) { return mp::eq<12>(a.v, b.v); }

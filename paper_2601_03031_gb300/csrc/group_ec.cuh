@@ -25,6 +25,29 @@ static __device__ __noinline__ fq2 e_sub(fq2 a, fq2 b) { return fq2_sub(a, b); }
 static __device__ __noinline__ fq2 e_dbl(fq2 a) { return fq2_dbl(a); }
 
 template <typename F> struct GPt { F X, Y, Z; };
+
+FPG_DEV fq f_sel(bool c, const fq& a, const fq& b) { return fq_select(c, a, b); }
+FPG_DEV fq2 f_sel(bool c, const fq2& a, const fq2& b) { return fq2_select(c, a, b); }
+// coordinate i (0: X, 1: Y, 2: Z) of P, without a per-lane branch
+template <typename F>
+FPG_DEV F gec_coord(const GPt<F>& P, int i) { return f_sel(i == 0, P.X, f_sel(i == 1, P.Y, P.Z)); }
+// the first phase of an addition: lanes 0..2 multiply coordinate q of P and Q, lanes 3..5 the sums
+// (X + Y), (Y + Z), (X + Z); every lane forms its operands with the same instructions
+template <typename F>
+FPG_DEV void gec_add_ops(int q, const GPt<F>& P, const GPt<F>& Q, F& a, F& b) {
+    const int i1 = q < 3 ? q : (q == 4 ? 1 : 0), i2 = q == 3 ? 1 : 2;
+    const F pa = gec_coord(P, i1), qa = gec_coord(Q, i1);
+    const F ps = e_add(pa, gec_coord(P, i2)), qs = e_add(qa, gec_coord(Q, i2));
+    a = f_sel(q >= 3, ps, pa);
+    b = f_sel(q >= 3, qs, qa);
+}
+// the second phase of an addition: (t4 y3), (t3 u1), (y3 x3), (u1 z3), (x3 t3), (z3 t4)
+template <typename F>
+FPG_DEV void gec_add_ops2(int q, const F& t3, const F& t4, const F& x3, const F& y3, const F& z3, const F& u1, F& a,
+                          F& b) {
+    a = f_sel(q == 0, t4, f_sel(q == 1, t3, f_sel(q == 2, y3, f_sel(q == 3, u1, f_sel(q == 4, x3, z3)))));
+    b = f_sel(q == 0, y3, f_sel(q == 1, u1, f_sel(q == 2, x3, f_sel(q == 3, z3, f_sel(q == 4, t3, t4)))));
+}
 template <typename F> struct GEc {
     F sc[8];          // products of the current phase
     GPt<F> tab[16];   // subset sums of the split bases
@@ -59,14 +82,7 @@ FPG_DEV GPt<F> gec_identity() {
 template <typename F>
 FPG_NOINL GPt<F> gec_add(GEc<F>& sm, int lane, const GPt<F>& P, const GPt<F>& Q) {
     F a, b;
-    switch (lane) {
-        case 0: a = P.X; b = Q.X; break;
-        case 1: a = P.Y; b = Q.Y; break;
-        case 2: a = P.Z; b = Q.Z; break;
-        case 3: a = e_add(P.X, P.Y); b = e_add(Q.X, Q.Y); break;
-        case 4: a = e_add(P.Y, P.Z); b = e_add(Q.Y, Q.Z); break;
-        default: a = e_add(P.X, P.Z); b = e_add(Q.X, Q.Z); break;
-    }
+    gec_add_ops(lane < 6 ? lane : 5, P, Q, a, b);
     gec_phase(sm, lane, a, b);
     const F t0 = sm.sc[0], t1 = sm.sc[1], t2 = sm.sc[2];
     const F t3 = e_sub(sm.sc[3], e_add(t0, t1));
@@ -76,14 +92,7 @@ FPG_NOINL GPt<F> gec_add(GEc<F>& sm, int lane, const GPt<F>& P, const GPt<F>& Q)
     const F bt2 = f_b3(t2);
     const F z3 = e_add(t1, bt2);
     const F u1 = e_sub(t1, bt2);
-    switch (lane) {
-        case 0: a = t4; b = y3; break;
-        case 1: a = t3; b = u1; break;
-        case 2: a = y3; b = x3; break;
-        case 3: a = u1; b = z3; break;
-        case 4: a = x3; b = t3; break;
-        default: a = z3; b = t4; break;
-    }
+    gec_add_ops2(lane < 6 ? lane : 5, t3, t4, x3, y3, z3, u1, a, b);
     gec_phase(sm, lane, a, b);
     GPt<F> r;
     r.X = e_sub(sm.sc[1], sm.sc[0]);
@@ -95,25 +104,18 @@ FPG_NOINL GPt<F> gec_add(GEc<F>& sm, int lane, const GPt<F>& P, const GPt<F>& Q)
 // 2P, complete (RCB16 Algorithm 9, a = 0)
 template <typename F>
 FPG_NOINL GPt<F> gec_dbl(GEc<F>& sm, int lane, const GPt<F>& P) {
-    F a, b;
-    switch (lane) {
-        case 0: a = P.Y; b = P.Y; break;
-        case 1: a = P.Y; b = P.Z; break;
-        case 2: a = P.Z; b = P.Z; break;
-        default: a = P.X; b = P.Y; break;
-    }
+    // lanes: 0 Y Y, 1 Y Z, 2 Z Z, 3 X Y
+    F a = f_sel(lane >= 3, P.X, f_sel(lane == 2, P.Z, P.Y));
+    F b = f_sel(lane == 0, P.Y, f_sel(lane >= 3, P.Y, P.Z));
     gec_phase(sm, lane, a, b);
     const F t0 = sm.sc[0], t1 = sm.sc[1], xy = sm.sc[3];
     const F z8 = e_dbl(e_dbl(e_dbl(t0)));
     const F bt2 = f_b3(sm.sc[2]);
     const F y3a = e_add(t0, bt2);
     const F t0p = e_sub(t0, e_add(e_dbl(bt2), bt2));
-    switch (lane) {
-        case 0: a = bt2; b = z8; break;
-        case 1: a = t1; b = z8; break;
-        case 2: a = t0p; b = y3a; break;
-        default: a = t0p; b = xy; break;
-    }
+    // lanes: 0 bt2 z8, 1 t1 z8, 2 t0p y3a, 3 t0p xy
+    a = f_sel(lane == 0, bt2, f_sel(lane == 1, t1, t0p));
+    b = f_sel(lane < 2, z8, f_sel(lane == 2, y3a, xy));
     gec_phase(sm, lane, a, b);
     GPt<F> r;
     r.X = e_dbl(sm.sc[3]);
@@ -165,15 +167,15 @@ FPG_DEV void gecw_phase(GEcW& sm, int L, Sel&& sel) {
         sel(q, a, b);
         fq zero;
         fq_zero(zero);
-        const fq x = fq_add(kind == 1 ? a.c1 : a.c0, kind == 2 ? a.c1 : zero);
-        const fq y = fq_add(kind == 1 ? b.c1 : b.c0, kind == 2 ? b.c1 : zero);
+        const fq x = fq_add(fq_select(kind == 1, a.c1, a.c0), fq_select(kind == 2, a.c1, zero));
+        const fq y = fq_add(fq_select(kind == 1, b.c1, b.c0), fq_select(kind == 2, b.c1, zero));
         sm.p[L] = fq_mul(x, y);
     }
     __syncwarp();
     fq r;
     if (L < 12) {
         const fq* m = &sm.p[3 * (L >> 1)];
-        r = (L & 1) ? fq_sub(m[2], fq_add(m[0], m[1])) : fq_sub(m[0], m[1]);
+        r = fq_select(L & 1, fq_sub(m[2], fq_add(m[0], m[1])), fq_sub(m[0], m[1]));
     }
     __syncwarp();
     if (L < 12) {
@@ -185,16 +187,7 @@ FPG_DEV void gecw_phase(GEcW& sm, int L, Sel&& sel) {
 
 // P + Q, complete (RCB16 Algorithm 7, a = 0), on one warp
 FPG_NOINL GPt<fq2> gecw_add(GEcW& sm, int L, const GPt<fq2>& P, const GPt<fq2>& Q) {
-    gecw_phase(sm, L, [&](int q, fq2& a, fq2& b) {
-        switch (q) {
-            case 0: a = P.X; b = Q.X; break;
-            case 1: a = P.Y; b = Q.Y; break;
-            case 2: a = P.Z; b = Q.Z; break;
-            case 3: a = e_add(P.X, P.Y); b = e_add(Q.X, Q.Y); break;
-            case 4: a = e_add(P.Y, P.Z); b = e_add(Q.Y, Q.Z); break;
-            default: a = e_add(P.X, P.Z); b = e_add(Q.X, Q.Z); break;
-        }
-    });
+    gecw_phase(sm, L, [&](int q, fq2& a, fq2& b) { gec_add_ops(q, P, Q, a, b); });
     const fq2 t0 = sm.sc[0], t1 = sm.sc[1], t2 = sm.sc[2];
     const fq2 t3 = e_sub(sm.sc[3], e_add(t0, t1));
     const fq2 t4 = e_sub(sm.sc[4], e_add(t1, t2));
@@ -203,16 +196,7 @@ FPG_NOINL GPt<fq2> gecw_add(GEcW& sm, int L, const GPt<fq2>& P, const GPt<fq2>& 
     const fq2 bt2 = f_b3(t2);
     const fq2 z3 = e_add(t1, bt2);
     const fq2 u1 = e_sub(t1, bt2);
-    gecw_phase(sm, L, [&](int q, fq2& a, fq2& b) {
-        switch (q) {
-            case 0: a = t4; b = y3; break;
-            case 1: a = t3; b = u1; break;
-            case 2: a = y3; b = x3; break;
-            case 3: a = u1; b = z3; break;
-            case 4: a = x3; b = t3; break;
-            default: a = z3; b = t4; break;
-        }
-    });
+    gecw_phase(sm, L, [&](int q, fq2& a, fq2& b) { gec_add_ops2(q, t3, t4, x3, y3, z3, u1, a, b); });
     GPt<fq2> r;
     r.X = e_sub(sm.sc[1], sm.sc[0]);
     r.Y = e_add(sm.sc[3], sm.sc[2]);
@@ -223,12 +207,8 @@ FPG_NOINL GPt<fq2> gecw_add(GEcW& sm, int L, const GPt<fq2>& P, const GPt<fq2>& 
 // 2P, complete (RCB16 Algorithm 9, a = 0), on one warp
 FPG_NOINL GPt<fq2> gecw_dbl(GEcW& sm, int L, const GPt<fq2>& P) {
     gecw_phase(sm, L, [&](int q, fq2& a, fq2& b) {
-        switch (q) {
-            case 0: a = P.Y; b = P.Y; break;
-            case 1: a = P.Y; b = P.Z; break;
-            case 2: a = P.Z; b = P.Z; break;
-            default: a = P.X; b = P.Y; break;
-        }
+        a = fq2_select(q >= 3, P.X, fq2_select(q == 2, P.Z, P.Y));
+        b = fq2_select(q == 0, P.Y, fq2_select(q >= 3, P.Y, P.Z));
     });
     const fq2 t0 = sm.sc[0], t1 = sm.sc[1], xy = sm.sc[3];
     const fq2 z8 = e_dbl(e_dbl(e_dbl(t0)));
@@ -236,12 +216,8 @@ FPG_NOINL GPt<fq2> gecw_dbl(GEcW& sm, int L, const GPt<fq2>& P) {
     const fq2 y3a = e_add(t0, bt2);
     const fq2 t0p = e_sub(t0, e_add(e_dbl(bt2), bt2));
     gecw_phase(sm, L, [&](int q, fq2& a, fq2& b) {
-        switch (q) {
-            case 0: a = bt2; b = z8; break;
-            case 1: a = t1; b = z8; break;
-            case 2: a = t0p; b = y3a; break;
-            default: a = t0p; b = xy; break;
-        }
+        a = fq2_select(q == 0, bt2, fq2_select(q == 1, t1, t0p));
+        b = fq2_select(q < 2, z8, fq2_select(q == 2, y3a, xy));
     });
     GPt<fq2> r;
     r.X = e_dbl(sm.sc[3]);

@@ -13,6 +13,7 @@ struct fq6 { fq2 c0, c1, c2; };
 struct fq12 { fq6 c0, c1; };
 
 // ------------------------------------------------------------------------------ Fq2
+FPG_DEV fq2 fq2_select(bool c, const fq2& a, const fq2& b) { return {fq_select(c, a.c0, b.c0), fq_select(c, a.c1, b.c1)}; }
 FPG_DEV fq2 fq2_add(const fq2& a, const fq2& b) { return {fq_add(a.c0, b.c0), fq_add(a.c1, b.c1)}; }
 FPG_DEV fq2 fq2_sub(const fq2& a, const fq2& b) { return {fq_sub(a.c0, b.c0), fq_sub(a.c1, b.c1)}; }
 FPG_DEV fq2 fq2_dbl(const fq2& a) { return {fq_dbl(a.c0), fq_dbl(a.c1)}; }

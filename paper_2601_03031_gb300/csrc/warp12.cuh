@@ -35,12 +35,7 @@ FPG_DEV int w_lane() { return (int)(threadIdx.x & (32 * NW - 1)); }
 // tower position of flat coefficient k (0..5): even k -> c0.c(k/2), odd k -> c1.c(k/2)
 FPG_DEV int w_tower_pos(int k) { return (k & 1) ? 3 + (k >> 1) : (k >> 1); }
 
-FPG_DEV fq fq_select(bool c, const fq& a, const fq& b) {
-    fq r;
-#pragma unroll
-    for (int j = 0; j < 12; j++) r.v[j] = c ? a.v[j] : b.v[j];
-    return r;
-}
+
 
 // dst (flat) <- f (tower order: six consecutive Fq2, each (c0, c1))
 template <int NW>
@@ -66,8 +61,8 @@ FPG_NOINL void w_mul(W12& W, fq* out, const fq* a, const fq* b) {
     for (int t = L; t < 108; t += 32 * NW) {
         const int q = t / 3, kind = t - 3 * q, i = q / 6, j = q - 6 * i;
         // kind 0: a_i.0 b_j.0, kind 1: a_i.1 b_j.1, kind 2: (a_i.0 + a_i.1)(b_j.0 + b_j.1)
-        const fq x = fq_add(a[2 * i + (kind == 1)], kind == 2 ? a[2 * i + 1] : zero);
-        const fq y = fq_add(b[2 * j + (kind == 1)], kind == 2 ? b[2 * j + 1] : zero);
+        const fq x = fq_add(a[2 * i + (kind == 1)], fq_select(kind == 2, a[2 * i + 1], zero));
+        const fq y = fq_add(b[2 * j + (kind == 1)], fq_select(kind == 2, b[2 * j + 1], zero));
         W.p[t] = fq_mul(x, y);
     }
     wsync<NW>();
@@ -84,7 +79,7 @@ FPG_NOINL void w_mul(W12& W, fq* out, const fq* a, const fq* b) {
             const fq re = fq_sub(m[0], m[1]);
             const fq im = fq_sub(m[2], m01);
             // (re + im u)(1 + u) = (re - im) + (re + im) u
-            const fq x = fq_select(wrap, fq_select(e, fq_add(re, im), fq_sub(re, im)), e ? im : re);
+            const fq x = fq_select(wrap, fq_select(e, fq_add(re, im), fq_sub(re, im)), fq_select(e, im, re));
             acc = fq_add(acc, x);
         }
         W.h[L] = acc;
@@ -102,21 +97,22 @@ FPG_NOINL void w_mul(W12& W, fq* out, const fq* a, const fq* b) {
 // t1 = (b0 + b1)(b0 - b1), t2 = b0 b1, k0 = a0 b0, k1 = a1 b1, k2 = (a0 + a1)(b0 + b1); then
 // a^2 = s1 + 2 s2 u, b^2 = t1 + 2 t2 u, a b = (k0 - k1) + (k2 - k0 - k1) u.
 template <int NW>
-FPG_NOINL void w_cyc_sqr(W12& W, fq* out, const fq* z) {
+FPG_DEV void w_cyc_sqr(W12& W, fq* out, const fq* z) {
     const int L = w_lane<NW>();
     if (L < 21) {
         const int p = L / 7, r = L - 7 * p;
         const fq a0 = z[2 * p], a1 = z[2 * p + 1], b0 = z[2 * p + 6], b1 = z[2 * p + 7];
         const bool ua = r < 2 || r == 4 || r == 5 || r == 6;            // x built from a
-        const fq xs = ua ? a0 : b0, xt = ua ? a1 : b1;
+        const fq xs = fq_select(ua, a0, b0), xt = fq_select(ua, a1, b1);
         // x: r in {0, 2, 6}: xs + xt; r in {1, 3, 4}: xs; r == 5: a1
         const fq xsum = fq_add(xs, xt);
-        fq x = (r == 0 || r == 2 || r == 6) ? xsum : (r == 5 ? a1 : xs);
+        const fq x = fq_select(r == 0 || r == 2 || r == 6, xsum, fq_select(r == 5, a1, xs));
         // y: r == 0: a0 - a1; r == 1: a1; r == 2: b0 - b1; r == 3: b1; r == 4: b0; r == 5: b1;
         //    r == 6: b0 + b1
-        const fq ys = (r < 2) ? a0 : b0, yt = (r < 2) ? a1 : b1;
+        const fq ys = fq_select(r < 2, a0, b0), yt = fq_select(r < 2, a1, b1);
         const fq ydiff = fq_sub(ys, yt), ysum = fq_add(ys, yt);
-        fq y = (r == 0 || r == 2) ? ydiff : (r == 6 ? ysum : (r == 4 ? b0 : (r == 1 ? a1 : b1)));
+        const fq y = fq_select(r == 0 || r == 2, ydiff,
+                               fq_select(r == 6, ysum, fq_select(r == 4, b0, fq_select(r == 1, a1, b1))));
         W.p[L] = fq_mul(x, y);
     }
     wsync<NW>();
@@ -140,11 +136,11 @@ FPG_NOINL void w_cyc_sqr(W12& W, fq* out, const fq* z) {
             } else if (w == 2) {
                 o = pl == 2 ? 2 : 6 + 4 * pl;
                 const fq k0 = m[4];
-                const fq u = pl == 2 ? fq_dbl(k0) : k0;
-                V = fq_dbl(fq_sub(u, pl == 2 ? m[6] : m[5]));
+                const fq u = fq_select(pl == 2, fq_dbl(k0), k0);
+                V = fq_dbl(fq_sub(u, fq_select(pl == 2, m[6], m[5])));
             } else {
                 o = pl == 2 ? 3 : 7 + 4 * pl;
-                const fq y = pl == 2 ? fq_dbl(m[5]) : fq_add(m[4], m[5]);
+                const fq y = fq_select(pl == 2, fq_dbl(m[5]), fq_add(m[4], m[5]));
                 V = fq_dbl(fq_sub(m[6], y));
             }
             const fq V3 = fq_add(fq_dbl(V), V);
@@ -165,13 +161,12 @@ FPG_NOINL void w_cyc_sqr(W12& W, fq* out, const fq* z) {
         const fq Aim = fq_add(fq_add(fq_dbl(s2), t1), t2d);
         const fq Bre = fq_dbl(fq_sub(k0, k1));
         const fq Bim = fq_dbl(fq_sub(k2, fq_add(k0, k1)));
-        fq V;
-        if (kind == 0) V = e ? Aim : Are;
-        else if (kind == 1) V = e ? Bim : Bre;
-        else V = e ? fq_add(Bre, Bim) : fq_sub(Bre, Bim);
+        const fq V = fq_select(kind == 0, fq_select(e, Aim, Are),
+                               fq_select(kind == 1, fq_select(e, Bim, Bre),
+                                         fq_select(e, fq_add(Bre, Bim), fq_sub(Bre, Bim))));
         const fq V3 = fq_add(fq_dbl(V), V);
         const fq z2 = fq_dbl(z[L]);
-        W.h[L] = kind == 0 ? fq_sub(V3, z2) : fq_add(V3, z2);
+        W.h[L] = fq_select(kind == 0, fq_sub(V3, z2), fq_add(V3, z2));
     }
     wsync<NW>();
     if (L < 12) out[L] = W.h[L];
@@ -185,7 +180,7 @@ FPG_DEV void w_conj(fq* out, const fq* a) {
     wsync<NW>();
     if (L < 12) {
         const fq v = a[L];
-        out[L] = ((L >> 1) & 1) ? fq_neg(v) : v;
+        out[L] = fq_select((L >> 1) & 1, fq_neg(v), v);
     }
     wsync<NW>();
 }
@@ -198,20 +193,16 @@ FPG_NOINL void w_frob(W12& W, fq* out, const fq* a) {
     if (L < 20) {
         const int k = 1 + (L >> 2), r = L & 3;
         const fq2 g = frob1_coef(k);
-        const fq x = (r == 0 || r == 2) ? a[2 * k] : a[2 * k + 1];
-        const fq y = (r == 0 || r == 3) ? g.c0 : g.c1;
+        const fq x = fq_select(r == 0 || r == 2, a[2 * k], a[2 * k + 1]);
+        const fq y = fq_select(r == 0 || r == 3, g.c0, g.c1);
         W.p[L] = fq_mul(x, y);
     }
     wsync<NW>();
     if (L < 12) {
         const int k = L >> 1, e = L & 1;
-        fq v;
-        if (k == 0) v = e ? fq_neg(a[1]) : a[0];
-        else {
-            const fq* m = &W.p[4 * (k - 1)];
-            v = e ? fq_sub(m[2], m[3]) : fq_add(m[0], m[1]);
-        }
-        W.h[L] = v;
+        const fq* m = &W.p[4 * (k ? k - 1 : 0)];
+        W.h[L] = fq_select(k == 0, fq_select(e, fq_neg(a[1]), a[0]),
+                           fq_select(e, fq_sub(m[2], m[3]), fq_add(m[0], m[1])));
     }
     wsync<NW>();
     if (L < 12) out[L] = W.h[L];
@@ -227,7 +218,7 @@ FPG_NOINL void w_frob2(W12& W, fq* out, const fq* a) {
         W.p[L] = fq_mul(a[2 * k + (L & 1)], frob2_coef(k));
     }
     wsync<NW>();
-    if (L < 12) W.h[L] = L < 2 ? a[L] : W.p[L - 2];
+    if (L < 12) W.h[L] = fq_select(L < 2, a[L < 2 ? L : 0], W.p[L < 2 ? 0 : L - 2]);
     wsync<NW>();
     if (L < 12) out[L] = W.h[L];
     wsync<NW>();
@@ -328,22 +319,41 @@ struct WMill {
     fq tm[72];      // per-term partial sums of the combines (block-wide engine)
 };
 
+// Operands x, y of one Fq product, formed with the same instructions on every lane (the lanes of a
+// round do different products; a per-lane branch between formulas would run the formulas one after
+// another):
+//   mode 0: Karatsuba product of Fq2 values a, b: kind 0: a0 b0, 1: a1 b1, 2: (a0 + a1)(b0 + b1);
+//   mode 1: square of a: kind 0: (a0 + a1)(a0 - a1), 1: a0 a1 (b is not read past b[1]: pass a);
+//   mode 2: component kind of a times the Fq value s (b as for mode 1).
+FPG_DEV void prod_ops(fq& x, fq& y, const fq* a, const fq* b, int kind, int mode, const fq& s) {
+    fq zero;
+    fq_zero(zero);
+    const bool sq = mode == 1, plain = mode == 2;
+    const bool with1 = (mode == 0 && kind == 2) || (sq && kind == 0);      // the other component added in
+    x = fq_add(a[(mode != 1 && kind == 1) ? 1 : 0], fq_select(with1, a[1], zero));
+    const fq* yb = mode == 0 ? b : a;
+    const int iy = mode == 0 ? (kind == 1) : (sq ? kind : 0);
+    const fq t = fq_select(with1, yb[1], zero);
+    y = fq_select(plain, s, fq_select(sq && kind == 0, fq_sub(yb[iy], t), fq_add(yb[iy], t)));
+}
 FPG_DEV void kara_ops(fq& x, fq& y, const fq* a, const fq* b, int kind) {
     fq zero;
     fq_zero(zero);
-    x = fq_add(a[kind == 1], kind == 2 ? a[1] : zero);
-    y = fq_add(b[kind == 1], kind == 2 ? b[1] : zero);
+    x = fq_add(a[kind == 1], fq_select(kind == 2, a[1], zero));
+    y = fq_add(b[kind == 1], fq_select(kind == 2, b[1], zero));
 }
 FPG_DEV void sq_ops(fq& x, fq& y, const fq* a, int kind) {
-    x = kind ? a[0] : fq_add(a[0], a[1]);
-    y = kind ? a[1] : fq_sub(a[0], a[1]);
+    x = fq_select(kind, a[0], fq_add(a[0], a[1]));
+    y = fq_select(kind, a[1], fq_sub(a[0], a[1]));
 }
 // component e of a Karatsuba product / of a square, from its products m
-FPG_DEV fq kara_part(const fq* m, int e) { return e ? fq_sub(m[2], fq_add(m[0], m[1])) : fq_sub(m[0], m[1]); }
-FPG_DEV fq sq_part(const fq* m, int e) { return e ? fq_dbl(m[1]) : m[0]; }
+FPG_DEV fq kara_part(const fq* m, int e) {
+    return fq_select(e, fq_sub(m[2], fq_add(m[0], m[1])), fq_sub(m[0], m[1]));
+}
+FPG_DEV fq sq_part(const fq* m, int e) { return fq_select(e, fq_dbl(m[1]), m[0]); }
 // component e of (re + im u) times xi = 1 + u when tw
 FPG_DEV fq twist_part(const fq& re, const fq& im, int e, bool tw) {
-    return tw ? (e ? fq_add(re, im) : fq_sub(re, im)) : (e ? im : re);
+    return fq_select(tw, fq_select(e, fq_add(re, im), fq_sub(re, im)), fq_select(e, im, re));
 }
 FPG_DEV fq fq_mul_small(const fq& a, unsigned k) {          // k a for a small constant k
     fq acc;
@@ -386,20 +396,29 @@ FPG_NOINL void wm_dbl(WMill& S, const fq& m3x, const fq& y2) {
     const int L = w_lane<NW>();
     // round A
     for (int t = L; t < 69; t += 32 * NW) {
-        fq x, y;
-        if (t < 12) {
-            sq_ops(x, y, S.f + 2 * (t >> 1), t & 1);
-        } else if (t < 57) {
-            const int c = (t - 12) / 3, kind = t - 12 - 3 * c;
+        const fq* a;
+        const fq* b;
+        int kind, mode;
+        if (t < 12) {                                                            // f_k^2
+            a = b = S.f + 2 * (t >> 1);
+            kind = t & 1;
+            mode = 1;
+        } else if (t < 57) {                                                     // f_i f_j, i < j
+            const int c = (t - 12) / 3;
             int i = 0, rem = c;
             while (rem >= 5 - i) { rem -= 5 - i; i++; }
-            kara_ops(x, y, S.f + 2 * i, S.f + 2 * (i + 1 + rem), kind);
+            a = S.f + 2 * i;
+            b = S.f + 2 * (i + 1 + rem);
+            kind = t - 12 - 3 * c;
+            mode = 0;
         } else {
             const int u = t - 57;
-            if (u < 6) sq_ops(x, y, S.T + 2 * (u >> 1), u & 1);                 // X^2, Y^2, Z^2
-            else if (u < 9) kara_ops(x, y, S.T + 2, S.T + 4, u - 6);             // Y Z
-            else kara_ops(x, y, S.T, S.T + 2, u - 9);                            // X Y
+            if (u < 6) { a = b = S.T + 2 * (u >> 1); kind = u & 1; mode = 1; }  // X^2, Y^2, Z^2
+            else if (u < 9) { a = S.T + 2; b = S.T + 4; kind = u - 6; mode = 0; }  // Y Z
+            else { a = S.T; b = S.T + 2; kind = u - 9; mode = 0; }                 // X Y
         }
+        fq x, y;
+        prod_ops(x, y, a, b, kind, mode, m3x);
         S.p[t] = fq_mul(x, y);
     }
     wsync<NW>();
@@ -407,25 +426,21 @@ FPG_NOINL void wm_dbl(WMill& S, const fq& m3x, const fq& y2) {
         const int o = L % 12, i = L / 12, k = o >> 1, e = o & 1;
         int j = k - i;
         if (j < 0) j += 6;
-        fq v;
-        fq_zero(v);
-        if (i <= j) {
-            fq re, im;
-            if (i == j) {
-                re = sq_part(&S.p[2 * i], 0);
-                im = sq_part(&S.p[2 * i], 1);
-            } else {
-                const int c = i * (11 - i) / 2 + (j - i - 1);
-                re = fq_dbl(kara_part(&S.p[12 + 3 * c], 0));
-                im = fq_dbl(kara_part(&S.p[12 + 3 * c], 1));
-            }
-            v = twist_part(re, im, e, i + j >= 6);
-        }
-        S.tm[L] = v;
+        // i == j: the square's parts; i < j: twice the Karatsuba parts; i > j: nothing (the pair is
+        // counted once, at i < j)
+        const int c = i < j ? i * (11 - i) / 2 + (j - i - 1) : 0;
+        const fq* ms = &S.p[2 * i];
+        const fq* mk = &S.p[12 + 3 * c];
+        const fq re = fq_select(i == j, sq_part(ms, 0), fq_dbl(kara_part(mk, 0)));
+        const fq im = fq_select(i == j, sq_part(ms, 1), fq_dbl(kara_part(mk, 1)));
+        fq zero;
+        fq_zero(zero);
+        S.tm[L] = fq_select(i <= j, twist_part(re, im, e, i + j >= 6), zero);
     }
     if (NW == 4 && L >= 96 && L < 106) {           // XX, YY, ZZ, YZ, XY (re, im)
         const int v = L - 96, which = v >> 1, e = v & 1;
-        S.v[v] = which < 3 ? sq_part(&S.p[57 + 2 * which], e) : kara_part(&S.p[57 + 6 + 3 * (which - 3)], e);
+        S.v[v] = fq_select(which < 3, sq_part(&S.p[57 + 2 * (which < 3 ? which : 0)], e),
+                           kara_part(&S.p[57 + 6 + 3 * (which < 3 ? 0 : which - 3)], e));
     }
     if (NW == 4) {
         wsync<NW>();
@@ -439,18 +454,17 @@ FPG_NOINL void wm_dbl(WMill& S, const fq& m3x, const fq& y2) {
             // 24: 6 bz, 26: 18 bz (so that (6 bz)(18 bz) = 108 bz^2 is a product of round B)
             const int u = L - 96, e = u & 1, kind = u >> 1;
             const fq zr = S.p[61], zi = fq_dbl(S.p[62]);
-            const fq bze = fq_dbl(fq_dbl(e ? fq_add(zr, zi) : fq_sub(zr, zi)));
-            const fq yy = e ? fq_dbl(S.p[60]) : S.p[59];
+            const fq bze = fq_dbl(fq_dbl(fq_select(e, fq_add(zr, zi), fq_sub(zr, zi))));
+            const fq yy = fq_select(e, fq_dbl(S.p[60]), S.p[59]);
             const fq b3 = fq_add(fq_dbl(bze), bze);
             const fq b9 = fq_add(fq_dbl(b3), b3);
-            fq r;
-            if (kind == 0) r = bze;
-            else if (kind == 1) r = fq_sub(yy, b9);
-            else if (kind == 2) r = fq_add(yy, b9);
-            else if (kind == 3) r = fq_sub(yy, b3);
-            else if (kind == 4) r = fq_dbl(b3);
-            else r = fq_add(fq_dbl(b3), fq_dbl(fq_dbl(b3)));
-            S.v[16 + u] = r;
+            const fq b6 = fq_dbl(b3);
+            // kind 0: bz, 1: YY - 9 bz, 2: YY + 9 bz, 3: YY - 3 bz, 4: 6 bz, 5: 18 bz
+            const fq sub_t = fq_select(kind == 1, b9, b3), add_t = fq_select(kind == 2, b9, b6);
+            const fq r_sub = fq_sub(yy, sub_t);
+            const fq r_add = fq_add(fq_select(kind == 2, yy, fq_dbl(b6)), add_t);   // kind 5: 12 bz + 6 bz
+            S.v[16 + u] = fq_select(kind == 0, bze,
+                                    fq_select(kind == 1 || kind == 3, r_sub, fq_select(kind == 4, b6, r_add)));
         }
     } else if (L < 12) {                           // f^2, coefficient k, component e
         const int k = L >> 1, e = L & 1;
@@ -485,13 +499,17 @@ FPG_NOINL void wm_dbl(WMill& S, const fq& m3x, const fq& y2) {
             const fq* YY = S.v + 2;
             const fq* YZ = S.v + 6;
             const fq* XY = S.v + 8;
+            const fq* a;
+            const fq* b;
+            int kind, mode;
+            if (L < 2) { a = b = XX; kind = L; mode = 2; }                           // m3x XX
+            else if (L < 4) { a = b = YZ; kind = L - 2; mode = 2; }                  // y2 YZ
+            else if (L < 7) { a = XY; b = S.v + 18; kind = L - 4; mode = 0; }        // XY (YY - 9 bz)
+            else if (L < 9) { a = b = S.v + 20; kind = L - 7; mode = 1; }            // (YY + 9 bz)^2
+            else if (L < 12) { a = S.v + 24; b = S.v + 26; kind = L - 9; mode = 0; } // 108 bz^2
+            else { a = YY; b = YZ; kind = L - 12; mode = 0; }                        // YY YZ
             fq x, y;
-            if (L < 2) { x = XX[L]; y = m3x; }
-            else if (L < 4) { x = YZ[L - 2]; y = y2; }
-            else if (L < 7) kara_ops(x, y, XY, S.v + 18, L - 4);        // XY (YY - 9 bz)
-            else if (L < 9) sq_ops(x, y, S.v + 20, L - 7);              // (YY + 9 bz)^2
-            else if (L < 12) kara_ops(x, y, S.v + 24, S.v + 26, L - 9); // 108 bz^2
-            else kara_ops(x, y, YY, YZ, L - 12);                        // YY YZ
+            prod_ops(x, y, a, b, kind, mode, fq_select(L < 2, m3x, y2));
             S.p[L] = fq_mul(x, y);
         }
         wsync<NW>();
@@ -499,7 +517,7 @@ FPG_NOINL void wm_dbl(WMill& S, const fq& m3x, const fq& y2) {
         const int w = L >> 5, pl = L & 31;
         if (w == 0 && pl < 6) {
             const int e = pl & 1, which = pl >> 1;                      // l0 = YY - 3 bz, l2, l3
-            S.l[pl] = which == 0 ? S.v[22 + e] : S.p[2 * (which - 1) + e];
+            S.l[pl] = fq_select(which == 0, S.v[22 + e], S.p[2 * (which ? which - 1 : 0) + e]);
         } else if (w > 0 && pl < 2) {
             const int e = pl;
             if (w == 1) S.T[e] = fq_dbl(kara_part(&S.p[4], e));
@@ -587,43 +605,57 @@ FPG_NOINL void wm_add(WMill& S, const fq& mxP, const fq& yP) {
     wsync<NW>();
     if (L < 4) {                                    // theta = Y - yQ Z, lambda = X - xQ Z
         const int e = L & 1;
-        S.v[L] = L < 2 ? fq_sub(Y[e], kara_part(&S.p[0], e)) : fq_sub(X[e], kara_part(&S.p[3], e));
+        S.v[L] = fq_sub(L < 2 ? Y[e] : X[e], kara_part(&S.p[L < 2 ? 0 : 3], e));
     }
     wsync<NW>();
     const fq* th = S.v;
     const fq* la = S.v + 2;
     // round B: theta xQ, lambda yQ, -theta xP, lambda yP, theta^2, lambda^2
     if (L < 14) {
+        const fq* a;
+        const fq* b;
+        int kind, mode;
+        if (L < 3) { a = th; b = xQ; kind = L; mode = 0; }
+        else if (L < 6) { a = la; b = yQ; kind = L - 3; mode = 0; }
+        else if (L < 8) { a = b = th; kind = L - 6; mode = 2; }
+        else if (L < 10) { a = b = la; kind = L - 8; mode = 2; }
+        else if (L < 12) { a = b = th; kind = L - 10; mode = 1; }
+        else { a = b = la; kind = L - 12; mode = 1; }
         fq x, y;
-        if (L < 3) kara_ops(x, y, th, xQ, L);
-        else if (L < 6) kara_ops(x, y, la, yQ, L - 3);
-        else if (L < 8) { x = th[L - 6]; y = mxP; }
-        else if (L < 10) { x = la[L - 8]; y = yP; }
-        else if (L < 12) sq_ops(x, y, th, L - 10);
-        else sq_ops(x, y, la, L - 12);
+        prod_ops(x, y, a, b, kind, mode, fq_select(L < 8, mxP, yP));
         S.p[L] = fq_mul(x, y);
     }
     wsync<NW>();
     if (L < 10) {
         const int w = L >> 1, e = L & 1;
-        if (w == 0) S.l[e] = fq_sub(kara_part(&S.p[0], e), kara_part(&S.p[3], e));
-        else if (w == 1) S.l[2 + e] = S.p[6 + e];
-        else if (w == 2) S.l[4 + e] = S.p[8 + e];
-        else if (w == 3) S.v[4 + e] = sq_part(&S.p[10], e);        // C = theta^2
-        else S.v[6 + e] = sq_part(&S.p[12], e);                     // D = lambda^2
+        // w 0: l0 = theta xQ - lambda yQ, 1: l2, 2: l3, 3: C = theta^2, 4: D = lambda^2
+        const fq l0 = fq_sub(kara_part(&S.p[0], e), kara_part(&S.p[3], e));
+        const fq sq = sq_part(&S.p[w == 3 ? 10 : 12], e);
+        const fq r = fq_select(w == 0, l0, fq_select(w < 3, S.p[6 + 2 * (w == 2) + e], sq));
+        fq* dst = w < 3 ? &S.l[2 * w + e] : &S.v[4 + 2 * (w - 3) + e];
+        *dst = r;
     }
     wsync<NW>();
     // round C: f * line (54) and E = D lambda, F = Z C, G = X D (9)
     for (int t = L; t < 63; t += 32 * NW) {
-        if (t < 54) {
-            wm_line_products(S, S.f, t);
-        } else {
+        const fq* a;
+        const fq* b;
+        int kind;
+        if (t < 54) {                                   // f * line: f_i l_term
+            const int q = t / 3, term = q / 6, k = q - 6 * term;
+            const int i = term == 0 ? k : (term == 1 ? (k + 4) % 6 : (k + 3) % 6);
+            a = S.f + 2 * i;
+            b = S.l + 2 * term;
+            kind = t - 3 * q;
+        } else {                                        // E = D lambda, F = Z C, G = X D
             const int u = t - 54, which = u / 3;
-            fq x, y;
-            kara_ops(x, y, which == 0 ? S.v + 6 : (which == 1 ? Z : X), which == 0 ? la : (which == 1 ? S.v + 4 : S.v + 6),
-                     u % 3);
-            S.p[t] = fq_mul(x, y);
+            a = which == 0 ? S.v + 6 : (which == 1 ? Z : X);
+            b = which == 0 ? la : (which == 1 ? S.v + 4 : S.v + 6);
+            kind = u % 3;
         }
+        fq x, y;
+        kara_ops(x, y, a, b, kind);
+        S.p[t] = fq_mul(x, y);
     }
     wsync<NW>();
     if (NW == 4) {
@@ -662,11 +694,11 @@ FPG_NOINL void wm_add(WMill& S, const fq& mxP, const fq& yP) {
     wsync<NW>();
     if (L < 6) {
         const int w = L >> 1, e = L & 1;
-        fq r;
-        if (w == 0) r = kara_part(&S.p[0], e);
-        else if (w == 1) r = fq_sub(kara_part(&S.p[3], e), kara_part(&S.p[6], e));
-        else r = kara_part(&S.p[9], e);
-        S.h[L] = r;
+        // w 0: X' = lambda H, 1: Y' = theta (G - H) - Y E, 2: Z' = Z E
+        const fq k0 = kara_part(&S.p[w == 0 ? 0 : (w == 1 ? 3 : 9)], e);
+        fq zero;
+        fq_zero(zero);
+        S.h[L] = fq_sub(k0, fq_select(w == 1, kara_part(&S.p[6], e), zero));
     }
     wsync<NW>();
     if (L < 6) S.T[L] = S.h[L];
@@ -688,7 +720,7 @@ FPG_NOINL void w_miller(WMill& S, g1a P, g2a Q) {
         fq_one(one);
         fq z;
         fq_zero(z);
-        S.f[L] = L == 0 ? one : z;
+        S.f[L] = fq_select(L == 0, one, z);
     }
     if (L == 0) {
         S.T[0] = Q.x.c0; S.T[1] = Q.x.c1; S.T[2] = Q.y.c0; S.T[3] = Q.y.c1;
@@ -706,8 +738,8 @@ FPG_NOINL void w_miller(WMill& S, g1a P, g2a Q) {
         fq_one(one);
         fq z;
         fq_zero(z);
-        const fq v = ((L >> 1) & 1) ? fq_neg(S.f[L]) : S.f[L];       // conjugation (x < 0)
-        S.f[L] = inf ? (L == 0 ? one : z) : v;
+        const fq v = fq_select((L >> 1) & 1, fq_neg(S.f[L]), S.f[L]);   // conjugation (x < 0)
+        S.f[L] = fq_select(inf, fq_select(L == 0, one, z), v);
     }
     wsync<NW>();
 }
