@@ -129,73 +129,159 @@ FPG_DEV bool lt(const uint32_t* a, const uint32_t* P) {
     return ptx::subc(0, 0) != 0;
 }
 
-// Plain modular inverse of x (0 < x < P, P odd) by the binary extended Euclidean algorithm
-// (Stein's gcd with the Bezout coefficients kept mod P).  Invariants: x1 * x = u, x2 * x = v (mod P).
-// Variable time; the values inverted here are public.  Returns 0 for x = 0.
+// Plain modular inverse of x (0 < x < P, P odd) by batched division steps (the divstep iteration of
+// Bernstein and Yang, "Fast constant-time gcd computation and modular inversion", 2019, run in its
+// variable-time form: the values inverted here are public).  State: integers f (odd) and g with
+// f = d x and g = e x (mod P), from f = P, g = x, d = 0, e = 1.  One division step, by delta and the
+// parity of g: if delta > 0 and g is odd, (f, g) <- (g, (g - f) / 2) and delta <- 1 - delta; else if g
+// is odd, g <- (g + f) / 2; else g <- g / 2; delta <- delta + 1 in the last two cases.  Thirty steps
+// depend only on the low 32 bits of f and g, so they run on one word each and yield a matrix
+// [[u, v], [q, r]] (|u| + |v|, |q| + |r| <= 2^30) with 2^30 (f', g') = (u f + v g, q f + r g); the
+// full-width f, g and the residues d, e (times 2^-30 mod P, by adding the multiple of P that clears
+// the low 30 bits) are then updated once per batch.  When g = 0, f = +-1 = gcd and x^-1 = +-d.
+// Returns 0 for x = 0.  pinv = -P^-1 mod 2^32.
 template <int N>
-FPG_DEV void binv(uint32_t* r, const uint32_t* x, const uint32_t* P) {
-    uint32_t u[N], v[N], x1[N], x2[N];
+FPG_DEV void ds_lincomb(uint32_t* out, int32_t a, const uint32_t* x, int32_t b, const uint32_t* y) {
+    // out (N + 2 words, two's complement) = a x + b y for signed N + 1 word x, y
+    int64_t carry = 0;
 #pragma unroll
-    for (int j = 0; j < N; j++) { u[j] = x[j]; v[j] = P[j]; x1[j] = 0; x2[j] = 0; }
-    x1[0] = 1;
-    if (is_zero<N>(u)) {
+    for (int i = 0; i <= N; i++) {
+        const int64_t xi = i < N ? (int64_t)x[i] : (int64_t)(int32_t)x[i];
+        const int64_t yi = i < N ? (int64_t)y[i] : (int64_t)(int32_t)y[i];
+        const int64_t t = (int64_t)a * xi + (int64_t)b * yi + carry;
+        out[i] = (uint32_t)t;
+        carry = t >> 32;
+    }
+    out[N + 1] = (uint32_t)carry;
+}
+// arithmetic right shift by 30 of an N + 2 word two's complement value into N + 1 words
+template <int N>
+FPG_DEV void ds_shr30(uint32_t* out, const uint32_t* t) {
+#pragma unroll
+    for (int i = 0; i <= N; i++) out[i] = (t[i] >> 30) | (t[i + 1] << 2);
+}
+template <int N>
+FPG_DEV bool ds_is_neg(const uint32_t* a) { return (int32_t)a[N] < 0; }
+
+template <int N>
+FPG_DEV void inv_ds(uint32_t* r, const uint32_t* x, const uint32_t* P, uint32_t pinv) {
+    uint32_t f[N + 1], g[N + 1], d[N + 1], e[N + 1];
+#pragma unroll
+    for (int j = 0; j < N; j++) { f[j] = P[j]; g[j] = x[j]; d[j] = 0; e[j] = 0; }
+    f[N] = g[N] = d[N] = e[N] = 0;
+    e[0] = 1;
+    if (is_zero<N>(x)) {
 #pragma unroll
         for (int j = 0; j < N; j++) r[j] = 0;
         return;
     }
-    auto is_one = [](const uint32_t* a) {
-        uint32_t acc = a[0] ^ 1u;
+    int32_t delta = 1;
+    const uint32_t mask30 = (1u << 30) - 1;
+    // d, e <- (a d + b e) 2^-30 mod P, kept in (-P, P) as N + 1 word two's complement
+    auto mod_update = [&](uint32_t* out, int32_t a, int32_t b) {
+        uint32_t t[N + 2];
+        ds_lincomb<N>(t, a, d, b, e);
+        const uint32_t k = (t[0] * pinv) & mask30;        // t + k P = 0 mod 2^30
+        uint64_t c = 0;
 #pragma unroll
-        for (int j = 1; j < N; j++) acc |= a[j];
-        return acc == 0;
+        for (int i = 0; i < N + 2; i++) {
+            const uint64_t s = (uint64_t)t[i] + (i < N ? (uint64_t)k * P[i] : 0) + c;
+            t[i] = (uint32_t)s;
+            c = s >> 32;
+        }
+        ds_shr30<N>(out, t);
+        // out in (-P, 2P) for d, e in (-P, P): subtract P once if out >= P, back into (-P, P)
+        if (!ds_is_neg<N>(out)) {
+            uint32_t z[N + 1];
+            uint64_t bw = 0;
+#pragma unroll
+            for (int j = 0; j <= N; j++) {
+                const uint64_t s = (uint64_t)out[j] - (j < N ? P[j] : 0) - bw;
+                z[j] = (uint32_t)s;
+                bw = (s >> 63) & 1;
+            }
+            if (!bw) {
+#pragma unroll
+                for (int j = 0; j <= N; j++) out[j] = z[j];
+            }
+        }
     };
-    // a <- a / 2 mod P for a < P: add P when odd (the sum has N+1 words), then shift right
-    auto halve = [&](uint32_t* a) {
-        uint32_t hi = 0;
-        if (a[0] & 1) {
-            a[0] = ptx::add_cc(a[0], P[0]);
+    // at most 2 x 32 N divsteps for P < 2^(32 N); the guard only bounds the loop on bad input
+    for (int batch = 0; batch < 4 * 32 * N / 30 + 4; batch++) {
+        if (is_zero<N + 1>(g)) break;
+        uint32_t fl = f[0], gl = g[0];
+        int32_t u = 1, v = 0, q = 0, w = 1;
+#pragma unroll 1
+        for (int i = 0; i < 30; i++) {
+            const bool godd = gl & 1;
+            if (delta > 0 && godd) {                        // swap rows, negate g so the add gives g - f
+                delta = -delta;
+                const uint32_t tf = fl;
+                fl = gl;
+                gl = 0u - tf;
+                const int32_t tu = u, tv = v;
+                u = q; v = w;
+                q = -tu; w = -tv;
+            }
+            if (godd) {
+                gl += fl;
+                q += u;
+                w += v;
+            }
+            delta += 1;
+            gl >>= 1;
+            u *= 2;
+            v *= 2;
+        }
+        uint32_t t[N + 2], nf[N + 1], ng[N + 1], nd[N + 1], ne[N + 1];
+        ds_lincomb<N>(t, u, f, v, g);
+        ds_shr30<N>(nf, t);
+        ds_lincomb<N>(t, q, f, w, g);
+        ds_shr30<N>(ng, t);
+        mod_update(nd, u, v);
+        mod_update(ne, q, w);
 #pragma unroll
-            for (int j = 1; j < N; j++) a[j] = ptx::addc_cc(a[j], P[j]);
-            hi = ptx::addc(0, 0);
+        for (int j = 0; j <= N; j++) { f[j] = nf[j]; g[j] = ng[j]; d[j] = nd[j]; e[j] = ne[j]; }
+    }
+    // f = +-1: x^-1 = d (f = 1) or -d (f = -1), normalised into [0, P)
+    const bool fneg = ds_is_neg<N>(f);
+    if (fneg) {                                              // d <- -d
+        uint32_t z[N + 1];
+        uint32_t bw = 0;
+#pragma unroll
+        for (int j = 0; j <= N; j++) {
+            const uint64_t s = (uint64_t)0 - d[j] - bw;
+            z[j] = (uint32_t)s;
+            bw = (uint32_t)(s >> 63);
         }
 #pragma unroll
-        for (int j = 0; j < N - 1; j++) a[j] = __funnelshift_r(a[j], a[j + 1], 1);
-        a[N - 1] = __funnelshift_r(a[N - 1], hi, 1);
-    };
-    auto shr1 = [](uint32_t* a) {
+        for (int j = 0; j <= N; j++) d[j] = z[j];
+    }
+    // d in (-P, P): add P when negative (the loops are bounds, one pass suffices)
+    for (int it = 0; it < 4 && ds_is_neg<N>(d); it++) {
+        uint64_t c = 0;
 #pragma unroll
-        for (int j = 0; j < N - 1; j++) a[j] = __funnelshift_r(a[j], a[j + 1], 1);
-        a[N - 1] >>= 1;
-    };
-    // every pass shifts or subtracts; for canonical input < 4 * 32N passes suffice, the bound only
-    // guarantees termination on a non-canonical input (the result is then meaningless)
-    for (int guard = 0; guard < 8 * 32 * N && !is_one(u) && !is_one(v); guard++) {
-        if (!(u[0] & 1)) { shr1(u); halve(x1); continue; }
-        if (!(v[0] & 1)) { shr1(v); halve(x2); continue; }
-        // u >= v ?  t = u - v
-        uint32_t t[N];
-        t[0] = ptx::sub_cc(u[0], v[0]);
-#pragma unroll
-        for (int j = 1; j < N; j++) t[j] = ptx::subc_cc(u[j], v[j]);
-        const uint32_t borrow = ptx::subc(0, 0);
-        if (!borrow) {
-#pragma unroll
-            for (int j = 0; j < N; j++) u[j] = t[j];
-            mod_sub<N>(x1, x1, x2, P);
-        } else {
-            v[0] = ptx::sub_cc(v[0], u[0]);
-#pragma unroll
-            for (int j = 1; j < N; j++) v[j] = ptx::subc_cc(v[j], u[j]);
-            mod_sub<N>(x2, x2, x1, P);
+        for (int j = 0; j <= N; j++) {
+            const uint64_t s = (uint64_t)d[j] + (j < N ? P[j] : 0) + c;
+            d[j] = (uint32_t)s;
+            c = s >> 32;
         }
     }
-    if (is_one(u)) {
+    for (int it = 0; it < 4; it++) {
+        uint32_t z[N + 1];
+        uint64_t bw = 0;
 #pragma unroll
-        for (int j = 0; j < N; j++) r[j] = x1[j];
-    } else {
+        for (int j = 0; j <= N; j++) {
+            const uint64_t s = (uint64_t)d[j] - (j < N ? P[j] : 0) - bw;
+            z[j] = (uint32_t)s;
+            bw = (s >> 63) & 1;
+        }
+        if (bw) break;                                       // d < P
 #pragma unroll
-        for (int j = 0; j < N; j++) r[j] = x2[j];
+        for (int j = 0; j <= N; j++) d[j] = z[j];
     }
+#pragma unroll
+    for (int j = 0; j < N; j++) r[j] = d[j];
 }
 
 }  // namespace mp
@@ -247,11 +333,11 @@ FPG_DEV fq fq_from_mont(const fq& a) {
     fq one; fq_zero(one); one.v[0] = 1;
     return fq_mul(a, one);
 }
-// Inverse of a Montgomery residue aR: the plain inverse (aR)^-1 by binary extended gcd, then one
+// Inverse of a Montgomery residue aR: the plain inverse (aR)^-1 by batched division steps, then one
 // Montgomery product with R^3 gives a^-1 R.  0 maps to 0.
 FPG_NOINL fq fq_inv(const fq& a) {
     fq t, r3;
-    mp::binv<12>(t.v, a.v, FQ_P);
+    mp::inv_ds<12>(t.v, a.v, FQ_P, FQ_PINV);
     fq_from_const(r3, FQ_R3);
     return fq_mul(t, r3);
 }
@@ -289,7 +375,7 @@ FPG_DEV fr fr_from_mont(const fr& a) {
 FPG_DEV bool fr_canonical_lt_r(const fr& a) { return mp::lt<8>(a.v, FR_P); }
 FPG_NOINL fr fr_inv(const fr& a) {
     fr t, r3;
-    mp::binv<8>(t.v, a.v, FR_P);
+    mp::inv_ds<8>(t.v, a.v, FR_P, FR_PINV);
 #pragma unroll
     for (int j = 0; j < 8; j++) r3.v[j] = FR_R3[j];
     return fr_mul(t, r3);

@@ -1,0 +1,52 @@
+"""The field inverse of the CUDA path (batched division steps, `mp::inv_ds` in fp.cuh), compiled for
+the host and checked against Python's modular inverse: x x^-1 = 1 for random and edge values of Fq
+and Fr (1, 2, p - 1, values with long runs of zero or one bits), and 0 maps to 0 (no GPU)."""
+import ctypes
+import os
+import random
+import shutil
+import subprocess
+
+import pytest
+
+from tests import _pyref as ref
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+CSRC = os.path.join(os.path.dirname(HERE), "paper_2601_03031_gb300", "csrc")
+
+
+@pytest.fixture(scope="module")
+def lib(tmp_path_factory):
+    gxx = shutil.which("g++")
+    if not gxx:
+        pytest.skip("g++ not available")
+    so = str(tmp_path_factory.mktemp("emu_inv") / "libinv.so")
+    subprocess.check_call([gxx, "-std=c++20", "-O1", "-shared", "-fPIC", f"-I{CSRC}", "-o", so,
+                           os.path.join(HERE, "emu", "inverse.cpp")])
+    L = ctypes.CDLL(so)
+    L.emu_inv_fq.restype = None
+    L.emu_inv_fr.restype = None
+    return L
+
+
+def call(fn, x: int, n: int) -> int:
+    xi = (ctypes.c_uint32 * n)(*[(x >> (32 * i)) & 0xFFFFFFFF for i in range(n)])
+    r = (ctypes.c_uint32 * n)()
+    fn(xi, r)
+    return sum(r[i] << (32 * i) for i in range(n))
+
+
+def edge_values(m: int):
+    vals = [1, 2, 3, m - 1, m - 2, (m - 1) // 2, 1 << 31, (1 << 64) - 1, m >> 1, (m >> 3) | 1]
+    vals += [((1 << k) - 1) % m for k in (30, 31, 32, 33, 63, 64, 200)]
+    return [v % m for v in vals if v % m]
+
+
+@pytest.mark.parametrize("field", ["fq", "fr"])
+def test_inverse_against_python(lib, field):
+    m, n, fn = (ref.P, 12, lib.emu_inv_fq) if field == "fq" else (ref.R, 8, lib.emu_inv_fr)
+    rnd = random.Random(17)
+    values = edge_values(m) + [rnd.randrange(1, m) for _ in range(400)]
+    for x in values:
+        assert call(fn, x, n) == pow(x, -1, m), hex(x)
+    assert call(fn, 0, n) == 0
