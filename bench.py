@@ -940,6 +940,9 @@ def main():
                        "one dependent product (fp_fq_mul_latency); combines and inversions excluded"}
     share = {k: round(v[1] / (total_ms if total_ms else 1), 4) for k, v in
              sorted(prof.items(), key=lambda kv: -kv[1][1])[:8]}
+    # every kernel: launches per step and mean CUDA-event time per launch (ms)
+    kernel_ms = {k: [round(v[0] / args.steps, 2), round(v[1] / v[0], 4)] for k, v in
+                 sorted(prof.items(), key=lambda kv: -kv[1][1]) if v[0]}
 
     cpu = None
     if not args.no_cpu_baseline:
@@ -987,6 +990,7 @@ def main():
         "roofline_kernels": roof_all,
         "latency_roofline": lat,
         "kernel_share": share,
+        "kernel_launches_and_ms": kernel_ms,
         "clocks": clk.summary(),
         "cpu_baseline": cpu,
         "sweeps": sweeps,
