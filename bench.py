@@ -41,6 +41,14 @@ FQ_MULS = {
     # by the 4 pairs, so a pair costs 7135 - 3/4 x 62 x 36
     "miller_loop_multi4": 7135 - 3 * 62 * 36 // 4,
     "g2_msm_madd": 30,       # XYZZ mixed addition over Fq2 (8M + 2S), 3 Fq products per Fq2 product
+    # comb folds of a point of A and of v (k_step1.cu): 64 table entries and the L half added with
+    # complete additions (12 Fq products on G1, 12 Fq2 products of 3 on G2)
+    "comb_fold": 65 * 12 + 65 * 36,
+    # their chains: 127 G1 and 63 G2 complete doublings (6M + 2S)
+    "comb_chain": 127 * 8 + 63 * 8 * 3,
+    # their tables: per G1 window 10 additions and 3 products by omega, per G2 position 11 additions
+    # and 3 psi maps (6 Fq2 products)
+    "comb_tab": 64 * (10 * 12 + 3) + 64 * (11 * 36 + 18),
 }
 
 
@@ -64,18 +72,17 @@ CRITICAL_ROUNDS = {
     # G1 by 8-lane groups, 2-bit joint GLV windows: 13 table formulas + 64 x (2 doublings + 1 addition),
     # 2 phases each, then the addition of A_L and the conversion (longer than the warp G2 chain)
     "k_fold_w": (13 + 64 * 3) * 2 + 2 + 3,
-    # split folds in four parts (rounds of at most 128 points): the G1 quarter chain (13 table
-    # formulas + 16 x (2 doublings + 1 addition)), two levels of sums of the parts and the addition of
-    # A_L, 2 phases each, then the conversion (the G2 quarter chain, 11 + 16 x 2 + 3 formulas, is
-    # shorter)
-    "k_fold_s": (13 + 16 * 3 + 2 + 1) * 2 + 3,
-    # shifted bases beside the round: 3 x 32 G1 doublings of 2 phases, each followed by a conversion
-    "k_fold_pre": 96 * 2 + 3 * 3,
+    # comb folds (rounds of at most 256 points): the G2 warp's 7 additions of table entries, 3 tree
+    # levels and the addition of v_L, 2 phases each, then the conversion (the G1 groups' 3 + 4 + 1
+    # additions are shorter)
+    "k_fold_c": (7 + 3 + 1) * 2 + 3,
+    # comb chains beside the round: 127 G1 doublings of 2 phases
+    "k_comb_chain": 127 * 2,
     "k_sparse_g": (13 + 64 * 3) * 2 + 2,
 }
 
 
-FOLD_SPLIT_MAX = 256          # rounds with at most this many fold points use the split folds
+FOLD_COMB_MAX = 256           # rounds with at most this many fold points use the comb folds
 
 # DRAM bytes per launch (dram__bytes_read.sum + dram__bytes_write.sum) from one ncu capture of the
 # kernel at this workload, keyed by (log N, b, kernel); an entry is removed when its kernel changes
@@ -105,8 +112,10 @@ def step_units(log_n: int, b: int, msm_window: int, msm_window_g2: int = 16) -> 
         "k_commit_miller_c": ("miller_loop", R if R <= 1024 else 0),
         "k_commit_miller_w": ("miller_loop", R if R > 1024 else 0),
         "k_sparse_g": ("g1_mul", sum(K * min(b, 2 * h) for h in hs)),
-        "k_fold_s": (("g1_mul", "g2_mul"), sum(K * h for h in hs if K * h <= FOLD_SPLIT_MAX)),
-        "k_fold_w": (("g1_mul", "g2_mul"), sum(K * h for h in hs if FOLD_SPLIT_MAX < K * h <= 4096)),
+        "k_fold_c": ("comb_fold", sum(K * h for h in hs if K * h <= FOLD_COMB_MAX)),
+        "k_comb_chain": ("comb_chain", sum(K * h for h in hs if K * h <= FOLD_COMB_MAX)),
+        "k_comb_tab": ("comb_tab", sum(K * h for h in hs if K * h <= FOLD_COMB_MAX)),
+        "k_fold_w": (("g1_mul", "g2_mul"), sum(K * h for h in hs if FOLD_COMB_MAX < K * h <= 4096)),
         "k_fold": (("g1_mul", "g2_mul"), sum(K * h for h in hs if K * h > 4096)),
         "k_msm_chunk": ("msm_madd", 2 * R * M * W),
         "k_msm_chunk_g2": ("g2_msm_madd", 4 * 2 * R * K * W2 if w_msm else 0),

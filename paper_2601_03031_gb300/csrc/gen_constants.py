@@ -204,6 +204,15 @@ out.append(arr("PSI_CX1", mont(PSI_CX[1], 12), 12))
 out.append(arr("PSI_CY0", mont(PSI_CY[0], 12), 12))
 out.append(arr("PSI_CY1", mont(PSI_CY[1], 12), 12))
 out.append(arr("BLS_H1", H1, 4))
+# the block-split Fq product (fq_split.cuh): c_k = 2^(32 k - 320) mod p for the limbs k < 10 of a
+# double-width product folded into its high part, and -p^-1 mod 2^64 for the closing two-limb
+# Montgomery step
+# (rows 10 and 11 are zero: the warps all run three fold rows, the surplus ones with a zero factor)
+out.append("__constant__ uint32_t FQ_FOLD[12][12] = {" + ", ".join(
+    "{" + ", ".join(f"0x{w:08x}u" for w in limbs(pow(2, 32 * k - 320, P) if k < 10 else 0, 12)) + "}"
+    for k in range(12)) + "};\n")
+out.append(f"#define FQ_PINV64_LO 0x{(-pow(P, -1, 2**64)) % 2**32:08x}u\n")
+out.append(f"#define FQ_PINV64_HI 0x{((-pow(P, -1, 2**64)) % 2**64) >> 32:08x}u\n")
 out.append("__constant__ uint32_t SHA256_K[64] = {" + ", ".join(f"0x{k:08x}u" for k in SHA_K) + "};\n")
 out.append("__constant__ uint32_t SHA256_H0[8] = {" + ", ".join(f"0x{k:08x}u" for k in SHA_H) + "};\n")
 open(os.path.join(os.path.dirname(os.path.abspath(__file__)), "constants.cuh"), "w").write("".join(out))

@@ -48,8 +48,11 @@ FPG_DEV void gec_add_ops2(int q, const F& t3, const F& t4, const F& x3, const F&
     a = f_sel(q == 0, t4, f_sel(q == 1, t3, f_sel(q == 2, y3, f_sel(q == 3, u1, f_sel(q == 4, x3, z3)))));
     b = f_sel(q == 0, y3, f_sel(q == 1, u1, f_sel(q == 2, x3, f_sel(q == 3, z3, f_sel(q == 4, t3, t4)))));
 }
-template <typename F> struct GEc {
-    F sc[8];          // products of the current phase
+// the formulas' scratch (products of the current phase), and the engine with a table of 16 points
+template <typename F> struct GEcs {
+    F sc[8];
+};
+template <typename F> struct GEc : GEcs<F> {
     GPt<F> tab[16];   // subset sums of the split bases
 };
 
@@ -64,7 +67,7 @@ static __device__ __noinline__ fq2 f_b3(fq2 a) {          // 3 b' = 12 (1 + u) o
 }
 
 template <typename F>
-FPG_DEV void gec_phase(GEc<F>& sm, int lane, const F& a, const F& b) {
+FPG_DEV void gec_phase(GEcs<F>& sm, int lane, const F& a, const F& b) {
     const F p = f_mul(a, b);
     gsync();
     if (lane < 6) sm.sc[lane] = p;
@@ -80,7 +83,7 @@ FPG_DEV GPt<F> gec_identity() {
 
 // P + Q, complete (RCB16 Algorithm 7, a = 0)
 template <typename F>
-FPG_NOINL GPt<F> gec_add(GEc<F>& sm, int lane, const GPt<F>& P, const GPt<F>& Q) {
+FPG_NOINL GPt<F> gec_add(GEcs<F>& sm, int lane, const GPt<F>& P, const GPt<F>& Q) {
     F a, b;
     gec_add_ops(lane < 6 ? lane : 5, P, Q, a, b);
     gec_phase(sm, lane, a, b);
@@ -103,7 +106,7 @@ FPG_NOINL GPt<F> gec_add(GEc<F>& sm, int lane, const GPt<F>& P, const GPt<F>& Q)
 
 // 2P, complete (RCB16 Algorithm 9, a = 0)
 template <typename F>
-FPG_NOINL GPt<F> gec_dbl(GEc<F>& sm, int lane, const GPt<F>& P) {
+FPG_NOINL GPt<F> gec_dbl(GEcs<F>& sm, int lane, const GPt<F>& P) {
     // lanes: 0 Y Y, 1 Y Z, 2 Z Z, 3 X Y
     F a = f_sel(lane >= 3, P.X, f_sel(lane == 2, P.Z, P.Y));
     F b = f_sel(lane == 0, P.Y, f_sel(lane >= 3, P.Y, P.Z));
@@ -152,15 +155,17 @@ FPG_DEV GPt<F> gec_from_affine_or_inf(const F& x, const F& y) {
 // Fq2 results (re = m0 - m1, im = m2 - m0 - m1) and every lane continues with the same linear
 // combinations.
 // ---------------------------------------------------------------------------------------
-struct GEcW {
+struct GEcWs {       // the formulas' scratch
     fq2 sc[8];
     fq p[18];
+};
+struct GEcW : GEcWs {
     GPt<fq2> tab[16];
 };
 
 // operands of product q = L / 3 come from sel(q, a, b); lane L computes component L % 3
 template <typename Sel>
-FPG_DEV void gecw_phase(GEcW& sm, int L, Sel&& sel) {
+FPG_DEV void gecw_phase(GEcWs& sm, int L, Sel&& sel) {
     if (L < 18) {
         const int q = L / 3, kind = L - 3 * q;
         fq2 a, b;
@@ -186,7 +191,7 @@ FPG_DEV void gecw_phase(GEcW& sm, int L, Sel&& sel) {
 }
 
 // P + Q, complete (RCB16 Algorithm 7, a = 0), on one warp
-FPG_NOINL GPt<fq2> gecw_add(GEcW& sm, int L, const GPt<fq2>& P, const GPt<fq2>& Q) {
+FPG_NOINL GPt<fq2> gecw_add(GEcWs& sm, int L, const GPt<fq2>& P, const GPt<fq2>& Q) {
     gecw_phase(sm, L, [&](int q, fq2& a, fq2& b) { gec_add_ops(q, P, Q, a, b); });
     const fq2 t0 = sm.sc[0], t1 = sm.sc[1], t2 = sm.sc[2];
     const fq2 t3 = e_sub(sm.sc[3], e_add(t0, t1));
@@ -205,7 +210,7 @@ FPG_NOINL GPt<fq2> gecw_add(GEcW& sm, int L, const GPt<fq2>& P, const GPt<fq2>& 
 }
 
 // 2P, complete (RCB16 Algorithm 9, a = 0), on one warp
-FPG_NOINL GPt<fq2> gecw_dbl(GEcW& sm, int L, const GPt<fq2>& P) {
+FPG_NOINL GPt<fq2> gecw_dbl(GEcWs& sm, int L, const GPt<fq2>& P) {
     gecw_phase(sm, L, [&](int q, fq2& a, fq2& b) {
         a = fq2_select(q >= 3, P.X, fq2_select(q == 2, P.Z, P.Y));
         b = fq2_select(q == 0, P.Y, fq2_select(q >= 3, P.Y, P.Z));
@@ -297,7 +302,7 @@ FPG_NOINL GPt<fq2> gecw_g2_mul_part(GEcW& sm, int L, const g2a& Qp, const uint32
 }
 
 // 2^n P by n complete doublings, on one warp
-FPG_NOINL GPt<fq2> gecw_g2_dbl_n(GEcW& sm, int L, GPt<fq2> acc, int n) {
+FPG_NOINL GPt<fq2> gecw_g2_dbl_n(GEcWs& sm, int L, GPt<fq2> acc, int n) {
     for (int i = 0; i < n; i++) acc = gecw_dbl(sm, L, acc);
     return acc;
 }
@@ -365,7 +370,86 @@ FPG_NOINL GPt<fq> gec_g1_mul_part(GEc<fq>& sm, int lane, const g1a& Pp, const ui
 }
 
 // 2^n P by n complete doublings, on an 8-lane group
-FPG_NOINL GPt<fq> gec_g1_dbl_n(GEc<fq>& sm, int lane, GPt<fq> acc, int n) {
+FPG_NOINL GPt<fq> gec_g1_dbl_n(GEcs<fq>& sm, int lane, GPt<fq> acc, int n) {
     for (int i = 0; i < n; i++) acc = gec_dbl(sm, lane, acc);
     return acc;
+}
+
+// ---------------------------------------------------------------------------------------
+// Fixed-base combs.  When the base of a scalar multiplication is known before its scalar, the
+// doublings can run ahead: with B_w = 4^w P (G1, two bits of each GLV half per window) or
+// B_i = 2^i Q (G2, one bit of each GLS digit per position) and a table of the window's or
+// position's 16 combinations, k P is the sum of one table entry per window, and the additions of
+// that sum are independent of each other.
+// ---------------------------------------------------------------------------------------
+// -phi(P) = (omega X : -Y : Z) for a projective P on G1 (phi: (x, y) -> (omega x, y))
+FPG_DEV GPt<fq> gec_g1_mphi(const GPt<fq>& P) {
+    fq om;
+    fq_from_const(om, GLV_OMEGA);
+    return {fq_mul(P.X, om), fq_neg(P.Y), P.Z};
+}
+// psi(P) = (cx conj(X) : cy conj(Y) : conj(Z)) for a projective P on the twist
+FPG_DEV GPt<fq2> gec_g2_psi(const GPt<fq2>& P) {
+    fq2 cx, cy;
+    fq_from_const(cx.c0, PSI_CX0); fq_from_const(cx.c1, PSI_CX1);
+    fq_from_const(cy.c0, PSI_CY0); fq_from_const(cy.c1, PSI_CY1);
+    return {fq2_mul(fq2_conj(P.X), cx), fq2_mul(fq2_conj(P.Y), cy), fq2_conj(P.Z)};
+}
+
+// P + Q on one thread: the formulas of gec_add (RCB16 Algorithm 7, a = 0) without the lanes, for
+// throughput work where many independent additions keep every lane busy
+template <typename F>
+FPG_NOINL GPt<F> gpt_add(const GPt<F> P, const GPt<F> Q) {
+    const F t0 = f_mul(P.X, Q.X), t1 = f_mul(P.Y, Q.Y), t2 = f_mul(P.Z, Q.Z);
+    const F s3 = f_mul(e_add(P.X, P.Y), e_add(Q.X, Q.Y));
+    const F s4 = f_mul(e_add(P.Y, P.Z), e_add(Q.Y, Q.Z));
+    const F s5 = f_mul(e_add(P.X, P.Z), e_add(Q.X, Q.Z));
+    const F t3 = e_sub(s3, e_add(t0, t1));
+    const F t4 = e_sub(s4, e_add(t1, t2));
+    const F y3 = f_b3(e_sub(s5, e_add(t0, t2)));
+    const F x3 = e_add(e_dbl(t0), t0);
+    const F bt2 = f_b3(t2);
+    const F z3 = e_add(t1, bt2), u1 = e_sub(t1, bt2);
+    GPt<F> r;
+    r.X = e_sub(f_mul(t3, u1), f_mul(t4, y3));
+    r.Y = e_add(f_mul(y3, x3), f_mul(u1, z3));
+    r.Z = e_add(f_mul(z3, t4), f_mul(x3, t3));
+    return r;
+}
+
+// out[a + 4 b] = a B + b (-phi(B)) for a, b < 4, from B and 2B, on one thread (the entries are read
+// back from out, which only this thread writes)
+FPG_DEV void gpt_g1_comb_table(const GPt<fq>& B, const GPt<fq>& B2, GPt<fq>* out) {
+    out[0] = gec_identity<fq>();
+    out[1] = B;
+    out[2] = B2;
+    out[3] = gpt_add(B2, B);
+    for (int i = 1; i < 4; i++) out[4 * i] = gec_g1_mphi(out[i]);
+    for (int b = 1; b < 4; b++)
+        for (int i = 1; i < 4; i++) out[i + 4 * b] = gpt_add(out[i], out[4 * b]);
+}
+// out[s] = sum_{j in s} (-1)^j psi^j(B) for s < 16, on one thread
+FPG_DEV void gpt_g2_comb_table(const GPt<fq2>& B, GPt<fq2>* out) {
+    out[0] = gec_identity<fq2>();
+    GPt<fq2> b = B;
+    for (int j = 0; j < 4; j++) {
+        if (j) b = gec_g2_psi(b);
+        GPt<fq2> bj = b;
+        if (j & 1) bj.Y = fq2_neg(bj.Y);
+        out[1 << j] = bj;
+    }
+    for (int s = 3; s < 16; s++) {
+        if (!(s & (s - 1))) continue;
+        const int top = 31 - __clz(s);
+        out[s] = gpt_add(out[s & ~(1 << top)], out[1 << top]);
+    }
+}
+
+// the window digit a + 4 b of window w of the GLV halves k0, k1, and the position digit of bit i of
+// the four GLS digits
+FPG_DEV int glv_window(const uint32_t* k0, const uint32_t* k1, int w) {
+    return (int)(((k0[w >> 4] >> (2 * (w & 15))) & 3) | (((k1[w >> 4] >> (2 * (w & 15))) & 3) << 2));
+}
+FPG_DEV int gls_position(const uint32_t (*d)[2], int i) {
+    return bit_of(d[0], i) | (bit_of(d[1], i) << 1) | (bit_of(d[2], i) << 2) | (bit_of(d[3], i) << 3);
 }

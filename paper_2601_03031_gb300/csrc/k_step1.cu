@@ -121,111 +121,164 @@ __global__ void __launch_bounds__(128) k_fold_w(g1a* A, g2a* v, fr* bvec, const 
     }
 }
 
-// Split folds for few points.  The scalar multiplications x_j A[h + i] and x_j^-1 v[h + i] are the
-// longest chain of a round after the challenge; the bases are known one round earlier, so
-// k_fold_pre, run beside the round's Miller loops and final exponentiations, forms the shifted
-// bases 2^(128 p / NP) A[h + i] and 2^(64 p / NP) v[h + i] for p = 1 .. NP - 1 (affine, at
-// A2[(p - 1) FOLD_SPLIT_MAX + t]), and k_fold_s then runs each multiplication as NP chains of 1/NP
-// of the length, part p on the p-th shifted bases (group_ec.cuh, *_mul_part), followed by a tree
-// sum of the parts and the addition of A[i] (v[i]).  Point t = (k, i < h) as in k_fold_w.
-template <int NP>
-__global__ void __launch_bounds__(128) k_fold_pre(const g1a* A, const g2a* v, g1a* A2, g2a* v2, uint32_t K,
-                                                  uint32_t R, uint32_t h, uint32_t nb2) {
-    __shared__ FoldSmemW sm;
-    if (blockIdx.x < nb2) {                                   // one warp per G2 point
+// Comb folds for few points.  The scalar multiplications x_j A[h + i] and x_j^-1 v[h + i] are the
+// longest chain of a round after the challenge, but their bases are known one round earlier.  So
+// k_comb_chain, run beside the round's Miller loops and final exponentiations, forms every
+// 2^i A[h + i'] (i < 128) and 2^i v[h + i'] (i < 64), k_comb_tab the 16-entry table of each G1 window
+// (B = 4^w A: entries a B + b (-phi(B)), a, b < 4) and of each G2 position (B = 2^i v: entries
+// sum_{j in s} (-1)^j psi^j(B)) (group_ec.cuh, fixed-base combs), and k_fold_c, after the challenge,
+// only adds one table entry per window or position: 64 independent additions per point, summed
+// as 16 (G1) or 8 (G2) chains and a tree instead of a chain of 64 doublings and additions.
+// Point t = (k, i < h) as in k_fold_w; the tables of point t start at t 64 16.
+struct CombPtrs {
+    GPt<fq>* chain1;     // [n][128]
+    GPt<fq2>* chain2;    // [n][64]
+    GPt<fq>* tab1;       // [n 64][16]
+    GPt<fq2>* tab2;      // [n 64][16]
+};
+static CombPtrs comb_ptrs(void* base, uint32_t n) {
+    CombPtrs c;
+    uint8_t* p = (uint8_t*)base;
+    c.chain1 = (GPt<fq>*)p;
+    p += (size_t)n * 128 * sizeof(GPt<fq>);
+    c.chain2 = (GPt<fq2>*)p;
+    p += (size_t)n * 64 * sizeof(GPt<fq2>);
+    c.tab1 = (GPt<fq>*)p;
+    p += (size_t)n * 64 * 16 * sizeof(GPt<fq>);
+    c.tab2 = (GPt<fq2>*)p;
+    return c;
+}
+size_t fold_comb_bytes(uint32_t n) {
+    return (size_t)n * 128 * sizeof(GPt<fq>) + (size_t)n * 64 * sizeof(GPt<fq2>) +
+           (size_t)n * 64 * 16 * sizeof(GPt<fq>) + (size_t)n * 64 * 16 * sizeof(GPt<fq2>);
+}
+
+union CombSmem {
+    GEcWs g2[4];
+    GEcs<fq> g1[16];
+};
+// blocks [0, nb2): one warp per G2 point; the others: one 8-lane group per G1 point
+__global__ void __launch_bounds__(128) k_comb_chain(const g1a* A, const g2a* v, uint32_t K, uint32_t R, uint32_t h,
+                                                    uint32_t nb2, GPt<fq>* chain1, GPt<fq2>* chain2) {
+    __shared__ CombSmem sm;
+    const uint64_t n = (uint64_t)K * h;
+    if (blockIdx.x < nb2) {
         const int w = threadIdx.x >> 5, L = threadIdx.x & 31;
         const uint64_t t = (uint64_t)blockIdx.x * 4 + w;
-        if (t >= (uint64_t)K * h) return;                     // warp-uniform
+        if (t >= n) return;                                   // warp-uniform
         const uint64_t hi = (t / h) * R + h + (uint32_t)(t % h);
         GPt<fq2> acc = gec_from_affine_or_inf(v[hi].x, v[hi].y);
-        for (int p = 1; p < NP; p++) {
-            acc = gecw_g2_dbl_n(sm.g2[w], L, acc, 64 / NP);
-            g2a o;
-            gec_to_affine(o.x, o.y, acc);
-            if (L == 0) v2[(p - 1) * FOLD_SPLIT_MAX + t] = o;
+        GPt<fq2>* out = chain2 + t * 64;
+        for (int i = 0; i < 64; i++) {
+            if (i) acc = gecw_dbl(sm.g2[w], L, acc);
+            if (L == 0) out[i] = acc;
         }
         return;
     }
-    const int grp = threadIdx.x >> 3, lane = threadIdx.x & 7;   // one 8-lane group per G1 point
+    const int grp = threadIdx.x >> 3, lane = threadIdx.x & 7;
     const uint64_t t0 = (uint64_t)(blockIdx.x - nb2) * 16 + grp;
-    const bool valid = t0 < (uint64_t)K * h;
-    const uint64_t t = valid ? t0 : 0;
+    const bool valid = t0 < n;
+    const uint64_t t = valid ? t0 : 0;                        // idle groups repeat point 0, store nothing
     const uint64_t hi = (t / h) * R + h + (uint32_t)(t % h);
     GPt<fq> acc = gec_from_affine_or_inf(A[hi].x, A[hi].y);
-    for (int p = 1; p < NP; p++) {
-        acc = gec_g1_dbl_n(sm.g1[grp], lane, acc, 128 / NP);
-        g1a o;
-        gec_to_affine(o.x, o.y, acc);
-        if (valid && lane == 0) A2[(p - 1) * FOLD_SPLIT_MAX + t] = o;
+    GPt<fq>* out = chain1 + t * 128;
+    for (int i = 0; i < 128; i++) {
+        if (i) acc = gec_dbl(sm.g1[grp], lane, acc);
+        if (valid && lane == 0) out[i] = acc;
     }
 }
 
-// G2: NP warps per point (blocks [0, nb2), 4 / NP points each); G1: NP 8-lane groups of one warp per
-// point (16 / NP points per block).  The parts of a point are summed pairwise (every chain keeps the
-// same instruction stream and ends with the whole sum; part 0 stores the result).  Chains past the
-// last point recompute point 0 and store nothing; their read of A[lo] / v[lo] may meet point 0's
-// store from another block, which only changes the discarded result (the arithmetic is bounded for
-// any input).
-struct FoldSmemS {
+// one thread per table: u < n 64 the G1 window table u = t 64 + w, then the G2 position tables
+// (independent tables keep every lane busy, so one lane per table issues far fewer instructions per
+// entry than the lane-parallel engines, which leaves more of the GPU to the round's pairings)
+__global__ void __launch_bounds__(64) k_comb_tab(uint32_t n, const GPt<fq>* chain1, const GPt<fq2>* chain2,
+                                                 GPt<fq>* tab1, GPt<fq2>* tab2) {
+    const uint64_t m = (uint64_t)n * 64, u = gtid();
+    if (u < m) {
+        const uint64_t t = u / 64, w = u % 64;
+        gpt_g1_comb_table(chain1[t * 128 + 2 * w], chain1[t * 128 + 2 * w + 1], tab1 + u * 16);
+    } else if (u < 2 * m) {
+        gpt_g2_comb_table(chain2[u - m], tab2 + (u - m) * 16);
+    }
+}
+
+// blocks [0, n): one G2 point each, 8 warps (warp g adds the entries of positions g, g + 8, ...,
+// g + 56, then a tree over the warps, then v[lo]); the others two G1 points each, 16 groups per
+// point (group g adds windows g, g + 16, g + 32, g + 48, then a tree over the groups, then A[lo]).
+// Every group of a warp runs every addition (the groups of a warp share one instruction stream);
+// additions whose result is not needed are discarded.
+struct FoldSmemC {
     union {
-        GEcW g2[4];
-        GEc<fq> g1[16];
+        GEcWs g2[8];
+        GEcs<fq> g1[32];
     } e;
     union {
-        GPt<fq2> g2[2][4];
+        GPt<fq2> g2[8];
         GPt<fq> g1[2][16];
     } part;
 };
-template <int NP>
-__global__ void __launch_bounds__(128) k_fold_s(g1a* A, g2a* v, fr* bvec, const g1a* A2, const g2a* v2,
-                                                const fr* x_mont, const fr* xinv_mont, uint32_t K, uint32_t R,
-                                                uint32_t h, uint32_t nb2) {
-    __shared__ FoldSmemS sm;
+__global__ void __launch_bounds__(256) k_fold_c(g1a* A, g2a* v, fr* bvec, const fr* x_mont, const fr* xinv_mont,
+                                                uint32_t K, uint32_t R, uint32_t h, const GPt<fq>* tab1,
+                                                const GPt<fq2>* tab2) {
+    __shared__ FoldSmemC sm;
+    const uint64_t n = (uint64_t)K * h;
     uint32_t kw[8];
-    if (blockIdx.x < nb2) {
-        const int w = threadIdx.x >> 5, L = threadIdx.x & 31, part = w % NP;
-        const uint64_t t0 = (uint64_t)blockIdx.x * (4 / NP) + w / NP;
-        const bool valid = t0 < (uint64_t)K * h;
-        const uint64_t t = valid ? t0 : 0;                    // every warp reaches the barriers below
-        const uint64_t k = t / h;
-        const uint32_t i = (uint32_t)(t % h);
-        const uint64_t lo = k * R + i, hi = k * R + h + i;
+    if (blockIdx.x < n) {
+        const int w = threadIdx.x >> 5, L = threadIdx.x & 31;
+        const uint64_t t = blockIdx.x, k = t / h;
+        const uint64_t lo = k * R + (uint32_t)(t % h);
         fr_canon_words(kw, xinv_mont[k]);
-        GPt<fq2> acc = gecw_g2_mul_part<NP>(sm.e.g2[w], L, part ? v2[(part - 1) * FOLD_SPLIT_MAX + t] : v[hi], kw,
-                                            part);
-        for (int sh = 1, b = 0; sh < NP; sh <<= 1, b ^= 1) {
-            if (L == 0) sm.part.g2[b][w] = acc;
-            __syncthreads();
-            acc = gecw_add(sm.e.g2[w], L, acc, sm.part.g2[b][w ^ sh]);
+        uint32_t d[4][2];
+        gls_digits(d, kw);
+        const GPt<fq2>* tb = tab2 + t * 64 * 16;
+        GPt<fq2> acc = tb[w * 16 + gls_position(d, w)];
+        for (int j = 1; j < 8; j++) {
+            const int i = w + 8 * j;
+            acc = gecw_add(sm.e.g2[w], L, acc, tb[i * 16 + gls_position(d, i)]);
         }
-        acc = gecw_add(sm.e.g2[w], L, acc, gec_from_affine_or_inf(v[lo].x, v[lo].y));
-        g2a o;
-        gec_to_affine(o.x, o.y, acc);
-        __syncthreads();                                      // v[lo] read by every part before the store
-        if (valid && part == 0 && L == 0) v[lo] = o;
+        for (int sh = 4; sh >= 1; sh >>= 1) {
+            __syncthreads();
+            if (L == 0) sm.part.g2[w] = acc;
+            __syncthreads();
+            if (w < sh) acc = gecw_add(sm.e.g2[w], L, acc, sm.part.g2[w + sh]);
+        }
+        if (w == 0) {
+            acc = gecw_add(sm.e.g2[0], L, acc, gec_from_affine_or_inf(v[lo].x, v[lo].y));
+            g2a o;
+            gec_to_affine(o.x, o.y, acc);
+            __syncwarp();
+            if (L == 0) v[lo] = o;
+        }
         return;
     }
-    const int grp = threadIdx.x >> 3, lane = threadIdx.x & 7, part = grp % NP;
-    const uint64_t t0 = (uint64_t)(blockIdx.x - nb2) * (16 / NP) + grp / NP;
-    const bool valid = t0 < (uint64_t)K * h;
-    const uint64_t t = valid ? t0 : 0;
+    const int grp = threadIdx.x >> 3, lane = threadIdx.x & 7, half = grp >> 4, g = grp & 15;
+    const uint64_t t0 = (blockIdx.x - n) * 2 + half;
+    const bool valid = t0 < n;
+    const uint64_t t = valid ? t0 : 0;                        // an idle half repeats point 0, stores nothing
     const uint64_t k = t / h;
     const uint32_t i = (uint32_t)(t % h);
     const uint64_t lo = k * R + i, hi = k * R + h + i;
     fr_canon_words(kw, x_mont[k]);
-    GPt<fq> acc = gec_g1_mul_part<NP>(sm.e.g1[grp], lane, part ? A2[(part - 1) * FOLD_SPLIT_MAX + t] : A[hi], kw,
-                                      part);
-    for (int sh = 1, b = 0; sh < NP; sh <<= 1, b ^= 1) {
-        gsync();
-        if (lane == 0) sm.part.g1[b][grp] = acc;
-        gsync();
-        acc = gec_add(sm.e.g1[grp], lane, acc, sm.part.g1[b][grp ^ sh]);
+    uint32_t k1[5], k0[4];
+    div_by_const<4, 5>(k1, k0, kw, GLV_D, GLV_BARRETT);
+    const GPt<fq>* tb = tab1 + t * 64 * 16;
+    GPt<fq> acc = tb[g * 16 + glv_window(k0, k1, g)];
+    for (int j = 1; j < 4; j++) {
+        const int w = g + 16 * j;
+        acc = gec_add(sm.e.g1[grp], lane, acc, tb[w * 16 + glv_window(k0, k1, w)]);
+    }
+    for (int sh = 8; sh >= 1; sh >>= 1) {
+        __syncthreads();
+        if (lane == 0) sm.part.g1[half][g] = acc;
+        __syncthreads();
+        const GPt<fq> r = gec_add(sm.e.g1[grp], lane, acc, sm.part.g1[half][g < sh ? g + sh : g]);
+        if (g < sh) acc = r;
     }
     acc = gec_add(sm.e.g1[grp], lane, acc, gec_from_affine_or_inf(A[lo].x, A[lo].y));
     g1a o;
     gec_to_affine(o.x, o.y, acc);
-    gsync();                                                  // A[lo] read by every part before the store
-    if (valid && part == 0 && lane == 0) {
+    __syncthreads();                                          // every read of A[lo] before the store
+    if (valid && g == 0 && lane == 0) {
         A[lo] = o;
         bvec[lo] = fr_add(bvec[lo], fr_mul(bvec[hi], xinv_mont[k]));
     }
@@ -483,35 +536,25 @@ uint64_t step1_miller_g(const void* A, const void* v, uint32_t K, uint32_t R, ui
     round_miller_w(A, v, K, R, h, ml_out, s);      // few pairs: one warp or block each, for latency
     return n;
 }
-// parts per fold multiplication for n points: 4 while the 4 n warps of the G2 chains and n warps of
-// the G1 chains fit the GPU at once, else 2
-static int fold_parts(uint64_t n) { return n <= FOLD_SPLIT4_MAX ? 4 : 2; }
-void step1_fold_pre(const void* A, const void* v, void* A2, void* v2, uint32_t K, uint32_t R, uint32_t h,
+void step1_fold_pre(const void* A, const void* v, void* comb, uint32_t n_max, uint32_t K, uint32_t R, uint32_t h,
                     cudaStream_t s) {
-    const uint32_t n = K * h, nb2 = (n + 3) / 4, nb1 = (n + 15) / 16;
-    if (fold_parts(n) == 4)
-        FP_KERNEL("k_fold_pre", s, k_fold_pre<4><<<nb2 + nb1, 128, 0, s>>>((const g1a*)A, (const g2a*)v, (g1a*)A2,
-                                                                           (g2a*)v2, K, R, h, nb2));
-    else
-        FP_KERNEL("k_fold_pre", s, k_fold_pre<2><<<nb2 + nb1, 128, 0, s>>>((const g1a*)A, (const g2a*)v, (g1a*)A2,
-                                                                           (g2a*)v2, K, R, h, nb2));
+    const uint32_t n = K * h;
+    if (n > n_max) return;
+    const CombPtrs c = comb_ptrs(comb, n_max);
+    const uint32_t nb2 = (n + 3) / 4, nb1 = (n + 15) / 16;
+    FP_KERNEL("k_comb_chain", s, k_comb_chain<<<nb2 + nb1, 128, 0, s>>>((const g1a*)A, (const g2a*)v, K, R, h, nb2,
+                                                                       c.chain1, c.chain2));
+    FP_KERNEL("k_comb_tab", s, k_comb_tab<<<grid_for((uint64_t)n * 128, 64), 64, 0, s>>>(n, c.chain1, c.chain2,
+                                                                                       c.tab1, c.tab2));
 }
 void step1_fold(void* A, void* v, void* bvec, const void* x_mont, const void* xinv_mont, uint32_t K, uint32_t R,
-                uint32_t h, const void* A2, const void* v2, cudaStream_t s) {
-    if (A2 && (uint64_t)K * h <= FOLD_SPLIT_MAX) {     // shifted bases ready: shorter chains
+                uint32_t h, const void* comb, uint32_t n_max, cudaStream_t s) {
+    if (comb && (uint64_t)K * h <= n_max) {            // comb tables ready: table entries only
         const uint32_t n = K * h;
-        const int np = fold_parts(n);
-        const uint32_t nb2 = (n * np + 3) / 4, nb1 = (n * np + 15) / 16;
-        if (np == 4)
-            FP_KERNEL("k_fold_s", s, k_fold_s<4><<<nb2 + nb1, 128, 0, s>>>((g1a*)A, (g2a*)v, (fr*)bvec,
-                                                                         (const g1a*)A2, (const g2a*)v2,
-                                                                         (const fr*)x_mont, (const fr*)xinv_mont,
-                                                                         K, R, h, nb2));
-        else
-            FP_KERNEL("k_fold_s", s, k_fold_s<2><<<nb2 + nb1, 128, 0, s>>>((g1a*)A, (g2a*)v, (fr*)bvec,
-                                                                         (const g1a*)A2, (const g2a*)v2,
-                                                                         (const fr*)x_mont, (const fr*)xinv_mont,
-                                                                         K, R, h, nb2));
+        const CombPtrs c = comb_ptrs(const_cast<void*>(comb), n_max);
+        FP_KERNEL("k_fold_c", s, k_fold_c<<<n + (n + 1) / 2, 256, 0, s>>>((g1a*)A, (g2a*)v, (fr*)bvec,
+                                                                         (const fr*)x_mont, (const fr*)xinv_mont, K,
+                                                                         R, h, c.tab1, c.tab2));
         return;
     }
     if ((uint64_t)K * h <= engine_limits().fold_warp_max) {   // few points: a warp per G2 point, 8 lanes per G1

@@ -98,14 +98,16 @@ uint64_t step1_miller_g(const void* A, const void* v, uint32_t K, uint32_t R, ui
                         cudaStream_t s);
 void step1_g1_out(const void* sp_g1j, uint32_t K, int j, void* blocks, size_t bopen_len, cudaStream_t s);
 void step1_gt_out(const void* ml_fq12, uint32_t K, int j, void* blocks, size_t bopen_len, cudaStream_t s);
-// Round j's folds.  With A2 / v2 (the shifted bases from step1_fold_pre: 3 FOLD_SPLIT_MAX points
-// each, for rounds of at most FOLD_SPLIT_MAX points) each scalar multiplication runs as four chains
-// of a quarter of the length (at most FOLD_SPLIT4_MAX points) or two of half the length.
-constexpr uint32_t FOLD_SPLIT_MAX = 256, FOLD_SPLIT4_MAX = 128;
-void step1_fold_pre(const void* A, const void* v, void* A2, void* v2, uint32_t K, uint32_t R, uint32_t h,
+// Round j's folds.  For rounds of at most FOLD_COMB_MAX points, step1_fold_pre forms the comb tables
+// of the round's bases in `comb` (fold_comb_bytes(n_max) bytes for up to n_max points) beside the
+// round's pairings, and step1_fold then adds one table entry per window; other rounds run the
+// whole scalar multiplications after the challenge.
+constexpr uint32_t FOLD_COMB_MAX = 256;
+size_t fold_comb_bytes(uint32_t n_max);
+void step1_fold_pre(const void* A, const void* v, void* comb, uint32_t n_max, uint32_t K, uint32_t R, uint32_t h,
                     cudaStream_t s);
 void step1_fold(void* A, void* v, void* bvec, const void* x_mont, const void* xinv_mont, uint32_t K, uint32_t R,
-                uint32_t h, const void* A2, const void* v2, cudaStream_t s);
+                uint32_t h, const void* comb, uint32_t n_max, cudaStream_t s);
 // Look-ahead rounds (lookahead.cuh): round j's record from round j-1's state (half-length h = 2 h2)
 // and challenge.  Before the challenge: la_miller (the 8 K h2 Miller values by class; then pairwise
 // products to 8 K and their final exponentiations, fe), la_sparse (the 6 K (4 h2) G1 terms; then

@@ -22,6 +22,7 @@ struct Rec { const char* name; cudaEvent_t a, b; };
 std::vector<Rec> g_open;
 std::vector<cudaEvent_t> g_pool;
 thread_local Rec t_cur{nullptr, nullptr, nullptr};
+std::vector<std::pair<const char*, float>> g_each;   // every timed launch in issue order, until listed
 
 cudaEvent_t get_event() {
     if (!g_pool.empty()) { cudaEvent_t e = g_pool.back(); g_pool.pop_back(); return e; }
@@ -68,6 +69,7 @@ size_t fp_profile_report(char* out, size_t cap) {
         e.second += ms;
         g_pool.push_back(r.a);
         g_pool.push_back(r.b);
+        g_each.push_back({r.name, ms});
     }
     g_open.clear();
     std::string txt;
@@ -82,6 +84,25 @@ size_t fp_profile_report(char* out, size_t cap) {
         memcpy(out, txt.data(), n);
         out[n] = 0;
         agg.clear();
+    }
+    return txt.size() + 1;
+}
+// One line per timed launch, "name ms", in the order the launches were issued, for the launches
+// that fp_profile_report has synchronised; cleared by a call that writes them out.
+size_t fp_profile_launches(char* out, size_t cap) {
+    using namespace fpk;
+    std::lock_guard<std::mutex> lk(g_mu);
+    std::string txt;
+    char line[256];
+    for (auto& e : g_each) {
+        snprintf(line, sizeof line, "%s %.6f\n", e.first, (double)e.second);
+        txt += line;
+    }
+    if (out && cap) {
+        size_t n = txt.size() < cap - 1 ? txt.size() : cap - 1;
+        memcpy(out, txt.data(), n);
+        out[n] = 0;
+        g_each.clear();
     }
     return txt.size() + 1;
 }

@@ -444,7 +444,8 @@ namespace {
 // outputs, the challenges and the fast-verification proof of v_l
 struct Step1Bufs {
     void *A, *v, *bvec, *xprev, *x_mont, *xinv_mont, *xinv_all, *ml, *ml2, *sp, *sp2, *pcoef, *q;
-    void *A2, *v2;                       // shifted fold bases of rounds with few points
+    void* comb = nullptr;                // comb tables of rounds with few points (step1_fold_pre)
+    uint32_t comb_n = 0;                 // points they hold
     void *wt = nullptr, *wt2 = nullptr, *wscr = nullptr;
     MsmShape wsh{};
     bool w_msm = false;
@@ -467,8 +468,8 @@ Step1Bufs step1_bufs(const fp_pp* pp, uint32_t Kc, Alloc&& T) {
     B.sp2 = T((KR / 2 + 1) * G1J_BYTES);
     B.pcoef = T((size_t)Kc * (2 * R - 1) * FR_BYTES);
     B.q = T((size_t)Kc * 2 * R * FR_BYTES);
-    B.A2 = T((size_t)3 * FOLD_SPLIT_MAX * G1A_BYTES);
-    B.v2 = T((size_t)3 * FOLD_SPLIT_MAX * G2A_BYTES);
+    B.comb_n = (uint32_t)std::min<uint64_t>(FOLD_COMB_MAX, KR / 2);
+    if (B.comb_n) B.comb = T(fold_comb_bytes(B.comb_n));
     // W proofs: one batched G2 MSM over the shared bases g2^{beta^i} when many blocks share them,
     // else one scalar multiplication per term and pairwise sums (with few batches the MSM's bucket
     // reduction runs nearly serially per window)
@@ -525,10 +526,10 @@ void step1_rounds(const fp_pp* pp, uint32_t k0, uint32_t Kc, uint32_t b, const S
     for (int j = 1; j <= lr; j++) {
         const uint32_t h = R >> j;
         check(cudaEventRecord(ev_folded, s1), "event");
-        const bool split = (uint64_t)Kc * h <= FOLD_SPLIT_MAX;
+        const bool split = (uint64_t)Kc * h <= B.comb_n;
         if (split) {
             check(cudaStreamWaitEvent(s4, ev_folded, 0), "wait");
-            step1_fold_pre(B.A, B.v, B.A2, B.v2, Kc, R, h, s4);
+            step1_fold_pre(B.A, B.v, B.comb, B.comb_n, Kc, R, h, s4);
             check(cudaEventRecord(ev_pre, s4), "event");
         }
         check(cudaStreamWaitEvent(s3, ev_folded, 0), "wait");
@@ -542,8 +543,7 @@ void step1_rounds(const fp_pp* pp, uint32_t k0, uint32_t Kc, uint32_t b, const S
         check(cudaStreamWaitEvent(s1, ev_sparse, 0), "wait");
         step1_challenge(blocks1, blen, Kc, j, B.xprev, B.x_mont, B.xinv_mont, B.xinv_all, lr, s1);
         if (split) check(cudaStreamWaitEvent(s1, ev_pre, 0), "wait");
-        step1_fold(B.A, B.v, B.bvec, B.x_mont, B.xinv_mont, Kc, R, h, split ? B.A2 : nullptr,
-                   split ? B.v2 : nullptr, s1);
+        step1_fold(B.A, B.v, B.bvec, B.x_mont, B.xinv_mont, Kc, R, h, split ? B.comb : nullptr, B.comb_n, s1);
     }
     step1_kzg(B.A, B.v, B.xprev, B.xinv_all, Kc, R, lr, blocks1, blen, B.pcoef, B.q, s1);
     uint8_t* w_out = blocks1 + (size_t)lr * ROUND_BYTES + G1_SER + G2_SER;
@@ -607,18 +607,18 @@ void step1_rounds_la(const fp_pp* pp, uint32_t k0, uint32_t Kc, uint32_t b, cons
     // round j's fold on sF (after x_j, the shifted bases and the snapshot of S_j for round j + 1)
     auto fold = [&](int j) {
         const uint32_t h = R >> j;
-        const bool split = (uint64_t)Kc * h <= FOLD_SPLIT_MAX;
+        const bool split = (uint64_t)Kc * h <= B.comb_n;
         wait(sF, ev_x[j]);
         if (split) wait(sF, ev_pre[j]);
         if (j + 1 <= lr) wait(sF, ev_snap[j + 1]);
-        step1_fold(B.A, B.v, B.bvec, xm(j), xim(j), Kc, R, h, split ? B.A2 : nullptr, split ? B.v2 : nullptr, sF);
+        step1_fold(B.A, B.v, B.bvec, xm(j), xim(j), Kc, R, h, split ? B.comb : nullptr, B.comb_n, sF);
         ev_S[j + 1] = rec(sF);
     };
     auto fold_pre = [&](int j, cudaEvent_t ready) {
         const uint32_t h = R >> j;
-        if ((uint64_t)Kc * h > FOLD_SPLIT_MAX) return;
+        if ((uint64_t)Kc * h > B.comb_n) return;
         wait(s4, ready);
-        step1_fold_pre(B.A, B.v, B.A2, B.v2, Kc, R, h, s4);
+        step1_fold_pre(B.A, B.v, B.comb, B.comb_n, Kc, R, h, s4);
         ev_pre[j] = rec(s4);
     };
 

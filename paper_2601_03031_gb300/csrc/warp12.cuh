@@ -16,6 +16,7 @@
 //   Frobenius p / p^2:      20 / 10 Fq products by constants
 #pragma once
 #include "pairing.cuh"
+#include "fq_split.cuh"
 
 struct W12 {
     fq p[108];          // products of the current operation
@@ -99,8 +100,11 @@ FPG_NOINL void w_mul(W12& W, fq* out, const fq* a, const fq* b) {
 template <int NW>
 FPG_DEV void w_cyc_sqr(W12& W, fq* out, const fq* z) {
     const int L = w_lane<NW>();
-    if (L < 21) {
-        const int p = L / 7, r = L - 7 * p;
+    // the block engine splits each product over its four warps (fq_split.cuh): lane t of every warp
+    // forms the operands of product t (lanes t >= 21 those of product 0, discarded)
+    if (NW == 4 || L < 21) {
+        const int tp = NW == 4 ? ((L & 31) < 21 ? (L & 31) : 0) : L;
+        const int p = tp / 7, r = tp - 7 * p;
         const fq a0 = z[2 * p], a1 = z[2 * p + 1], b0 = z[2 * p + 6], b1 = z[2 * p + 7];
         const bool ua = r < 2 || r == 4 || r == 5 || r == 6;            // x built from a
         const fq xs = fq_select(ua, a0, b0), xt = fq_select(ua, a1, b1);
@@ -113,7 +117,12 @@ FPG_DEV void w_cyc_sqr(W12& W, fq* out, const fq* z) {
         const fq ydiff = fq_sub(ys, yt), ysum = fq_add(ys, yt);
         const fq y = fq_select(r == 0 || r == 2, ydiff,
                                fq_select(r == 6, ysum, fq_select(r == 4, b0, fq_select(r == 1, a1, b1))));
-        W.p[L] = fq_mul(x, y);
+        if (NW == 4) {
+            const fq m = fq_mul_split(x, y);
+            if (L < 21) W.p[L] = m;
+        } else {
+            W.p[L] = fq_mul(x, y);
+        }
     }
     wsync<NW>();
     if (NW == 4) {
@@ -494,7 +503,8 @@ FPG_NOINL void wm_dbl(WMill& S, const fq& m3x, const fq& y2) {
     wsync<NW>();
     // round B
     if (NW == 4) {
-        if (L < 15) {
+        {                                           // 15 products, each split over the four warps
+            const int t = (L & 31) < 15 ? (L & 31) : 0;
             const fq* XX = S.v;
             const fq* YY = S.v + 2;
             const fq* YZ = S.v + 6;
@@ -502,15 +512,16 @@ FPG_NOINL void wm_dbl(WMill& S, const fq& m3x, const fq& y2) {
             const fq* a;
             const fq* b;
             int kind, mode;
-            if (L < 2) { a = b = XX; kind = L; mode = 2; }                           // m3x XX
-            else if (L < 4) { a = b = YZ; kind = L - 2; mode = 2; }                  // y2 YZ
-            else if (L < 7) { a = XY; b = S.v + 18; kind = L - 4; mode = 0; }        // XY (YY - 9 bz)
-            else if (L < 9) { a = b = S.v + 20; kind = L - 7; mode = 1; }            // (YY + 9 bz)^2
-            else if (L < 12) { a = S.v + 24; b = S.v + 26; kind = L - 9; mode = 0; } // 108 bz^2
-            else { a = YY; b = YZ; kind = L - 12; mode = 0; }                        // YY YZ
+            if (t < 2) { a = b = XX; kind = t; mode = 2; }                           // m3x XX
+            else if (t < 4) { a = b = YZ; kind = t - 2; mode = 2; }                  // y2 YZ
+            else if (t < 7) { a = XY; b = S.v + 18; kind = t - 4; mode = 0; }        // XY (YY - 9 bz)
+            else if (t < 9) { a = b = S.v + 20; kind = t - 7; mode = 1; }            // (YY + 9 bz)^2
+            else if (t < 12) { a = S.v + 24; b = S.v + 26; kind = t - 9; mode = 0; } // 108 bz^2
+            else { a = YY; b = YZ; kind = t - 12; mode = 0; }                        // YY YZ
             fq x, y;
-            prod_ops(x, y, a, b, kind, mode, fq_select(L < 2, m3x, y2));
-            S.p[L] = fq_mul(x, y);
+            prod_ops(x, y, a, b, kind, mode, fq_select(t < 2, m3x, y2));
+            const fq m = fq_mul_split(x, y);
+            if (L < 15) S.p[L] = m;
         }
         wsync<NW>();
         // the line (warp 0) and 2T (X' on warp 1, Y' on warp 2, Z' on warp 3)
@@ -596,11 +607,18 @@ FPG_NOINL void wm_add(WMill& S, const fq& mxP, const fq& yP) {
     const fq* Z = S.T + 4;
     const fq* xQ = S.Q;
     const fq* yQ = S.Q + 2;
-    // round A: yQ Z, xQ Z
-    if (L < 6) {
+    // round A: yQ Z, xQ Z (the block engine splits each product over its four warps: lane t of every
+    // warp forms the operands of product t)
+    if (NW == 4 || L < 6) {
+        const int t = NW == 4 ? ((L & 31) < 6 ? (L & 31) : 0) : L;
         fq x, y;
-        kara_ops(x, y, L < 3 ? yQ : xQ, Z, L % 3);
-        S.p[L] = fq_mul(x, y);
+        kara_ops(x, y, t < 3 ? yQ : xQ, Z, t % 3);
+        if (NW == 4) {
+            const fq m = fq_mul_split(x, y);
+            if (L < 6) S.p[L] = m;
+        } else {
+            S.p[L] = fq_mul(x, y);
+        }
     }
     wsync<NW>();
     if (L < 4) {                                    // theta = Y - yQ Z, lambda = X - xQ Z
@@ -611,19 +629,25 @@ FPG_NOINL void wm_add(WMill& S, const fq& mxP, const fq& yP) {
     const fq* th = S.v;
     const fq* la = S.v + 2;
     // round B: theta xQ, lambda yQ, -theta xP, lambda yP, theta^2, lambda^2
-    if (L < 14) {
+    if (NW == 4 || L < 14) {
+        const int t = NW == 4 ? ((L & 31) < 14 ? (L & 31) : 0) : L;
         const fq* a;
         const fq* b;
         int kind, mode;
-        if (L < 3) { a = th; b = xQ; kind = L; mode = 0; }
-        else if (L < 6) { a = la; b = yQ; kind = L - 3; mode = 0; }
-        else if (L < 8) { a = b = th; kind = L - 6; mode = 2; }
-        else if (L < 10) { a = b = la; kind = L - 8; mode = 2; }
-        else if (L < 12) { a = b = th; kind = L - 10; mode = 1; }
-        else { a = b = la; kind = L - 12; mode = 1; }
+        if (t < 3) { a = th; b = xQ; kind = t; mode = 0; }
+        else if (t < 6) { a = la; b = yQ; kind = t - 3; mode = 0; }
+        else if (t < 8) { a = b = th; kind = t - 6; mode = 2; }
+        else if (t < 10) { a = b = la; kind = t - 8; mode = 2; }
+        else if (t < 12) { a = b = th; kind = t - 10; mode = 1; }
+        else { a = b = la; kind = t - 12; mode = 1; }
         fq x, y;
-        prod_ops(x, y, a, b, kind, mode, fq_select(L < 8, mxP, yP));
-        S.p[L] = fq_mul(x, y);
+        prod_ops(x, y, a, b, kind, mode, fq_select(t < 8, mxP, yP));
+        if (NW == 4) {
+            const fq m = fq_mul_split(x, y);
+            if (L < 14) S.p[L] = m;
+        } else {
+            S.p[L] = fq_mul(x, y);
+        }
     }
     wsync<NW>();
     if (L < 10) {
@@ -679,8 +703,8 @@ FPG_NOINL void wm_add(WMill& S, const fq& mxP, const fq& yP) {
     const fq* E = S.v + 8;
     const fq* Fv = S.v + 10;
     const fq* G = S.v + 12;
-    if (L >= 16 && L < 28) {
-        const int u = L - 16, which = u / 3;
+    if (NW == 4 || (L >= 16 && L < 28)) {
+        const int u = NW == 4 ? ((L & 31) < 12 ? (L & 31) : 0) : L - 16, which = u / 3;
         fq H[2], GH[2];
         for (int e = 0; e < 2; e++) {
             H[e] = fq_sub(fq_add(E[e], Fv[e]), fq_dbl(G[e]));
@@ -689,7 +713,12 @@ FPG_NOINL void wm_add(WMill& S, const fq& mxP, const fq& yP) {
         fq x, y;
         kara_ops(x, y, which == 0 ? la : (which == 1 ? th : (which == 2 ? Y : Z)),
                  which == 0 ? H : (which == 1 ? GH : E), u % 3);
-        S.p[u] = fq_mul(x, y);
+        if (NW == 4) {
+            const fq m = fq_mul_split(x, y);
+            if (L < 12) S.p[L] = m;
+        } else {
+            S.p[u] = fq_mul(x, y);
+        }
     }
     wsync<NW>();
     if (L < 6) {

@@ -52,6 +52,18 @@ GEcW g_g2;
 }  // namespace
 
 extern "C" {
+// the block-split Fq product (fq_split.cuh) of 32 operand pairs (canonical integers, 12 little-endian
+// words each, below p; not Montgomery form): out[w 32 + t] = x_t y_t 2^-384 mod p as warp w's lane t
+// holds it
+void emu_fq_mul_split(const uint32_t* x, const uint32_t* y, uint32_t* out) {
+    lanes(128, [&] {
+        const int L = (int)threadIdx.x, t = L & 31;
+        fq a, b;
+        for (int j = 0; j < 12; j++) { a.v[j] = x[12 * t + j]; b.v[j] = y[12 * t + j]; }
+        const fq r = fq_mul_split(a, b);
+        for (int j = 0; j < 12; j++) out[12 * L + j] = r.v[j];
+    });
+}
 void emu_miller(int nw, const uint8_t* p, const uint8_t* q, uint8_t* out) {
     const g1a P = be_g1(p);
     const g2a Q = be_g2(q);
@@ -115,6 +127,60 @@ void emu_g2_mul(const uint8_t* q, const uint32_t* k, int np, int part, uint8_t* 
                            : np == 2 ? gecw_g2_mul_part<2>(g_g2, L, Q, k, part)
                                      : gecw_g2_mul_proj(g_g2, L, Q, k);
         if (L == 0) r = x;
+    });
+    g2a a;
+    gec_to_affine(a.x, a.y, r);
+    g2a_to_be(out, a);
+}
+// k P through the fixed-base comb of Step 1's folds: the chain 2^i P (i < 128) and the sum of one
+// entry per window on an 8-lane group, the 64 window tables (gpt_g1_comb_table) on one thread
+void emu_g1_comb(const uint8_t* p, const uint32_t* k, uint8_t* out) {
+    const g1a P = be_g1(p);
+    static GPt<fq> chain[128], tab[64 * 16];
+    GPt<fq> r;
+    lanes(8, [&] {
+        const int L = (int)threadIdx.x;
+        GPt<fq> acc = gec_from_affine_or_inf(P.x, P.y);
+        for (int i = 0; i < 128; i++) {
+            if (i) acc = gec_dbl(g_g1, L, acc);
+            if (L == 0) chain[i] = acc;
+            __syncwarp();
+        }
+        if (L == 0)
+            for (int w = 0; w < 64; w++) gpt_g1_comb_table(chain[2 * w], chain[2 * w + 1], tab + 16 * w);
+        __syncwarp();
+        uint32_t k1[5], k0[4];
+        div_by_const<4, 5>(k1, k0, k, GLV_D, GLV_BARRETT);
+        GPt<fq> s = gec_identity<fq>();
+        for (int w = 0; w < 64; w++) s = gec_add(g_g1, L, s, tab[16 * w + glv_window(k0, k1, w)]);
+        if (L == 0) r = s;
+    });
+    g1a a;
+    gec_to_affine(a.x, a.y, r);
+    g1a_to_be(out, a);
+}
+// k Q through the comb on G2: the chain 2^i Q (i < 64) and the sum of one entry per position on one
+// warp, the 64 position tables (gpt_g2_comb_table) on one thread
+void emu_g2_comb(const uint8_t* q, const uint32_t* k, uint8_t* out) {
+    const g2a Q = be_g2(q);
+    static GPt<fq2> chain[64], tab[64 * 16];
+    GPt<fq2> r;
+    lanes(32, [&] {
+        const int L = (int)threadIdx.x;
+        GPt<fq2> acc = gec_from_affine_or_inf(Q.x, Q.y);
+        for (int i = 0; i < 64; i++) {
+            if (i) acc = gecw_dbl(g_g2, L, acc);
+            if (L == 0) chain[i] = acc;
+            __syncwarp();
+        }
+        if (L == 0)
+            for (int i = 0; i < 64; i++) gpt_g2_comb_table(chain[i], tab + 16 * i);
+        __syncwarp();
+        uint32_t d[4][2];
+        gls_digits(d, k);
+        GPt<fq2> s = gec_identity<fq2>();
+        for (int i = 0; i < 64; i++) s = gecw_add(g_g2, L, s, tab[16 * i + gls_position(d, i)]);
+        if (L == 0) r = s;
     });
     g2a a;
     gec_to_affine(a.x, a.y, r);

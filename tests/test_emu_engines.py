@@ -39,8 +39,8 @@ def emu(tmp_path_factory):
     subprocess.check_call([gxx, "-std=c++20", "-O1", "-shared", "-fPIC", f"-I{CSRC}", "-o", lib,
                            os.path.join(HERE, "emu", "engines.cpp")])
     L = ctypes.CDLL(lib)
-    for n in ("emu_miller", "emu_final_exp", "emu_gt_pow", "emu_g1_mul", "emu_g1_dbl_n", "emu_g2_mul",
-              "emu_g2_dbl_n"):
+    for n in ("emu_fq_mul_split", "emu_miller", "emu_final_exp", "emu_gt_pow", "emu_g1_mul", "emu_g1_dbl_n", "emu_g2_mul",
+              "emu_g2_dbl_n", "emu_g1_comb", "emu_g2_comb"):
         getattr(L, n).restype = None
     return L
 
@@ -62,6 +62,28 @@ def g2_mul(L, Q, k, np_=1, part=0):
     o = ctypes.create_string_buffer(192)
     L.emu_g2_mul(Q, words(k), np_, part, o)
     return o.raw
+
+
+def test_fq_product_split_over_four_warps(emu):
+    """fq_split.cuh: every warp's lane t ends with x_t y_t 2^-384 mod p, canonical, for random operands
+    and the edges 0, 1, p - 1, p - 2, 2^380, 2^381 - 1 mod p (the largest T and S the bounds allow)."""
+    P = O.const_p()
+    rnd = random.Random(23)
+    edges = [0, 1, P - 1, P - 2, 1 << 380, ((1 << 381) - 1) % P, (1 << 32) - 1, 1 << 352]
+    pairs = [(a, b) for a in edges for b in (P - 1, edges[-3], 1)]
+    pairs += [(rnd.randrange(P), rnd.randrange(P)) for _ in range(96 - len(pairs))]
+    rinv = pow(1 << 384, -1, P)
+    for i in range(0, len(pairs), 32):
+        batch = pairs[i:i + 32]
+        batch += [(0, 0)] * (32 - len(batch))
+        xs = (ctypes.c_uint32 * 384)(*[(a >> (32 * j)) & 0xFFFFFFFF for a, _ in batch for j in range(12)])
+        ys = (ctypes.c_uint32 * 384)(*[(b >> (32 * j)) & 0xFFFFFFFF for _, b in batch for j in range(12)])
+        out = (ctypes.c_uint32 * (128 * 12))()
+        emu.emu_fq_mul_split(xs, ys, out)
+        for L in range(128):
+            a, b = batch[L & 31]
+            got = sum(out[12 * L + j] << (32 * j) for j in range(12))
+            assert got == a * b * rinv % P, (L, hex(a), hex(b))
 
 
 @pytest.mark.parametrize("nw", [1, 4])
@@ -140,3 +162,25 @@ def test_g2_scalar_mul_whole_and_split(emu):
                 acc = O.g2_add(acc, g2_mul(emu, base, k, np_, part))
             assert acc == e, (k, np_)
     assert g2_mul(emu, bytes(192), rnd.randrange(R), 2, 1) == bytes(192)
+
+
+def test_fixed_base_combs(emu):
+    """Step 1's comb folds (group_ec.cuh, k_step1.cu): the chain of doublings, the window tables of
+    G1 (GLV, 2-bit windows, entries a B - b phi(B)) and the position tables of G2 (GLS, entries
+    sum (-1)^j psi^j(B)), and the sum of one entry per window give k P and k Q as the oracle's
+    double-and-add does, for edge and random scalars and the identity."""
+    rnd = random.Random(41)
+    P = O.g1_mul(O.g1_gen(), rnd.randrange(1, R))
+    Q = O.g2_mul(O.g2_gen(), rnd.randrange(1, R))
+    scalars = [0, 1, 2, R - 1, (1 << 128) - 1, rnd.randrange(R), rnd.randrange(R)]
+    for k in scalars:
+        o = ctypes.create_string_buffer(96)
+        emu.emu_g1_comb(P, words(k), o)
+        assert o.raw == O.g1_mul(P, k), hex(k)
+    for k in scalars[:5]:
+        o = ctypes.create_string_buffer(192)
+        emu.emu_g2_comb(Q, words(k), o)
+        assert o.raw == O.g2_mul(Q, k), hex(k)
+    o = ctypes.create_string_buffer(96)
+    emu.emu_g1_comb(O.g1_mul(O.g1_gen(), 0), words(5), o)
+    assert o.raw == O.g1_mul(O.g1_gen(), 0)
