@@ -57,6 +57,21 @@ def _cyc_exp_rounds(e: int) -> int:
     return (e.bit_length() - 1) + (bin(e).count("1") - 1)
 
 
+def _wnaf4_exp_rounds(e: int) -> int:
+    """Product rounds of an exponentiation by e on its width-4 NAF: base^2, 3, 5, 7, then a squaring
+    per digit below the top one and a product per nonzero digit below it."""
+    digits = []
+    while e:
+        d = 0
+        if e & 1:
+            d = e % 16
+            d = d - 16 if d >= 8 else d
+            e -= d
+        digits.append(d)
+        e >>= 1
+    return 4 + (len(digits) - 1) + sum(1 for d in digits[:-1] if d)
+
+
 X_ABS = 0xd201000000010000                   # |x| of BLS12-381 (x < 0)
 H1 = (X_ABS + 1) ** 2 // 3                   # h1 = (x - 1)^2 / 3
 # Sequential Fq-product rounds on one launch's critical path in the lane-parallel engines: every
@@ -66,7 +81,7 @@ H1 = (X_ABS + 1) ** 2 // 3                   # h1 = (x - 1)^2 / 3
 CRITICAL_ROUNDS = {
     # easy part 8 rounds (n, two Frobenius^2, u, n u, c^2, c^2 u, t) + 5 products of the Fq2 inverse,
     # g 2, hard part h1 and 3 |x| cyclotomic exponentiations + 6 Frobenius / product rounds
-    "k_final_exp_c": 8 + 5 + 2 + _cyc_exp_rounds(H1) + 3 * _cyc_exp_rounds(X_ABS) + 6,
+    "k_final_exp_c": 8 + 5 + 2 + _wnaf4_exp_rounds(H1) + 3 * _cyc_exp_rounds(X_ABS) + 6,
     # 63 doubling steps of 3 rounds, 5 addition steps of 4
     "k_round_miller_c": 63 * 3 + 5 * 4,
     # G1 by 8-lane groups, 2-bit joint GLV windows: 13 table formulas + 64 x (2 doublings + 1 addition),

@@ -362,9 +362,10 @@ int fp_get_schedule(void);
 uint64_t fp_launch_count(void);
 void fp_profile_enable(int on);
 size_t fp_profile_report(char* out, size_t cap);
-/* fp_profile_launches: one "name ms" line per launch that fp_profile_report has synchronised, in
- * the order the launches were issued (NUL-terminated, truncated to cap); returns the size needed
- * and clears the list only by a call that writes it out (out != NULL, cap > 0). */
+/* fp_profile_launches: one "name start_ms ms" line per launch that fp_profile_report has
+ * synchronised, in the order the launches were issued, the start measured from the first listed
+ * launch's start (NUL-terminated, truncated to cap); returns the size needed and clears the list
+ * only by a call that writes it out (out != NULL, cap > 0). */
 size_t fp_profile_launches(char* out, size_t cap);
 /* Measured rate of the 32-bit integer multiply-add pipe on the current device (lane operations
  * per second, independent chains, all SMs), the denominator of the integer roofline.  Returns a

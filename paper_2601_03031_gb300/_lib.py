@@ -474,16 +474,16 @@ def profile_report() -> dict:
 
 
 def profile_launches() -> list:
-    """[(kernel name, ms)] per timed launch, in issue order, of the launches the last
-    profile_report synchronised."""
+    """[(kernel name, start_ms, ms)] per timed launch, in issue order, of the launches the last
+    profile_report synchronised (start_ms from the first listed launch's start)."""
     L = load()
     n = L.fp_profile_launches(None, 0)
     buf = ctypes.create_string_buffer(n)
     L.fp_profile_launches(buf, n)
     out = []
     for line in buf.value.decode().splitlines():
-        name, ms = line.split()
-        out.append((name, float(ms)))
+        name, start, ms = line.split()
+        out.append((name, float(start), float(ms)))
     return out
 
 

@@ -204,6 +204,30 @@ out.append(arr("PSI_CX1", mont(PSI_CX[1], 12), 12))
 out.append(arr("PSI_CY0", mont(PSI_CY[0], 12), 12))
 out.append(arr("PSI_CY1", mont(PSI_CY[1], 12), 12))
 out.append(arr("BLS_H1", H1, 4))
+
+
+def wnaf(k, w):
+    """Width-w non-adjacent form of k > 0, least significant digit first: odd digits |d| < 2^(w-1),
+    every nonzero digit followed by at least w - 1 zeros."""
+    digits = []
+    while k:
+        if k & 1:
+            d = k % (1 << w)
+            if d >= 1 << (w - 1):
+                d -= 1 << w
+            k -= d
+        else:
+            d = 0
+        digits.append(d)
+        k >>= 1
+    return digits
+
+
+H1_WNAF = wnaf(H1, 4)
+assert sum(d << i for i, d in enumerate(H1_WNAF)) == H1
+out.append(f"#define BLS_H1_WNAF_LEN {len(H1_WNAF)}\n")
+out.append("__constant__ signed char BLS_H1_WNAF[" + str(len(H1_WNAF)) + "] = {" +
+           ", ".join(str(d) for d in H1_WNAF) + "};\n")
 # the block-split Fq product (fq_split.cuh): c_k = 2^(32 k - 320) mod p for the limbs k < 10 of a
 # double-width product folded into its high part, and -p^-1 mod 2^64 for the closing two-limb
 # Montgomery step

@@ -22,7 +22,9 @@ struct Rec { const char* name; cudaEvent_t a, b; };
 std::vector<Rec> g_open;
 std::vector<cudaEvent_t> g_pool;
 thread_local Rec t_cur{nullptr, nullptr, nullptr};
-std::vector<std::pair<const char*, float>> g_each;   // every timed launch in issue order, until listed
+struct Each { const char* name; float start_ms, ms; };
+std::vector<Each> g_each;    // every timed launch in issue order, until listed
+cudaEvent_t g_origin = nullptr;   // the first timed launch's start since the list was last cleared
 
 cudaEvent_t get_event() {
     if (!g_pool.empty()) { cudaEvent_t e = g_pool.back(); g_pool.pop_back(); return e; }
@@ -67,9 +69,15 @@ size_t fp_profile_report(char* out, size_t cap) {
         auto& e = agg[r.name];
         e.first++;
         e.second += ms;
-        g_pool.push_back(r.a);
+        float start = 0.f;
+        if (!g_origin) {
+            g_origin = r.a;
+        } else {
+            cudaEventElapsedTime(&start, g_origin, r.a);
+        }
+        g_each.push_back({r.name, start, ms});
+        if (r.a != g_origin) g_pool.push_back(r.a);
         g_pool.push_back(r.b);
-        g_each.push_back({r.name, ms});
     }
     g_open.clear();
     std::string txt;
@@ -87,15 +95,16 @@ size_t fp_profile_report(char* out, size_t cap) {
     }
     return txt.size() + 1;
 }
-// One line per timed launch, "name ms", in the order the launches were issued, for the launches
-// that fp_profile_report has synchronised; cleared by a call that writes them out.
+// One line per timed launch, "name start_ms ms" (start relative to the first listed launch's start),
+// in the order the launches were issued, for the launches that fp_profile_report has synchronised;
+// cleared by a call that writes them out.
 size_t fp_profile_launches(char* out, size_t cap) {
     using namespace fpk;
     std::lock_guard<std::mutex> lk(g_mu);
     std::string txt;
     char line[256];
     for (auto& e : g_each) {
-        snprintf(line, sizeof line, "%s %.6f\n", e.first, (double)e.second);
+        snprintf(line, sizeof line, "%s %.6f %.6f\n", e.name, (double)e.start_ms, (double)e.ms);
         txt += line;
     }
     if (out && cap) {
@@ -103,6 +112,8 @@ size_t fp_profile_launches(char* out, size_t cap) {
         memcpy(out, txt.data(), n);
         out[n] = 0;
         g_each.clear();
+        if (g_origin) g_pool.push_back(g_origin);
+        g_origin = nullptr;
     }
     return txt.size() + 1;
 }

@@ -6,7 +6,7 @@
 
 struct sha256_ctx {
     uint32_t h[8];
-    uint8_t buf[64];
+    alignas(16) uint8_t buf[64];
     uint32_t nbuf;
     uint64_t total;
 };
@@ -54,9 +54,33 @@ FPG_DEV void sha256_init(sha256_ctx& c) {
     c.nbuf = 0;
     c.total = 0;
 }
-// whole 64-byte blocks of the input are compressed in place; only partial blocks are buffered
+// whole 64-byte blocks of the input are compressed in place; only partial blocks are buffered.
+// When the buffered length and the input address are multiples of 4 (long inputs after a header
+// of whole words: statements, tree nodes), the input moves into the buffer a word at a time.
 FPG_DEV void sha256_update(sha256_ctx& c, const uint8_t* data, uint32_t n) {
     c.total += n;
+    if (((c.nbuf | (uint32_t)(uintptr_t)data) & 3) == 0) {
+        const uint32_t* d32 = reinterpret_cast<const uint32_t*>(data);
+        uint32_t* b32 = reinterpret_cast<uint32_t*>(c.buf);
+        while (n >= 4) {
+            if (c.nbuf == 0 && n >= 64) {
+                sha256_compress(c.h, reinterpret_cast<const uint8_t*>(d32));
+                d32 += 16;
+                n -= 64;
+                continue;
+            }
+            const uint32_t o = c.nbuf >> 2, take = min(16u - o, n >> 2);
+            for (uint32_t i = 0; i < take; i++) b32[o + i] = d32[i];
+            d32 += take;
+            n -= 4 * take;
+            c.nbuf += 4 * take;
+            if (c.nbuf == 64) {
+                sha256_compress(c.h, c.buf);
+                c.nbuf = 0;
+            }
+        }
+        data = reinterpret_cast<const uint8_t*>(d32);
+    }
     while (n) {
         if (c.nbuf == 0 && n >= 64) {
             sha256_compress(c.h, data);

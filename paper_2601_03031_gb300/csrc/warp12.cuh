@@ -259,11 +259,39 @@ FPG_NOINL void w_cyc_exp(W12& W, fq* acc, const fq* base, const uint32_t* e, int
     }
 }
 
+// acc = base^e for base in the cyclotomic subgroup and e > 0 given by its width-4 NAF (d[0] least
+// significant, n digits, the top one positive): base, base^3, base^5, base^7 (t3, t5, t7 hold the
+// powers; acc, base, t3, t5, t7 distinct slots), then a squaring per digit and a product per nonzero
+// digit; a negative digit multiplies by the inverse, which in the cyclotomic subgroup is the
+// conjugate: acc T^-1 = conj(conj(acc) T)
+template <int NW>
+FPG_NOINL void w_cyc_exp_wnaf4(W12& W, fq* acc, const fq* base, fq* t3, fq* t5, fq* t7, const signed char* d,
+                               int n) {
+    w_cyc_sqr<NW>(W, acc, base);            // base^2
+    w_mul<NW>(W, t3, acc, base);
+    w_mul<NW>(W, t5, t3, acc);
+    w_mul<NW>(W, t7, t5, acc);
+    const int top = d[n - 1];
+    w_copy<NW>(acc, top == 1 ? base : top == 3 ? t3 : top == 5 ? t5 : t7);
+    for (int i = n - 2; i >= 0; i--) {
+        w_cyc_sqr<NW>(W, acc, acc);
+        const int di = d[i];
+        if (di) {
+            const int a = di < 0 ? -di : di;
+            const fq* T = a == 1 ? base : a == 3 ? t3 : a == 5 ? t5 : t7;
+            if (di < 0) w_conj<NW>(acc, acc);
+            w_mul<NW>(W, acc, acc, T);
+            if (di < 0) w_conj<NW>(acc, acc);
+        }
+    }
+}
+
 // slot 2 <- f^((p^12 - 1)/r) for f in slot 0 (slots 0..4 are used).  Easy part t = conj(f) f^-1,
 // g = t^(p^2) t; hard part g^d with d = h1 (x + p)(x^2 + p^2 - 1) + 1, h1 = (x - 1)^2 / 3, x < 0.
 // The inverse goes through norms: n = f conj(f) lies in Fq6, u = n^(p^2) n^(p^4), and n u is the
 // norm of n to Fq2, so f^-1 = conj(f) / n = conj(f) u / (n u) and t = conj(f)^2 u (n u)^-1: six
-// lane-parallel Fq12 products, two Frobenius maps and one Fq2 inversion on one lane.
+// lane-parallel Fq12 products, two Frobenius maps and one Fq2 inversion on one lane.  g^h1 runs on
+// the width-4 NAF of h1 (24 nonzero digits instead of 48 set bits).
 template <int NW>
 FPG_NOINL void w_final_exp(W12& W) {
     fq* s0 = W.s[0];
@@ -272,7 +300,6 @@ FPG_NOINL void w_final_exp(W12& W) {
     fq* s3 = W.s[3];
     fq* s4 = W.s[4];
     const uint32_t xabs[2] = {(uint32_t)BLS_X_ABS, (uint32_t)(BLS_X_ABS >> 32)};
-    const uint32_t h1[4] = {BLS_H1[0], BLS_H1[1], BLS_H1[2], BLS_H1[3]};
     w_conj<NW>(s1, s0);                     // c = conj(f)
     w_mul<NW>(W, s2, s0, s1);               // n = f c, in Fq6
     w_frob2<NW>(W, s3, s2);
@@ -285,7 +312,7 @@ FPG_NOINL void w_final_exp(W12& W) {
     w_mul<NW>(W, s2, s2, s4);               // t = c^2 u (n u)^-1 = conj(f) f^-1
     w_frob2<NW>(W, s3, s2);
     w_mul<NW>(W, s3, s3, s2);               // g = t^(p^2) t
-    w_cyc_exp<NW>(W, s4, s3, h1, 126);      // a = g^h1
+    w_cyc_exp_wnaf4<NW>(W, s4, s3, s0, s1, s2, BLS_H1_WNAF, BLS_H1_WNAF_LEN);   // a = g^h1
     w_cyc_exp<NW>(W, s0, s4, xabs, 64);     // a^|x|
     w_conj<NW>(s0, s0);                     // a^x
     w_frob<NW>(W, s1, s4);                  // a^p
@@ -316,6 +343,15 @@ FPG_NOINL void w_final_exp(W12& W) {
 // re = m0 - m1, im = m2 - m0 - m1; squares x^2: m0 = (x0 + x1)(x0 - x1), m1 = x0 x1, re = m0,
 // im = 2 m1.
 // ---------------------------------------------------------------------------------------
+// The block engine's narrow Miller rounds (up to 15 products) run one product per lane; built with
+// FPG_MILLER_SPLIT=1 they split each product over the four warps (fq_split.cuh).  Measured in the
+// whole ProveAll step the split rounds were slower (N = 2^16, b = 256: 0.82 against 0.89 ms per
+// round's Miller loops): the rounds between them are one product per lane on three warps anyway,
+// and the split's extra instructions compete with the kernels running beside the chain.
+#ifndef FPG_MILLER_SPLIT
+#define FPG_MILLER_SPLIT 0
+#endif
+
 struct WMill {
     fq p[72];       // products of a round
     fq f[12];       // running value (flat)
@@ -503,8 +539,9 @@ FPG_NOINL void wm_dbl(WMill& S, const fq& m3x, const fq& y2) {
     wsync<NW>();
     // round B
     if (NW == 4) {
-        {                                           // 15 products, each split over the four warps
-            const int t = (L & 31) < 15 ? (L & 31) : 0;
+        constexpr bool SPLIT = FPG_MILLER_SPLIT != 0;
+        if (SPLIT || L < 15) {                      // 15 products, each split over the four warps
+            const int t = SPLIT ? ((L & 31) < 15 ? (L & 31) : 0) : L;
             const fq* XX = S.v;
             const fq* YY = S.v + 2;
             const fq* YZ = S.v + 6;
@@ -520,8 +557,12 @@ FPG_NOINL void wm_dbl(WMill& S, const fq& m3x, const fq& y2) {
             else { a = YY; b = YZ; kind = t - 12; mode = 0; }                        // YY YZ
             fq x, y;
             prod_ops(x, y, a, b, kind, mode, fq_select(t < 2, m3x, y2));
-            const fq m = fq_mul_split(x, y);
-            if (L < 15) S.p[L] = m;
+            if (SPLIT) {
+                const fq m = fq_mul_split(x, y);
+                if (L < 15) S.p[L] = m;
+            } else {
+                S.p[L] = fq_mul(x, y);
+            }
         }
         wsync<NW>();
         // the line (warp 0) and 2T (X' on warp 1, Y' on warp 2, Z' on warp 3)
@@ -607,13 +648,14 @@ FPG_NOINL void wm_add(WMill& S, const fq& mxP, const fq& yP) {
     const fq* Z = S.T + 4;
     const fq* xQ = S.Q;
     const fq* yQ = S.Q + 2;
+    constexpr bool SPLIT = NW == 4 && FPG_MILLER_SPLIT != 0;
     // round A: yQ Z, xQ Z (the block engine splits each product over its four warps: lane t of every
     // warp forms the operands of product t)
-    if (NW == 4 || L < 6) {
-        const int t = NW == 4 ? ((L & 31) < 6 ? (L & 31) : 0) : L;
+    if (SPLIT || L < 6) {
+        const int t = SPLIT ? ((L & 31) < 6 ? (L & 31) : 0) : L;
         fq x, y;
         kara_ops(x, y, t < 3 ? yQ : xQ, Z, t % 3);
-        if (NW == 4) {
+        if (SPLIT) {
             const fq m = fq_mul_split(x, y);
             if (L < 6) S.p[L] = m;
         } else {
@@ -629,8 +671,8 @@ FPG_NOINL void wm_add(WMill& S, const fq& mxP, const fq& yP) {
     const fq* th = S.v;
     const fq* la = S.v + 2;
     // round B: theta xQ, lambda yQ, -theta xP, lambda yP, theta^2, lambda^2
-    if (NW == 4 || L < 14) {
-        const int t = NW == 4 ? ((L & 31) < 14 ? (L & 31) : 0) : L;
+    if (SPLIT || L < 14) {
+        const int t = SPLIT ? ((L & 31) < 14 ? (L & 31) : 0) : L;
         const fq* a;
         const fq* b;
         int kind, mode;
@@ -642,7 +684,7 @@ FPG_NOINL void wm_add(WMill& S, const fq& mxP, const fq& yP) {
         else { a = b = la; kind = t - 12; mode = 1; }
         fq x, y;
         prod_ops(x, y, a, b, kind, mode, fq_select(t < 8, mxP, yP));
-        if (NW == 4) {
+        if (SPLIT) {
             const fq m = fq_mul_split(x, y);
             if (L < 14) S.p[L] = m;
         } else {
@@ -703,8 +745,8 @@ FPG_NOINL void wm_add(WMill& S, const fq& mxP, const fq& yP) {
     const fq* E = S.v + 8;
     const fq* Fv = S.v + 10;
     const fq* G = S.v + 12;
-    if (NW == 4 || (L >= 16 && L < 28)) {
-        const int u = NW == 4 ? ((L & 31) < 12 ? (L & 31) : 0) : L - 16, which = u / 3;
+    if (SPLIT || (L >= 16 && L < 28)) {
+        const int u = SPLIT ? ((L & 31) < 12 ? (L & 31) : 0) : L - 16, which = u / 3;
         fq H[2], GH[2];
         for (int e = 0; e < 2; e++) {
             H[e] = fq_sub(fq_add(E[e], Fv[e]), fq_dbl(G[e]));
@@ -713,7 +755,7 @@ FPG_NOINL void wm_add(WMill& S, const fq& mxP, const fq& yP) {
         fq x, y;
         kara_ops(x, y, which == 0 ? la : (which == 1 ? th : (which == 2 ? Y : Z)),
                  which == 0 ? H : (which == 1 ? GH : E), u % 3);
-        if (NW == 4) {
+        if (SPLIT) {
             const fq m = fq_mul_split(x, y);
             if (L < 12) S.p[L] = m;
         } else {

@@ -69,6 +69,13 @@ static inline uint32_t __funnelshift_r(uint32_t lo, uint32_t hi, unsigned s) {
     return (uint32_t)((((uint64_t)hi << 32) | lo) >> (s & 31));
 }
 static inline uint32_t __umulhi(uint32_t a, uint32_t b) { return (uint32_t)(((uint64_t)a * b) >> 32); }
+// byte i of the result is byte (s >> 4 i) & 7 of the 8 bytes y:x
+static inline uint32_t __byte_perm(uint32_t x, uint32_t y, uint32_t s) {
+    const uint64_t v = ((uint64_t)y << 32) | x;
+    uint32_t r = 0;
+    for (int i = 0; i < 4; i++) r |= (uint32_t)((v >> (8 * ((s >> (4 * i)) & 7))) & 0xff) << (8 * i);
+    return r;
+}
 
 // kernels: one block at a time, its shared variables as statics, blockIdx per lane thread
 #define __shared__ static
