@@ -1,6 +1,7 @@
 // Setup, commit-MSM terms and the generic group kernels (pairwise reductions, normalisation,
 // serialisation).
 #include "k_common.cuh"
+#include "group_ec.cuh"
 
 namespace fpk {
 
@@ -102,6 +103,69 @@ void g1_pair_reduce(const void* in, void* out, uint64_t n, cudaStream_t s) {
 }
 void g2_pair_reduce(const void* in, void* out, uint64_t n, cudaStream_t s) {
     if (n) FP_KERNEL("k_g2_pair", s, k_g2_pair<<<grid_for(n, 64), 64, 0, s>>>((const g2j*)in, (g2j*)out, n));
+}
+
+// Jacobian (x = X / Z^2, y = Y / Z^3) <-> homogeneous projective (x = X / Z, y = Y / Z), the
+// identity to the identity (a Jacobian point with Z = 0, whatever X and Y, maps to (0 : 1 : 0))
+template <typename F>
+FPG_DEV GPt<F> jac_to_proj(const jac<F>& p) {
+    const F z2 = f_sqr(p.Z);
+    F one;
+    f_set_one(one);
+    return {f_mul(p.X, p.Z), f_sel(f_is_zero(p.Z), one, p.Y), f_mul(z2, p.Z)};
+}
+template <typename F>
+FPG_DEV jac<F> proj_to_jac(const GPt<F>& p) {
+    return {f_mul(p.X, p.Z), f_mul(p.Y, f_sqr(p.Z)), p.Z};
+}
+
+// Latency-bound sums of consecutive points, in one launch per factor of 16 or 32: out[g] = the sum of
+// in[gs g .. gs g + gs - 1] (gs <= 32 for G1, <= 16 for G2; inputs past n_in count as the identity).
+// G1: a 128-thread block per sum, 16 8-lane groups (group_ec.cuh) each adding two inputs, then a tree
+// over the groups; G2: a 256-thread block per sum, 8 warps each adding two inputs, then a tree.  Every
+// group of a warp runs every addition (one instruction stream); the unneeded ones are discarded.
+__global__ void __launch_bounds__(128) k_g1_tree(const g1j* in, g1j* out, uint64_t n_in, uint32_t gs) {
+    __shared__ GEcs<fq> e[16];
+    __shared__ GPt<fq> part[16];
+    const int grp = threadIdx.x >> 3, lane = threadIdx.x & 7;
+    const uint64_t i0 = blockIdx.x * (uint64_t)gs + 2 * grp;
+    const bool in0 = 2 * grp < (int)gs && i0 < n_in, in1 = 2 * grp + 1 < (int)gs && i0 + 1 < n_in;
+    const GPt<fq> a = in0 ? jac_to_proj(in[i0]) : gec_identity<fq>();
+    const GPt<fq> b = in1 ? jac_to_proj(in[i0 + 1]) : gec_identity<fq>();
+    GPt<fq> acc = gec_add(e[grp], lane, a, b);
+    for (int sh = 8; sh >= 1; sh >>= 1) {
+        __syncthreads();
+        if (lane == 0) part[grp] = acc;
+        __syncthreads();
+        const GPt<fq> r = gec_add(e[grp], lane, acc, part[grp < sh ? grp + sh : grp]);
+        if (grp < sh) acc = r;
+    }
+    if (grp == 0 && lane == 0) out[blockIdx.x] = proj_to_jac(acc);
+}
+__global__ void __launch_bounds__(256) k_g2_tree(const g2j* in, g2j* out, uint64_t n_in, uint32_t gs) {
+    __shared__ GEcWs e[8];
+    __shared__ GPt<fq2> part[8];
+    const int w = threadIdx.x >> 5, L = threadIdx.x & 31;
+    const uint64_t i0 = blockIdx.x * (uint64_t)gs + 2 * w;
+    const bool in0 = 2 * w < (int)gs && i0 < n_in, in1 = 2 * w + 1 < (int)gs && i0 + 1 < n_in;
+    const GPt<fq2> a = in0 ? jac_to_proj(in[i0]) : gec_identity<fq2>();
+    const GPt<fq2> b = in1 ? jac_to_proj(in[i0 + 1]) : gec_identity<fq2>();
+    GPt<fq2> acc = gecw_add(e[w], L, a, b);
+    for (int sh = 4; sh >= 1; sh >>= 1) {
+        __syncthreads();
+        if (L == 0) part[w] = acc;
+        __syncthreads();
+        if (w < sh) acc = gecw_add(e[w], L, acc, part[w + sh]);
+    }
+    if (w == 0 && L == 0) out[blockIdx.x] = proj_to_jac(acc);
+}
+void g1_tree_reduce(const void* in, void* out, uint64_t n_in, uint32_t gs, cudaStream_t s) {
+    const uint64_t n_out = (n_in + gs - 1) / gs;
+    if (n_out) FP_KERNEL("k_g1_tree", s, k_g1_tree<<<(unsigned)n_out, 128, 0, s>>>((const g1j*)in, (g1j*)out, n_in, gs));
+}
+void g2_tree_reduce(const void* in, void* out, uint64_t n_in, uint32_t gs, cudaStream_t s) {
+    const uint64_t n_out = (n_in + gs - 1) / gs;
+    if (n_out) FP_KERNEL("k_g2_tree", s, k_g2_tree<<<(unsigned)n_out, 256, 0, s>>>((const g2j*)in, (g2j*)out, n_in, gs));
 }
 
 __global__ void k_g1j_affine(const g1j* in, g1a* out, uint8_t* ser, size_t stride, uint64_t n) {

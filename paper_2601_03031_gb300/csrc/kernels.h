@@ -60,6 +60,10 @@ void g2_gen_mul(const void* scal_canon, uint32_t n, void* out_g2a, cudaStream_t 
 // ---- generic group helpers
 void g1_pair_reduce(const void* in_g1j, void* out_g1j, uint64_t n_out, cudaStream_t s);
 void g2_pair_reduce(const void* in_g2j, void* out_g2j, uint64_t n_out, cudaStream_t s);
+// out[g] = sum of in[gs g .. gs g + gs - 1] (Jacobian; gs <= 32 on G1, <= 16 on G2), one block per
+// sum on the lane-parallel group engines: few sums of many points, for latency
+void g1_tree_reduce(const void* in_g1j, void* out_g1j, uint64_t n_in, uint32_t gs, cudaStream_t s);
+void g2_tree_reduce(const void* in_g2j, void* out_g2j, uint64_t n_in, uint32_t gs, cudaStream_t s);
 void fq12_pair_reduce(const void* in, void* out, uint64_t n_out, cudaStream_t s);
 void g1j_to_affine(const void* in_g1j, void* out_g1a, void* ser_out, size_t ser_stride, uint64_t n, cudaStream_t s);
 void g2j_to_affine(const void* in_g2j, void* out_g2a, void* ser_out, size_t ser_stride, uint64_t n, cudaStream_t s);

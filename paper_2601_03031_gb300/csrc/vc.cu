@@ -128,6 +128,21 @@ void* reduce_pairs(void* a, void* b, uint64_t n, uint64_t target, Red red, cudaS
     return a;
 }
 
+// the same reduction by block trees (g1_tree_reduce / g2_tree_reduce): a factor of up to gmax per
+// launch, for few sums whose pairwise launches would each wait one addition's latency
+template <typename Red>
+void* reduce_tree(void* a, void* b, uint64_t n, uint64_t target, uint32_t gmax, Red red, cudaStream_t s) {
+    while (n > target) {
+        const uint32_t gs = (uint32_t)std::min<uint64_t>(gmax, n / target);
+        red(a, b, n, gs, s);
+        std::swap(a, b);
+        n /= gs;
+    }
+    return a;
+}
+// sums of few points (one block per sum is enough to fill the GPU's share the round leaves free)
+constexpr uint64_t TREE_REDUCE_MAX = 8192;
+
 size_t bopen_len(uint32_t log_r) { return (size_t)log_r * ROUND_BYTES + G1_SER + 2 * G2_SER; }
 
 // Internal non-blocking streams: OpenAll's latency-bound Step 1 runs on three high-priority
@@ -534,7 +549,9 @@ void step1_rounds(const fp_pp* pp, uint32_t k0, uint32_t Kc, uint32_t b, const S
         }
         check(cudaStreamWaitEvent(s3, ev_folded, 0), "wait");
         step1_sparse_terms(B.A, B.bvec, k0, Kc, R, h, b, B.sp, s3);
-        void* spr = reduce_pairs(B.sp, B.sp2, (uint64_t)Kc * 2 * h, (uint64_t)Kc * 2, g1_pair_reduce, s3);
+        void* spr = (uint64_t)Kc * 2 * h <= TREE_REDUCE_MAX
+                        ? reduce_tree(B.sp, B.sp2, (uint64_t)Kc * 2 * h, (uint64_t)Kc * 2, 32, g1_tree_reduce, s3)
+                        : reduce_pairs(B.sp, B.sp2, (uint64_t)Kc * 2 * h, (uint64_t)Kc * 2, g1_pair_reduce, s3);
         step1_g1_out(spr, Kc, j, blocks1, blen, s3);
         check(cudaEventRecord(ev_sparse, s3), "event");
         const uint64_t nml = step1_miller_g(B.A, B.v, Kc, R, h, B.ml, s1);
@@ -551,7 +568,9 @@ void step1_rounds(const fp_pp* pp, uint32_t k0, uint32_t Kc, uint32_t b, const S
         msm_g2(pp->g2w_tab, B.q, B.wsh, B.wscr, nullptr, w_out, blen, s1);
     } else {
         step1_w_terms(pp->g2pow, B.q, Kc, R, B.wt, s1);
-        void* wr = reduce_pairs(B.wt, B.wt2, (uint64_t)Kc * 2 * R, Kc, g2_pair_reduce, s1);
+        void* wr = (uint64_t)Kc * 2 * R <= TREE_REDUCE_MAX
+                       ? reduce_tree(B.wt, B.wt2, (uint64_t)Kc * 2 * R, Kc, 16, g2_tree_reduce, s1)
+                       : reduce_pairs(B.wt, B.wt2, (uint64_t)Kc * 2 * R, Kc, g2_pair_reduce, s1);
         g2j_to_affine(wr, nullptr, w_out, blen, Kc, s1);
     }
     cudaEventDestroy(ev_folded);
@@ -632,7 +651,9 @@ void step1_rounds_la(const fp_pp* pp, uint32_t k0, uint32_t Kc, uint32_t b, cons
     {   // round 1, direct
         const uint32_t h = R >> 1;
         step1_sparse_terms(B.A, B.bvec, k0, Kc, R, h, b, B.sp, s3);
-        void* spr = reduce_pairs(B.sp, B.sp2, (uint64_t)Kc * 2 * h, (uint64_t)Kc * 2, g1_pair_reduce, s3);
+        void* spr = (uint64_t)Kc * 2 * h <= TREE_REDUCE_MAX
+                        ? reduce_tree(B.sp, B.sp2, (uint64_t)Kc * 2 * h, (uint64_t)Kc * 2, 32, g1_tree_reduce, s3)
+                        : reduce_pairs(B.sp, B.sp2, (uint64_t)Kc * 2 * h, (uint64_t)Kc * 2, g1_pair_reduce, s3);
         step1_g1_out(spr, Kc, 1, blocks1, blen, s3);
         cudaEvent_t ev_sp = rec(s3);
         const uint64_t nml = step1_miller_g(B.A, B.v, Kc, R, h, B.ml, s1);
@@ -663,7 +684,9 @@ void step1_rounds_la(const fp_pp* pp, uint32_t k0, uint32_t Kc, uint32_t b, cons
         msm_g2(pp->g2w_tab, B.q, B.wsh, B.wscr, nullptr, w_out, blen, s1);
     } else {
         step1_w_terms(pp->g2pow, B.q, Kc, R, B.wt, s1);
-        void* wr = reduce_pairs(B.wt, B.wt2, (uint64_t)Kc * 2 * R, Kc, g2_pair_reduce, s1);
+        void* wr = (uint64_t)Kc * 2 * R <= TREE_REDUCE_MAX
+                       ? reduce_tree(B.wt, B.wt2, (uint64_t)Kc * 2 * R, Kc, 16, g2_tree_reduce, s1)
+                       : reduce_pairs(B.wt, B.wt2, (uint64_t)Kc * 2 * R, Kc, g2_pair_reduce, s1);
         g2j_to_affine(wr, nullptr, w_out, blen, Kc, s1);
     }
     for (cudaEvent_t e : evs) cudaEventDestroy(e);
