@@ -11,8 +11,10 @@
  * Readings where the paper is silent (each one is listed in the design notes):
  *   - serialisation: Fr 32 B, G1 96 B (x||y), G2 192 B (x.c0||x.c1||y.c0||y.c1), GT 576 B in
  *     tower order, all canonical big-endian; the identity is all-zero bytes;
- *   - the FC statement hashed for r_a is C || u32be(k) || u32be(b) || u32be(|S_k|) || C_a..., and
- *     r_a = HFr("FP-r", SHA256(statement) || u32be(a));
+ *   - the FC statement hashed for r_a is C || u32be(k) || u32be(b) || u32be(|S_k|) || D_k with D_k
+ *     the root of a binary tree over the block's C_a (leaves SHA256("FP-sleaf"||C_a) in row order,
+ *     nodes SHA256("FP-snode"||left||right) pairing each level left to right, an odd last node
+ *     carried up unchanged), and r_a = HFr("FP-r", SHA256(statement) || u32be(a));
  *   - x_j = HFr("FP-x", x_{j-1} || L_j.T || L_j.1 || R_j.T || R_j.1), x_0 the empty string;
  *   - v_l is proven KZG-style in G2: z = HFr("FP-z", x_l || v_l),
  *     W = g2^{(P(beta)-P(z))/(beta-z)}, P(X) = prod_j (1 + x_j^{-1} X^{2^{l_R-j+1}});
@@ -212,16 +214,38 @@ int or_commit(const or_pp* pp, const u64* m, u8* C_out, u8* rows_out) {
  * ------------------------------------------------------------------------------ */
 size_t or_bopen_len(const or_pp* pp) { return (size_t)pp->log_r * 1344 + 480; }
 
+/* D_k: the tree over the nk >= 1 row commitments ca[0 .. nk - 1] (96 bytes each), level by level */
+static void stmt_rows_root(u8 out[32], const u8* ca, u32 nk) {
+    u8* lv = (u8*)malloc(32 * (size_t)nk);
+    for (u32 t = 0; t < nk; t++) {
+        u8 buf[8 + 96];
+        memcpy(buf, "FP-sleaf", 8);
+        memcpy(buf + 8, ca + 96 * (size_t)t, 96);
+        sha256(lv + 32 * (size_t)t, buf, sizeof buf);
+    }
+    for (u32 n = nk; n > 1;) {
+        u32 m = 0;
+        for (u32 i = 0; i + 1 < n; i += 2, m++) {
+            u8 buf[8 + 64];
+            memcpy(buf, "FP-snode", 8);
+            memcpy(buf + 8, lv + 32 * (size_t)i, 64);
+            sha256(lv + 32 * (size_t)m, buf, sizeof buf);
+        }
+        if (n & 1) { memmove(lv + 32 * (size_t)m, lv + 32 * (size_t)(n - 1), 32); m++; }
+        n = m;
+    }
+    memcpy(out, lv, 32);
+    free(lv);
+}
+
 static void block_challenges(fe* r_out, const u8* C, const u8* rows, u32 R, u32 b, u32 k, u32* nk_out) {
     u32 lo = k * b, hi = (k + 1) * b < R ? (k + 1) * b : R, nk = hi - lo;
-    size_t sl = 576 + 12 + 96 * (size_t)nk;
-    u8* stmt = (u8*)malloc(sl);
+    u8 stmt[576 + 12 + 32];
     memcpy(stmt, C, 576);
     be32(stmt + 576, k); be32(stmt + 580, b); be32(stmt + 584, nk);
-    memcpy(stmt + 588, rows + 96 * (size_t)lo, 96 * (size_t)nk);
+    stmt_rows_root(stmt + 588, rows + 96 * (size_t)lo, nk);
     u8 buf[36];
-    sha256(buf, stmt, sl);
-    free(stmt);
+    sha256(buf, stmt, sizeof stmt);
     for (u32 a = lo; a < hi; a++) {
         be32(buf + 32, a);
         hfr(&r_out[a - lo], "FP-r", buf, 36);
@@ -687,7 +711,7 @@ static int fc_bverify(const or_pp* pp, const fq12* Cgp, const u8* C, u32 b, u32 
     u8 hdr[576 + 4]; memcpy(hdr, C, 576); be32(hdr + 576, k);
     u8 bkey[32]; int cached = 0, cval = 0;
     if (use_memo) {
-        memo_key(bkey, "bverify", pid, sizeof pid, hdr, sizeof hdr, blk, 96 * (size_t)nk, fc, or_bopen_len(pp));
+        memo_key(bkey, "bverify-t", pid, sizeof pid, hdr, sizeof hdr, blk, 96 * (size_t)nk, fc, or_bopen_len(pp));
         cached = memo_get(bkey, &cval);
         if (cached) ok = cval;
     }

@@ -19,20 +19,60 @@ __global__ void k_step1_init(const g1a* rows, const g2a* g2pow, uint32_t K, uint
 
 // SHA256(C || u32be(k) || u32be(b) || u32be(|S_k|) || C_a for a in S_k), for the K blocks
 // k = k0 .. k0 + K - 1 (stored at local index k - k0)
-__global__ void k_stmt_hash(const uint8_t* C_ser, const uint8_t* rows_ser, uint32_t k0, uint32_t K, uint32_t R,
-                            uint32_t b, uint8_t* hstmt) {
-    const uint64_t kl = gtid();
-    if (kl >= K) return;
-    const uint32_t k = k0 + (uint32_t)kl;
-    uint32_t lo = k * b, hi = min(lo + b, R), nk = hi - lo;
-    sha256_ctx c;
-    sha256_init(c);
-    sha256_update(c, C_ser, 576);
-    uint8_t hdr[12];
-    put_be32(hdr, (uint32_t)k); put_be32(hdr + 4, b); put_be32(hdr + 8, nk);
-    sha256_update(c, hdr, 12);
-    sha256_update(c, rows_ser + (size_t)lo * 96, nk * 96);
-    sha256_final(c, hstmt + kl * 32);
+// SHA256 of block k's statement C || u32be(k) || u32be(b) || u32be(|S_k|) || D_k, D_k the root of the
+// tree over the block's row commitments C_a (leaves SHA256("FP-sleaf" || C_a), nodes
+// SHA256("FP-snode" || left || right) pairing each level left to right, an odd last node carried up).
+// One block per k: warps 0..7 hash the leaves and the levels (ping-pong between two halves of the
+// scratch, nk digests each), warp 8 meanwhile absorbs C and the header into the final hash's state.
+constexpr int STMT_TPB = 288;
+__global__ void __launch_bounds__(STMT_TPB) k_stmt_hash(const uint8_t* C_ser, const uint8_t* rows_ser, uint32_t k0,
+                                                        uint32_t R, uint32_t b, uint8_t* scratch, uint8_t* hstmt) {
+    __shared__ sha256_ctx pre;
+    __shared__ uint8_t* root;
+    const uint32_t kl = blockIdx.x, k = k0 + kl, lo = k * b, hi = min(lo + b, R), nk = hi - lo;
+    const uint32_t bb = min(b, R), tid = threadIdx.x, nt = STMT_TPB - 32;
+    if (tid >= nt) {                      // warp 8: C and the header, beside the tree
+        if (tid == nt) {
+            sha256_init(pre);
+            sha256_update(pre, C_ser, 576);
+            uint8_t hdr[12];
+            put_be32(hdr, k); put_be32(hdr + 4, b); put_be32(hdr + 8, nk);
+            sha256_update(pre, hdr, 12);
+        }
+    } else {                              // warps 0..7: leaves, then the levels (barrier 1 of 256)
+        uint8_t* src = scratch + (size_t)kl * 2 * bb * 32;
+        uint8_t* dst = src + (size_t)bb * 32;
+        for (uint32_t t = tid; t < nk; t += nt) {
+            sha256_ctx c;
+            sha256_init(c);
+            sha256_update(c, (const uint8_t*)"FP-sleaf", 8);
+            sha256_update(c, rows_ser + (size_t)(lo + t) * 96, 96);
+            sha256_final(c, src + (size_t)t * 32);
+        }
+        for (uint32_t n = nk; n > 1; n = (n + 1) / 2) {
+            asm volatile("bar.sync 1, %0;" ::"r"(nt) : "memory");
+            for (uint32_t i = tid; i < (n + 1) / 2; i += nt) {
+                if (2 * i + 1 < n) {
+                    sha256_ctx c;
+                    sha256_init(c);
+                    sha256_update(c, (const uint8_t*)"FP-snode", 8);
+                    sha256_update(c, src + (size_t)(2 * i) * 32, 64);
+                    sha256_final(c, dst + (size_t)i * 32);
+                } else {
+                    for (int q = 0; q < 32; q++) dst[(size_t)i * 32 + q] = src[(size_t)(2 * i) * 32 + q];
+                }
+            }
+            uint8_t* t = src;
+            src = dst;
+            dst = t;
+        }
+        if (tid == 0) root = src;
+    }
+    __syncthreads();
+    if (tid == 0) {
+        sha256_update(pre, root, 32);
+        sha256_final(pre, hstmt + (size_t)kl * 32);
+    }
 }
 
 // r_a = HFr("FP-r", SHA256(statement_k) || u32be(a)) placed at b[a] of block k (local index k - k0)
@@ -468,10 +508,11 @@ void step1_init(const void* rows, const void* g2pow, uint32_t K, uint32_t R, voi
     FP_KERNEL("k_step1_init", s, k_step1_init<<<grid_for((uint64_t)K * R), TPB, 0, s>>>((const g1a*)rows, (const g2a*)g2pow, K, R, (g1a*)A,
                                                           (g2a*)v, (fr*)bvec));
 }
+size_t stmt_hash_scratch_bytes(uint32_t K, uint32_t R, uint32_t b) { return (size_t)K * 2 * std::min(b, R) * 32; }
 void step1_stmt_hash(const void* C_ser, const void* rows_ser, uint32_t k0, uint32_t K, uint32_t R, uint32_t b,
-                     void* hstmt, cudaStream_t s) {
-    FP_KERNEL("k_stmt_hash", s, k_stmt_hash<<<grid_for(K, 64), 64, 0, s>>>((const uint8_t*)C_ser, (const uint8_t*)rows_ser,
-                                                                         k0, K, R, b, (uint8_t*)hstmt));
+                     void* scratch, void* hstmt, cudaStream_t s) {
+    FP_KERNEL("k_stmt_hash", s, k_stmt_hash<<<K, STMT_TPB, 0, s>>>((const uint8_t*)C_ser, (const uint8_t*)rows_ser, k0,
+                                                                   R, b, (uint8_t*)scratch, (uint8_t*)hstmt));
 }
 void step1_block_r(const void* hstmt, uint32_t k0, uint32_t K, uint32_t R, uint32_t b, void* bvec, cudaStream_t s) {
     FP_KERNEL("k_block_r", s, k_block_r<<<grid_for((uint64_t)K * b, 64), 64, 0, s>>>((const uint8_t*)hstmt, k0, K, R, b,

@@ -82,9 +82,11 @@ void final_exp_group(const void* in_fq12, uint32_t n, void* out_fq12, void* ser,
 // ---- Step 1 (FC.BOpen for all blocks at once)
 void step1_init(const void* rows_g1a, const void* g2pow, uint32_t K, uint32_t R, void* A, void* v, void* bvec,
                 cudaStream_t s);
-// blocks k0 .. k0 + K - 1 of size b (stored at local indices 0 .. K - 1)
+// blocks k0 .. k0 + K - 1 of size b (stored at local indices 0 .. K - 1); the statement digests go
+// to hstmt (32 bytes per block), through scratch (stmt_hash_scratch_bytes) for the row trees
+size_t stmt_hash_scratch_bytes(uint32_t K, uint32_t R, uint32_t b);
 void step1_stmt_hash(const void* C_ser, const void* rows_ser, uint32_t k0, uint32_t K, uint32_t R, uint32_t b,
-                     void* hstmt, cudaStream_t s);
+                     void* scratch, void* hstmt, cudaStream_t s);
 void step1_block_r(const void* hstmt, uint32_t k0, uint32_t K, uint32_t R, uint32_t b, void* bvec, cudaStream_t s);
 // one thread per step1_miller_group(h) pairs of a product (multi-pair Miller loop); the outputs are
 // the products over those groups, in pair order

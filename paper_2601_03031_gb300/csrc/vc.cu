@@ -740,6 +740,7 @@ fp_proofs* prove_impl(const fp_pp* pp, const fp_commit* cm, uint32_t b, uint32_t
             const bool la = lookahead_on(lr);
             const LaBufs L = la ? la_bufs(pp, Kc, T) : LaBufs{};
             void* hstmt = T(Kc * DIGEST);
+            void* hscr = T(stmt_hash_scratch_bytes(Kc, R, b));
             const Streams st = streams(s);
             cudaStream_t s2 = st.lo, s1 = st.hi, s3 = st.sp;
             cudaEvent_t ev_fork = new_event(), ev_join = new_event(), ev_join1 = new_event();
@@ -781,7 +782,7 @@ fp_proofs* prove_impl(const fp_pp* pp, const fp_commit* cm, uint32_t b, uint32_t
             // while s1 starts the first round's Miller loops
             check(cudaEventRecord(ev_init, s1), "event");
             check(cudaStreamWaitEvent(s3, ev_init, 0), "wait");
-            step1_stmt_hash(cm->C_ser, cm->rows_ser, k0, Kc, R, b, hstmt, s3);
+            step1_stmt_hash(cm->C_ser, cm->rows_ser, k0, Kc, R, b, hscr, hstmt, s3);
             step1_block_r(hstmt, k0, Kc, R, b, B.bvec, s3);
             if (la) step1_rounds_la(pp, k0, Kc, b, B, L, blocks1, blen, s1, s3, st.pre, st.la, st.fold);
             else step1_rounds(pp, k0, Kc, b, B, blocks1, blen, s1, s3, st.pre);

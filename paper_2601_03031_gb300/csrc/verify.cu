@@ -188,6 +188,42 @@ __global__ void k_v_cdec(const uint8_t* C_be, fq12* Cd, uint32_t* cbad) {
     *cbad = fq12_decode(C_be, *Cd) ? 0u : 1u;
 }
 
+// D_k, the tree root over the nk >= 1 row commitments at blk (96 bytes each), on one thread: the
+// leaves SHA256("FP-sleaf" || C_a) go in order onto a stack of subtree roots, two subtrees of equal
+// height merge as SHA256("FP-snode" || left || right) as soon as they meet, and the stack is then
+// folded from the top; this is the level-by-level tree with an odd last node carried up
+FPG_DEV void stmt_rows_root(const uint8_t* blk, uint32_t nk, uint8_t* out) {
+    uint8_t st[33][32];
+    int hgt[33];
+    int sp = 0;
+    auto node = [&](int l) {                           // st[l] <- H(st[l] || st[l + 1])
+        sha256_ctx c;
+        sha256_init(c);
+        sha256_update(c, (const uint8_t*)"FP-snode", 8);
+        sha256_update(c, st[l], 32);
+        sha256_update(c, st[l + 1], 32);
+        sha256_final(c, st[l]);
+    };
+    for (uint32_t t = 0; t < nk; t++) {
+        sha256_ctx c;
+        sha256_init(c);
+        sha256_update(c, (const uint8_t*)"FP-sleaf", 8);
+        sha256_update(c, blk + (size_t)t * 96, 96);
+        sha256_final(c, st[sp]);
+        hgt[sp++] = 0;
+        while (sp >= 2 && hgt[sp - 1] == hgt[sp - 2]) {
+            node(sp - 2);
+            hgt[sp - 2]++;
+            sp--;
+        }
+    }
+    while (sp >= 2) {
+        node(sp - 2);
+        sp--;
+    }
+    for (int q = 0; q < 32; q++) out[q] = st[0][q];
+}
+
 // statement hash, x_j and x_j^-1, A_l, v_l, W, z and P(z) = prod_j (1 + x_j^-1 z^(2^(l - j + 1)))
 __global__ void k_vb_transcript(VSrc S, const uint8_t* C_be, VBlk* st) {
     const uint64_t q = gtid();
@@ -205,7 +241,9 @@ __global__ void k_vb_transcript(VSrc S, const uint8_t* C_be, VBlk* st) {
         uint8_t hdr[12];
         put_be32(hdr, k); put_be32(hdr + 4, S.b); put_be32(hdr + 8, nk);
         sha256_update(c, hdr, 12);
-        sha256_update(c, blk, 96 * nk);
+        uint8_t root[32];
+        stmt_rows_root(blk, nk, root);
+        sha256_update(c, root, 32);
         sha256_final(c, B.hstmt);
     }
     uint8_t xprev[32];

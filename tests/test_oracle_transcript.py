@@ -10,7 +10,10 @@ generators, its trapdoor (beta, tau) and the proofs being checked.
 The readings re-derived (the paper leaves the random oracles and the Merkle instantiation open:
 Sec. 2 "random oracles", Sec. 3 FC.BOpen with Eq. b, Sec. 4.2 "Making our protocol
 non-interactive"):
-  * r_a = HFr("FP-r", SHA256(C || u32be(k) || u32be(b) || u32be(|S_k|) || C_a ...) || u32be(a));
+  * r_a = HFr("FP-r", SHA256(C || u32be(k) || u32be(b) || u32be(|S_k|) || D_k) || u32be(a)), D_k the
+    root of the tree over the block's C_a: leaves SHA256("FP-sleaf" || C_a), nodes
+    SHA256("FP-snode" || left || right) pairing each level left to right, an odd last node carried
+    up unchanged;
   * x_j = HFr("FP-x", x_{j-1} || L_j.T || L_j.1 || R_j.T || R_j.1), x_0 empty;
   * z = HFr("FP-z", x_l || v_l), W = g2^{(P(beta) - P(z)) / (beta - z)},
     P(X) = prod_j (1 + x_j^{-1} X^{2^{l_R - j + 1}});
@@ -42,6 +45,8 @@ class Reading:
     node_swap: bool = False         # hash (right, left) instead of (left, right)
     x0_zero: bool = False           # x_0 as 32 zero bytes instead of the empty string
     stmt_no_counts: bool = False    # leave u32(b) || u32(|S_k|) out of the statement
+    stmt_rows_flat: bool = False    # the C_a themselves in the statement instead of their tree root
+    stmt_odd_dup: bool = False      # an odd last node of the statement tree paired with itself
     z_without_x: bool = False       # z from v_l alone
     path_root_first: bool = False   # path digests listed root-down instead of leaf-up
     rho_tag: str = "FP-rho"
@@ -57,6 +62,20 @@ def u32(v: int, rd: Reading) -> bytes:
 
 def u64(v: int, rd: Reading) -> bytes:
     return v.to_bytes(8, rd.int_order)
+
+
+def stmt_rows(rows: list, rd: Reading) -> bytes:
+    """D_k: the tree over the block's row commitments (or, read flat, the commitments themselves)."""
+    if rd.stmt_rows_flat:
+        return b"".join(rows)
+    level = [sha(b"FP-sleaf", r) for r in rows]
+    while len(level) > 1:
+        pairs = [(level[i], level[i + 1]) for i in range(0, len(level) - 1, 2)]
+        up = [sha(b"FP-snode", *((r, l) if rd.node_swap else (l, r))) for l, r in pairs]
+        if len(level) % 2:
+            up.append(sha(b"FP-snode", level[-1], level[-1]) if rd.stmt_odd_dup else level[-1])
+        level = up
+    return level[0]
 
 
 def hfr_nonzero(tag: str, data: bytes) -> int:
@@ -103,7 +122,7 @@ class Derivation:
         stmt = self.C + u32(k, rd)
         if not rd.stmt_no_counts:
             stmt += u32(b, rd) + u32(hi - lo, rd)
-        stmt += b"".join(self.rows[lo:hi])
+        stmt += stmt_rows(self.rows[lo:hi], rd)
         hs = sha(stmt)
         bv = [0] * R
         for a in range(lo, hi):
@@ -249,6 +268,8 @@ MUTATIONS = [
     Reading(node_swap=True),
     Reading(x0_zero=True),
     Reading(stmt_no_counts=True),
+    Reading(stmt_rows_flat=True),
+    Reading(stmt_odd_dup=True),
     Reading(z_without_x=True),
     Reading(path_root_first=True),
     Reading(rho_tag="FP-r"),
