@@ -776,6 +776,178 @@ FPG_NOINL void wm_add(WMill& S, const fq& mxP, const fq& yP) {
     wsync<NW>();
 }
 
+// ---------------------------------------------------------------------------------------
+// Pipelined doubling steps on the block engine.  The line of a doubling step and the next point
+// 2T depend on T alone, not on f, so the point's chain runs one round ahead of f's:
+//   round 1: f^2 (57 products) and the line / 2T products of T (15, from the operands formed in
+//            the previous round);  round 2: f^2 * line (54) and the products of the new T (12).
+// Two product rounds per doubling step instead of three; the same products and sums as wm_dbl.
+// Layout of S.p: round 1: f^2 at 0..56, line / 2T at 57..71; round 2: f^2 * line at 0..53, the
+// point's products at 54..65 (X^2 54, 55; Y^2 56, 57; Z^2 58, 59; Y Z 60..62; X Y 63..65).
+// ---------------------------------------------------------------------------------------
+constexpr int WMP_T = 54, WMP_B = 57;
+
+// product u < 12 of the point T (S.T): X^2, Y^2, Z^2 (squares), Y Z, X Y (Karatsuba)
+FPG_DEV void wmp_point_ops(const WMill& S, int u, fq& x, fq& y) {
+    fq zero;
+    fq_zero(zero);
+    const fq* a;
+    const fq* b;
+    int kind, mode;
+    if (u < 6) { a = b = S.T + 2 * (u >> 1); kind = u & 1; mode = 1; }
+    else if (u < 9) { a = S.T + 2; b = S.T + 4; kind = u - 6; mode = 0; }
+    else { a = S.T; b = S.T + 2; kind = u - 9; mode = 0; }
+    prod_ops(x, y, a, b, kind, mode, zero);
+}
+// from the point's products: XX, YY, ZZ, YZ, XY (S.v[0..9]) on lanes 96..105
+FPG_DEV void wmp_point_parts(WMill& S, int L) {
+    if (L >= 96 && L < 106) {
+        const int v = L - 96, which = v >> 1, e = v & 1;
+        S.v[v] = fq_select(which < 3, sq_part(&S.p[WMP_T + 2 * (which < 3 ? which : 0)], e),
+                           kara_part(&S.p[WMP_T + 6 + 3 * (which < 3 ? 0 : which - 3)], e));
+    }
+}
+// round B's operands from ZZ and YY (S.v[16..27]) on lanes 96..107, as in wm_dbl
+FPG_DEV void wmp_line_operands(WMill& S, int L) {
+    if (L >= 96 && L < 108) {
+        const int u = L - 96, e = u & 1, kind = u >> 1;
+        const fq zr = S.p[WMP_T + 4], zi = fq_dbl(S.p[WMP_T + 5]);
+        const fq bze = fq_dbl(fq_dbl(fq_select(e, fq_add(zr, zi), fq_sub(zr, zi))));
+        const fq yy = fq_select(e, fq_dbl(S.p[WMP_T + 3]), S.p[WMP_T + 2]);
+        const fq b3 = fq_add(fq_dbl(bze), bze);
+        const fq b9 = fq_add(fq_dbl(b3), b3);
+        const fq b6 = fq_dbl(b3);
+        const fq sub_t = fq_select(kind == 1, b9, b3), add_t = fq_select(kind == 2, b9, b6);
+        const fq r_sub = fq_sub(yy, sub_t);
+        const fq r_add = fq_add(fq_select(kind == 2, yy, fq_dbl(b6)), add_t);
+        S.v[16 + u] = fq_select(kind == 0, bze,
+                                fq_select(kind == 1 || kind == 3, r_sub, fq_select(kind == 4, b6, r_add)));
+    }
+}
+// the point's products of S.T and what the next step's line needs from them (start of the chain,
+// and after an addition step)
+template <int NW>
+FPG_NOINL void wmp_prime(WMill& S) {
+    const int L = w_lane<NW>();
+    if (L >= WMP_T && L < WMP_T + 12) {
+        fq x, y;
+        wmp_point_ops(S, L - WMP_T, x, y);
+        S.p[L] = fq_mul(x, y);
+    }
+    wsync<NW>();
+    wmp_point_parts(S, L);
+    wsync<NW>();
+    wmp_line_operands(S, L);
+    wsync<NW>();
+}
+// one doubling step: S.f <- S.f^2 * line(T), S.T <- 2T, with XX .. XY and round B's operands of T
+// in S.v on entry and of 2T on exit
+template <int NW>
+FPG_NOINL void wmp_dbl(WMill& S, const fq& m3x, const fq& y2) {
+    const int L = w_lane<NW>();
+    // round 1: f^2 and the line / 2T products (the lanes choose their operands, then one product
+    // call for all: a warp whose lanes reached the product through two branches would run it twice)
+    if (L < WMP_B + 15) {
+        const fq* a;
+        const fq* b;
+        int kind, mode;
+        fq sc = m3x;
+        if (L < 12) {                                                            // f_k^2
+            a = b = S.f + 2 * (L >> 1);
+            kind = L & 1;
+            mode = 1;
+        } else if (L < WMP_B) {                                                  // f_i f_j, i < j
+            const int c = (L - 12) / 3;
+            int i = 0, rem = c;
+            while (rem >= 5 - i) { rem -= 5 - i; i++; }
+            a = S.f + 2 * i;
+            b = S.f + 2 * (i + 1 + rem);
+            kind = L - 12 - 3 * c;
+            mode = 0;
+        } else {
+            const int t = L - WMP_B;
+            const fq* XX = S.v;
+            const fq* YY = S.v + 2;
+            const fq* YZ = S.v + 6;
+            const fq* XY = S.v + 8;
+            if (t < 2) { a = b = XX; kind = t; mode = 2; }                           // m3x XX
+            else if (t < 4) { a = b = YZ; kind = t - 2; mode = 2; sc = y2; }         // y2 YZ
+            else if (t < 7) { a = XY; b = S.v + 18; kind = t - 4; mode = 0; }        // XY (YY - 9 bz)
+            else if (t < 9) { a = b = S.v + 20; kind = t - 7; mode = 1; }            // (YY + 9 bz)^2
+            else if (t < 12) { a = S.v + 24; b = S.v + 26; kind = t - 9; mode = 0; } // 108 bz^2
+            else { a = YY; b = YZ; kind = t - 12; mode = 0; }                        // YY YZ
+        }
+        fq x, y;
+        prod_ops(x, y, a, b, kind, mode, sc);
+        S.p[L] = fq_mul(x, y);
+    }
+    wsync<NW>();
+    // f^2 terms (lanes 0..71); then beside their sums (warp 0) the line (warp 3: l0 = YY - 3 bz,
+    // l2 = m3x XX, l3 = y2 YZ) and 2T, one formula per warp (X' = 2 XY (YY - 9 bz) on warp 1,
+    // Y' = (YY + 9 bz)^2 - 108 bz^2 on warp 2, Z' = 8 YY YZ on warp 3)
+    if (L < 72) {
+        const int o = L % 12, i = L / 12, k = o >> 1, e = o & 1;
+        int j = k - i;
+        if (j < 0) j += 6;
+        const int c = i < j ? i * (11 - i) / 2 + (j - i - 1) : 0;
+        const fq* ms = &S.p[2 * i];
+        const fq* mk = &S.p[12 + 3 * c];
+        const fq re = fq_select(i == j, sq_part(ms, 0), fq_dbl(kara_part(mk, 0)));
+        const fq im = fq_select(i == j, sq_part(ms, 1), fq_dbl(kara_part(mk, 1)));
+        fq zero;
+        fq_zero(zero);
+        S.tm[L] = fq_select(i <= j, twist_part(re, im, e, i + j >= 6), zero);
+    }
+    wsync<NW>();
+    {
+        const int w = L >> 5, pl = L & 31;
+        if (w == 0 && pl < 12) {
+            fq acc = S.tm[L];
+            for (int i = 1; i < 6; i++) acc = fq_add(acc, S.tm[12 * i + L]);
+            S.g[L] = acc;
+        } else if (w == 1 && pl < 2) {
+            S.T[pl] = fq_dbl(kara_part(&S.p[WMP_B + 4], pl));
+        } else if (w == 2 && pl < 2) {
+            S.T[2 + pl] = fq_sub(sq_part(&S.p[WMP_B + 7], pl), kara_part(&S.p[WMP_B + 9], pl));
+        } else if (w == 3 && pl < 2) {
+            S.T[4 + pl] = fq_dbl(fq_dbl(fq_dbl(kara_part(&S.p[WMP_B + 12], pl))));
+        } else if (w == 3 && pl >= 8 && pl < 14) {
+            const int q = pl - 8, e = q & 1, which = q >> 1;
+            S.l[q] = fq_select(which == 0, S.v[22 + e], S.p[WMP_B + 2 * (which ? which - 1 : 0) + e]);
+        }
+    }
+    wsync<NW>();
+    // round 2: f^2 * line and the products of the new point (one product call, as above)
+    if (L < WMP_T + 12) {
+        const fq* a;
+        const fq* b;
+        int kind, mode;
+        if (L < 54) {                              // f^2 * line: f^2_i l_term (wm_line_products)
+            const int q = L / 3, term = q / 6, k = q - 6 * term;
+            const int i = term == 0 ? k : (term == 1 ? (k + 4) % 6 : (k + 3) % 6);
+            a = S.g + 2 * i;
+            b = S.l + 2 * term;
+            kind = L - 3 * q;
+            mode = 0;
+        } else {
+            const int u = L - WMP_T;
+            if (u < 6) { a = b = S.T + 2 * (u >> 1); kind = u & 1; mode = 1; }
+            else if (u < 9) { a = S.T + 2; b = S.T + 4; kind = u - 6; mode = 0; }
+            else { a = S.T; b = S.T + 2; kind = u - 9; mode = 0; }
+        }
+        fq x, y;
+        prod_ops(x, y, a, b, kind, mode, m3x);
+        S.p[L] = fq_mul(x, y);
+    }
+    wsync<NW>();
+    wm_line_terms(S, L);
+    wmp_point_parts(S, L);
+    wsync<NW>();
+    if (L < 12) S.f[L] = wm_line_sum(S, L);
+    wmp_line_operands(S, L);
+    wsync<NW>();
+}
+
 // S.f <- conj(f_{|x|,Q}(P)) in flat order; 1 when P or Q is the identity
 template <int NW>
 FPG_NOINL void w_miller(WMill& S, g1a P, g2a Q) {
@@ -800,9 +972,20 @@ FPG_NOINL void w_miller(WMill& S, g1a P, g2a Q) {
         S.Q[0] = Q.x.c0; S.Q[1] = Q.x.c1; S.Q[2] = Q.y.c0; S.Q[3] = Q.y.c1;
     }
     wsync<NW>();
-    for (int i = 62; i >= 0; i--) {
-        wm_dbl<NW>(S, m3x, y2);
-        if ((BLS_X_ABS >> i) & 1) wm_add<NW>(S, mxP, P.y);
+    if (NW == 4) {                                  // pipelined doubling steps
+        wmp_prime<NW>(S);
+        for (int i = 62; i >= 0; i--) {
+            wmp_dbl<NW>(S, m3x, y2);
+            if ((BLS_X_ABS >> i) & 1) {
+                wm_add<NW>(S, mxP, P.y);
+                if (i) wmp_prime<NW>(S);
+            }
+        }
+    } else {
+        for (int i = 62; i >= 0; i--) {
+            wm_dbl<NW>(S, m3x, y2);
+            if ((BLS_X_ABS >> i) & 1) wm_add<NW>(S, mxP, P.y);
+        }
     }
     if (L < 12) {
         fq one;
