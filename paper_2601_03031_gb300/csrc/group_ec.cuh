@@ -453,3 +453,17 @@ FPG_DEV int glv_window(const uint32_t* k0, const uint32_t* k1, int w) {
 FPG_DEV int gls_position(const uint32_t (*d)[2], int i) {
     return bit_of(d[0], i) | (bit_of(d[1], i) << 1) | (bit_of(d[2], i) << 2) | (bit_of(d[3], i) << 3);
 }
+
+// Jacobian (x = X / Z^2, y = Y / Z^3) <-> homogeneous projective (x = X / Z, y = Y / Z), the
+// identity to the identity (a Jacobian point with Z = 0, whatever X and Y, maps to (0 : 1 : 0))
+template <typename F>
+FPG_DEV GPt<F> jac_to_proj(const jac<F>& p) {
+    const F z2 = f_sqr(p.Z);
+    F one;
+    f_set_one(one);
+    return {f_mul(p.X, p.Z), f_sel(f_is_zero(p.Z), one, p.Y), f_mul(z2, p.Z)};
+}
+template <typename F>
+FPG_DEV jac<F> proj_to_jac(const GPt<F>& p) {
+    return {f_mul(p.X, p.Z), f_mul(p.Y, f_sqr(p.Z)), p.Z};
+}

@@ -105,20 +105,6 @@ void g2_pair_reduce(const void* in, void* out, uint64_t n, cudaStream_t s) {
     if (n) FP_KERNEL("k_g2_pair", s, k_g2_pair<<<grid_for(n, 64), 64, 0, s>>>((const g2j*)in, (g2j*)out, n));
 }
 
-// Jacobian (x = X / Z^2, y = Y / Z^3) <-> homogeneous projective (x = X / Z, y = Y / Z), the
-// identity to the identity (a Jacobian point with Z = 0, whatever X and Y, maps to (0 : 1 : 0))
-template <typename F>
-FPG_DEV GPt<F> jac_to_proj(const jac<F>& p) {
-    const F z2 = f_sqr(p.Z);
-    F one;
-    f_set_one(one);
-    return {f_mul(p.X, p.Z), f_sel(f_is_zero(p.Z), one, p.Y), f_mul(z2, p.Z)};
-}
-template <typename F>
-FPG_DEV jac<F> proj_to_jac(const GPt<F>& p) {
-    return {f_mul(p.X, p.Z), f_mul(p.Y, f_sqr(p.Z)), p.Z};
-}
-
 // Latency-bound sums of consecutive points, in one launch per factor of 16 or 32: out[g] = the sum of
 // in[gs g .. gs g + gs - 1] (gs <= 32 for G1, <= 16 for G2; inputs past n_in count as the identity).
 // G1: a 128-thread block per sum, 16 8-lane groups (group_ec.cuh) each adding two inputs, then a tree

@@ -550,6 +550,66 @@ void step1_kzg(const void* A, const void* v, const void* xprev, const void* xinv
                                                              (const fr*)xinv_all, K, R, log_r, (uint8_t*)blocks,
                                                              bopen_len, (fr*)pcoef, (fr*)q_canon, C));
 }
+// Comb tables of fixed G2 bases (the W proofs' g2^{beta^i}, built once at setup): per base its 64
+// position tables (gpt_g2_comb_table) at tab[(i 64 + pos) 16], from the chain 2^pos B_i (a warp per
+// base, then a thread per table).
+__global__ void __launch_bounds__(128) k_g2_chain(const g2a* pts, uint32_t n, GPt<fq2>* chain) {
+    __shared__ GEcWs sm[4];
+    const int w = threadIdx.x >> 5, L = threadIdx.x & 31;
+    const uint64_t t = (uint64_t)blockIdx.x * 4 + w;
+    if (t >= n) return;                                       // warp-uniform
+    GPt<fq2> acc = gec_from_affine_or_inf(pts[t].x, pts[t].y);
+    for (int i = 0; i < 64; i++) {
+        if (i) acc = gecw_dbl(sm[w], L, acc);
+        if (L == 0) chain[t * 64 + i] = acc;
+    }
+}
+__global__ void __launch_bounds__(64) k_g2_comb_tab(uint64_t m, const GPt<fq2>* chain, GPt<fq2>* tab) {
+    const uint64_t u = gtid();
+    if (u < m) gpt_g2_comb_table(chain[u], tab + u * 16);
+}
+size_t g2_comb_bytes(uint32_t n) { return (size_t)n * 64 * 16 * sizeof(GPt<fq2>); }
+size_t g2_comb_chain_bytes(uint32_t n) { return (size_t)n * 64 * sizeof(GPt<fq2>); }
+void g2_comb_tables(const void* pts_g2a, uint32_t n, void* chain_scratch, void* tab, cudaStream_t s) {
+    if (!n) return;
+    FP_KERNEL("k_g2_chain", s, k_g2_chain<<<(n + 3) / 4, 128, 0, s>>>((const g2a*)pts_g2a, n, (GPt<fq2>*)chain_scratch));
+    FP_KERNEL("k_g2_comb_tab", s, k_g2_comb_tab<<<grid_for((uint64_t)n * 64, 64), 64, 0, s>>>(
+                                      (uint64_t)n * 64, (const GPt<fq2>*)chain_scratch, (GPt<fq2>*)tab));
+}
+
+// W terms q_i g2^{beta^i} from the comb tables: one 128-thread block per term (k, i < 2R), 16 8-lane
+// groups on G2 (group_ec.cuh with F = Fq2) each adding the entries of positions g, g + 16, g + 32,
+// g + 48 of the GLS digits of q_i, then a tree over the groups; term 2R - 1 is the identity
+__global__ void __launch_bounds__(128) k_w_comb(const GPt<fq2>* tab, const fr* q_canon, uint32_t R, g2j* out) {
+    __shared__ GEcs<fq2> e[16];
+    __shared__ GPt<fq2> part[16];
+    const int grp = threadIdx.x >> 3, lane = threadIdx.x & 7;
+    const uint64_t t = blockIdx.x;
+    const uint32_t i = (uint32_t)(t % (2 * R));
+    const bool live = i < 2 * R - 1;
+    uint32_t d[4][2];
+    gls_digits(d, q_canon[t].v);
+    const GPt<fq2>* tb = tab + (size_t)(live ? i : 0) * 64 * 16;
+    const GPt<fq2> id = gec_identity<fq2>();
+    GPt<fq2> acc = live ? tb[grp * 16 + gls_position(d, grp)] : id;
+    for (int j = 1; j < 4; j++) {
+        const int pos = grp + 16 * j;
+        acc = gec_add(e[grp], lane, acc, live ? tb[pos * 16 + gls_position(d, pos)] : id);
+    }
+    for (int sh = 8; sh >= 1; sh >>= 1) {
+        __syncthreads();
+        if (lane == 0) part[grp] = acc;
+        __syncthreads();
+        const GPt<fq2> r = gec_add(e[grp], lane, acc, part[grp < sh ? grp + sh : grp]);
+        if (grp < sh) acc = r;
+    }
+    if (grp == 0 && lane == 0) out[t] = proj_to_jac(acc);
+}
+void step1_w_comb(const void* tab, const void* q_canon, uint32_t K, uint32_t R, void* out, cudaStream_t s) {
+    FP_KERNEL("k_w_comb", s, k_w_comb<<<(unsigned)((uint64_t)K * 2 * R), 128, 0, s>>>((const GPt<fq2>*)tab,
+                                                                                    (const fr*)q_canon, R, (g2j*)out));
+}
+
 void step1_w_terms(const void* g2pow, const void* q_canon, uint32_t K, uint32_t R, void* out, cudaStream_t s) {
     const uint64_t n = (uint64_t)K * 2 * R;
     if (n <= engine_limits().wterm_warp_max) {      // few terms: a warp per term for latency

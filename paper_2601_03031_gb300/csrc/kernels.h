@@ -133,6 +133,14 @@ void step1_challenge(void* blocks, size_t bopen_len, uint32_t K, int j, void* xp
 void step1_kzg(const void* A, const void* v, const void* xprev, const void* xinv_all, uint32_t K, uint32_t R,
                int log_r, void* blocks, size_t bopen_len, void* pcoef, void* q_canon, cudaStream_t s);
 void step1_w_terms(const void* g2pow, const void* q_canon, uint32_t K, uint32_t R, void* out_g2j, cudaStream_t s);
+// the same terms from the comb tables of g2pow (g2_comb_tables): one table entry per position
+void step1_w_comb(const void* tab, const void* q_canon, uint32_t K, uint32_t R, void* out_g2j, cudaStream_t s);
+// comb tables of n fixed G2 points (64 positions x 16 entries each, g2_comb_bytes(n) bytes), through
+// a scratch of n 64 projective points
+constexpr uint32_t G2_COMB_MAX_R = 1024;        // setups with R <= this keep the W proofs' comb tables
+size_t g2_comb_bytes(uint32_t n);
+size_t g2_comb_chain_bytes(uint32_t n);
+void g2_comb_tables(const void* pts_g2a, uint32_t n, void* chain_scratch, void* tab, cudaStream_t s);
 
 // ---- Step 2
 void step2_leaves(const void* m_canon, uint32_t R, uint32_t M, void* row_tree, cudaStream_t s);

@@ -25,6 +25,7 @@ struct fp_pp {
     void* lam = nullptr;      // G1 affine, 2M - 1: Lambda_t at offset 2^t - 1
     void* lam_tab = nullptr;  // G1 affine, 2M: Lambda_{l_c} and its GLV partners (MSM bases)
     void* g2w_tab = nullptr;  // G2 affine, 4 x 2R: (-1)^h psi^h(g2^{beta^i}) (W-proof MSM bases)
+    void* g2comb = nullptr;   // comb tables of g2^{beta^i}, i < 2R - 1 (W proofs of few blocks; R <= G2_COMB_MAX_R)
     void* g1beta = nullptr;   // G1 affine
     void* g2pow = nullptr;    // G2 affine, 2R - 1: g2^{beta^i}
     void* g2tau = nullptr;    // G2 affine, l_c
@@ -259,6 +260,12 @@ fp_status vc_setup_split(uint32_t log_r, uint32_t log_c, uint32_t b, uint64_t se
             g1_gen_mul(beta_s, 1, pp->g1beta, s);
             g2_gen_mul(pow_s, 2 * R - 1, pp->g2pow, s);
             msm_bases_g2(pp->g2pow, 2 * R - 1, 2 * R, pp->g2w_tab, s);
+            if (R <= G2_COMB_MAX_R) {
+                pp->g2comb = dalloc(g2_comb_bytes(2 * R - 1), s);
+                void* chain = dalloc(g2_comb_chain_bytes(2 * R - 1), s);
+                g2_comb_tables(pp->g2pow, 2 * R - 1, chain, pp->g2comb, s);
+                dfree(chain, s);
+            }
             g2_gen_mul(tau_s, log_c, pp->g2tau, s);
             check_launch("vc_setup kernels");
             // the trapdoor and its scalar tables are cleared before release
@@ -421,6 +428,7 @@ fp_status vc_pp_view_split(const fp_pp* pp, uint32_t log_r, uint32_t log_c, fp_p
         v->g1beta = root->g1beta;
         v->g2pow = root->g2pow;             // g2^{beta^i}, i < 2R - 1: a prefix
         v->g2tau = root->g2tau;             // tau_0 .. tau_{l_c - 1}: a prefix
+        v->g2comb = root->g2comb;           // the tables of a prefix of g2pow
         cudaStream_t s = 0;
         try {
             v->lam_tab = dalloc(2 * (size_t)M * G1A_BYTES, s);
@@ -567,7 +575,8 @@ void step1_rounds(const fp_pp* pp, uint32_t k0, uint32_t Kc, uint32_t b, const S
     if (B.w_msm) {
         msm_g2(pp->g2w_tab, B.q, B.wsh, B.wscr, nullptr, w_out, blen, s1);
     } else {
-        step1_w_terms(pp->g2pow, B.q, Kc, R, B.wt, s1);
+        if (pp->g2comb) step1_w_comb(pp->g2comb, B.q, Kc, R, B.wt, s1);
+        else step1_w_terms(pp->g2pow, B.q, Kc, R, B.wt, s1);
         void* wr = (uint64_t)Kc * 2 * R <= TREE_REDUCE_MAX
                        ? reduce_tree(B.wt, B.wt2, (uint64_t)Kc * 2 * R, Kc, 16, g2_tree_reduce, s1)
                        : reduce_pairs(B.wt, B.wt2, (uint64_t)Kc * 2 * R, Kc, g2_pair_reduce, s1);
@@ -683,7 +692,8 @@ void step1_rounds_la(const fp_pp* pp, uint32_t k0, uint32_t Kc, uint32_t b, cons
     if (B.w_msm) {
         msm_g2(pp->g2w_tab, B.q, B.wsh, B.wscr, nullptr, w_out, blen, s1);
     } else {
-        step1_w_terms(pp->g2pow, B.q, Kc, R, B.wt, s1);
+        if (pp->g2comb) step1_w_comb(pp->g2comb, B.q, Kc, R, B.wt, s1);
+        else step1_w_terms(pp->g2pow, B.q, Kc, R, B.wt, s1);
         void* wr = (uint64_t)Kc * 2 * R <= TREE_REDUCE_MAX
                        ? reduce_tree(B.wt, B.wt2, (uint64_t)Kc * 2 * R, Kc, 16, g2_tree_reduce, s1)
                        : reduce_pairs(B.wt, B.wt2, (uint64_t)Kc * 2 * R, Kc, g2_pair_reduce, s1);
@@ -1587,7 +1597,7 @@ void fp_pp_free(fp_pp* pp) {
     cudaFree(pp->lam_tab);
     cudaFree(pp->g2w_tab);
     if (!pp->parent) {
-        cudaFree(pp->lam); cudaFree(pp->g1beta); cudaFree(pp->g2pow); cudaFree(pp->g2tau);
+        cudaFree(pp->lam); cudaFree(pp->g1beta); cudaFree(pp->g2pow); cudaFree(pp->g2tau); cudaFree(pp->g2comb);
     }
     delete pp;
 }
