@@ -159,8 +159,8 @@ void emu_g1_comb(const uint8_t* p, const uint32_t* k, uint8_t* out) {
     gec_to_affine(a.x, a.y, r);
     g1a_to_be(out, a);
 }
-// k Q through the comb on G2: the chain 2^i Q (i < 64) and the sum of one entry per position on one
-// warp, the 64 position tables (gpt_g2_comb_table) on one thread
+// k Q through the comb on G2: the chain 2^i Q (i < 64) on one warp, the 64 position tables
+// (gpt_g2_comb_table) on one thread, the sum of one entry per position on an 8-lane group
 void emu_g2_comb(const uint8_t* q, const uint32_t* k, uint8_t* out) {
     const g2a Q = be_g2(q);
     static GPt<fq2> chain[64], tab[64 * 16];
@@ -176,10 +176,15 @@ void emu_g2_comb(const uint8_t* q, const uint32_t* k, uint8_t* out) {
         if (L == 0)
             for (int i = 0; i < 64; i++) gpt_g2_comb_table(chain[i], tab + 16 * i);
         __syncwarp();
+    });
+    // the sum on an 8-lane group with Fq2 products on each lane (the engine of k_fold_c, k_w_comb)
+    static GEcs<fq2> e2;
+    lanes(8, [&] {
+        const int L = (int)threadIdx.x;
         uint32_t d[4][2];
         gls_digits(d, k);
         GPt<fq2> s = gec_identity<fq2>();
-        for (int i = 0; i < 64; i++) s = gecw_add(g_g2, L, s, tab[16 * i + gls_position(d, i)]);
+        for (int i = 0; i < 64; i++) s = gec_add(e2, L, s, tab[16 * i + gls_position(d, i)]);
         if (L == 0) r = s;
     });
     g2a a;
