@@ -141,6 +141,16 @@ constexpr uint32_t G2_COMB_MAX_R = 1024;        // setups with R <= this keep th
 size_t g2_comb_bytes(uint32_t n);
 size_t g2_comb_chain_bytes(uint32_t n);
 void g2_comb_tables(const void* pts_g2a, uint32_t n, void* chain_scratch, void* tab, cudaStream_t s);
+// Commit by fixed-base combs of the bases Lambda_a (k_lamcomb.cu): lam_comb_tables builds, at setup,
+// 32 windows x 256 affine entries per base (lam_comb_bytes(M); scratch lam_comb_scratch_bytes(M));
+// lam_comb_partials writes lam_comb_parts() Jacobian partial sums per (row j, base a) at
+// partial[(j M + a) parts + q], whose sum over (a, q) is C_j
+constexpr uint32_t LAM_COMB_MAX_M = 1024;       // setups with M <= this keep the commit's comb tables
+size_t lam_comb_bytes(uint32_t M);
+size_t lam_comb_scratch_bytes(uint32_t M);
+void lam_comb_tables(const void* bases_g1a, uint32_t M, void* scratch, void* tab, cudaStream_t s);
+void lam_comb_partials(const void* tab, const void* m_canon, uint32_t R, uint32_t M, void* partial_g1j, cudaStream_t s);
+uint32_t lam_comb_parts();
 
 // ---- Step 2
 void step2_leaves(const void* m_canon, uint32_t R, uint32_t M, void* row_tree, cudaStream_t s);

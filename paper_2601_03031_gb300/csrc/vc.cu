@@ -26,6 +26,7 @@ struct fp_pp {
     void* lam_tab = nullptr;  // G1 affine, 2M: Lambda_{l_c} and its GLV partners (MSM bases)
     void* g2w_tab = nullptr;  // G2 affine, 4 x 2R: (-1)^h psi^h(g2^{beta^i}) (W-proof MSM bases)
     void* g2comb = nullptr;   // comb tables of g2^{beta^i}, i < 2R - 1 (W proofs of few blocks; R <= G2_COMB_MAX_R)
+    void* lam_comb = nullptr; // comb tables of Lambda_{l_c} (the commit's bases; M <= LAM_COMB_MAX_M), own per view
     void* g1beta = nullptr;   // G1 affine
     void* g2pow = nullptr;    // G2 affine, 2R - 1: g2^{beta^i}
     void* g2tau = nullptr;    // G2 affine, l_c
@@ -256,6 +257,12 @@ fp_status vc_setup_split(uint32_t log_r, uint32_t log_c, uint32_t b, uint64_t se
             check(cudaMemcpyAsync(pp->lam_tab, (uint8_t*)pp->lam + ((size_t)M - 1) * G1A_BYTES, (size_t)M * G1A_BYTES,
                                   cudaMemcpyDeviceToDevice, s), "D2D");
             msm_bases_endo(pp->lam_tab, M, s);
+            if (M <= LAM_COMB_MAX_M) {
+                pp->lam_comb = dalloc(lam_comb_bytes(M), s);
+                void* scr = dalloc(lam_comb_scratch_bytes(M), s);
+                lam_comb_tables(pp->lam_tab, M, scr, pp->lam_comb, s);
+                dfree(scr, s);
+            }
             pp->g2w_tab = dalloc(8 * (size_t)R * G2A_BYTES, s);
             g1_gen_mul(beta_s, 1, pp->g1beta, s);
             g2_gen_mul(pow_s, 2 * R - 1, pp->g2pow, s);
@@ -328,7 +335,7 @@ fp_commit* commit_enqueue(const fp_pp* pp, const uint64_t* m, int on_device, cud
     const uint64_t N = (uint64_t)R * M;
     fp_commit* cm = new fp_commit{pp};
     cm->stream = s;
-    void *src = nullptr, *t1 = nullptr, *ml = nullptr, *ml2 = nullptr;
+    void *src = nullptr, *t1 = nullptr, *t2 = nullptr, *ml = nullptr, *ml2 = nullptr;
     try {
         cm->m_canon = dalloc(N * FR_BYTES, s);
         cm->m_mont = dalloc(N * FR_BYTES, s);
@@ -346,10 +353,23 @@ fp_commit* commit_enqueue(const fp_pp* pp, const uint64_t* m, int on_device, cud
             msrc = src;
         }
         load_vector(msrc, N, cm->m_canon, cm->m_mont, cm->err, s);
-        // C_j = sum_a m[jM + a] Lambda_{l_c}[a]: R MSMs of M terms over the shared bases
-        const MsmShape sh = msm_shape(M, R, M, fp_msm_window(M, R));
-        t1 = dalloc(msm_scratch_bytes(sh), s);
-        msm_g1(pp->lam_tab, cm->m_canon, sh, t1, cm->rows, cm->rows_ser, s);
+        // C_j = sum_a m[jM + a] Lambda_{l_c}[a]: R sums of M terms over the shared bases, from their
+        // comb tables when the setup has them (partial sums per base and quarter of the windows,
+        // reduced pairwise and then by block trees), else R MSMs
+        if (pp->lam_comb) {
+            const uint64_t np = (uint64_t)R * M * lam_comb_parts();
+            t1 = dalloc(np * G1J_BYTES, s);
+            t2 = dalloc((np / 2 + 1) * G1J_BYTES, s);
+            lam_comb_partials(pp->lam_comb, cm->m_canon, R, M, t1, s);
+            void* r1 = reduce_pairs(t1, t2, np, std::min<uint64_t>(np, (uint64_t)R * 32), g1_pair_reduce, s);
+            void* r2 = reduce_tree(r1, r1 == t1 ? t2 : t1, std::min<uint64_t>(np, (uint64_t)R * 32), R, 32,
+                                   g1_tree_reduce, s);
+            g1j_to_affine(r2, cm->rows, cm->rows_ser, G1_SER, R, s);
+        } else {
+            const MsmShape sh = msm_shape(M, R, M, fp_msm_window(M, R));
+            t1 = dalloc(msm_scratch_bytes(sh), s);
+            msm_g1(pp->lam_tab, cm->m_canon, sh, t1, cm->rows, cm->rows_ser, s);
+        }
         // C = prod_j e(C_j, v_j): R Miller loops, pairwise products, one final exponentiation
         ml = dalloc(R * FQ12_BYTES, s);
         ml2 = dalloc((R / 2 + 1) * FQ12_BYTES, s);
@@ -357,11 +377,11 @@ fp_commit* commit_enqueue(const fp_pp* pp, const uint64_t* m, int on_device, cud
         void* prod = reduce_pairs(ml, ml2, R, 1, fq12_pair_reduce, s);
         final_exp_group(prod, 1, cm->C, cm->C_ser, 1, GT_SER, 0, s);
         check_launch("vc_commit kernels");
-        dfree(src, s); dfree(t1, s); dfree(ml, s); dfree(ml2, s);
+        dfree(src, s); dfree(t1, s); dfree(t2, s); dfree(ml, s); dfree(ml2, s);
         check(cudaEventRecord(cm->done, s), "event");
     } catch (...) {
         cudaStreamSynchronize(s);
-        dfree(src, s); dfree(t1, s); dfree(ml, s); dfree(ml2, s);
+        dfree(src, s); dfree(t1, s); dfree(t2, s); dfree(ml, s); dfree(ml2, s);
         fp_commit_free(cm);
         throw;
     }
@@ -435,6 +455,12 @@ fp_status vc_pp_view_split(const fp_pp* pp, uint32_t log_r, uint32_t log_c, fp_p
             check(cudaMemcpyAsync(v->lam_tab, (uint8_t*)root->lam + ((size_t)M - 1) * G1A_BYTES, (size_t)M * G1A_BYTES,
                                   cudaMemcpyDeviceToDevice, s), "D2D");
             msm_bases_endo(v->lam_tab, M, s);
+            if (M <= LAM_COMB_MAX_M) {
+                v->lam_comb = dalloc(lam_comb_bytes(M), s);
+                void* scr = dalloc(lam_comb_scratch_bytes(M), s);
+                lam_comb_tables(v->lam_tab, M, scr, v->lam_comb, s);
+                dfree(scr, s);
+            }
             v->g2w_tab = dalloc(8 * (size_t)R * G2A_BYTES, s);
             msm_bases_g2(v->g2pow, 2 * R - 1, 2 * R, v->g2w_tab, s);
             check_launch("vc_pp_view");
@@ -1595,6 +1621,7 @@ void fp_pp_free(fp_pp* pp) {
     if (!pp) return;
     cudaDeviceSynchronize();
     cudaFree(pp->lam_tab);
+    cudaFree(pp->lam_comb);
     cudaFree(pp->g2w_tab);
     if (!pp->parent) {
         cudaFree(pp->lam); cudaFree(pp->g1beta); cudaFree(pp->g2pow); cudaFree(pp->g2tau); cudaFree(pp->g2comb);
