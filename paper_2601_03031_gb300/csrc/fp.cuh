@@ -211,23 +211,26 @@ FPG_DEV void inv_ds(uint32_t* r, const uint32_t* x, const uint32_t* P, uint32_t 
         if (is_zero<N + 1>(g)) break;
         uint32_t fl = f[0], gl = g[0];
         int32_t u = 1, v = 0, q = 0, w = 1;
-#pragma unroll 1
+        // 30 divsteps on the low words, without branches: a swap (delta > 0 and g odd) exchanges
+        // (f, g) <- (g, -f), (u, v, q, w) <- (q, w, -u, -v), delta <- -delta, by masks; then g odd
+        // adds f to g and (u, v) to (q, w); then delta + 1, g / 2, (u, v) * 2
+#pragma unroll 5
         for (int i = 0; i < 30; i++) {
-            const bool godd = gl & 1;
-            if (delta > 0 && godd) {                        // swap rows, negate g so the add gives g - f
-                delta = -delta;
-                const uint32_t tf = fl;
-                fl = gl;
-                gl = 0u - tf;
-                const int32_t tu = u, tv = v;
-                u = q; v = w;
-                q = -tu; w = -tv;
-            }
-            if (godd) {
-                gl += fl;
-                q += u;
-                w += v;
-            }
+            const uint32_t godd = 0u - (gl & 1u);
+            const uint32_t sw = godd & (uint32_t)((0 - delta) >> 31);
+            const int32_t ms = (int32_t)sw, mo = (int32_t)godd;
+            const uint32_t tf = fl;
+            fl ^= (fl ^ gl) & sw;
+            gl ^= (gl ^ (0u - tf)) & sw;
+            const int32_t tu = u, tv = v;
+            u ^= (u ^ q) & ms;
+            v ^= (v ^ w) & ms;
+            q ^= (q ^ (0 - tu)) & ms;
+            w ^= (w ^ (0 - tv)) & ms;
+            delta ^= (delta ^ (0 - delta)) & ms;
+            gl += fl & godd;
+            q += u & mo;
+            w += v & mo;
             delta += 1;
             gl >>= 1;
             u *= 2;
