@@ -428,21 +428,33 @@ FPG_DEV void gpt_g1_comb_table(const GPt<fq>& B, const GPt<fq>& B2, GPt<fq>* out
     for (int b = 1; b < 4; b++)
         for (int i = 1; i < 4; i++) out[i + 4 * b] = gpt_add(out[i], out[4 * b]);
 }
-// out[s] = sum_{j in s} (-1)^j psi^j(B) for s < 16, on one thread
+// out[s] = sum_{j in s} (-1)^j psi^j(B) for s < 16, on one thread.  -psi maps T[s] to T[2 s] for s
+// without bit 3, so the seven subsets holding base 0 are additions and the others psi maps:
+//   1, 2 = -psi(1), 4 = -psi(2), 8 = -psi(4); 3 = 1 + 2, 5 = 1 + 4, 9 = 1 + 8, 7 = 3 + 4, 11 = 3 + 8,
+//   13 = 5 + 8, 15 = 7 + 8; 6 = -psi(3), 10 = -psi(5), 12 = -psi(6), 14 = -psi(7)
+// (entries indexed by the subset's bit mask)
+FPG_DEV GPt<fq2> gpt_mpsi(const GPt<fq2>& P) {             // -psi(P), projective
+    GPt<fq2> r = gec_g2_psi(P);
+    r.Y = fq2_neg(r.Y);
+    return r;
+}
 FPG_DEV void gpt_g2_comb_table(const GPt<fq2>& B, GPt<fq2>* out) {
     out[0] = gec_identity<fq2>();
-    GPt<fq2> b = B;
-    for (int j = 0; j < 4; j++) {
-        if (j) b = gec_g2_psi(b);
-        GPt<fq2> bj = b;
-        if (j & 1) bj.Y = fq2_neg(bj.Y);
-        out[1 << j] = bj;
-    }
-    for (int s = 3; s < 16; s++) {
-        if (!(s & (s - 1))) continue;
-        const int top = 31 - __clz(s);
-        out[s] = gpt_add(out[s & ~(1 << top)], out[1 << top]);
-    }
+    out[1] = B;
+    out[2] = gpt_mpsi(out[1]);
+    out[4] = gpt_mpsi(out[2]);
+    out[8] = gpt_mpsi(out[4]);
+    out[3] = gpt_add(out[1], out[2]);
+    out[5] = gpt_add(out[1], out[4]);
+    out[9] = gpt_add(out[1], out[8]);
+    out[7] = gpt_add(out[3], out[4]);
+    out[11] = gpt_add(out[3], out[8]);
+    out[13] = gpt_add(out[5], out[8]);
+    out[15] = gpt_add(out[7], out[8]);
+    out[6] = gpt_mpsi(out[3]);
+    out[10] = gpt_mpsi(out[5]);
+    out[12] = gpt_mpsi(out[6]);
+    out[14] = gpt_mpsi(out[7]);
 }
 
 // the window digit a + 4 b of window w of the GLV halves k0, k1, and the position digit of bit i of
