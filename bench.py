@@ -80,10 +80,13 @@ H1 = (X_ABS + 1) ** 2 // 3                   # h1 = (x - 1)^2 / 3
 # binary-gcd inversions are left out, so the bound is optimistic).
 CRITICAL_ROUNDS = {
     # easy part 8 rounds (n, two Frobenius^2, u, n u, c^2, c^2 u, t) + 5 products of the Fq2 inverse,
-    # g 2, hard part h1 and 3 |x| cyclotomic exponentiations + 6 Frobenius / product rounds
+    # g 2, hard part: h1 on its width-4 NAF and 3 |x| exponentiations (cyclotomic squarings split over
+    # the block's warps, products one per lane) + 6 Frobenius / product rounds
     "k_final_exp_c": 8 + 5 + 2 + _wnaf4_exp_rounds(H1) + 3 * _cyc_exp_rounds(X_ABS) + 6,
-    # 63 doubling steps of 3 rounds, 5 addition steps of 4
-    "k_round_miller_c": 63 * 3 + 5 * 4,
+    # pipelined Miller loop: a priming round, 63 doubling steps of 2 rounds, 5 addition steps of 4
+    # each followed by a priming round
+    "k_round_miller_c": 1 + 63 * 2 + 5 * (4 + 1),
+    "k_commit_miller_c": 1 + 63 * 2 + 5 * (4 + 1),
     # G1 by 8-lane groups, 2-bit joint GLV windows: 13 table formulas + 64 x (2 doublings + 1 addition),
     # 2 phases each, then the addition of A_L and the conversion (longer than the warp G2 chain)
     "k_fold_w": (13 + 64 * 3) * 2 + 2 + 3,
@@ -95,6 +98,11 @@ CRITICAL_ROUNDS = {
     "k_comb_chain": 127 * 2,
     "k_sparse_g": (13 + 64 * 3) * 2 + 2,
 }
+# of those rounds, the ones whose product is split over a block's four warps (fq_split.cuh): the
+# cyclotomic squarings (h1's NAF has one digit more than h1 has bits: base^2 and one per lower digit)
+SPLIT_ROUNDS = {"k_final_exp_c": (H1.bit_length() + 1) + 3 * (X_ABS.bit_length() - 1)}
+# the kernels of Step 1's round chain (the rest of a round runs beside it)
+CHAIN_KERNELS = ("k_final_exp_c", "k_round_miller_c", "k_fold_c", "k_challenge2")
 
 
 FOLD_COMB_MAX = 256           # rounds with at most this many fold points use the comb folds
@@ -952,16 +960,28 @@ def main():
         if r:
             roof_all[kname] = {"frac": round(r["frac"], 4), "avg_launch_ms": round(r["avg_launch_ms"], 4),
                                "units_per_step": r["units_per_step"], "unit_op": r["unit_op"]}
+    # latency bound of every round-structured kernel: rounds x the measured latency of one dependent
+    # product (one lane; for the split rounds, the block's four warps together); the headline is the
+    # round chain's kernel with the most time per step
+    t_lane, t_split = F.fq_mul_latency_ns(), F.fq_mul_split_latency_ns()
+    lat_all = {}
+    for kname, (kc, kt) in prof.items():
+        if kname in CRITICAL_ROUNDS and kc and kt > 0:
+            rounds = CRITICAL_ROUNDS[kname]
+            sr = SPLIT_ROUNDS.get(kname, 0)
+            bound_ms = ((rounds - sr) * t_lane + sr * t_split) * 1e-6
+            lat_all[kname] = {"critical_rounds": rounds, "split_rounds": sr, "bound_ms": round(bound_ms, 4),
+                              "achieved_ms": round(kt / kc, 4), "frac": round(bound_ms / (kt / kc), 4),
+                              "on_round_chain": kname in CHAIN_KERNELS, "ms_per_step": round(kt / args.steps, 3)}
     lat = None
-    if name in CRITICAL_ROUNDS and kms > 0:
-        t_ns = F.fq_mul_latency_ns()
-        rounds = CRITICAL_ROUNDS[name]
-        avg_ms = kms / cnt
-        bound_ms = rounds * t_ns * 1e-6
-        lat = {"kernel": name, "critical_rounds": rounds, "fq_mul_ns": t_ns, "bound_ms": bound_ms,
-               "achieved_ms": avg_ms, "frac": bound_ms / avg_ms,
-               "note": "sequential Fq-product rounds on the launch's critical path x measured latency of "
-                       "one dependent product (fp_fq_mul_latency); combines and inversions excluded"}
+    chain = [k for k in lat_all if lat_all[k]["on_round_chain"]]
+    if chain:
+        top = max(chain, key=lambda k: lat_all[k]["ms_per_step"])
+        lat = dict(kernel=top, **lat_all[top], fq_mul_ns=t_lane, fq_mul_split_ns=t_split,
+                   note="sequential Fq-product rounds of the round chain's largest kernel x the measured "
+                        "latency of one dependent product (one lane, or split over a block's four warps for "
+                        "the split rounds); combines and inversions excluded; every such kernel in "
+                        "latency_rooflines")
     share = {k: round(v[1] / (total_ms if total_ms else 1), 4) for k, v in
              sorted(prof.items(), key=lambda kv: -kv[1][1])[:8]}
     # every kernel: launches per step and mean CUDA-event time per launch (ms)
@@ -1013,6 +1033,7 @@ def main():
         "roofline": roof,
         "roofline_kernels": roof_all,
         "latency_roofline": lat,
+        "latency_rooflines": lat_all,
         "kernel_share": share,
         "kernel_launches_and_ms": kernel_ms,
         "clocks": clk.summary(),

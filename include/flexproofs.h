@@ -376,6 +376,9 @@ int fp_imad_probe(double* ops_per_s, double* ms);
  * current device, CUDA-event timed), in ns: the unit of the latency bound of the lane-parallel
  * engines, whose every round waits for one product.  Returns a fp_status code. */
 int fp_fq_mul_latency(double* ns_per_product);
+/* The same for one Fq product computed by the four warps of a 128-thread block together (the block
+ * engine's cyclotomic squarings), in ns.  Returns a fp_status code. */
+int fp_fq_mul_split_latency(double* ns_per_product);
 
 const char* fp_strerror(fp_status s);
 /* Text of the last CUDA error seen by this thread's calls (empty if none). */

@@ -17,7 +17,7 @@ FP_STATUS = {0: "FP_OK", 1: "FP_EINVAL", 2: "FP_ENOMEM", 3: "FP_EDEVICE", 4: "FP
 EXPORTED = ["vc_setup", "vc_pp_export", "vc_pp_dims", "vc_commit", "vc_commit_get", "vc_prove_all",
             "vc_proof_len", "vc_proof_get", "vc_proofs_export", "vc_proofs_state", "vc_proofs_step2_parts",
             "fp_pp_free", "fp_commit_free", "fp_proofs_free", "fp_strerror", "fp_last_error", "fp_launch_count",
-            "fp_profile_enable", "fp_profile_report", "fp_profile_launches", "fp_imad_probe", "fp_fq_mul_latency", "vc_commit_rows_noalloc",
+            "fp_profile_enable", "fp_profile_report", "fp_profile_launches", "fp_imad_probe", "fp_fq_mul_latency", "fp_fq_mul_split_latency", "vc_commit_rows_noalloc",
             "fp_g1_bases_from_scalars", "fp_g1_bases_load", "fp_g1_bases_count", "fp_g1_bases_free", "fp_msm_g1",
             "fp_msm_window", "fp_msm_autotune", "vc_prove_one", "vc_pp_view", "vc_commit_async",
             "vc_commit_status", "vc_prove_all_batch", "vc_verify", "vc_verify_all", "vc_setup_split",
@@ -104,6 +104,7 @@ def load(path: str = LIB_PATH):
     L.fp_profile_launches.restype = sz
     L.fp_imad_probe.argtypes = [ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double)]
     L.fp_fq_mul_latency.argtypes = [ctypes.POINTER(ctypes.c_double)]
+    L.fp_fq_mul_split_latency.argtypes = [ctypes.POINTER(ctypes.c_double)]
     L.vc_commit_rows_noalloc.argtypes = [vp, vp, vp, vp]
     L.fp_g1_bases_from_scalars.argtypes = [vp, u64, ctypes.c_int, vp, pp]
     L.fp_g1_bases_load.argtypes = [vp, u64, ctypes.c_int, vp, pp]
@@ -498,6 +499,13 @@ def fq_mul_latency_ns() -> float:
     """Measured latency of one dependent Fq Montgomery product on one lane (ns)."""
     ns = ctypes.c_double()
     _check("fp_fq_mul_latency", load().fp_fq_mul_latency(ctypes.byref(ns)))
+    return ns.value
+
+
+def fq_mul_split_latency_ns() -> float:
+    """Measured latency of one dependent Fq product split over a 128-thread block's warps (ns)."""
+    ns = ctypes.c_double()
+    _check("fp_fq_mul_split_latency", load().fp_fq_mul_split_latency(ctypes.byref(ns)))
     return ns.value
 
 

@@ -12,6 +12,7 @@
 #include "../../include/flexproofs.h"
 #include "fp.cuh"
 #include "kernels.h"
+#include "fq_split.cuh"
 
 namespace fpk {
 namespace {
@@ -172,6 +173,35 @@ __global__ void k_fq_mul_chain(uint32_t n, uint32_t* sink) {
     fq_from_const(b, FQ_R3);
     for (uint32_t i = 0; i < n; i++) a = fq_mul(a, b);
     if (a.v[0] == 0x12345678u) sink[0] = a.v[1];
+}
+
+// the same chain with each product split over the four warps of a 128-thread block (fq_split.cuh):
+// the unit of the block engine's cyclotomic squarings
+__global__ void __launch_bounds__(128) k_fq_mul_split_chain(uint32_t n, uint32_t* sink) {
+    fq a, b;
+    fq_from_const(a, FQ_R2);
+    fq_from_const(b, FQ_R3);
+    for (uint32_t i = 0; i < n; i++) a = fq_mul_split(a, b);
+    if (a.v[0] == 0x12345678u) sink[0] = a.v[1];
+}
+
+extern "C" int fp_fq_mul_split_latency(double* ns_per_product) {
+    uint32_t* sink = nullptr;
+    if (cudaMalloc(&sink, 4) != cudaSuccess) return 2;
+    const uint32_t n = 4096;
+    cudaEvent_t a, b;
+    cudaEventCreate(&a); cudaEventCreate(&b);
+    k_fq_mul_split_chain<<<1, 128>>>(64, sink);          // warm-up
+    cudaEventRecord(a);
+    k_fq_mul_split_chain<<<1, 128>>>(n, sink);
+    cudaEventRecord(b);
+    cudaError_t e = cudaEventSynchronize(b);
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, a, b);
+    cudaEventDestroy(a); cudaEventDestroy(b); cudaFree(sink);
+    if (e != cudaSuccess) return 3;
+    *ns_per_product = (double)ms * 1e6 / n;
+    return 0;
 }
 
 extern "C" int fp_fq_mul_latency(double* ns_per_product) {

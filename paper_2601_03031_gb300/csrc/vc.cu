@@ -41,7 +41,8 @@ struct fp_commit {
     void* C = nullptr;        // fq12
     void* C_ser = nullptr;    // 576
     uint32_t* err = nullptr;  // device word: non-zero if an input value was >= r
-    cudaEvent_t done = nullptr;
+    cudaEvent_t done = nullptr;       // C (and everything) ready
+    cudaEvent_t rows_done = nullptr;  // m, the row commitments and their serialisation ready
     cudaStream_t stream;
     // completion events of the calls that read this handle on other streams (vc_prove_all); the
     // free waits for them, stream-ordered, without blocking the host
@@ -155,6 +156,7 @@ size_t bopen_len(uint32_t log_r) { return (size_t)log_r * ROUND_BYTES + G1_SER +
 // concurrent).
 struct Streams {
     cudaStream_t hi = nullptr, sp = nullptr, pre = nullptr, la[2] = {nullptr, nullptr}, fold = nullptr, lo = nullptr;
+    cudaStream_t tail = nullptr;   // Commit's pairings of the row commitments (high priority)
 };
 struct StreamKey { int dev; cudaStream_t user; Streams set; };
 std::vector<StreamKey> g_sets;
@@ -170,6 +172,7 @@ Streams make_set() {
     check(cudaStreamCreateWithPriority(&a.la[1], cudaStreamNonBlocking, hi), "cudaStreamCreate");
     check(cudaStreamCreateWithPriority(&a.fold, cudaStreamNonBlocking, hi), "cudaStreamCreate");
     check(cudaStreamCreateWithPriority(&a.lo, cudaStreamNonBlocking, lo), "cudaStreamCreate");
+    check(cudaStreamCreateWithPriority(&a.tail, cudaStreamNonBlocking, hi), "cudaStreamCreate");
     return a;
 }
 Streams streams(cudaStream_t user) {
@@ -345,6 +348,7 @@ fp_commit* commit_enqueue(const fp_pp* pp, const uint64_t* m, int on_device, cud
         cm->C_ser = dalloc(GT_SER, s);
         cm->err = (uint32_t*)dalloc(sizeof(uint32_t), s);
         check(cudaEventCreateWithFlags(&cm->done, cudaEventDisableTiming), "cudaEventCreate");
+        check(cudaEventCreateWithFlags(&cm->rows_done, cudaEventDisableTiming), "cudaEventCreate");
         check(cudaMemsetAsync(cm->err, 0, sizeof(uint32_t), s), "memset");
         const void* msrc = m;
         if (!on_device) {
@@ -370,17 +374,22 @@ fp_commit* commit_enqueue(const fp_pp* pp, const uint64_t* m, int on_device, cud
             t1 = dalloc(msm_scratch_bytes(sh), s);
             msm_g1(pp->lam_tab, cm->m_canon, sh, t1, cm->rows, cm->rows_ser, s);
         }
-        // C = prod_j e(C_j, v_j): R Miller loops, pairwise products, one final exponentiation
+        // C = prod_j e(C_j, v_j): R Miller loops, pairwise products, one final exponentiation, on an
+        // internal stream after the rows: the caller's stream goes on (OpenAll's pairings and Step 2
+        // need the rows only), cm->done marks C
         ml = dalloc(R * FQ12_BYTES, s);
         ml2 = dalloc((R / 2 + 1) * FQ12_BYTES, s);
-        commit_miller(cm->rows, pp->g2pow, R, ml, s);
-        void* prod = reduce_pairs(ml, ml2, R, 1, fq12_pair_reduce, s);
-        final_exp_group(prod, 1, cm->C, cm->C_ser, 1, GT_SER, 0, s);
+        check(cudaEventRecord(cm->rows_done, s), "event");
+        cudaStream_t st = streams(s).tail;
+        check(cudaStreamWaitEvent(st, cm->rows_done, 0), "wait");
+        commit_miller(cm->rows, pp->g2pow, R, ml, st);
+        void* prod = reduce_pairs(ml, ml2, R, 1, fq12_pair_reduce, st);
+        final_exp_group(prod, 1, cm->C, cm->C_ser, 1, GT_SER, 0, st);
         check_launch("vc_commit kernels");
-        dfree(src, s); dfree(t1, s); dfree(t2, s); dfree(ml, s); dfree(ml2, s);
-        check(cudaEventRecord(cm->done, s), "event");
+        dfree(src, s); dfree(t1, s); dfree(t2, s); dfree(ml, st); dfree(ml2, st);
+        check(cudaEventRecord(cm->done, st), "event");
     } catch (...) {
-        cudaStreamSynchronize(s);
+        cudaDeviceSynchronize();                     // the caller's stream and the internal one
         dfree(src, s); dfree(t1, s); dfree(t2, s); dfree(ml, s); dfree(ml2, s);
         fp_commit_free(cm);
         throw;
@@ -479,6 +488,7 @@ fp_status vc_commit_get(const fp_commit* cm, uint8_t* gt576, uint8_t* rows) {
     if (!cm) return FP_EINVAL;
     return guarded([&]() -> fp_status {
         cudaStream_t s = cm->stream;
+        if (cm->done) check(cudaStreamWaitEvent(s, cm->done, 0), "wait");
         if (gt576) check(cudaMemcpyAsync(gt576, cm->C_ser, GT_SER, cudaMemcpyDeviceToHost, s), "D2H");
         if (rows) check(cudaMemcpyAsync(rows, cm->rows_ser, cm->pp->R * G1_SER, cudaMemcpyDeviceToHost, s), "D2H");
         check(cudaStreamSynchronize(s), "vc_commit_get");
@@ -751,8 +761,10 @@ fp_proofs* prove_impl(const fp_pp* pp, const fp_commit* cm, uint32_t b, uint32_t
         std::vector<void*> tmp;
         auto T = [&](size_t bytes) { void* p = dalloc(bytes, s); tmp.push_back(p); return p; };
         try {
-            // the commitment may have been made on another stream: order after it
-            if (track_use && cm->done) check(cudaStreamWaitEvent(s, cm->done, 0), "wait");
+            // the commitment may have been made on another stream: order after its rows (C, which only
+            // the statement hashes read, is awaited on their stream)
+            if (track_use && (cm->rows_done || cm->done))
+                check(cudaStreamWaitEvent(s, cm->rows_done ? cm->rows_done : cm->done, 0), "wait");
             pf->rows_ser = dalloc(R * G1_SER, s);
             check(cudaMemcpyAsync(pf->rows_ser, cm->rows_ser, R * G1_SER, cudaMemcpyDeviceToDevice, s), "D2D");
             pf->blocks = dalloc(K * blen, s);
@@ -818,6 +830,7 @@ fp_proofs* prove_impl(const fp_pp* pp, const fp_commit* cm, uint32_t b, uint32_t
             // while s1 starts the first round's Miller loops
             check(cudaEventRecord(ev_init, s1), "event");
             check(cudaStreamWaitEvent(s3, ev_init, 0), "wait");
+            if (track_use && cm->done) check(cudaStreamWaitEvent(s3, cm->done, 0), "wait");
             step1_stmt_hash(cm->C_ser, cm->rows_ser, k0, Kc, R, b, hscr, hstmt, s3);
             step1_block_r(hstmt, k0, Kc, R, b, B.bvec, s3);
             if (la) step1_rounds_la(pp, k0, Kc, b, B, L, blocks1, blen, s1, s3, st.pre, st.la, st.fold);
@@ -1648,6 +1661,7 @@ void fp_commit_free(fp_commit* cm) {
     for (void* p : {cm->m_canon, cm->m_mont, cm->rows, cm->rows_ser, cm->C, cm->C_ser, (void*)cm->err})
         if (p) cudaFreeAsync(p, fs);
     if (cm->done) cudaEventDestroy(cm->done);
+    if (cm->rows_done) cudaEventDestroy(cm->rows_done);
     for (cudaEvent_t e : cm->uses) cudaEventDestroy(e);
     delete cm;
 }
