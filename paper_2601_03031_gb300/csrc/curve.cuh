@@ -20,6 +20,7 @@ FPG_DEV fq f_mul(const fq& a, const fq& b) { return fq_mul(a, b); }
 FPG_DEV fq f_sqr(const fq& a) { return fq_sqr(a); }
 FPG_DEV fq f_neg(const fq& a) { return fq_neg(a); }
 FPG_DEV fq f_inv(const fq& a) { return fq_inv(a); }
+FPG_DEV fq f_inv_quad(const fq& a) { return fq_inv_quad(a); }
 FPG_DEV bool f_is_zero(const fq& a) { return fq_is_zero(a); }
 FPG_DEV bool f_eq(const fq& a, const fq& b) { return fq_eq(a, b); }
 FPG_DEV void f_set_zero(fq& a) { fq_zero(a); }
@@ -31,6 +32,7 @@ FPG_DEV fq2 f_mul(const fq2& a, const fq2& b) { return fq2_mul(a, b); }
 FPG_DEV fq2 f_sqr(const fq2& a) { return fq2_sqr(a); }
 FPG_DEV fq2 f_neg(const fq2& a) { return fq2_neg(a); }
 FPG_DEV fq2 f_inv(const fq2& a) { return fq2_inv(a); }
+FPG_DEV fq2 f_inv_quad(const fq2& a) { return fq2_inv_quad(a); }
 FPG_DEV bool f_is_zero(const fq2& a) { return fq2_is_zero(a); }
 FPG_DEV bool f_eq(const fq2& a, const fq2& b) { return fq2_eq(a, b); }
 FPG_DEV void f_set_zero(fq2& a) { fq2_zero(a); }
@@ -127,6 +129,16 @@ template <typename F>
 FPG_DEV void jac_to_affine(F& x, F& y, const jac<F>& p) {
     if (jac_is_inf(p)) { f_set_zero(x); f_set_zero(y); return; }
     F zi = f_inv(p.Z);
+    F zi2 = f_sqr(zi);
+    x = f_mul(p.X, zi2);
+    y = f_mul(p.Y, f_mul(zi2, zi));
+}
+
+// the same with the inverse on the four lanes of a quad (f_inv_quad: all four call converged with
+// the same point); the inverse of 0 is 0, so the identity (Z = 0) gives (0, 0) without a branch
+template <typename F>
+FPG_DEV void jac_to_affine_quad(F& x, F& y, const jac<F>& p) {
+    F zi = f_inv_quad(p.Z);
     F zi2 = f_sqr(zi);
     x = f_mul(p.X, zi2);
     y = f_mul(p.Y, f_mul(zi2, zi));

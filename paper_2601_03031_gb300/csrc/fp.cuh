@@ -163,6 +163,79 @@ FPG_DEV void ds_shr30(uint32_t* out, const uint32_t* t) {
 template <int N>
 FPG_DEV bool ds_is_neg(const uint32_t* a) { return (int32_t)a[N] < 0; }
 
+// thirty division steps on the low words fl, gl of f and g (delta updated), without branches: a swap
+// (delta > 0 and g odd) exchanges (f, g) <- (g, -f), (u, v, q, w) <- (q, w, -u, -v), delta <- -delta,
+// by masks; then g odd adds f to g and (u, v) to (q, w); then delta + 1, g / 2, (u, v) * 2.  Returns
+// the batch's matrix: 2^30 (f', g') = (u f + v g, q f + w g).
+FPG_DEV void ds_batch30(uint32_t fl, uint32_t gl, int32_t& delta, int32_t& u, int32_t& v, int32_t& q,
+                        int32_t& w) {
+    u = 1; v = 0; q = 0; w = 1;
+#pragma unroll 5
+    for (int i = 0; i < 30; i++) {
+        const uint32_t godd = 0u - (gl & 1u);
+        const uint32_t sw = godd & (uint32_t)((0 - delta) >> 31);
+        const int32_t ms = (int32_t)sw, mo = (int32_t)godd;
+        const uint32_t tf = fl;
+        fl ^= (fl ^ gl) & sw;
+        gl ^= (gl ^ (0u - tf)) & sw;
+        const int32_t tu = u, tv = v;
+        u ^= (u ^ q) & ms;
+        v ^= (v ^ w) & ms;
+        q ^= (q ^ (0 - tu)) & ms;
+        w ^= (w ^ (0 - tv)) & ms;
+        delta ^= (delta ^ (0 - delta)) & ms;
+        gl += fl & godd;
+        q += u & mo;
+        w += v & mo;
+        delta += 1;
+        gl >>= 1;
+        u *= 2;
+        v *= 2;
+    }
+}
+
+// r = +-d (minus when fneg) normalised into [0, P), for d in (-P, P) (N + 1 word two's complement)
+template <int N>
+FPG_DEV void ds_finish(uint32_t* r, uint32_t* d, bool fneg, const uint32_t* P) {
+    if (fneg) {                                              // d <- -d
+        uint32_t z[N + 1];
+        uint32_t bw = 0;
+#pragma unroll
+        for (int j = 0; j <= N; j++) {
+            const uint64_t s = (uint64_t)0 - d[j] - bw;
+            z[j] = (uint32_t)s;
+            bw = (uint32_t)(s >> 63);
+        }
+#pragma unroll
+        for (int j = 0; j <= N; j++) d[j] = z[j];
+    }
+    // d in (-P, P): add P when negative (the loops are bounds, one pass suffices)
+    for (int it = 0; it < 4 && ds_is_neg<N>(d); it++) {
+        uint64_t c = 0;
+#pragma unroll
+        for (int j = 0; j <= N; j++) {
+            const uint64_t s = (uint64_t)d[j] + (j < N ? P[j] : 0) + c;
+            d[j] = (uint32_t)s;
+            c = s >> 32;
+        }
+    }
+    for (int it = 0; it < 4; it++) {
+        uint32_t z[N + 1];
+        uint64_t bw = 0;
+#pragma unroll
+        for (int j = 0; j <= N; j++) {
+            const uint64_t s = (uint64_t)d[j] - (j < N ? P[j] : 0) - bw;
+            z[j] = (uint32_t)s;
+            bw = (s >> 63) & 1;
+        }
+        if (bw) break;                                       // d < P
+#pragma unroll
+        for (int j = 0; j <= N; j++) d[j] = z[j];
+    }
+#pragma unroll
+    for (int j = 0; j < N; j++) r[j] = d[j];
+}
+
 template <int N>
 FPG_DEV void inv_ds(uint32_t* r, const uint32_t* x, const uint32_t* P, uint32_t pinv) {
     uint32_t f[N + 1], g[N + 1], d[N + 1], e[N + 1];
@@ -209,33 +282,8 @@ FPG_DEV void inv_ds(uint32_t* r, const uint32_t* x, const uint32_t* P, uint32_t 
     // at most 2 x 32 N divsteps for P < 2^(32 N); the guard only bounds the loop on bad input
     for (int batch = 0; batch < 4 * 32 * N / 30 + 4; batch++) {
         if (is_zero<N + 1>(g)) break;
-        uint32_t fl = f[0], gl = g[0];
-        int32_t u = 1, v = 0, q = 0, w = 1;
-        // 30 divsteps on the low words, without branches: a swap (delta > 0 and g odd) exchanges
-        // (f, g) <- (g, -f), (u, v, q, w) <- (q, w, -u, -v), delta <- -delta, by masks; then g odd
-        // adds f to g and (u, v) to (q, w); then delta + 1, g / 2, (u, v) * 2
-#pragma unroll 5
-        for (int i = 0; i < 30; i++) {
-            const uint32_t godd = 0u - (gl & 1u);
-            const uint32_t sw = godd & (uint32_t)((0 - delta) >> 31);
-            const int32_t ms = (int32_t)sw, mo = (int32_t)godd;
-            const uint32_t tf = fl;
-            fl ^= (fl ^ gl) & sw;
-            gl ^= (gl ^ (0u - tf)) & sw;
-            const int32_t tu = u, tv = v;
-            u ^= (u ^ q) & ms;
-            v ^= (v ^ w) & ms;
-            q ^= (q ^ (0 - tu)) & ms;
-            w ^= (w ^ (0 - tv)) & ms;
-            delta ^= (delta ^ (0 - delta)) & ms;
-            gl += fl & godd;
-            q += u & mo;
-            w += v & mo;
-            delta += 1;
-            gl >>= 1;
-            u *= 2;
-            v *= 2;
-        }
+        int32_t u, v, q, w;
+        ds_batch30(f[0], g[0], delta, u, v, q, w);
         uint32_t t[N + 2], nf[N + 1], ng[N + 1], nd[N + 1], ne[N + 1];
         ds_lincomb<N>(t, u, f, v, g);
         ds_shr30<N>(nf, t);
@@ -246,45 +294,81 @@ FPG_DEV void inv_ds(uint32_t* r, const uint32_t* x, const uint32_t* P, uint32_t 
 #pragma unroll
         for (int j = 0; j <= N; j++) { f[j] = nf[j]; g[j] = ng[j]; d[j] = nd[j]; e[j] = ne[j]; }
     }
-    // f = +-1: x^-1 = d (f = 1) or -d (f = -1), normalised into [0, P)
-    const bool fneg = ds_is_neg<N>(f);
-    if (fneg) {                                              // d <- -d
-        uint32_t z[N + 1];
-        uint32_t bw = 0;
+    ds_finish<N>(r, d, ds_is_neg<N>(f), P);
+}
+
+// The same inverse computed by the four lanes of a quad (lanes 4m .. 4m + 3 of one warp, all four
+// calling converged).  Lane q keeps one state value (q = 0: f, 1: g, 2: d, 3: e) and lanes q and
+// q ^ 1 hold a pair, so a batch is the thirty division steps (every lane runs them on the broadcast
+// low words of f and g), an exchange of the pair's values and one update per lane instead of four
+// updates on one lane.  x is taken from the quad's first lane, so the four lanes agree on every
+// branch; every lane returns the inverse.
+template <int N>
+FPG_DEV void inv_ds_quad(uint32_t* r, const uint32_t* x_in, const uint32_t* P, uint32_t pinv) {
+    const int lane = (int)(threadIdx.x & 31), base = lane & 28, qd = lane & 3;
+    const unsigned qmask = 0xfu << base;
+    uint32_t x[N];
+#pragma unroll
+    for (int j = 0; j < N; j++) x[j] = __shfl_sync(qmask, x_in[j], base);
+    if (is_zero<N>(x)) {
+#pragma unroll
+        for (int j = 0; j < N; j++) r[j] = 0;
+        return;
+    }
+    uint32_t s[N + 1];                                       // this lane's value: f = P, g = x, d = 0, e = 1
+#pragma unroll
+    for (int j = 0; j < N; j++) s[j] = qd == 0 ? P[j] : qd == 1 ? x[j] : (qd == 3 && j == 0) ? 1u : 0u;
+    s[N] = 0;
+    const bool second = (qd & 1) != 0;                       // g or e: the second value of its pair
+    const uint32_t modm = qd >= 2 ? 0xffffffffu : 0u;        // d and e are residues mod P
+    const uint32_t mask30 = (1u << 30) - 1;
+    int32_t delta = 1;
+    for (int batch = 0; batch < 4 * 32 * N / 30 + 4; batch++) {
+        const uint32_t fl = __shfl_sync(qmask, s[0], base);
+        const uint32_t gl = __shfl_sync(qmask, s[0], base + 1);
+        const int gz = __shfl_sync(qmask, (int)is_zero<N + 1>(s), base + 1);
+        if (gz) break;
+        int32_t u, v, q, w;
+        ds_batch30(fl, gl, delta, u, v, q, w);
+        uint32_t X[N + 1], Y[N + 1];                         // the pair (f, g) or (d, e)
 #pragma unroll
         for (int j = 0; j <= N; j++) {
-            const uint64_t s = (uint64_t)0 - d[j] - bw;
-            z[j] = (uint32_t)s;
-            bw = (uint32_t)(s >> 63);
+            const uint32_t o = __shfl_xor_sync(qmask, s[j], 1);
+            X[j] = second ? o : s[j];
+            Y[j] = second ? s[j] : o;
         }
-#pragma unroll
-        for (int j = 0; j <= N; j++) d[j] = z[j];
-    }
-    // d in (-P, P): add P when negative (the loops are bounds, one pass suffices)
-    for (int it = 0; it < 4 && ds_is_neg<N>(d); it++) {
+        // f' = (u f + v g) / 2^30, g' = (q f + w g) / 2^30; d', e' the same times 2^-30 mod P: the
+        // multiple k P that clears the low 30 bits is added on the residue lanes only
+        uint32_t t[N + 2];
+        ds_lincomb<N>(t, second ? q : u, X, second ? w : v, Y);
+        const uint32_t k = (t[0] * pinv) & mask30 & modm;
         uint64_t c = 0;
 #pragma unroll
-        for (int j = 0; j <= N; j++) {
-            const uint64_t s = (uint64_t)d[j] + (j < N ? P[j] : 0) + c;
-            d[j] = (uint32_t)s;
-            c = s >> 32;
+        for (int i = 0; i < N + 2; i++) {
+            const uint64_t a = (uint64_t)t[i] + (i < N ? (uint64_t)k * P[i] : 0) + c;
+            t[i] = (uint32_t)a;
+            c = a >> 32;
         }
-    }
-    for (int it = 0; it < 4; it++) {
+        ds_shr30<N>(s, t);
+        // residues: from (-P, 2P) back into (-P, P) by subtracting P when s >= P
         uint32_t z[N + 1];
         uint64_t bw = 0;
 #pragma unroll
         for (int j = 0; j <= N; j++) {
-            const uint64_t s = (uint64_t)d[j] - (j < N ? P[j] : 0) - bw;
-            z[j] = (uint32_t)s;
-            bw = (s >> 63) & 1;
+            const uint64_t a = (uint64_t)s[j] - (j < N ? P[j] : 0) - bw;
+            z[j] = (uint32_t)a;
+            bw = (a >> 63) & 1;
         }
-        if (bw) break;                                       // d < P
+        const uint32_t take = modm & ~(0u - (uint32_t)ds_is_neg<N>(s)) & ((uint32_t)bw - 1u);
 #pragma unroll
-        for (int j = 0; j <= N; j++) d[j] = z[j];
+        for (int j = 0; j <= N; j++) s[j] = (z[j] & take) | (s[j] & ~take);
     }
+    // f = +-1 (lane 0) and d (lane 2): x^-1 = +-d
+    const bool fneg = __shfl_sync(qmask, (int)ds_is_neg<N>(s), base) != 0;
+    uint32_t d[N + 1];
 #pragma unroll
-    for (int j = 0; j < N; j++) r[j] = d[j];
+    for (int j = 0; j <= N; j++) d[j] = __shfl_sync(qmask, s[j], base + 2);
+    ds_finish<N>(r, d, fneg, P);
 }
 
 }  // namespace mp
@@ -344,6 +428,14 @@ FPG_NOINL fq fq_inv(const fq& a) {
     fq_from_const(r3, FQ_R3);
     return fq_mul(t, r3);
 }
+// the same on the four lanes of a quad (mp::inv_ds_quad: all four call converged; the value of the
+// quad's first lane is inverted, every lane returns it)
+FPG_NOINL fq fq_inv_quad(const fq& a) {
+    fq t, r3;
+    mp::inv_ds_quad<12>(t.v, a.v, FQ_P, FQ_PINV);
+    fq_from_const(r3, FQ_R3);
+    return fq_mul(t, r3);
+}
 
 // ---------------------------------------------------------------------------------------
 // Fr
@@ -379,6 +471,14 @@ FPG_DEV bool fr_canonical_lt_r(const fr& a) { return mp::lt<8>(a.v, FR_P); }
 FPG_NOINL fr fr_inv(const fr& a) {
     fr t, r3;
     mp::inv_ds<8>(t.v, a.v, FR_P, FR_PINV);
+#pragma unroll
+    for (int j = 0; j < 8; j++) r3.v[j] = FR_R3[j];
+    return fr_mul(t, r3);
+}
+// the same on the four lanes of a quad (as fq_inv_quad)
+FPG_NOINL fr fr_inv_quad(const fr& a) {
+    fr t, r3;
+    mp::inv_ds_quad<8>(t.v, a.v, FR_P, FR_PINV);
 #pragma unroll
     for (int j = 0; j < 8; j++) r3.v[j] = FR_R3[j];
     return fr_mul(t, r3);

@@ -143,6 +143,16 @@ FPG_DEV void gec_to_affine(F& x, F& y, const GPt<F>& P) {
     y = f_mul(P.Y, zi);
 }
 
+// the same with the inverse on the four lanes of each quad (f_inv_quad; every lane of a quad calls it
+// converged with the same point): the inverse of Z = 0 is 0, so the identity gives (0, 0) without a
+// branch
+template <typename F>
+FPG_DEV void gec_to_affine_quad(F& x, F& y, const GPt<F>& P) {
+    const F zi = f_inv_quad(P.Z);
+    x = f_mul(P.X, zi);
+    y = f_mul(P.Y, zi);
+}
+
 template <typename F>
 FPG_DEV GPt<F> gec_from_affine_or_inf(const F& x, const F& y) {
     return (f_is_zero(x) && f_is_zero(y)) ? gec_identity<F>() : gec_from_affine(x, y);

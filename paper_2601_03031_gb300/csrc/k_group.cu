@@ -168,6 +168,28 @@ __global__ void k_g2j_affine(const g2j* in, g2a* out, uint8_t* ser, size_t strid
     if (out) out[i] = a;
     if (ser) g2a_to_be(ser + i * stride, a);
 }
+// the same for few points: a quad of four threads per point shares its inversion (jac_to_affine_quad);
+// whole quads leave together, the quad's first lane stores
+__global__ void k_g1j_affine_q(const g1j* in, g1a* out, uint8_t* ser, size_t stride, uint64_t n) {
+    const uint64_t i = gtid() >> 2;
+    if (i >= n) return;
+    g1a a;
+    jac_to_affine_quad(a.x, a.y, in[i]);
+    if ((threadIdx.x & 3) == 0) {
+        if (out) out[i] = a;
+        if (ser) g1a_to_be(ser + i * stride, a);
+    }
+}
+__global__ void k_g2j_affine_q(const g2j* in, g2a* out, uint8_t* ser, size_t stride, uint64_t n) {
+    const uint64_t i = gtid() >> 2;
+    if (i >= n) return;
+    g2a a;
+    jac_to_affine_quad(a.x, a.y, in[i]);
+    if ((threadIdx.x & 3) == 0) {
+        if (out) out[i] = a;
+        if (ser) g2a_to_be(ser + i * stride, a);
+    }
+}
 __global__ void k_g1a_ser(const g1a* in, uint8_t* ser, size_t stride, uint64_t n) {
     uint64_t i = gtid();
     if (i < n) g1a_to_be(ser + i * stride, in[i]);
@@ -176,11 +198,20 @@ __global__ void k_g2a_ser(const g2a* in, uint8_t* ser, size_t stride, uint64_t n
     uint64_t i = gtid();
     if (i < n) g2a_to_be(ser + i * stride, in[i]);
 }
+// up to AFFINE_QUAD_MAX points a quad per point (a shorter inversion on the latency-bound paths), above
+// it a thread per point (the quads' repeated division steps would cost throughput)
+constexpr uint64_t AFFINE_QUAD_MAX = 4096;
 void g1j_to_affine(const void* in, void* out, void* ser, size_t stride, uint64_t n, cudaStream_t s) {
-    if (n) FP_KERNEL("k_g1j_affine", s, k_g1j_affine<<<grid_for(n, 64), 64, 0, s>>>((const g1j*)in, (g1a*)out, (uint8_t*)ser, stride, n));
+    if (n && n <= AFFINE_QUAD_MAX)
+        FP_KERNEL("k_g1j_affine_q", s, k_g1j_affine_q<<<grid_for(4 * n, 64), 64, 0, s>>>((const g1j*)in, (g1a*)out, (uint8_t*)ser, stride, n));
+    else if (n)
+        FP_KERNEL("k_g1j_affine", s, k_g1j_affine<<<grid_for(n, 64), 64, 0, s>>>((const g1j*)in, (g1a*)out, (uint8_t*)ser, stride, n));
 }
 void g2j_to_affine(const void* in, void* out, void* ser, size_t stride, uint64_t n, cudaStream_t s) {
-    if (n) FP_KERNEL("k_g2j_affine", s, k_g2j_affine<<<grid_for(n, 64), 64, 0, s>>>((const g2j*)in, (g2a*)out, (uint8_t*)ser, stride, n));
+    if (n && n <= AFFINE_QUAD_MAX)
+        FP_KERNEL("k_g2j_affine_q", s, k_g2j_affine_q<<<grid_for(4 * n, 64), 64, 0, s>>>((const g2j*)in, (g2a*)out, (uint8_t*)ser, stride, n));
+    else if (n)
+        FP_KERNEL("k_g2j_affine", s, k_g2j_affine<<<grid_for(n, 64), 64, 0, s>>>((const g2j*)in, (g2a*)out, (uint8_t*)ser, stride, n));
 }
 void g1a_serialize(const void* in, void* ser, size_t stride, uint64_t n, cudaStream_t s) {
     if (n) FP_KERNEL("k_g1a_ser", s, k_g1a_ser<<<grid_for(n), TPB, 0, s>>>((const g1a*)in, (uint8_t*)ser, stride, n));

@@ -107,13 +107,18 @@ __global__ void __launch_bounds__(64) k_fold(g1a* A, g2a* v, fr* bvec, const fr*
     }
 }
 
-// the G1 parts of round j's record (the GT parts are written by the final exponentiation)
+// the G1 parts of round j's record (the GT parts are written by the final exponentiation); a quad of
+// four threads per point shares the inversion (jac_to_affine_quad), whole quads leave together
 __global__ void __launch_bounds__(64) k_round_g1_out(const g1j* sp, uint32_t K, int j, uint8_t* blocks,
                                                      size_t bopen_len) {
-    uint64_t t = gtid();
+    const uint64_t t = gtid() >> 2;
     if (t >= (uint64_t)K * 2) return;
-    uint8_t* rec = blocks + (t >> 1) * bopen_len + (size_t)(j - 1) * ROUND_BYTES + (t & 1) * (GT_SER + G1_SER);
-    g1a_to_be(rec + GT_SER, g1_affine(sp[t]));
+    g1a a;
+    jac_to_affine_quad(a.x, a.y, sp[t]);
+    if ((threadIdx.x & 3) == 0) {
+        uint8_t* rec = blocks + (t >> 1) * bopen_len + (size_t)(j - 1) * ROUND_BYTES + (t & 1) * (GT_SER + G1_SER);
+        g1a_to_be(rec + GT_SER, a);
+    }
 }
 
 // Both folds of round j for few points: blocks [0, nb2) fold 4 points of v each (one warp per point,
@@ -285,7 +290,7 @@ __global__ void __launch_bounds__(256) k_fold_c(g1a* A, g2a* v, fr* bvec, const 
         if (w == 0) {
             acc = gecw_add(sm.e.g2[0], L, acc, gec_from_affine_or_inf(v[lo].x, v[lo].y));
             g2a o;
-            gec_to_affine(o.x, o.y, acc);
+            gec_to_affine_quad(o.x, o.y, acc);                 // every quad of warp 0 (converged)
             __syncwarp();
             if (L == 0) v[lo] = o;
         }
@@ -316,7 +321,7 @@ __global__ void __launch_bounds__(256) k_fold_c(g1a* A, g2a* v, fr* bvec, const 
     }
     acc = gec_add(sm.e.g1[grp], lane, acc, gec_from_affine_or_inf(A[lo].x, A[lo].y));
     g1a o;
-    gec_to_affine(o.x, o.y, acc);
+    gec_to_affine_quad(o.x, o.y, acc);                        // the two quads of each group
     __syncthreads();                                          // every read of A[lo] before the store
     if (valid && g == 0 && lane == 0) {
         A[lo] = o;
@@ -376,14 +381,16 @@ __global__ void __launch_bounds__(64) k_challenge2(const uint8_t* blocks, size_t
         sha256_final(c, wide[w] + 32 * L);
     }
     __syncwarp();
-    if (L == 0) {
+    if (L < 4) {                                              // the inverse on the quad of lanes 0 .. 3
         fr x = fr_from_be64(wide[w]);
         if (fr_is_zero(x)) x = hash_to_fr_nonzero("FP-x", 4, xp, j > 1 ? 32 : 0, rec, ROUND_BYTES, nullptr, 0);
-        const fr xi = fr_inv(x);
-        x_mont[k] = x;
-        xinv_mont[k] = xi;
-        xinv_all[k * log_r + (j - 1)] = xi;
-        fr_to_be(xp, x);
+        const fr xi = fr_inv_quad(x);
+        if (L == 0) {
+            x_mont[k] = x;
+            xinv_mont[k] = xi;
+            xinv_all[k * log_r + (j - 1)] = xi;
+            fr_to_be(xp, x);
+        }
     }
 }
 
@@ -530,7 +537,7 @@ void step1_gt_out(const void* ml, uint32_t K, int j, void* blocks, size_t bopen_
                     GT_SER + G1_SER, s);
 }
 void step1_g1_out(const void* sp, uint32_t K, int j, void* blocks, size_t bopen_len, cudaStream_t s) {
-    FP_KERNEL("k_round_g1_out", s, k_round_g1_out<<<grid_for((uint64_t)K * 2, 64), 64, 0, s>>>((const g1j*)sp, K, j,
+    FP_KERNEL("k_round_g1_out", s, k_round_g1_out<<<grid_for((uint64_t)K * 8, 64), 64, 0, s>>>((const g1j*)sp, K, j,
                                                                                           (uint8_t*)blocks,
                                                                                           bopen_len));
 }

@@ -39,6 +39,12 @@ FPG_NOINL fq2 fq2_inv(const fq2& a) {
     fq ni = fq_inv(n);
     return {fq_mul(a.c0, ni), fq_neg(fq_mul(a.c1, ni))};
 }
+// the same with the Fq inverse on the four lanes of a quad (fq_inv_quad)
+FPG_NOINL fq2 fq2_inv_quad(const fq2& a) {
+    fq n = fq_add(fq_sqr(a.c0), fq_sqr(a.c1));
+    fq ni = fq_inv_quad(n);
+    return {fq_mul(a.c0, ni), fq_neg(fq_mul(a.c1, ni))};
+}
 
 // ------------------------------------------------------------------------------ Fq6
 FPG_DEV fq6 fq6_add(const fq6& a, const fq6& b) { return {fq2_add(a.c0, b.c0), fq2_add(a.c1, b.c1), fq2_add(a.c2, b.c2)}; }

@@ -233,16 +233,18 @@ FPG_NOINL void w_frob2(W12& W, fq* out, const fq* a) {
     wsync<NW>();
 }
 
-// a <- a^-1 for a in Fq2 (flat coefficient 0; the others are zero), on one lane
+// a <- a^-1 for a in Fq2 (flat coefficient 0; the others are zero), on the quad of lanes 0 .. 3
 template <int NW>
 FPG_NOINL void w_inv_fq2(fq* a) {
     const int L = w_lane<NW>();
     wsync<NW>();
-    if (L == 0) {
+    if (L < 4) {
         const fq2 v{a[0], a[1]};
-        const fq2 vi = fq2_inv(v);
-        a[0] = vi.c0;
-        a[1] = vi.c1;
+        const fq2 vi = fq2_inv_quad(v);
+        if (L == 0) {
+            a[0] = vi.c0;
+            a[1] = vi.c1;
+        }
     }
     wsync<NW>();
 }

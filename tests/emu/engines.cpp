@@ -40,6 +40,7 @@ template <typename Fn>
 void lanes(int n, Fn fn) {
     std::barrier<> bar(n);
     g_lanes = &bar;
+    emu_setup_quads(n);
     std::vector<std::thread> th;
     for (int lane = 0; lane < n; lane++) th.emplace_back([&, lane] { threadIdx.x = lane; fn(); });
     for (auto& t : th) t.join();
@@ -153,11 +154,17 @@ void emu_g1_comb(const uint8_t* p, const uint32_t* k, uint8_t* out) {
         div_by_const<4, 5>(k1, k0, k, GLV_D, GLV_BARRETT);
         GPt<fq> s = gec_identity<fq>();
         for (int w = 0; w < 64; w++) s = gec_add(g_g1, L, s, tab[16 * w + glv_window(k0, k1, w)]);
-        if (L == 0) r = s;
+        // to affine as k_fold_c does (the two quads of the group), and through Jacobian coordinates as
+        // the quad conversion kernels do; a disagreement leaves the output zero
+        g1a a, b;
+        gec_to_affine_quad(a.x, a.y, s);
+        jac_to_affine_quad(b.x, b.y, proj_to_jac(s));
+        if (L == 0) {
+            r = s;
+            if (fq_eq(a.x, b.x) && fq_eq(a.y, b.y)) g1a_to_be(out, a);
+            else memset(out, 0, 96);
+        }
     });
-    g1a a;
-    gec_to_affine(a.x, a.y, r);
-    g1a_to_be(out, a);
 }
 // k Q through the comb on G2: the chain 2^i Q (i < 64) on one warp, the 64 position tables
 // (gpt_g2_comb_table) on one thread, the sum of one entry per position on an 8-lane group
@@ -185,11 +192,15 @@ void emu_g2_comb(const uint8_t* q, const uint32_t* k, uint8_t* out) {
         gls_digits(d, k);
         GPt<fq2> s = gec_identity<fq2>();
         for (int i = 0; i < 64; i++) s = gec_add(e2, L, s, tab[16 * i + gls_position(d, i)]);
-        if (L == 0) r = s;
+        g2a a, b;
+        gec_to_affine_quad(a.x, a.y, s);
+        jac_to_affine_quad(b.x, b.y, proj_to_jac(s));
+        if (L == 0) {
+            r = s;
+            if (fq2_eq(a.x, b.x) && fq2_eq(a.y, b.y)) g2a_to_be(out, a);
+            else memset(out, 0, 192);
+        }
     });
-    g2a a;
-    gec_to_affine(a.x, a.y, r);
-    g2a_to_be(out, a);
 }
 void emu_g2_dbl_n(const uint8_t* q, int n, uint8_t* out) {
     const g2a Q = be_g2(q);

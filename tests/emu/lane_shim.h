@@ -89,3 +89,34 @@ struct LaneIdx { unsigned x; };
 static thread_local LaneIdx threadIdx;
 static thread_local LaneIdx blockIdx;
 static const LaneIdx blockDim{128};
+
+// __shfl_sync / __shfl_xor_sync for the quads of four lanes (mask 0xf << 4m, the only form the device
+// code uses): each quad has a barrier of its own and the values pass through a shared array; any
+// other mask or a source outside the quad aborts the test
+#include <cstdlib>
+static std::barrier<>* g_quad[256] = {};
+static uint32_t g_xchg[1024];
+static inline void emu_setup_quads(int n) {
+    for (int i = 0; i < 256; i++) {
+        delete g_quad[i];
+        g_quad[i] = i < (n + 3) / 4 ? new std::barrier<>(4) : nullptr;
+    }
+}
+static inline uint32_t emu_quad_xchg(unsigned mask, uint32_t v, unsigned src) {
+    const unsigned L = threadIdx.x;
+    if (mask != (0xfu << (L & 28)) || (src & 28) != (L & 28) || !g_quad[L >> 2]) std::abort();
+    g_xchg[L] = v;
+    g_quad[L >> 2]->arrive_and_wait();
+    const uint32_t r = g_xchg[(L & ~31u) | src];
+    g_quad[L >> 2]->arrive_and_wait();
+    return r;
+}
+static inline uint32_t __shfl_sync(unsigned mask, uint32_t v, int src) {
+    return emu_quad_xchg(mask, v, (unsigned)src & 31);
+}
+static inline int __shfl_sync(unsigned mask, int v, int src) {
+    return (int)emu_quad_xchg(mask, (uint32_t)v, (unsigned)src & 31);
+}
+static inline uint32_t __shfl_xor_sync(unsigned mask, uint32_t v, int m) {
+    return emu_quad_xchg(mask, v, (threadIdx.x & 31) ^ (unsigned)m);
+}

@@ -1,6 +1,7 @@
-"""The field inverse of the CUDA path (batched division steps, `mp::inv_ds` in fp.cuh), compiled for
-the host and checked against Python's modular inverse: x x^-1 = 1 for random and edge values of Fq
-and Fr (1, 2, p - 1, values with long runs of zero or one bits), and 0 maps to 0 (no GPU)."""
+"""The field inverse of the CUDA path (batched division steps, `mp::inv_ds` in fp.cuh, and its form
+on the four lanes of a quad, `mp::inv_ds_quad`), compiled for the host and checked against Python's
+modular inverse: x x^-1 = 1 for random and edge values of Fq and Fr (1, 2, p - 1, values with long
+runs of zero or one bits), and 0 maps to 0 (no GPU)."""
 import ctypes
 import os
 import random
@@ -24,8 +25,8 @@ def lib(tmp_path_factory):
     subprocess.check_call([gxx, "-std=c++20", "-O1", "-shared", "-fPIC", f"-I{CSRC}", "-o", so,
                            os.path.join(HERE, "emu", "inverse.cpp")])
     L = ctypes.CDLL(so)
-    L.emu_inv_fq.restype = None
-    L.emu_inv_fr.restype = None
+    for f in (L.emu_inv_fq, L.emu_inv_fr, L.emu_inv_fq_quad, L.emu_inv_fr_quad):
+        f.restype = None
     return L
 
 
@@ -50,3 +51,21 @@ def test_inverse_against_python(lib, field):
     for x in values:
         assert call(fn, x, n) == pow(x, -1, m), hex(x)
     assert call(fn, 0, n) == 0
+
+
+@pytest.mark.parametrize("field", ["fq", "fr"])
+def test_quad_inverse_against_python(lib, field):
+    """The quad form: the four lanes start from different values (only the first lane's is the
+    input), every lane must return the first lane's inverse."""
+    m, n, fn = (ref.P, 12, lib.emu_inv_fq_quad) if field == "fq" else (ref.R, 8, lib.emu_inv_fr_quad)
+    rnd = random.Random(23)
+    values = edge_values(m) + [rnd.randrange(1, m) for _ in range(150)] + [0]
+    for x in values:
+        lanes = [x] + [rnd.randrange(0, m) for _ in range(3)]
+        xi = (ctypes.c_uint32 * (4 * n))(*[(v >> (32 * i)) & 0xFFFFFFFF for v in lanes for i in range(n)])
+        r = (ctypes.c_uint32 * (4 * n))()
+        fn(xi, r)
+        want = pow(x, -1, m) if x else 0
+        for q in range(4):
+            got = sum(r[q * n + i] << (32 * i) for i in range(n))
+            assert got == want, (hex(x), q)
