@@ -110,7 +110,6 @@ FOLD_COMB_MAX = 256           # rounds with at most this many fold points use th
 # DRAM bytes per launch (dram__bytes_read.sum + dram__bytes_write.sum) from one ncu capture of the
 # kernel at this workload, keyed by (log N, b, kernel); an entry is removed when its kernel changes
 NCU_TRAFFIC = {
-    (16, 256, "k_final_exp_c"): 143e3,
     (16, 256, "k_round_miller_c"): 277e3,
     (16, 256, "k_lamc_sum"): 310e6,
 }

@@ -163,35 +163,36 @@ FPG_DEV void ds_shr30(uint32_t* out, const uint32_t* t) {
 template <int N>
 FPG_DEV bool ds_is_neg(const uint32_t* a) { return (int32_t)a[N] < 0; }
 
-// thirty division steps on the low words fl, gl of f and g (delta updated), without branches: a swap
-// (delta > 0 and g odd) exchanges (f, g) <- (g, -f), (u, v, q, w) <- (q, w, -u, -v), delta <- -delta,
-// by masks; then g odd adds f to g and (u, v) to (q, w); then delta + 1, g / 2, (u, v) * 2.  Returns
-// the batch's matrix: 2^30 (f', g') = (u f + v g, q f + w g).
+// thirty division steps on the low words fl, gl of f and g (delta updated), without branches.  With
+// s = all-ones for a swap (delta > 0 and g odd) and o = all-ones for g odd, one step is
+//   g <- g + ((f & o) ^ s) - s    (g - f on a swap, g + f for g odd, g otherwise)
+//   f <- f + (g & s)              (on a swap the old g), then g <- g / 2,
+// the same on the matrix (q <- q + ((u & o) ^ s) - s, u <- 2 (u + (q & s)), likewise v, w) and
+// nd = -delta <- (nd ^ s) - s - 1 (1 - delta on a swap, 1 + delta otherwise).  The dependent chain
+// from one step's g to the next is four operations.  Returns the batch's matrix:
+// 2^30 (f', g') = (u f + v g, q f + w g).
 FPG_DEV void ds_batch30(uint32_t fl, uint32_t gl, int32_t& delta, int32_t& u, int32_t& v, int32_t& q,
                         int32_t& w) {
-    u = 1; v = 0; q = 0; w = 1;
-#pragma unroll 5
+    uint32_t f = fl, g = gl, nd = 0u - (uint32_t)delta;
+    uint32_t uu = 1, vv = 0, qq = 0, ww = 1;
+#pragma unroll 6
     for (int i = 0; i < 30; i++) {
-        const uint32_t godd = 0u - (gl & 1u);
-        const uint32_t sw = godd & (uint32_t)((0 - delta) >> 31);
-        const int32_t ms = (int32_t)sw, mo = (int32_t)godd;
-        const uint32_t tf = fl;
-        fl ^= (fl ^ gl) & sw;
-        gl ^= (gl ^ (0u - tf)) & sw;
-        const int32_t tu = u, tv = v;
-        u ^= (u ^ q) & ms;
-        v ^= (v ^ w) & ms;
-        q ^= (q ^ (0 - tu)) & ms;
-        w ^= (w ^ (0 - tv)) & ms;
-        delta ^= (delta ^ (0 - delta)) & ms;
-        gl += fl & godd;
-        q += u & mo;
-        w += v & mo;
-        delta += 1;
-        gl >>= 1;
-        u *= 2;
-        v *= 2;
+        const uint32_t o = 0u - (g & 1u);
+        const uint32_t sw = o & (uint32_t)((int32_t)nd >> 31);
+        g = g + ((f & o) ^ sw) - sw;
+        f += g & sw;
+        g >>= 1;
+        qq = qq + ((uu & o) ^ sw) - sw;
+        ww = ww + ((vv & o) ^ sw) - sw;
+        uu = (uu + (qq & sw)) << 1;
+        vv = (vv + (ww & sw)) << 1;
+        nd = (nd ^ sw) - sw - 1u;
     }
+    delta = (int32_t)(0u - nd);
+    u = (int32_t)uu;
+    v = (int32_t)vv;
+    q = (int32_t)qq;
+    w = (int32_t)ww;
 }
 
 // r = +-d (minus when fneg) normalised into [0, P), for d in (-P, P) (N + 1 word two's complement)
