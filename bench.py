@@ -46,9 +46,13 @@ FQ_MULS = {
     "comb_fold": 65 * 12 + 65 * 36,
     # their chains: 127 G1 and 63 G2 complete doublings (6M + 2S)
     "comb_chain": 127 * 8 + 63 * 8 * 3,
-    # their tables: per G1 window 10 additions and 3 products by omega, per G2 position 11 additions
-    # and 3 psi maps (6 Fq2 products)
-    "comb_tab": 64 * (10 * 12 + 3) + 64 * (11 * 36 + 18),
+    # their tables: per G1 window 10 additions and 3 products by omega, per G2 position 7 additions
+    # and 7 psi maps (2 Fq2 products each)
+    "comb_tab": 64 * (10 * 12 + 3) + 64 * (7 * 36 + 7 * 6),
+    # a commitment term by the setup's combs (k_lamcomb.cu): 32 mixed additions (7M + 4S)
+    "lamc_term": 32 * 11,
+    # a W term by the setup's G2 combs: 64 position entries summed, 63 complete additions over Fq2
+    "w_comb_term": 63 * 36,
 }
 
 
@@ -106,6 +110,8 @@ CHAIN_KERNELS = ("k_final_exp_c", "k_round_miller_c", "k_fold_c", "k_challenge2"
 
 
 FOLD_COMB_MAX = 256           # rounds with at most this many fold points use the comb folds
+LAM_COMB_MAX_M = 1024         # setups with M <= this commit by the fixed-base combs of their bases
+G2_COMB_MAX_R = 1024          # setups with R <= this keep the W proofs' comb tables
 
 # DRAM bytes per launch (dram__bytes_read.sum + dram__bytes_write.sum) from one ncu capture of the
 # kernel at this workload, keyed by (log N, b, kernel); an entry is removed when its kernel changes
@@ -141,10 +147,12 @@ def step_units(log_n: int, b: int, msm_window: int, msm_window_g2: int = 16) -> 
         "k_comb_tab": ("comb_tab", sum(K * h for h in hs if K * h <= FOLD_COMB_MAX)),
         "k_fold_w": (("g1_mul", "g2_mul"), sum(K * h for h in hs if FOLD_COMB_MAX < K * h <= 4096)),
         "k_fold": (("g1_mul", "g2_mul"), sum(K * h for h in hs if K * h > 4096)),
-        "k_msm_chunk": ("msm_madd", 2 * R * M * W),
+        "k_lamc_sum": ("lamc_term", R * M if M <= LAM_COMB_MAX_M else 0),
+        "k_msm_chunk": ("msm_madd", 2 * R * M * W if M > LAM_COMB_MAX_M else 0),
         "k_msm_chunk_g2": ("g2_msm_madd", 4 * 2 * R * K * W2 if w_msm else 0),
-        "k_w_terms": ("g2_mul", K * (2 * R - 2) if not w_msm and K * 2 * R > 4096 else 0),
-        "k_w_terms_w": ("g2_mul", K * (2 * R - 2) if not w_msm and K * 2 * R <= 4096 else 0),
+        "k_w_comb": ("w_comb_term", K * (2 * R - 2) if not w_msm and R <= G2_COMB_MAX_R else 0),
+        "k_w_terms": ("g2_mul", K * (2 * R - 2) if not w_msm and R > G2_COMB_MAX_R and K * 2 * R > 4096 else 0),
+        "k_w_terms_w": ("g2_mul", K * (2 * R - 2) if not w_msm and R > G2_COMB_MAX_R and K * 2 * R <= 4096 else 0),
         "k_pst_terms": ("g1_mul", M * lc // 2),
     }
 
