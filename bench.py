@@ -121,8 +121,14 @@ NCU_TRAFFIC = {
 }
 
 
-def step_units(log_n: int, b: int, msm_window: int, msm_window_g2: int = 16) -> dict:
-    """Per kernel: (unit, units processed per step) for one Commit + OpenAll step."""
+def step_units(log_n: int, b: int, msm_window: int, msm_window_g2: int = 16, lim: dict | None = None) -> dict:
+    """Per kernel: (unit, units processed per step) for one Commit + OpenAll step.  `lim` is the
+    library's engine-choice limits (fp_get_engine_limits: the launch sizes at which a kernel moves
+    from a block to a warp to a thread per item, chosen as the library's launchers do); None reads
+    the current ones."""
+    if lim is None:
+        from paper_2601_03031_gb300 import _lib as F
+        lim = F.engine_limits()
     lr = log_n // 2
     lc = log_n - lr
     R, M = 1 << lr, 1 << lc
@@ -131,28 +137,49 @@ def step_units(log_n: int, b: int, msm_window: int, msm_window_g2: int = 16) -> 
     W = -(-129 // msm_window)
     W2 = -(-65 // msm_window_g2)
     w_msm = K * R * 2 > 4096 and K >= 8         # the W proofs by one batched G2 MSM
+
+    def engine(n, block_max, warp_max):         # "c" a block, "w" a warp, "t" a thread per item
+        if n > warp_max and n > block_max:
+            return "t"
+        return "c" if n <= block_max else "w"
+
+    mb, mw, mg = lim["miller_block_max"], lim["miller_warp_max"], lim["miller_group_min"]
+    miller = {"c": 0, "w": 0, "t": 0, "t4": 0}
+    for h in hs:
+        n = K * 2 * h
+        e = engine(n, mb, mw)
+        miller["t4" if e == "t" and h >= 4 and n >= mg else e] += n
+    fe = {"c": 0, "w": 0, "t": 0}
+    fe[engine(1, lim["fe_block_max"], lim["fe_warp_max"])] += 1                  # Commit's one
+    fe[engine(2 * K, lim["fe_block_max"], lim["fe_warp_max"])] += 2 * K * lr     # two per block and round
+    cm = {"c": 0, "w": 0, "t": 0}
+    cm[engine(R, lim["commit_block_max"], lim["commit_warp_max"])] += R
+    comb = sum(K * h for h in hs if K * h <= FOLD_COMB_MAX)
+    fw = lim["fold_warp_max"]
+    w_terms = K * (2 * R - 2) if not w_msm and R > G2_COMB_MAX_R else 0
     return {
-        "k_final_exp_c": ("final_exp", 1 + (2 * K * lr if 2 * K <= 256 else 0)),
-        "k_final_exp_w": ("final_exp", 2 * K * lr if 2 * K > 256 else 0),
-        "k_round_miller_c": ("miller_loop", sum(K * 2 * h for h in hs if K * 2 * h <= 1024)),
-        "k_round_miller_w": ("miller_loop", sum(K * 2 * h for h in hs if 1024 < K * 2 * h < 16384)),
-        "k_step1_miller_multi": ("miller_loop_multi4", sum(K * 2 * h for h in hs if K * 2 * h >= 1 << 18 and h >= 4)),
-        "k_step1_miller": ("miller_loop", sum(K * 2 * h for h in hs
-                                              if K * 2 * h >= 16384 and not (K * 2 * h >= 1 << 18 and h >= 4))),
-        "k_commit_miller_c": ("miller_loop", R if R <= 1024 else 0),
-        "k_commit_miller_w": ("miller_loop", R if R > 1024 else 0),
+        "k_final_exp_c": ("final_exp", fe["c"]),
+        "k_final_exp_w": ("final_exp", fe["w"]),
+        "k_final_exp_t": ("final_exp", fe["t"]),
+        "k_round_miller_c": ("miller_loop", miller["c"]),
+        "k_round_miller_w": ("miller_loop", miller["w"]),
+        "k_step1_miller_multi": ("miller_loop_multi4", miller["t4"]),
+        "k_step1_miller": ("miller_loop", miller["t"]),
+        "k_commit_miller_c": ("miller_loop", cm["c"]),
+        "k_commit_miller_w": ("miller_loop", cm["w"]),
+        "k_commit_miller": ("miller_loop", cm["t"]),
         "k_sparse_g": ("g1_mul", sum(K * min(b, 2 * h) for h in hs)),
-        "k_fold_c": ("comb_fold", sum(K * h for h in hs if K * h <= FOLD_COMB_MAX)),
-        "k_comb_chain": ("comb_chain", sum(K * h for h in hs if K * h <= FOLD_COMB_MAX)),
-        "k_comb_tab": ("comb_tab", sum(K * h for h in hs if K * h <= FOLD_COMB_MAX)),
-        "k_fold_w": (("g1_mul", "g2_mul"), sum(K * h for h in hs if FOLD_COMB_MAX < K * h <= 4096)),
-        "k_fold": (("g1_mul", "g2_mul"), sum(K * h for h in hs if K * h > 4096)),
+        "k_fold_c": ("comb_fold", comb),
+        "k_comb_chain": ("comb_chain", comb),
+        "k_comb_tab": ("comb_tab", comb),
+        "k_fold_w": (("g1_mul", "g2_mul"), sum(K * h for h in hs if FOLD_COMB_MAX < K * h <= fw)),
+        "k_fold": (("g1_mul", "g2_mul"), sum(K * h for h in hs if K * h > max(fw, FOLD_COMB_MAX))),
         "k_lamc_sum": ("lamc_term", R * M if M <= LAM_COMB_MAX_M else 0),
         "k_msm_chunk": ("msm_madd", 2 * R * M * W if M > LAM_COMB_MAX_M else 0),
         "k_msm_chunk_g2": ("g2_msm_madd", 4 * 2 * R * K * W2 if w_msm else 0),
         "k_w_comb": ("w_comb_term", K * (2 * R - 2) if not w_msm and R <= G2_COMB_MAX_R else 0),
-        "k_w_terms": ("g2_mul", K * (2 * R - 2) if not w_msm and R > G2_COMB_MAX_R and K * 2 * R > 4096 else 0),
-        "k_w_terms_w": ("g2_mul", K * (2 * R - 2) if not w_msm and R > G2_COMB_MAX_R and K * 2 * R <= 4096 else 0),
+        "k_w_terms": ("g2_mul", w_terms if K * 2 * R > lim["wterm_warp_max"] else 0),
+        "k_w_terms_w": ("g2_mul", w_terms if K * 2 * R <= lim["wterm_warp_max"] else 0),
         "k_pst_terms": ("g1_mul", M * lc // 2),
     }
 
