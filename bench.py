@@ -184,6 +184,75 @@ def step_units(log_n: int, b: int, msm_window: int, msm_window_g2: int = 16, lim
     }
 
 
+def roofline_report(prof: dict, units: dict, peak: float, t_lane: float, t_split: float, steps: int,
+                    log_n: int, b: int, total_ms: float) -> dict:
+    """The rooflines of one run from its per-kernel CUDA-event totals `prof` (name -> (launches, ms)
+    over `steps` timed steps): the dominant kernel and every kernel with a unit count against the
+    multiply-add peak `peak` (lane ops/s), and every round-structured kernel against its latency
+    bound (critical product rounds x the measured latency of one dependent product, `t_lane` on one
+    lane and `t_split` split over a block's four warps, in ns)."""
+
+    def kernel_roof(kname, cnt, kms):
+        if kname not in units or kms <= 0 or units[kname][1] <= 0:
+            return None
+        unit, n_units = units[kname]
+        per_unit = sum(FQ_MULS[u] for u in (unit if isinstance(unit, tuple) else (unit,)))
+        ops_step = n_units * per_unit * FQ_MUL_IMAD
+        launches_per_step = cnt / steps
+        avg_ms = kms / cnt
+        achieved = ops_step / launches_per_step / (avg_ms * 1e-3)
+        return {"achieved": achieved / 1e12, "frac": achieved / peak, "units_per_step": n_units, "unit_op": unit,
+                "launches_per_step": launches_per_step, "avg_launch_ms": avg_ms}
+
+    dom = max(prof.items(), key=lambda kv: kv[1][1]) if prof else ("", (0, 0.0))
+    name, (cnt, kms) = dom
+    roof = None
+    r = kernel_roof(name, cnt, kms)
+    if r:
+        roof = {"bound": "alu", "kernel": name, "achieved": r["achieved"], "peak": peak / 1e12,
+                "unit": "Tops/s (32-bit multiply-add lane ops)", "frac": r["frac"],
+                "traffic": NCU_TRAFFIC.get((log_n, b, name)),
+                "traffic_source": "ncu dram__bytes_read.sum + dram__bytes_write.sum, one capture of this kernel"
+                                  if (log_n, b, name) in NCU_TRAFFIC else None,
+                "units_per_step": r["units_per_step"], "unit_op": r["unit_op"],
+                "launches_per_step": r["launches_per_step"], "avg_launch_ms": r["avg_launch_ms"],
+                "peak_source": "measured: fp_imad_probe on this GPU in this run"}
+    roof_all = {}
+    for kname, (kc, kt) in prof.items():
+        r = kernel_roof(kname, kc, kt)
+        if r:
+            roof_all[kname] = {"frac": round(r["frac"], 4), "avg_launch_ms": round(r["avg_launch_ms"], 4),
+                               "units_per_step": r["units_per_step"], "unit_op": r["unit_op"]}
+    # latency bound of every round-structured kernel: rounds x the measured latency of one dependent
+    # product (one lane; for the split rounds, the block's four warps together); the headline is the
+    # round chain's kernel with the most time per step
+    lat_all = {}
+    for kname, (kc, kt) in prof.items():
+        if kname in CRITICAL_ROUNDS and kc and kt > 0:
+            rounds = CRITICAL_ROUNDS[kname]
+            sr = SPLIT_ROUNDS.get(kname, 0)
+            bound_ms = ((rounds - sr) * t_lane + sr * t_split) * 1e-6
+            lat_all[kname] = {"critical_rounds": rounds, "split_rounds": sr, "bound_ms": round(bound_ms, 4),
+                              "achieved_ms": round(kt / kc, 4), "frac": round(bound_ms / (kt / kc), 4),
+                              "on_round_chain": kname in CHAIN_KERNELS, "ms_per_step": round(kt / steps, 3)}
+    lat = None
+    chain = [k for k in lat_all if lat_all[k]["on_round_chain"]]
+    if chain:
+        top = max(chain, key=lambda k: lat_all[k]["ms_per_step"])
+        lat = dict(kernel=top, **lat_all[top], fq_mul_ns=t_lane, fq_mul_split_ns=t_split,
+                   note="sequential Fq-product rounds of the round chain's largest kernel x the measured "
+                        "latency of one dependent product (one lane, or split over a block's four warps for "
+                        "the split rounds); combines and inversions excluded; every such kernel in "
+                        "latency_rooflines")
+    share = {k: round(v[1] / (total_ms if total_ms else 1), 4) for k, v in
+             sorted(prof.items(), key=lambda kv: -kv[1][1])[:8]}
+    # every kernel: launches per step and mean CUDA-event time per launch (ms)
+    kernel_ms = {k: [round(v[0] / steps, 2), round(v[1] / v[0], 4)] for k, v in
+                 sorted(prof.items(), key=lambda kv: -kv[1][1]) if v[0]}
+    return {"roofline": roof, "roofline_kernels": roof_all, "latency_roofline": lat, "latency_rooflines": lat_all,
+            "kernel_share": share, "kernel_launches_and_ms": kernel_ms}
+
+
 class ClockSampler:
     """nvidia-smi clocks during the timed region (median SM clock, throttle reasons seen)."""
 
@@ -961,68 +1030,14 @@ def main():
             dist.destroy_process_group()
         return
 
-    # roofline of the dominant kernel (integer multiply-add pipe), and of every kernel with a unit count
-    peak = F.imad_peak()
+    # rooflines: the dominant kernel against the multiply-add pipe, every kernel with a unit count, and
+    # the latency bound of every round-structured kernel
     units = step_units(log_n, b, F.msm_window(pp.M, pp.R), F.msm_window_g2(2 * pp.R, -(-pp.R // b)))
-
-    def kernel_roof(kname, cnt, kms):
-        if kname not in units or kms <= 0 or units[kname][1] <= 0:
-            return None
-        unit, n_units = units[kname]
-        per_unit = sum(FQ_MULS[u] for u in (unit if isinstance(unit, tuple) else (unit,)))
-        ops_step = n_units * per_unit * FQ_MUL_IMAD
-        launches_per_step = cnt / args.steps
-        avg_ms = kms / cnt
-        achieved = ops_step / launches_per_step / (avg_ms * 1e-3)
-        return {"achieved": achieved / 1e12, "frac": achieved / peak, "units_per_step": n_units, "unit_op": unit,
-                "launches_per_step": launches_per_step, "avg_launch_ms": avg_ms}
-
-    dom = max(prof.items(), key=lambda kv: kv[1][1]) if prof else ("", (0, 0.0))
-    name, (cnt, kms) = dom
-    roof = None
-    r = kernel_roof(name, cnt, kms)
-    if r:
-        roof = {"bound": "alu", "kernel": name, "achieved": r["achieved"], "peak": peak / 1e12,
-                "unit": "Tops/s (32-bit multiply-add lane ops)", "frac": r["frac"],
-                "traffic": NCU_TRAFFIC.get((log_n, b, name)),
-                "traffic_source": "ncu dram__bytes_read.sum + dram__bytes_write.sum, one capture of this kernel"
-                                  if (log_n, b, name) in NCU_TRAFFIC else None,
-                "units_per_step": r["units_per_step"], "unit_op": r["unit_op"],
-                "launches_per_step": r["launches_per_step"], "avg_launch_ms": r["avg_launch_ms"],
-                "peak_source": "measured: fp_imad_probe on this GPU in this run"}
-    roof_all = {}
-    for kname, (kc, kt) in prof.items():
-        r = kernel_roof(kname, kc, kt)
-        if r:
-            roof_all[kname] = {"frac": round(r["frac"], 4), "avg_launch_ms": round(r["avg_launch_ms"], 4),
-                               "units_per_step": r["units_per_step"], "unit_op": r["unit_op"]}
-    # latency bound of every round-structured kernel: rounds x the measured latency of one dependent
-    # product (one lane; for the split rounds, the block's four warps together); the headline is the
-    # round chain's kernel with the most time per step
-    t_lane, t_split = F.fq_mul_latency_ns(), F.fq_mul_split_latency_ns()
-    lat_all = {}
-    for kname, (kc, kt) in prof.items():
-        if kname in CRITICAL_ROUNDS and kc and kt > 0:
-            rounds = CRITICAL_ROUNDS[kname]
-            sr = SPLIT_ROUNDS.get(kname, 0)
-            bound_ms = ((rounds - sr) * t_lane + sr * t_split) * 1e-6
-            lat_all[kname] = {"critical_rounds": rounds, "split_rounds": sr, "bound_ms": round(bound_ms, 4),
-                              "achieved_ms": round(kt / kc, 4), "frac": round(bound_ms / (kt / kc), 4),
-                              "on_round_chain": kname in CHAIN_KERNELS, "ms_per_step": round(kt / args.steps, 3)}
-    lat = None
-    chain = [k for k in lat_all if lat_all[k]["on_round_chain"]]
-    if chain:
-        top = max(chain, key=lambda k: lat_all[k]["ms_per_step"])
-        lat = dict(kernel=top, **lat_all[top], fq_mul_ns=t_lane, fq_mul_split_ns=t_split,
-                   note="sequential Fq-product rounds of the round chain's largest kernel x the measured "
-                        "latency of one dependent product (one lane, or split over a block's four warps for "
-                        "the split rounds); combines and inversions excluded; every such kernel in "
-                        "latency_rooflines")
-    share = {k: round(v[1] / (total_ms if total_ms else 1), 4) for k, v in
-             sorted(prof.items(), key=lambda kv: -kv[1][1])[:8]}
-    # every kernel: launches per step and mean CUDA-event time per launch (ms)
-    kernel_ms = {k: [round(v[0] / args.steps, 2), round(v[1] / v[0], 4)] for k, v in
-                 sorted(prof.items(), key=lambda kv: -kv[1][1]) if v[0]}
+    rep = roofline_report(prof, units, F.imad_peak(), F.fq_mul_latency_ns(), F.fq_mul_split_latency_ns(),
+                          args.steps, log_n, b, total_ms)
+    roof, roof_all, lat, lat_all = rep["roofline"], rep["roofline_kernels"], rep["latency_roofline"], \
+        rep["latency_rooflines"]
+    share, kernel_ms = rep["kernel_share"], rep["kernel_launches_and_ms"]
 
     cpu = None
     if not args.no_cpu_baseline:

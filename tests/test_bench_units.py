@@ -71,3 +71,32 @@ def test_every_unit_has_a_product_count(log_n, b):
     for kernel, (unit, n) in bench.step_units(log_n, b, 16, lim=DEFAULT_LIMITS).items():
         for x in unit if isinstance(unit, tuple) else (unit,):
             assert bench.FQ_MULS[x] > 0, (kernel, x)
+
+
+def test_roofline_report_from_event_totals():
+    """The bench line's rooflines from per-kernel CUDA-event totals: the dominant kernel's fraction is
+    its algorithmic multiply-adds per launch over its mean launch time against the peak, and every
+    round-structured kernel's latency fraction is its bound over its mean launch time."""
+    steps, peak, t_lane, t_split = 10, 12.0e12, 1380.0, 980.0
+    # name -> (launches, total ms) over `steps` steps, shaped like an N = 2^16, b = 256 run
+    prof = {"k_sparse_g": (80, 113.4), "k_final_exp_c": (90, 78.8), "k_round_miller_c": (80, 62.8),
+            "k_fold_c": (80, 15.1), "k_lamc_sum": (10, 12.4), "k_g1_pair": (330, 10.6)}
+    units = bench.step_units(16, 256, 16, lim=DEFAULT_LIMITS)
+    rep = bench.roofline_report(prof, units, peak, t_lane, t_split, steps, 16, 256, 204.0)
+    roof = rep["roofline"]
+    assert roof["kernel"] == "k_sparse_g" and roof["bound"] == "alu"
+    ops_per_launch = 510 * bench.FQ_MULS["g1_mul"] * bench.FQ_MUL_IMAD / 8
+    assert roof["frac"] == pytest.approx(ops_per_launch / (113.4 / 80 * 1e-3) / peak)
+    assert roof["traffic"] is None                       # no capture of this kernel on this build
+    lam = rep["roofline_kernels"]["k_lamc_sum"]
+    assert lam["units_per_step"] == 1 << 16
+    assert lam["frac"] == pytest.approx((1 << 16) * 352 * bench.FQ_MUL_IMAD / 1.24e-3 / peak, abs=1e-4)
+    assert "k_g1_pair" not in rep["roofline_kernels"]   # no unit count: not a roofline kernel
+    lat = rep["latency_roofline"]
+    assert lat["kernel"] == "k_final_exp_c"             # the round chain's kernel with the most time
+    fe = bench.CRITICAL_ROUNDS["k_final_exp_c"], bench.SPLIT_ROUNDS["k_final_exp_c"]
+    bound = ((fe[0] - fe[1]) * t_lane + fe[1] * t_split) * 1e-6
+    assert lat["bound_ms"] == pytest.approx(bound, abs=1e-4)
+    assert lat["frac"] == pytest.approx(bound / (78.8 / 90), abs=1e-4)
+    assert not rep["latency_rooflines"]["k_sparse_g"]["on_round_chain"]
+    assert rep["kernel_launches_and_ms"]["k_g1_pair"] == [33.0, round(10.6 / 330, 4)]
