@@ -292,7 +292,7 @@ FPG_NOINL void w_cyc_exp_wnaf4(W12& W, fq* acc, const fq* base, fq* t3, fq* t5, 
 // g = t^(p^2) t; hard part g^d with d = h1 (x + p)(x^2 + p^2 - 1) + 1, h1 = (x - 1)^2 / 3, x < 0.
 // The inverse goes through norms: n = f conj(f) lies in Fq6, u = n^(p^2) n^(p^4), and n u is the
 // norm of n to Fq2, so f^-1 = conj(f) / n = conj(f) u / (n u) and t = conj(f)^2 u (n u)^-1: six
-// lane-parallel Fq12 products, two Frobenius maps and one Fq2 inversion on one lane.  g^h1 runs on
+// lane-parallel Fq12 products, two Frobenius maps and one Fq2 inversion on a quad of lanes.  g^h1 runs on
 // the width-4 NAF of h1 (24 nonzero digits instead of 48 set bits).
 template <int NW>
 FPG_NOINL void w_final_exp(W12& W) {
