@@ -25,7 +25,7 @@ def lib(tmp_path_factory):
     subprocess.check_call([gxx, "-std=c++20", "-O1", "-shared", "-fPIC", f"-I{CSRC}", "-o", so,
                            os.path.join(HERE, "emu", "inverse.cpp")])
     L = ctypes.CDLL(so)
-    for f in (L.emu_inv_fq, L.emu_inv_fr, L.emu_inv_fq_quad, L.emu_inv_fr_quad):
+    for f in (L.emu_inv_fq, L.emu_inv_fr, L.emu_inv_fq_quad, L.emu_inv_fr_quad, L.emu_inv_fq_warp):
         f.restype = None
     return L
 
@@ -69,3 +69,22 @@ def test_quad_inverse_against_python(lib, field):
         for q in range(4):
             got = sum(r[q * n + i] << (32 * i) for i in range(n))
             assert got == want, (hex(x), q)
+
+
+def test_quad_inverse_eight_quads_of_a_warp(lib):
+    """Eight quads of one warp invert eight different values at once (zero among them): each quad's
+    lanes return its first lane's inverse, whatever the other quads do."""
+    rnd = random.Random(29)
+    n, m = 12, ref.P
+    for trial in range(6):
+        firsts = [rnd.randrange(1, m) for _ in range(8)]
+        if trial == 0:
+            firsts[3] = 0
+        lanes = [firsts[q // 4] if q % 4 == 0 else rnd.randrange(0, m) for q in range(32)]
+        xi = (ctypes.c_uint32 * (32 * n))(*[(v >> (32 * i)) & 0xFFFFFFFF for v in lanes for i in range(n)])
+        r = (ctypes.c_uint32 * (32 * n))()
+        lib.emu_inv_fq_warp(xi, r)
+        for q in range(32):
+            x = firsts[q // 4]
+            got = sum(r[q * n + i] << (32 * i) for i in range(n))
+            assert got == (pow(x, -1, m) if x else 0), (trial, q)
