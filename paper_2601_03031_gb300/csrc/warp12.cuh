@@ -345,14 +345,11 @@ FPG_NOINL void w_final_exp(W12& W) {
 // re = m0 - m1, im = m2 - m0 - m1; squares x^2: m0 = (x0 + x1)(x0 - x1), m1 = x0 x1, re = m0,
 // im = 2 m1.
 // ---------------------------------------------------------------------------------------
-// The block engine's narrow Miller rounds (up to 15 products) run one product per lane; built with
-// FPG_MILLER_SPLIT=1 they split each product over the four warps (fq_split.cuh).  Measured in the
-// whole ProveAll step the split rounds were slower (N = 2^16, b = 256: 0.82 against 0.89 ms per
-// round's Miller loops): the rounds between them are one product per lane on three warps anyway,
-// and the split's extra instructions compete with the kernels running beside the chain.
-#ifndef FPG_MILLER_SPLIT
-#define FPG_MILLER_SPLIT 0
-#endif
+// The block engine's narrow Miller rounds (up to 15 products) run one product per lane.  Split over
+// the four warps (fq_split.cuh) they were slower in the whole ProveAll step (N = 2^16, b = 256: 0.82
+// against 0.89 ms per round's Miller loops): the rounds between them are one product per lane on
+// three warps anyway, and the split's extra instructions compete with the kernels running beside the
+// chain.
 
 struct WMill {
     fq p[72];       // products of a round
@@ -541,9 +538,8 @@ FPG_NOINL void wm_dbl(WMill& S, const fq& m3x, const fq& y2) {
     wsync<NW>();
     // round B
     if (NW == 4) {
-        constexpr bool SPLIT = FPG_MILLER_SPLIT != 0;
-        if (SPLIT || L < 15) {                      // 15 products, each split over the four warps
-            const int t = SPLIT ? ((L & 31) < 15 ? (L & 31) : 0) : L;
+        if (L < 15) {                               // 15 products, one per lane
+            const int t = L;
             const fq* XX = S.v;
             const fq* YY = S.v + 2;
             const fq* YZ = S.v + 6;
@@ -559,12 +555,7 @@ FPG_NOINL void wm_dbl(WMill& S, const fq& m3x, const fq& y2) {
             else { a = YY; b = YZ; kind = t - 12; mode = 0; }                        // YY YZ
             fq x, y;
             prod_ops(x, y, a, b, kind, mode, fq_select(t < 2, m3x, y2));
-            if (SPLIT) {
-                const fq m = fq_mul_split(x, y);
-                if (L < 15) S.p[L] = m;
-            } else {
-                S.p[L] = fq_mul(x, y);
-            }
+            S.p[L] = fq_mul(x, y);
         }
         wsync<NW>();
         // the line (warp 0) and 2T (X' on warp 1, Y' on warp 2, Z' on warp 3)
@@ -650,19 +641,11 @@ FPG_NOINL void wm_add(WMill& S, const fq& mxP, const fq& yP) {
     const fq* Z = S.T + 4;
     const fq* xQ = S.Q;
     const fq* yQ = S.Q + 2;
-    constexpr bool SPLIT = NW == 4 && FPG_MILLER_SPLIT != 0;
-    // round A: yQ Z, xQ Z (the block engine splits each product over its four warps: lane t of every
-    // warp forms the operands of product t)
-    if (SPLIT || L < 6) {
-        const int t = SPLIT ? ((L & 31) < 6 ? (L & 31) : 0) : L;
+    // round A: yQ Z, xQ Z
+    if (L < 6) {
         fq x, y;
-        kara_ops(x, y, t < 3 ? yQ : xQ, Z, t % 3);
-        if (SPLIT) {
-            const fq m = fq_mul_split(x, y);
-            if (L < 6) S.p[L] = m;
-        } else {
-            S.p[L] = fq_mul(x, y);
-        }
+        kara_ops(x, y, L < 3 ? yQ : xQ, Z, L % 3);
+        S.p[L] = fq_mul(x, y);
     }
     wsync<NW>();
     if (L < 4) {                                    // theta = Y - yQ Z, lambda = X - xQ Z
@@ -673,8 +656,8 @@ FPG_NOINL void wm_add(WMill& S, const fq& mxP, const fq& yP) {
     const fq* th = S.v;
     const fq* la = S.v + 2;
     // round B: theta xQ, lambda yQ, -theta xP, lambda yP, theta^2, lambda^2
-    if (SPLIT || L < 14) {
-        const int t = SPLIT ? ((L & 31) < 14 ? (L & 31) : 0) : L;
+    if (L < 14) {
+        const int t = L;
         const fq* a;
         const fq* b;
         int kind, mode;
@@ -686,12 +669,7 @@ FPG_NOINL void wm_add(WMill& S, const fq& mxP, const fq& yP) {
         else { a = b = la; kind = t - 12; mode = 1; }
         fq x, y;
         prod_ops(x, y, a, b, kind, mode, fq_select(t < 8, mxP, yP));
-        if (SPLIT) {
-            const fq m = fq_mul_split(x, y);
-            if (L < 14) S.p[L] = m;
-        } else {
-            S.p[L] = fq_mul(x, y);
-        }
+        S.p[L] = fq_mul(x, y);
     }
     wsync<NW>();
     if (L < 10) {
@@ -747,8 +725,8 @@ FPG_NOINL void wm_add(WMill& S, const fq& mxP, const fq& yP) {
     const fq* E = S.v + 8;
     const fq* Fv = S.v + 10;
     const fq* G = S.v + 12;
-    if (SPLIT || (L >= 16 && L < 28)) {
-        const int u = SPLIT ? ((L & 31) < 12 ? (L & 31) : 0) : L - 16, which = u / 3;
+    if (L >= 16 && L < 28) {
+        const int u = L - 16, which = u / 3;
         fq H[2], GH[2];
         for (int e = 0; e < 2; e++) {
             H[e] = fq_sub(fq_add(E[e], Fv[e]), fq_dbl(G[e]));
@@ -757,12 +735,7 @@ FPG_NOINL void wm_add(WMill& S, const fq& mxP, const fq& yP) {
         fq x, y;
         kara_ops(x, y, which == 0 ? la : (which == 1 ? th : (which == 2 ? Y : Z)),
                  which == 0 ? H : (which == 1 ? GH : E), u % 3);
-        if (SPLIT) {
-            const fq m = fq_mul_split(x, y);
-            if (L < 12) S.p[L] = m;
-        } else {
-            S.p[u] = fq_mul(x, y);
-        }
+        S.p[u] = fq_mul(x, y);
     }
     wsync<NW>();
     if (L < 6) {
