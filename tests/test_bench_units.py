@@ -100,3 +100,32 @@ def test_roofline_report_from_event_totals():
     assert lat["frac"] == pytest.approx(bound / (78.8 / 90), abs=1e-4)
     assert not rep["latency_rooflines"]["k_sparse_g"]["on_round_chain"]
     assert rep["kernel_launches_and_ms"]["k_g1_pair"] == [33.0, round(10.6 / 330, 4)]
+
+
+@pytest.mark.parametrize("log_n,b", [(4, 1), (4, 4), (5, 2), (6, 8)])
+def test_units_match_the_oracles_counted_operations(log_n, b):
+    """The same counts against the operations the oracle performs (counted inside it) when it
+    commits and opens every block: Miller loops, final exponentiations, G2 multiplications (folds
+    of v and the W terms) and the commitment's terms; the GPU's sparse G1 terms are at most the
+    oracle's, which folds a dense b."""
+    import oracle as O
+    from paper_2601_03031_gb300 import inputs as I
+    pp = O.PP(log_n, 5)
+    m = I.vector(7, log_n).tobytes()
+    R = pp.R
+    K = -(-R // b)
+    O.ops_reset()
+    C, rows = O.commit(pp, m)
+    for k in range(K):
+        O.bopen(pp, C, rows, b, k)
+    ops = O.ops()
+    u = bench.step_units(log_n, b, 16, lim=DEFAULT_LIMITS)
+    assert ops["miller"] == units(u, {"miller_loop", "miller_loop_multi4"})
+    assert ops["final_exp"] == units(u, {"final_exp"})
+    g2 = sum(n for k, (unit, n) in u.items() if k in ("k_fold_c", "k_fold_w", "k_fold")) + \
+        sum(u[k][1] for k in ("k_w_comb", "k_w_terms", "k_w_terms_w"))
+    assert ops["g2_mul"] == g2
+    folds_g1 = sum(n for k, (unit, n) in u.items() if k in ("k_fold_c", "k_fold_w", "k_fold"))
+    commit_terms = u["k_lamc_sum"][1]
+    assert commit_terms == pp.R * pp.M
+    assert folds_g1 + u["k_sparse_g"][1] <= ops["g1_mul"] - commit_terms
